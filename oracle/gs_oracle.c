@@ -1,0 +1,1500 @@
+/*
+ * gs_oracle.c -- plain FP64 CPU oracle for the TMSmesh 2.0 meshing path
+ * (Liu, Chen & Lu, "Efficient and qualified mesh generation for Gaussian
+ * molecular surface using piecewise trilinear polynomial approximation").
+ *
+ * TEST INFRASTRUCTURE.  Only the test-suite, the smoke check and the
+ * benchmark's CPU-baseline leg call this code.  It shares nothing with the
+ * CUDA library: both implement the same readings of the paper independently.
+ *
+ * Everything is brute force and in the paper's order: every atom is visited
+ * for every cube and every point (no cell lists), sums run in ascending atom
+ * index, the SVD is a textbook one-sided Jacobi iteration.  Build with
+ * -O2 -ffp-contract=off and no fast-math.
+ *
+ * Parity status: every function is pinned by a test against a closed form,
+ * a library routine or brute force, except the per-cube triangulation of
+ * general (non-sphere) inputs, whose pins are invariants (closed manifold,
+ * |g - c| = 0 at points, single-valued pieces) rather than exact values.
+ */
+#include <math.h>
+#include <stdint.h>
+#include <stdlib.h>
+#include <string.h>
+
+/* ------------------------------------------------------------------ */
+/* Key format (shared *format*, not code, with the CUDA library):      */
+/*   bits  0..17 x, 18..35 y, 36..53 z  (lattice coordinates)          */
+/*   bits 54..58 type, 59..63 level                                    */
+/* type 0..2   : surface point on a cube edge along axis 0/1/2; xyz =  */
+/*               finest-lattice coords of the edge's lower endpoint    */
+/* type 8..19  : extreme point, 8 + 4*axis + 2*side + rank; xyz =      */
+/*               finest-lattice coords of the face's lower corner;     */
+/*               side 1 = the fold belongs to the cube on the + side   */
+/* type 20..31 : critical point, 20 + 4*(a+b-1) + 2*i + j for roots i  */
+/*               of the a-fold and j of the b-fold (a < b); xyz = the  */
+/*               cube's lower corner (finest lattice)                  */
+/* cube keys (own namespace): type 30, xyz at the cube's own level     */
+/* lattice-vertex keys (own namespace): type 31, finest coords, lvl 0  */
+/* ------------------------------------------------------------------ */
+#define OK_BITS 18
+#define OK_MASK ((1ull << OK_BITS) - 1)
+#define T_CUBE 30u
+#define T_VERT 31u
+
+static uint64_t okey(uint64_t x, uint64_t y, uint64_t z, unsigned type, unsigned level)
+{
+    return x | (y << 18) | (z << 36) | ((uint64_t)type << 54) | ((uint64_t)level << 59);
+}
+static void okey_xyz(uint64_t k, int64_t *x, int64_t *y, int64_t *z)
+{
+    *x = (int64_t)(k & OK_MASK);
+    *y = (int64_t)((k >> 18) & OK_MASK);
+    *z = (int64_t)((k >> 36) & OK_MASK);
+}
+static unsigned okey_level(uint64_t k) { return (unsigned)(k >> 59); }
+
+/* status codes (same meaning as the library's) */
+#define OR_OK 0
+#define OR_ERR_ARG -1
+#define OR_ERR_OOM -2
+#define OR_ERR_CAP -3
+
+/* decisions */
+#define DEC_DISCARD 0
+#define DEC_ACCEPT 1
+#define DEC_SPLIT 2
+#define DEC_FORCED 3 /* accepted because the level is max_depth */
+
+/* ================================================================== */
+/* Problem setup: eq (Gaussian1) and the neighbourhood truncation.     */
+/* ================================================================== */
+
+typedef struct {
+    int64_t n;
+    const double *xyz; /* [n,3] */
+    const double *r;   /* [n] */
+    double D, c, cutoff_rel, precision, min_edge;
+    int max_depth;
+    double *R2;     /* per-atom squared cutoff radius */
+    double pad;     /* max cutoff radius */
+    double origin[3];
+    int64_t nroot[3];
+    double h0;
+} oprob;
+
+/* Terms exp(-D(|x-xi|^2 - ri^2)) below cutoff_rel*c are dropped:
+ *   term >= cutoff_rel*c  <=>  |x-xi|^2 <= ri^2 + K/D,  K = -ln(cutoff_rel*c). */
+static double cut_K(double cutoff_rel, double c) { return -log(cutoff_rel * c); }
+
+static int oprob_init(oprob *P, int64_t n, const double *xyz, const double *r, double D, double c,
+                      double cutoff_rel, double precision, double min_edge, int max_depth)
+{
+    if (n <= 0 || !(D > 0) || !(c > 0) || !(precision > 0) || !(min_edge > 0) || max_depth < 0 ||
+        max_depth > 20 || !(cutoff_rel > 0) || !(cutoff_rel < 1))
+        return OR_ERR_ARG;
+    memset(P, 0, sizeof(*P));
+    P->n = n; P->xyz = xyz; P->r = r; P->D = D; P->c = c; P->cutoff_rel = cutoff_rel;
+    P->precision = precision; P->min_edge = min_edge; P->max_depth = max_depth;
+    P->R2 = (double *)malloc(sizeof(double) * (size_t)n);
+    if (!P->R2) return OR_ERR_OOM;
+    double K = cut_K(cutoff_rel, c);
+    double KD = K / D;
+    double lo[3] = {INFINITY, INFINITY, INFINITY}, hi[3] = {-INFINITY, -INFINITY, -INFINITY};
+    double r2max = 0;
+    for (int64_t i = 0; i < n; i++) {
+        double ri = r[i];
+        P->R2[i] = ri * ri + KD;
+        if (P->R2[i] > r2max) r2max = P->R2[i];
+        for (int a = 0; a < 3; a++) {
+            double v = xyz[3 * i + a];
+            if (!isfinite(v) || !isfinite(ri) || ri < 0) { free(P->R2); P->R2 = NULL; return OR_ERR_ARG; }
+            if (v < lo[a]) lo[a] = v;
+            if (v > hi[a]) hi[a] = v;
+        }
+    }
+    /* Root grid (section 2.2, "very coarse" initial grid): edge h0 =
+     * min_edge * 2^max_depth, origin aligned to h0, covering the atoms'
+     * bounding box grown by the largest cutoff radius. */
+    P->pad = sqrt(r2max);
+    P->h0 = ldexp(min_edge, max_depth);
+    for (int a = 0; a < 3; a++) {
+        P->origin[a] = P->h0 * floor((lo[a] - P->pad) / P->h0);
+        int64_t m = (int64_t)ceil((hi[a] + P->pad - P->origin[a]) / P->h0);
+        P->nroot[a] = m < 1 ? 1 : m;
+        if ((P->nroot[a] << max_depth) + 1 > (int64_t)OK_MASK) { free(P->R2); P->R2 = NULL; return OR_ERR_ARG; }
+    }
+    return OR_OK;
+}
+
+static void oprob_free(oprob *P) { free(P->R2); P->R2 = NULL; }
+
+/* cube edge at level l */
+static double lvl_h(const oprob *P, int l) { return ldexp(P->min_edge, P->max_depth - l); }
+/* world coordinate of lattice index i at level l along axis a */
+static double lat_x(const oprob *P, int a, int64_t i, int l) { return P->origin[a] + (double)i * lvl_h(P, l); }
+
+/* ================================================================== */
+/* Gauss-Legendre rule (nodes by Newton iteration on P_n).              */
+/* ================================================================== */
+
+static void gauss_legendre(int q, double *x, double *w)
+{
+    const double pi = 3.14159265358979323846;
+    for (int i = 0; i < q; i++) {
+        double t = cos(pi * (i + 0.75) / (q + 0.5));
+        double dp = 1;
+        for (int it = 0; it < 100; it++) {
+            double p0 = 1, p1 = t;
+            for (int k = 2; k <= q; k++) {
+                double p2 = ((2 * k - 1) * t * p1 - (k - 1) * p0) / k;
+                p0 = p1; p1 = p2;
+            }
+            /* p1 = P_q(t), p0 = P_{q-1}(t) */
+            dp = q * (t * p1 - p0) / (t * t - 1);
+            double dt = p1 / dp;
+            t -= dt;
+            if (fabs(dt) < 1e-16) break;
+        }
+        x[i] = t;
+        w[i] = 2.0 / ((1 - t * t) * dp * dp);
+    }
+}
+
+#define OR_Q 24
+static double gl_x[OR_Q], gl_w[OR_Q];
+static int gl_ready = 0;
+static void gl_init(void)
+{
+    if (!gl_ready) { gauss_legendre(OR_Q, gl_x, gl_w); gl_ready = 1; }
+}
+
+static double leg(int j, double t)
+{
+    switch (j) {
+    case 0: return 1.0;
+    case 1: return t;
+    case 2: return (3.0 * t * t - 1.0) / 2.0;
+    default: return (5.0 * t * t * t - 3.0 * t) / 2.0;
+    }
+}
+
+/* ================================================================== */
+/* Per-axis Legendre projection with the C0 endpoint correction        */
+/* (eqs poly2_1..poly2_3, the alpha/beta/gamma integrals, eqs poly3,    */
+/* condition1, pn and alpha; n = 3).                                   */
+/* f(x) = exp(-D (x - xi)^2) on [a,b]; t = (2x-(a+b))/(b-a).            */
+/* alpha_j = (2j+1)/(b-a) * int_a^b f(x) L_j(t(x)) dx                   */
+/*         = (2j+1)/2 * int_{-1}^{1} f(x(t)) L_j(t) dt                  */
+/* (the orthogonal L2 projection; the printed prefactor 2/(b-a) and     */
+/* the integrand phi(t) are read as this projection).                  */
+/* ================================================================== */
+
+void or_axis_projection(double xi, double a, double b, double D, int q, double *out4)
+{
+    double xs[64], ws[64];
+    if (q < 1) q = 1;
+    if (q > 64) q = 64;
+    gauss_legendre(q, xs, ws);
+    double m = 0.5 * (a + b), hh = 0.5 * (b - a);
+    for (int j = 0; j < 4; j++) {
+        double s = 0;
+        for (int k = 0; k < q; k++) {
+            double x = m + hh * xs[k];
+            double d = x - xi;
+            s += ws[k] * exp(-D * d * d) * leg(j, xs[k]);
+        }
+        out4[j] = 0.5 * (2 * j + 1) * s;
+    }
+}
+
+/* C0 correction: add eps0 L_2 + eps1 L_3 so that the cubic equals f at
+ * both ends (L_j(1) = 1, L_j(-1) = (-1)^j). */
+void or_axis_coeffs(double xi, double a, double b, double D, double *out4)
+{
+    gl_init();
+    double m = 0.5 * (a + b), hh = 0.5 * (b - a);
+    double al[4];
+    for (int j = 0; j < 4; j++) {
+        double s = 0;
+        for (int k = 0; k < OR_Q; k++) {
+            double d = (m + hh * gl_x[k]) - xi;
+            s += gl_w[k] * exp(-D * d * d) * leg(j, gl_x[k]);
+        }
+        al[j] = 0.5 * (2 * j + 1) * s;
+    }
+    double fa = exp(-D * (a - xi) * (a - xi));
+    double fb = exp(-D * (b - xi) * (b - xi));
+    double eR = fb - (al[0] + al[1] + al[2] + al[3]);
+    double eL = fa - (al[0] - al[1] + al[2] - al[3]);
+    double e0 = 0.5 * (eR + eL), e1 = 0.5 * (eR - eL);
+    out4[0] = al[0];
+    out4[1] = al[1];
+    out4[2] = al[2] + e0;
+    out4[3] = al[3] + e1;
+}
+
+/* squared distance from point x to the box [lo, lo+h]^3, axes in order */
+static double box_dist2(const double *lo, const double *hi, const double *x)
+{
+    double s = 0;
+    for (int a = 0; a < 3; a++) {
+        double d = 0;
+        if (lo[a] - x[a] > 0) d = lo[a] - x[a];
+        else if (x[a] - hi[a] > 0) d = x[a] - hi[a];
+        s += d * d;
+    }
+    return s;
+}
+
+/* Coefficient tensor A (eqs polynew, tensor1, tensor2): A[j][k][l] =
+ * sum_i e^{D r_i^2} atilde_j(x) btilde_k(y) gtilde_l(z), j<->x, k<->y,
+ * l<->z, over atoms whose cutoff sphere meets the box; returns the count. */
+static int64_t cube_tensor(const oprob *P, const double *lo, const double *hi, double *A)
+{
+    memset(A, 0, 64 * sizeof(double));
+    int64_t cnt = 0;
+    for (int64_t i = 0; i < P->n; i++) {
+        const double *x = P->xyz + 3 * i;
+        if (box_dist2(lo, hi, x) > P->R2[i]) continue;
+        cnt++;
+        double w = exp(P->D * P->r[i] * P->r[i]);
+        double ax[4], ay[4], az[4];
+        or_axis_coeffs(x[0], lo[0], hi[0], P->D, ax);
+        or_axis_coeffs(x[1], lo[1], hi[1], P->D, ay);
+        or_axis_coeffs(x[2], lo[2], hi[2], P->D, az);
+        for (int j = 0; j < 4; j++)
+            for (int k = 0; k < 4; k++)
+                for (int l = 0; l < 4; l++) A[16 * j + 4 * k + l] += w * ax[j] * ay[k] * az[l];
+    }
+    return cnt;
+}
+
+/* ================================================================== */
+/* One-sided (Hestenes) Jacobi SVD of an m x n matrix by rows.          */
+/* On return rows of M are mutually orthogonal and Q (m x m) holds the   */
+/* accumulated rotations: M_in = Q^T M_out.                             */
+/* ================================================================== */
+
+static void jacobi_rows(double *M, int m, int n, double *Q)
+{
+    for (int i = 0; i < m; i++)
+        for (int j = 0; j < m; j++) Q[i * m + j] = (i == j);
+    for (int sweep = 0; sweep < 80; sweep++) {
+        int rotated = 0;
+        for (int p = 0; p < m; p++)
+            for (int q = p + 1; q < m; q++) {
+                double al = 0, be = 0, ga = 0;
+                for (int k = 0; k < n; k++) {
+                    al += M[p * n + k] * M[p * n + k];
+                    be += M[q * n + k] * M[q * n + k];
+                    ga += M[p * n + k] * M[q * n + k];
+                }
+                if (ga == 0 || fabs(ga) <= 1e-15 * sqrt(al * be)) continue;
+                rotated = 1;
+                double zeta = (be - al) / (2 * ga);
+                double t = (zeta >= 0 ? 1.0 : -1.0) / (fabs(zeta) + sqrt(1 + zeta * zeta));
+                double cs = 1 / sqrt(1 + t * t), sn = cs * t;
+                for (int k = 0; k < n; k++) {
+                    double mp = M[p * n + k], mq = M[q * n + k];
+                    M[p * n + k] = cs * mp - sn * mq;
+                    M[q * n + k] = sn * mp + cs * mq;
+                }
+                for (int k = 0; k < m; k++) {
+                    double qp = Q[p * m + k], qq = Q[q * m + k];
+                    Q[p * m + k] = cs * qp - sn * qq;
+                    Q[q * m + k] = sn * qp + cs * qq;
+                }
+            }
+        if (!rotated) break;
+    }
+}
+
+/* SVD of an m x n (m <= n, m <= 4) row-major matrix: X = sum_p s_p u_p v_p^T
+ * with s sorted descending; u: [m][m] (u_p in row p), v: [m][n]. */
+void or_svd_rows(const double *X, int m, int n, double *s, double *u, double *v)
+{
+    double M[64], Q[16];
+    memcpy(M, X, sizeof(double) * (size_t)(m * n));
+    jacobi_rows(M, m, n, Q);
+    double sv[4];
+    int order[4];
+    for (int p = 0; p < m; p++) {
+        double s2 = 0;
+        for (int k = 0; k < n; k++) s2 += M[p * n + k] * M[p * n + k];
+        sv[p] = sqrt(s2);
+        order[p] = p;
+    }
+    /* stable insertion sort by descending singular value */
+    for (int i = 1; i < m; i++) {
+        int o = order[i], j = i - 1;
+        while (j >= 0 && sv[order[j]] < sv[o]) { order[j + 1] = order[j]; j--; }
+        order[j + 1] = o;
+    }
+    for (int i = 0; i < m; i++) {
+        int p = order[i];
+        s[i] = sv[p];
+        for (int k = 0; k < m; k++) u[i * m + k] = Q[p * m + k];
+        for (int k = 0; k < n; k++) v[i * n + k] = sv[p] > 0 ? M[p * n + k] / sv[p] : 0.0;
+    }
+}
+
+/* exact range of the cubic sum_j c_j L_j(t) on [-1,1]: endpoints and the
+ * real zeros of the derivative inside the interval */
+void or_cubic_bounds(const double *cf, double *lo, double *hi)
+{
+    double c0 = cf[0], c1 = cf[1], c2 = cf[2], c3 = cf[3];
+    double m0 = c0 - 0.5 * c2, m1 = c1 - 1.5 * c3, m2 = 1.5 * c2, m3 = 2.5 * c3;
+    double vals[4];
+    int nv = 0;
+    vals[nv++] = c0 + c1 + c2 + c3;
+    vals[nv++] = c0 - c1 + c2 - c3;
+    /* p'(t) = m1 + 2 m2 t + 3 m3 t^2 */
+    double A2 = 3 * m3, B2 = 2 * m2, C2 = m1;
+    double roots[2];
+    int nr = 0;
+    if (A2 == 0) {
+        if (B2 != 0) roots[nr++] = -C2 / B2;
+    } else {
+        double disc = B2 * B2 - 4 * A2 * C2;
+        if (disc >= 0) {
+            double sq = sqrt(disc);
+            double qq = -0.5 * (B2 + (B2 >= 0 ? sq : -sq));
+            if (qq != 0) { roots[nr++] = qq / A2; roots[nr++] = C2 / qq; }
+            else roots[nr++] = 0.0; /* B2 == 0 and disc == 0 -> C2 == 0 */
+        }
+    }
+    for (int i = 0; i < nr; i++) {
+        double t = roots[i];
+        if (t > -1 && t < 1) vals[nv++] = m0 + t * (m1 + t * (m2 + t * m3));
+    }
+    double a = vals[0], b = vals[0];
+    for (int i = 1; i < nv; i++) { if (vals[i] < a) a = vals[i]; if (vals[i] > b) b = vals[i]; }
+    *lo = a; *hi = b;
+}
+
+/* smallest j with sum_{i<=j} s_i >= 0.99 * sum s (eq SVD3); returns count */
+static int rank99(const double *s, int m)
+{
+    double tot = 0;
+    for (int i = 0; i < m; i++) tot += s[i];
+    double acc = 0;
+    for (int j = 0; j < m; j++) {
+        acc += s[j];
+        if (acc >= 0.99 * tot) return j + 1;
+    }
+    return m;
+}
+
+/* ================================================================== */
+/* Bounds of Ptilde on the cube (section 2.2.2): two-level truncated    */
+/* SVD (eqs matrix1, SVD1-SVD7), 1-D cubic bounds, interval products,    */
+/* residual bound (eq bound1), U and L (eqs bound2, bound3).             */
+/* Unfolding read as A1[j][4k+l] (rows follow x, as U^i(x) requires).    */
+/* out[0]=L out[1]=U out[2]=sum|R| out[3]=sum of |high-order| entries    */
+/* out[4]=rank j  out[5]=sum of inner ranks                              */
+/* ================================================================== */
+
+void or_bounds(const double *A, double *out)
+{
+    double s[4], u[16], v[64];
+    or_svd_rows(A, 4, 16, s, u, v);
+    double high = 0;
+    for (int j = 0; j < 4; j++)
+        for (int k = 0; k < 4; k++)
+            for (int l = 0; l < 4; l++)
+                if (j >= 2 || k >= 2 || l >= 2) high += fabs(A[16 * j + 4 * k + l]);
+    double stot = s[0] + s[1] + s[2] + s[3];
+    if (stot == 0) {
+        out[0] = out[1] = out[2] = 0; out[3] = high; out[4] = 0; out[5] = 0;
+        return;
+    }
+    int jr = rank99(s, 4);
+    double At[64];
+    memset(At, 0, sizeof(At));
+    double M = 0, m = 0;
+    int inner = 0;
+    for (int i = 0; i < jr; i++) {
+        double Vi[16], d[4], w[16], z[16];
+        for (int k = 0; k < 4; k++)
+            for (int l = 0; l < 4; l++) Vi[4 * k + l] = v[16 * i + 4 * k + l];
+        or_svd_rows(Vi, 4, 4, d, w, z);
+        int ji = rank99(d, 4);
+        inner += ji;
+        double Myz = 0, myz = 0;
+        for (int k = 0; k < ji; k++) {
+            double ly, hy, lz, hz;
+            or_cubic_bounds(w + 4 * k, &ly, &hy);
+            or_cubic_bounds(z + 4 * k, &lz, &hz);
+            double p[4] = {hy * hz, hy * lz, ly * hz, ly * lz};
+            double pmx = p[0], pmn = p[0];
+            for (int t = 1; t < 4; t++) { if (p[t] > pmx) pmx = p[t]; if (p[t] < pmn) pmn = p[t]; }
+            Myz += d[k] * pmx;
+            myz += d[k] * pmn;
+            for (int a = 0; a < 4; a++)
+                for (int b = 0; b < 4; b++)
+                    for (int cc = 0; cc < 4; cc++)
+                        At[16 * a + 4 * b + cc] += s[i] * u[4 * i + a] * d[k] * w[4 * k + b] * z[4 * k + cc];
+        }
+        double lx, hx;
+        or_cubic_bounds(u + 4 * i, &lx, &hx);
+        double p[4] = {hx * Myz, hx * myz, lx * Myz, lx * myz};
+        double pmx = p[0], pmn = p[0];
+        for (int t = 1; t < 4; t++) { if (p[t] > pmx) pmx = p[t]; if (p[t] < pmn) pmn = p[t]; }
+        M += s[i] * pmx;
+        m += s[i] * pmn;
+    }
+    double sr = 0;
+    for (int t = 0; t < 64; t++) sr += fabs(A[t] - At[t]);
+    out[0] = m - sr;
+    out[1] = M + sr;
+    out[2] = sr;
+    out[3] = high;
+    out[4] = jr;
+    out[5] = inner;
+}
+
+/* Decision (steps 1-3 of section 2.2, reading: bound test first, then the
+ * trilinear-fit test, forced acceptance at max_depth). */
+int or_decide(const double *A, double c, double precision, int level, int max_depth, double *out6)
+{
+    or_bounds(A, out6);
+    double L = out6[0], U = out6[1];
+    if (out6[4] == 0) return DEC_DISCARD; /* A == 0 */
+    if (!(L <= c && c <= U)) return DEC_DISCARD;
+    if (out6[3] <= precision) return DEC_ACCEPT;
+    if (level >= max_depth) return DEC_FORCED;
+    return DEC_SPLIT;
+}
+
+/* ================================================================== */
+/* Field at points (eq Gaussian1, same truncation, point distance).      */
+/* ================================================================== */
+
+static double phi_at(const oprob *P, const double *x, double *grad)
+{
+    double s = 0, g0 = 0, g1 = 0, g2 = 0;
+    for (int64_t i = 0; i < P->n; i++) {
+        const double *xi = P->xyz + 3 * i;
+        double dx = x[0] - xi[0], dy = x[1] - xi[1], dz = x[2] - xi[2];
+        double d2 = dx * dx + dy * dy + dz * dz;
+        if (d2 > P->R2[i]) continue;
+        double t = exp(-P->D * (d2 - P->r[i] * P->r[i]));
+        s += t;
+        g0 += -2 * P->D * dx * t;
+        g1 += -2 * P->D * dy * t;
+        g2 += -2 * P->D * dz * t;
+    }
+    if (grad) { grad[0] = g0; grad[1] = g1; grad[2] = g2; }
+    return s;
+}
+
+/* ================================================================== */
+/* Sorted uint64 sets                                                   */
+/* ================================================================== */
+
+static int cmp_u64(const void *a, const void *b)
+{
+    uint64_t x = *(const uint64_t *)a, y = *(const uint64_t *)b;
+    return x < y ? -1 : x > y;
+}
+static int64_t find_u64(const uint64_t *arr, int64_t n, uint64_t k)
+{
+    int64_t lo = 0, hi = n - 1;
+    while (lo <= hi) {
+        int64_t mid = (lo + hi) / 2;
+        if (arr[mid] == k) return mid;
+        if (arr[mid] < k) lo = mid + 1; else hi = mid - 1;
+    }
+    return -1;
+}
+static int64_t sort_unique(uint64_t *a, int64_t n)
+{
+    if (n <= 0) return 0;
+    qsort(a, (size_t)n, sizeof(uint64_t), cmp_u64);
+    int64_t m = 1;
+    for (int64_t i = 1; i < n; i++)
+        if (a[i] != a[m - 1]) a[m++] = a[i];
+    return m;
+}
+
+typedef struct { uint64_t *a; int64_t n, cap; } vec64;
+static int v_push(vec64 *v, uint64_t x)
+{
+    if (v->n == v->cap) {
+        int64_t nc = v->cap ? 2 * v->cap : 1024;
+        uint64_t *p = (uint64_t *)realloc(v->a, sizeof(uint64_t) * (size_t)nc);
+        if (!p) return OR_ERR_OOM;
+        v->a = p; v->cap = nc;
+    }
+    v->a[v->n++] = x;
+    return OR_OK;
+}
+
+/* ================================================================== */
+/* Adaptive partition (steps 1-3 of section 2.2), level by level.        */
+/* ================================================================== */
+
+typedef struct {
+    int64_t examined[21], discarded[21], accepted[21], forced[21], split[21];
+    int64_t pair_terms;       /* (cube, atom) terms inside the cutoff */
+    int64_t conformity_splits;
+    int64_t vertex_terms;
+    int64_t n_vertices_lattice;
+    int64_t n_cubes_final, n_cubes_surface;
+    int64_t open_faces, degenerate_ears, loop_errors;
+    double min_margin;        /* smallest |c-L|,|U-c|,|precision-high| seen (relative) */
+} ostats;
+
+static void cube_box(const oprob *P, uint64_t key, double *lo, double *hi)
+{
+    int64_t x, y, z;
+    okey_xyz(key, &x, &y, &z);
+    int l = (int)okey_level(key);
+    int64_t ix[3] = {x, y, z};
+    for (int a = 0; a < 3; a++) {
+        lo[a] = lat_x(P, a, ix[a], l);
+        hi[a] = lat_x(P, a, ix[a] + 1, l);
+    }
+}
+
+static int partition(const oprob *P, vec64 *accepted, ostats *st, uint8_t *dec_log_unused)
+{
+    (void)dec_log_unused;
+    vec64 cur = {0}, nxt = {0};
+    for (int64_t z = 0; z < P->nroot[2]; z++)
+        for (int64_t y = 0; y < P->nroot[1]; y++)
+            for (int64_t x = 0; x < P->nroot[0]; x++)
+                if (v_push(&cur, okey((uint64_t)x, (uint64_t)y, (uint64_t)z, T_CUBE, 0))) return OR_ERR_OOM;
+    st->min_margin = INFINITY;
+    for (int l = 0; l <= P->max_depth && cur.n > 0; l++) {
+        st->examined[l] = cur.n;
+        nxt.n = 0;
+        for (int64_t q = 0; q < cur.n; q++) {
+            double lo[3], hi[3], A[64], o6[6];
+            cube_box(P, cur.a[q], lo, hi);
+            st->pair_terms += cube_tensor(P, lo, hi, A);
+            int d = or_decide(A, P->c, P->precision, l, P->max_depth, o6);
+            if (o6[4] > 0) {
+                double scale = fabs(P->c) + fabs(o6[0]) + fabs(o6[1]);
+                double mg = fmin(fabs(P->c - o6[0]), fabs(o6[1] - P->c)) / scale;
+                if (d != DEC_DISCARD) mg = fmin(mg, fabs(P->precision - o6[3]) / (P->precision + o6[3]));
+                if (mg < st->min_margin) st->min_margin = mg;
+            }
+            if (d == DEC_DISCARD) { st->discarded[l]++; continue; }
+            if (d == DEC_ACCEPT || d == DEC_FORCED) {
+                if (d == DEC_ACCEPT) st->accepted[l]++; else st->forced[l]++;
+                if (v_push(accepted, cur.a[q])) return OR_ERR_OOM;
+                continue;
+            }
+            st->split[l]++;
+            int64_t x, y, zz;
+            okey_xyz(cur.a[q], &x, &y, &zz);
+            for (int c8 = 0; c8 < 8; c8++)
+                if (v_push(&nxt, okey((uint64_t)(2 * x + (c8 & 1)), (uint64_t)(2 * y + ((c8 >> 1) & 1)),
+                                      (uint64_t)(2 * zz + ((c8 >> 2) & 1)), T_CUBE, (unsigned)(l + 1))))
+                    return OR_ERR_OOM;
+        }
+        vec64 t = cur; cur = nxt; nxt = t;
+    }
+    free(cur.a); free(nxt.a);
+    return OR_OK;
+}
+
+/* ================================================================== */
+/* Mixed-size neighbours (section 2.3: points of neighbouring cubes     */
+/* inside the current cube must be considered).  Reading: an accepted   */
+/* cube that touches a finer accepted cube along a face or an edge is    */
+/* split into 8 accepted children, until no such contact remains; all    */
+/* surface points on shared faces and edges then come from cubes of one  */
+/* size.                                                                 */
+/* ================================================================== */
+
+static int touches_finer(const uint64_t *S, int64_t n, uint64_t key, int max_depth)
+{
+    int64_t x, y, z;
+    okey_xyz(key, &x, &y, &z);
+    int l = (int)okey_level(key);
+    for (int lf = l + 1; lf <= max_depth; lf++) {
+        int64_t s = (int64_t)1 << (lf - l);
+        int64_t I0[3] = {x * s, y * s, z * s};
+        for (int64_t a = -1; a <= s; a++)
+            for (int64_t b = -1; b <= s; b++)
+                for (int64_t cc = -1; cc <= s; cc++) {
+                    int out = (a < 0 || a >= s) + (b < 0 || b >= s) + (cc < 0 || cc >= s);
+                    if (out == 0 || out == 3) continue;
+                    int64_t X = I0[0] + a, Y = I0[1] + b, Z = I0[2] + cc;
+                    if (X < 0 || Y < 0 || Z < 0) continue;
+                    if (find_u64(S, n, okey((uint64_t)X, (uint64_t)Y, (uint64_t)Z, T_CUBE, (unsigned)lf)) >= 0)
+                        return 1;
+                }
+    }
+    return 0;
+}
+
+static int conformity(const oprob *P, vec64 *S, ostats *st)
+{
+    for (int pass = 0; pass < 64; pass++) {
+        S->n = sort_unique(S->a, S->n);
+        vec64 out = {0};
+        int64_t splits = 0;
+        for (int64_t i = 0; i < S->n; i++) {
+            uint64_t k = S->a[i];
+            int l = (int)okey_level(k);
+            if (l < P->max_depth && touches_finer(S->a, S->n, k, P->max_depth)) {
+                int64_t x, y, z;
+                okey_xyz(k, &x, &y, &z);
+                for (int c8 = 0; c8 < 8; c8++)
+                    if (v_push(&out, okey((uint64_t)(2 * x + (c8 & 1)), (uint64_t)(2 * y + ((c8 >> 1) & 1)),
+                                          (uint64_t)(2 * z + ((c8 >> 2) & 1)), T_CUBE, (unsigned)(l + 1))))
+                        return OR_ERR_OOM;
+                splits++;
+            } else if (v_push(&out, k)) return OR_ERR_OOM;
+        }
+        free(S->a);
+        *S = out;
+        st->conformity_splits += splits;
+        if (splits == 0) { S->n = sort_unique(S->a, S->n); return OR_OK; }
+    }
+    return OR_ERR_CAP;
+}
+
+/* ================================================================== */
+/* Per-cube trilinear surface (eq linear1) and its triangulation         */
+/* (section 2.3, eqs intersection, curve, fold1, critical).              */
+/* Local coordinates in [0,1]^3; corner v = bx + 2 by + 4 bz.            */
+/* ================================================================== */
+
+typedef struct {
+    double p[3];   /* local coords */
+    uint64_t key;
+    int kind;      /* 0 edge point, 1 own extreme point, 2 neighbour's extreme point, 3 critical point */
+    int nb[4];     /* fold neighbours: extreme point -> nb[0]; critical point -> +a, -a, +b, -b */
+    int fa, fb;    /* critical point: the two fold axes (fa < fb) */
+    int rh;        /* critical point: (+a, +b, outward normal) is right-handed */
+} opoint;
+
+#define MAXP 64
+#ifdef OR_DEBUG
+#include <stdio.h>
+#define LOOPERR(site) do { st->loop_errors++; fprintf(stderr, "looperr site %d cube %llx\n", site, (unsigned long long)ckey); } while (0)
+#else
+#define LOOPERR(site) (st->loop_errors++)
+#endif
+
+/* other two axes of a in increasing order */
+static void other_axes(int a, int *u, int *v)
+{
+    *u = a == 0 ? 1 : 0;
+    *v = a == 2 ? 1 : 2;
+}
+
+/* corner value with per-axis bits */
+static double gv(const double *g, int bx, int by, int bz) { return g[bx | (by << 1) | (bz << 2)]; }
+
+/* Fold lines along axis a (eq fold1): g = A(u,v) + s B(u,v) with s the
+ * coordinate along a; the fold set {dg/ds = 0, g = c} = {B = 0, A = c} is a
+ * set of segments parallel to a at the (u,v) roots.  Returns the roots that
+ * lie strictly inside the unit square, ordered by u then v. */
+static int fold_roots(const double *g, int a, double c, double ru[2], double rv[2])
+{
+    int ua, va;
+    other_axes(a, &ua, &va);
+    double A00, A10, A01, A11, B00, B10, B01, B11;
+    int b[3];
+    double F0[4], F1[4];
+    for (int iv = 0; iv < 2; iv++)
+        for (int iu = 0; iu < 2; iu++) {
+            b[a] = 0; b[ua] = iu; b[va] = iv;
+            F0[iu + 2 * iv] = gv(g, b[0], b[1], b[2]);
+            b[a] = 1;
+            F1[iu + 2 * iv] = gv(g, b[0], b[1], b[2]);
+        }
+    A00 = F0[0]; A10 = F0[1]; A01 = F0[2]; A11 = F0[3];
+    B00 = F1[0] - F0[0]; B10 = F1[1] - F0[1]; B01 = F1[2] - F0[2]; B11 = F1[3] - F0[3];
+    /* bilinear monomials: A = a0 + a1 u + a2 v + a3 uv (minus c), B likewise */
+    double a0 = A00 - c, a1 = A10 - A00, a2 = A01 - A00, a3 = A11 - A10 - A01 + A00;
+    double b0 = B00, b1 = B10 - B00, b2 = B01 - B00, b3 = B11 - B10 - B01 + B00;
+    if (b0 == 0 && b1 == 0 && b2 == 0 && b3 == 0) return 0; /* g independent of s: no fold */
+    /* eliminate v: from B = 0, v (b2 + b3 u) = -(b0 + b1 u);  A = 0 gives
+     * (a0 + a1 u)(b2 + b3 u) - (a2 + a3 u)(b0 + b1 u) = 0 */
+    double q2 = a1 * b3 - a3 * b1;
+    double q1 = a0 * b3 + a1 * b2 - a2 * b1 - a3 * b0;
+    double q0 = a0 * b2 - a2 * b0;
+    double us[2];
+    int nu = 0;
+    if (q2 == 0) {
+        if (q1 != 0) us[nu++] = -q0 / q1;
+    } else {
+        double disc = q1 * q1 - 4 * q2 * q0;
+        if (disc >= 0) {
+            double sq = sqrt(disc);
+            double qq = -0.5 * (q1 + (q1 >= 0 ? sq : -sq));
+            if (qq != 0) { us[nu++] = qq / q2; us[nu++] = q0 / qq; }
+            else us[nu++] = 0.0;
+            if (nu == 2 && us[0] == us[1]) nu = 1;
+        }
+    }
+    /* both end faces must carry a face curve for the segment to end on it */
+    int f0in = 0, f1in = 0;
+    for (int k = 0; k < 4; k++) { f0in += F0[k] >= c; f1in += F1[k] >= c; }
+    if (f0in == 0 || f0in == 4 || f1in == 0 || f1in == 4) return 0;
+    double sa = fabs(a0) + fabs(a1) + fabs(a2) + fabs(a3);
+    double sb = fabs(b0) + fabs(b1) + fabs(b2) + fabs(b3);
+    int nr = 0;
+    for (int i = 0; i < nu; i++) {
+        double u = us[i];
+        if (!(u > 0 && u < 1)) continue;
+        /* v from B = 0 or from A = c, whichever is better conditioned at u
+         * (B = 0 degenerates when B has a factor (b2 + b3 u) vanishing at the
+         * root; A = c likewise); keep a candidate only if it solves both */
+        double dB = b2 + b3 * u, dA = a2 + a3 * u;
+        double cand[2];
+        int nc = 0;
+        if (fabs(dB) >= fabs(dA)) {
+            if (dB != 0) cand[nc++] = -(b0 + b1 * u) / dB;
+            if (dA != 0) cand[nc++] = -(a0 + a1 * u) / dA;
+        } else {
+            if (dA != 0) cand[nc++] = -(a0 + a1 * u) / dA;
+            if (dB != 0) cand[nc++] = -(b0 + b1 * u) / dB;
+        }
+        for (int k = 0; k < nc; k++) {
+            double v = cand[k];
+            if (!(v > 0 && v < 1)) continue;
+            if (fabs(a0 + a1 * u + a2 * v + a3 * u * v) > 1e-9 * sa) continue;
+            if (fabs(b0 + b1 * u + b2 * v + b3 * u * v) > 1e-9 * sb) continue;
+            ru[nr] = u; rv[nr] = v; nr++;
+            break;
+        }
+    }
+    if (nr == 2 && (ru[1] < ru[0] || (ru[1] == ru[0] && rv[1] < rv[0]))) {
+        double t = ru[0]; ru[0] = ru[1]; ru[1] = t;
+        t = rv[0]; rv[0] = rv[1]; rv[1] = t;
+    }
+    return nr;
+}
+
+typedef struct {
+    const oprob *P;
+    const uint64_t *cubes; int64_t ncubes;
+    const uint64_t *vkeys; const double *vphi; int64_t nv;
+} omesh_ctx;
+
+static int lookup_phi(const omesh_ctx *M, int64_t X, int64_t Y, int64_t Z, double *out)
+{
+    if (X < 0 || Y < 0 || Z < 0) return 0;
+    int64_t i = find_u64(M->vkeys, M->nv, okey((uint64_t)X, (uint64_t)Y, (uint64_t)Z, T_VERT, 0));
+    if (i < 0) return 0;
+    *out = M->vphi[i];
+    return 1;
+}
+
+/* 8 corner values of the level-l cube at lattice (x,y,z); 0 if missing */
+static int cube_values(const omesh_ctx *M, int l, int64_t x, int64_t y, int64_t z, double *g)
+{
+    int64_t s = (int64_t)1 << (M->P->max_depth - l);
+    for (int v = 0; v < 8; v++)
+        if (!lookup_phi(M, (x + (v & 1)) * s, (y + ((v >> 1) & 1)) * s, (z + ((v >> 2) & 1)) * s, &g[v]))
+            return 0;
+    return 1;
+}
+
+typedef struct { uint64_t k[3]; int64_t piece; } otri;
+typedef struct { otri *t; int64_t n, cap; int64_t piece; } vtri;
+static int t_push(vtri *v, uint64_t a, uint64_t b, uint64_t c)
+{
+    if (v->n == v->cap) {
+        int64_t nc = v->cap ? 2 * v->cap : 1024;
+        otri *p = (otri *)realloc(v->t, sizeof(otri) * (size_t)nc);
+        if (!p) return OR_ERR_OOM;
+        v->t = p; v->cap = nc;
+    }
+    v->t[v->n].k[0] = a; v->t[v->n].k[1] = b; v->t[v->n].k[2] = c;
+    v->t[v->n].piece = v->piece;
+    v->n++;
+    return OR_OK;
+}
+
+typedef struct { uint64_t key; double x[3]; } overt;
+typedef struct { overt *p; int64_t n, cap; } vvert;
+static int p_push(vvert *v, uint64_t key, const double *x)
+{
+    if (v->n == v->cap) {
+        int64_t nc = v->cap ? 2 * v->cap : 1024;
+        overt *p = (overt *)realloc(v->p, sizeof(overt) * (size_t)nc);
+        if (!p) return OR_ERR_OOM;
+        v->p = p; v->cap = nc;
+    }
+    v->p[v->n].key = key;
+    memcpy(v->p[v->n].x, x, sizeof(double) * 3);
+    v->n++;
+    return OR_OK;
+}
+
+/* 2-D orientation of (a,b,c) in the plane of axes (i,j) */
+static double orient2(const double *a, const double *b, const double *c, int i, int j)
+{
+    return (b[i] - a[i]) * (c[j] - a[j]) - (b[j] - a[j]) * (c[i] - a[i]);
+}
+
+/* Ear clipping (two-ears theorem; Meisters) of one single-valued piece,
+ * projected along the axis of largest |Newell normal|.  The clipped ear is
+ * always the valid (convex, empty) ear whose tip has the smallest key. */
+static int ear_clip(const opoint *pts, const int *poly, int n, vtri *tris, ostats *st)
+{
+    double N[3] = {0, 0, 0};
+    for (int i = 0; i < n; i++) {
+        const double *p = pts[poly[i]].p, *q = pts[poly[(i + 1) % n]].p;
+        N[0] += (p[1] - q[1]) * (p[2] + q[2]);
+        N[1] += (p[2] - q[2]) * (p[0] + q[0]);
+        N[2] += (p[0] - q[0]) * (p[1] + q[1]);
+    }
+    int k = 0;
+    if (fabs(N[1]) > fabs(N[k])) k = 1;
+    if (fabs(N[2]) > fabs(N[k])) k = 2;
+    int ia = (k + 1) % 3, ib = (k + 2) % 3;
+    double sg = N[k] >= 0 ? 1.0 : -1.0;
+    int idx[MAXP];
+    int m = n;
+    for (int i = 0; i < n; i++) idx[i] = poly[i];
+    while (m > 3) {
+        int best = -1, fb = -1;
+        for (int i = 0; i < m; i++) {
+            int a = idx[(i + m - 1) % m], b = idx[i], c = idx[(i + 1) % m];
+            double cr = sg * orient2(pts[a].p, pts[b].p, pts[c].p, ia, ib);
+            if (fb < 0 || pts[b].key < pts[idx[fb]].key) fb = i;
+            if (!(cr > 0)) continue;
+            int empty = 1;
+            for (int j = 0; j < m && empty; j++) {
+                int d = idx[j];
+                if (d == a || d == b || d == c) continue;
+                const double *pd = pts[d].p;
+                double s1 = sg * orient2(pts[a].p, pts[b].p, pd, ia, ib);
+                double s2 = sg * orient2(pts[b].p, pts[c].p, pd, ia, ib);
+                double s3 = sg * orient2(pts[c].p, pts[a].p, pd, ia, ib);
+                if (s1 >= 0 && s2 >= 0 && s3 >= 0) empty = 0;
+            }
+            if (!empty) continue;
+            if (best < 0 || pts[b].key < pts[idx[best]].key) best = i;
+        }
+        if (best < 0) { best = fb; st->degenerate_ears++; }
+        int a = idx[(best + m - 1) % m], b = idx[best], c = idx[(best + 1) % m];
+        if (a != b && b != c && a != c)
+            if (t_push(tris, pts[a].key, pts[b].key, pts[c].key)) return OR_ERR_OOM;
+        for (int j = best; j < m - 1; j++) idx[j] = idx[j + 1];
+        m--;
+    }
+    if (m == 3 && idx[0] != idx[1] && idx[1] != idx[2] && idx[0] != idx[2])
+        if (t_push(tris, pts[idx[0]].key, pts[idx[1]].key, pts[idx[2]].key)) return OR_ERR_OOM;
+    return OR_OK;
+}
+
+static int new_point(opoint *pts, int *np, int kind)
+{
+    if (*np >= MAXP) return -1;
+    opoint *p = &pts[*np];
+    memset(p, 0, sizeof(*p));
+    p->kind = kind;
+    p->nb[0] = p->nb[1] = p->nb[2] = p->nb[3] = -1;
+    return (*np)++;
+}
+
+static int triangulate_cube(const omesh_ctx *M, uint64_t ckey, vtri *tris, vvert *verts, ostats *st)
+{
+    const oprob *P = M->P;
+    int l = (int)okey_level(ckey);
+    int64_t cx, cy, cz;
+    okey_xyz(ckey, &cx, &cy, &cz);
+    int64_t s = (int64_t)1 << (P->max_depth - l);
+    int64_t C[3] = {cx, cy, cz};
+    double g[8];
+    if (!cube_values(M, l, cx, cy, cz, g)) return OR_ERR_CAP;
+    double c = P->c;
+    int nin = 0;
+    for (int v = 0; v < 8; v++) nin += g[v] >= c;
+    if (nin == 0 || nin == 8) return OR_OK;
+    st->n_cubes_surface++;
+
+    opoint pts[MAXP];
+    int np = 0;
+    /* edge points (eq intersection): eid[a][o1][o2], o1/o2 = bits of the
+     * other two axes in increasing axis order */
+    int eid[3][2][2];
+    for (int a = 0; a < 3; a++) {
+        int ua, va;
+        other_axes(a, &ua, &va);
+        for (int o1 = 0; o1 < 2; o1++)
+            for (int o2 = 0; o2 < 2; o2++) {
+                int b0[3], b1[3];
+                b0[a] = 0; b1[a] = 1; b0[ua] = b1[ua] = o1; b0[va] = b1[va] = o2;
+                double g0 = gv(g, b0[0], b0[1], b0[2]), g1 = gv(g, b1[0], b1[1], b1[2]);
+                eid[a][o1][o2] = -1;
+                if ((g0 >= c) == (g1 >= c)) continue;
+                int id = new_point(pts, &np, 0);
+                opoint *p = &pts[id];
+                p->p[a] = (c - g0) / (g1 - g0); p->p[ua] = o1; p->p[va] = o2;
+                int64_t L[3];
+                L[a] = C[a] * s; L[ua] = (C[ua] + o1) * s; L[va] = (C[va] + o2) * s;
+                p->key = okey((uint64_t)L[0], (uint64_t)L[1], (uint64_t)L[2], (unsigned)a, (unsigned)l);
+                eid[a][o1][o2] = id;
+            }
+    }
+    /* Own fold lines (eq fold1) along each axis: a segment across the cube
+     * whose ends on the two faces normal to the axis are extreme points
+     * (eq curve).  A neighbour's folds end on the face it shares with this
+     * cube; they become further points of that face curve. */
+    int fp[3][2][4];
+    int nfp[3][2] = {{0, 0}, {0, 0}, {0, 0}};
+    double fr[3][2][2];   /* own roots: fr[a][r] = (u, v) */
+    int fend[3][2][2];    /* own fold ends: fend[a][r][side] */
+    int nfr[3];
+    for (int a = 0; a < 3; a++) {
+        int ua, va;
+        other_axes(a, &ua, &va);
+        double ru[2], rv[2];
+        nfr[a] = fold_roots(g, a, c, ru, rv);
+        for (int r = 0; r < nfr[a]; r++) {
+            fr[a][r][0] = ru[r]; fr[a][r][1] = rv[r];
+            for (int sd = 0; sd < 2; sd++) {
+                int id = new_point(pts, &np, 1);
+                if (id < 0) return OR_ERR_CAP;
+                opoint *p = &pts[id];
+                p->p[a] = sd; p->p[ua] = ru[r]; p->p[va] = rv[r];
+                int64_t L[3] = {C[0] * s, C[1] * s, C[2] * s};
+                L[a] = (C[a] + sd) * s;
+                /* face at sd=0: this cube lies on its + side; sd=1: - side */
+                unsigned type = 8u + 4u * (unsigned)a + 2u * (unsigned)(sd == 0) + (unsigned)r;
+                p->key = okey((uint64_t)L[0], (uint64_t)L[1], (uint64_t)L[2], type, (unsigned)l);
+                fend[a][r][sd] = id;
+                fp[a][sd][nfp[a][sd]++] = id;
+            }
+        }
+        for (int sd = 0; sd < 2; sd++) {
+            int64_t N[3] = {C[0], C[1], C[2]};
+            N[a] += sd ? 1 : -1;
+            if (N[a] < 0) continue;
+            uint64_t nk = okey((uint64_t)N[0], (uint64_t)N[1], (uint64_t)N[2], T_CUBE, (unsigned)l);
+            if (find_u64(M->cubes, M->ncubes, nk) < 0) continue;
+            double gn[8];
+            if (!cube_values(M, l, N[0], N[1], N[2], gn)) return OR_ERR_CAP;
+            double nu_[2], nv_[2];
+            int nn = fold_roots(gn, a, c, nu_, nv_);
+            for (int r = 0; r < nn; r++) {
+                int id = new_point(pts, &np, 2);
+                if (id < 0) return OR_ERR_CAP;
+                opoint *p = &pts[id];
+                p->p[a] = sd; p->p[ua] = nu_[r]; p->p[va] = nv_[r];
+                int64_t L[3] = {C[0] * s, C[1] * s, C[2] * s};
+                L[a] = (C[a] + sd) * s;
+                /* the neighbour lies on the + side of the shared face iff sd = 1 */
+                unsigned type = 8u + 4u * (unsigned)a + 2u * (unsigned)(sd == 1) + (unsigned)r;
+                p->key = okey((uint64_t)L[0], (uint64_t)L[1], (uint64_t)L[2], type, (unsigned)l);
+                fp[a][sd][nfp[a][sd]++] = id;
+            }
+        }
+    }
+
+    /* Critical points (eq critical): in the slice through an a-fold line
+     * normal to a third axis, the level set of the bilinear slice function
+     * is a pair of crossing lines, so fold lines of two axes meet whenever
+     * their roots share the coordinate of the remaining axis. */
+    int chain[3][2][4];   /* points along each own fold line, ordered by the fold coordinate */
+    int nch[3][2];
+    for (int a = 0; a < 3; a++)
+        for (int r = 0; r < nfr[a]; r++) { chain[a][r][0] = fend[a][r][0]; nch[a][r] = 1; }
+    for (int a = 0; a < 3; a++)
+        for (int b = a + 1; b < 3; b++) {
+            int cc = 3 - a - b;
+            int ua, va, ub, vb;
+            other_axes(a, &ua, &va);
+            other_axes(b, &ub, &vb);
+            for (int i = 0; i < nfr[a]; i++)
+                for (int j = 0; j < nfr[b]; j++) {
+                    double ca = fr[a][i][cc == ua ? 0 : 1];
+                    double cb = fr[b][j][cc == ub ? 0 : 1];
+                    if (fabs(ca - cb) > 1e-9) continue;
+                    int id = new_point(pts, &np, 3);
+                    if (id < 0) return OR_ERR_CAP;
+                    opoint *p = &pts[id];
+                    p->p[a] = fr[b][j][a == ub ? 0 : 1];
+                    p->p[b] = fr[a][i][b == ua ? 0 : 1];
+                    p->p[cc] = ca;
+                    p->fa = a; p->fb = b;
+                    /* outward normal = -grad g = -(dg/dx_cc) e_cc at the point */
+                    double x = p->p[0], y = p->p[1], z = p->p[2];
+                    double dgc;
+                    {
+                        double w[3] = {x, y, z};
+                        double acc = 0;
+                        for (int v = 0; v < 8; v++) {
+                            double f = 1;
+                            for (int t = 0; t < 3; t++) {
+                                int bit = (v >> t) & 1;
+                                if (t == cc) f *= bit ? 1.0 : -1.0;
+                                else f *= bit ? w[t] : 1.0 - w[t];
+                            }
+                            acc += f * g[v];
+                        }
+                        dgc = acc;
+                    }
+                    int even = (a == 0 && b == 1) || (a == 1 && b == 2) ? 1 : 0; /* (a,b,cc) cyclic */
+                    if (a == 0 && b == 2) even = 0;
+                    p->rh = (even == (dgc < 0));
+                    if (dgc == 0) LOOPERR(1);
+                    p->key = okey((uint64_t)(C[0] * s), (uint64_t)(C[1] * s), (uint64_t)(C[2] * s),
+                                  20u + 4u * (unsigned)(a + b - 1) + 2u * (unsigned)i + (unsigned)j, (unsigned)l);
+                    if (nch[a][i] < 3) chain[a][i][nch[a][i]++] = id;
+                    if (nch[b][j] < 3) chain[b][j][nch[b][j]++] = id;
+                }
+        }
+    /* close the chains, sort interior points along the fold axis, link */
+    for (int a = 0; a < 3; a++)
+        for (int r = 0; r < nfr[a]; r++) {
+            int *ch = chain[a][r];
+            int n = nch[a][r];
+            if (n == 3 && pts[ch[2]].p[a] < pts[ch[1]].p[a]) { int t = ch[1]; ch[1] = ch[2]; ch[2] = t; }
+            ch[n++] = fend[a][r][1];
+            nch[a][r] = n;
+            for (int k = 0; k + 1 < n; k++) {
+                int p0 = ch[k], p1 = ch[k + 1];
+                /* p0 -> p1 is the + direction along a */
+                if (pts[p0].kind == 3) pts[p0].nb[pts[p0].fa == a ? 0 : 2] = p1;
+                else pts[p0].nb[0] = p1;
+                if (pts[p1].kind == 3) pts[p1].nb[pts[p1].fa == a ? 1 : 3] = p0;
+                else pts[p1].nb[0] = p0;
+            }
+        }
+
+    /* Face curves: arcs of the bilinear face function between edge points,
+     * extreme points inserted in order along their branch, oriented so that
+     * the inside (g >= c) is on the right seen from outside the cube.  All
+     * face decisions use the face's own (u,v) frame (global axis order), so
+     * both cubes sharing the face take the same ones. */
+    int next[MAXP];
+    for (int i = 0; i < np; i++) next[i] = -1;
+    for (int a = 0; a < 3; a++) {
+        int ua, va;
+        other_axes(a, &ua, &va);
+        for (int sd = 0; sd < 2; sd++) {
+            double h[2][2];
+            int b[3];
+            for (int iu = 0; iu < 2; iu++)
+                for (int iv = 0; iv < 2; iv++) {
+                    b[a] = sd; b[ua] = iu; b[va] = iv;
+                    h[iu][iv] = gv(g, b[0], b[1], b[2]);
+                }
+            /* face edges: E0 v=0, E1 u=1, E2 v=1, E3 u=0 */
+            int ep[4];
+            for (int e = 0; e < 4; e++) {
+                int along = (e == 0 || e == 2) ? ua : va;
+                int fixed_other = (e == 0 || e == 2) ? va : ua;
+                int fixed_val = (e == 1 || e == 2) ? 1 : 0;
+                int bits[3];
+                bits[along] = 0; bits[a] = sd; bits[fixed_other] = fixed_val;
+                int o1, o2;
+                other_axes(along, &o1, &o2);
+                ep[e] = eid[along][bits[o1]][bits[o2]];
+            }
+            int ncross = (ep[0] >= 0) + (ep[1] >= 0) + (ep[2] >= 0) + (ep[3] >= 0);
+            if (ncross == 0) {
+                if (nfp[a][sd] > 0) LOOPERR(2);
+                continue;
+            }
+            int hs = (sd ? 1 : -1) * (a == 1 ? -1 : 1);
+            double stq[4];
+            stq[0] = hs * (h[1][0] - h[0][0]);
+            stq[1] = hs * (h[1][1] - h[1][0]);
+            stq[2] = -hs * (h[1][1] - h[0][1]);
+            stq[3] = -hs * (h[0][1] - h[0][0]);
+            int arcs[2][2];
+            int narc = 0, around00 = 0;
+            double us = 0;
+            if (ncross == 2) {
+                int e1 = -1, e2 = -1;
+                for (int e = 0; e < 4; e++)
+                    if (ep[e] >= 0) { if (e1 < 0) e1 = e; else e2 = e; }
+                arcs[0][0] = e1; arcs[0][1] = e2;
+                narc = 1;
+            } else if (ncross == 4) {
+                double d = h[0][0] - h[1][0] - h[0][1] + h[1][1];
+                double hsad = (h[0][0] * h[1][1] - h[1][0] * h[0][1]) / d;
+                us = (h[0][0] - h[0][1]) / d;
+                int in00 = h[0][0] >= c;
+                int separated = hsad < c;
+                around00 = (in00 && separated) || (!in00 && !separated);
+                if (around00) { arcs[0][0] = 0; arcs[0][1] = 3; arcs[1][0] = 2; arcs[1][1] = 1; }
+                else { arcs[0][0] = 0; arcs[0][1] = 1; arcs[1][0] = 2; arcs[1][1] = 3; }
+                narc = 2;
+            } else {
+                LOOPERR(3);
+                continue;
+            }
+            for (int ai = 0; ai < narc; ai++) {
+                int e1 = arcs[ai][0], e2 = arcs[ai][1];
+                int P1 = ep[e1], P2 = ep[e2];
+                int st1 = stq[e1] > 0, st2 = stq[e2] > 0;
+                if (st1 == st2) { LOOPERR(4); continue; }
+                int S = st1 ? P1 : P2, T = st1 ? P2 : P1;
+                int mid[8], nm = 0;
+                for (int t = 0; t < nfp[a][sd]; t++) {
+                    int id = fp[a][sd][t];
+                    if (narc == 2) {
+                        int branch_lowu = pts[id].p[ua] < us;
+                        int arc_lowu = (ai == 0) ? around00 : !around00;
+                        if (branch_lowu != arc_lowu) continue;
+                    }
+                    if (nm < 8) mid[nm++] = id;
+                }
+                double du = pts[T].p[ua] - pts[S].p[ua], dv = pts[T].p[va] - pts[S].p[va];
+                int ax = fabs(du) >= fabs(dv) ? ua : va;
+                double sgn = (ax == ua ? du : dv) >= 0 ? 1.0 : -1.0;
+                for (int i1 = 1; i1 < nm; i1++) {
+                    int x = mid[i1], j = i1 - 1;
+                    while (j >= 0) {
+                        double kx = sgn * pts[x].p[ax], kj = sgn * pts[mid[j]].p[ax];
+                        if (kj > kx || (kj == kx && pts[mid[j]].key > pts[x].key)) { mid[j + 1] = mid[j]; j--; }
+                        else break;
+                    }
+                    mid[j + 1] = x;
+                }
+                int seq[12], ns = 0;
+                seq[ns++] = S;
+                for (int i1 = 0; i1 < nm; i1++) seq[ns++] = mid[i1];
+                seq[ns++] = T;
+                for (int i1 = 0; i1 + 1 < ns; i1++) {
+                    if (next[seq[i1]] >= 0) LOOPERR(5);
+                    next[seq[i1]] = seq[i1 + 1];
+                }
+            }
+        }
+    }
+    for (int i = 0; i < np; i++)
+        if (pts[i].kind != 3 && next[i] < 0) { LOOPERR(6); return OR_OK; }
+
+    /* Pieces: trace every face of the graph formed by the loops and the fold
+     * segments, keeping the face on the left (seen from outside).  After a
+     * loop edge into an own extreme point the walk turns onto its fold; after
+     * a fold segment into an extreme point it continues along the loop; at a
+     * critical point it takes the segment next clockwise from the one it
+     * arrived on. */
+    int used_loop[MAXP], used_fold[MAXP][4];
+    for (int i = 0; i < np; i++) { used_loop[i] = 0; used_fold[i][0] = used_fold[i][1] = used_fold[i][2] = used_fold[i][3] = 0; }
+    for (int i0 = 0; i0 < np; i0++) {
+        if (pts[i0].kind == 3 || used_loop[i0]) continue;
+        int poly[2 * MAXP], n = 0;
+        int cur = i0, slot = -1; /* slot < 0: loop edge from cur; else fold slot */
+        int ok = 1;
+        for (int steps = 0;; steps++) {
+            if (steps > 4 * MAXP || n >= 2 * MAXP) { ok = 0; break; }
+            poly[n++] = cur;
+            int nx;
+            if (slot < 0) { used_loop[cur] = 1; nx = next[cur]; }
+            else { used_fold[cur][slot] = 1; nx = pts[cur].nb[slot]; }
+            if (nx < 0) { ok = 0; break; }
+            int nslot;
+            if (slot < 0) {
+                nslot = pts[nx].kind == 1 ? 0 : -1;
+            } else if (pts[nx].kind != 3) {
+                nslot = -1;
+            } else {
+                /* arrived at a critical point from cur: direction back to cur */
+                opoint *X = &pts[nx];
+                int back = -1;
+                for (int k = 0; k < 4; k++) if (X->nb[k] == cur) back = k;
+                /* slots: 0 +a, 1 -a, 2 +b, 3 -b; clockwise successor */
+                static const int cw_rh[4] = {3, 2, 0, 1};  /* +a->-b, -a->+b, +b->+a, -b->-a */
+                static const int cw_lh[4] = {2, 3, 1, 0};  /* +a->+b, -a->-b, +b->-a, -b->+a */
+                if (back < 0) { ok = 0; break; }
+                nslot = X->rh ? cw_rh[back] : cw_lh[back];
+                if (X->nb[nslot] < 0) { ok = 0; break; }
+            }
+            cur = nx;
+            slot = nslot;
+            if (slot < 0 && cur == i0) break;
+            if (slot < 0 && used_loop[cur]) { ok = 0; break; }
+            if (slot >= 0 && used_fold[cur][slot]) { ok = 0; break; }
+        }
+        if (!ok) { LOOPERR(7); continue; }
+        if (n >= 3 && n <= MAXP) {
+            tris->piece++;
+            int r = ear_clip(pts, poly, n, tris, st);
+            if (r) return r;
+        } else if (n > MAXP) LOOPERR(8);
+    }
+    /* world positions */
+    double lo[3];
+    for (int a = 0; a < 3; a++) lo[a] = lat_x(P, a, C[a], l);
+    double h = lvl_h(P, l);
+    for (int i = 0; i < np; i++) {
+        double x[3];
+        for (int a = 0; a < 3; a++) {
+            double f = pts[i].p[a];
+            if (f == 0) x[a] = lo[a];
+            else if (f == 1) x[a] = lat_x(P, a, C[a] + 1, l);
+            else x[a] = lo[a] + f * h;
+        }
+        if (p_push(verts, pts[i].key, x)) return OR_ERR_OOM;
+    }
+    return OR_OK;
+}
+
+static int cmp_vert(const void *a, const void *b)
+{
+    uint64_t x = ((const overt *)a)->key, y = ((const overt *)b)->key;
+    return x < y ? -1 : x > y;
+}
+
+/* ================================================================== */
+/* Public entry points (ctypes)                                         */
+/* ================================================================== */
+
+typedef struct {
+    int64_t n_vertices, n_triangles, n_cubes, n_accepted_pre;
+    double *vertices;     /* [nv,3] */
+    uint64_t *vkeys;      /* [nv] sorted */
+    int32_t *triangles;   /* [nt,3] */
+    int64_t *tri_piece;   /* [nt] piece each triangle came from */
+    uint64_t *cube_keys;  /* [n_cubes] final accepted cubes, sorted */
+    uint64_t *pre_keys;   /* accepted cubes before conformity, sorted */
+    int64_t n_lattice;
+    uint64_t *lattice_keys; double *lattice_phi; /* vertex field at cube corners */
+    ostats st;
+} or_mesh_out;
+
+void or_mesh_free(or_mesh_out *o)
+{
+    free(o->vertices); free(o->vkeys); free(o->triangles); free(o->tri_piece); free(o->cube_keys); free(o->pre_keys);
+    free(o->lattice_keys); free(o->lattice_phi);
+    memset(o, 0, sizeof(*o));
+}
+
+int or_root_grid(int64_t n, const double *xyz, const double *r, double D, double c, double cutoff_rel,
+                 double min_edge, int max_depth, double *origin, int64_t *nroot, double *pad)
+{
+    oprob P;
+    int e = oprob_init(&P, n, xyz, r, D, c, cutoff_rel, 1.0, min_edge, max_depth);
+    if (e) return e;
+    for (int a = 0; a < 3; a++) { origin[a] = P.origin[a]; nroot[a] = P.nroot[a]; }
+    *pad = P.pad;
+    oprob_free(&P);
+    return OR_OK;
+}
+
+int or_field(int64_t n, const double *xyz, const double *r, double D, double c, double cutoff_rel,
+             int64_t npts, const double *pts, double *phi, double *grad)
+{
+    oprob P;
+    int e = oprob_init(&P, n, xyz, r, D, c, cutoff_rel, 1.0, 1.0, 0);
+    if (e) return e;
+    for (int64_t i = 0; i < npts; i++) phi[i] = phi_at(&P, pts + 3 * i, grad ? grad + 3 * i : NULL);
+    oprob_free(&P);
+    return OR_OK;
+}
+
+/* tensor A of the cube [lo, lo+h]^3 (brute force over atoms) */
+int64_t or_cube_tensor(int64_t n, const double *xyz, const double *r, double D, double c, double cutoff_rel,
+                       const double *lo, double h, double *A)
+{
+    oprob P;
+    if (oprob_init(&P, n, xyz, r, D, c, cutoff_rel, 1.0, 1.0, 0)) return -1;
+    double hi[3] = {lo[0] + h, lo[1] + h, lo[2] + h};
+    int64_t cnt = cube_tensor(&P, lo, hi, A);
+    oprob_free(&P);
+    return cnt;
+}
+
+/* tensors and decisions for listed cube keys (type 30) of the problem's grid */
+int or_cube_batch(int64_t n, const double *xyz, const double *r, double D, double c, double cutoff_rel,
+                  double precision, double min_edge, int max_depth, int64_t ncubes, const uint64_t *keys,
+                  double *A_out, double *bounds_out, int32_t *dec_out)
+{
+    oprob P;
+    int e = oprob_init(&P, n, xyz, r, D, c, cutoff_rel, precision, min_edge, max_depth);
+    if (e) return e;
+    for (int64_t q = 0; q < ncubes; q++) {
+        double lo[3], hi[3], A[64], o6[6];
+        cube_box(&P, keys[q], lo, hi);
+        cube_tensor(&P, lo, hi, A);
+        dec_out[q] = or_decide(A, c, precision, (int)okey_level(keys[q]), max_depth, o6);
+        if (A_out) memcpy(A_out + 64 * q, A, sizeof(A));
+        if (bounds_out) memcpy(bounds_out + 6 * q, o6, sizeof(o6));
+    }
+    oprob_free(&P);
+    return OR_OK;
+}
+
+/* the whole path: partition, conformity, vertex field, triangulation, weld */
+int or_mesh(int64_t n, const double *xyz, const double *r, double D, double c, double cutoff_rel,
+            double precision, double min_edge, int max_depth, or_mesh_out *out)
+{
+    memset(out, 0, sizeof(*out));
+    oprob P;
+    int e = oprob_init(&P, n, xyz, r, D, c, cutoff_rel, precision, min_edge, max_depth);
+    if (e) return e;
+    ostats *st = &out->st;
+    vec64 acc = {0};
+    e = partition(&P, &acc, st, NULL);
+    if (e) goto done;
+    acc.n = sort_unique(acc.a, acc.n);
+    out->n_accepted_pre = acc.n;
+    out->pre_keys = (uint64_t *)malloc(sizeof(uint64_t) * (size_t)(acc.n ? acc.n : 1));
+    if (acc.n) memcpy(out->pre_keys, acc.a, sizeof(uint64_t) * (size_t)acc.n);
+    e = conformity(&P, &acc, st);
+    if (e) goto done;
+    st->n_cubes_final = acc.n;
+    /* lattice vertices of accepted cubes and their field values */
+    {
+        vec64 vk = {0};
+        for (int64_t i = 0; i < acc.n; i++) {
+            int64_t x, y, z;
+            okey_xyz(acc.a[i], &x, &y, &z);
+            int l = (int)okey_level(acc.a[i]);
+            int64_t s = (int64_t)1 << (max_depth - l);
+            for (int v = 0; v < 8; v++)
+                if (v_push(&vk, okey((uint64_t)((x + (v & 1)) * s), (uint64_t)((y + ((v >> 1) & 1)) * s),
+                                     (uint64_t)((z + ((v >> 2) & 1)) * s), T_VERT, 0))) { e = OR_ERR_OOM; goto done; }
+        }
+        vk.n = sort_unique(vk.a, vk.n);
+        double *vphi = (double *)malloc(sizeof(double) * (size_t)(vk.n ? vk.n : 1));
+        for (int64_t i = 0; i < vk.n; i++) {
+            int64_t x, y, z;
+            okey_xyz(vk.a[i], &x, &y, &z);
+            double p[3] = {lat_x(&P, 0, x, max_depth), lat_x(&P, 1, y, max_depth), lat_x(&P, 2, z, max_depth)};
+            vphi[i] = phi_at(&P, p, NULL);
+        }
+        st->n_vertices_lattice = vk.n;
+        out->n_lattice = vk.n;
+        out->lattice_keys = vk.a;
+        out->lattice_phi = vphi;
+        omesh_ctx M = {&P, acc.a, acc.n, vk.a, vphi, vk.n};
+        vtri tris = {0};
+        vvert verts = {0};
+        for (int64_t i = 0; i < acc.n; i++) {
+            e = triangulate_cube(&M, acc.a[i], &tris, &verts, st);
+            if (e) goto done;
+        }
+        /* weld: unique keys (sorted), triangles remapped to indices */
+        if (verts.n) qsort(verts.p, (size_t)verts.n, sizeof(overt), cmp_vert);
+        int64_t m = 0;
+        for (int64_t i = 0; i < verts.n; i++)
+            if (m == 0 || verts.p[i].key != verts.p[m - 1].key) verts.p[m++] = verts.p[i];
+        out->n_vertices = m;
+        out->vertices = (double *)malloc(sizeof(double) * 3 * (size_t)(m ? m : 1));
+        out->vkeys = (uint64_t *)malloc(sizeof(uint64_t) * (size_t)(m ? m : 1));
+        for (int64_t i = 0; i < m; i++) {
+            out->vkeys[i] = verts.p[i].key;
+            memcpy(out->vertices + 3 * i, verts.p[i].x, sizeof(double) * 3);
+        }
+        out->n_triangles = tris.n;
+        out->triangles = (int32_t *)malloc(sizeof(int32_t) * 3 * (size_t)(tris.n ? tris.n : 1));
+        out->tri_piece = (int64_t *)malloc(sizeof(int64_t) * (size_t)(tris.n ? tris.n : 1));
+        for (int64_t i = 0; i < tris.n; i++) out->tri_piece[i] = tris.t[i].piece;
+        for (int64_t i = 0; i < tris.n; i++)
+            for (int j = 0; j < 3; j++) {
+                int64_t id = find_u64(out->vkeys, m, tris.t[i].k[j]);
+                out->triangles[3 * i + j] = (int32_t)id;
+                if (id < 0) st->loop_errors++;
+            }
+        free(tris.t);
+        free(verts.p);
+    }
+    out->n_cubes = acc.n;
+    out->cube_keys = acc.a;
+    acc.a = NULL;
+done:
+    free(acc.a);
+    oprob_free(&P);
+    if (e) or_mesh_free(out);
+    return e;
+}
+
+/* partition only (level loop), returns the accepted cubes (sorted) */
+int or_partition(int64_t n, const double *xyz, const double *r, double D, double c, double cutoff_rel,
+                 double precision, double min_edge, int max_depth, or_mesh_out *out)
+{
+    memset(out, 0, sizeof(*out));
+    oprob P;
+    int e = oprob_init(&P, n, xyz, r, D, c, cutoff_rel, precision, min_edge, max_depth);
+    if (e) return e;
+    vec64 acc = {0};
+    e = partition(&P, &acc, &out->st, NULL);
+    if (!e) {
+        acc.n = sort_unique(acc.a, acc.n);
+        out->n_accepted_pre = acc.n;
+        out->pre_keys = acc.a;
+        acc.a = NULL;
+    }
+    free(acc.a);
+    oprob_free(&P);
+    return e;
+}
+
+
+/* Triangulate a uniform grid of given corner values (all cubes accepted at
+ * one level, unit spacing, origin 0): the per-cube path on exact trilinear
+ * data.  values: [(nz+1)][(ny+1)][(nx+1)], x fastest. */
+int or_mesh_grid(int64_t nx, int64_t ny, int64_t nz, const double *values, double c, or_mesh_out *out)
+{
+    memset(out, 0, sizeof(*out));
+    if (nx <= 0 || ny <= 0 || nz <= 0 || nx > 4096 || ny > 4096 || nz > 4096) return OR_ERR_ARG;
+    oprob P;
+    memset(&P, 0, sizeof(P));
+    P.c = c; P.min_edge = 1.0; P.max_depth = 0; P.h0 = 1.0;
+    P.nroot[0] = nx; P.nroot[1] = ny; P.nroot[2] = nz;
+    int64_t nc = nx * ny * nz, nv = (nx + 1) * (ny + 1) * (nz + 1);
+    uint64_t *cubes = (uint64_t *)malloc(sizeof(uint64_t) * (size_t)nc);
+    uint64_t *vk = (uint64_t *)malloc(sizeof(uint64_t) * (size_t)nv);
+    double *vp = (double *)malloc(sizeof(double) * (size_t)nv);
+    if (!cubes || !vk || !vp) { free(cubes); free(vk); free(vp); return OR_ERR_OOM; }
+    int64_t q = 0;
+    for (int64_t z = 0; z < nz; z++)
+        for (int64_t y = 0; y < ny; y++)
+            for (int64_t x = 0; x < nx; x++) cubes[q++] = okey((uint64_t)x, (uint64_t)y, (uint64_t)z, T_CUBE, 0);
+    qsort(cubes, (size_t)nc, sizeof(uint64_t), cmp_u64);
+    /* keys sort by (z, y, x) because z occupies the high bits */
+    q = 0;
+    for (int64_t z = 0; z <= nz; z++)
+        for (int64_t y = 0; y <= ny; y++)
+            for (int64_t x = 0; x <= nx; x++) {
+                vk[q] = okey((uint64_t)x, (uint64_t)y, (uint64_t)z, T_VERT, 0);
+                vp[q] = values[q];
+                q++;
+            }
+    omesh_ctx M = {&P, cubes, nc, vk, vp, nv};
+    vtri tris = {0};
+    vvert verts = {0};
+    int e = OR_OK;
+    for (int64_t i = 0; i < nc && !e; i++) e = triangulate_cube(&M, cubes[i], &tris, &verts, &out->st);
+    if (!e) {
+        if (verts.n) qsort(verts.p, (size_t)verts.n, sizeof(overt), cmp_vert);
+        int64_t m = 0;
+        for (int64_t i = 0; i < verts.n; i++)
+            if (m == 0 || verts.p[i].key != verts.p[m - 1].key) verts.p[m++] = verts.p[i];
+        out->n_vertices = m;
+        out->vertices = (double *)malloc(sizeof(double) * 3 * (size_t)(m ? m : 1));
+        out->vkeys = (uint64_t *)malloc(sizeof(uint64_t) * (size_t)(m ? m : 1));
+        for (int64_t i = 0; i < m; i++) {
+            out->vkeys[i] = verts.p[i].key;
+            memcpy(out->vertices + 3 * i, verts.p[i].x, sizeof(double) * 3);
+        }
+        out->n_triangles = tris.n;
+        out->triangles = (int32_t *)malloc(sizeof(int32_t) * 3 * (size_t)(tris.n ? tris.n : 1));
+        out->tri_piece = (int64_t *)malloc(sizeof(int64_t) * (size_t)(tris.n ? tris.n : 1));
+        for (int64_t i = 0; i < tris.n; i++) out->tri_piece[i] = tris.t[i].piece;
+        for (int64_t i = 0; i < tris.n; i++)
+            for (int j = 0; j < 3; j++) {
+                int64_t id = find_u64(out->vkeys, m, tris.t[i].k[j]);
+                out->triangles[3 * i + j] = (int32_t)id;
+                if (id < 0) out->st.loop_errors++;
+            }
+    }
+    free(tris.t); free(verts.p);
+    out->n_cubes = nc;
+    out->cube_keys = cubes;
+    free(vk); free(vp);
+    if (e) or_mesh_free(out);
+    return e;
+}
+
+int or_sizeof_mesh_out(void) { return (int)sizeof(or_mesh_out); }
+int or_sizeof_stats(void) { return (int)sizeof(ostats); }
