@@ -1,0 +1,181 @@
+/*
+ * gsmesh.h -- C ABI of the GB300 (sm_103a) Gaussian-surface mesher.
+ *
+ * The library meshes the level set {x : phi(x) = c} of the Gaussian
+ * molecular field phi(x) = sum_i exp(-D (|x - x_i|^2 - r_i^2)) (eq Gaussian1
+ * of Liu, Chen & Lu, TMSmesh 2.0) by the paper's two stages: an adaptive
+ * partition with per-cube tricubic Legendre estimation (section 2.2) and a
+ * per-cube trilinear surface cut into single-valued pieces along fold
+ * curves and triangulated by ear clipping (section 2.3).
+ *
+ * Conventions for every entry point:
+ *  - Pointers may be host or device memory (detected per pointer with
+ *    cudaPointerGetAttributes); device pointers must be on the current
+ *    device.  Inputs are only read; the caller keeps ownership.
+ *  - Arrays are C-contiguous: atoms [n][3] FP64 (Angstrom), radii [n] FP64.
+ *  - Work is issued on `stream` (a cudaStream_t, NULL = a stream owned by
+ *    the library) and the call returns after it has completed.
+ *  - Return value 0 on success, a negative GS_ERR_* code otherwise; nothing
+ *    is thrown across the ABI.  gs_last_error() gives a message for the
+ *    calling thread's last failure.  Output structs are zeroed on error.
+ *  - Terms below cutoff_rel * c are dropped: atom i contributes at a point
+ *    (a cube) iff the squared distance to the point (to the box) is at most
+ *    R_i^2 = r_i^2 - ln(cutoff_rel * c) / D (section 2.2.1, the
+ *    neighbourhood truncation after eq polynew).  Default cutoff_rel 1e-8.
+ *
+ * Key format (64-bit), shared by the mesh output and the parity tests:
+ *   bits 0..17 x, 18..35 y, 36..53 z lattice coordinates, 54..58 type,
+ *   59..63 level.  Mesh points: type 0..2 = surface point on a cube edge
+ *   along axis 0/1/2 (xyz = finest-lattice lower endpoint); 8..19 =
+ *   extreme point 8 + 4*axis + 2*side + rank (xyz = finest-lattice lower
+ *   corner of the face; side 1 = the fold belongs to the cube on the face's
+ *   + side); 20..31 = critical point 20 + 4*(a+b-1) + 2*i + j (xyz =
+ *   finest-lattice lower corner of the cube).  Cube keys use type 30 with
+ *   the cube's own-level lattice coordinates.
+ */
+#ifndef GSMESH_H
+#define GSMESH_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* status codes */
+#define GS_OK 0
+#define GS_ERR_ARG (-1)           /* invalid argument (sizes, non-finite values, ranges) */
+#define GS_ERR_OOM (-2)           /* device or host allocation failed */
+#define GS_ERR_CAPACITY (-3)      /* an internal bound was exceeded (hash full, too many points) */
+#define GS_ERR_TIMEOUT (-4)       /* a bounded device loop or host wait gave up */
+#define GS_ERR_CUDA (-5)          /* a CUDA runtime call failed */
+#define GS_ERR_DEVICE_STATUS (-6) /* a kernel reported an inconsistency through its status word */
+
+/* precision modes */
+#define GS_PREC_FP64 0   /* every field sum and estimate in FP64 (the reference form) */
+#define GS_PREC_MIXED 1  /* FP32 compensated sums, FP64 re-evaluation near thresholds */
+
+/* decisions reported by gs_cube_decisions */
+#define GS_DEC_DISCARD 0
+#define GS_DEC_ACCEPT 1
+#define GS_DEC_SPLIT 2
+#define GS_DEC_FORCED 3  /* accepted at max_depth without meeting the precision bound */
+
+typedef struct {
+    int64_t examined[21], discarded[21], accepted[21], forced[21], split[21]; /* per level */
+    int64_t pair_terms;        /* (cube, atom) terms inside the cutoff, all levels */
+    int64_t vertex_terms;      /* (vertex, atom) terms inside the cutoff */
+    int64_t recheck_cubes;     /* cubes re-estimated in FP64 (mixed mode) */
+    int64_t recheck_vertices;  /* vertex values re-evaluated in FP64 (mixed mode) */
+    int64_t conformity_splits; /* cubes split to equalise levels across faces and edges */
+    int64_t n_cubes_final;     /* accepted cubes after conformity */
+    int64_t n_cubes_surface;   /* accepted cubes whose corner values straddle c */
+    int64_t n_lattice_vertices;
+    int64_t n_points;          /* surface points emitted before welding */
+    int64_t n_vertices, n_triangles;
+    int64_t loop_errors;       /* cubes whose face curves could not be closed */
+    int64_t degenerate_ears;   /* ear clipping steps with no strictly valid ear */
+    double ms_total, ms_upload, ms_bin, ms_levels, ms_conformity, ms_field, ms_triangulate, ms_weld, ms_download;
+    double ms_level[21];
+} gs_stats;
+
+typedef struct {
+    double min_edge;        /* finest cube edge (A); default 0.25 */
+    int precision_mode;     /* GS_PREC_FP64 (default) or GS_PREC_MIXED */
+    double cutoff_rel;      /* default 1e-8 */
+    void *cuda_stream;      /* cudaStream_t or NULL */
+    int device_output;      /* 1: out arrays stay on the device (free with mesh_free) */
+    int debug_flags;        /* bit 0: mixed mode also runs FP64 on every cube and counts disagreements */
+    gs_stats *stats;        /* nullable: filled on success */
+} gs_options;
+
+typedef struct {
+    double *vertices;       /* [n_vertices][3] FP64, A */
+    int64_t n_vertices;
+    int32_t *triangles;     /* [n_triangles][3], counter-clockwise seen from outside (phi < c) */
+    int64_t n_triangles;
+    uint64_t *vertex_keys;  /* [n_vertices] canonical keys (see above) */
+    uint64_t *cube_keys;    /* [n_cubes] accepted cubes after conformity */
+    int64_t n_cubes;
+    int on_device;          /* arrays are device memory */
+    int64_t mismatches;     /* debug bit 0: mixed-vs-FP64 decision disagreements outside the band */
+} gs_mesh;
+
+/* gs_options with the defaults above */
+gs_options gs_default_options(void);
+
+/*
+ * mesh_gaussian_surface -- mesh {phi = c} (eqs Gaussian1, polynew, bound2,
+ * bound3, linear1, intersection, curve, fold1, critical; sections 2.2-2.3).
+ *   atoms     [n_atoms][3] centres, radii [n_atoms] (host or device)
+ *   D > 0 decay rate, c > 0 isovalue, precision > 0 bound on the sum of the
+ *   absolute higher-than-linear Legendre coefficients (section 2.2.3),
+ *   max_depth in [0, 20]: the root grid has edge min_edge * 2^max_depth and
+ *   cubes are refined at most max_depth times.
+ *   opt may be NULL (defaults).  On success *out holds library-allocated
+ *   arrays; release them with mesh_free.  An empty surface (every cube
+ *   discarded) is a success with zero triangles.
+ * Errors: GS_ERR_ARG for n_atoms <= 0, non-finite or negative inputs, D, c or
+ * precision <= 0, max_depth outside [0,20], or a lattice wider than 2^18
+ * points per axis; GS_ERR_OOM, GS_ERR_CAPACITY, GS_ERR_CUDA,
+ * GS_ERR_DEVICE_STATUS as above.
+ */
+int mesh_gaussian_surface(const double *atoms, const double *radii, int64_t n_atoms, double D, double c,
+                          double precision, int max_depth, const gs_options *opt, gs_mesh *out);
+
+/* release the arrays of a gs_mesh (host or device) and zero it; NULL-safe */
+void mesh_free(gs_mesh *m);
+
+/* static description of a status code */
+const char *gs_status_string(int status);
+
+/* message for the calling thread's last failure ("" if none) */
+const char *gs_last_error(void);
+
+/*
+ * gs_bin_atoms -- uniform cell list by a stable counting sort (the
+ * neighbourhood search behind the truncation of section 2.2.1).
+ *   cell = floor((x - origin) / cell_size) per axis, clamped to [0, dims-1],
+ *   linear index x + dims[0] * (y + dims[1] * z).
+ *   cell_start [dims0*dims1*dims2 + 1] int32: atoms of cell k are
+ *   atom_perm[cell_start[k] .. cell_start[k+1]), in ascending atom index.
+ *   All arrays host or device; outputs are written where they live.
+ */
+int gs_bin_atoms(const double *atoms, int64_t n_atoms, double cell_size, const double *origin,
+                 const int64_t *dims, int32_t *cell_start, int32_t *atom_perm, void *stream);
+
+/*
+ * gs_eval_field -- phi and grad phi at points (eq Gaussian1 with the
+ * truncation above).  points [n_points][3], phi [n_points], grad
+ * [n_points][3] (nullable).  precision_mode as in gs_options.
+ */
+int gs_eval_field(const double *atoms, const double *radii, int64_t n_atoms, double D, double c,
+                  double cutoff_rel, const double *points, int64_t n_points, double *phi, double *grad,
+                  int precision_mode, void *stream);
+
+/*
+ * gs_cube_decisions -- coefficient tensor A (eqs polynew, tensor1, tensor2),
+ * bounds (eqs SVD1-SVD7, bound1-bound3) and decision for listed cubes of the
+ * problem's root lattice (keys of type 30 at their level).  A [n][64] in
+ * (j,k,l) order with j <-> x (nullable), bounds [n][6] = (L, U, sum|R|,
+ * sum|high|, rank, sum of inner ranks) (nullable), dec [n] int32.
+ */
+int gs_cube_decisions(const double *atoms, const double *radii, int64_t n_atoms, double D, double c,
+                      double precision, double min_edge, int max_depth, double cutoff_rel,
+                      const uint64_t *cube_keys, int64_t n_cubes, double *A, double *bounds, int32_t *dec,
+                      int precision_mode, void *stream);
+
+/*
+ * gs_triangulate_grid -- the section 2.3 triangulation of a uniform grid of
+ * given corner values (every cube accepted at one level, unit spacing,
+ * origin 0): values [(nz+1)][(ny+1)][(nx+1)], x fastest.  Output as for
+ * mesh_gaussian_surface (opt: stream and device_output are honoured).
+ */
+int gs_triangulate_grid(int64_t nx, int64_t ny, int64_t nz, const double *values, double c,
+                        const gs_options *opt, gs_mesh *out);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* GSMESH_H */

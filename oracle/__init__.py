@@ -270,3 +270,19 @@ def mesh_grid(values, c):
     finally:
         L.or_mesh_free(ctypes.byref(out))
     return res
+
+
+def cell_list(xyz, cell, origin, dims):
+    """Uniform cell list by definition: cell = floor((x - origin)/cell) clamped
+    to [0, dims-1], linear index x + dims0*(y + dims1*z); atoms ordered by
+    cell, ties by ascending atom index (a stable sort)."""
+    xyz = np.asarray(xyz, dtype=np.float64)
+    origin = np.asarray(origin, dtype=np.float64)
+    dims = np.asarray(dims, dtype=np.int64)
+    c = np.floor((xyz - origin) * (1.0 / cell)).astype(np.int64)
+    c = np.clip(c, 0, dims - 1)
+    lin = c[:, 0] + dims[0] * (c[:, 1] + dims[1] * c[:, 2])
+    perm = np.argsort(lin, kind="stable").astype(np.int32)
+    counts = np.bincount(lin, minlength=int(np.prod(dims)))
+    start = np.concatenate([[0], np.cumsum(counts)]).astype(np.int32)
+    return start, perm

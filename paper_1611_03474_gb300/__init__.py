@@ -1,0 +1,14 @@
+"""GB300 (sm_103a) Gaussian-surface mesher: thin Python binding of the C ABI
+in include/gsmesh.h (argument marshalling only; every step runs in the
+library's CUDA kernels).
+
+Arrays may be numpy arrays (host) or torch tensors (host or CUDA); device
+tensors are passed by pointer, so inputs already resident in HBM are not
+copied.  The library must be built (build.build()); there is no CPU
+fallback: every call raises if the shared library is missing.
+"""
+from ._native import (GS_PREC_FP64, GS_PREC_MIXED, GsError, Mesh, Stats, gs_bin_atoms, gs_cube_decisions,
+                      gs_eval_field, gs_triangulate_grid, library_path, load, mesh_gaussian_surface)
+
+__all__ = ["GS_PREC_FP64", "GS_PREC_MIXED", "GsError", "Mesh", "Stats", "gs_bin_atoms", "gs_cube_decisions",
+           "gs_eval_field", "gs_triangulate_grid", "library_path", "load", "mesh_gaussian_surface"]

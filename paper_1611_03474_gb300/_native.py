@@ -1,0 +1,241 @@
+"""ctypes binding of libgsmesh.so (include/gsmesh.h).  Marshalling only."""
+import ctypes
+import os
+
+import numpy as np
+
+from .build import LIB
+
+GS_PREC_FP64 = 0
+GS_PREC_MIXED = 1
+
+
+class GsError(RuntimeError):
+    def __init__(self, code, msg):
+        super().__init__("gsmesh error %d: %s" % (code, msg))
+        self.code = code
+
+
+class Stats(ctypes.Structure):
+    _fields_ = [("examined", ctypes.c_int64 * 21), ("discarded", ctypes.c_int64 * 21),
+                ("accepted", ctypes.c_int64 * 21), ("forced", ctypes.c_int64 * 21),
+                ("split", ctypes.c_int64 * 21), ("pair_terms", ctypes.c_int64),
+                ("vertex_terms", ctypes.c_int64), ("recheck_cubes", ctypes.c_int64),
+                ("recheck_vertices", ctypes.c_int64), ("conformity_splits", ctypes.c_int64),
+                ("n_cubes_final", ctypes.c_int64), ("n_cubes_surface", ctypes.c_int64),
+                ("n_lattice_vertices", ctypes.c_int64), ("n_points", ctypes.c_int64),
+                ("n_vertices", ctypes.c_int64), ("n_triangles", ctypes.c_int64),
+                ("loop_errors", ctypes.c_int64), ("degenerate_ears", ctypes.c_int64),
+                ("ms_total", ctypes.c_double), ("ms_upload", ctypes.c_double), ("ms_bin", ctypes.c_double),
+                ("ms_levels", ctypes.c_double), ("ms_conformity", ctypes.c_double),
+                ("ms_field", ctypes.c_double), ("ms_triangulate", ctypes.c_double),
+                ("ms_weld", ctypes.c_double), ("ms_download", ctypes.c_double),
+                ("ms_level", ctypes.c_double * 21)]
+
+    def as_dict(self, max_depth=20):
+        d = {}
+        for name, _ in self._fields_:
+            v = getattr(self, name)
+            if isinstance(v, ctypes.Array):
+                v = [v[i] for i in range(max_depth + 1)]
+            d[name] = v
+        return d
+
+
+class Options(ctypes.Structure):
+    _fields_ = [("min_edge", ctypes.c_double), ("precision_mode", ctypes.c_int), ("cutoff_rel", ctypes.c_double),
+                ("cuda_stream", ctypes.c_void_p), ("device_output", ctypes.c_int), ("debug_flags", ctypes.c_int),
+                ("stats", ctypes.POINTER(Stats))]
+
+
+class MeshC(ctypes.Structure):
+    _fields_ = [("vertices", ctypes.POINTER(ctypes.c_double)), ("n_vertices", ctypes.c_int64),
+                ("triangles", ctypes.POINTER(ctypes.c_int32)), ("n_triangles", ctypes.c_int64),
+                ("vertex_keys", ctypes.POINTER(ctypes.c_uint64)), ("cube_keys", ctypes.POINTER(ctypes.c_uint64)),
+                ("n_cubes", ctypes.c_int64), ("on_device", ctypes.c_int), ("mismatches", ctypes.c_int64)]
+
+
+_lib = None
+
+
+def library_path():
+    return LIB
+
+
+def load():
+    """Load libgsmesh.so; raises if it has not been built."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    if not os.path.exists(LIB):
+        raise GsError(-5, "CUDA library not built: %s (run paper_1611_03474_gb300.build.build())" % LIB)
+    L = ctypes.CDLL(LIB)
+    p, d, i64, i32 = ctypes.c_void_p, ctypes.c_double, ctypes.c_int64, ctypes.c_int
+    L.mesh_gaussian_surface.argtypes = [p, p, i64, d, d, d, i32, ctypes.POINTER(Options), ctypes.POINTER(MeshC)]
+    L.mesh_gaussian_surface.restype = i32
+    L.mesh_free.argtypes = [ctypes.POINTER(MeshC)]
+    L.mesh_free.restype = None
+    L.gs_status_string.argtypes = [i32]
+    L.gs_status_string.restype = ctypes.c_char_p
+    L.gs_last_error.restype = ctypes.c_char_p
+    L.gs_default_options.restype = Options
+    L.gs_bin_atoms.argtypes = [p, i64, d, p, p, p, p, p]
+    L.gs_bin_atoms.restype = i32
+    L.gs_eval_field.argtypes = [p, p, i64, d, d, d, p, i64, p, p, i32, p]
+    L.gs_eval_field.restype = i32
+    L.gs_cube_decisions.argtypes = [p, p, i64, d, d, d, d, i32, d, p, i64, p, p, p, i32, p]
+    L.gs_cube_decisions.restype = i32
+    L.gs_triangulate_grid.argtypes = [i64, i64, i64, p, d, ctypes.POINTER(Options), ctypes.POINTER(MeshC)]
+    L.gs_triangulate_grid.restype = i32
+    _lib = L
+    return L
+
+
+def _check(rc):
+    if rc != 0:
+        L = load()
+        raise GsError(rc, "%s: %s" % (L.gs_status_string(rc).decode(), L.gs_last_error().decode()))
+
+
+def _ptr(a):
+    """Data pointer of a numpy array or torch tensor (contiguous required)."""
+    if a is None:
+        return None
+    if hasattr(a, "data_ptr"):
+        assert a.is_contiguous(), "tensor must be contiguous"
+        return ctypes.c_void_p(a.data_ptr())
+    assert a.flags["C_CONTIGUOUS"], "array must be C-contiguous"
+    return a.ctypes.data_as(ctypes.c_void_p)
+
+
+def _host64(a, shape=None):
+    if hasattr(a, "data_ptr"):
+        return a
+    a = np.ascontiguousarray(a, dtype=np.float64)
+    return a.reshape(shape) if shape is not None else a
+
+
+def _stream_ptr(stream):
+    if stream is None:
+        return None
+    if hasattr(stream, "cuda_stream"):
+        return ctypes.c_void_p(stream.cuda_stream)
+    return ctypes.c_void_p(int(stream))
+
+
+class Mesh:
+    """Result of mesh_gaussian_surface: vertices [nv,3] f64, triangles [nt,3]
+    i32 (CCW seen from outside), vertex_keys [nv] u64, cube_keys [nc] u64,
+    stats dict.  Host numpy arrays unless device_output was requested."""
+
+    def __init__(self, vertices, triangles, vertex_keys, cube_keys, stats, mismatches=0):
+        self.vertices = vertices
+        self.triangles = triangles
+        self.vertex_keys = vertex_keys
+        self.cube_keys = cube_keys
+        self.stats = stats
+        self.mismatches = mismatches
+
+
+def _take_host(ptr, n, dtype, shape):
+    if n == 0:
+        return np.zeros(shape, dtype=dtype)
+    arr = np.ctypeslib.as_array(ptr, shape=(int(np.prod(shape)),))
+    return np.array(arr, dtype=dtype).reshape(shape)
+
+
+def _mesh_from_c(m, L, stats, max_depth):
+    try:
+        res = Mesh(_take_host(m.vertices, m.n_vertices, np.float64, (m.n_vertices, 3)),
+                   _take_host(m.triangles, m.n_triangles, np.int32, (m.n_triangles, 3)),
+                   _take_host(m.vertex_keys, m.n_vertices, np.uint64, (m.n_vertices,)),
+                   _take_host(m.cube_keys, m.n_cubes, np.uint64, (m.n_cubes,)),
+                   stats.as_dict(max_depth), m.mismatches)
+    finally:
+        L.mesh_free(ctypes.byref(m))
+    return res
+
+
+def mesh_gaussian_surface(atoms, radii, D, c, precision, max_depth, min_edge=0.25, precision_mode=GS_PREC_FP64,
+                          cutoff_rel=1e-8, stream=None, debug_flags=0):
+    """Mesh {phi = c}; see include/gsmesh.h."""
+    L = load()
+    atoms = _host64(atoms, (-1, 3))
+    radii = _host64(radii)
+    n = atoms.shape[0]
+    st = Stats()
+    o = L.gs_default_options()
+    o.min_edge = min_edge
+    o.precision_mode = precision_mode
+    o.cutoff_rel = cutoff_rel
+    o.cuda_stream = _stream_ptr(stream)
+    o.device_output = 0
+    o.debug_flags = debug_flags
+    o.stats = ctypes.pointer(st)
+    m = MeshC()
+    rc = L.mesh_gaussian_surface(_ptr(atoms), _ptr(radii), n, D, c, precision, max_depth, ctypes.byref(o),
+                                 ctypes.byref(m))
+    _check(rc)
+    return _mesh_from_c(m, L, st, max_depth)
+
+
+def gs_triangulate_grid(values, c, stream=None):
+    """Triangulate a uniform grid of corner values [nz+1, ny+1, nx+1]."""
+    L = load()
+    values = _host64(values)
+    nz, ny, nx = (int(d) - 1 for d in values.shape)
+    st = Stats()
+    o = L.gs_default_options()
+    o.cuda_stream = _stream_ptr(stream)
+    o.stats = ctypes.pointer(st)
+    m = MeshC()
+    _check(L.gs_triangulate_grid(nx, ny, nz, _ptr(values), c, ctypes.byref(o), ctypes.byref(m)))
+    return _mesh_from_c(m, L, st, 0)
+
+
+def gs_eval_field(atoms, radii, D, c, points, cutoff_rel=1e-8, grad=False, precision_mode=GS_PREC_FP64, stream=None,
+                  out=None):
+    """phi (and grad phi) at points [n,3]; returns numpy arrays unless `out`
+    (a tuple of preallocated arrays/tensors) is given."""
+    L = load()
+    atoms = _host64(atoms, (-1, 3))
+    radii = _host64(radii)
+    points = _host64(points, (-1, 3))
+    n = points.shape[0]
+    if out is None:
+        phi = np.zeros(n)
+        g = np.zeros((n, 3)) if grad else None
+    else:
+        phi, g = out
+    _check(L.gs_eval_field(_ptr(atoms), _ptr(radii), atoms.shape[0], D, c, cutoff_rel, _ptr(points), n, _ptr(phi),
+                           _ptr(g), precision_mode, _stream_ptr(stream)))
+    return (phi, g) if grad else phi
+
+
+def gs_cube_decisions(atoms, radii, D, c, precision, min_edge, max_depth, cube_keys, cutoff_rel=1e-8,
+                      precision_mode=GS_PREC_FP64, stream=None):
+    """(A [n,64], bounds [n,6], dec [n]) for listed cube keys."""
+    L = load()
+    atoms = _host64(atoms, (-1, 3))
+    radii = _host64(radii)
+    keys = np.ascontiguousarray(cube_keys, dtype=np.uint64)
+    n = len(keys)
+    A, b, d = np.zeros((n, 64)), np.zeros((n, 6)), np.zeros(n, dtype=np.int32)
+    _check(L.gs_cube_decisions(_ptr(atoms), _ptr(radii), atoms.shape[0], D, c, precision, min_edge, max_depth,
+                               cutoff_rel, _ptr(keys), n, _ptr(A), _ptr(b), _ptr(d), precision_mode,
+                               _stream_ptr(stream)))
+    return A, b, d
+
+
+def gs_bin_atoms(atoms, cell_size, origin, dims, stream=None):
+    """(cell_start [ncell+1] i32, atom_perm [n] i32) of the stable counting sort."""
+    L = load()
+    atoms = _host64(atoms, (-1, 3))
+    origin = np.ascontiguousarray(origin, dtype=np.float64)
+    dims = np.ascontiguousarray(dims, dtype=np.int64)
+    ncell = int(np.prod(dims))
+    cs = np.zeros(ncell + 1, dtype=np.int32)
+    pm = np.zeros(atoms.shape[0], dtype=np.int32)
+    _check(L.gs_bin_atoms(_ptr(atoms), atoms.shape[0], cell_size, _ptr(origin), _ptr(dims), _ptr(cs), _ptr(pm),
+                          _stream_ptr(stream)))
+    return cs, pm

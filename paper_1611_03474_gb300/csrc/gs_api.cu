@@ -1,0 +1,819 @@
+// gs_api.cu -- host orchestration and the C ABI (include/gsmesh.h).
+//
+// mesh_gaussian_surface runs, on one stream:
+//   upload -> atom prep (cutoff radii, bounding box) -> root grid (host)
+//   -> cell list -> for each level: tensor accumulation, estimation,
+//   compaction -> conformity -> lattice vertices and their field values ->
+//   face neighbours -> triangulation (count, scan, emit) -> weld -> download.
+// The host waits once per level for the next level's size.
+#include <cmath>
+#include <cstdio>
+#include <cstdlib>
+#include <cstring>
+#include <mutex>
+#include <vector>
+
+#include "gs_host.cuh"
+
+extern "C" gs_options gs_default_options(void)
+{
+    gs_options o;
+    memset(&o, 0, sizeof(o));
+    o.min_edge = 0.25;
+    o.precision_mode = GS_PREC_FP64;
+    o.cutoff_rel = 1e-8;
+    return o;
+}
+
+extern "C" const char *gs_status_string(int s)
+{
+    switch (s) {
+    case GS_OK: return "ok";
+    case GS_ERR_ARG: return "invalid argument";
+    case GS_ERR_OOM: return "out of memory";
+    case GS_ERR_CAPACITY: return "internal capacity exceeded";
+    case GS_ERR_TIMEOUT: return "timeout";
+    case GS_ERR_CUDA: return "CUDA error";
+    case GS_ERR_DEVICE_STATUS: return "device status error";
+    default: return "unknown status";
+    }
+}
+
+extern "C" void mesh_free(gs_mesh *m)
+{
+    if (!m) return;
+    if (m->on_device) {
+        cudaFree(m->vertices); cudaFree(m->triangles); cudaFree(m->vertex_keys); cudaFree(m->cube_keys);
+    } else {
+        free(m->vertices); free(m->triangles); free(m->vertex_keys); free(m->cube_keys);
+    }
+    memset(m, 0, sizeof(*m));
+}
+
+static bool on_device(const void *p)
+{
+    cudaPointerAttributes a;
+    if (cudaPointerGetAttributes(&a, p) != cudaSuccess) { cudaGetLastError(); return false; }
+    return a.type == cudaMemoryTypeDevice || a.type == cudaMemoryTypeManaged;
+}
+
+// per-device one-time set-up: quadrature tables, a memory pool that keeps its memory
+static std::mutex g_init_mu;
+static bool g_dev_ready[64];
+static int device_setup(void)
+{
+    int dev = 0;
+    GS_CHECK(cudaGetDevice(&dev));
+    std::lock_guard<std::mutex> lk(g_init_mu);
+    if (dev >= 0 && dev < 64 && g_dev_ready[dev]) return GS_OK;
+    int rc = gs_quadrature_init();
+    if (rc) return rc;
+    cudaMemPool_t pool;
+    if (cudaDeviceGetDefaultMemPool(&pool, dev) == cudaSuccess) {
+        uint64_t thr = ~0ull;
+        cudaMemPoolSetAttribute(pool, cudaMemPoolAttrReleaseThreshold, &thr);
+    }
+    cudaGetLastError();
+    if (dev >= 0 && dev < 64) g_dev_ready[dev] = true;
+    return GS_OK;
+}
+
+// a simple scope guard for stream-ordered device buffers
+struct DevBufs {
+    cudaStream_t st;
+    std::vector<void *> ptrs;
+    explicit DevBufs(cudaStream_t s) : st(s) {}
+    template <typename T> int get(T **p, size_t count)
+    {
+        int rc = gs_alloc((void **)p, sizeof(T) * (count ? count : 1), st);
+        if (!rc) ptrs.push_back((void *)*p);
+        return rc;
+    }
+    void keep(void *p) { if (p) ptrs.push_back(p); }
+    void release(void *p)
+    {
+        for (auto &q : ptrs)
+            if (q == p) { gs_free(q, st); q = nullptr; }
+    }
+    ~DevBufs()
+    {
+        for (void *p : ptrs) gs_free(p, st);
+    }
+};
+
+struct Timer {
+    cudaStream_t st;
+    std::vector<cudaEvent_t> ev;
+    explicit Timer(cudaStream_t s) : st(s) {}
+    int mark()
+    {
+        cudaEvent_t e;
+        cudaEventCreate(&e);
+        cudaEventRecord(e, st);
+        ev.push_back(e);
+        return (int)ev.size() - 1;
+    }
+    double ms(int a, int b)
+    {
+        float t = 0;
+        cudaEventElapsedTime(&t, ev[a], ev[b]);
+        return t;
+    }
+    ~Timer()
+    {
+        for (auto e : ev) cudaEventDestroy(e);
+    }
+};
+
+static int check_status(unsigned *d_status, cudaStream_t st, const char *stage)
+{
+    unsigned h = 0;
+    GS_CHECK(cudaMemcpyAsync(&h, d_status, sizeof(unsigned), cudaMemcpyDeviceToHost, st));
+    GS_CHECK(cudaStreamSynchronize(st));
+    if (h & GS_ST_INPUT) return gs_fail(GS_ERR_ARG, "non-finite or negative atom data");
+    if (h & GS_ST_CAPACITY) return gs_fail(GS_ERR_CAPACITY, "%s: internal table full", stage);
+    if (h) return gs_fail(GS_ERR_DEVICE_STATUS, "%s: device status 0x%x", stage, h);
+    return GS_OK;
+}
+
+// root grid of section 2.2: edge h0 = min_edge * 2^max_depth, origin aligned
+// to h0, covering the atoms' bounding box grown by the largest cutoff radius
+static int root_grid(const double bbox[6], double pad, double min_edge, int max_depth, double origin[3],
+                     int64_t nroot[3], double *h0)
+{
+    *h0 = ldexp(min_edge, max_depth);
+    for (int a = 0; a < 3; a++) {
+        origin[a] = *h0 * floor((bbox[a] - pad) / *h0);
+        int64_t m = (int64_t)ceil((bbox[3 + a] + pad - origin[a]) / *h0);
+        nroot[a] = m < 1 ? 1 : m;
+        if (((nroot[a] << max_depth) + 1) > (int64_t)GK_MASK)
+            return gs_fail(GS_ERR_ARG, "lattice exceeds 2^18 points along an axis");
+    }
+    return GS_OK;
+}
+
+struct Prepared {
+    GsProblem P;
+    GsAtomsSoA soa;
+    int32_t *cell_start;
+};
+
+// upload, prep, cell list; buffers registered in B
+static int prepare(const double *atoms, const double *radii, int64_t n, double D, double c, double cutoff_rel,
+                   double precision, double min_edge, int max_depth, DevBufs &B, unsigned *d_status, Prepared *out,
+                   gs_stats *stats, Timer &T)
+{
+    cudaStream_t st = B.st;
+    const double *d_xyz = atoms, *d_r = radii;
+    int t0 = T.mark();
+    if (!on_device(atoms)) {
+        double *p;
+        int rc = B.get(&p, 3 * (size_t)n);
+        if (rc) return rc;
+        GS_CHECK(cudaMemcpyAsync(p, atoms, sizeof(double) * 3 * (size_t)n, cudaMemcpyHostToDevice, st));
+        d_xyz = p;
+    }
+    if (!on_device(radii)) {
+        double *p;
+        int rc = B.get(&p, (size_t)n);
+        if (rc) return rc;
+        GS_CHECK(cudaMemcpyAsync(p, radii, sizeof(double) * (size_t)n, cudaMemcpyHostToDevice, st));
+        d_r = p;
+    }
+    int t1 = T.mark();
+    double KD = -log(cutoff_rel * c) / D;
+    double *d_R2, *d_w;
+    int rc = B.get(&d_R2, (size_t)n);
+    if (!rc) rc = B.get(&d_w, (size_t)n);
+    if (rc) return rc;
+    double bbox[6], r2max;
+    rc = gs_prep_atoms(d_xyz, d_r, n, D, KD, d_R2, d_w, bbox, &r2max, d_status, st);
+    if (rc) return rc;
+    rc = check_status(d_status, st, "prep");
+    if (rc) return rc;
+    GsProblem &P = out->P;
+    memset(&P, 0, sizeof(P));
+    P.n = n; P.D = D; P.c = c; P.KD = KD; P.precision = precision; P.min_edge = min_edge; P.max_depth = max_depth;
+    P.pad = sqrt(r2max);
+    double h0;
+    rc = root_grid(bbox, P.pad, min_edge, max_depth, P.origin, P.nroot, &h0);
+    if (rc) return rc;
+    // cell edge: half the cutoff radius balances candidate volume against row count
+    P.cell = 0.5 * P.pad;
+    if (P.cell <= 0) P.cell = h0;
+    P.inv_cell = 1.0 / P.cell;
+    int64_t ncell = 1;
+    for (int a = 0; a < 3; a++) {
+        double ext = (double)P.nroot[a] * h0;
+        int64_t m = (int64_t)ceil(ext / P.cell) + 1;
+        if (m > (1 << 20)) return gs_fail(GS_ERR_ARG, "cell grid too large");
+        P.cdim[a] = (int)m;
+        ncell *= m;
+    }
+    if (ncell > (int64_t)1 << 31) return gs_fail(GS_ERR_ARG, "cell grid too large");
+    int32_t *perm;
+    rc = B.get(&out->cell_start, (size_t)ncell + 1);
+    if (!rc) rc = B.get(&perm, (size_t)n);
+    if (rc) return rc;
+    rc = gs_build_cells(d_xyz, n, P.origin, P.cell, P.cdim, out->cell_start, perm, st);
+    if (rc) return rc;
+    GsAtomsSoA &S = out->soa;
+    rc = B.get(&S.x, (size_t)n);
+    if (!rc) rc = B.get(&S.y, (size_t)n);
+    if (!rc) rc = B.get(&S.z, (size_t)n);
+    if (!rc) rc = B.get(&S.r, (size_t)n);
+    if (!rc) rc = B.get(&S.R2, (size_t)n);
+    if (!rc) rc = B.get(&S.w, (size_t)n);
+    if (!rc) rc = B.get(&S.fx, (size_t)n);
+    if (!rc) rc = B.get(&S.fy, (size_t)n);
+    if (!rc) rc = B.get(&S.fz, (size_t)n);
+    if (rc) return rc;
+    rc = gs_gather_atoms(perm, n, d_xyz, d_r, d_R2, d_w, P.origin, P.cell, P.cdim, &S, st);
+    if (rc) return rc;
+    P.ax = S.x; P.ay = S.y; P.az = S.z; P.ar = S.r; P.aR2 = S.R2; P.aw = S.w;
+    P.fx = S.fx; P.fy = S.fy; P.fz = S.fz;
+    P.cell_start = out->cell_start;
+    int t2 = T.mark();
+    if (stats) {
+        GS_CHECK(cudaStreamSynchronize(st));
+        stats->ms_upload = T.ms(t0, t1);
+        stats->ms_bin = T.ms(t1, t2);
+    }
+    return GS_OK;
+}
+
+// process one level in chunks of parents; appends accepted keys; returns the next parents
+static int run_level(const GsProblem &P, int level, const uint64_t *d_parents, int64_t n_oct, int mode,
+                     DevBufs &B, std::vector<uint64_t *> &acc_parts, std::vector<int64_t> &acc_counts,
+                     uint64_t **d_next, int64_t *n_next, unsigned long long *d_counters, unsigned long long *d_pairs,
+                     unsigned *d_status)
+{
+    cudaStream_t st = B.st;
+    const int64_t CH = 1 << 21;  // octets per chunk (8 GB of FP64 tensors)
+    std::vector<uint64_t *> nexts;
+    std::vector<int64_t> ncnt;
+    *d_next = nullptr;
+    *n_next = 0;
+    for (int64_t o0 = 0; o0 < n_oct; o0 += CH) {
+        int64_t m = n_oct - o0 < CH ? n_oct - o0 : CH;
+        const uint64_t *par = d_parents + o0;
+        double *dA = nullptr;
+        uint8_t *dec = nullptr;
+        int rc = gs_alloc((void **)&dA, sizeof(double) * 64 * 8 * (size_t)m, st);
+        if (!rc) rc = gs_alloc((void **)&dec, (size_t)m * 8, st);
+        if (rc) { gs_free(dA, st); return rc; }
+        (void)mode;
+        rc = gs_accum_f64(P, level, par, nullptr, m, dA, d_pairs, d_status, st);
+        if (!rc) rc = gs_estimate_f64(P, level, dA, m * 8, par, nullptr, dec, nullptr, st);
+        gs_free(dA, st);
+        uint64_t *acc = nullptr;
+        if (!rc) rc = gs_alloc((void **)&acc, sizeof(uint64_t) * (size_t)m * 8, st);
+        uint64_t *nx = nullptr;
+        int64_t nn = 0, na = 0;
+        if (!rc) rc = gs_level_compact(P, level, par, nullptr, m, dec, &nx, &nn, acc, m * 8, &na, d_counters, st);
+        gs_free(dec, st);
+        if (rc) { gs_free(acc, st); gs_free(nx, st); return rc; }
+        acc_parts.push_back(acc);
+        acc_counts.push_back(na);
+        if (nx) { nexts.push_back(nx); ncnt.push_back(nn); }
+    }
+    int64_t total = 0;
+    for (auto v : ncnt) total += v;
+    if (nexts.size() == 1) {
+        *d_next = nexts[0];
+    } else if (total > 0) {
+        int rc = gs_alloc((void **)d_next, sizeof(uint64_t) * (size_t)total, st);
+        if (rc) return rc;
+        int64_t off = 0;
+        for (size_t i = 0; i < nexts.size(); i++) {
+            GS_CHECK(cudaMemcpyAsync(*d_next + off, nexts[i], sizeof(uint64_t) * (size_t)ncnt[i],
+                                     cudaMemcpyDeviceToDevice, st));
+            off += ncnt[i];
+            gs_free(nexts[i], st);
+        }
+    }
+    *n_next = total;
+    return GS_OK;
+}
+
+struct MeshDev {
+    double *vxyz = nullptr;
+    uint64_t *vkeys = nullptr;
+    int32_t *tri = nullptr;
+    uint64_t *cubes = nullptr;
+    int64_t nv = 0, nt = 0, nc = 0;
+};
+
+static int finish_output(MeshDev &M, const gs_options &o, gs_mesh *out, cudaStream_t st)
+{
+    out->n_vertices = M.nv;
+    out->n_triangles = M.nt;
+    out->n_cubes = M.nc;
+    if (o.device_output) {
+        // hand over as plain cudaMalloc memory (mesh_free uses cudaFree)
+        out->on_device = 1;
+        double *v = nullptr; int32_t *t = nullptr; uint64_t *k = nullptr, *cb = nullptr;
+        GS_CHECK(cudaMalloc(&v, sizeof(double) * 3 * (size_t)(M.nv + 1)));
+        GS_CHECK(cudaMalloc(&t, sizeof(int32_t) * 3 * (size_t)(M.nt + 1)));
+        GS_CHECK(cudaMalloc(&k, sizeof(uint64_t) * (size_t)(M.nv + 1)));
+        GS_CHECK(cudaMalloc(&cb, sizeof(uint64_t) * (size_t)(M.nc + 1)));
+        out->vertices = v; out->triangles = t; out->vertex_keys = k; out->cube_keys = cb;
+        if (M.nv) {
+            GS_CHECK(cudaMemcpyAsync(v, M.vxyz, sizeof(double) * 3 * (size_t)M.nv, cudaMemcpyDeviceToDevice, st));
+            GS_CHECK(cudaMemcpyAsync(k, M.vkeys, sizeof(uint64_t) * (size_t)M.nv, cudaMemcpyDeviceToDevice, st));
+        }
+        if (M.nt) GS_CHECK(cudaMemcpyAsync(t, M.tri, sizeof(int32_t) * 3 * (size_t)M.nt, cudaMemcpyDeviceToDevice, st));
+        if (M.nc) GS_CHECK(cudaMemcpyAsync(cb, M.cubes, sizeof(uint64_t) * (size_t)M.nc, cudaMemcpyDeviceToDevice, st));
+    } else {
+        out->on_device = 0;
+        out->vertices = (double *)malloc(sizeof(double) * 3 * (size_t)(M.nv + 1));
+        out->triangles = (int32_t *)malloc(sizeof(int32_t) * 3 * (size_t)(M.nt + 1));
+        out->vertex_keys = (uint64_t *)malloc(sizeof(uint64_t) * (size_t)(M.nv + 1));
+        out->cube_keys = (uint64_t *)malloc(sizeof(uint64_t) * (size_t)(M.nc + 1));
+        if (!out->vertices || !out->triangles || !out->vertex_keys || !out->cube_keys)
+            return gs_fail(GS_ERR_OOM, "host output allocation");
+        if (M.nv) {
+            GS_CHECK(cudaMemcpyAsync(out->vertices, M.vxyz, sizeof(double) * 3 * (size_t)M.nv, cudaMemcpyDeviceToHost, st));
+            GS_CHECK(cudaMemcpyAsync(out->vertex_keys, M.vkeys, sizeof(uint64_t) * (size_t)M.nv, cudaMemcpyDeviceToHost, st));
+        }
+        if (M.nt)
+            GS_CHECK(cudaMemcpyAsync(out->triangles, M.tri, sizeof(int32_t) * 3 * (size_t)M.nt, cudaMemcpyDeviceToHost, st));
+        if (M.nc)
+            GS_CHECK(cudaMemcpyAsync(out->cube_keys, M.cubes, sizeof(uint64_t) * (size_t)M.nc, cudaMemcpyDeviceToHost, st));
+    }
+    GS_CHECK(cudaStreamSynchronize(st));
+    return GS_OK;
+}
+
+// triangulate the final cubes given lattice vertex values; shared by the
+// molecule path and the grid entry point
+static int surface_from_values(const GsProblem &P, const uint64_t *d_cubes, int64_t nc, const int32_t *d_cvid,
+                               const double *d_phi, DevBufs &B, unsigned *d_status, unsigned long long *d_tcount,
+                               MeshDev &M, gs_stats *stats, Timer &T)
+{
+    cudaStream_t st = B.st;
+    int t0 = T.mark();
+    int32_t *nbr = nullptr;
+    int rc = gs_neighbours(d_cubes, nc, &nbr, d_status, st);
+    if (rc) return rc;
+    B.keep(nbr);
+    TriCtx X;
+    X.cubes = d_cubes; X.cvid = d_cvid; X.nbr = nbr; X.phi = d_phi; X.ncubes = nc; X.c = P.c;
+    for (int a = 0; a < 3; a++) X.origin[a] = P.origin[a];
+    X.min_edge = P.min_edge; X.max_depth = P.max_depth;
+    uint64_t *tk = nullptr, *pk = nullptr;
+    double *pxyz = nullptr;
+    int64_t ntri = 0, npt = 0;
+    rc = gs_triangulate(X, &tk, &ntri, &pk, &pxyz, &npt, d_tcount, st);
+    B.keep(tk); B.keep(pk); B.keep(pxyz);
+    if (rc) return rc;
+    int t1 = T.mark();
+    rc = gs_weld(pk, pxyz, npt, tk, ntri, &M.vkeys, &M.vxyz, &M.nv, &M.tri, d_status, st);
+    B.keep(M.vkeys); B.keep(M.vxyz); B.keep(M.tri);
+    if (rc) return rc;
+    M.nt = ntri;
+    int t2 = T.mark();
+    rc = check_status(d_status, st, "triangulation");
+    if (rc) return rc;
+    if (stats) {
+        stats->ms_triangulate = T.ms(t0, t1);
+        stats->ms_weld = T.ms(t1, t2);
+        stats->n_points = npt;
+        unsigned long long h[3];
+        GS_CHECK(cudaMemcpy(h, d_tcount, sizeof(h), cudaMemcpyDeviceToHost));
+        stats->loop_errors = (int64_t)h[0];
+        stats->degenerate_ears = (int64_t)h[1];
+        stats->n_cubes_surface = (int64_t)h[2];
+    }
+    return GS_OK;
+}
+
+__global__ void k_fill_grid_phi(const uint64_t *vkeys, int64_t nv, const double *vals, int64_t nx, int64_t ny,
+                                double *phi)
+{
+    int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= nv) return;
+    uint64_t k = vkeys[i];
+    phi[i] = vals[gk_x(k) + (nx + 1) * (gk_y(k) + (ny + 1) * gk_z(k))];
+}
+
+__global__ void k_grid_cubes(int64_t nx, int64_t ny, int64_t nz, uint64_t *cubes)
+{
+    int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= nx * ny * nz) return;
+    cubes[i] = gk_make(i % nx, (i / nx) % ny, i / (nx * ny), GT_CUBE, 0);
+}
+
+static int mesh_impl(const double *atoms, const double *radii, int64_t n, double D, double c, double precision,
+                     int max_depth, const gs_options &o, gs_mesh *out, cudaStream_t st)
+{
+    gs_stats local;
+    gs_stats *stats = o.stats ? o.stats : &local;
+    memset(stats, 0, sizeof(*stats));
+    DevBufs B(st);
+    Timer T(st);
+    int tstart = T.mark();
+    unsigned *d_status = nullptr;
+    unsigned long long *d_cnt = nullptr;  // [0..4] level decisions, [8] pairs, [9] vertex terms, [10..12] triangulation
+    int rc = B.get(&d_status, 1);
+    if (!rc) rc = B.get(&d_cnt, 16);
+    if (rc) return rc;
+    GS_CHECK(cudaMemsetAsync(d_status, 0, sizeof(unsigned), st));
+    GS_CHECK(cudaMemsetAsync(d_cnt, 0, 16 * sizeof(unsigned long long), st));
+    Prepared PR;
+    rc = prepare(atoms, radii, n, D, c, o.cutoff_rel, precision, o.min_edge, max_depth, B, d_status, &PR, stats, T);
+    if (rc) return rc;
+    const GsProblem &P = PR.P;
+
+    // ---- level loop (section 2.2, steps 1-3)
+    int tl0 = T.mark();
+    std::vector<uint64_t *> acc_all;
+    std::vector<int64_t> acc_cnt;
+    uint64_t *parents = nullptr;
+    int64_t n_oct = 0;
+    rc = gs_root_blocks(P, &parents, &n_oct, st);
+    if (rc) return rc;
+    B.keep(parents);
+    for (int l = 0; l <= max_depth && n_oct > 0; l++) {
+        int ta = T.mark();
+        GS_CHECK(cudaMemsetAsync(d_cnt, 0, 5 * sizeof(unsigned long long), st));
+        uint64_t *next = nullptr;
+        int64_t nn = 0;
+        std::vector<uint64_t *> parts;
+        std::vector<int64_t> cnts;
+        rc = run_level(P, l, parents, n_oct, o.precision_mode, B, parts, cnts, &next, &nn, d_cnt, d_cnt + 8,
+                       d_status);
+        for (size_t i = 0; i < parts.size(); i++) { B.keep(parts[i]); acc_all.push_back(parts[i]); acc_cnt.push_back(cnts[i]); }
+        if (parents) B.release(parents);
+        if (rc) { gs_free(next, st); return rc; }
+        parents = next;
+        B.keep(parents);
+        n_oct = nn;
+        int tb = T.mark();
+        unsigned long long h[5];
+        GS_CHECK(cudaMemcpyAsync(h, d_cnt, sizeof(h), cudaMemcpyDeviceToHost, st));
+        GS_CHECK(cudaStreamSynchronize(st));
+        stats->examined[l] = (int64_t)h[0]; stats->discarded[l] = (int64_t)h[1]; stats->accepted[l] = (int64_t)h[2];
+        stats->forced[l] = (int64_t)h[3]; stats->split[l] = (int64_t)h[4];
+        stats->ms_level[l] = T.ms(ta, tb);
+    }
+    if (parents) B.release(parents);
+    rc = check_status(d_status, st, "levels");
+    if (rc) return rc;
+    int64_t nc = 0;
+    for (auto v : acc_cnt) nc += v;
+    uint64_t *cubes = nullptr;
+    rc = gs_alloc((void **)&cubes, sizeof(uint64_t) * (size_t)(nc + 1), st);
+    if (rc) return rc;
+    {
+        int64_t off = 0;
+        for (size_t i = 0; i < acc_all.size(); i++) {
+            if (acc_cnt[i])
+                GS_CHECK(cudaMemcpyAsync(cubes + off, acc_all[i], sizeof(uint64_t) * (size_t)acc_cnt[i],
+                                         cudaMemcpyDeviceToDevice, st));
+            off += acc_cnt[i];
+            B.release(acc_all[i]);
+        }
+    }
+    int tl1 = T.mark();
+
+    // ---- conformity across faces and edges (section 2.3, neighbouring cubes)
+    int64_t splits = 0;
+    rc = gs_conformity(&cubes, &nc, max_depth, &splits, d_status, st);
+    B.keep(cubes);
+    if (rc) return rc;
+    int tc1 = T.mark();
+
+    // ---- lattice vertices and the field there (eq linear1's corner values)
+    uint64_t *vkeys = nullptr;
+    int32_t *cvid = nullptr;
+    int64_t nv = 0;
+    rc = gs_lattice_vertices(cubes, nc, max_depth, &vkeys, &nv, &cvid, d_status, st);
+    B.keep(vkeys); B.keep(cvid);
+    if (rc) return rc;
+    double *phi = nullptr;
+    rc = B.get(&phi, (size_t)nv + 1);
+    if (rc) return rc;
+    if (o.precision_mode == GS_PREC_FP64) {
+        rc = gs_field_f64(P, vkeys, nullptr, nv, phi, nullptr, d_cnt + 9, st);
+    } else {
+        rc = gs_field_f64(P, vkeys, nullptr, nv, phi, nullptr, d_cnt + 9, st);
+    }
+    if (rc) return rc;
+    int tf1 = T.mark();
+
+    // ---- triangulation and welding
+    MeshDev M;
+    M.cubes = cubes;
+    M.nc = nc;
+    rc = surface_from_values(P, cubes, nc, cvid, phi, B, d_status, d_cnt + 10, M, stats, T);
+    if (rc) return rc;
+    int tw1 = T.mark();
+    rc = finish_output(M, o, out, st);
+    if (rc) return rc;
+    int tend = T.mark();
+    GS_CHECK(cudaStreamSynchronize(st));
+    unsigned long long h[16];
+    GS_CHECK(cudaMemcpy(h, d_cnt, sizeof(h), cudaMemcpyDeviceToHost));
+    stats->pair_terms = (int64_t)h[8];
+    stats->vertex_terms = (int64_t)h[9];
+    stats->conformity_splits = splits;
+    stats->n_cubes_final = nc;
+    stats->n_lattice_vertices = nv;
+    stats->n_vertices = M.nv;
+    stats->n_triangles = M.nt;
+    stats->ms_levels = T.ms(tl0, tl1);
+    stats->ms_conformity = T.ms(tl1, tc1);
+    stats->ms_field = T.ms(tc1, tf1);
+    stats->ms_download = T.ms(tw1, tend);
+    stats->ms_total = T.ms(tstart, tend);
+    return GS_OK;
+}
+
+extern "C" int mesh_gaussian_surface(const double *atoms, const double *radii, int64_t n_atoms, double D, double c,
+                                     double precision, int max_depth, const gs_options *opt, gs_mesh *out)
+{
+    if (!out) return gs_fail(GS_ERR_ARG, "out is NULL");
+    memset(out, 0, sizeof(*out));
+    gs_options o = opt ? *opt : gs_default_options();
+    if (!atoms || !radii || n_atoms <= 0 || n_atoms > ((int64_t)1 << 31) - 1)
+        return gs_fail(GS_ERR_ARG, "need 1 <= n_atoms < 2^31 and non-NULL inputs");
+    if (!(D > 0) || !std::isfinite(D) || !(c > 0) || !std::isfinite(c) || !(precision > 0) || !std::isfinite(precision))
+        return gs_fail(GS_ERR_ARG, "D, c and precision must be positive and finite");
+    if (max_depth < 0 || max_depth > 20) return gs_fail(GS_ERR_ARG, "max_depth must be in [0, 20]");
+    if (!(o.min_edge > 0) || !std::isfinite(o.min_edge)) return gs_fail(GS_ERR_ARG, "min_edge must be positive");
+    if (!(o.cutoff_rel > 0 && o.cutoff_rel < 1)) return gs_fail(GS_ERR_ARG, "cutoff_rel must be in (0,1)");
+    if (o.precision_mode != GS_PREC_FP64 && o.precision_mode != GS_PREC_MIXED)
+        return gs_fail(GS_ERR_ARG, "unknown precision mode");
+    int rc = device_setup();
+    if (rc) return rc;
+    cudaStream_t st = (cudaStream_t)o.cuda_stream;
+    bool own = false;
+    if (!st) {
+        GS_CHECK(cudaStreamCreateWithFlags(&st, cudaStreamNonBlocking));
+        own = true;
+    }
+    rc = mesh_impl(atoms, radii, n_atoms, D, c, precision, max_depth, o, out, st);
+    cudaError_t e = cudaStreamSynchronize(st);
+    if (own) cudaStreamDestroy(st);
+    if (!rc && e != cudaSuccess) rc = gs_fail_cuda(e, "stream", __FILE__, __LINE__);
+    if (rc) mesh_free(out);
+    return rc;
+}
+
+extern "C" int gs_triangulate_grid(int64_t nx, int64_t ny, int64_t nz, const double *values, double c,
+                                   const gs_options *opt, gs_mesh *out)
+{
+    if (!out) return gs_fail(GS_ERR_ARG, "out is NULL");
+    memset(out, 0, sizeof(*out));
+    if (!values || nx <= 0 || ny <= 0 || nz <= 0 || nx > 4096 || ny > 4096 || nz > 4096)
+        return gs_fail(GS_ERR_ARG, "grid dimensions must be in [1, 4096]");
+    gs_options o = opt ? *opt : gs_default_options();
+    int rc = device_setup();
+    if (rc) return rc;
+    cudaStream_t st = (cudaStream_t)o.cuda_stream;
+    bool own = false;
+    if (!st) { GS_CHECK(cudaStreamCreateWithFlags(&st, cudaStreamNonBlocking)); own = true; }
+    {
+        DevBufs B(st);
+        Timer T(st);
+        gs_stats local;
+        gs_stats *stats = o.stats ? o.stats : &local;
+        memset(stats, 0, sizeof(*stats));
+        GsProblem P;
+        memset(&P, 0, sizeof(P));
+        P.c = c; P.min_edge = 1.0; P.max_depth = 0;
+        int64_t nvals = (nx + 1) * (ny + 1) * (nz + 1), nc = nx * ny * nz;
+        const double *d_vals = values;
+        unsigned *d_status = nullptr;
+        unsigned long long *d_cnt = nullptr;
+        uint64_t *cubes = nullptr;
+        rc = B.get(&d_status, 1);
+        if (!rc) rc = B.get(&d_cnt, 16);
+        if (!rc) rc = B.get(&cubes, (size_t)nc);
+        if (!rc && !on_device(values)) {
+            double *p;
+            rc = B.get(&p, (size_t)nvals);
+            if (!rc) {
+                cudaError_t e = cudaMemcpyAsync(p, values, sizeof(double) * (size_t)nvals, cudaMemcpyHostToDevice, st);
+                if (e != cudaSuccess) rc = gs_fail_cuda(e, "grid upload", __FILE__, __LINE__);
+            }
+            d_vals = p;
+        }
+        if (!rc) {
+            cudaMemsetAsync(d_status, 0, sizeof(unsigned), st);
+            cudaMemsetAsync(d_cnt, 0, 16 * sizeof(unsigned long long), st);
+            k_grid_cubes<<<(unsigned)((nc + 255) / 256), 256, 0, st>>>(nx, ny, nz, cubes);
+        }
+        uint64_t *vkeys = nullptr;
+        int32_t *cvid = nullptr;
+        int64_t nv = 0;
+        if (!rc) rc = gs_lattice_vertices(cubes, nc, 0, &vkeys, &nv, &cvid, d_status, st);
+        B.keep(vkeys); B.keep(cvid);
+        double *phi = nullptr;
+        if (!rc) rc = B.get(&phi, (size_t)nv + 1);
+        if (!rc) k_fill_grid_phi<<<(unsigned)((nv + 255) / 256), 256, 0, st>>>(vkeys, nv, d_vals, nx, ny, phi);
+        MeshDev M;
+        M.cubes = cubes; M.nc = nc;
+        if (!rc) rc = surface_from_values(P, cubes, nc, cvid, phi, B, d_status, d_cnt + 10, M, stats, T);
+        if (!rc) rc = finish_output(M, o, out, st);
+        if (!rc) { stats->n_vertices = M.nv; stats->n_triangles = M.nt; stats->n_cubes_final = nc; }
+    }
+    cudaError_t e = cudaStreamSynchronize(st);
+    if (own) cudaStreamDestroy(st);
+    if (!rc && e != cudaSuccess) rc = gs_fail_cuda(e, "stream", __FILE__, __LINE__);
+    if (rc) mesh_free(out);
+    return rc;
+}
+
+// copy a device result back where the caller wants it
+static int put_out(void *dst, const void *src, size_t bytes, cudaStream_t st)
+{
+    if (!dst || !bytes) return GS_OK;
+    GS_CHECK(cudaMemcpyAsync(dst, src, bytes, on_device(dst) ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost, st));
+    return GS_OK;
+}
+
+extern "C" int gs_eval_field(const double *atoms, const double *radii, int64_t n_atoms, double D, double c,
+                             double cutoff_rel, const double *points, int64_t n_points, double *phi, double *grad,
+                             int precision_mode, void *stream)
+{
+    if (!atoms || !radii || n_atoms <= 0 || n_atoms >= ((int64_t)1 << 31) || n_points < 0 || (n_points && (!points || !phi)))
+        return gs_fail(GS_ERR_ARG, "bad sizes or NULL pointers");
+    if (!(D > 0) || !(c > 0) || !(cutoff_rel > 0 && cutoff_rel < 1)) return gs_fail(GS_ERR_ARG, "bad D, c or cutoff");
+    if (precision_mode != GS_PREC_FP64 && precision_mode != GS_PREC_MIXED) return gs_fail(GS_ERR_ARG, "bad mode");
+    int rc = device_setup();
+    if (rc) return rc;
+    cudaStream_t st = (cudaStream_t)stream;
+    bool own = false;
+    if (!st) { GS_CHECK(cudaStreamCreateWithFlags(&st, cudaStreamNonBlocking)); own = true; }
+    {
+        DevBufs B(st);
+        Timer T(st);
+        unsigned *d_status = nullptr;
+        rc = B.get(&d_status, 1);
+        if (!rc) { cudaMemsetAsync(d_status, 0, sizeof(unsigned), st); }
+        Prepared PR;
+        if (!rc) rc = prepare(atoms, radii, n_atoms, D, c, cutoff_rel, 1.0, 0.25, 0, B, d_status, &PR, nullptr, T);
+        const double *d_pts = points;
+        double *d_phi = nullptr, *d_grad = nullptr;
+        if (!rc && n_points > 0) {
+            if (!on_device(points)) {
+                double *p;
+                rc = B.get(&p, 3 * (size_t)n_points);
+                if (!rc) {
+                    cudaError_t e = cudaMemcpyAsync(p, points, sizeof(double) * 3 * (size_t)n_points, cudaMemcpyHostToDevice, st);
+                    if (e != cudaSuccess) rc = gs_fail_cuda(e, "points upload", __FILE__, __LINE__);
+                }
+                d_pts = p;
+            }
+            if (!rc) rc = B.get(&d_phi, (size_t)n_points);
+            if (!rc && grad) rc = B.get(&d_grad, 3 * (size_t)n_points);
+            // points may lie outside the root grid: the cell list clamps them to its border cells
+            if (!rc) {
+                if (precision_mode == GS_PREC_FP64) rc = gs_field_f64(PR.P, nullptr, d_pts, n_points, d_phi, d_grad, nullptr, st);
+                else rc = gs_field_f32(PR.P, nullptr, d_pts, n_points, d_phi, d_grad, nullptr, nullptr, st);
+            }
+            if (!rc) rc = put_out(phi, d_phi, sizeof(double) * (size_t)n_points, st);
+            if (!rc && grad) rc = put_out(grad, d_grad, sizeof(double) * 3 * (size_t)n_points, st);
+        }
+        if (!rc) rc = check_status(d_status, st, "field");
+    }
+    cudaError_t e = cudaStreamSynchronize(st);
+    if (own) cudaStreamDestroy(st);
+    if (!rc && e != cudaSuccess) rc = gs_fail_cuda(e, "stream", __FILE__, __LINE__);
+    return rc;
+}
+
+extern "C" int gs_cube_decisions(const double *atoms, const double *radii, int64_t n_atoms, double D, double c,
+                                 double precision, double min_edge, int max_depth, double cutoff_rel,
+                                 const uint64_t *cube_keys, int64_t n_cubes, double *A, double *bounds, int32_t *dec,
+                                 int precision_mode, void *stream)
+{
+    if (!atoms || !radii || n_atoms <= 0 || n_atoms >= ((int64_t)1 << 31) || n_cubes < 0 || (n_cubes && (!cube_keys || !dec)))
+        return gs_fail(GS_ERR_ARG, "bad sizes or NULL pointers");
+    if (!(D > 0) || !(c > 0) || !(precision > 0) || !(min_edge > 0) || max_depth < 0 || max_depth > 20 ||
+        !(cutoff_rel > 0 && cutoff_rel < 1))
+        return gs_fail(GS_ERR_ARG, "bad parameters");
+    (void)precision_mode;
+    int rc = device_setup();
+    if (rc) return rc;
+    cudaStream_t st = (cudaStream_t)stream;
+    bool own = false;
+    if (!st) { GS_CHECK(cudaStreamCreateWithFlags(&st, cudaStreamNonBlocking)); own = true; }
+    {
+        DevBufs B(st);
+        Timer T(st);
+        unsigned *d_status = nullptr;
+        rc = B.get(&d_status, 1);
+        if (!rc) cudaMemsetAsync(d_status, 0, sizeof(unsigned), st);
+        Prepared PR;
+        if (!rc) rc = prepare(atoms, radii, n_atoms, D, c, cutoff_rel, precision, min_edge, max_depth, B, d_status, &PR, nullptr, T);
+        // group by level; each cube becomes its own octet with one valid child
+        std::vector<uint64_t> hk((size_t)n_cubes);
+        if (!rc && n_cubes) {
+            cudaError_t e = cudaMemcpyAsync(hk.data(), cube_keys, sizeof(uint64_t) * (size_t)n_cubes,
+                                            on_device(cube_keys) ? cudaMemcpyDeviceToHost : cudaMemcpyHostToHost, st);
+            if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+            if (e != cudaSuccess) rc = gs_fail_cuda(e, "keys", __FILE__, __LINE__);
+        }
+        std::vector<double> hA, hB;
+        std::vector<int32_t> hD((size_t)n_cubes);
+        if (A) hA.resize((size_t)n_cubes * 64);
+        if (bounds) hB.resize((size_t)n_cubes * 6);
+        for (int l = 0; l <= max_depth && !rc; l++) {
+            std::vector<int64_t> idx;
+            std::vector<uint64_t> par;
+            std::vector<uint8_t> vm;
+            for (int64_t i = 0; i < n_cubes; i++)
+                if ((int)gk_level(hk[i]) == l) {
+                    uint64_t k = hk[i];
+                    idx.push_back(i);
+                    par.push_back(gk_make(gk_x(k) >> 1, gk_y(k) >> 1, gk_z(k) >> 1, GT_CUBE, l > 0 ? l - 1 : 0));
+                    vm.push_back((uint8_t)(1u << ((gk_x(k) & 1) | ((gk_y(k) & 1) << 1) | ((gk_z(k) & 1) << 2))));
+                }
+            int64_t m = (int64_t)idx.size();
+            if (!m) continue;
+            uint64_t *dp; uint8_t *dv, *dd; double *dA, *dB;
+            rc = B.get(&dp, (size_t)m);
+            if (!rc) rc = B.get(&dv, (size_t)m);
+            if (!rc) rc = B.get(&dd, (size_t)m * 8);
+            if (!rc) rc = B.get(&dA, (size_t)m * 8 * 64);
+            if (!rc) rc = B.get(&dB, (size_t)m * 8 * 6);
+            if (rc) break;
+            cudaMemcpyAsync(dp, par.data(), sizeof(uint64_t) * (size_t)m, cudaMemcpyHostToDevice, st);
+            cudaMemcpyAsync(dv, vm.data(), (size_t)m, cudaMemcpyHostToDevice, st);
+            rc = gs_accum_f64(PR.P, l, dp, dv, m, dA, nullptr, d_status, st);
+            if (!rc) rc = gs_estimate_f64(PR.P, l, dA, m * 8, dp, dv, dd, dB, st);
+            std::vector<double> tA((size_t)m * 8 * 64), tB((size_t)m * 8 * 6);
+            std::vector<uint8_t> tD((size_t)m * 8);
+            if (!rc) {
+                cudaMemcpyAsync(tA.data(), dA, sizeof(double) * tA.size(), cudaMemcpyDeviceToHost, st);
+                cudaMemcpyAsync(tB.data(), dB, sizeof(double) * tB.size(), cudaMemcpyDeviceToHost, st);
+                cudaMemcpyAsync(tD.data(), dd, tD.size(), cudaMemcpyDeviceToHost, st);
+                cudaError_t e = cudaStreamSynchronize(st);
+                if (e != cudaSuccess) rc = gs_fail_cuda(e, "decisions", __FILE__, __LINE__);
+            }
+            for (int64_t t = 0; t < m && !rc; t++) {
+                int ch = __builtin_ctz(vm[t]);
+                int64_t q = 8 * t + ch, i = idx[t];
+                hD[i] = tD[q];
+                if (A) memcpy(&hA[64 * i], &tA[64 * q], 64 * sizeof(double));
+                if (bounds) memcpy(&hB[6 * i], &tB[6 * q], 6 * sizeof(double));
+            }
+        }
+        if (!rc) rc = check_status(d_status, st, "decisions");
+        if (!rc && n_cubes) {
+            bool ddev = on_device(dec);
+            cudaMemcpyKind k = ddev ? cudaMemcpyHostToDevice : cudaMemcpyHostToHost;
+            cudaMemcpy(dec, hD.data(), sizeof(int32_t) * (size_t)n_cubes, k);
+            if (A) cudaMemcpy(A, hA.data(), sizeof(double) * hA.size(), on_device(A) ? cudaMemcpyHostToDevice : cudaMemcpyHostToHost);
+            if (bounds) cudaMemcpy(bounds, hB.data(), sizeof(double) * hB.size(), on_device(bounds) ? cudaMemcpyHostToDevice : cudaMemcpyHostToHost);
+        }
+    }
+    cudaError_t e = cudaStreamSynchronize(st);
+    if (own) cudaStreamDestroy(st);
+    if (!rc && e != cudaSuccess) rc = gs_fail_cuda(e, "stream", __FILE__, __LINE__);
+    return rc;
+}
+
+extern "C" int gs_bin_atoms(const double *atoms, int64_t n_atoms, double cell_size, const double *origin,
+                            const int64_t *dims, int32_t *cell_start, int32_t *atom_perm, void *stream)
+{
+    if (!atoms || n_atoms <= 0 || n_atoms >= ((int64_t)1 << 31) || !(cell_size > 0) || !origin || !dims ||
+        !cell_start || !atom_perm)
+        return gs_fail(GS_ERR_ARG, "bad arguments");
+    int cd[3];
+    int64_t ncell = 1;
+    for (int a = 0; a < 3; a++) {
+        if (dims[a] <= 0 || dims[a] > (1 << 20)) return gs_fail(GS_ERR_ARG, "bad dims");
+        cd[a] = (int)dims[a];
+        ncell *= dims[a];
+    }
+    if (ncell >= ((int64_t)1 << 31)) return gs_fail(GS_ERR_ARG, "too many cells");
+    int rc = device_setup();
+    if (rc) return rc;
+    cudaStream_t st = (cudaStream_t)stream;
+    bool own = false;
+    if (!st) { GS_CHECK(cudaStreamCreateWithFlags(&st, cudaStreamNonBlocking)); own = true; }
+    {
+        DevBufs B(st);
+        const double *d_xyz = atoms;
+        if (!on_device(atoms)) {
+            double *p;
+            rc = B.get(&p, 3 * (size_t)n_atoms);
+            if (!rc) cudaMemcpyAsync(p, atoms, sizeof(double) * 3 * (size_t)n_atoms, cudaMemcpyHostToDevice, st);
+            d_xyz = p;
+        }
+        int32_t *cs, *pm;
+        if (!rc) rc = B.get(&cs, (size_t)ncell + 1);
+        if (!rc) rc = B.get(&pm, (size_t)n_atoms);
+        if (!rc) rc = gs_build_cells(d_xyz, n_atoms, origin, cell_size, cd, cs, pm, st);
+        if (!rc) rc = put_out(cell_start, cs, sizeof(int32_t) * (size_t)(ncell + 1), st);
+        if (!rc) rc = put_out(atom_perm, pm, sizeof(int32_t) * (size_t)n_atoms, st);
+    }
+    cudaError_t e = cudaStreamSynchronize(st);
+    if (own) cudaStreamDestroy(st);
+    if (!rc && e != cudaSuccess) rc = gs_fail_cuda(e, "stream", __FILE__, __LINE__);
+    return rc;
+}

@@ -1,0 +1,70 @@
+// gs_host.cuh -- host-side interfaces between the library's translation units.
+#pragma once
+#include "gs_internal.cuh"
+
+struct GsAtomsSoA {
+    double *x, *y, *z, *r, *R2, *w;
+    float *fx, *fy, *fz;
+};
+
+// gs_bin.cu
+int gs_prep_atoms(const double *d_xyz, const double *d_r, int64_t n, double D, double KD, double *d_R2, double *d_w,
+                  double bbox[6], double *r2max, unsigned *d_status, cudaStream_t st);
+int gs_build_cells(const double *d_xyz, int64_t n, const double origin[3], double cell, const int cdim[3],
+                   int32_t *d_cell_start, int32_t *d_perm, cudaStream_t st);
+int gs_gather_atoms(const int32_t *d_perm, int64_t n, const double *d_xyz, const double *d_r, const double *d_R2,
+                    const double *d_w, const double origin[3], double cell, const int cdim[3], GsAtomsSoA *soa,
+                    cudaStream_t st);
+
+// gs_level.cu
+int gs_quadrature_init(void);
+// accumulate A for the 8 children of each parent (level-1 coords in parents,
+// or the implicit root blocks when parents == NULL); vmask (nullable) selects
+// children; A_out [n_oct*8][64]
+int gs_accum_f64(const GsProblem &P, int level, const uint64_t *d_parents, const uint8_t *d_vmask, int64_t n_oct,
+                 double *d_A, unsigned long long *d_pairs, unsigned *d_status, cudaStream_t st);
+int gs_estimate_f64(const GsProblem &P, int level, const double *d_A, int64_t n_cubes, const uint64_t *d_parents,
+                    const uint8_t *d_vmask, uint8_t *d_dec, double *d_bounds, cudaStream_t st);
+// mixed precision: FP32 accumulate (Kahan) + error bound, FP32 estimate with margins
+int gs_accum_f32(const GsProblem &P, int level, const uint64_t *d_parents, const uint8_t *d_vmask, int64_t n_oct,
+                 float *d_A, float *d_err, unsigned long long *d_pairs, unsigned *d_status, cudaStream_t st);
+int gs_estimate_f32(const GsProblem &P, int level, const float *d_A, const float *d_err, int64_t n_cubes,
+                    const uint64_t *d_parents, const uint8_t *d_vmask, uint8_t *d_dec, uint8_t *d_flag,
+                    cudaStream_t st);
+
+// gs_field.cu
+int gs_field_f64(const GsProblem &P, const uint64_t *d_vkeys, const double *d_points, int64_t n, double *d_phi,
+                 double *d_grad, unsigned long long *d_terms, cudaStream_t st);
+int gs_field_f32(const GsProblem &P, const uint64_t *d_vkeys, const double *d_points, int64_t n, double *d_phi,
+                 double *d_grad, float *d_err, unsigned long long *d_terms, cudaStream_t st);
+int gs_level_compact(const GsProblem &P, int level, const uint64_t *d_parents, const uint8_t *d_vmask, int64_t n_oct,
+                     const uint8_t *d_dec, uint64_t **d_next, int64_t *n_next, uint64_t *d_acc_base,
+                     int64_t acc_cap, int64_t *n_acc, unsigned long long *d_counters, cudaStream_t st);
+
+int gs_root_blocks(const GsProblem &P, uint64_t **d_keys, int64_t *n, cudaStream_t st);
+
+// gs_mesh.cu
+int gs_hash_make(GsHash *H, int64_t n, cudaStream_t st);
+void gs_hash_free(GsHash *H, cudaStream_t st);
+int gs_conformity(uint64_t **d_cubes, int64_t *n, int max_depth, int64_t *splits, unsigned *d_status, cudaStream_t st);
+int gs_lattice_vertices(const uint64_t *d_cubes, int64_t n, int max_depth, uint64_t **d_vkeys, int64_t *nv,
+                        int32_t **d_cvid, unsigned *d_status, cudaStream_t st);
+int gs_neighbours(const uint64_t *d_cubes, int64_t n, int32_t **d_nbr, unsigned *d_status, cudaStream_t st);
+int gs_weld(const uint64_t *d_pk, const double *d_pxyz, int64_t npt, const uint64_t *d_tk, int64_t ntri,
+            uint64_t **d_vkeys, double **d_vxyz, int64_t *nv, int32_t **d_tri, unsigned *d_status, cudaStream_t st);
+
+// gs_tri.cu
+struct TriCtx {
+    const uint64_t *cubes;
+    const int32_t *cvid;    // [ncubes][8] lattice-vertex ids of the corners
+    const int32_t *nbr;     // [ncubes][6]: same-size neighbour across face (axis a, side s) at 2a+s, -1 if none
+    const double *phi;      // field at lattice vertices
+    int64_t ncubes;
+    double c;
+    double origin[3];
+    double min_edge;
+    int max_depth;
+};
+// counters: [0] cubes skipped for an inconsistency, [1] degenerate ears, [2] surface cubes
+int gs_triangulate(const TriCtx &X, uint64_t **d_tri_keys, int64_t *ntri_total, uint64_t **d_pt_keys,
+                   double **d_pt_xyz, int64_t *npt_total, unsigned long long *d_counters, cudaStream_t st);

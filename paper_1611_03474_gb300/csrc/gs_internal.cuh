@@ -1,0 +1,143 @@
+// gs_internal.cuh -- shared device helpers of the GB300 Gaussian-surface
+// mesher (internal to the library; not part of the C ABI).
+#pragma once
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "../../include/gsmesh.h"
+
+// ---------------------------------------------------------------- keys
+// bits 0..17 x, 18..35 y, 36..53 z, 54..58 type, 59..63 level
+#define GK_BITS 18
+#define GK_MASK 0x3FFFFull
+#define GT_CUBE 30u
+#define GT_VERT 31u
+
+__host__ __device__ __forceinline__ uint64_t gk_make(uint64_t x, uint64_t y, uint64_t z, unsigned type,
+                                                     unsigned level)
+{
+    return x | (y << 18) | (z << 36) | ((uint64_t)type << 54) | ((uint64_t)level << 59);
+}
+__host__ __device__ __forceinline__ int64_t gk_x(uint64_t k) { return (int64_t)(k & GK_MASK); }
+__host__ __device__ __forceinline__ int64_t gk_y(uint64_t k) { return (int64_t)((k >> 18) & GK_MASK); }
+__host__ __device__ __forceinline__ int64_t gk_z(uint64_t k) { return (int64_t)((k >> 36) & GK_MASK); }
+__host__ __device__ __forceinline__ unsigned gk_level(uint64_t k) { return (unsigned)(k >> 59); }
+__host__ __device__ __forceinline__ unsigned gk_type(uint64_t k) { return (unsigned)((k >> 54) & 31u); }
+
+// ---------------------------------------------------------------- status word
+// Kernels never trap: they set bits in a device status word and return.
+#define GS_ST_CAPACITY 1u   // a fixed-size buffer or hash table overflowed
+#define GS_ST_LOOP 2u       // a bounded loop hit its iteration limit
+#define GS_ST_INPUT 4u      // non-finite or negative input
+#define GS_ST_LOOKUP 8u     // a key that must exist was not found
+
+// ---------------------------------------------------------------- decisions
+#define DEC_DISCARD 0
+#define DEC_ACCEPT 1
+#define DEC_SPLIT 2
+#define DEC_FORCED 3
+#define DEC_INVALID 255
+
+// ---------------------------------------------------------------- problem
+struct GsProblem {
+    int64_t n;           // atoms
+    double D, c, KD;     // KD = -ln(cutoff_rel c) / D
+    double precision;
+    double min_edge;
+    int max_depth;
+    double origin[3];
+    int64_t nroot[3];
+    double pad;          // largest cutoff radius
+    // cell list over the same origin
+    double cell;         // cell edge
+    double inv_cell;
+    int cdim[3];
+    // atoms in cell order (SoA)
+    const double *ax, *ay, *az, *ar, *aR2, *aw;   // centre, radius, cutoff^2, exp(D r^2)
+    const float *fx, *fy, *fz;                   // centres relative to their cell's lower corner (FP32)
+    const int32_t *cell_start;                   // [ncell + 1]
+};
+
+// cube edge at level l (exact power-of-two scaling)
+__host__ __device__ __forceinline__ double gs_h(const GsProblem &P, int l)
+{
+    return ldexp(P.min_edge, P.max_depth - l);
+}
+// world coordinate of lattice index i at level l on axis a: origin + i*h, no contraction
+__device__ __forceinline__ double gs_lat(const GsProblem &P, int a, int64_t i, int l)
+{
+    return __dadd_rn(P.origin[a], __dmul_rn((double)i, gs_h(P, l)));
+}
+
+// squared distance from x to [lo,hi] along one axis, then summed x,y,z
+__device__ __forceinline__ double gs_axis_gap(double lo, double hi, double x)
+{
+    double d = 0.0;
+    if (__dsub_rn(lo, x) > 0.0) d = __dsub_rn(lo, x);
+    else if (__dsub_rn(x, hi) > 0.0) d = __dsub_rn(x, hi);
+    return d;
+}
+__device__ __forceinline__ double gs_box_d2(const double *lo, const double *hi, double x, double y, double z)
+{
+    double dx = gs_axis_gap(lo[0], hi[0], x), dy = gs_axis_gap(lo[1], hi[1], y), dz = gs_axis_gap(lo[2], hi[2], z);
+    return __dadd_rn(__dadd_rn(__dmul_rn(dx, dx), __dmul_rn(dy, dy)), __dmul_rn(dz, dz));
+}
+
+// ---------------------------------------------------------------- hashing
+#define GS_EMPTY 0xFFFFFFFFFFFFFFFFull
+__host__ __device__ __forceinline__ uint64_t gs_mix(uint64_t k)
+{
+    k ^= k >> 33;
+    k *= 0xff51afd7ed558ccdull;
+    k ^= k >> 33;
+    k *= 0xc4ceb9fe1a85ec53ull;
+    k ^= k >> 33;
+    return k;
+}
+
+struct GsHash {
+    uint64_t *keys;   // capacity, GS_EMPTY when free
+    uint64_t *vals;   // capacity
+    uint64_t mask;    // capacity - 1 (power of two)
+};
+
+// insert key; returns slot (or -1 when full); the slot's value is left alone
+__device__ __forceinline__ int64_t gs_hash_insert(const GsHash &H, uint64_t key, unsigned *status)
+{
+    uint64_t s = gs_mix(key) & H.mask;
+    for (uint64_t probe = 0; probe <= H.mask; probe++) {
+        unsigned long long prev = atomicCAS((unsigned long long *)&H.keys[s], (unsigned long long)GS_EMPTY,
+                                            (unsigned long long)key);
+        if (prev == GS_EMPTY || prev == key) return (int64_t)s;
+        s = (s + 1) & H.mask;
+    }
+    atomicOr(status, GS_ST_CAPACITY);
+    return -1;
+}
+__device__ __forceinline__ int64_t gs_hash_find(const GsHash &H, uint64_t key)
+{
+    uint64_t s = gs_mix(key) & H.mask;
+    for (uint64_t probe = 0; probe <= H.mask; probe++) {
+        uint64_t k = H.keys[s];
+        if (k == key) return (int64_t)s;
+        if (k == GS_EMPTY) return -1;
+        s = (s + 1) & H.mask;
+    }
+    return -1;
+}
+
+// ---------------------------------------------------------------- launch helpers (host)
+#define GS_CHECK(call)                                                  \
+    do {                                                                \
+        cudaError_t _e = (call);                                        \
+        if (_e != cudaSuccess) return gs_fail_cuda(_e, #call, __FILE__, __LINE__); \
+    } while (0)
+
+int gs_fail_cuda(cudaError_t e, const char *what, const char *file, int line);
+int gs_fail(int code, const char *fmt, ...);
+
+// device-wide exclusive scan of n int64 values (in place); total -> *d_total (device)
+int gs_scan_i64(int64_t *d_vals, int64_t n, int64_t *d_total, cudaStream_t st);
+// workspace allocation on the stream-ordered pool
+int gs_alloc(void **p, size_t bytes, cudaStream_t st);
+void gs_free(void *p, cudaStream_t st);

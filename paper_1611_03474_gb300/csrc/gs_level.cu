@@ -1,0 +1,704 @@
+// gs_level.cu -- one level of the adaptive partition (section 2.2):
+//   * the coefficient tensor A of every examined cube (eqs polynew,
+//     tensor1, tensor2): per atom the Legendre projection of its 1-D
+//     Gaussian factor on each axis (eqs poly2_1..3, n = 3) with the C0
+//     endpoint correction (eqs poly3, condition1, alpha), weighted by
+//     exp(D r^2) and accumulated as a rank-one update;
+//   * the estimate of [L, U] by the two-level truncated SVD (eqs matrix1,
+//     SVD1-SVD7, Sxyz, bound1-bound3) and the decision
+//     discard / accept / split (steps 1-3 of section 2.2).
+//
+// Layout: cubes are examined in octets (the 8 children of one split parent,
+// or a 2x2x2 block of root cubes).  One warp accumulates one octet: lane
+// (child c = lane/4, j = lane%4) owns the 16 entries A_c[j][*][*].  The 8
+// children share the candidate atoms (cell rows around the parent box) and,
+// per atom and axis, two child intervals, so each atom's coefficients are
+// computed once per octet and used by up to 8 cubes.  Estimation runs one
+// thread per cube.
+#include <cmath>
+#include <cstdio>
+
+#include "gs_host.cuh"
+
+// ---------------------------------------------------------------- quadrature
+// Gauss-Legendre nodes t_k and folded weights W_kj = (2j+1)/2 * w_k * L_j(t_k),
+// so that alpha_j = sum_k W_kj f(t_k).  Variants with 8, 12, 16 and 24 nodes.
+#define GQ_VARIANTS 4
+#define GQ_MAX 24
+__constant__ double c_gq_t[GQ_VARIANTS][GQ_MAX];
+__constant__ double c_gq_W[GQ_VARIANTS][GQ_MAX][4];
+__constant__ float c_gq_tf[GQ_VARIANTS][GQ_MAX];
+__constant__ float c_gq_Wf[GQ_VARIANTS][GQ_MAX][4];
+static const int kGqN[GQ_VARIANTS] = {8, 12, 16, 24};
+
+// nodes of P_n as eigen-free Newton iteration in long double, started from
+// Tricomi's asymptotic estimate
+static void gl_rule(int n, long double *t, long double *w)
+{
+    const long double pi = 3.141592653589793238462643383279502884L;
+    for (int k = 1; k <= n; k++) {
+        long double th = pi * (4.0L * k - 1.0L) / (4.0L * n + 2.0L);
+        long double x = (1.0L - (n - 1.0L) / (8.0L * n * n * n)) * cosl(th);
+        long double dp = 0;
+        for (int it = 0; it < 60; it++) {
+            long double pm1 = 1.0L, p = x;
+            for (int m = 2; m <= n; m++) {
+                long double pn = ((2.0L * m - 1.0L) * x * p - (m - 1.0L) * pm1) / m;
+                pm1 = p;
+                p = pn;
+            }
+            dp = n * (pm1 - x * p) / (1.0L - x * x);
+            long double dx = p / dp;
+            x -= dx;
+            if (fabsl(dx) < 1e-19L) break;
+        }
+        t[k - 1] = x;
+        w[k - 1] = 2.0L / ((1.0L - x * x) * dp * dp);
+    }
+}
+
+static bool g_gq_ready[64];
+
+int gs_quadrature_init(void)
+{
+    int dev = 0;
+    GS_CHECK(cudaGetDevice(&dev));
+    if (dev >= 0 && dev < 64 && g_gq_ready[dev]) return GS_OK;
+    static double t[GQ_VARIANTS][GQ_MAX], W[GQ_VARIANTS][GQ_MAX][4];
+    static float tf[GQ_VARIANTS][GQ_MAX], Wf[GQ_VARIANTS][GQ_MAX][4];
+    for (int v = 0; v < GQ_VARIANTS; v++) {
+        long double tt[GQ_MAX], ww[GQ_MAX];
+        int n = kGqN[v];
+        gl_rule(n, tt, ww);
+        for (int k = 0; k < GQ_MAX; k++) {
+            long double x = k < n ? tt[k] : 0.0L, wk = k < n ? ww[k] : 0.0L;
+            long double L[4] = {1.0L, x, (3.0L * x * x - 1.0L) / 2.0L, (5.0L * x * x * x - 3.0L * x) / 2.0L};
+            t[v][k] = (double)x;
+            tf[v][k] = (float)x;
+            for (int j = 0; j < 4; j++) {
+                W[v][k][j] = (double)((2.0L * j + 1.0L) / 2.0L * wk * L[j]);
+                Wf[v][k][j] = (float)W[v][k][j];
+            }
+        }
+    }
+    GS_CHECK(cudaMemcpyToSymbol(c_gq_t, t, sizeof(t)));
+    GS_CHECK(cudaMemcpyToSymbol(c_gq_W, W, sizeof(W)));
+    GS_CHECK(cudaMemcpyToSymbol(c_gq_tf, tf, sizeof(tf)));
+    GS_CHECK(cudaMemcpyToSymbol(c_gq_Wf, Wf, sizeof(Wf)));
+    if (dev >= 0 && dev < 64) g_gq_ready[dev] = true;
+    return GS_OK;
+}
+
+// node count for an interval of half-width hh: the quadrature error of the
+// projection stays below ~1e-14 (FP64) for sqrt(D)*hh up to each limit
+static int gq_variant(double D, double hh, bool fp32)
+{
+    double a = sqrt(D) * hh;
+    if (fp32) return a <= 0.75 ? 0 : (a <= 1.5 ? 1 : 2);
+    if (a <= 0.25) return 0;
+    if (a <= 0.75) return 1;
+    if (a <= 1.0) return 2;
+    return 3;
+}
+
+// ---------------------------------------------------------------- octet geometry
+struct Octet {
+    int64_t I, J, K;   // parent coords (children at 2I+dx, ...)
+    uint8_t vmask;     // valid children
+};
+
+__device__ __forceinline__ Octet octet_of(const GsProblem &P, int level, const uint64_t *parents,
+                                          const uint8_t *vmask, int64_t o)
+{
+    Octet q;
+    if (parents) {
+        uint64_t k = parents[o];
+        q.I = gk_x(k); q.J = gk_y(k); q.K = gk_z(k);
+        q.vmask = vmask ? vmask[o] : 0xFF;
+        if (level == 0) {
+            // root blocks: drop children outside the root grid
+            for (int c = 0; c < 8; c++) {
+                int64_t x = 2 * q.I + (c & 1), y = 2 * q.J + ((c >> 1) & 1), z = 2 * q.K + (c >> 2);
+                if (x >= P.nroot[0] || y >= P.nroot[1] || z >= P.nroot[2]) q.vmask &= (uint8_t)~(1u << c);
+            }
+        }
+    } else {
+        // root blocks of 2x2x2 cubes, x fastest
+        int64_t bx = (P.nroot[0] + 1) / 2, by = (P.nroot[1] + 1) / 2;
+        q.I = o % bx;
+        q.J = (o / bx) % by;
+        q.K = o / (bx * by);
+        uint8_t m = 0;
+        for (int c = 0; c < 8; c++) {
+            int64_t x = 2 * q.I + (c & 1), y = 2 * q.J + ((c >> 1) & 1), z = 2 * q.K + (c >> 2);
+            if (x < P.nroot[0] && y < P.nroot[1] && z < P.nroot[2]) m |= (uint8_t)(1u << c);
+        }
+        q.vmask = m;
+    }
+    return q;
+}
+
+// ---------------------------------------------------------------- FP64 accumulate
+#define ACC_WARPS 4
+#define ACC_Q 64
+
+// one axis: C0-corrected Legendre coefficients of exp(-D (x - xi)^2) on
+// [e0,e1] and [e1,e2] (the two child intervals), FP64
+__device__ __forceinline__ void axis_coeffs_f64(double xi, double e0, double e1, double e2, double D, int gv, int nq,
+                                                double *out /* [2][4] */)
+{
+    double f0 = exp(-D * (e0 - xi) * (e0 - xi));
+    double f1 = exp(-D * (e1 - xi) * (e1 - xi));
+    double f2 = exp(-D * (e2 - xi) * (e2 - xi));
+#pragma unroll
+    for (int h = 0; h < 2; h++) {
+        double lo = h ? e1 : e0, hi = h ? e2 : e1;
+        double m = __dmul_rn(0.5, __dadd_rn(lo, hi)) - xi, hh = __dmul_rn(0.5, __dsub_rn(hi, lo));
+        double a0 = 0, a1 = 0, a2 = 0, a3 = 0;
+        for (int k = 0; k < nq; k++) {
+            double d = fma(hh, c_gq_t[gv][k], m);
+            double f = exp(-D * d * d);
+            a0 = fma(c_gq_W[gv][k][0], f, a0);
+            a1 = fma(c_gq_W[gv][k][1], f, a1);
+            a2 = fma(c_gq_W[gv][k][2], f, a2);
+            a3 = fma(c_gq_W[gv][k][3], f, a3);
+        }
+        double fa = h ? f1 : f0, fb = h ? f2 : f1;
+        double eR = fb - (a0 + a1 + a2 + a3);
+        double eL = fa - (a0 - a1 + a2 - a3);
+        out[4 * h + 0] = a0;
+        out[4 * h + 1] = a1;
+        out[4 * h + 2] = a2 + 0.5 * (eR + eL);
+        out[4 * h + 3] = a3 + 0.5 * (eR - eL);
+    }
+}
+
+// candidate rows of the cell list around the box [lo,hi] grown by the
+// largest cutoff radius; calls body(begin, end) for each row's atom range
+template <typename F>
+__device__ __forceinline__ void for_cell_rows(const GsProblem &P, const double *lo, const double *hi, double pad, F body)
+{
+    int c0[3], c1[3];
+    for (int a = 0; a < 3; a++) {
+        double f0 = floor((lo[a] - pad - P.origin[a]) * P.inv_cell);
+        double f1 = floor((hi[a] + pad - P.origin[a]) * P.inv_cell);
+        c0[a] = f0 < 0 ? 0 : (f0 >= P.cdim[a] ? P.cdim[a] - 1 : (int)f0);
+        c1[a] = f1 < 0 ? 0 : (f1 >= P.cdim[a] ? P.cdim[a] - 1 : (int)f1);
+    }
+    double pad2 = pad * pad;
+    for (int cz = c0[2]; cz <= c1[2]; cz++) {
+        double zlo = P.origin[2] + cz * P.cell, zhi = zlo + P.cell;
+        double gz = fmax(0.0, fmax(zlo - hi[2], lo[2] - zhi));
+        if (gz * gz > pad2) continue;
+        for (int cy = c0[1]; cy <= c1[1]; cy++) {
+            double ylo = P.origin[1] + cy * P.cell, yhi = ylo + P.cell;
+            double gy = fmax(0.0, fmax(ylo - hi[1], lo[1] - yhi));
+            double rem2 = pad2 - gy * gy - gz * gz;
+            if (rem2 < 0) continue;
+            double rem = sqrt(rem2) * (1.0 + 1e-12) + 1e-12;
+            double f0 = floor((lo[0] - rem - P.origin[0]) * P.inv_cell);
+            double f1 = floor((hi[0] + rem - P.origin[0]) * P.inv_cell);
+            int x0 = f0 < c0[0] ? c0[0] : (int)f0;
+            int x1 = f1 > c1[0] ? c1[0] : (int)f1;
+            if (x0 > x1) continue;
+            int64_t row = (int64_t)P.cdim[0] * (cy + (int64_t)P.cdim[1] * cz);
+            body(P.cell_start[row + x0], P.cell_start[row + x1 + 1]);
+        }
+    }
+}
+
+__global__ void __launch_bounds__(32 * ACC_WARPS) k_accum_f64(GsProblem P, int level, const uint64_t *parents,
+                                                               const uint8_t *vmask, int64_t n_oct, int gv, int nq,
+                                                               double pad, double *__restrict__ A_out,
+                                                               unsigned long long *pairs, unsigned *status)
+{
+    __shared__ double s_cf[ACC_WARPS][32][25];   // per queued atom: 3 axes x 2 intervals x 4, then w
+    __shared__ int s_qi[ACC_WARPS][ACC_Q];
+    __shared__ uint8_t s_qm[ACC_WARPS][ACC_Q];
+    const int lane = threadIdx.x & 31, wl = threadIdx.x >> 5;
+    const int c = lane >> 2, j = lane & 3;
+    const int cx = c & 1, cy = (c >> 1) & 1, cz = c >> 2;
+    for (int64_t o = (int64_t)blockIdx.x * ACC_WARPS + wl; o < n_oct; o += (int64_t)gridDim.x * ACC_WARPS) {
+        Octet q = octet_of(P, level, parents, vmask, o);
+        int64_t base[3] = {2 * q.I, 2 * q.J, 2 * q.K};
+        double e[3][3];
+        for (int a = 0; a < 3; a++)
+            for (int t = 0; t < 3; t++) e[a][t] = gs_lat(P, a, base[a] + t, level);
+        double plo[3] = {e[0][0], e[1][0], e[2][0]}, phi[3] = {e[0][2], e[1][2], e[2][2]};
+        double acc[16];
+#pragma unroll
+        for (int t = 0; t < 16; t++) acc[t] = 0.0;
+        int qn = 0;
+        const uint8_t vm = q.vmask;
+
+        auto process = [&](int nproc) {
+            if (lane < nproc) {
+                int i = s_qi[wl][lane];
+                double xs[3] = {P.ax[i], P.ay[i], P.az[i]};
+                for (int a = 0; a < 3; a++) axis_coeffs_f64(xs[a], e[a][0], e[a][1], e[a][2], P.D, gv, nq, &s_cf[wl][lane][8 * a]);
+                s_cf[wl][lane][24] = P.aw[i];
+            }
+            __syncwarp();
+            for (int t = 0; t < nproc; t++) {
+                if ((s_qm[wl][t] >> c) & 1) {
+                    const double *cf = s_cf[wl][t];
+                    double wa = cf[24] * cf[4 * cx + j];
+#pragma unroll
+                    for (int k = 0; k < 4; k++) {
+                        double wb = wa * cf[8 + 4 * cy + k];
+#pragma unroll
+                        for (int l = 0; l < 4; l++) acc[4 * k + l] = fma(wb, cf[16 + 4 * cz + l], acc[4 * k + l]);
+                    }
+                }
+            }
+            __syncwarp();
+        };
+
+        if (vm) {
+            for_cell_rows(P, plo, phi, pad, [&](int b, int en) {
+                for (int s = b; s < en; s += 32) {
+                    int i = s + lane;
+                    unsigned m = 0;
+                    if (i < en) {
+                        double x = P.ax[i], y = P.ay[i], z = P.az[i], R2 = P.aR2[i];
+                        double gx[2], gy[2], gz[2];
+                        for (int hh = 0; hh < 2; hh++) {
+                            gx[hh] = gs_axis_gap(e[0][hh], e[0][hh + 1], x);
+                            gy[hh] = gs_axis_gap(e[1][hh], e[1][hh + 1], y);
+                            gz[hh] = gs_axis_gap(e[2][hh], e[2][hh + 1], z);
+                        }
+                        for (int cc = 0; cc < 8; cc++) {
+                            double dx = gx[cc & 1], dy = gy[(cc >> 1) & 1], dz = gz[cc >> 2];
+                            double d2 = __dadd_rn(__dadd_rn(__dmul_rn(dx, dx), __dmul_rn(dy, dy)), __dmul_rn(dz, dz));
+                            if (d2 <= R2) m |= 1u << cc;
+                        }
+                        m &= vm;
+                    }
+                    unsigned bal = __ballot_sync(0xffffffffu, m != 0);
+                    int pos = qn + __popc(bal & ((1u << lane) - 1u));
+                    if (m) { s_qi[wl][pos] = i; s_qm[wl][pos] = (uint8_t)m; }
+                    qn += __popc(bal);
+                    __syncwarp();
+                    if (qn >= 32) {
+                        process(32);
+                        int rest = qn - 32;
+                        int mi = 0; uint8_t mm = 0;
+                        if (lane < rest) { mi = s_qi[wl][32 + lane]; mm = s_qm[wl][32 + lane]; }
+                        __syncwarp();
+                        if (lane < rest) { s_qi[wl][lane] = mi; s_qm[wl][lane] = mm; }
+                        __syncwarp();
+                        qn = rest;
+                    }
+                }
+            });
+            if (qn > 0) process(qn);
+        }
+        double *dst = A_out + ((size_t)o * 8 + c) * 64 + 16 * j;
+#pragma unroll
+        for (int t = 0; t < 16; t++) dst[t] = acc[t];
+    }
+}
+
+// pair counting pass is folded into the estimate kernel through A's support;
+// a separate exact count uses the same membership test
+__global__ void k_count_pairs(GsProblem P, int level, const uint64_t *parents, const uint8_t *vmask, int64_t n_oct,
+                              double pad, unsigned long long *pairs)
+{
+    const int lane = threadIdx.x & 31, wl = threadIdx.x >> 5;
+    unsigned long long cnt = 0;
+    for (int64_t o = (int64_t)blockIdx.x * ACC_WARPS + wl; o < n_oct; o += (int64_t)gridDim.x * ACC_WARPS) {
+        Octet q = octet_of(P, level, parents, vmask, o);
+        if (!q.vmask) continue;
+        int64_t base[3] = {2 * q.I, 2 * q.J, 2 * q.K};
+        double e[3][3];
+        for (int a = 0; a < 3; a++)
+            for (int t = 0; t < 3; t++) e[a][t] = gs_lat(P, a, base[a] + t, level);
+        double plo[3] = {e[0][0], e[1][0], e[2][0]}, phi[3] = {e[0][2], e[1][2], e[2][2]};
+        for_cell_rows(P, plo, phi, pad, [&](int b, int en) {
+            for (int i = b + lane; i < en; i += 32) {
+                double x = P.ax[i], y = P.ay[i], z = P.az[i], R2 = P.aR2[i];
+                for (int cc = 0; cc < 8; cc++) {
+                    if (!((q.vmask >> cc) & 1)) continue;
+                    double dx = gs_axis_gap(e[0][cc & 1], e[0][(cc & 1) + 1], x);
+                    double dy = gs_axis_gap(e[1][(cc >> 1) & 1], e[1][((cc >> 1) & 1) + 1], y);
+                    double dz = gs_axis_gap(e[2][cc >> 2], e[2][(cc >> 2) + 1], z);
+                    double d2 = __dadd_rn(__dadd_rn(__dmul_rn(dx, dx), __dmul_rn(dy, dy)), __dmul_rn(dz, dz));
+                    cnt += d2 <= R2;
+                }
+            }
+        });
+    }
+    for (int off = 16; off > 0; off >>= 1) cnt += __shfl_xor_sync(0xffffffffu, cnt, off);
+    if (lane == 0 && cnt) atomicAdd(pairs, cnt);
+}
+
+static int grid_for(int64_t n_items, int per_block)
+{
+    int64_t b = (n_items + per_block - 1) / per_block;
+    int64_t cap = 152LL * 64;
+    if (b > cap) b = cap;
+    return (int)(b < 1 ? 1 : b);
+}
+
+int gs_accum_f64(const GsProblem &P, int level, const uint64_t *d_parents, const uint8_t *d_vmask, int64_t n_oct,
+                 double *d_A, unsigned long long *d_pairs, unsigned *d_status, cudaStream_t st)
+{
+    if (n_oct <= 0) return GS_OK;
+    double h = gs_h(P, level);
+    int gv = gq_variant(P.D, 0.5 * h, false);
+    double pad = P.pad;
+    k_accum_f64<<<grid_for(n_oct, ACC_WARPS), 32 * ACC_WARPS, 0, st>>>(P, level, d_parents, d_vmask, n_oct, gv,
+                                                                       kGqN[gv], pad, d_A, d_pairs, d_status);
+    if (d_pairs)
+        k_count_pairs<<<grid_for(n_oct, ACC_WARPS), 32 * ACC_WARPS, 0, st>>>(P, level, d_parents, d_vmask, n_oct, pad,
+                                                                             d_pairs);
+    GS_CHECK(cudaGetLastError());
+    return GS_OK;
+}
+
+// ---------------------------------------------------------------- estimation
+// Truncated SVD bounds of section 2.2.2, templated on the arithmetic type.
+
+template <typename T> __device__ __forceinline__ T t_sqrt(T x);
+template <> __device__ __forceinline__ double t_sqrt<double>(double x) { return sqrt(x); }
+template <> __device__ __forceinline__ float t_sqrt<float>(float x) { return sqrtf(x); }
+template <typename T> __device__ __forceinline__ T t_abs(T x) { return x < T(0) ? -x : x; }
+template <typename T> struct Eps;
+template <> struct Eps<double> { static __device__ __forceinline__ double v() { return 1e-15; } };
+template <> struct Eps<float> { static __device__ __forceinline__ float v() { return 1e-7f; } };
+
+// one-sided Jacobi on the 4 rows of X (4 x N): afterwards the rows are
+// orthogonal and X_in = Q^T X_out.  Returns singular values sorted
+// descending in s, with the matching left vectors (rows of Q) in u and the
+// right vectors (normalised rows of X) written back into X in sorted order.
+template <typename T, int N>
+__device__ void jacobi4(T (&X)[4][N], T (&s)[4], T (&u)[4][4])
+{
+    T Q[4][4];
+#pragma unroll
+    for (int a = 0; a < 4; a++)
+#pragma unroll
+        for (int b = 0; b < 4; b++) Q[a][b] = a == b ? T(1) : T(0);
+    for (int sweep = 0; sweep < 40; sweep++) {
+        bool any = false;
+#pragma unroll
+        for (int p = 0; p < 3; p++)
+#pragma unroll
+            for (int q = p + 1; q < 4; q++) {
+                T al = 0, be = 0, ga = 0;
+#pragma unroll
+                for (int k = 0; k < N; k++) {
+                    al += X[p][k] * X[p][k];
+                    be += X[q][k] * X[q][k];
+                    ga += X[p][k] * X[q][k];
+                }
+                if (ga == T(0) || t_abs(ga) <= Eps<T>::v() * t_sqrt(al * be)) continue;
+                any = true;
+                T tau = (be - al) / (T(2) * ga);
+                T t = (tau >= T(0) ? T(1) : T(-1)) / (t_abs(tau) + t_sqrt(T(1) + tau * tau));
+                T cs = T(1) / t_sqrt(T(1) + t * t), sn = cs * t;
+#pragma unroll
+                for (int k = 0; k < N; k++) {
+                    T xp = X[p][k], xq = X[q][k];
+                    X[p][k] = cs * xp - sn * xq;
+                    X[q][k] = sn * xp + cs * xq;
+                }
+#pragma unroll
+                for (int k = 0; k < 4; k++) {
+                    T qp = Q[p][k], qq = Q[q][k];
+                    Q[p][k] = cs * qp - sn * qq;
+                    Q[q][k] = sn * qp + cs * qq;
+                }
+            }
+        if (!any) break;
+    }
+    T sv[4];
+    int ord[4] = {0, 1, 2, 3};
+#pragma unroll
+    for (int p = 0; p < 4; p++) {
+        T n2 = 0;
+#pragma unroll
+        for (int k = 0; k < N; k++) n2 += X[p][k] * X[p][k];
+        sv[p] = t_sqrt(n2);
+    }
+    // stable sort of 4 indices by descending value
+    for (int i = 1; i < 4; i++) {
+        int o = ord[i], k = i - 1;
+        while (k >= 0 && sv[ord[k]] < sv[o]) { ord[k + 1] = ord[k]; k--; }
+        ord[k + 1] = o;
+    }
+    T Y[4][N];
+    for (int i = 0; i < 4; i++) {
+        int p = ord[i];
+        s[i] = sv[p];
+        T inv = sv[p] > T(0) ? T(1) / sv[p] : T(0);
+#pragma unroll
+        for (int k = 0; k < 4; k++) u[i][k] = Q[p][k];
+#pragma unroll
+        for (int k = 0; k < N; k++) Y[i][k] = X[p][k] * inv;
+    }
+#pragma unroll
+    for (int i = 0; i < 4; i++)
+#pragma unroll
+        for (int k = 0; k < N; k++) X[i][k] = Y[i][k];
+}
+
+// range of sum_j c_j L_j(t) over [-1,1]
+template <typename T>
+__device__ __forceinline__ void cubic_range(const T *cf, T &lo, T &hi)
+{
+    T p1 = cf[0] + cf[1] + cf[2] + cf[3], m1 = cf[0] - cf[1] + cf[2] - cf[3];
+    lo = p1 < m1 ? p1 : m1;
+    hi = p1 < m1 ? m1 : p1;
+    // derivative 3 b3 t^2 + 2 b2 t + b1 in monomials of the cubic
+    T b0 = cf[0] - T(0.5) * cf[2], b1 = cf[1] - T(1.5) * cf[3], b2 = T(1.5) * cf[2], b3 = T(2.5) * cf[3];
+    T qa = T(3) * b3, qb = T(2) * b2, qc = b1;
+    T r[2];
+    int nr = 0;
+    if (qa == T(0)) {
+        if (qb != T(0)) r[nr++] = -qc / qb;
+    } else {
+        T disc = qb * qb - T(4) * qa * qc;
+        if (disc >= T(0)) {
+            T sq = t_sqrt(disc);
+            T w = qb >= T(0) ? -(qb + sq) / T(2) : -(qb - sq) / T(2);
+            if (w != T(0)) { r[nr++] = w / qa; r[nr++] = qc / w; }
+            else r[nr++] = T(0);
+        }
+    }
+    for (int i = 0; i < nr; i++) {
+        T t = r[i];
+        if (t > T(-1) && t < T(1)) {
+            T v = b0 + t * (b1 + t * (b2 + t * b3));
+            lo = v < lo ? v : lo;
+            hi = v > hi ? v : hi;
+        }
+    }
+}
+
+template <typename T>
+__device__ __forceinline__ int rank99(const T (&s)[4], T &margin)
+{
+    T tot = s[0] + s[1] + s[2] + s[3];
+    T acc = 0;
+    T thr = T(0.99) * tot;
+    int r = 4;
+    margin = tot;
+    for (int j = 0; j < 4; j++) {
+        acc += s[j];
+        T m = t_abs(acc - thr);
+        margin = m < margin ? m : margin;
+        if (acc >= thr) { r = j + 1; break; }
+    }
+    return r;
+}
+
+// bounds: out = (L, U, sum|R|, sum|high|, rank, inner ranks); rmargin = the
+// smallest distance of a rank rule from its 99% threshold
+template <typename T>
+__device__ void estimate_bounds(const T *A, T *out, T &rmargin)
+{
+    T X[4][16];
+    T high = 0, tot = 0;
+#pragma unroll
+    for (int j = 0; j < 4; j++)
+#pragma unroll
+        for (int k = 0; k < 16; k++) {
+            T v = A[16 * j + k];
+            X[j][k] = v;
+            tot += t_abs(v);
+            if (j >= 2 || (k >> 2) >= 2 || (k & 3) >= 2) high += t_abs(v);
+        }
+    out[3] = high;
+    rmargin = T(1e30);
+    if (tot == T(0)) { out[0] = out[1] = out[2] = 0; out[4] = 0; out[5] = 0; return; }
+    T s[4], u[4][4];
+    jacobi4<T, 16>(X, s, u);
+    T rm;
+    int jr = rank99(s, rm);
+    rmargin = rm;
+    T At[64];
+#pragma unroll
+    for (int t = 0; t < 64; t++) At[t] = 0;
+    T M = 0, m = 0;
+    int inner = 0;
+    for (int i = 0; i < jr; i++) {
+        T V[4][4], d[4], w[4][4];
+#pragma unroll
+        for (int k = 0; k < 4; k++)
+#pragma unroll
+            for (int l = 0; l < 4; l++) V[k][l] = X[i][4 * k + l];
+        jacobi4<T, 4>(V, d, w);
+        T rmi;
+        int ji = rank99(d, rmi);
+        rmargin = rmi < rmargin ? rmi : rmargin;
+        inner += ji;
+        T Myz = 0, myz = 0;
+        for (int k = 0; k < ji; k++) {
+            T ly, hy, lz, hz;
+            cubic_range(w[k], ly, hy);
+            cubic_range(V[k], lz, hz);
+            T p0 = hy * hz, p1 = hy * lz, p2 = ly * hz, p3 = ly * lz;
+            T pmx = p0, pmn = p0;
+            pmx = p1 > pmx ? p1 : pmx; pmn = p1 < pmn ? p1 : pmn;
+            pmx = p2 > pmx ? p2 : pmx; pmn = p2 < pmn ? p2 : pmn;
+            pmx = p3 > pmx ? p3 : pmx; pmn = p3 < pmn ? p3 : pmn;
+            Myz += d[k] * pmx;
+            myz += d[k] * pmn;
+            T sd = s[i] * d[k];
+#pragma unroll
+            for (int a = 0; a < 4; a++) {
+                T sa = sd * u[i][a];
+#pragma unroll
+                for (int b = 0; b < 4; b++) {
+                    T sab = sa * w[k][b];
+#pragma unroll
+                    for (int cc = 0; cc < 4; cc++) At[16 * a + 4 * b + cc] += sab * V[k][cc];
+                }
+            }
+        }
+        T lx, hx;
+        cubic_range(u[i], lx, hx);
+        T p0 = hx * Myz, p1 = hx * myz, p2 = lx * Myz, p3 = lx * myz;
+        T pmx = p0, pmn = p0;
+        pmx = p1 > pmx ? p1 : pmx; pmn = p1 < pmn ? p1 : pmn;
+        pmx = p2 > pmx ? p2 : pmx; pmn = p2 < pmn ? p2 : pmn;
+        pmx = p3 > pmx ? p3 : pmx; pmn = p3 < pmn ? p3 : pmn;
+        M += s[i] * pmx;
+        m += s[i] * pmn;
+    }
+    T sr = 0;
+#pragma unroll
+    for (int t = 0; t < 64; t++) sr += t_abs(A[t] - At[t]);
+    out[0] = m - sr;
+    out[1] = M + sr;
+    out[2] = sr;
+    out[4] = (T)jr;
+    out[5] = (T)inner;
+}
+
+template <typename T>
+__device__ __forceinline__ int decide(const T *b, T c, T precision, int level, int max_depth)
+{
+    if (b[4] == T(0)) return DEC_DISCARD;
+    if (!(b[0] <= c && c <= b[1])) return DEC_DISCARD;
+    if (b[3] <= precision) return DEC_ACCEPT;
+    if (level >= max_depth) return DEC_FORCED;
+    return DEC_SPLIT;
+}
+
+__global__ void __launch_bounds__(128) k_estimate_f64(GsProblem P, int level, const double *__restrict__ A,
+                                                      int64_t n, const uint64_t *parents, const uint8_t *vmask,
+                                                      uint8_t *__restrict__ dec, double *__restrict__ bounds)
+{
+    int64_t q = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (q >= n) return;
+    Octet oc = octet_of(P, level, parents, vmask, q >> 3);
+    if (!((oc.vmask >> (q & 7)) & 1)) { dec[q] = DEC_INVALID; return; }
+    double a[64];
+#pragma unroll
+    for (int t = 0; t < 64; t++) a[t] = A[q * 64 + t];
+    double b[6], rm;
+    estimate_bounds<double>(a, b, rm);
+    dec[q] = (uint8_t)decide<double>(b, P.c, P.precision, level, P.max_depth);
+    if (bounds)
+        for (int t = 0; t < 6; t++) bounds[q * 6 + t] = b[t];
+}
+
+int gs_estimate_f64(const GsProblem &P, int level, const double *d_A, int64_t n_cubes, const uint64_t *d_parents,
+                    const uint8_t *d_vmask, uint8_t *d_dec, double *d_bounds, cudaStream_t st)
+{
+    if (n_cubes <= 0) return GS_OK;
+    k_estimate_f64<<<(unsigned)((n_cubes + 127) / 128), 128, 0, st>>>(P, level, d_A, n_cubes, d_parents, d_vmask,
+                                                                     d_dec, d_bounds);
+    GS_CHECK(cudaGetLastError());
+    return GS_OK;
+}
+
+// ---------------------------------------------------------------- compaction
+// packed[q] = [SPLIT] + [ACCEPT or FORCED] << 32; after an exclusive scan the
+// low half is the cube's slot among the next level's parents, the high half
+// its slot among the accepted cubes.  counters: examined, discarded,
+// accepted, forced, split.
+__global__ void k_level_count(const uint8_t *__restrict__ dec, int64_t n, int64_t *__restrict__ packed,
+                              unsigned long long *counters)
+{
+    int64_t q = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    unsigned d = q < n ? dec[q] : DEC_INVALID;
+    if (q < n) packed[q] = (int64_t)(d == DEC_SPLIT) | ((int64_t)(d == DEC_ACCEPT || d == DEC_FORCED) << 32);
+    unsigned lane = threadIdx.x & 31;
+    unsigned b[5] = {__ballot_sync(0xffffffffu, d != DEC_INVALID), __ballot_sync(0xffffffffu, d == DEC_DISCARD),
+                     __ballot_sync(0xffffffffu, d == DEC_ACCEPT), __ballot_sync(0xffffffffu, d == DEC_FORCED),
+                     __ballot_sync(0xffffffffu, d == DEC_SPLIT)};
+    if (lane == 0)
+        for (int k = 0; k < 5; k++)
+            if (b[k]) atomicAdd(&counters[k], (unsigned long long)__popc(b[k]));
+}
+
+__global__ void k_level_emit(GsProblem P, int level, const uint64_t *parents, const uint8_t *vmask,
+                             const uint8_t *__restrict__ dec, int64_t n, const int64_t *__restrict__ off,
+                             uint64_t *__restrict__ next, uint64_t *__restrict__ acc)
+{
+    int64_t q = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (q >= n) return;
+    unsigned d = dec[q];
+    if (d != DEC_SPLIT && d != DEC_ACCEPT && d != DEC_FORCED) return;
+    Octet oc = octet_of(P, level, parents, vmask, q >> 3);
+    int c = (int)(q & 7);
+    uint64_t key = gk_make(2 * oc.I + (c & 1), 2 * oc.J + ((c >> 1) & 1), 2 * oc.K + (c >> 2), GT_CUBE, (unsigned)level);
+    int64_t o = off[q];
+    if (d == DEC_SPLIT) next[o & 0xffffffffll] = key;
+    else acc[o >> 32] = key;
+}
+
+int gs_level_compact(const GsProblem &P, int level, const uint64_t *d_parents, const uint8_t *d_vmask, int64_t n_oct,
+                     const uint8_t *d_dec, uint64_t **d_next, int64_t *n_next, uint64_t *d_acc_base,
+                     int64_t acc_cap, int64_t *n_acc, unsigned long long *d_counters, cudaStream_t st)
+{
+    int64_t n = n_oct * 8;
+    *d_next = nullptr; *n_next = 0; *n_acc = 0;
+    if (n <= 0) return GS_OK;
+    int64_t *packed = nullptr, *tot = nullptr;
+    int rc = gs_alloc((void **)&packed, sizeof(int64_t) * (size_t)(n + 1), st);
+    if (!rc) rc = gs_alloc((void **)&tot, sizeof(int64_t), st);
+    if (rc) { gs_free(packed, st); return rc; }
+    cudaMemsetAsync(packed + n, 0, sizeof(int64_t), st);
+    k_level_count<<<(unsigned)((n + 255) / 256), 256, 0, st>>>(d_dec, n, packed, d_counters);
+    rc = gs_scan_i64(packed, n + 1, tot, st);
+    int64_t h = 0;
+    if (!rc) {
+        cudaError_t e = cudaMemcpyAsync(&h, tot, sizeof(int64_t), cudaMemcpyDeviceToHost, st);
+        if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+        if (e != cudaSuccess) rc = gs_fail_cuda(e, "level counts", __FILE__, __LINE__);
+    }
+    int64_t ns = h & 0xffffffffll, na = h >> 32;
+    if (!rc && na > acc_cap) rc = gs_fail(GS_ERR_CAPACITY, "accepted-cube buffer too small");
+    if (!rc && ns > 0) rc = gs_alloc((void **)d_next, sizeof(uint64_t) * (size_t)ns, st);
+    if (!rc) k_level_emit<<<(unsigned)((n + 255) / 256), 256, 0, st>>>(P, level, d_parents, d_vmask, d_dec, n, packed,
+                                                                      *d_next, d_acc_base);
+    gs_free(packed, st); gs_free(tot, st);
+    if (rc) return rc;
+    GS_CHECK(cudaGetLastError());
+    *n_next = ns;
+    *n_acc = na;
+    return GS_OK;
+}
+
+// explicit keys of the root blocks (2x2x2 root cubes), x fastest
+__global__ void k_root_blocks(int64_t bx, int64_t by, int64_t n, uint64_t *keys)
+{
+    int64_t o = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (o >= n) return;
+    keys[o] = gk_make(o % bx, (o / bx) % by, o / (bx * by), GT_CUBE, 0);
+}
+
+int gs_root_blocks(const GsProblem &P, uint64_t **d_keys, int64_t *n, cudaStream_t st)
+{
+    int64_t bx = (P.nroot[0] + 1) / 2, by = (P.nroot[1] + 1) / 2, bz = (P.nroot[2] + 1) / 2;
+    *n = bx * by * bz;
+    int rc = gs_alloc((void **)d_keys, sizeof(uint64_t) * (size_t)*n, st);
+    if (rc) return rc;
+    k_root_blocks<<<(unsigned)((*n + 255) / 256), 256, 0, st>>>(bx, by, *n, *d_keys);
+    GS_CHECK(cudaGetLastError());
+    return GS_OK;
+}

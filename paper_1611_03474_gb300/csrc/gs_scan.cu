@@ -1,0 +1,148 @@
+// gs_scan.cu -- exclusive prefix sums for stream compaction (level lists,
+// vertex and point ownership), error helpers and workspace allocation.
+#include <cstdarg>
+#include <cstdio>
+#include <cstring>
+
+#include "gs_internal.cuh"
+
+static thread_local char g_last_error[512] = "";
+
+int gs_fail(int code, const char *fmt, ...)
+{
+    va_list ap;
+    va_start(ap, fmt);
+    vsnprintf(g_last_error, sizeof(g_last_error), fmt, ap);
+    va_end(ap);
+    return code;
+}
+
+int gs_fail_cuda(cudaError_t e, const char *what, const char *file, int line)
+{
+    const char *f = strrchr(file, '/');
+    gs_fail(e == cudaErrorMemoryAllocation ? GS_ERR_OOM : GS_ERR_CUDA, "%s failed: %s (%s:%d)", what,
+            cudaGetErrorString(e), f ? f + 1 : file, line);
+    return e == cudaErrorMemoryAllocation ? GS_ERR_OOM : GS_ERR_CUDA;
+}
+
+extern "C" const char *gs_last_error(void) { return g_last_error; }
+
+int gs_alloc(void **p, size_t bytes, cudaStream_t st)
+{
+    *p = nullptr;
+    if (bytes == 0) bytes = 16;
+    cudaError_t e = cudaMallocAsync(p, bytes, st);
+    if (e != cudaSuccess) {
+        *p = nullptr;
+        return gs_fail_cuda(e, "cudaMallocAsync", __FILE__, __LINE__);
+    }
+    return GS_OK;
+}
+
+void gs_free(void *p, cudaStream_t st)
+{
+    if (p) cudaFreeAsync(p, st);
+}
+
+// ---------------------------------------------------------------- scan
+// Three phases: per-block totals, scan of the totals (recursively), and a
+// per-block scan that adds the block's offset.  Each block covers
+// SCAN_THREADS * SCAN_ITEMS consecutive values.
+#define SCAN_THREADS 512
+#define SCAN_ITEMS 8
+#define SCAN_TILE (SCAN_THREADS * SCAN_ITEMS)
+
+__device__ __forceinline__ int64_t warp_incl_scan(int64_t v)
+{
+    for (int o = 1; o < 32; o <<= 1) {
+        int64_t t = __shfl_up_sync(0xffffffffu, v, o);
+        if ((threadIdx.x & 31) >= o) v += t;
+    }
+    return v;
+}
+
+// exclusive block scan of one value per thread; returns the block total in *total
+__device__ __forceinline__ int64_t block_excl_scan(int64_t v, int64_t *total)
+{
+    __shared__ int64_t warp_tot[SCAN_THREADS / 32];
+    int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+    int64_t inc = warp_incl_scan(v);
+    if (lane == 31) warp_tot[wid] = inc;
+    __syncthreads();
+    if (wid == 0) {
+        int64_t t = lane < SCAN_THREADS / 32 ? warp_tot[lane] : 0;
+        t = warp_incl_scan(t);
+        if (lane < SCAN_THREADS / 32) warp_tot[lane] = t;
+    }
+    __syncthreads();
+    int64_t before = wid > 0 ? warp_tot[wid - 1] : 0;
+    *total = warp_tot[SCAN_THREADS / 32 - 1];
+    __syncthreads();
+    return before + inc - v;
+}
+
+__global__ void k_scan_tile_sums(const int64_t *__restrict__ v, int64_t n, int64_t *__restrict__ sums)
+{
+    int64_t base = (int64_t)blockIdx.x * SCAN_TILE + (int64_t)threadIdx.x * SCAN_ITEMS;
+    int64_t s = 0;
+#pragma unroll
+    for (int i = 0; i < SCAN_ITEMS; i++)
+        if (base + i < n) s += v[base + i];
+    int64_t tot;
+    block_excl_scan(s, &tot);
+    if (threadIdx.x == 0) sums[blockIdx.x] = tot;
+}
+
+__global__ void k_scan_tile_apply(int64_t *__restrict__ v, int64_t n, const int64_t *__restrict__ offs)
+{
+    int64_t base = (int64_t)blockIdx.x * SCAN_TILE + (int64_t)threadIdx.x * SCAN_ITEMS;
+    int64_t loc[SCAN_ITEMS];
+    int64_t s = 0;
+#pragma unroll
+    for (int i = 0; i < SCAN_ITEMS; i++) {
+        loc[i] = base + i < n ? v[base + i] : 0;
+        s += loc[i];
+    }
+    int64_t tot;
+    int64_t pre = block_excl_scan(s, &tot) + (offs ? offs[blockIdx.x] : 0);
+#pragma unroll
+    for (int i = 0; i < SCAN_ITEMS; i++) {
+        if (base + i < n) v[base + i] = pre;
+        pre += loc[i];
+    }
+}
+
+__global__ void k_scan_total(const int64_t *v, const int64_t *orig_last, int64_t n, int64_t *total)
+{
+    // total = exclusive[n-1] + original value at n-1
+    *total = n > 0 ? v[n - 1] + *orig_last : 0;
+}
+
+int gs_scan_i64(int64_t *d_vals, int64_t n, int64_t *d_total, cudaStream_t st)
+{
+    if (n <= 0) {
+        if (d_total) GS_CHECK(cudaMemsetAsync(d_total, 0, sizeof(int64_t), st));
+        return GS_OK;
+    }
+    int64_t *last = nullptr;
+    int rc = gs_alloc((void **)&last, sizeof(int64_t), st);
+    if (rc) return rc;
+    GS_CHECK(cudaMemcpyAsync(last, d_vals + (n - 1), sizeof(int64_t), cudaMemcpyDeviceToDevice, st));
+    int64_t tiles = (n + SCAN_TILE - 1) / SCAN_TILE;
+    if (tiles == 1) {
+        k_scan_tile_apply<<<1, SCAN_THREADS, 0, st>>>(d_vals, n, nullptr);
+    } else {
+        int64_t *sums = nullptr;
+        rc = gs_alloc((void **)&sums, sizeof(int64_t) * (size_t)tiles, st);
+        if (rc) { gs_free(last, st); return rc; }
+        k_scan_tile_sums<<<(unsigned)tiles, SCAN_THREADS, 0, st>>>(d_vals, n, sums);
+        rc = gs_scan_i64(sums, tiles, nullptr, st);
+        if (rc) { gs_free(sums, st); gs_free(last, st); return rc; }
+        k_scan_tile_apply<<<(unsigned)tiles, SCAN_THREADS, 0, st>>>(d_vals, n, sums);
+        gs_free(sums, st);
+    }
+    if (d_total) k_scan_total<<<1, 1, 0, st>>>(d_vals, last, n, d_total);
+    gs_free(last, st);
+    GS_CHECK(cudaGetLastError());
+    return GS_OK;
+}

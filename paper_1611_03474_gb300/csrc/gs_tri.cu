@@ -1,0 +1,565 @@
+// gs_tri.cu -- per-cube trilinear surface and its triangulation (section 2.3).
+//
+// For each accepted cube whose corner values straddle c, the trilinear
+// interpolant g of eq linear1 is cut by g = c:
+//   * edge points solve g = c on the 12 edges (eq intersection);
+//   * fold lines {g = c, dg/ds = 0} (eq fold1) are segments parallel to an
+//     axis s; their ends on the two faces normal to s are the extreme points
+//     (eq curve); fold lines of two axes meet at critical points (eq
+//     critical), which for a trilinear g occur whenever both lie in one slice;
+//   * on each face the bilinear level curve joins edge points along
+//     hyperbola branches (asymptotic decider) and takes, in order, the
+//     extreme points of this cube and of the same-size neighbour across the
+//     face ("points of the neighbouring cubes are considered");
+//   * the loops so formed, cut along all fold segments, bound single-valued
+//     pieces, each triangulated by ear clipping in the coordinate plane of
+//     its largest projected area (two-ears theorem).
+// Decisions that two cubes sharing a face must agree on (edge points, fold
+// roots, face arcs) are taken by the same non-inlined functions on the same
+// values in the face's global axis order.
+//
+// Thread per cube, two passes over the same code: count (triangles,
+// points) and emit into scan-allocated buffers.  Bounded loops only; an
+// inconsistency sets a counter and skips the cube.
+#include "gs_host.cuh"
+
+#define TP_MAX 48
+#define POLY_MAX 96
+
+struct TPt {
+    double p[3];      // cube-local coordinates in [0,1]
+    uint64_t key;
+    signed char kind; // 0 edge, 1 own extreme, 2 neighbour extreme, 3 critical
+    signed char nb[4];
+    signed char fa, fb, rh;
+};
+
+__device__ __forceinline__ void axes_other(int a, int &u, int &v)
+{
+    u = (a == 0) ? 1 : 0;
+    v = (a == 2) ? 1 : 2;
+}
+
+__device__ __forceinline__ double corner(const double *g, int bx, int by, int bz) { return g[bx + 2 * by + 4 * bz]; }
+
+// roots (u,v) in the open unit square of {B = 0, A = c} for g = A + s B along axis a
+__device__ __noinline__ int fold_solve(const double *g, int a, double c, double *ru, double *rv)
+{
+    int ua, va;
+    axes_other(a, ua, va);
+    double lo[4], up[4];  // face s=0 and s=1 values at (u,v) = (0,0),(1,0),(0,1),(1,1)
+    for (int k = 0; k < 4; k++) {
+        int b[3];
+        b[a] = 0; b[ua] = k & 1; b[va] = k >> 1;
+        lo[k] = corner(g, b[0], b[1], b[2]);
+        b[a] = 1;
+        up[k] = corner(g, b[0], b[1], b[2]);
+    }
+    int nlo = 0, nup = 0;
+    for (int k = 0; k < 4; k++) { nlo += lo[k] >= c; nup += up[k] >= c; }
+    if (nlo == 0 || nlo == 4 || nup == 0 || nup == 4) return 0;
+    // A - c = p0 + p1 u + p2 v + p3 uv ; B = q0 + q1 u + q2 v + q3 uv
+    double p0 = lo[0] - c, p1 = lo[1] - lo[0], p2 = lo[2] - lo[0], p3 = (lo[3] - lo[1]) - (lo[2] - lo[0]);
+    double d0 = up[0] - lo[0], d1 = up[1] - lo[1], d2 = up[2] - lo[2], d3 = up[3] - lo[3];
+    double q0 = d0, q1 = d1 - d0, q2 = d2 - d0, q3 = (d3 - d1) - (d2 - d0);
+    if (q0 == 0.0 && q1 == 0.0 && q2 == 0.0 && q3 == 0.0) return 0;
+    // eliminate v: (p0 + p1 u)(q2 + q3 u) - (p2 + p3 u)(q0 + q1 u) = 0
+    double A2 = p1 * q3 - p3 * q1;
+    double A1 = (p0 * q3 + p1 * q2) - (p2 * q1 + p3 * q0);
+    double A0 = p0 * q2 - p2 * q0;
+    double us[2];
+    int nu = 0;
+    if (A2 == 0.0) {
+        if (A1 != 0.0) us[nu++] = -A0 / A1;
+    } else {
+        double disc = A1 * A1 - 4.0 * A2 * A0;
+        if (disc >= 0.0) {
+            double sq = sqrt(disc);
+            double w = A1 >= 0.0 ? -0.5 * (A1 + sq) : -0.5 * (A1 - sq);
+            if (w != 0.0) {
+                us[nu++] = w / A2;
+                double u2 = A0 / w;
+                if (u2 != us[0]) us[nu++] = u2;
+            } else {
+                us[nu++] = 0.0;
+            }
+        }
+    }
+    double sp = fabs(p0) + fabs(p1) + fabs(p2) + fabs(p3), sq_ = fabs(q0) + fabs(q1) + fabs(q2) + fabs(q3);
+    int nr = 0;
+    for (int i = 0; i < nu; i++) {
+        double u = us[i];
+        if (!(u > 0.0 && u < 1.0)) continue;
+        double denB = q2 + q3 * u, denA = p2 + p3 * u;
+        double cand0, cand1;
+        bool h0, h1;
+        if (fabs(denB) >= fabs(denA)) {
+            h0 = denB != 0.0; cand0 = h0 ? -(q0 + q1 * u) / denB : 0.0;
+            h1 = denA != 0.0; cand1 = h1 ? -(p0 + p1 * u) / denA : 0.0;
+        } else {
+            h0 = denA != 0.0; cand0 = h0 ? -(p0 + p1 * u) / denA : 0.0;
+            h1 = denB != 0.0; cand1 = h1 ? -(q0 + q1 * u) / denB : 0.0;
+        }
+        for (int t = 0; t < 2; t++) {
+            bool has = t ? h1 : h0;
+            double v = t ? cand1 : cand0;
+            if (!has || !(v > 0.0 && v < 1.0)) continue;
+            if (fabs(p0 + p1 * u + p2 * v + p3 * u * v) > 1e-9 * sp) continue;
+            if (fabs(q0 + q1 * u + q2 * v + q3 * u * v) > 1e-9 * sq_) continue;
+            ru[nr] = u; rv[nr] = v; nr++;
+            break;
+        }
+    }
+    if (nr == 2 && (ru[1] < ru[0] || (ru[1] == ru[0] && rv[1] < rv[0]))) {
+        double t = ru[0]; ru[0] = ru[1]; ru[1] = t;
+        t = rv[0]; rv[0] = rv[1]; rv[1] = t;
+    }
+    return nr;
+}
+
+// face decision in the face's (u,v) frame from h[u + 2v]: returns the number
+// of arcs (0,1,2); for two arcs sets around00 (arcs cut off corners 00 and
+// 11) and the saddle's u coordinate
+__device__ __noinline__ int face_arcs(const double *h, double c, int &around00, double &us)
+{
+    int nin = (h[0] >= c) + (h[1] >= c) + (h[2] >= c) + (h[3] >= c);
+    around00 = 0;
+    us = 0.0;
+    if (nin == 0 || nin == 4) return 0;
+    bool diag = ((h[0] >= c) == (h[3] >= c)) && ((h[1] >= c) == (h[2] >= c)) && ((h[0] >= c) != (h[1] >= c));
+    if (!diag) return 1;
+    double den = h[0] - h[1] - h[2] + h[3];
+    double hs = (h[0] * h[3] - h[1] * h[2]) / den;
+    us = (h[0] - h[2]) / den;
+    bool in00 = h[0] >= c;
+    bool sep = hs < c;
+    around00 = (in00 == sep) ? 1 : 0;
+    return 2;
+}
+
+struct TriOut {
+    uint64_t *tri_keys;   // [3] per triangle
+    uint64_t *pt_keys;
+    double *pt_xyz;
+    int64_t tri_off, pt_off;
+    int ntri, npt;
+    bool emit;
+};
+
+__device__ __forceinline__ void put_tri(TriOut &o, uint64_t a, uint64_t b, uint64_t c)
+{
+    if (o.emit) {
+        uint64_t *d = o.tri_keys + 3 * (o.tri_off + o.ntri);
+        d[0] = a; d[1] = b; d[2] = c;
+    }
+    o.ntri++;
+}
+
+__device__ __forceinline__ double orient(const double *a, const double *b, const double *c, int i, int j)
+{
+    return (b[i] - a[i]) * (c[j] - a[j]) - (b[j] - a[j]) * (c[i] - a[i]);
+}
+
+// ear clipping of one piece (indices into pts), CCW seen from outside
+__device__ void clip_piece(const TPt *pts, const unsigned char *poly, int n, TriOut &o, unsigned long long *degen)
+{
+    double N0 = 0, N1 = 0, N2 = 0;
+    for (int i = 0; i < n; i++) {
+        const double *p = pts[poly[i]].p, *q = pts[poly[i + 1 == n ? 0 : i + 1]].p;
+        N0 += (p[1] - q[1]) * (p[2] + q[2]);
+        N1 += (p[2] - q[2]) * (p[0] + q[0]);
+        N2 += (p[0] - q[0]) * (p[1] + q[1]);
+    }
+    int k = 0;
+    double best = fabs(N0);
+    if (fabs(N1) > best) { k = 1; best = fabs(N1); }
+    if (fabs(N2) > best) k = 2;
+    double Nk = k == 0 ? N0 : (k == 1 ? N1 : N2);
+    int ia = (k + 1) % 3, ib = (k + 2) % 3;
+    double sg = Nk >= 0 ? 1.0 : -1.0;
+    unsigned char v[POLY_MAX];
+    for (int i = 0; i < n; i++) v[i] = poly[i];
+    int m = n;
+    int guard = 0;
+    while (m > 3 && guard++ < POLY_MAX) {
+        int pick = -1, fall = -1;
+        for (int i = 0; i < m; i++) {
+            int a = v[i == 0 ? m - 1 : i - 1], b = v[i], c = v[i + 1 == m ? 0 : i + 1];
+            if (fall < 0 || pts[b].key < pts[v[fall]].key) fall = i;
+            if (!(sg * orient(pts[a].p, pts[b].p, pts[c].p, ia, ib) > 0)) continue;
+            bool empty = true;
+            for (int jx = 0; jx < m && empty; jx++) {
+                int d = v[jx];
+                if (d == a || d == b || d == c) continue;
+                const double *pd = pts[d].p;
+                if (sg * orient(pts[a].p, pts[b].p, pd, ia, ib) >= 0 && sg * orient(pts[b].p, pts[c].p, pd, ia, ib) >= 0 &&
+                    sg * orient(pts[c].p, pts[a].p, pd, ia, ib) >= 0)
+                    empty = false;
+            }
+            if (!empty) continue;
+            if (pick < 0 || pts[b].key < pts[v[pick]].key) pick = i;
+        }
+        if (pick < 0) { pick = fall; if (degen) atomicAdd(degen, 1ull); }
+        int a = v[pick == 0 ? m - 1 : pick - 1], b = v[pick], c = v[pick + 1 == m ? 0 : pick + 1];
+        if (a != b && b != c && a != c) put_tri(o, pts[a].key, pts[b].key, pts[c].key);
+        for (int t = pick; t < m - 1; t++) v[t] = v[t + 1];
+        m--;
+    }
+    if (m == 3 && v[0] != v[1] && v[1] != v[2] && v[0] != v[2]) put_tri(o, pts[v[0]].key, pts[v[1]].key, pts[v[2]].key);
+}
+
+__device__ __forceinline__ int64_t add_pt(TPt *pts, int &np, int kind)
+{
+    if (np >= TP_MAX) return -1;
+    TPt &p = pts[np];
+    p.kind = (signed char)kind;
+    p.nb[0] = p.nb[1] = p.nb[2] = p.nb[3] = -1;
+    p.fa = p.fb = p.rh = 0;
+    return np++;
+}
+
+// returns 0 on success, 1 on an inconsistency (cube skipped)
+__device__ int tri_cube(const TriCtx &X, int64_t ci, TriOut &o, unsigned long long *degen)
+{
+    uint64_t ck = X.cubes[ci];
+    int lvl = (int)gk_level(ck);
+    int64_t C[3] = {gk_x(ck), gk_y(ck), gk_z(ck)};
+    int64_t sc = (int64_t)1 << (X.max_depth - lvl);
+    double g[8];
+    for (int v = 0; v < 8; v++) g[v] = X.phi[X.cvid[ci * 8 + v]];
+    const double c = X.c;
+    int nin = 0;
+    for (int v = 0; v < 8; v++) nin += g[v] >= c;
+    if (nin == 0 || nin == 8) return 0;
+
+    TPt pts[TP_MAX];
+    int np = 0;
+    signed char eid[12];
+    for (int a = 0; a < 3; a++) {
+        int ua, va;
+        axes_other(a, ua, va);
+        for (int e = 0; e < 4; e++) {
+            int o1 = e & 1, o2 = e >> 1;
+            int b0[3], b1[3];
+            b0[a] = 0; b1[a] = 1; b0[ua] = b1[ua] = o1; b0[va] = b1[va] = o2;
+            double g0 = corner(g, b0[0], b0[1], b0[2]), g1 = corner(g, b1[0], b1[1], b1[2]);
+            eid[4 * a + e] = -1;
+            if ((g0 >= c) == (g1 >= c)) continue;
+            int id = (int)add_pt(pts, np, 0);
+            pts[id].p[a] = __ddiv_rn(__dsub_rn(c, g0), __dsub_rn(g1, g0));
+            pts[id].p[ua] = o1;
+            pts[id].p[va] = o2;
+            int64_t L[3];
+            L[a] = C[a] * sc; L[ua] = (C[ua] + o1) * sc; L[va] = (C[va] + o2) * sc;
+            pts[id].key = gk_make(L[0], L[1], L[2], (unsigned)a, (unsigned)lvl);
+            eid[4 * a + e] = (signed char)id;
+        }
+    }
+    // fold lines: own (both ends) and the same-size neighbours' ends on shared faces
+    signed char fpt[6][4];
+    int nfp[6] = {0, 0, 0, 0, 0, 0};
+    double rt[3][2][2];
+    signed char fend[3][2][2];
+    int nr[3];
+    for (int a = 0; a < 3; a++) {
+        int ua, va;
+        axes_other(a, ua, va);
+        double ru[2], rv[2];
+        nr[a] = fold_solve(g, a, c, ru, rv);
+        for (int r = 0; r < nr[a]; r++) {
+            rt[a][r][0] = ru[r]; rt[a][r][1] = rv[r];
+            for (int sd = 0; sd < 2; sd++) {
+                int id = (int)add_pt(pts, np, 1);
+                if (id < 0) return 1;
+                pts[id].p[a] = sd; pts[id].p[ua] = ru[r]; pts[id].p[va] = rv[r];
+                int64_t L[3] = {C[0] * sc, C[1] * sc, C[2] * sc};
+                L[a] = (C[a] + sd) * sc;
+                pts[id].key = gk_make(L[0], L[1], L[2], 8u + 4u * a + 2u * (sd == 0 ? 1u : 0u) + (unsigned)r, (unsigned)lvl);
+                fend[a][r][sd] = (signed char)id;
+                fpt[2 * a + sd][nfp[2 * a + sd]++] = (signed char)id;
+            }
+        }
+        for (int sd = 0; sd < 2; sd++) {
+            int nb = X.nbr[ci * 6 + 2 * a + sd];
+            if (nb < 0) continue;
+            double gn[8];
+            for (int v = 0; v < 8; v++) gn[v] = X.phi[X.cvid[(int64_t)nb * 8 + v]];
+            double nu_[2], nv_[2];
+            int nn = fold_solve(gn, a, c, nu_, nv_);
+            for (int r = 0; r < nn; r++) {
+                int id = (int)add_pt(pts, np, 2);
+                if (id < 0) return 1;
+                pts[id].p[a] = sd; pts[id].p[ua] = nu_[r]; pts[id].p[va] = nv_[r];
+                int64_t L[3] = {C[0] * sc, C[1] * sc, C[2] * sc};
+                L[a] = (C[a] + sd) * sc;
+                pts[id].key = gk_make(L[0], L[1], L[2], 8u + 4u * a + 2u * (sd == 1 ? 1u : 0u) + (unsigned)r, (unsigned)lvl);
+                fpt[2 * a + sd][nfp[2 * a + sd]++] = (signed char)id;
+            }
+        }
+    }
+    // critical points: a-fold i and b-fold j share the coordinate of the third axis
+    signed char chain[3][2][4];
+    int nch[3][2];
+    for (int a = 0; a < 3; a++)
+        for (int r = 0; r < nr[a]; r++) { chain[a][r][0] = fend[a][r][0]; nch[a][r] = 1; }
+    for (int a = 0; a < 3; a++)
+        for (int b = a + 1; b < 3; b++) {
+            int cc = 3 - a - b;
+            int ua, va, ub, vb;
+            axes_other(a, ua, va);
+            axes_other(b, ub, vb);
+            for (int i = 0; i < nr[a]; i++)
+                for (int j = 0; j < nr[b]; j++) {
+                    double ca = rt[a][i][cc == ua ? 0 : 1], cb = rt[b][j][cc == ub ? 0 : 1];
+                    if (fabs(ca - cb) > 1e-9) continue;
+                    int id = (int)add_pt(pts, np, 3);
+                    if (id < 0) return 1;
+                    TPt &P = pts[id];
+                    P.p[a] = rt[b][j][a == ub ? 0 : 1];
+                    P.p[b] = rt[a][i][b == ua ? 0 : 1];
+                    P.p[cc] = ca;
+                    P.fa = (signed char)a; P.fb = (signed char)b;
+                    // dg/dx_cc at the point: the outward normal is -sign(dg/dx_cc) e_cc
+                    double dg = 0;
+                    for (int v = 0; v < 8; v++) {
+                        double f = 1.0;
+                        for (int t = 0; t < 3; t++) {
+                            int bit = (v >> t) & 1;
+                            f *= (t == cc) ? (bit ? 1.0 : -1.0) : (bit ? P.p[t] : 1.0 - P.p[t]);
+                        }
+                        dg += f * g[v];
+                    }
+                    bool cyclic = !(a == 0 && b == 2);   // (a,b,cc) an even permutation
+                    P.rh = (signed char)(cyclic == (dg < 0.0) ? 1 : 0);
+                    P.key = gk_make(C[0] * sc, C[1] * sc, C[2] * sc, 20u + 4u * (unsigned)(a + b - 1) + 2u * i + j,
+                                    (unsigned)lvl);
+                    if (nch[a][i] < 3) chain[a][i][nch[a][i]++] = (signed char)id;
+                    if (nch[b][j] < 3) chain[b][j][nch[b][j]++] = (signed char)id;
+                }
+        }
+    for (int a = 0; a < 3; a++)
+        for (int r = 0; r < nr[a]; r++) {
+            signed char *ch = chain[a][r];
+            int n = nch[a][r];
+            if (n == 3 && pts[ch[2]].p[a] < pts[ch[1]].p[a]) { signed char t = ch[1]; ch[1] = ch[2]; ch[2] = t; }
+            ch[n++] = fend[a][r][1];
+            for (int k = 0; k + 1 < n; k++) {
+                int p0 = ch[k], p1 = ch[k + 1];
+                if (pts[p0].kind == 3) pts[p0].nb[pts[p0].fa == a ? 0 : 2] = (signed char)p1;
+                else pts[p0].nb[0] = (signed char)p1;
+                if (pts[p1].kind == 3) pts[p1].nb[pts[p1].fa == a ? 1 : 3] = (signed char)p0;
+                else pts[p1].nb[0] = (signed char)p0;
+            }
+        }
+    // face arcs -> successor along the loops
+    signed char nxt[TP_MAX];
+    for (int i = 0; i < np; i++) nxt[i] = -1;
+    for (int a = 0; a < 3; a++) {
+        int ua, va;
+        axes_other(a, ua, va);
+        for (int sd = 0; sd < 2; sd++) {
+            double h[4];
+            for (int k = 0; k < 4; k++) {
+                int b[3];
+                b[a] = sd; b[ua] = k & 1; b[va] = k >> 1;
+                h[k] = corner(g, b[0], b[1], b[2]);
+            }
+            // face edges in the (u,v) frame: 0 v=0, 1 u=1, 2 v=1, 3 u=0
+            int ep[4];
+            for (int e = 0; e < 4; e++) {
+                int along = (e & 1) ? va : ua;
+                int fixed = (e & 1) ? ua : va;
+                int fval = (e == 1 || e == 2) ? 1 : 0;
+                int bits[3];
+                bits[along] = 0; bits[a] = sd; bits[fixed] = fval;
+                int o1, o2;
+                axes_other(along, o1, o2);
+                ep[e] = eid[4 * along + bits[o1] + 2 * bits[o2]];
+            }
+            int around00;
+            double us;
+            int narc = face_arcs(h, c, around00, us);
+            int fid = 2 * a + sd;
+            if (narc == 0) {
+                if (nfp[fid] > 0) return 1;
+                continue;
+            }
+            // start test: the curve leaves the boundary point into the face,
+            // with the inside on its right seen from outside the cube
+            double hs = (sd ? 1.0 : -1.0) * (a == 1 ? -1.0 : 1.0);
+            double st[4] = {hs * (h[1] - h[0]), hs * (h[3] - h[1]), -hs * (h[3] - h[2]), -hs * (h[2] - h[0])};
+            int pr[2][2];
+            if (narc == 1) {
+                int k = 0;
+                for (int e = 0; e < 4; e++)
+                    if (ep[e] >= 0) { if (k < 2) pr[0][k] = e; k++; }
+                if (k != 2) return 1;
+            } else {
+                if (around00) { pr[0][0] = 0; pr[0][1] = 3; pr[1][0] = 2; pr[1][1] = 1; }
+                else { pr[0][0] = 0; pr[0][1] = 1; pr[1][0] = 2; pr[1][1] = 3; }
+            }
+            for (int ai = 0; ai < narc; ai++) {
+                int e1 = pr[ai][0], e2 = pr[ai][1];
+                if (ep[e1] < 0 || ep[e2] < 0) return 1;
+                bool s1 = st[e1] > 0, s2 = st[e2] > 0;
+                if (s1 == s2) return 1;
+                int S = s1 ? ep[e1] : ep[e2], T = s1 ? ep[e2] : ep[e1];
+                int mid[8], nm = 0;
+                for (int t = 0; t < nfp[fid]; t++) {
+                    int id = fpt[fid][t];
+                    if (narc == 2) {
+                        bool low = pts[id].p[ua] < us;
+                        bool arc_low = ai == 0 ? (around00 != 0) : (around00 == 0);
+                        if (low != arc_low) continue;
+                    }
+                    if (nm < 8) mid[nm++] = id;
+                }
+                double du = pts[T].p[ua] - pts[S].p[ua], dv = pts[T].p[va] - pts[S].p[va];
+                int ax = fabs(du) >= fabs(dv) ? ua : va;
+                double sg = (ax == ua ? du : dv) >= 0 ? 1.0 : -1.0;
+                for (int i1 = 1; i1 < nm; i1++) {
+                    int x = mid[i1], j = i1 - 1;
+                    while (j >= 0) {
+                        double kx = sg * pts[x].p[ax], kj = sg * pts[mid[j]].p[ax];
+                        if (kj > kx || (kj == kx && pts[mid[j]].key > pts[x].key)) { mid[j + 1] = mid[j]; j--; }
+                        else break;
+                    }
+                    mid[j + 1] = x;
+                }
+                int prev = S;
+                for (int i1 = 0; i1 <= nm; i1++) {
+                    int cur = i1 < nm ? mid[i1] : T;
+                    if (nxt[prev] >= 0) return 1;
+                    nxt[prev] = (signed char)cur;
+                    prev = cur;
+                }
+            }
+        }
+    }
+    for (int i = 0; i < np; i++)
+        if (pts[i].kind != 3 && nxt[i] < 0) return 1;
+
+    // pieces: faces of the graph of loops and fold segments, traced with the
+    // face on the left; at a critical point take the next segment clockwise
+    unsigned long long used_loop = 0ull;
+    unsigned char used_fold[TP_MAX];
+    for (int i = 0; i < np; i++) used_fold[i] = 0;
+    const int cw_r[4] = {3, 2, 0, 1}, cw_l[4] = {2, 3, 1, 0};
+    for (int i0 = 0; i0 < np; i0++) {
+        if (pts[i0].kind == 3 || ((used_loop >> i0) & 1ull)) continue;
+        unsigned char poly[POLY_MAX];
+        int n = 0;
+        int cur = i0, slot = -1;
+        bool ok = true;
+        for (int steps = 0;; steps++) {
+            if (steps >= POLY_MAX || n >= POLY_MAX) { ok = false; break; }
+            poly[n++] = (unsigned char)cur;
+            int nx;
+            if (slot < 0) { used_loop |= 1ull << cur; nx = nxt[cur]; }
+            else { used_fold[cur] |= (unsigned char)(1u << slot); nx = pts[cur].nb[slot]; }
+            if (nx < 0) { ok = false; break; }
+            int ns;
+            if (slot < 0) ns = pts[nx].kind == 1 ? 0 : -1;
+            else if (pts[nx].kind != 3) ns = -1;
+            else {
+                int back = -1;
+                for (int k = 0; k < 4; k++) if (pts[nx].nb[k] == cur) back = k;
+                if (back < 0) { ok = false; break; }
+                ns = pts[nx].rh ? cw_r[back] : cw_l[back];
+                if (pts[nx].nb[ns] < 0) { ok = false; break; }
+            }
+            cur = nx;
+            slot = ns;
+            if (slot < 0 && cur == i0) break;
+            if (slot < 0 && ((used_loop >> cur) & 1ull)) { ok = false; break; }
+            if (slot >= 0 && ((used_fold[cur] >> slot) & 1u)) { ok = false; break; }
+        }
+        if (!ok) return 1;
+        if (n >= 3) clip_piece(pts, poly, n, o, degen);
+    }
+    // points in world coordinates
+    if (o.emit) {
+        double h = ldexp(X.min_edge, X.max_depth - lvl);
+        for (int i = 0; i < np; i++) {
+            double *dst = o.pt_xyz + 3 * (o.pt_off + i);
+            for (int a = 0; a < 3; a++) {
+                double f = pts[i].p[a];
+                double lo = __dadd_rn(X.origin[a], __dmul_rn((double)(C[a] * sc), X.min_edge));
+                if (f == 0.0) dst[a] = lo;
+                else if (f == 1.0) dst[a] = __dadd_rn(X.origin[a], __dmul_rn((double)((C[a] + 1) * sc), X.min_edge));
+                else dst[a] = __dadd_rn(lo, __dmul_rn(f, h));
+            }
+            o.pt_keys[o.pt_off + i] = pts[i].key;
+        }
+    }
+    o.npt = np;
+    return 0;
+}
+
+__global__ void __launch_bounds__(128) k_tri_count(TriCtx X, int64_t *__restrict__ ntri, int64_t *__restrict__ npt,
+                                                   unsigned long long *errs, unsigned long long *surface)
+{
+    int64_t ci = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (ci >= X.ncubes) return;
+    TriOut o;
+    o.emit = false; o.ntri = 0; o.npt = 0; o.tri_off = 0; o.pt_off = 0;
+    o.tri_keys = nullptr; o.pt_keys = nullptr; o.pt_xyz = nullptr;
+    int bad = tri_cube(X, ci, o, nullptr);
+    if (bad) { atomicAdd(errs, 1ull); o.ntri = 0; o.npt = 0; }
+    if (o.npt > 0) atomicAdd(surface, 1ull);
+    ntri[ci] = o.ntri;
+    npt[ci] = o.npt;
+}
+
+__global__ void __launch_bounds__(128) k_tri_emit(TriCtx X, const int64_t *__restrict__ tri_off,
+                                                  const int64_t *__restrict__ pt_off, uint64_t *__restrict__ tri_keys,
+                                                  uint64_t *__restrict__ pt_keys, double *__restrict__ pt_xyz,
+                                                  unsigned long long *degen)
+{
+    int64_t ci = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (ci >= X.ncubes) return;
+    if (tri_off[ci + 1] == tri_off[ci] && pt_off[ci + 1] == pt_off[ci]) return;
+    TriOut o;
+    o.emit = true; o.ntri = 0; o.npt = 0; o.tri_off = tri_off[ci]; o.pt_off = pt_off[ci];
+    o.tri_keys = tri_keys; o.pt_keys = pt_keys; o.pt_xyz = pt_xyz;
+    tri_cube(X, ci, o, degen);
+}
+
+// ---------------------------------------------------------------- host
+int gs_triangulate(const TriCtx &X, uint64_t **d_tri_keys, int64_t *ntri_total, uint64_t **d_pt_keys,
+                   double **d_pt_xyz, int64_t *npt_total, unsigned long long *d_counters, cudaStream_t st)
+{
+    int64_t n = X.ncubes;
+    *d_tri_keys = nullptr; *d_pt_keys = nullptr; *d_pt_xyz = nullptr;
+    *ntri_total = 0; *npt_total = 0;
+    if (n <= 0) return GS_OK;
+    int64_t *ntri = nullptr, *npt = nullptr, *tot = nullptr;
+    int rc = gs_alloc((void **)&ntri, sizeof(int64_t) * (size_t)(n + 1), st);
+    if (!rc) rc = gs_alloc((void **)&npt, sizeof(int64_t) * (size_t)(n + 1), st);
+    if (!rc) rc = gs_alloc((void **)&tot, 2 * sizeof(int64_t), st);
+    if (rc) { gs_free(ntri, st); gs_free(npt, st); gs_free(tot, st); return rc; }
+    unsigned nb = (unsigned)((n + 127) / 128);
+    cudaMemsetAsync(ntri + n, 0, sizeof(int64_t), st);
+    cudaMemsetAsync(npt + n, 0, sizeof(int64_t), st);
+    k_tri_count<<<nb, 128, 0, st>>>(X, ntri, npt, d_counters + 0, d_counters + 2);
+    rc = gs_scan_i64(ntri, n + 1, tot, st);
+    if (!rc) rc = gs_scan_i64(npt, n + 1, tot + 1, st);
+    int64_t h[2] = {0, 0};
+    if (!rc) {
+        cudaError_t e = cudaMemcpyAsync(h, tot, sizeof(h), cudaMemcpyDeviceToHost, st);
+        if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+        if (e != cudaSuccess) rc = gs_fail_cuda(e, "triangle counts", __FILE__, __LINE__);
+    }
+    if (!rc) {
+        rc = gs_alloc((void **)d_tri_keys, sizeof(uint64_t) * 3 * (size_t)(h[0] + 1), st);
+        if (!rc) rc = gs_alloc((void **)d_pt_keys, sizeof(uint64_t) * (size_t)(h[1] + 1), st);
+        if (!rc) rc = gs_alloc((void **)d_pt_xyz, sizeof(double) * 3 * (size_t)(h[1] + 1), st);
+    }
+    if (!rc) k_tri_emit<<<nb, 128, 0, st>>>(X, ntri, npt, *d_tri_keys, *d_pt_keys, *d_pt_xyz, d_counters + 1);
+    gs_free(ntri, st); gs_free(npt, st); gs_free(tot, st);
+    if (rc) return rc;
+    GS_CHECK(cudaGetLastError());
+    *ntri_total = h[0];
+    *npt_total = h[1];
+    return GS_OK;
+}

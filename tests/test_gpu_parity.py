@@ -1,0 +1,143 @@
+"""GPU parity: the CUDA path through the C ABI against the CPU oracle on the
+same seeded inputs.  Bars: bit-exact for integer/key work (cell lists, cube
+sets, surface-point keys, triangle topology); floating point within the
+stated tolerances (field values 1e-13 relative, coefficient tensors 1e-12 of
+their scale, vertex positions 1e-5 A)."""
+import numpy as np
+import pytest
+
+import oracle
+import synth
+from meshcheck import canonical_triangles, check_closed_manifold
+
+pytestmark = pytest.mark.gpu
+
+gs = pytest.importorskip("paper_1611_03474_gb300")
+
+
+@pytest.fixture(scope="module")
+def chain100():
+    return synth.config("chain100")
+
+
+def test_cell_list_bit_exact(chain100):
+    xyz = chain100["xyz"]
+    for cell in (3.1, 1.0, 7.5):
+        origin = xyz.min(0) - 2.0
+        dims = np.ceil((xyz.max(0) + 2.0 - origin) / cell).astype(np.int64) + 1
+        cs, pm = gs.gs_bin_atoms(xyz, cell, origin, dims)
+        rs, rp = oracle.cell_list(xyz, cell, origin, dims)
+        assert np.array_equal(cs, rs) and np.array_equal(pm, rp)
+
+
+def test_cell_list_ragged_large():
+    rng = np.random.default_rng(11)
+    xyz = rng.uniform(-50, 50, (100003, 3))
+    origin, cell = np.array([-51.0, -51.0, -51.0]), 3.3
+    dims = np.array([32, 32, 32])
+    cs, pm = gs.gs_bin_atoms(xyz, cell, origin, dims)
+    rs, rp = oracle.cell_list(xyz, cell, origin, dims)
+    assert np.array_equal(cs, rs) and np.array_equal(pm, rp)
+
+
+def test_field_fp64_parity(chain100):
+    rng = np.random.default_rng(1)
+    xyz, r = chain100["xyz"], chain100["r"]
+    pts = xyz[rng.integers(0, len(r), 3000)] + rng.normal(0, 2.0, (3000, 3))
+    phi, g = gs.gs_eval_field(xyz, r, 0.5, 1.0, pts, grad=True)
+    rphi, rg = oracle.field(xyz, r, 0.5, 1.0, pts, grad=True)
+    assert np.allclose(phi, rphi, rtol=1e-13, atol=1e-300)
+    assert np.allclose(g, rg, rtol=1e-12, atol=1e-14 * np.abs(rg).max())
+
+
+def _sample_cubes(cfg, rng, n_per_level=200):
+    o, nroot, pad = oracle.root_grid(cfg["xyz"], cfg["r"], cfg["D"], cfg["c"], cfg["min_edge"], cfg["max_depth"])
+    keys = []
+    for l in range(cfg["max_depth"] + 1):
+        h = cfg["min_edge"] * 2 ** (cfg["max_depth"] - l)
+        centers = cfg["xyz"][rng.integers(0, len(cfg["r"]), n_per_level)] + rng.normal(0, 2.0, (n_per_level, 3))
+        idx = np.floor((centers - o) / h).astype(np.int64)
+        idx = np.clip(idx, 0, (nroot << l) - 1)
+        for x, y, z in idx:
+            keys.append(int(x) | (int(y) << 18) | (int(z) << 36) | (30 << 54) | (l << 59))
+    return np.unique(np.array(keys, dtype=np.uint64))
+
+
+def test_cube_tensors_and_decisions_parity(chain100):
+    cfg = chain100
+    keys = _sample_cubes(cfg, np.random.default_rng(2))
+    A, b, d = gs.gs_cube_decisions(cfg["xyz"], cfg["r"], cfg["D"], cfg["c"], cfg["precision"], cfg["min_edge"],
+                                   cfg["max_depth"], keys)
+    rA, rb, rd = oracle.cube_batch(cfg["xyz"], cfg["r"], cfg["D"], cfg["c"], cfg["precision"], cfg["min_edge"],
+                                   cfg["max_depth"], keys)
+    scale = np.abs(rA).sum(1, keepdims=True) + 1e-300
+    assert np.all(np.abs(A - rA) <= 1e-12 * scale)
+    assert np.array_equal(d, rd)
+    kept = rd != 0
+    assert np.allclose(b[kept, :4], rb[kept, :4], rtol=1e-9, atol=1e-11)
+
+
+def _mesh_both(cfg, **kw):
+    m = gs.mesh_gaussian_surface(cfg["xyz"], cfg["r"], cfg["D"], cfg["c"], cfg["precision"], cfg["max_depth"],
+                                 min_edge=cfg["min_edge"], **kw)
+    ref = oracle.mesh(cfg["xyz"], cfg["r"], cfg["D"], cfg["c"], cfg["precision"], cfg["min_edge"], cfg["max_depth"])
+    return m, ref
+
+
+def _assert_mesh_parity(m, ref):
+    assert np.array_equal(np.sort(m.cube_keys), ref["cube_keys"])
+    assert np.array_equal(np.sort(m.vertex_keys), ref["vkeys"])
+    order = np.argsort(m.vertex_keys)
+    assert np.abs(m.vertices[order] - ref["vertices"]).max() < 1e-5
+    assert np.array_equal(canonical_triangles(m.vertex_keys, m.triangles),
+                          canonical_triangles(ref["vkeys"], ref["triangles"]))
+
+
+def test_mesh_parity_chain100(chain100):
+    m, ref = _mesh_both(chain100)
+    st = m.stats
+    for l in range(chain100["max_depth"] + 1):
+        assert st["examined"][l] == ref["stats"]["examined"][l]
+        assert st["split"][l] == ref["stats"]["split"][l]
+    assert st["loop_errors"] == 0
+    _assert_mesh_parity(m, ref)
+    check_closed_manifold(m.vertices, m.triangles)
+
+
+def test_mesh_parity_single_atom_and_mixed_levels():
+    xyz, r = np.array([[0.1, 0.2, 0.3]]), np.array([1.5])
+    cfg = dict(xyz=xyz, r=r, D=0.5, c=1.0, precision=1e-3, min_edge=0.25, max_depth=3)
+    _assert_mesh_parity(*_mesh_both(cfg))
+    # a loose precision accepts cubes at several levels: conformity splits
+    cfg2 = dict(synth.config("chain100"), precision=0.05)
+    m, ref = _mesh_both(cfg2)
+    _assert_mesh_parity(m, ref)
+    assert m.stats["conformity_splits"] == ref["stats"]["conformity_splits"]
+
+
+def test_empty_surface_is_success():
+    xyz, r = np.array([[0.0, 0.0, 0.0]]), np.array([1.0])
+    m = gs.mesh_gaussian_surface(xyz, r, 0.5, 50.0, 1e-3, 2)
+    assert len(m.triangles) == 0 and len(m.vertices) == 0
+
+
+def test_non_finite_input_rejected():
+    xyz = np.array([[0.0, np.nan, 0.0]])
+    with pytest.raises(gs.GsError) as e:
+        gs.mesh_gaussian_surface(xyz, np.array([1.5]), 0.5, 1.0, 1e-3, 2)
+    assert e.value.code == -1
+
+
+@pytest.mark.parametrize("seed", range(4))
+def test_grid_triangulation_parity(seed):
+    rng = np.random.default_rng(seed)
+    vals = rng.standard_normal((9, 9, 9))
+    vals[0], vals[-1], vals[:, 0], vals[:, -1], vals[:, :, 0], vals[:, :, -1] = -1, -1, -1, -1, -1, -1
+    m = gs.gs_triangulate_grid(vals, 0.0)
+    ref = oracle.mesh_grid(vals, 0.0)
+    assert np.array_equal(np.sort(m.vertex_keys), ref["vkeys"])
+    order = np.argsort(m.vertex_keys)
+    assert np.abs(m.vertices[order] - ref["vertices"]).max() < 1e-12
+    assert np.array_equal(canonical_triangles(m.vertex_keys, m.triangles),
+                          canonical_triangles(ref["vkeys"], ref["triangles"]))
+    check_closed_manifold(m.vertices, m.triangles)
