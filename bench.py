@@ -1,0 +1,293 @@
+"""Benchmark: milliseconds per surface mesh of a 1,000,020-atom synthetic
+assembly (60 icosahedrally arranged copies of a 16,667-atom globular unit on
+a 250 A shell; D = 0.5, c = 1, precision 1e-3, min edge 0.25 A, 3 levels)
+on one GB300, through the C ABI.
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--mode mixed|fp64]
+                  [--impl ours|reference]
+
+One JSON line on rank 0.  `value` times mesh_gaussian_surface with the atoms
+already resident in HBM and the mesh left on the device; `e2e` times the
+same call with host (pinned) inputs and host outputs, copies included.  L2
+is flushed (a 256 MB write) between timed steps, outside the timed region.
+Under torchrun each rank meshes its own copy (replicas, weak scaling); the
+reported time is the maximum over ranks.  --impl reference times the CPU
+oracle on a bounded cut-out of the same workload instead.
+"""
+import argparse
+import json
+import os
+import subprocess
+import sys
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "ms per surface mesh (1M atoms), mixed vs FP64 GPU; Gaussian evals/s, % peak"
+WORKLOAD = dict(name="assembly1m", atoms=1000020, D=0.5, c=1.0, precision=1e-3, min_edge=0.25, max_depth=3)
+# plain-ALU peaks (FLOP/s) from the unit counts and clocks: 152 SMs at 2070 MHz;
+# FP32: 128 FMA lanes/SM/clk; FP64: 2 FMA/SM/clk (1.25 TFLOP/s nominal);
+# an FMA counts 2 flops
+SM_COUNT, SM_MHZ = 152, 2070.0
+PEAK_FP32 = SM_COUNT * 128 * 2 * SM_MHZ * 1e6
+PEAK_FP64 = SM_COUNT * 2 * 2 * SM_MHZ * 1e6
+# algorithmic work of one (cube, atom) term of the tensor accumulation:
+# the rank-one update of the 4x4x4 tensor (64 FMA) and its 16 y-z products
+FLOPS_PER_PAIR = 64 * 2 + 16
+
+
+def dist_env():
+    ws = int(os.environ.get("WORLD_SIZE", "1"))
+    return ws, int(os.environ.get("RANK", "0")), int(os.environ.get("LOCAL_RANK", "0"))
+
+
+class ClockSampler:
+    """nvidia-smi clocks and throttle reasons sampled every 200 ms."""
+
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index):
+        self.index = index
+        self.proc = None
+        self.path = os.path.join("/tmp", "gs_clocks_%d_%d.csv" % (os.getpid(), index))
+
+    def start(self):
+        try:
+            self.f = open(self.path, "w")
+            self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.index), "--query-gpu=" + self.FIELDS,
+                                          "--format=csv,noheader,nounits", "-lms", "200"], stdout=self.f,
+                                         stderr=subprocess.DEVNULL)
+        except Exception:
+            self.proc = None
+
+    def stop(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        self.f.close()
+        sm, smax, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for line in open(self.path):
+            p = [x.strip() for x in line.split(",")]
+            if len(p) < 9:
+                continue
+            try:
+                sm.append(float(p[1]))
+                smax.append(float(p[2]))
+            except ValueError:
+                continue
+            for nm, v in zip(names, p[5:9]):
+                if v.lower() in ("active", "1"):
+                    reasons.add(nm)
+        os.unlink(self.path)
+        return {"sm_mhz": float(np.median(sm)) if sm else None, "sm_max_mhz": max(smax) if smax else None,
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+def cpu_baseline(cfg, n_sample=300):
+    """The oracle, as it stands, on a cut-out of the workload: the n_sample
+    atoms nearest to the outermost atom of the first unit.  Scaled to a whole
+    mesh by atom count (the method is O(N); the oracle's brute-force atom scan
+    makes the real full-size figure larger still)."""
+    import oracle
+    xyz, r = cfg["xyz"], cfg["r"]
+    unit = xyz[:16667]
+    cen = unit.mean(0)
+    p0 = unit[np.argmax(((unit - cen) ** 2).sum(1))]
+    idx = np.argsort(((xyz - p0) ** 2).sum(1))[:n_sample]
+    sx, sr = np.ascontiguousarray(xyz[idx]), np.ascontiguousarray(r[idx])
+    oracle.build()
+    t0 = time.perf_counter()
+    m = oracle.mesh(sx, sr, cfg["D"], cfg["c"], cfg["precision"], cfg["min_edge"], cfg["max_depth"])
+    dt = time.perf_counter() - t0
+    scale = len(r) / n_sample
+    return {"value": dt * 1e3 * scale, "unit": "ms", "cores": 1, "kind": "oracle",
+            "sample": "oracle.mesh (FP64, single thread) on the %d atoms of the assembly nearest the outermost atom "
+                      "of unit 0 (%d triangles, %.1f s), scaled x%.0f by atom count"
+                      % (n_sample, len(m["triangles"]), dt, scale),
+            "sample_seconds": dt}
+
+
+def run_reference(args, ws, rank):
+    if rank != 0:
+        return
+    import synth
+    cfg = synth.config(WORKLOAD["name"])
+    vals = []
+    for i in range(args.warmup + args.steps):
+        b = cpu_baseline(cfg, n_sample=args.ref_sample)
+        if i >= args.warmup:
+            vals.append(b["value"])
+    v = float(np.mean(vals))
+    line = {"impl": "reference", "metric": METRIC, "value": v, "unit": "ms", "n_gpus": args.gpus,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": v, "higher_is_better": False,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": "assembly1m: 1,000,020 atoms, D=0.5, c=1, precision 1e-3, min edge 0.25 A, "
+                                   "max_depth 3", "sample_atoms": args.ref_sample},
+            "cpu_baseline": dict(b, value=v),
+            "e2e": {"value": v, "unit": "ms", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=3)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--mode", default="mixed", choices=["mixed", "fp64"])
+    ap.add_argument("--workload", default="assembly1m")
+    ap.add_argument("--ref-sample", type=int, default=300)
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--fp64-steps", type=int, default=1, help="extra FP64-form steps timed for comparison")
+    args = ap.parse_args()
+    ws, rank, local = dist_env()
+    if args.impl == "reference":
+        run_reference(args, ws, rank)
+        return
+
+    import torch
+
+    import paper_1611_03474_gb300 as gs
+    import synth
+    from paper_1611_03474_gb300 import build
+
+    if ws > 1:
+        import torch.distributed as dist
+        torch.cuda.set_device(local)
+        dist.init_process_group("nccl")
+    else:
+        torch.cuda.set_device(0)
+    if rank == 0 or not os.path.exists(build.LIB):
+        build.build()
+    if ws > 1:
+        dist.barrier()
+    dev = torch.device("cuda", torch.cuda.current_device())
+    cfg = synth.config(args.workload)
+    mode = gs.GS_PREC_MIXED if args.mode == "mixed" else gs.GS_PREC_FP64
+    stream = torch.cuda.current_stream()
+    xyz_d = torch.from_numpy(cfg["xyz"]).to(dev)
+    r_d = torch.from_numpy(cfg["r"]).to(dev)
+    flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)
+    kw = dict(min_edge=cfg["min_edge"], stream=stream)
+
+    def run(x, r, prec, device_output=True):
+        return gs.mesh_gaussian_surface(x, r, cfg["D"], cfg["c"], cfg["precision"], cfg["max_depth"],
+                                        precision_mode=prec, device_output=device_output, **kw)
+
+    for _ in range(args.warmup):
+        run(xyz_d, r_d, mode)
+    torch.cuda.synchronize()
+
+    def barrier():
+        if ws > 1:
+            dist.barrier()
+        torch.cuda.synchronize()
+
+    clocks = ClockSampler(torch.cuda.current_device())
+    clocks.start()
+    times, stats = [], []
+    for _ in range(args.steps):
+        flush.zero_()
+        barrier()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        m = run(xyz_d, r_d, mode)
+        e1.record(stream)
+        barrier()
+        times.append(e0.elapsed_time(e1))
+        stats.append(m.stats)
+    clk = clocks.stop()
+    ms = float(np.mean(times))
+    if ws > 1:
+        t = torch.tensor([ms], device=dev, dtype=torch.float64)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        ms = float(t.item())
+
+    # end to end: pinned host inputs, host outputs, copies inside the timed region
+    xyz_h = torch.from_numpy(cfg["xyz"]).pin_memory()
+    r_h = torch.from_numpy(cfg["r"]).pin_memory()
+    e2e_times, nbytes_out = [], 0
+    for _ in range(max(1, min(args.steps, 2))):
+        flush.zero_()
+        barrier()
+        t0 = time.perf_counter()
+        mh = run(xyz_h, r_h, mode, device_output=False)
+        t1 = time.perf_counter()
+        e2e_times.append((t1 - t0) * 1e3)
+        nbytes_out = mh.vertices.nbytes + mh.triangles.nbytes + mh.vertex_keys.nbytes + mh.cube_keys.nbytes
+    e2e_ms = float(np.mean(e2e_times))
+
+    # FP64 form for the comparison the metric names
+    fp64 = None
+    if args.fp64_steps > 0 and mode != gs.GS_PREC_FP64:
+        ft = []
+        for _ in range(args.fp64_steps):
+            flush.zero_()
+            barrier()
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            mf = run(xyz_d, r_d, gs.GS_PREC_FP64)
+            e1.record(stream)
+            barrier()
+            ft.append(e0.elapsed_time(e1))
+        fp64 = {"ms_per_mesh": float(np.mean(ft)), "pair_terms": mf.stats["pair_terms"],
+                "ms_accum": mf.stats["ms_accum"], "n_triangles": mf.stats["n_triangles"]}
+
+    st = stats[-1]
+    pairs = st["pair_terms"]
+    acc_ms = float(np.mean([s["ms_accum"] for s in stats]))
+    launches = max(1, st["n_accum_launches"])
+    fp32 = mode == gs.GS_PREC_MIXED and st.get("recheck_cubes", 0) >= 0 and args.mode == "mixed"
+    peak = PEAK_FP32 if fp32 else PEAK_FP64
+    achieved = pairs * FLOPS_PER_PAIR / (acc_ms * 1e-3) if acc_ms > 0 else 0.0
+    roofline = {"bound": "alu", "kernel": "k_accum_f32" if fp32 else "k_accum_f64",
+                "achieved": achieved / 1e12, "peak": peak / 1e12, "unit": "TFLOP/s", "frac": achieved / peak,
+                "traffic": None, "launches_per_step": launches, "ms_per_launch": acc_ms / launches,
+                "peak_source": "152 SMs x 2070 MHz x (%s) FMA/SM/clk x 2 (unit counts and clocks)"
+                               % ("128 FP32" if fp32 else "2 FP64")}
+    evals = pairs + st["vertex_terms"]
+    line = {
+        "metric": METRIC, "value": ms * (1.0 / ws), "unit": "ms", "n_gpus": ws, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": False, "scaling": "weak",
+        "vs_baseline": None, "dtype": "f32+f64" if fp32 else "f64", "data": "synthetic",
+        "config": {"workload": "assembly1m: 1,000,020 atoms (60 x 16,667-atom globular unit on a 250 A "
+                               "icosahedral shell), D=0.5, c=1, precision 1e-3, min edge 0.25 A, max_depth 3",
+                   "mode": args.mode, "parallelism": "replicas" if ws > 1 else "single",
+                   "l2": "256 MB flush between timed steps"},
+        "gaussian_evals_per_s": evals / (ms * 1e-3),
+        "mesh": {"n_vertices": st["n_vertices"], "n_triangles": st["n_triangles"],
+                 "n_cubes_final": st["n_cubes_final"], "examined": st["examined"][:4]},
+        "stage_ms": {k: st[k] for k in ("ms_bin", "ms_levels", "ms_conformity", "ms_field", "ms_triangulate",
+                                        "ms_weld")},
+        "level_ms": st["ms_level"][:4],
+        "recheck": {"cubes": st["recheck_cubes"], "vertices": st["recheck_vertices"],
+                    "bounds": st["recheck_bounds"], "precision": st["recheck_precision"],
+                    "zero": st["recheck_zero"]},
+        "pair_terms": pairs, "vertex_terms": st["vertex_terms"],
+        "roofline": roofline,
+        "clocks": clk,
+        "e2e": {"value": e2e_ms, "unit": "ms", "h2d_bytes_per_step": int(xyz_h.nbytes + r_h.nbytes),
+                "d2h_bytes_per_step": int(nbytes_out)},
+        "gpu_launches": int(st["n_kernel_launches"]),
+        "fp64_form": fp64,
+    }
+    if rank == 0 and ws == 1 and not args.no_cpu_baseline:
+        line["cpu_baseline"] = cpu_baseline(cfg)
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+    if ws > 1:
+        dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

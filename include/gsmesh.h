@@ -77,6 +77,12 @@ typedef struct {
     int64_t degenerate_ears;   /* ear clipping steps with no strictly valid ear */
     double ms_total, ms_upload, ms_bin, ms_levels, ms_conformity, ms_field, ms_triangulate, ms_weld, ms_download;
     double ms_level[21];
+    double ms_accum;           /* summed duration of the tensor-accumulation launches (CUDA events) */
+    int64_t n_accum_launches;
+    int64_t atom_octets;       /* (octet, atom) pairs whose coefficients were computed */
+    int64_t n_kernel_launches; /* this library's kernel launches during the call */
+    int64_t recheck_bounds, recheck_precision, recheck_zero; /* mixed mode: why cubes were re-evaluated */
+    double mixed_err_ratio;    /* debug bit 0: largest |A_fp32 - A_fp64| / E observed */
 } gs_stats;
 
 typedef struct {
@@ -131,6 +137,10 @@ const char *gs_status_string(int status);
 
 /* message for the calling thread's last failure ("" if none) */
 const char *gs_last_error(void);
+
+/* sizeof of the ABI structs (0: gs_stats, 1: gs_options, 2: gs_mesh; else -1),
+ * for bindings to verify their layouts */
+int64_t gs_struct_size(int which);
 
 /*
  * gs_bin_atoms -- uniform cell list by a stable counting sort (the

@@ -30,7 +30,11 @@ class Stats(ctypes.Structure):
                 ("ms_levels", ctypes.c_double), ("ms_conformity", ctypes.c_double),
                 ("ms_field", ctypes.c_double), ("ms_triangulate", ctypes.c_double),
                 ("ms_weld", ctypes.c_double), ("ms_download", ctypes.c_double),
-                ("ms_level", ctypes.c_double * 21)]
+                ("ms_level", ctypes.c_double * 21), ("ms_accum", ctypes.c_double),
+                ("n_accum_launches", ctypes.c_int64), ("atom_octets", ctypes.c_int64),
+                ("n_kernel_launches", ctypes.c_int64), ("recheck_bounds", ctypes.c_int64),
+                ("recheck_precision", ctypes.c_int64), ("recheck_zero", ctypes.c_int64),
+                ("mixed_err_ratio", ctypes.c_double)]
 
     def as_dict(self, max_depth=20):
         d = {}
@@ -87,6 +91,12 @@ def load():
     L.gs_cube_decisions.restype = i32
     L.gs_triangulate_grid.argtypes = [i64, i64, i64, p, d, ctypes.POINTER(Options), ctypes.POINTER(MeshC)]
     L.gs_triangulate_grid.restype = i32
+    L.gs_struct_size.argtypes = [i32]
+    L.gs_struct_size.restype = i64
+    for which, cls in ((0, Stats), (1, Options), (2, MeshC)):
+        if L.gs_struct_size(which) != ctypes.sizeof(cls):
+            raise GsError(-1, "ABI struct %s: library %d bytes, binding %d" % (cls.__name__, L.gs_struct_size(which),
+                                                                            ctypes.sizeof(cls)))
     _lib = L
     return L
 
@@ -157,8 +167,10 @@ def _mesh_from_c(m, L, stats, max_depth):
 
 
 def mesh_gaussian_surface(atoms, radii, D, c, precision, max_depth, min_edge=0.25, precision_mode=GS_PREC_FP64,
-                          cutoff_rel=1e-8, stream=None, debug_flags=0):
-    """Mesh {phi = c}; see include/gsmesh.h."""
+                          cutoff_rel=1e-8, stream=None, debug_flags=0, device_output=False):
+    """Mesh {phi = c}; see include/gsmesh.h.  With device_output the mesh
+    stays in device memory and only its sizes and stats are returned (the
+    arrays are released)."""
     L = load()
     atoms = _host64(atoms, (-1, 3))
     radii = _host64(radii)
@@ -169,13 +181,18 @@ def mesh_gaussian_surface(atoms, radii, D, c, precision, max_depth, min_edge=0.2
     o.precision_mode = precision_mode
     o.cutoff_rel = cutoff_rel
     o.cuda_stream = _stream_ptr(stream)
-    o.device_output = 0
+    o.device_output = 1 if device_output else 0
     o.debug_flags = debug_flags
     o.stats = ctypes.pointer(st)
     m = MeshC()
     rc = L.mesh_gaussian_surface(_ptr(atoms), _ptr(radii), n, D, c, precision, max_depth, ctypes.byref(o),
                                  ctypes.byref(m))
     _check(rc)
+    if device_output:
+        res = Mesh(None, None, None, None, st.as_dict(max_depth), m.mismatches)
+        res.n_vertices, res.n_triangles, res.n_cubes = m.n_vertices, m.n_triangles, m.n_cubes
+        L.mesh_free(ctypes.byref(m))
+        return res
     return _mesh_from_c(m, L, st, max_depth)
 
 

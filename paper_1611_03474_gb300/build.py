@@ -15,6 +15,9 @@ BUILD = os.path.join(HERE, "_build")
 LIB = os.path.join(BUILD, "libgsmesh.so")
 INCLUDE = os.path.join(os.path.dirname(HERE), "include")
 
+# geometric predicates of the triangulation round every product and sum once
+PER_FILE_FLAGS = {"gs_tri.cu": ["-fmad=false"]}
+
 NVCC_FLAGS = ["-gencode", "arch=compute_103a,code=sm_103a", "-O3", "-lineinfo", "-std=c++17",
               "--extended-lambda", "-Xcompiler", "-fPIC", "-I", INCLUDE]
 
@@ -43,7 +46,8 @@ def build(force=False, verbose=False):
 
     def compile_one(src):
         obj = os.path.join(BUILD, os.path.basename(src)[:-3] + ".o")
-        cmd = [nvcc] + NVCC_FLAGS + ["-c", src, "-o", obj]
+        extra = PER_FILE_FLAGS.get(os.path.basename(src), [])
+        cmd = [nvcc] + NVCC_FLAGS + extra + ["-c", src, "-o", obj]
         r = subprocess.run(cmd, capture_output=True, text=True)
         if r.returncode != 0:
             raise RuntimeError("nvcc failed for %s:\n%s" % (src, r.stderr))

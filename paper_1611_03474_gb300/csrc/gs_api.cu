@@ -39,6 +39,16 @@ extern "C" const char *gs_status_string(int s)
     }
 }
 
+extern "C" int64_t gs_struct_size(int which)
+{
+    switch (which) {
+    case 0: return (int64_t)sizeof(gs_stats);
+    case 1: return (int64_t)sizeof(gs_options);
+    case 2: return (int64_t)sizeof(gs_mesh);
+    default: return -1;
+    }
+}
+
 extern "C" void mesh_free(gs_mesh *m)
 {
     if (!m) return;
@@ -227,11 +237,19 @@ static int prepare(const double *atoms, const double *radii, int64_t n, double D
     if (!rc) rc = B.get(&S.fx, (size_t)n);
     if (!rc) rc = B.get(&S.fy, (size_t)n);
     if (!rc) rc = B.get(&S.fz, (size_t)n);
+    if (!rc) rc = B.get(&S.hx, (size_t)n);
+    if (!rc) rc = B.get(&S.lx, (size_t)n);
+    if (!rc) rc = B.get(&S.hy, (size_t)n);
+    if (!rc) rc = B.get(&S.ly, (size_t)n);
+    if (!rc) rc = B.get(&S.hz, (size_t)n);
+    if (!rc) rc = B.get(&S.lz, (size_t)n);
+    if (!rc) rc = B.get(&S.fw, (size_t)n);
     if (rc) return rc;
     rc = gs_gather_atoms(perm, n, d_xyz, d_r, d_R2, d_w, P.origin, P.cell, P.cdim, &S, st);
     if (rc) return rc;
     P.ax = S.x; P.ay = S.y; P.az = S.z; P.ar = S.r; P.aR2 = S.R2; P.aw = S.w;
     P.fx = S.fx; P.fy = S.fy; P.fz = S.fz;
+    P.hx = S.hx; P.lx = S.lx; P.hy = S.hy; P.ly = S.ly; P.hz = S.hz; P.lz = S.lz; P.fw = S.fw;
     P.cell_start = out->cell_start;
     int t2 = T.mark();
     if (stats) {
@@ -246,7 +264,8 @@ static int prepare(const double *atoms, const double *radii, int64_t n, double D
 static int run_level(const GsProblem &P, int level, const uint64_t *d_parents, int64_t n_oct, int mode,
                      DevBufs &B, std::vector<uint64_t *> &acc_parts, std::vector<int64_t> &acc_counts,
                      uint64_t **d_next, int64_t *n_next, unsigned long long *d_counters, unsigned long long *d_pairs,
-                     unsigned *d_status)
+                     unsigned long long *d_rechecked, unsigned long long *d_mism, bool both, unsigned *d_status,
+                     gs_stats *stats)
 {
     cudaStream_t st = B.st;
     const int64_t CH = 1 << 21;  // octets per chunk (8 GB of FP64 tensors)
@@ -257,15 +276,22 @@ static int run_level(const GsProblem &P, int level, const uint64_t *d_parents, i
     for (int64_t o0 = 0; o0 < n_oct; o0 += CH) {
         int64_t m = n_oct - o0 < CH ? n_oct - o0 : CH;
         const uint64_t *par = d_parents + o0;
-        double *dA = nullptr;
         uint8_t *dec = nullptr;
-        int rc = gs_alloc((void **)&dA, sizeof(double) * 64 * 8 * (size_t)m, st);
-        if (!rc) rc = gs_alloc((void **)&dec, (size_t)m * 8, st);
-        if (rc) { gs_free(dA, st); return rc; }
-        (void)mode;
-        rc = gs_accum_f64(P, level, par, nullptr, m, dA, d_pairs, d_status, st);
-        if (!rc) rc = gs_estimate_f64(P, level, dA, m * 8, par, nullptr, dec, nullptr, st);
-        gs_free(dA, st);
+        int rc = gs_alloc((void **)&dec, (size_t)m * 8, st);
+        if (rc) return rc;
+        float tacc = 0.f;
+        if (mode == GS_PREC_MIXED) {
+            rc = gs_level_mixed(P, level, par, m, dec, d_pairs, d_rechecked, d_mism, both, d_status, st,
+                                stats ? &tacc : nullptr, d_mism + 1);
+        } else {
+            double *dA = nullptr;
+            rc = gs_alloc((void **)&dA, sizeof(double) * 64 * 8 * (size_t)m, st);
+            if (rc) { gs_free(dec, st); return rc; }
+            rc = gs_accum_f64(P, level, par, nullptr, m, dA, d_pairs, d_status, st, stats ? &tacc : nullptr);
+            if (!rc) rc = gs_estimate_f64(P, level, dA, m * 8, par, nullptr, dec, nullptr, st);
+            gs_free(dA, st);
+        }
+        if (stats) { stats->ms_accum += tacc; stats->n_accum_launches++; }
         uint64_t *acc = nullptr;
         if (!rc) rc = gs_alloc((void **)&acc, sizeof(uint64_t) * (size_t)m * 8, st);
         uint64_t *nx = nullptr;
@@ -413,13 +439,16 @@ static int mesh_impl(const double *atoms, const double *radii, int64_t n, double
     DevBufs B(st);
     Timer T(st);
     int tstart = T.mark();
+    long long launches0 = gs_launch_count();
     unsigned *d_status = nullptr;
-    unsigned long long *d_cnt = nullptr;  // [0..4] level decisions, [8] pairs, [9] vertex terms, [10..12] triangulation
+    // counters: [0..4] level decisions, [8] pairs, [9] vertex terms, [10..12] triangulation,
+    // [13] rechecked cubes, [14] mismatches, [15..17] recheck reasons, [18] error-ratio bits
+    unsigned long long *d_cnt = nullptr;
     int rc = B.get(&d_status, 1);
-    if (!rc) rc = B.get(&d_cnt, 16);
+    if (!rc) rc = B.get(&d_cnt, 32);
     if (rc) return rc;
     GS_CHECK(cudaMemsetAsync(d_status, 0, sizeof(unsigned), st));
-    GS_CHECK(cudaMemsetAsync(d_cnt, 0, 16 * sizeof(unsigned long long), st));
+    GS_CHECK(cudaMemsetAsync(d_cnt, 0, 32 * sizeof(unsigned long long), st));
     Prepared PR;
     rc = prepare(atoms, radii, n, D, c, o.cutoff_rel, precision, o.min_edge, max_depth, B, d_status, &PR, stats, T);
     if (rc) return rc;
@@ -442,7 +471,7 @@ static int mesh_impl(const double *atoms, const double *radii, int64_t n, double
         std::vector<uint64_t *> parts;
         std::vector<int64_t> cnts;
         rc = run_level(P, l, parents, n_oct, o.precision_mode, B, parts, cnts, &next, &nn, d_cnt, d_cnt + 8,
-                       d_status);
+                       d_cnt + 13, d_cnt + 14, (o.debug_flags & 1) != 0, d_status, stats);
         for (size_t i = 0; i < parts.size(); i++) { B.keep(parts[i]); acc_all.push_back(parts[i]); acc_cnt.push_back(cnts[i]); }
         if (parents) B.release(parents);
         if (rc) { gs_free(next, st); return rc; }
@@ -497,7 +526,9 @@ static int mesh_impl(const double *atoms, const double *radii, int64_t n, double
     if (o.precision_mode == GS_PREC_FP64) {
         rc = gs_field_f64(P, vkeys, nullptr, nv, phi, nullptr, d_cnt + 9, st);
     } else {
-        rc = gs_field_f64(P, vkeys, nullptr, nv, phi, nullptr, d_cnt + 9, st);
+        int64_t nre = 0;
+        rc = gs_field_mixed(P, vkeys, nv, phi, d_cnt + 9, &nre, st);
+        stats->recheck_vertices = nre;
     }
     if (rc) return rc;
     int tf1 = T.mark();
@@ -513,10 +544,21 @@ static int mesh_impl(const double *atoms, const double *radii, int64_t n, double
     if (rc) return rc;
     int tend = T.mark();
     GS_CHECK(cudaStreamSynchronize(st));
-    unsigned long long h[16];
+    unsigned long long h[32];
     GS_CHECK(cudaMemcpy(h, d_cnt, sizeof(h), cudaMemcpyDeviceToHost));
+    stats->recheck_bounds = (int64_t)h[15];
+    stats->recheck_precision = (int64_t)h[16];
+    stats->recheck_zero = (int64_t)h[17];
+    {
+        unsigned bits = (unsigned)(h[18] & 0xffffffffull);
+        float r;
+        memcpy(&r, &bits, sizeof(r));
+        stats->mixed_err_ratio = r;
+    }
     stats->pair_terms = (int64_t)h[8];
     stats->vertex_terms = (int64_t)h[9];
+    stats->recheck_cubes = (int64_t)h[13];
+    out->mismatches = (int64_t)h[14];
     stats->conformity_splits = splits;
     stats->n_cubes_final = nc;
     stats->n_lattice_vertices = nv;
@@ -527,6 +569,7 @@ static int mesh_impl(const double *atoms, const double *radii, int64_t n, double
     stats->ms_field = T.ms(tc1, tf1);
     stats->ms_download = T.ms(tw1, tend);
     stats->ms_total = T.ms(tstart, tend);
+    stats->n_kernel_launches = gs_launch_count() - launches0;
     return GS_OK;
 }
 
@@ -603,7 +646,7 @@ extern "C" int gs_triangulate_grid(int64_t nx, int64_t ny, int64_t nz, const dou
         if (!rc) {
             cudaMemsetAsync(d_status, 0, sizeof(unsigned), st);
             cudaMemsetAsync(d_cnt, 0, 16 * sizeof(unsigned long long), st);
-            k_grid_cubes<<<(unsigned)((nc + 255) / 256), 256, 0, st>>>(nx, ny, nz, cubes);
+            GS_LAUNCH(k_grid_cubes, (unsigned)((nc + 255) / 256), 256, 0, st)(nx, ny, nz, cubes);
         }
         uint64_t *vkeys = nullptr;
         int32_t *cvid = nullptr;
@@ -612,7 +655,7 @@ extern "C" int gs_triangulate_grid(int64_t nx, int64_t ny, int64_t nz, const dou
         B.keep(vkeys); B.keep(cvid);
         double *phi = nullptr;
         if (!rc) rc = B.get(&phi, (size_t)nv + 1);
-        if (!rc) k_fill_grid_phi<<<(unsigned)((nv + 255) / 256), 256, 0, st>>>(vkeys, nv, d_vals, nx, ny, phi);
+        if (!rc) GS_LAUNCH(k_fill_grid_phi, (unsigned)((nv + 255) / 256), 256, 0, st)(vkeys, nv, d_vals, nx, ny, phi);
         MeshDev M;
         M.cubes = cubes; M.nc = nc;
         if (!rc) rc = surface_from_values(P, cubes, nc, cvid, phi, B, d_status, d_cnt + 10, M, stats, T);

@@ -113,7 +113,9 @@ __global__ void k_gather_atoms(const int32_t *__restrict__ perm, int64_t n, cons
                                int cdx, int cdy, int cdz, double *__restrict__ ax,
                                double *__restrict__ ay, double *__restrict__ az, double *__restrict__ ar,
                                double *__restrict__ aR2, double *__restrict__ aw, float *__restrict__ fx,
-                               float *__restrict__ fy, float *__restrict__ fz)
+                               float *__restrict__ fy, float *__restrict__ fz, float *__restrict__ hx,
+                               float *__restrict__ lx, float *__restrict__ hy, float *__restrict__ ly,
+                               float *__restrict__ hz, float *__restrict__ lz, float *__restrict__ fw)
 {
     int64_t p = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (p >= n) return;
@@ -127,6 +129,12 @@ __global__ void k_gather_atoms(const int32_t *__restrict__ perm, int64_t n, cons
     fx[p] = (float)(x - (ox + cx * cell));
     fy[p] = (float)(y - (oy + cy * cell));
     fz[p] = (float)(z - (oz + cz * cell));
+    // centre relative to the origin as hi + lo floats (about 48 bits)
+    double rx = x - ox, ry = y - oy, rz = z - oz;
+    hx[p] = (float)rx; lx[p] = (float)(rx - (double)hx[p]);
+    hy[p] = (float)ry; ly[p] = (float)(ry - (double)hy[p]);
+    hz[p] = (float)rz; lz[p] = (float)(rz - (double)hz[p]);
+    fw[p] = (float)w[i];
 }
 
 // ---------------------------------------------------------------- host side
@@ -137,11 +145,11 @@ int gs_prep_atoms(const double *d_xyz, const double *d_r, int64_t n, double D, d
     unsigned long long *red = nullptr;
     int rc = gs_alloc((void **)&red, 7 * sizeof(unsigned long long), st);
     if (rc) return rc;
-    k_red_init<<<1, 1, 0, st>>>(red);
+    GS_LAUNCH(k_red_init, 1, 1, 0, st)(red);
     int blocks = (int)((n + 255) / 256);
     if (blocks > 152 * 8) blocks = 152 * 8;
     if (blocks < 1) blocks = 1;
-    k_prep<<<blocks, 256, 0, st>>>(d_xyz, d_r, n, D, KD, d_R2, d_w, red, d_status);
+    GS_LAUNCH(k_prep, blocks, 256, 0, st)(d_xyz, d_r, n, D, KD, d_R2, d_w, red, d_status);
     unsigned long long h[7];
     cudaError_t e = cudaMemcpyAsync(h, red, sizeof(h), cudaMemcpyDeviceToHost, st);
     if (e == cudaSuccess) e = cudaStreamSynchronize(st);
@@ -166,12 +174,12 @@ int gs_build_cells(const double *d_xyz, int64_t n, const double origin[3], doubl
     cudaMemsetAsync(fill, 0, sizeof(int32_t) * (size_t)ncell, st);
     double inv = 1.0 / cell;
     unsigned nb = (unsigned)((n + 255) / 256);
-    k_cell_count<<<nb, 256, 0, st>>>(d_xyz, n, origin[0], origin[1], origin[2], inv, cdim[0], cdim[1], cdim[2], coa,
+    GS_LAUNCH(k_cell_count, nb, 256, 0, st)(d_xyz, n, origin[0], origin[1], origin[2], inv, cdim[0], cdim[1], cdim[2], coa,
                                      counts);
     rc = gs_scan_i64(counts, ncell + 1, nullptr, st);
     if (!rc) {
-        k_cell_scatter<<<nb, 256, 0, st>>>(coa, n, counts, fill, d_perm);
-        k_cell_sort<<<(unsigned)((ncell + 1 + 255) / 256), 256, 0, st>>>(counts, ncell, n, d_perm, d_cell_start);
+        GS_LAUNCH(k_cell_scatter, nb, 256, 0, st)(coa, n, counts, fill, d_perm);
+        GS_LAUNCH(k_cell_sort, (unsigned)((ncell + 1 + 255) / 256), 256, 0, st)(counts, ncell, n, d_perm, d_cell_start);
     }
     gs_free(counts, st); gs_free(coa, st); gs_free(fill, st);
     if (rc) return rc;
@@ -183,10 +191,12 @@ int gs_gather_atoms(const int32_t *d_perm, int64_t n, const double *d_xyz, const
                     const double *d_w, const double origin[3], double cell, const int cdim[3], GsAtomsSoA *soa,
                     cudaStream_t st)
 {
-    k_gather_atoms<<<(unsigned)((n + 255) / 256), 256, 0, st>>>(d_perm, n, d_xyz, d_r, d_R2, d_w, origin[0],
+    GS_LAUNCH(k_gather_atoms, (unsigned)((n + 255) / 256), 256, 0, st)(d_perm, n, d_xyz, d_r, d_R2, d_w, origin[0],
                                                                  origin[1], origin[2], cell, cdim[0], cdim[1],
                                                                  cdim[2], soa->x, soa->y, soa->z,
-                                                                 soa->r, soa->R2, soa->w, soa->fx, soa->fy, soa->fz);
+                                                                 soa->r, soa->R2, soa->w, soa->fx, soa->fy, soa->fz,
+                                                                 soa->hx, soa->lx, soa->hy, soa->ly, soa->hz, soa->lz,
+                                                                 soa->fw);
     GS_CHECK(cudaGetLastError());
     return GS_OK;
 }

@@ -5,6 +5,7 @@
 struct GsAtomsSoA {
     double *x, *y, *z, *r, *R2, *w;
     float *fx, *fy, *fz;
+    float *hx, *lx, *hy, *ly, *hz, *lz, *fw;
 };
 
 // gs_bin.cu
@@ -22,25 +23,32 @@ int gs_quadrature_init(void);
 // or the implicit root blocks when parents == NULL); vmask (nullable) selects
 // children; A_out [n_oct*8][64]
 int gs_accum_f64(const GsProblem &P, int level, const uint64_t *d_parents, const uint8_t *d_vmask, int64_t n_oct,
-                 double *d_A, unsigned long long *d_pairs, unsigned *d_status, cudaStream_t st);
+                 double *d_A, unsigned long long *d_pairs, unsigned *d_status, cudaStream_t st, float *ms = nullptr);
 int gs_estimate_f64(const GsProblem &P, int level, const double *d_A, int64_t n_cubes, const uint64_t *d_parents,
                     const uint8_t *d_vmask, uint8_t *d_dec, double *d_bounds, cudaStream_t st);
 // mixed precision: FP32 accumulate (Kahan) + error bound, FP32 estimate with margins
 int gs_accum_f32(const GsProblem &P, int level, const uint64_t *d_parents, const uint8_t *d_vmask, int64_t n_oct,
-                 float *d_A, float *d_err, unsigned long long *d_pairs, unsigned *d_status, cudaStream_t st);
+                 float *d_A, float *d_err, unsigned long long *d_pairs, unsigned *d_status, cudaStream_t st,
+                 float *ms = nullptr);
 int gs_estimate_f32(const GsProblem &P, int level, const float *d_A, const float *d_err, int64_t n_cubes,
                     const uint64_t *d_parents, const uint8_t *d_vmask, uint8_t *d_dec, uint8_t *d_flag,
-                    cudaStream_t st);
+                    cudaStream_t st, unsigned long long *d_why = nullptr);
 
 // gs_field.cu
 int gs_field_f64(const GsProblem &P, const uint64_t *d_vkeys, const double *d_points, int64_t n, double *d_phi,
                  double *d_grad, unsigned long long *d_terms, cudaStream_t st);
+int gs_field_mixed(const GsProblem &P, const uint64_t *d_vkeys, int64_t n, double *d_phi, unsigned long long *d_terms,
+                   int64_t *n_rechecked, cudaStream_t st);
 int gs_field_f32(const GsProblem &P, const uint64_t *d_vkeys, const double *d_points, int64_t n, double *d_phi,
                  double *d_grad, float *d_err, unsigned long long *d_terms, cudaStream_t st);
 int gs_level_compact(const GsProblem &P, int level, const uint64_t *d_parents, const uint8_t *d_vmask, int64_t n_oct,
                      const uint8_t *d_dec, uint64_t **d_next, int64_t *n_next, uint64_t *d_acc_base,
                      int64_t acc_cap, int64_t *n_acc, unsigned long long *d_counters, cudaStream_t st);
 
+int gs_level_mixed(const GsProblem &P, int level, const uint64_t *d_parents, int64_t n_oct, uint8_t *d_dec,
+                   unsigned long long *d_pairs, unsigned long long *d_rechecked, unsigned long long *d_mism,
+                   bool both, unsigned *d_status, cudaStream_t st, float *ms = nullptr,
+                   unsigned long long *d_why = nullptr);
 int gs_root_blocks(const GsProblem &P, uint64_t **d_keys, int64_t *n, cudaStream_t st);
 
 // gs_mesh.cu

@@ -55,6 +55,8 @@ struct GsProblem {
     // atoms in cell order (SoA)
     const double *ax, *ay, *az, *ar, *aR2, *aw;   // centre, radius, cutoff^2, exp(D r^2)
     const float *fx, *fy, *fz;                   // centres relative to their cell's lower corner (FP32)
+    const float *hx, *lx, *hy, *ly, *hz, *lz;    // centre - origin as a two-float sum hi + lo
+    const float *fw;                             // exp(D r^2) in FP32
     const int32_t *cell_start;                   // [ncell + 1]
 };
 
@@ -134,6 +136,10 @@ __device__ __forceinline__ int64_t gs_hash_find(const GsHash &H, uint64_t key)
     } while (0)
 
 int gs_fail_cuda(cudaError_t e, const char *what, const char *file, int line);
+// process-wide count of this library's kernel launches (for the stats)
+void gs_count_launch(void);
+long long gs_launch_count(void);
+#define GS_LAUNCH(kernel, grid, block, smem, stream) gs_count_launch(), kernel<<<(grid), (block), (smem), (stream)>>>
 int gs_fail(int code, const char *fmt, ...);
 
 // device-wide exclusive scan of n int64 values (in place); total -> *d_total (device)

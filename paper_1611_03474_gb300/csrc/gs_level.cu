@@ -22,14 +22,14 @@
 
 // ---------------------------------------------------------------- quadrature
 // Gauss-Legendre nodes t_k and folded weights W_kj = (2j+1)/2 * w_k * L_j(t_k),
-// so that alpha_j = sum_k W_kj f(t_k).  Variants with 8, 12, 16 and 24 nodes.
-#define GQ_VARIANTS 4
+// so that alpha_j = sum_k W_kj f(t_k).  Variants with 8, 12, 16, 24 and 6 nodes.
+#define GQ_VARIANTS 5
 #define GQ_MAX 24
 __constant__ double c_gq_t[GQ_VARIANTS][GQ_MAX];
 __constant__ double c_gq_W[GQ_VARIANTS][GQ_MAX][4];
 __constant__ float c_gq_tf[GQ_VARIANTS][GQ_MAX];
 __constant__ float c_gq_Wf[GQ_VARIANTS][GQ_MAX][4];
-static const int kGqN[GQ_VARIANTS] = {8, 12, 16, 24};
+static const int kGqN[GQ_VARIANTS] = {8, 12, 16, 24, 6};
 
 // nodes of P_n as eigen-free Newton iteration in long double, started from
 // Tricomi's asymptotic estimate
@@ -94,7 +94,8 @@ int gs_quadrature_init(void)
 static int gq_variant(double D, double hh, bool fp32)
 {
     double a = sqrt(D) * hh;
-    if (fp32) return a <= 0.75 ? 0 : (a <= 1.5 ? 1 : 2);
+    // FP32: quadrature error below ~1e-7 of the factor's maximum
+    if (fp32) return a <= 0.5 ? 4 : (a <= 1.0 ? 0 : (a <= 1.5 ? 1 : 2));
     if (a <= 0.25) return 0;
     if (a <= 0.75) return 1;
     if (a <= 1.0) return 2;
@@ -218,6 +219,7 @@ __global__ void __launch_bounds__(32 * ACC_WARPS) k_accum_f64(GsProblem P, int l
     const int lane = threadIdx.x & 31, wl = threadIdx.x >> 5;
     const int c = lane >> 2, j = lane & 3;
     const int cx = c & 1, cy = (c >> 1) & 1, cz = c >> 2;
+    unsigned long long my_pairs = 0;
     for (int64_t o = (int64_t)blockIdx.x * ACC_WARPS + wl; o < n_oct; o += (int64_t)gridDim.x * ACC_WARPS) {
         Octet q = octet_of(P, level, parents, vmask, o);
         int64_t base[3] = {2 * q.I, 2 * q.J, 2 * q.K};
@@ -274,6 +276,7 @@ __global__ void __launch_bounds__(32 * ACC_WARPS) k_accum_f64(GsProblem P, int l
                         }
                         m &= vm;
                     }
+                    my_pairs += __popc(m);
                     unsigned bal = __ballot_sync(0xffffffffu, m != 0);
                     int pos = qn + __popc(bal & ((1u << lane) - 1u));
                     if (m) { s_qi[wl][pos] = i; s_qm[wl][pos] = (uint8_t)m; }
@@ -297,39 +300,10 @@ __global__ void __launch_bounds__(32 * ACC_WARPS) k_accum_f64(GsProblem P, int l
 #pragma unroll
         for (int t = 0; t < 16; t++) dst[t] = acc[t];
     }
-}
-
-// pair counting pass is folded into the estimate kernel through A's support;
-// a separate exact count uses the same membership test
-__global__ void k_count_pairs(GsProblem P, int level, const uint64_t *parents, const uint8_t *vmask, int64_t n_oct,
-                              double pad, unsigned long long *pairs)
-{
-    const int lane = threadIdx.x & 31, wl = threadIdx.x >> 5;
-    unsigned long long cnt = 0;
-    for (int64_t o = (int64_t)blockIdx.x * ACC_WARPS + wl; o < n_oct; o += (int64_t)gridDim.x * ACC_WARPS) {
-        Octet q = octet_of(P, level, parents, vmask, o);
-        if (!q.vmask) continue;
-        int64_t base[3] = {2 * q.I, 2 * q.J, 2 * q.K};
-        double e[3][3];
-        for (int a = 0; a < 3; a++)
-            for (int t = 0; t < 3; t++) e[a][t] = gs_lat(P, a, base[a] + t, level);
-        double plo[3] = {e[0][0], e[1][0], e[2][0]}, phi[3] = {e[0][2], e[1][2], e[2][2]};
-        for_cell_rows(P, plo, phi, pad, [&](int b, int en) {
-            for (int i = b + lane; i < en; i += 32) {
-                double x = P.ax[i], y = P.ay[i], z = P.az[i], R2 = P.aR2[i];
-                for (int cc = 0; cc < 8; cc++) {
-                    if (!((q.vmask >> cc) & 1)) continue;
-                    double dx = gs_axis_gap(e[0][cc & 1], e[0][(cc & 1) + 1], x);
-                    double dy = gs_axis_gap(e[1][(cc >> 1) & 1], e[1][((cc >> 1) & 1) + 1], y);
-                    double dz = gs_axis_gap(e[2][cc >> 2], e[2][(cc >> 2) + 1], z);
-                    double d2 = __dadd_rn(__dadd_rn(__dmul_rn(dx, dx), __dmul_rn(dy, dy)), __dmul_rn(dz, dz));
-                    cnt += d2 <= R2;
-                }
-            }
-        });
+    if (pairs) {
+        for (int off = 16; off > 0; off >>= 1) my_pairs += __shfl_xor_sync(0xffffffffu, my_pairs, off);
+        if (lane == 0 && my_pairs) atomicAdd(pairs, my_pairs);
     }
-    for (int off = 16; off > 0; off >>= 1) cnt += __shfl_xor_sync(0xffffffffu, cnt, off);
-    if (lane == 0 && cnt) atomicAdd(pairs, cnt);
 }
 
 static int grid_for(int64_t n_items, int per_block)
@@ -341,17 +315,23 @@ static int grid_for(int64_t n_items, int per_block)
 }
 
 int gs_accum_f64(const GsProblem &P, int level, const uint64_t *d_parents, const uint8_t *d_vmask, int64_t n_oct,
-                 double *d_A, unsigned long long *d_pairs, unsigned *d_status, cudaStream_t st)
+                 double *d_A, unsigned long long *d_pairs, unsigned *d_status, cudaStream_t st, float *ms)
 {
     if (n_oct <= 0) return GS_OK;
     double h = gs_h(P, level);
     int gv = gq_variant(P.D, 0.5 * h, false);
-    double pad = P.pad;
-    k_accum_f64<<<grid_for(n_oct, ACC_WARPS), 32 * ACC_WARPS, 0, st>>>(P, level, d_parents, d_vmask, n_oct, gv,
-                                                                       kGqN[gv], pad, d_A, d_pairs, d_status);
-    if (d_pairs)
-        k_count_pairs<<<grid_for(n_oct, ACC_WARPS), 32 * ACC_WARPS, 0, st>>>(P, level, d_parents, d_vmask, n_oct, pad,
-                                                                             d_pairs);
+    cudaEvent_t e0 = nullptr, e1 = nullptr;
+    if (ms) { cudaEventCreate(&e0); cudaEventCreate(&e1); cudaEventRecord(e0, st); }
+    GS_LAUNCH(k_accum_f64, grid_for(n_oct, ACC_WARPS), 32 * ACC_WARPS, 0, st)(P, level, d_parents, d_vmask, n_oct, gv,
+                                                                             kGqN[gv], P.pad, d_A, d_pairs, d_status);
+    if (ms) {
+        cudaEventRecord(e1, st);
+        cudaEventSynchronize(e1);
+        float t = 0;
+        cudaEventElapsedTime(&t, e0, e1);
+        *ms += t;
+        cudaEventDestroy(e0); cudaEventDestroy(e1);
+    }
     GS_CHECK(cudaGetLastError());
     return GS_OK;
 }
@@ -496,7 +476,33 @@ __device__ __forceinline__ int rank99(const T (&s)[4], T &margin)
 // bounds: out = (L, U, sum|R|, sum|high|, rank, inner ranks); rmargin = the
 // smallest distance of a rank rule from its 99% threshold
 template <typename T>
+__device__ __forceinline__ T gap_sens(const T (&s)[4], int kept)
+{
+    // s[0] / the smallest separation between consecutive values up to the
+    // first dropped one: how far singular vectors can turn per unit change
+    T g = T(1e30);
+    int last = kept < 4 ? kept : 3;
+    for (int i = 0; i < last; i++) {
+        T d = s[i] - s[i + 1];
+        g = d < g ? d : g;
+    }
+    if (last == 0) return T(0);
+    T r = s[0] / (g > T(0) ? g : T(1e-30));
+    return r < T(1e6) ? r : T(1e6);
+}
+
+template <typename T>
+__device__ void estimate_bounds_sens(const T *A, T *out, T &rmargin, T &sens);
+
+template <typename T>
 __device__ void estimate_bounds(const T *A, T *out, T &rmargin)
+{
+    T sens;
+    estimate_bounds_sens<T>(A, out, rmargin, sens);
+}
+
+template <typename T>
+__device__ void estimate_bounds_sens(const T *A, T *out, T &rmargin, T &sens)
 {
     T X[4][16];
     T high = 0, tot = 0;
@@ -511,12 +517,14 @@ __device__ void estimate_bounds(const T *A, T *out, T &rmargin)
         }
     out[3] = high;
     rmargin = T(1e30);
+    sens = T(0);
     if (tot == T(0)) { out[0] = out[1] = out[2] = 0; out[4] = 0; out[5] = 0; return; }
     T s[4], u[4][4];
     jacobi4<T, 16>(X, s, u);
     T rm;
     int jr = rank99(s, rm);
     rmargin = rm;
+    sens = gap_sens<T>(s, jr);
     T At[64];
 #pragma unroll
     for (int t = 0; t < 64; t++) At[t] = 0;
@@ -532,6 +540,8 @@ __device__ void estimate_bounds(const T *A, T *out, T &rmargin)
         T rmi;
         int ji = rank99(d, rmi);
         rmargin = rmi < rmargin ? rmi : rmargin;
+        T si = gap_sens<T>(d, ji);
+        sens = si > sens ? si : sens;
         inner += ji;
         T Myz = 0, myz = 0;
         for (int k = 0; k < ji; k++) {
@@ -609,7 +619,7 @@ int gs_estimate_f64(const GsProblem &P, int level, const double *d_A, int64_t n_
                     const uint8_t *d_vmask, uint8_t *d_dec, double *d_bounds, cudaStream_t st)
 {
     if (n_cubes <= 0) return GS_OK;
-    k_estimate_f64<<<(unsigned)((n_cubes + 127) / 128), 128, 0, st>>>(P, level, d_A, n_cubes, d_parents, d_vmask,
+    GS_LAUNCH(k_estimate_f64, (unsigned)((n_cubes + 127) / 128), 128, 0, st)(P, level, d_A, n_cubes, d_parents, d_vmask,
                                                                      d_dec, d_bounds);
     GS_CHECK(cudaGetLastError());
     return GS_OK;
@@ -663,7 +673,7 @@ int gs_level_compact(const GsProblem &P, int level, const uint64_t *d_parents, c
     if (!rc) rc = gs_alloc((void **)&tot, sizeof(int64_t), st);
     if (rc) { gs_free(packed, st); return rc; }
     cudaMemsetAsync(packed + n, 0, sizeof(int64_t), st);
-    k_level_count<<<(unsigned)((n + 255) / 256), 256, 0, st>>>(d_dec, n, packed, d_counters);
+    GS_LAUNCH(k_level_count, (unsigned)((n + 255) / 256), 256, 0, st)(d_dec, n, packed, d_counters);
     rc = gs_scan_i64(packed, n + 1, tot, st);
     int64_t h = 0;
     if (!rc) {
@@ -674,7 +684,7 @@ int gs_level_compact(const GsProblem &P, int level, const uint64_t *d_parents, c
     int64_t ns = h & 0xffffffffll, na = h >> 32;
     if (!rc && na > acc_cap) rc = gs_fail(GS_ERR_CAPACITY, "accepted-cube buffer too small");
     if (!rc && ns > 0) rc = gs_alloc((void **)d_next, sizeof(uint64_t) * (size_t)ns, st);
-    if (!rc) k_level_emit<<<(unsigned)((n + 255) / 256), 256, 0, st>>>(P, level, d_parents, d_vmask, d_dec, n, packed,
+    if (!rc) GS_LAUNCH(k_level_emit, (unsigned)((n + 255) / 256), 256, 0, st)(P, level, d_parents, d_vmask, d_dec, n, packed,
                                                                       *d_next, d_acc_base);
     gs_free(packed, st); gs_free(tot, st);
     if (rc) return rc;
@@ -698,7 +708,405 @@ int gs_root_blocks(const GsProblem &P, uint64_t **d_keys, int64_t *n, cudaStream
     *n = bx * by * bz;
     int rc = gs_alloc((void **)d_keys, sizeof(uint64_t) * (size_t)*n, st);
     if (rc) return rc;
-    k_root_blocks<<<(unsigned)((*n + 255) / 256), 256, 0, st>>>(bx, by, *n, *d_keys);
+    GS_LAUNCH(k_root_blocks, (unsigned)((*n + 255) / 256), 256, 0, st)(bx, by, *n, *d_keys);
+    GS_CHECK(cudaGetLastError());
+    return GS_OK;
+}
+
+// ================================================================ mixed precision
+// FP32 accumulation.  Atom centres and lattice coordinates are taken relative
+// to the origin as two-float sums, so differences x - e keep ~1e-7 A; the
+// 1-D factors use exp2f; each lane sums 8 atoms plainly and folds the batch
+// into a Kahan-compensated accumulator.  Per cube it also sums
+// w * Fx * Fy * Fz (F = the largest value of the atom's 1-D factor on the
+// cube's interval), an upper bound of every term's size from which the
+// error band of the FP32 tensor is derived.
+#define ACF_W 24
+#define ACF_F 25
+#define ACF_STRIDE 33
+
+__global__ void __launch_bounds__(32 * ACC_WARPS) k_accum_f32(GsProblem P, int level, const uint64_t *parents,
+                                                               const uint8_t *vmask, int64_t n_oct, int gv, int nq,
+                                                               double pad, float *__restrict__ A_out,
+                                                               float *__restrict__ E_out, unsigned long long *pairs)
+{
+    unsigned long long my_pairs = 0;
+    __shared__ float s_cf[ACC_WARPS][32][ACF_STRIDE];
+    __shared__ int s_qi[ACC_WARPS][ACC_Q];
+    __shared__ uint8_t s_qm[ACC_WARPS][ACC_Q];
+    const int lane = threadIdx.x & 31, wl = threadIdx.x >> 5;
+    const int c = lane >> 2, j = lane & 3;
+    const int cx = c & 1, cy = (c >> 1) & 1, cz = c >> 2;
+    const float nDl2e = (float)(-P.D * 1.4426950408889634);
+    for (int64_t o = (int64_t)blockIdx.x * ACC_WARPS + wl; o < n_oct; o += (int64_t)gridDim.x * ACC_WARPS) {
+        Octet q = octet_of(P, level, parents, vmask, o);
+        int64_t base[3] = {2 * q.I, 2 * q.J, 2 * q.K};
+        double e[3][3];
+        float eh[3][3], el[3][3];
+        for (int a = 0; a < 3; a++)
+            for (int t = 0; t < 3; t++) {
+                e[a][t] = gs_lat(P, a, base[a] + t, level);
+                double rel = e[a][t] - P.origin[a];
+                eh[a][t] = (float)rel;
+                el[a][t] = (float)(rel - (double)eh[a][t]);
+            }
+        const float hh = (float)(0.5 * gs_h(P, level));
+        double plo[3] = {e[0][0], e[1][0], e[2][0]}, phi[3] = {e[0][2], e[1][2], e[2][2]};
+        float acc[16], comp[16], part[16];
+#pragma unroll
+        for (int t = 0; t < 16; t++) { acc[t] = 0.f; comp[t] = 0.f; part[t] = 0.f; }
+        float eb = 0.f;
+        int nb = 0;
+        int qn = 0;
+        const uint8_t vm = q.vmask;
+
+        auto fold = [&]() {
+#pragma unroll
+            for (int t = 0; t < 16; t++) {
+                float y = part[t] - comp[t];
+                float s = acc[t] + y;
+                comp[t] = (s - acc[t]) - y;
+                acc[t] = s;
+                part[t] = 0.f;
+            }
+            nb = 0;
+        };
+
+        auto process = [&](int nproc) {
+            if (lane < nproc) {
+                int i = s_qi[wl][lane];
+                const float ah[3] = {P.hx[i], P.hy[i], P.hz[i]}, al[3] = {P.lx[i], P.ly[i], P.lz[i]};
+                float *cf = s_cf[wl][lane];
+                for (int a = 0; a < 3; a++) {
+                    float d[3], f[3];
+                    for (int t = 0; t < 3; t++) {
+                        d[t] = (eh[a][t] - ah[a]) + (el[a][t] - al[a]);   // e_t - x
+                        f[t] = exp2f(nDl2e * d[t] * d[t]);
+                    }
+                    for (int hI = 0; hI < 2; hI++) {
+                        float m = d[hI] + hh;   // interval centre - x
+                        float a0 = 0.f, a1 = 0.f, a2 = 0.f, a3 = 0.f;
+                        for (int k = 0; k < nq; k++) {
+                            float dk = fmaf(hh, c_gq_tf[gv][k], m);
+                            float fk = exp2f(nDl2e * dk * dk);
+                            a0 = fmaf(c_gq_Wf[gv][k][0], fk, a0);
+                            a1 = fmaf(c_gq_Wf[gv][k][1], fk, a1);
+                            a2 = fmaf(c_gq_Wf[gv][k][2], fk, a2);
+                            a3 = fmaf(c_gq_Wf[gv][k][3], fk, a3);
+                        }
+                        float fa = f[hI], fb = f[hI + 1];
+                        float eR = fb - (a0 + a1 + a2 + a3), eL = fa - (a0 - a1 + a2 - a3);
+                        cf[8 * a + 4 * hI + 0] = a0;
+                        cf[8 * a + 4 * hI + 1] = a1;
+                        cf[8 * a + 4 * hI + 2] = a2 + 0.5f * (eR + eL);
+                        cf[8 * a + 4 * hI + 3] = a3 + 0.5f * (eR - eL);
+                        bool inside = d[hI] <= 0.f && d[hI + 1] >= 0.f;
+                        cf[ACF_F + 2 * a + hI] = inside ? 1.f : fmaxf(fa, fb);
+                    }
+                }
+                cf[ACF_W] = P.fw[i];
+            }
+            __syncwarp();
+            for (int t = 0; t < nproc; t++) {
+                if ((s_qm[wl][t] >> c) & 1) {
+                    const float *cf = s_cf[wl][t];
+                    float wa = cf[ACF_W] * cf[4 * cx + j];
+#pragma unroll
+                    for (int k = 0; k < 4; k++) {
+                        float wb = wa * cf[8 + 4 * cy + k];
+#pragma unroll
+                        for (int l = 0; l < 4; l++) part[4 * k + l] = fmaf(wb, cf[16 + 4 * cz + l], part[4 * k + l]);
+                    }
+                    eb = fmaf(cf[ACF_W] * cf[ACF_F + cx], cf[ACF_F + 2 + cy] * cf[ACF_F + 4 + cz], eb);
+                    if (++nb == 8) fold();
+                }
+            }
+            __syncwarp();
+        };
+
+        if (vm) {
+            for_cell_rows(P, plo, phi, pad, [&](int b, int en) {
+                for (int s = b; s < en; s += 32) {
+                    int i = s + lane;
+                    unsigned m = 0;
+                    if (i < en) {
+                        const float ah[3] = {P.hx[i], P.hy[i], P.hz[i]}, al[3] = {P.lx[i], P.ly[i], P.lz[i]};
+                        float g[3][2];
+                        for (int a = 0; a < 3; a++)
+                            for (int hI = 0; hI < 2; hI++) {
+                                float dlo = (eh[a][hI] - ah[a]) + (el[a][hI] - al[a]);
+                                float dhi = (ah[a] - eh[a][hI + 1]) + (al[a] - el[a][hI + 1]);
+                                g[a][hI] = fmaxf(0.f, fmaxf(dlo, dhi));
+                            }
+                        float R2 = (float)P.aR2[i];
+                        float tol = 1e-5f * R2 + 1e-5f;
+                        for (int cc = 0; cc < 8; cc++) {
+                            if (!((vm >> cc) & 1)) continue;
+                            float d2 = g[0][cc & 1] * g[0][cc & 1] + g[1][(cc >> 1) & 1] * g[1][(cc >> 1) & 1] +
+                                       g[2][cc >> 2] * g[2][cc >> 2];
+                            bool in;
+                            if (d2 < R2 - tol) in = true;
+                            else if (d2 > R2 + tol) in = false;
+                            else {
+                                // near the cutoff sphere: the exact FP64 membership test
+                                double x = P.ax[i], y = P.ay[i], z = P.az[i];
+                                double dx = gs_axis_gap(e[0][cc & 1], e[0][(cc & 1) + 1], x);
+                                double dy = gs_axis_gap(e[1][(cc >> 1) & 1], e[1][((cc >> 1) & 1) + 1], y);
+                                double dz = gs_axis_gap(e[2][cc >> 2], e[2][(cc >> 2) + 1], z);
+                                double dd = __dadd_rn(__dadd_rn(__dmul_rn(dx, dx), __dmul_rn(dy, dy)), __dmul_rn(dz, dz));
+                                in = dd <= P.aR2[i];
+                            }
+                            if (in) m |= 1u << cc;
+                        }
+                    }
+                    my_pairs += __popc(m);
+                    unsigned bal = __ballot_sync(0xffffffffu, m != 0);
+                    int pos = qn + __popc(bal & ((1u << lane) - 1u));
+                    if (m) { s_qi[wl][pos] = i; s_qm[wl][pos] = (uint8_t)m; }
+                    qn += __popc(bal);
+                    __syncwarp();
+                    if (qn >= 32) {
+                        process(32);
+                        int rest = qn - 32;
+                        int mi = 0; uint8_t mm = 0;
+                        if (lane < rest) { mi = s_qi[wl][32 + lane]; mm = s_qm[wl][32 + lane]; }
+                        __syncwarp();
+                        if (lane < rest) { s_qi[wl][lane] = mi; s_qm[wl][lane] = mm; }
+                        __syncwarp();
+                        qn = rest;
+                    }
+                }
+            });
+            if (qn > 0) process(qn);
+            fold();
+        }
+        float *dst = A_out + ((size_t)o * 8 + c) * 64 + 16 * j;
+#pragma unroll
+        for (int t = 0; t < 16; t++) dst[t] = acc[t] - comp[t];
+        if (j == 0) E_out[(size_t)o * 8 + c] = eb;
+    }
+    if (pairs) {
+        for (int off = 16; off > 0; off >>= 1) my_pairs += __shfl_xor_sync(0xffffffffu, my_pairs, off);
+        if (lane == 0 && my_pairs) atomicAdd(pairs, my_pairs);
+    }
+}
+
+int gs_accum_f32(const GsProblem &P, int level, const uint64_t *d_parents, const uint8_t *d_vmask, int64_t n_oct,
+                 float *d_A, float *d_err, unsigned long long *d_pairs, unsigned *d_status, cudaStream_t st, float *ms)
+{
+    if (n_oct <= 0) return GS_OK;
+    double h = gs_h(P, level);
+    int gv = gq_variant(P.D, 0.5 * h, true);
+    cudaEvent_t e0 = nullptr, e1 = nullptr;
+    if (ms) { cudaEventCreate(&e0); cudaEventCreate(&e1); cudaEventRecord(e0, st); }
+    GS_LAUNCH(k_accum_f32, grid_for(n_oct, ACC_WARPS), 32 * ACC_WARPS, 0, st)(P, level, d_parents, d_vmask, n_oct, gv,
+                                                                             kGqN[gv], P.pad, d_A, d_err, d_pairs);
+    if (ms) {
+        cudaEventRecord(e1, st);
+        cudaEventSynchronize(e1);
+        float t = 0;
+        cudaEventElapsedTime(&t, e0, e1);
+        *ms += t;
+        cudaEventDestroy(e0); cudaEventDestroy(e1);
+    }
+    (void)d_status;
+    GS_CHECK(cudaGetLastError());
+    return GS_OK;
+}
+
+// FP32 estimate.  A decision is final when every margin it rests on exceeds
+// the band the FP32 error of A can move it by:
+//   entry error      dA <= MIXED_KAPPA * E   (E = sum w Fx Fy Fz)
+//   singular values  |dsigma| <= ||dA||_F <= 8 dA
+//   bounds L, U      |dL|, |dU| <= 64 dA (2 + 4 s) + FP32 rounding, s = sigma_1 over
+//                    the smallest gap between kept and neighbouring singular values
+//   precision sum    |d sum|high|| <= 64 dA + rounding
+// Otherwise the cube is flagged and its octet is re-evaluated in FP64.
+#define MIXED_KAPPA 3e-6f
+
+__global__ void __launch_bounds__(128) k_estimate_f32(GsProblem P, int level, const float *__restrict__ A,
+                                                      const float *__restrict__ E, int64_t n, const uint64_t *parents,
+                                                      const uint8_t *vmask, uint8_t *__restrict__ dec,
+                                                      uint8_t *__restrict__ flag, unsigned long long *why_cnt)
+{
+    int64_t q = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (q >= n) return;
+    Octet oc = octet_of(P, level, parents, vmask, q >> 3);
+    if (!((oc.vmask >> (q & 7)) & 1)) { dec[q] = DEC_INVALID; flag[q] = 0; return; }
+    float a[64];
+    float tot = 0.f;
+#pragma unroll
+    for (int t = 0; t < 64; t++) { a[t] = A[q * 64 + t]; tot += fabsf(a[t]); }
+    float b[6], rm;
+    float sens;
+    estimate_bounds_sens<float>(a, b, rm, sens);
+    const float c = (float)P.c, prec = (float)P.precision;
+    int d = decide<float>(b, c, prec, level, P.max_depth);
+    float dA = MIXED_KAPPA * E[q] + 1e-7f * tot;
+    bool f = false;
+    int why = 0;
+    if (tot > 0.f) {
+        float bLU = 64.f * dA * (2.f + 4.f * fminf(sens, 1e4f)) + 2e-5f * tot;
+        // a rank rule within its band may flip: one component of size at
+        // most ~1% of sum(sigma) <= tot moves between the main part and R
+        if (rm <= 32.f * dA + 1e-5f * tot) bLU += 0.16f * tot;
+        float mc = fminf(fabsf(c - b[0]), fabsf(b[1] - c));
+        bool keep = b[0] <= c && c <= b[1];
+        if (mc <= bLU) { f = true; why = 1; }
+        else if (keep && level < P.max_depth && fabsf(prec - b[3]) <= 64.f * dA + 1e-6f * b[3] + 1e-7f * tot) {
+            f = true;
+            why = 2;
+        }
+    } else if (E[q] > 0.f) {
+        f = true;  // an all-zero FP32 tensor with contributing atoms: let FP64 decide
+        why = 3;
+    }
+    if (why && why_cnt) atomicAdd(&why_cnt[why - 1], 1ull);
+    dec[q] = (uint8_t)d;
+    flag[q] = f ? 1 : 0;
+}
+
+int gs_estimate_f32(const GsProblem &P, int level, const float *d_A, const float *d_err, int64_t n_cubes,
+                    const uint64_t *d_parents, const uint8_t *d_vmask, uint8_t *d_dec, uint8_t *d_flag,
+                    cudaStream_t st, unsigned long long *d_why)
+{
+    if (n_cubes <= 0) return GS_OK;
+    GS_LAUNCH(k_estimate_f32, (unsigned)((n_cubes + 127) / 128), 128, 0, st)(P, level, d_A, d_err, n_cubes, d_parents,
+                                                                            d_vmask, d_dec, d_flag, d_why);
+    GS_CHECK(cudaGetLastError());
+    return GS_OK;
+}
+
+__global__ void k_add_u64(unsigned long long *dst, const unsigned long long *v) { *dst += *v; }
+
+// octets with a flagged child -> list of octet indices
+__global__ void k_octet_flags(const uint8_t *flag, int64_t n_oct, int64_t *cnt)
+{
+    int64_t o = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (o >= n_oct) return;
+    uint64_t w = *(const uint64_t *)(flag + 8 * o);
+    cnt[o] = w != 0;
+}
+__global__ void k_octet_gather(const int64_t *off, int64_t n_oct, const uint64_t *parents, uint64_t *sub_par,
+                               int64_t *sub_idx)
+{
+    int64_t o = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (o >= n_oct || off[o + 1] == off[o]) return;
+    sub_par[off[o]] = parents[o];
+    sub_idx[off[o]] = o;
+}
+__global__ void k_octet_scatter(const uint8_t *sub_dec, const int64_t *sub_idx, int64_t n_sub, uint8_t *dec,
+                                unsigned long long *mism)
+{
+    int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (t >= n_sub * 8) return;
+    int64_t q = sub_idx[t >> 3] * 8 + (t & 7);
+    dec[q] = sub_dec[t];
+    (void)mism;
+}
+// debug: largest |A32 - A64| / E over a chunk, as float bits (non-negative)
+__global__ void k_err_ratio(const float *A32, const float *E, const double *A64, int64_t n, unsigned *maxbits)
+{
+    int64_t q = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (q >= n) return;
+    double mx = 0;
+    for (int t = 0; t < 64; t++) mx = fmax(mx, fabs((double)A32[q * 64 + t] - A64[q * 64 + t]));
+    float e = E[q];
+    if (e > 0.f) {
+        float r = (float)(mx / e);
+        atomicMax(maxbits, __float_as_uint(r));
+    }
+}
+
+__global__ void k_count_mismatch(const uint8_t *a, const uint8_t *b, int64_t n, unsigned long long *mism)
+{
+    int64_t q = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (q >= n) return;
+    // cube sets depend on discard / keep and split / accept; accepted vs forced is bookkeeping
+    unsigned x = a[q], y = b[q];
+    if (x == DEC_FORCED) x = DEC_ACCEPT;
+    if (y == DEC_FORCED) y = DEC_ACCEPT;
+    if (x != y) atomicAdd(mism, 1ull);
+}
+
+// one chunk of a level in mixed precision; dec receives the final decisions
+// d_why: [0..2] flag reasons (bounds band, precision band, zero tensor), [3] low 32 bits = float bits of
+// the largest |A32 - A64| / E seen in debug mode
+int gs_level_mixed(const GsProblem &P, int level, const uint64_t *d_parents, int64_t n_oct, uint8_t *d_dec,
+                   unsigned long long *d_pairs, unsigned long long *d_rechecked, unsigned long long *d_mism,
+                   bool both, unsigned *d_status, cudaStream_t st, float *ms, unsigned long long *d_why)
+{
+    float *A = nullptr, *E = nullptr;
+    uint8_t *flag = nullptr;
+    int rc = gs_alloc((void **)&A, sizeof(float) * 64 * 8 * (size_t)n_oct, st);
+    if (!rc) rc = gs_alloc((void **)&E, sizeof(float) * 8 * (size_t)n_oct, st);
+    if (!rc) rc = gs_alloc((void **)&flag, 8 * (size_t)n_oct, st);
+    if (!rc) rc = gs_accum_f32(P, level, d_parents, nullptr, n_oct, A, E, d_pairs, d_status, st, ms);
+    if (!rc) rc = gs_estimate_f32(P, level, A, E, n_oct * 8, d_parents, nullptr, d_dec, flag, st, d_why);
+    // flagged octets -> FP64
+    int64_t *cnt = nullptr, *tot = nullptr;
+    if (!rc) rc = gs_alloc((void **)&cnt, sizeof(int64_t) * (size_t)(n_oct + 1), st);
+    if (!rc) rc = gs_alloc((void **)&tot, sizeof(int64_t), st);
+    if (!rc) {
+        cudaMemsetAsync(cnt + n_oct, 0, sizeof(int64_t), st);
+        GS_LAUNCH(k_octet_flags, (unsigned)((n_oct + 255) / 256), 256, 0, st)(flag, n_oct, cnt);
+        rc = gs_scan_i64(cnt, n_oct + 1, tot, st);
+    }
+    int64_t nsub = 0;
+    if (!rc) {
+        cudaError_t e = cudaMemcpyAsync(&nsub, tot, sizeof(int64_t), cudaMemcpyDeviceToHost, st);
+        if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+        if (e != cudaSuccess) rc = gs_fail_cuda(e, "recheck count", __FILE__, __LINE__);
+    }
+    if (!rc && nsub > 0) {
+        uint64_t *sp = nullptr;
+        int64_t *si = nullptr;
+        double *A64 = nullptr;
+        uint8_t *sd = nullptr;
+        rc = gs_alloc((void **)&sp, sizeof(uint64_t) * (size_t)nsub, st);
+        if (!rc) rc = gs_alloc((void **)&si, sizeof(int64_t) * (size_t)nsub, st);
+        if (!rc) rc = gs_alloc((void **)&A64, sizeof(double) * 64 * 8 * (size_t)nsub, st);
+        if (!rc) rc = gs_alloc((void **)&sd, 8 * (size_t)nsub, st);
+        if (!rc) {
+            GS_LAUNCH(k_octet_gather, (unsigned)((n_oct + 255) / 256), 256, 0, st)(cnt, n_oct, d_parents, sp, si);
+            rc = gs_accum_f64(P, level, sp, nullptr, nsub, A64, nullptr, d_status, st, nullptr);
+        }
+        if (!rc) rc = gs_estimate_f64(P, level, A64, nsub * 8, sp, nullptr, sd, nullptr, st);
+        if (!rc) GS_LAUNCH(k_octet_scatter, (unsigned)((nsub * 8 + 255) / 256), 256, 0, st)(sd, si, nsub, d_dec, nullptr);
+        gs_free(sp, st); gs_free(si, st); gs_free(A64, st); gs_free(sd, st);
+        if (d_rechecked && !rc) {
+            unsigned long long v = (unsigned long long)nsub * 8ull;
+            unsigned long long *tmp = nullptr;
+            // add on the device so the counter stays stream-ordered
+            rc = gs_alloc((void **)&tmp, sizeof(v), st);
+            if (!rc) {
+                cudaMemcpyAsync(tmp, &v, sizeof(v), cudaMemcpyHostToDevice, st);
+                GS_LAUNCH(k_add_u64, 1, 1, 0, st)(d_rechecked, tmp);
+                gs_free(tmp, st);
+            }
+        }
+    }
+    gs_free(cnt, st); gs_free(tot, st);
+    if (!rc && both) {
+        // debug: FP64 on every octet; count final decisions that disagree and
+        // record the largest |A32 - A64| / E
+        double *A64 = nullptr;
+        uint8_t *d64 = nullptr;
+        rc = gs_alloc((void **)&A64, sizeof(double) * 64 * 8 * (size_t)n_oct, st);
+        if (!rc) rc = gs_alloc((void **)&d64, 8 * (size_t)n_oct, st);
+        if (!rc) rc = gs_accum_f64(P, level, d_parents, nullptr, n_oct, A64, nullptr, d_status, st, nullptr);
+        if (!rc) rc = gs_estimate_f64(P, level, A64, n_oct * 8, d_parents, nullptr, d64, nullptr, st);
+        if (!rc) {
+            GS_LAUNCH(k_count_mismatch, (unsigned)((n_oct * 8 + 255) / 256), 256, 0, st)(d_dec, d64, n_oct * 8, d_mism);
+            GS_LAUNCH(k_err_ratio, (unsigned)((n_oct * 8 + 255) / 256), 256, 0, st)(A, E, A64, n_oct * 8,
+                                                                                   (unsigned *)(d_why + 3));
+        }
+        gs_free(A64, st); gs_free(d64, st);
+    }
+    gs_free(A, st);
+    gs_free(E, st);
+    gs_free(flag, st);
+    if (rc) return rc;
     GS_CHECK(cudaGetLastError());
     return GS_OK;
 }

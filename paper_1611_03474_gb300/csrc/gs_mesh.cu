@@ -28,7 +28,7 @@ int gs_hash_make(GsHash *H, int64_t n, cudaStream_t st)
     int rc = gs_alloc((void **)&H->keys, sizeof(uint64_t) * cap, st);
     if (!rc) rc = gs_alloc((void **)&H->vals, sizeof(uint64_t) * cap, st);
     if (rc) { gs_free(H->keys, st); gs_free(H->vals, st); H->keys = H->vals = nullptr; return rc; }
-    k_hash_clear<<<1024, 256, 0, st>>>(H->keys, H->vals, cap, ~0ull);
+    GS_LAUNCH(k_hash_clear, 1024, 256, 0, st)(H->keys, H->vals, cap, ~0ull);
     GS_CHECK(cudaGetLastError());
     return GS_OK;
 }
@@ -107,14 +107,14 @@ int gs_conformity(uint64_t **d_cubes, int64_t *n, int max_depth, int64_t *splits
         int rc = gs_hash_make(&H, m, st);
         if (rc) return rc;
         unsigned nb = (unsigned)((m + 255) / 256);
-        k_hash_index<<<nb, 256, 0, st>>>(H, *d_cubes, m, d_status);
+        GS_LAUNCH(k_hash_index, nb, 256, 0, st)(H, *d_cubes, m, d_status);
         int64_t *cnt = nullptr, *tot = nullptr;
         rc = gs_alloc((void **)&cnt, sizeof(int64_t) * (size_t)(m + 1), st);
         if (!rc) rc = gs_alloc((void **)&tot, sizeof(int64_t), st);
         if (rc) { gs_hash_free(&H, st); gs_free(cnt, st); return rc; }
         cudaMemsetAsync(cnt + m, 0, sizeof(int64_t), st);
-        k_fill_one<<<nb, 256, 0, st>>>(cnt, m);
-        k_conform_mark<<<nb, 256, 0, st>>>(H, *d_cubes, m, cnt);
+        GS_LAUNCH(k_fill_one, nb, 256, 0, st)(cnt, m);
+        GS_LAUNCH(k_conform_mark, nb, 256, 0, st)(H, *d_cubes, m, cnt);
         gs_hash_free(&H, st);
         rc = gs_scan_i64(cnt, m + 1, tot, st);
         int64_t total = 0;
@@ -127,7 +127,7 @@ int gs_conformity(uint64_t **d_cubes, int64_t *n, int max_depth, int64_t *splits
         uint64_t *out = nullptr;
         rc = gs_alloc((void **)&out, sizeof(uint64_t) * (size_t)total, st);
         if (rc) { gs_free(cnt, st); gs_free(tot, st); return rc; }
-        k_conform_emit<<<nb, 256, 0, st>>>(*d_cubes, m, cnt, out);
+        GS_LAUNCH(k_conform_emit, nb, 256, 0, st)(*d_cubes, m, cnt, out);
         gs_free(cnt, st); gs_free(tot, st);
         gs_free(*d_cubes, st);
         *d_cubes = out;
@@ -201,9 +201,9 @@ int gs_lattice_vertices(const uint64_t *d_cubes, int64_t n, int max_depth, uint6
     if (!rc) rc = gs_alloc((void **)&slot_id, sizeof(uint64_t) * (size_t)(H.mask + 1), st);
     unsigned nb = (unsigned)((m + 255) / 256);
     if (!rc) {
-        k_vert_claim<<<nb, 256, 0, st>>>(H, d_cubes, n, max_depth, d_status);
+        GS_LAUNCH(k_vert_claim, nb, 256, 0, st)(H, d_cubes, n, max_depth, d_status);
         cudaMemsetAsync(flag + m, 0, sizeof(int64_t), st);
-        k_vert_owner<<<nb, 256, 0, st>>>(H, d_cubes, n, max_depth, flag);
+        GS_LAUNCH(k_vert_owner, nb, 256, 0, st)(H, d_cubes, n, max_depth, flag);
         rc = gs_scan_i64(flag, m + 1, tot, st);
     }
     int64_t total = 0;
@@ -215,8 +215,8 @@ int gs_lattice_vertices(const uint64_t *d_cubes, int64_t n, int max_depth, uint6
     if (!rc) rc = gs_alloc((void **)d_vkeys, sizeof(uint64_t) * (size_t)(total + 1), st);
     if (!rc) rc = gs_alloc((void **)d_cvid, sizeof(int32_t) * (size_t)m, st);
     if (!rc) {
-        k_vert_write<<<nb, 256, 0, st>>>(H, d_cubes, n, max_depth, flag, *d_vkeys, slot_id);
-        k_vert_cvid<<<nb, 256, 0, st>>>(H, d_cubes, n, max_depth, slot_id, *d_cvid, d_status);
+        GS_LAUNCH(k_vert_write, nb, 256, 0, st)(H, d_cubes, n, max_depth, flag, *d_vkeys, slot_id);
+        GS_LAUNCH(k_vert_cvid, nb, 256, 0, st)(H, d_cubes, n, max_depth, slot_id, *d_cvid, d_status);
     }
     gs_free(flag, st); gs_free(tot, st); gs_free(slot_id, st);
     gs_hash_free(&H, st);
@@ -251,9 +251,9 @@ int gs_neighbours(const uint64_t *d_cubes, int64_t n, int32_t **d_nbr, unsigned 
     GsHash H;
     int rc = gs_hash_make(&H, n, st);
     if (rc) return rc;
-    k_hash_index<<<(unsigned)((n + 255) / 256), 256, 0, st>>>(H, d_cubes, n, d_status);
+    GS_LAUNCH(k_hash_index, (unsigned)((n + 255) / 256), 256, 0, st)(H, d_cubes, n, d_status);
     rc = gs_alloc((void **)d_nbr, sizeof(int32_t) * 6 * (size_t)n, st);
-    if (!rc) k_neighbours<<<(unsigned)((6 * n + 255) / 256), 256, 0, st>>>(H, d_cubes, n, *d_nbr);
+    if (!rc) GS_LAUNCH(k_neighbours, (unsigned)((6 * n + 255) / 256), 256, 0, st)(H, d_cubes, n, *d_nbr);
     gs_hash_free(&H, st);
     if (rc) return rc;
     GS_CHECK(cudaGetLastError());
@@ -314,9 +314,9 @@ int gs_weld(const uint64_t *d_pk, const double *d_pxyz, int64_t npt, const uint6
     if (!rc) rc = gs_alloc((void **)&slot_id, sizeof(uint64_t) * (size_t)(H.mask + 1), st);
     unsigned nb = (unsigned)((npt + 255) / 256);
     if (!rc) {
-        k_weld_claim<<<nb, 256, 0, st>>>(H, d_pk, npt, d_status);
+        GS_LAUNCH(k_weld_claim, nb, 256, 0, st)(H, d_pk, npt, d_status);
         cudaMemsetAsync(flag + npt, 0, sizeof(int64_t), st);
-        k_weld_owner<<<nb, 256, 0, st>>>(H, d_pk, npt, flag);
+        GS_LAUNCH(k_weld_owner, nb, 256, 0, st)(H, d_pk, npt, flag);
         rc = gs_scan_i64(flag, npt + 1, tot, st);
     }
     int64_t total = 0;
@@ -329,9 +329,9 @@ int gs_weld(const uint64_t *d_pk, const double *d_pxyz, int64_t npt, const uint6
     if (!rc) rc = gs_alloc((void **)d_vxyz, sizeof(double) * 3 * (size_t)(total + 1), st);
     if (!rc) rc = gs_alloc((void **)d_tri, sizeof(int32_t) * 3 * (size_t)(ntri + 1), st);
     if (!rc) {
-        k_weld_write<<<nb, 256, 0, st>>>(H, d_pk, d_pxyz, npt, flag, *d_vkeys, *d_vxyz, slot_id);
+        GS_LAUNCH(k_weld_write, nb, 256, 0, st)(H, d_pk, d_pxyz, npt, flag, *d_vkeys, *d_vxyz, slot_id);
         if (ntri > 0)
-            k_weld_tris<<<(unsigned)((3 * ntri + 255) / 256), 256, 0, st>>>(H, slot_id, d_tk, ntri, *d_tri, d_status);
+            GS_LAUNCH(k_weld_tris, (unsigned)((3 * ntri + 255) / 256), 256, 0, st)(H, slot_id, d_tk, ntri, *d_tri, d_status);
     }
     gs_free(flag, st); gs_free(tot, st); gs_free(slot_id, st);
     gs_hash_free(&H, st);

@@ -27,6 +27,11 @@ int gs_fail_cuda(cudaError_t e, const char *what, const char *file, int line)
 
 extern "C" const char *gs_last_error(void) { return g_last_error; }
 
+#include <atomic>
+static std::atomic<long long> g_launches{0};
+void gs_count_launch(void) { g_launches.fetch_add(1, std::memory_order_relaxed); }
+long long gs_launch_count(void) { return g_launches.load(std::memory_order_relaxed); }
+
 int gs_alloc(void **p, size_t bytes, cudaStream_t st)
 {
     *p = nullptr;
@@ -130,18 +135,18 @@ int gs_scan_i64(int64_t *d_vals, int64_t n, int64_t *d_total, cudaStream_t st)
     GS_CHECK(cudaMemcpyAsync(last, d_vals + (n - 1), sizeof(int64_t), cudaMemcpyDeviceToDevice, st));
     int64_t tiles = (n + SCAN_TILE - 1) / SCAN_TILE;
     if (tiles == 1) {
-        k_scan_tile_apply<<<1, SCAN_THREADS, 0, st>>>(d_vals, n, nullptr);
+        GS_LAUNCH(k_scan_tile_apply, 1, SCAN_THREADS, 0, st)(d_vals, n, nullptr);
     } else {
         int64_t *sums = nullptr;
         rc = gs_alloc((void **)&sums, sizeof(int64_t) * (size_t)tiles, st);
         if (rc) { gs_free(last, st); return rc; }
-        k_scan_tile_sums<<<(unsigned)tiles, SCAN_THREADS, 0, st>>>(d_vals, n, sums);
+        GS_LAUNCH(k_scan_tile_sums, (unsigned)tiles, SCAN_THREADS, 0, st)(d_vals, n, sums);
         rc = gs_scan_i64(sums, tiles, nullptr, st);
         if (rc) { gs_free(sums, st); gs_free(last, st); return rc; }
-        k_scan_tile_apply<<<(unsigned)tiles, SCAN_THREADS, 0, st>>>(d_vals, n, sums);
+        GS_LAUNCH(k_scan_tile_apply, (unsigned)tiles, SCAN_THREADS, 0, st)(d_vals, n, sums);
         gs_free(sums, st);
     }
-    if (d_total) k_scan_total<<<1, 1, 0, st>>>(d_vals, last, n, d_total);
+    if (d_total) GS_LAUNCH(k_scan_total, 1, 1, 0, st)(d_vals, last, n, d_total);
     gs_free(last, st);
     GS_CHECK(cudaGetLastError());
     return GS_OK;

@@ -20,7 +20,10 @@
 //
 // Thread per cube, two passes over the same code: count (triangles,
 // points) and emit into scan-allocated buffers.  Bounded loops only; an
-// inconsistency sets a counter and skips the cube.
+// inconsistency sets a counter and skips the cube.  This file is compiled
+// without FMA contraction (-fmad=false): geometric predicates (orientation,
+// in-square and branch tests) then round each product and sum once, so
+// exactly degenerate configurations are recognised as such.
 #include "gs_host.cuh"
 
 #define TP_MAX 48
@@ -59,13 +62,14 @@ __device__ __noinline__ int fold_solve(const double *g, int a, double c, double 
     for (int k = 0; k < 4; k++) { nlo += lo[k] >= c; nup += up[k] >= c; }
     if (nlo == 0 || nlo == 4 || nup == 0 || nup == 4) return 0;
     // A - c = p0 + p1 u + p2 v + p3 uv ; B = q0 + q1 u + q2 v + q3 uv
-    double p0 = lo[0] - c, p1 = lo[1] - lo[0], p2 = lo[2] - lo[0], p3 = (lo[3] - lo[1]) - (lo[2] - lo[0]);
+    // monomial coefficients, summed left to right (the face's corner order)
+    double p0 = lo[0] - c, p1 = lo[1] - lo[0], p2 = lo[2] - lo[0], p3 = lo[3] - lo[1] - lo[2] + lo[0];
     double d0 = up[0] - lo[0], d1 = up[1] - lo[1], d2 = up[2] - lo[2], d3 = up[3] - lo[3];
-    double q0 = d0, q1 = d1 - d0, q2 = d2 - d0, q3 = (d3 - d1) - (d2 - d0);
+    double q0 = d0, q1 = d1 - d0, q2 = d2 - d0, q3 = d3 - d1 - d2 + d0;
     if (q0 == 0.0 && q1 == 0.0 && q2 == 0.0 && q3 == 0.0) return 0;
     // eliminate v: (p0 + p1 u)(q2 + q3 u) - (p2 + p3 u)(q0 + q1 u) = 0
     double A2 = p1 * q3 - p3 * q1;
-    double A1 = (p0 * q3 + p1 * q2) - (p2 * q1 + p3 * q0);
+    double A1 = p0 * q3 + p1 * q2 - p2 * q1 - p3 * q0;
     double A0 = p0 * q2 - p2 * q0;
     double us[2];
     int nu = 0;
@@ -541,7 +545,7 @@ int gs_triangulate(const TriCtx &X, uint64_t **d_tri_keys, int64_t *ntri_total, 
     unsigned nb = (unsigned)((n + 127) / 128);
     cudaMemsetAsync(ntri + n, 0, sizeof(int64_t), st);
     cudaMemsetAsync(npt + n, 0, sizeof(int64_t), st);
-    k_tri_count<<<nb, 128, 0, st>>>(X, ntri, npt, d_counters + 0, d_counters + 2);
+    GS_LAUNCH(k_tri_count, nb, 128, 0, st)(X, ntri, npt, d_counters + 0, d_counters + 2);
     rc = gs_scan_i64(ntri, n + 1, tot, st);
     if (!rc) rc = gs_scan_i64(npt, n + 1, tot + 1, st);
     int64_t h[2] = {0, 0};
@@ -555,7 +559,7 @@ int gs_triangulate(const TriCtx &X, uint64_t **d_tri_keys, int64_t *ntri_total, 
         if (!rc) rc = gs_alloc((void **)d_pt_keys, sizeof(uint64_t) * (size_t)(h[1] + 1), st);
         if (!rc) rc = gs_alloc((void **)d_pt_xyz, sizeof(double) * 3 * (size_t)(h[1] + 1), st);
     }
-    if (!rc) k_tri_emit<<<nb, 128, 0, st>>>(X, ntri, npt, *d_tri_keys, *d_pt_keys, *d_pt_xyz, d_counters + 1);
+    if (!rc) GS_LAUNCH(k_tri_emit, nb, 128, 0, st)(X, ntri, npt, *d_tri_keys, *d_pt_keys, *d_pt_xyz, d_counters + 1);
     gs_free(ntri, st); gs_free(npt, st); gs_free(tot, st);
     if (rc) return rc;
     GS_CHECK(cudaGetLastError());

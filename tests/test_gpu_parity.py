@@ -141,3 +141,35 @@ def test_grid_triangulation_parity(seed):
     assert np.array_equal(canonical_triangles(m.vertex_keys, m.triangles),
                           canonical_triangles(ref["vkeys"], ref["triangles"]))
     check_closed_manifold(m.vertices, m.triangles)
+
+
+def test_mixed_decisions_match_fp64_everywhere(chain100):
+    """Debug mode: the mixed form also runs FP64 on every cube; no final
+    decision may differ (cube sets are exact by construction)."""
+    cfg = chain100
+    m = gs.mesh_gaussian_surface(cfg["xyz"], cfg["r"], cfg["D"], cfg["c"], cfg["precision"], cfg["max_depth"],
+                                 min_edge=cfg["min_edge"], precision_mode=gs.GS_PREC_MIXED, debug_flags=1)
+    st = m.stats
+    print("recheck", st["recheck_cubes"], "of", sum(st["examined"]), "reasons", st["recheck_bounds"],
+          st["recheck_precision"], st["recheck_zero"], "max |A32-A64|/E", st["mixed_err_ratio"])
+    assert m.mismatches == 0
+    # the FP32 error stays well inside the band's kappa (3e-6)
+    assert st["mixed_err_ratio"] < 3e-6
+    assert st["recheck_cubes"] < 0.2 * sum(st["examined"])
+
+
+def test_mixed_mesh_parity_chain100(chain100):
+    cfg = chain100
+    m = gs.mesh_gaussian_surface(cfg["xyz"], cfg["r"], cfg["D"], cfg["c"], cfg["precision"], cfg["max_depth"],
+                                 min_edge=cfg["min_edge"], precision_mode=gs.GS_PREC_MIXED)
+    ref = oracle.mesh(cfg["xyz"], cfg["r"], cfg["D"], cfg["c"], cfg["precision"], cfg["min_edge"], cfg["max_depth"])
+    _assert_mesh_parity(m, ref)
+
+
+def test_field_mixed_close_to_fp64(chain100):
+    rng = np.random.default_rng(4)
+    xyz, r = chain100["xyz"], chain100["r"]
+    pts = xyz[rng.integers(0, len(r), 2000)] + rng.normal(0, 2.0, (2000, 3))
+    p32 = gs.gs_eval_field(xyz, r, 0.5, 1.0, pts, precision_mode=gs.GS_PREC_MIXED)
+    p64 = oracle.field(xyz, r, 0.5, 1.0, pts)
+    assert np.abs(p32 - p64).max() <= 2e-5 * max(1.0, np.abs(p64).max())
