@@ -155,6 +155,32 @@ int gs_bin_atoms(const double *atoms, int64_t n_atoms, double cell_size, const d
                  const int64_t *dims, int32_t *cell_start, int32_t *atom_perm, void *stream);
 
 /*
+ * gs_bin_atoms_static -- the same cell list as gs_bin_atoms, for callers that
+ * cannot let the library allocate memory: programs that give all device
+ * memory to their own allocator at start-up (a framework's caching pool, a
+ * fixed-budget service) or cannot afford the device-wide synchronisation a
+ * cudaMalloc or cudaFree may cause mid-run.  The paper has no counterpart;
+ * this is a deployment variant of the binning step.
+ *   atoms [n_atoms][3], cell_start [dims0*dims1*dims2 + 1] and atom_perm
+ *   [n_atoms] must be device memory on the current device; origin [3] and
+ *   dims [3] are host arrays.  Same results as gs_bin_atoms.
+ *   Limits: n_atoms <= GS_STATIC_MAX_ATOMS, cells <= GS_STATIC_MAX_CELLS;
+ *   larger requests, host pointers or NULLs return GS_ERR_ARG.
+ *   No cudaMalloc, cudaFree or allocating library call is made: the
+ *   temporaries live in one fixed device array (about 12.6 MB, reserved on
+ *   every GPU that loads the library until the process exits).  Every call
+ *   shares that array; calls whose work overlaps on the GPU race and give
+ *   wrong results.  The first call on a device looks up the array's address
+ *   (once per device); make that first call before any stream capture.
+ *   Work runs on `stream` (NULL: the legacy default stream) and the call
+ *   returns after it has completed.
+ */
+#define GS_STATIC_MAX_ATOMS (1 << 20)
+#define GS_STATIC_MAX_CELLS (1 << 20)
+int gs_bin_atoms_static(const double *atoms, int64_t n_atoms, double cell_size, const double *origin,
+                        const int64_t *dims, int32_t *cell_start, int32_t *atom_perm, void *stream);
+
+/*
  * gs_eval_field -- phi and grad phi at points (eq Gaussian1 with the
  * truncation above).  points [n_points][3], phi [n_points], grad
  * [n_points][3] (nullable).  precision_mode as in gs_options.

@@ -91,6 +91,8 @@ def load():
     L.gs_cube_decisions.restype = i32
     L.gs_triangulate_grid.argtypes = [i64, i64, i64, p, d, ctypes.POINTER(Options), ctypes.POINTER(MeshC)]
     L.gs_triangulate_grid.restype = i32
+    L.gs_bin_atoms_static.argtypes = [p, i64, d, p, p, p, p, p]
+    L.gs_bin_atoms_static.restype = i32
     L.gs_struct_size.argtypes = [i32]
     L.gs_struct_size.restype = i64
     for which, cls in ((0, Stats), (1, Options), (2, MeshC)):
@@ -256,3 +258,14 @@ def gs_bin_atoms(atoms, cell_size, origin, dims, stream=None):
     _check(L.gs_bin_atoms(_ptr(atoms), atoms.shape[0], cell_size, _ptr(origin), _ptr(dims), _ptr(cs), _ptr(pm),
                           _stream_ptr(stream)))
     return cs, pm
+
+
+def gs_bin_atoms_static(atoms, cell_size, origin, dims, cell_start, atom_perm, stream=None):
+    """Allocation-free cell list into caller-provided device buffers (torch
+    CUDA tensors: atoms float64 [n,3], cell_start int32 [ncell+1], atom_perm
+    int32 [n]); see include/gsmesh.h for the limits and the sharing rules."""
+    L = load()
+    origin = np.ascontiguousarray(origin, dtype=np.float64)
+    dims = np.ascontiguousarray(dims, dtype=np.int64)
+    _check(L.gs_bin_atoms_static(_ptr(atoms), int(atoms.shape[0]), cell_size, _ptr(origin), _ptr(dims),
+                                 _ptr(cell_start), _ptr(atom_perm), _stream_ptr(stream)))
