@@ -83,6 +83,7 @@ typedef struct {
     int64_t n_kernel_launches; /* this library's kernel launches during the call */
     int64_t recheck_bounds, recheck_precision, recheck_zero; /* mixed mode: why cubes were re-evaluated */
     double mixed_err_ratio;    /* debug bit 0: largest |A_fp32 - A_fp64| / E observed */
+    double mixed_band_ratio;   /* debug bit 0: largest |dL|,|dU| / ((dA + 1e-7 sum|A|)(1 + s)) observed */
 } gs_stats;
 
 typedef struct {

@@ -949,17 +949,42 @@ static int triangulate_cube(const omesh_ctx *M, uint64_t ckey, vtri *tris, vvert
     int fend[3][2][2];    /* own fold ends: fend[a][r][side] */
     int nfr[3];
     for (int a = 0; a < 3; a++) {
-        int ua, va;
-        other_axes(a, &ua, &va);
         double ru[2], rv[2];
         nfr[a] = fold_roots(g, a, c, ru, rv);
+        for (int r = 0; r < nfr[a]; r++) { fr[a][r][0] = ru[r]; fr[a][r][1] = rv[r]; }
+    }
+    /* Critical points (eq critical): in the slice through an a-fold line
+     * normal to a third axis, the level set of the bilinear slice function
+     * is a pair of crossing lines, so fold lines of two axes meet whenever
+     * their roots share the coordinate of the remaining axis.  That shared
+     * coordinate is one number; the later fold takes the earlier fold's
+     * value, so every segment along a fold line is exactly axis-parallel. */
+    int xing[12][4], nx = 0;
+    for (int a = 0; a < 3; a++)
+        for (int b = a + 1; b < 3; b++) {
+            int cc = 3 - a - b;
+            int ua, va, ub, vb;
+            other_axes(a, &ua, &va);
+            other_axes(b, &ub, &vb);
+            for (int i = 0; i < nfr[a]; i++)
+                for (int j = 0; j < nfr[b]; j++) {
+                    double ca = fr[a][i][cc == ua ? 0 : 1];
+                    double cb = fr[b][j][cc == ub ? 0 : 1];
+                    if (fabs(ca - cb) > 1e-9) continue;
+                    fr[b][j][cc == ub ? 0 : 1] = ca;
+                    xing[nx][0] = a; xing[nx][1] = i; xing[nx][2] = b; xing[nx][3] = j;
+                    nx++;
+                }
+        }
+    for (int a = 0; a < 3; a++) {
+        int ua, va;
+        other_axes(a, &ua, &va);
         for (int r = 0; r < nfr[a]; r++) {
-            fr[a][r][0] = ru[r]; fr[a][r][1] = rv[r];
             for (int sd = 0; sd < 2; sd++) {
                 int id = new_point(pts, &np, 1);
                 if (id < 0) return OR_ERR_CAP;
                 opoint *p = &pts[id];
-                p->p[a] = sd; p->p[ua] = ru[r]; p->p[va] = rv[r];
+                p->p[a] = sd; p->p[ua] = fr[a][r][0]; p->p[va] = fr[a][r][1];
                 int64_t L[3] = {C[0] * s, C[1] * s, C[2] * s};
                 L[a] = (C[a] + sd) * s;
                 /* face at sd=0: this cube lies on its + side; sd=1: - side */
@@ -993,60 +1018,43 @@ static int triangulate_cube(const omesh_ctx *M, uint64_t ckey, vtri *tris, vvert
             }
         }
     }
-
-    /* Critical points (eq critical): in the slice through an a-fold line
-     * normal to a third axis, the level set of the bilinear slice function
-     * is a pair of crossing lines, so fold lines of two axes meet whenever
-     * their roots share the coordinate of the remaining axis. */
     int chain[3][2][4];   /* points along each own fold line, ordered by the fold coordinate */
     int nch[3][2];
     for (int a = 0; a < 3; a++)
         for (int r = 0; r < nfr[a]; r++) { chain[a][r][0] = fend[a][r][0]; nch[a][r] = 1; }
-    for (int a = 0; a < 3; a++)
-        for (int b = a + 1; b < 3; b++) {
-            int cc = 3 - a - b;
-            int ua, va, ub, vb;
-            other_axes(a, &ua, &va);
-            other_axes(b, &ub, &vb);
-            for (int i = 0; i < nfr[a]; i++)
-                for (int j = 0; j < nfr[b]; j++) {
-                    double ca = fr[a][i][cc == ua ? 0 : 1];
-                    double cb = fr[b][j][cc == ub ? 0 : 1];
-                    if (fabs(ca - cb) > 1e-9) continue;
-                    int id = new_point(pts, &np, 3);
-                    if (id < 0) return OR_ERR_CAP;
-                    opoint *p = &pts[id];
-                    p->p[a] = fr[b][j][a == ub ? 0 : 1];
-                    p->p[b] = fr[a][i][b == ua ? 0 : 1];
-                    p->p[cc] = ca;
-                    p->fa = a; p->fb = b;
-                    /* outward normal = -grad g = -(dg/dx_cc) e_cc at the point */
-                    double x = p->p[0], y = p->p[1], z = p->p[2];
-                    double dgc;
-                    {
-                        double w[3] = {x, y, z};
-                        double acc = 0;
-                        for (int v = 0; v < 8; v++) {
-                            double f = 1;
-                            for (int t = 0; t < 3; t++) {
-                                int bit = (v >> t) & 1;
-                                if (t == cc) f *= bit ? 1.0 : -1.0;
-                                else f *= bit ? w[t] : 1.0 - w[t];
-                            }
-                            acc += f * g[v];
-                        }
-                        dgc = acc;
-                    }
-                    int even = (a == 0 && b == 1) || (a == 1 && b == 2) ? 1 : 0; /* (a,b,cc) cyclic */
-                    if (a == 0 && b == 2) even = 0;
-                    p->rh = (even == (dgc < 0));
-                    if (dgc == 0) LOOPERR(1);
-                    p->key = okey((uint64_t)(C[0] * s), (uint64_t)(C[1] * s), (uint64_t)(C[2] * s),
-                                  20u + 4u * (unsigned)(a + b - 1) + 2u * (unsigned)i + (unsigned)j, (unsigned)l);
-                    if (nch[a][i] < 3) chain[a][i][nch[a][i]++] = id;
-                    if (nch[b][j] < 3) chain[b][j][nch[b][j]++] = id;
-                }
+    for (int t = 0; t < nx; t++) {
+        int a = xing[t][0], i = xing[t][1], b = xing[t][2], j = xing[t][3];
+        int cc = 3 - a - b;
+        int ua, va, ub, vb;
+        other_axes(a, &ua, &va);
+        other_axes(b, &ub, &vb);
+        int id = new_point(pts, &np, 3);
+        if (id < 0) return OR_ERR_CAP;
+        opoint *p = &pts[id];
+        p->p[a] = fr[b][j][a == ub ? 0 : 1];
+        p->p[b] = fr[a][i][b == ua ? 0 : 1];
+        p->p[cc] = fr[a][i][cc == ua ? 0 : 1];
+        p->fa = a; p->fb = b;
+        /* outward normal = -grad g = -(dg/dx_cc) e_cc at the point */
+        double w[3] = {p->p[0], p->p[1], p->p[2]};
+        double dgc = 0;
+        for (int v = 0; v < 8; v++) {
+            double f = 1;
+            for (int q = 0; q < 3; q++) {
+                int bit = (v >> q) & 1;
+                if (q == cc) f *= bit ? 1.0 : -1.0;
+                else f *= bit ? w[q] : 1.0 - w[q];
+            }
+            dgc += f * g[v];
         }
+        int even = (a == 0 && b == 1) || (a == 1 && b == 2) ? 1 : 0; /* (a,b,cc) cyclic */
+        p->rh = (even == (dgc < 0));
+        if (dgc == 0) LOOPERR(1);
+        p->key = okey((uint64_t)(C[0] * s), (uint64_t)(C[1] * s), (uint64_t)(C[2] * s),
+                      20u + 4u * (unsigned)(a + b - 1) + 2u * (unsigned)i + (unsigned)j, (unsigned)l);
+        if (nch[a][i] < 3) chain[a][i][nch[a][i]++] = id;
+        if (nch[b][j] < 3) chain[b][j][nch[b][j]++] = id;
+    }
     /* close the chains, sort interior points along the fold axis, link */
     for (int a = 0; a < 3; a++)
         for (int r = 0; r < nfr[a]; r++) {

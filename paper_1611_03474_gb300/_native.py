@@ -34,7 +34,7 @@ class Stats(ctypes.Structure):
                 ("n_accum_launches", ctypes.c_int64), ("atom_octets", ctypes.c_int64),
                 ("n_kernel_launches", ctypes.c_int64), ("recheck_bounds", ctypes.c_int64),
                 ("recheck_precision", ctypes.c_int64), ("recheck_zero", ctypes.c_int64),
-                ("mixed_err_ratio", ctypes.c_double)]
+                ("mixed_err_ratio", ctypes.c_double), ("mixed_band_ratio", ctypes.c_double)]
 
     def as_dict(self, max_depth=20):
         d = {}

@@ -212,6 +212,16 @@ static int prepare(const double *atoms, const double *radii, int64_t n, double D
     P.cell = 0.5 * P.pad;
     if (P.cell <= 0) P.cell = h0;
     P.inv_cell = 1.0 / P.cell;
+    P.cell_f = (float)P.cell;
+    P.inv_cell_f = (float)P.inv_cell;
+    P.pad_f = (float)P.pad;
+    {
+        // min_edge = k 2^e with k < 64 and indices < 2^18: index * spacing fits 24 bits
+        int ex;
+        double mant = frexp(min_edge, &ex);
+        double k64 = ldexp(mant, 6);
+        P.lat_exact_f32 = (k64 == floor(k64)) ? 1 : 0;
+    }
     int64_t ncell = 1;
     for (int a = 0; a < 3; a++) {
         double ext = (double)P.nroot[a] * h0;
@@ -244,12 +254,14 @@ static int prepare(const double *atoms, const double *radii, int64_t n, double D
     if (!rc) rc = B.get(&S.hz, (size_t)n);
     if (!rc) rc = B.get(&S.lz, (size_t)n);
     if (!rc) rc = B.get(&S.fw, (size_t)n);
+    if (!rc) rc = B.get(&S.fR2, (size_t)n);
+    if (!rc) rc = B.get(&S.fr2, (size_t)n);
     if (rc) return rc;
     rc = gs_gather_atoms(perm, n, d_xyz, d_r, d_R2, d_w, P.origin, P.cell, P.cdim, &S, st);
     if (rc) return rc;
     P.ax = S.x; P.ay = S.y; P.az = S.z; P.ar = S.r; P.aR2 = S.R2; P.aw = S.w;
     P.fx = S.fx; P.fy = S.fy; P.fz = S.fz;
-    P.hx = S.hx; P.lx = S.lx; P.hy = S.hy; P.ly = S.ly; P.hz = S.hz; P.lz = S.lz; P.fw = S.fw;
+    P.hx = S.hx; P.lx = S.lx; P.hy = S.hy; P.ly = S.ly; P.hz = S.hz; P.lz = S.lz; P.fw = S.fw; P.fR2 = S.fR2; P.fr2 = S.fr2;
     P.cell_start = out->cell_start;
     int t2 = T.mark();
     if (stats) {
@@ -526,8 +538,28 @@ static int mesh_impl(const double *atoms, const double *radii, int64_t n, double
     if (o.precision_mode == GS_PREC_FP64) {
         rc = gs_field_f64(P, vkeys, nullptr, nv, phi, nullptr, d_cnt + 9, st);
     } else {
-        int64_t nre = 0;
-        rc = gs_field_mixed(P, vkeys, nv, phi, d_cnt + 9, &nre, st);
+        // FP32 values; FP64 where the inside test, a surface point's position
+        // (first-order bound 8e-6 A) or a face or fold decision could depend on
+        // the FP32 error:
+        // first the values near c, then, with those exact, the sensitive corners
+        float *err = nullptr;
+        int64_t *mark = nullptr;
+        rc = B.get(&err, (size_t)nv + 1);
+        if (!rc) rc = B.get(&mark, (size_t)nv + 1);
+        if (!rc) rc = gs_field_f32_marked(P, vkeys, nv, phi, err, mark, d_cnt + 9, st);
+        int64_t nre = 0, nre2 = 0;
+        if (!rc) rc = gs_field_recompute(P, vkeys, nv, mark, phi, err, &nre, st);
+        if (!rc) {
+            GS_CHECK(cudaMemsetAsync(mark, 0, sizeof(int64_t) * (size_t)(nv + 1), st));
+            TriCtx X;
+            memset(&X, 0, sizeof(X));
+            X.cubes = cubes; X.cvid = cvid; X.phi = phi; X.ncubes = nc; X.c = P.c;
+            for (int a3 = 0; a3 < 3; a3++) X.origin[a3] = P.origin[a3];
+            X.min_edge = P.min_edge; X.max_depth = P.max_depth;
+            rc = gs_tri_marks(X, err, 8e-6, mark, st);
+        }
+        if (!rc) rc = gs_field_recompute(P, vkeys, nv, mark, phi, err, &nre2, st);
+        nre += nre2;
         stats->recheck_vertices = nre;
     }
     if (rc) return rc;
@@ -554,6 +586,9 @@ static int mesh_impl(const double *atoms, const double *radii, int64_t n, double
         float r;
         memcpy(&r, &bits, sizeof(r));
         stats->mixed_err_ratio = r;
+        bits = (unsigned)(h[19] & 0xffffffffull);
+        memcpy(&r, &bits, sizeof(r));
+        stats->mixed_band_ratio = r;
     }
     stats->pair_terms = (int64_t)h[8];
     stats->vertex_terms = (int64_t)h[9];

@@ -115,7 +115,8 @@ __global__ void k_gather_atoms(const int32_t *__restrict__ perm, int64_t n, cons
                                double *__restrict__ aR2, double *__restrict__ aw, float *__restrict__ fx,
                                float *__restrict__ fy, float *__restrict__ fz, float *__restrict__ hx,
                                float *__restrict__ lx, float *__restrict__ hy, float *__restrict__ ly,
-                               float *__restrict__ hz, float *__restrict__ lz, float *__restrict__ fw)
+                               float *__restrict__ hz, float *__restrict__ lz, float *__restrict__ fw,
+                               float *__restrict__ fR2, float *__restrict__ fr2)
 {
     int64_t p = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (p >= n) return;
@@ -135,6 +136,8 @@ __global__ void k_gather_atoms(const int32_t *__restrict__ perm, int64_t n, cons
     hy[p] = (float)ry; ly[p] = (float)(ry - (double)hy[p]);
     hz[p] = (float)rz; lz[p] = (float)(rz - (double)hz[p]);
     fw[p] = (float)w[i];
+    fR2[p] = (float)R2[i];
+    fr2[p] = (float)(r[i] * r[i]);
 }
 
 // ---------------------------------------------------------------- host side
@@ -196,7 +199,7 @@ int gs_gather_atoms(const int32_t *d_perm, int64_t n, const double *d_xyz, const
                                                                  cdim[2], soa->x, soa->y, soa->z,
                                                                  soa->r, soa->R2, soa->w, soa->fx, soa->fy, soa->fz,
                                                                  soa->hx, soa->lx, soa->hy, soa->ly, soa->hz, soa->lz,
-                                                                 soa->fw);
+                                                                 soa->fw, soa->fR2, soa->fr2);
     GS_CHECK(cudaGetLastError());
     return GS_OK;
 }

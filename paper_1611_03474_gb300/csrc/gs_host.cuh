@@ -5,7 +5,7 @@
 struct GsAtomsSoA {
     double *x, *y, *z, *r, *R2, *w;
     float *fx, *fy, *fz;
-    float *hx, *lx, *hy, *ly, *hz, *lz, *fw;
+    float *hx, *lx, *hy, *ly, *hz, *lz, *fw, *fR2, *fr2;
 };
 
 // gs_bin.cu
@@ -32,11 +32,17 @@ int gs_accum_f32(const GsProblem &P, int level, const uint64_t *d_parents, const
                  float *ms = nullptr);
 int gs_estimate_f32(const GsProblem &P, int level, const float *d_A, const float *d_err, int64_t n_cubes,
                     const uint64_t *d_parents, const uint8_t *d_vmask, uint8_t *d_dec, uint8_t *d_flag,
-                    cudaStream_t st, unsigned long long *d_why = nullptr);
+                    cudaStream_t st, unsigned long long *d_why = nullptr, float *d_dbg = nullptr);
 
 // gs_field.cu
 int gs_field_f64(const GsProblem &P, const uint64_t *d_vkeys, const double *d_points, int64_t n, double *d_phi,
                  double *d_grad, unsigned long long *d_terms, cudaStream_t st);
+// FP32 values and their bounds; mark[v] = 1 where |phi - c| is within 4 bounds
+int gs_field_f32_marked(const GsProblem &P, const uint64_t *d_vkeys, int64_t n, double *d_phi, float *d_err,
+                        int64_t *d_mark, unsigned long long *d_terms, cudaStream_t st);
+// re-evaluate in FP64 the vertices with mark[v] = 1 (mark: n + 1 entries, scanned in place)
+int gs_field_recompute(const GsProblem &P, const uint64_t *d_vkeys, int64_t n, int64_t *d_mark, double *d_phi,
+                       float *d_err, int64_t *n_recomputed, cudaStream_t st);
 int gs_field_mixed(const GsProblem &P, const uint64_t *d_vkeys, int64_t n, double *d_phi, unsigned long long *d_terms,
                    int64_t *n_rechecked, cudaStream_t st);
 int gs_field_f32(const GsProblem &P, const uint64_t *d_vkeys, const double *d_points, int64_t n, double *d_phi,
@@ -73,6 +79,9 @@ struct TriCtx {
     double min_edge;
     int max_depth;
 };
+// mixed precision: mark (mark[v] = 1) the corners whose FP32 error could move
+// a surface point by more than tol_A or flip a face or fold decision
+int gs_tri_marks(const TriCtx &X, const float *d_err, double tol_A, int64_t *d_mark, cudaStream_t st);
 // counters: [0] cubes skipped for an inconsistency, [1] degenerate ears, [2] surface cubes
 int gs_triangulate(const TriCtx &X, uint64_t **d_tri_keys, int64_t *ntri_total, uint64_t **d_pt_keys,
                    double **d_pt_xyz, int64_t *npt_total, unsigned long long *d_counters, cudaStream_t st);

@@ -57,6 +57,10 @@ struct GsProblem {
     const float *fx, *fy, *fz;                   // centres relative to their cell's lower corner (FP32)
     const float *hx, *lx, *hy, *ly, *hz, *lz;    // centre - origin as a two-float sum hi + lo
     const float *fw;                             // exp(D r^2) in FP32
+    const float *fR2;                            // cutoff^2 in FP32 (prefilters only)
+    const float *fr2;                            // r^2 in FP32
+    float cell_f, inv_cell_f, pad_f;             // FP32 copies for candidate enumeration
+    int lat_exact_f32;                           // lattice coordinates (index * spacing) are exact in FP32
     const int32_t *cell_start;                   // [ncell + 1]
 };
 
@@ -83,6 +87,45 @@ __device__ __forceinline__ double gs_box_d2(const double *lo, const double *hi, 
 {
     double dx = gs_axis_gap(lo[0], hi[0], x), dy = gs_axis_gap(lo[1], hi[1], y), dz = gs_axis_gap(lo[2], hi[2], z);
     return __dadd_rn(__dadd_rn(__dmul_rn(dx, dx), __dmul_rn(dy, dy)), __dmul_rn(dz, dz));
+}
+
+// Candidate cell rows around the box [lo, hi] (coordinates relative to the
+// origin) grown by the largest cutoff radius, enumerated in FP32 -- GB300
+// issues FP64 at 1/64 of the FP32 rate, so the per-row bookkeeping must not
+// use it.  The 1e-3 A margins make the enumeration conservative: every atom
+// within the cutoff of the box lies in a visited row; membership itself is
+// decided by the caller.  body(begin, end, row, x0) gets each row's atom range.
+template <typename F>
+__device__ __forceinline__ void gs_for_rows(const GsProblem &P, const float *lo, const float *hi, F body)
+{
+    const float cs = P.cell_f, inv = P.inv_cell_f, pad = P.pad_f + 1e-3f;
+    int c0[3], c1[3];
+    for (int a = 0; a < 3; a++) {
+        float f0 = floorf((lo[a] - pad) * inv), f1 = floorf((hi[a] + pad) * inv);
+        f0 = fminf(fmaxf(f0, 0.f), (float)(P.cdim[a] - 1));
+        f1 = fminf(fmaxf(f1, 0.f), (float)(P.cdim[a] - 1));
+        c0[a] = (int)f0;
+        c1[a] = (int)f1;
+    }
+    const float pad2 = pad * pad;
+    for (int cz = c0[2]; cz <= c1[2]; cz++) {
+        float zlo = cz * cs;
+        float gz = fmaxf(0.f, fmaxf(zlo - hi[2], lo[2] - (zlo + cs)));
+        if (gz * gz > pad2) continue;
+        for (int cy = c0[1]; cy <= c1[1]; cy++) {
+            float ylo = cy * cs;
+            float gy = fmaxf(0.f, fmaxf(ylo - hi[1], lo[1] - (ylo + cs)));
+            float rem2 = pad2 - gy * gy - gz * gz;
+            if (rem2 < 0.f) continue;
+            float rem = sqrtf(rem2) + 1e-3f;
+            float f0 = fmaxf(floorf((lo[0] - rem) * inv), (float)c0[0]);
+            float f1 = fminf(floorf((hi[0] + rem) * inv), (float)c1[0]);
+            int x0 = (int)f0, x1 = (int)f1;
+            if (x0 > x1) continue;
+            int64_t row = (int64_t)P.cdim[0] * (cy + (int64_t)P.cdim[1] * cz);
+            body(P.cell_start[row + x0], P.cell_start[row + x1 + 1], row, x0);
+        }
+    }
 }
 
 // ---------------------------------------------------------------- hashing

@@ -144,15 +144,17 @@ __device__ __forceinline__ Octet octet_of(const GsProblem &P, int level, const u
 #define ACC_Q 64
 
 // one axis: C0-corrected Legendre coefficients of exp(-D (x - xi)^2) on
-// [e0,e1] and [e1,e2] (the two child intervals), FP64
+// [e0,e1] and [e1,e2] (the two child intervals), FP64; `need` selects the
+// intervals (bit 0: [e0,e1], bit 1: [e1,e2]) some accumulated child uses
 __device__ __forceinline__ void axis_coeffs_f64(double xi, double e0, double e1, double e2, double D, int gv, int nq,
-                                                double *out /* [2][4] */)
+                                                double *out /* [2][4] */, int need = 3)
 {
-    double f0 = exp(-D * (e0 - xi) * (e0 - xi));
+    double f0 = (need & 1) ? exp(-D * (e0 - xi) * (e0 - xi)) : 0.0;
     double f1 = exp(-D * (e1 - xi) * (e1 - xi));
-    double f2 = exp(-D * (e2 - xi) * (e2 - xi));
+    double f2 = (need & 2) ? exp(-D * (e2 - xi) * (e2 - xi)) : 0.0;
 #pragma unroll
     for (int h = 0; h < 2; h++) {
+        if (!((need >> h) & 1)) continue;
         double lo = h ? e1 : e0, hi = h ? e2 : e1;
         double m = __dmul_rn(0.5, __dadd_rn(lo, hi)) - xi, hh = __dmul_rn(0.5, __dsub_rn(hi, lo));
         double a0 = 0, a1 = 0, a2 = 0, a3 = 0;
@@ -174,40 +176,6 @@ __device__ __forceinline__ void axis_coeffs_f64(double xi, double e0, double e1,
     }
 }
 
-// candidate rows of the cell list around the box [lo,hi] grown by the
-// largest cutoff radius; calls body(begin, end) for each row's atom range
-template <typename F>
-__device__ __forceinline__ void for_cell_rows(const GsProblem &P, const double *lo, const double *hi, double pad, F body)
-{
-    int c0[3], c1[3];
-    for (int a = 0; a < 3; a++) {
-        double f0 = floor((lo[a] - pad - P.origin[a]) * P.inv_cell);
-        double f1 = floor((hi[a] + pad - P.origin[a]) * P.inv_cell);
-        c0[a] = f0 < 0 ? 0 : (f0 >= P.cdim[a] ? P.cdim[a] - 1 : (int)f0);
-        c1[a] = f1 < 0 ? 0 : (f1 >= P.cdim[a] ? P.cdim[a] - 1 : (int)f1);
-    }
-    double pad2 = pad * pad;
-    for (int cz = c0[2]; cz <= c1[2]; cz++) {
-        double zlo = P.origin[2] + cz * P.cell, zhi = zlo + P.cell;
-        double gz = fmax(0.0, fmax(zlo - hi[2], lo[2] - zhi));
-        if (gz * gz > pad2) continue;
-        for (int cy = c0[1]; cy <= c1[1]; cy++) {
-            double ylo = P.origin[1] + cy * P.cell, yhi = ylo + P.cell;
-            double gy = fmax(0.0, fmax(ylo - hi[1], lo[1] - yhi));
-            double rem2 = pad2 - gy * gy - gz * gz;
-            if (rem2 < 0) continue;
-            double rem = sqrt(rem2) * (1.0 + 1e-12) + 1e-12;
-            double f0 = floor((lo[0] - rem - P.origin[0]) * P.inv_cell);
-            double f1 = floor((hi[0] + rem - P.origin[0]) * P.inv_cell);
-            int x0 = f0 < c0[0] ? c0[0] : (int)f0;
-            int x1 = f1 > c1[0] ? c1[0] : (int)f1;
-            if (x0 > x1) continue;
-            int64_t row = (int64_t)P.cdim[0] * (cy + (int64_t)P.cdim[1] * cz);
-            body(P.cell_start[row + x0], P.cell_start[row + x1 + 1]);
-        }
-    }
-}
-
 __global__ void __launch_bounds__(32 * ACC_WARPS) k_accum_f64(GsProblem P, int level, const uint64_t *parents,
                                                                const uint8_t *vmask, int64_t n_oct, int gv, int nq,
                                                                double pad, double *__restrict__ A_out,
@@ -216,7 +184,9 @@ __global__ void __launch_bounds__(32 * ACC_WARPS) k_accum_f64(GsProblem P, int l
     __shared__ double s_cf[ACC_WARPS][32][25];   // per queued atom: 3 axes x 2 intervals x 4, then w
     __shared__ int s_qi[ACC_WARPS][ACC_Q];
     __shared__ uint8_t s_qm[ACC_WARPS][ACC_Q];
+    __shared__ int s_cand[ACC_WARPS][64];
     const int lane = threadIdx.x & 31, wl = threadIdx.x >> 5;
+    const unsigned below = (1u << lane) - 1u;
     const int c = lane >> 2, j = lane & 3;
     const int cx = c & 1, cy = (c >> 1) & 1, cz = c >> 2;
     unsigned long long my_pairs = 0;
@@ -224,20 +194,34 @@ __global__ void __launch_bounds__(32 * ACC_WARPS) k_accum_f64(GsProblem P, int l
         Octet q = octet_of(P, level, parents, vmask, o);
         int64_t base[3] = {2 * q.I, 2 * q.J, 2 * q.K};
         double e[3][3];
+        float eh[3][3], el[3][3];
         for (int a = 0; a < 3; a++)
-            for (int t = 0; t < 3; t++) e[a][t] = gs_lat(P, a, base[a] + t, level);
-        double plo[3] = {e[0][0], e[1][0], e[2][0]}, phi[3] = {e[0][2], e[1][2], e[2][2]};
+            for (int t = 0; t < 3; t++) {
+                e[a][t] = gs_lat(P, a, base[a] + t, level);
+                double rel = e[a][t] - P.origin[a];
+                eh[a][t] = (float)rel;
+                el[a][t] = (float)(rel - (double)eh[a][t]);
+            }
         double acc[16];
 #pragma unroll
         for (int t = 0; t < 16; t++) acc[t] = 0.0;
-        int qn = 0;
+        int qn = 0, cn = 0;
         const uint8_t vm = q.vmask;
 
+        // intervals used by the selected children, per axis
+        int need[3] = {0, 0, 0};
+        for (int cc = 0; cc < 8; cc++)
+            if ((vm >> cc) & 1) {
+                need[0] |= 1 << (cc & 1);
+                need[1] |= 1 << ((cc >> 1) & 1);
+                need[2] |= 1 << (cc >> 2);
+            }
         auto process = [&](int nproc) {
             if (lane < nproc) {
                 int i = s_qi[wl][lane];
                 double xs[3] = {P.ax[i], P.ay[i], P.az[i]};
-                for (int a = 0; a < 3; a++) axis_coeffs_f64(xs[a], e[a][0], e[a][1], e[a][2], P.D, gv, nq, &s_cf[wl][lane][8 * a]);
+                for (int a = 0; a < 3; a++)
+                    axis_coeffs_f64(xs[a], e[a][0], e[a][1], e[a][2], P.D, gv, nq, &s_cf[wl][lane][8 * a], need[a]);
                 s_cf[wl][lane][24] = P.aw[i];
             }
             __syncwarp();
@@ -256,44 +240,81 @@ __global__ void __launch_bounds__(32 * ACC_WARPS) k_accum_f64(GsProblem P, int l
             __syncwarp();
         };
 
-        if (vm) {
-            for_cell_rows(P, plo, phi, pad, [&](int b, int en) {
-                for (int s = b; s < en; s += 32) {
-                    int i = s + lane;
-                    unsigned m = 0;
-                    if (i < en) {
-                        double x = P.ax[i], y = P.ay[i], z = P.az[i], R2 = P.aR2[i];
-                        double gx[2], gy[2], gz[2];
-                        for (int hh = 0; hh < 2; hh++) {
-                            gx[hh] = gs_axis_gap(e[0][hh], e[0][hh + 1], x);
-                            gy[hh] = gs_axis_gap(e[1][hh], e[1][hh + 1], y);
-                            gz[hh] = gs_axis_gap(e[2][hh], e[2][hh + 1], z);
-                        }
-                        for (int cc = 0; cc < 8; cc++) {
-                            double dx = gx[cc & 1], dy = gy[(cc >> 1) & 1], dz = gz[cc >> 2];
-                            double d2 = __dadd_rn(__dadd_rn(__dmul_rn(dx, dx), __dmul_rn(dy, dy)), __dmul_rn(dz, dz));
-                            if (d2 <= R2) m |= 1u << cc;
-                        }
-                        m &= vm;
+        // membership: FP32 box distance with a margin, the exact FP64 test
+        // (the definition) inside the margin
+        auto filter = [&](int ncand) {
+            unsigned m = 0;
+            int i = -1;
+            if (lane < ncand) {
+                i = s_cand[wl][lane];
+                const float ah[3] = {P.hx[i], P.hy[i], P.hz[i]}, al[3] = {P.lx[i], P.ly[i], P.lz[i]};
+                float g[3][2];
+                for (int a = 0; a < 3; a++)
+                    for (int hI = 0; hI < 2; hI++) {
+                        float dlo = (eh[a][hI] - ah[a]) + (el[a][hI] - al[a]);
+                        float dhi = (ah[a] - eh[a][hI + 1]) + (al[a] - el[a][hI + 1]);
+                        g[a][hI] = fmaxf(0.f, fmaxf(dlo, dhi));
                     }
-                    my_pairs += __popc(m);
-                    unsigned bal = __ballot_sync(0xffffffffu, m != 0);
-                    int pos = qn + __popc(bal & ((1u << lane) - 1u));
-                    if (m) { s_qi[wl][pos] = i; s_qm[wl][pos] = (uint8_t)m; }
-                    qn += __popc(bal);
+                float R2 = P.fR2[i];
+                float tol = 1e-5f * R2 + 1e-5f;
+                for (int cc = 0; cc < 8; cc++) {
+                    if (!((vm >> cc) & 1)) continue;
+                    float d2 = g[0][cc & 1] * g[0][cc & 1] + g[1][(cc >> 1) & 1] * g[1][(cc >> 1) & 1] +
+                               g[2][cc >> 2] * g[2][cc >> 2];
+                    bool in;
+                    if (d2 < R2 - tol) in = true;
+                    else if (d2 > R2 + tol) in = false;
+                    else {
+                        double x = P.ax[i], y = P.ay[i], z = P.az[i];
+                        double dx = gs_axis_gap(e[0][cc & 1], e[0][(cc & 1) + 1], x);
+                        double dy = gs_axis_gap(e[1][(cc >> 1) & 1], e[1][((cc >> 1) & 1) + 1], y);
+                        double dz = gs_axis_gap(e[2][cc >> 2], e[2][(cc >> 2) + 1], z);
+                        double dd = __dadd_rn(__dadd_rn(__dmul_rn(dx, dx), __dmul_rn(dy, dy)), __dmul_rn(dz, dz));
+                        in = dd <= P.aR2[i];
+                    }
+                    if (in) m |= 1u << cc;
+                }
+            }
+            my_pairs += __popc(m);
+            unsigned bal = __ballot_sync(0xffffffffu, m != 0);
+            int pos = qn + __popc(bal & below);
+            if (m) { s_qi[wl][pos] = i; s_qm[wl][pos] = (uint8_t)m; }
+            qn += __popc(bal);
+            __syncwarp();
+            if (qn >= 32) {
+                process(32);
+                int rest = qn - 32;
+                int mi = 0; uint8_t mm = 0;
+                if (lane < rest) { mi = s_qi[wl][32 + lane]; mm = s_qm[wl][32 + lane]; }
+                __syncwarp();
+                if (lane < rest) { s_qi[wl][lane] = mi; s_qm[wl][lane] = mm; }
+                __syncwarp();
+                qn = rest;
+            }
+        };
+
+        if (vm) {
+            float flo[3] = {eh[0][0], eh[1][0], eh[2][0]}, fhi[3] = {eh[0][2], eh[1][2], eh[2][2]};
+            gs_for_rows(P, flo, fhi, [&](int b, int en, int64_t, int) {
+                for (int s = b; s < en; s += 32) {
+                    int idx = s + lane;
+                    bool v = idx < en;
+                    unsigned bal = __ballot_sync(0xffffffffu, v);
+                    if (v) s_cand[wl][cn + __popc(bal & below)] = idx;
+                    cn += __popc(bal);
                     __syncwarp();
-                    if (qn >= 32) {
-                        process(32);
-                        int rest = qn - 32;
-                        int mi = 0; uint8_t mm = 0;
-                        if (lane < rest) { mi = s_qi[wl][32 + lane]; mm = s_qm[wl][32 + lane]; }
+                    if (cn >= 32) {
+                        filter(32);
+                        int rest = cn - 32;
+                        int mv = lane < rest ? s_cand[wl][32 + lane] : 0;
                         __syncwarp();
-                        if (lane < rest) { s_qi[wl][lane] = mi; s_qm[wl][lane] = mm; }
+                        if (lane < rest) s_cand[wl][lane] = mv;
                         __syncwarp();
-                        qn = rest;
+                        cn = rest;
                     }
                 }
             });
+            if (cn > 0) filter(cn);
             if (qn > 0) process(qn);
         }
         double *dst = A_out + ((size_t)o * 8 + c) * 64 + 16 * j;
@@ -304,6 +325,8 @@ __global__ void __launch_bounds__(32 * ACC_WARPS) k_accum_f64(GsProblem P, int l
         for (int off = 16; off > 0; off >>= 1) my_pairs += __shfl_xor_sync(0xffffffffu, my_pairs, off);
         if (lane == 0 && my_pairs) atomicAdd(pairs, my_pairs);
     }
+    (void)status;
+    (void)pad;
 }
 
 static int grid_for(int64_t n_items, int per_block)
@@ -723,41 +746,48 @@ int gs_root_blocks(const GsProblem &P, uint64_t **d_keys, int64_t *n, cudaStream
 // error band of the FP32 tensor is derived.
 #define ACF_W 24
 #define ACF_F 25
-#define ACF_STRIDE 33
+#define ACF_STRIDE 36   // 144 B per atom: 16-byte aligned rows for float4 loads
 
-__global__ void __launch_bounds__(32 * ACC_WARPS) k_accum_f32(GsProblem P, int level, const uint64_t *parents,
-                                                               const uint8_t *vmask, int64_t n_oct, int gv, int nq,
-                                                               double pad, float *__restrict__ A_out,
-                                                               float *__restrict__ E_out, unsigned long long *pairs)
+__global__ void __launch_bounds__(32 * ACC_WARPS, 4) k_accum_f32(GsProblem P, int level, const uint64_t *parents,
+                                                                  const uint8_t *vmask, int64_t n_oct, int gv, int nq,
+                                                                  float hf, int lat_exact, float *__restrict__ A_out,
+                                                                  float *__restrict__ E_out,
+                                                                  unsigned long long *pairs)
 {
     unsigned long long my_pairs = 0;
-    __shared__ float s_cf[ACC_WARPS][32][ACF_STRIDE];
+    __shared__ __align__(16) float s_cf[ACC_WARPS][32][ACF_STRIDE];
     __shared__ int s_qi[ACC_WARPS][ACC_Q];
     __shared__ uint8_t s_qm[ACC_WARPS][ACC_Q];
+    __shared__ int s_cand[ACC_WARPS][64];
     const int lane = threadIdx.x & 31, wl = threadIdx.x >> 5;
+    const unsigned below = (1u << lane) - 1u;
     const int c = lane >> 2, j = lane & 3;
     const int cx = c & 1, cy = (c >> 1) & 1, cz = c >> 2;
     const float nDl2e = (float)(-P.D * 1.4426950408889634);
+    const float hh = 0.5f * hf;
     for (int64_t o = (int64_t)blockIdx.x * ACC_WARPS + wl; o < n_oct; o += (int64_t)gridDim.x * ACC_WARPS) {
         Octet q = octet_of(P, level, parents, vmask, o);
         int64_t base[3] = {2 * q.I, 2 * q.J, 2 * q.K};
-        double e[3][3];
+        // interval ends relative to the origin as hi + lo floats; when the
+        // lattice spacing has few mantissa bits the products are exact in FP32
         float eh[3][3], el[3][3];
         for (int a = 0; a < 3; a++)
             for (int t = 0; t < 3; t++) {
-                e[a][t] = gs_lat(P, a, base[a] + t, level);
-                double rel = e[a][t] - P.origin[a];
-                eh[a][t] = (float)rel;
-                el[a][t] = (float)(rel - (double)eh[a][t]);
+                if (lat_exact) {
+                    // indices < 2^18: convert through int32 (64-bit conversions are slow)
+                    eh[a][t] = (float)(int)(base[a] + t) * hf;
+                    el[a][t] = 0.f;
+                } else {
+                    double rel = gs_lat(P, a, base[a] + t, level) - P.origin[a];
+                    eh[a][t] = (float)rel;
+                    el[a][t] = (float)(rel - (double)eh[a][t]);
+                }
             }
-        const float hh = (float)(0.5 * gs_h(P, level));
-        double plo[3] = {e[0][0], e[1][0], e[2][0]}, phi[3] = {e[0][2], e[1][2], e[2][2]};
         float acc[16], comp[16], part[16];
 #pragma unroll
         for (int t = 0; t < 16; t++) { acc[t] = 0.f; comp[t] = 0.f; part[t] = 0.f; }
         float eb = 0.f;
-        int nb = 0;
-        int qn = 0;
+        int nb = 0, qn = 0, cn = 0;
         const uint8_t vm = q.vmask;
 
         auto fold = [&]() {
@@ -772,6 +802,8 @@ __global__ void __launch_bounds__(32 * ACC_WARPS) k_accum_f32(GsProblem P, int l
             nb = 0;
         };
 
+        // coefficients of the queued atoms (one lane per atom), then the
+        // rank-one updates (lane = child, x index)
         auto process = [&](int nproc) {
             if (lane < nproc) {
                 int i = s_qi[wl][lane];
@@ -811,11 +843,14 @@ __global__ void __launch_bounds__(32 * ACC_WARPS) k_accum_f32(GsProblem P, int l
                 if ((s_qm[wl][t] >> c) & 1) {
                     const float *cf = s_cf[wl][t];
                     float wa = cf[ACF_W] * cf[4 * cx + j];
+                    const float4 by = *reinterpret_cast<const float4 *>(cf + 8 + 4 * cy);
+                    const float4 gz = *reinterpret_cast<const float4 *>(cf + 16 + 4 * cz);
+                    const float bv[4] = {by.x, by.y, by.z, by.w}, gv4[4] = {gz.x, gz.y, gz.z, gz.w};
 #pragma unroll
                     for (int k = 0; k < 4; k++) {
-                        float wb = wa * cf[8 + 4 * cy + k];
+                        float wb = wa * bv[k];
 #pragma unroll
-                        for (int l = 0; l < 4; l++) part[4 * k + l] = fmaf(wb, cf[16 + 4 * cz + l], part[4 * k + l]);
+                        for (int l = 0; l < 4; l++) part[4 * k + l] = fmaf(wb, gv4[l], part[4 * k + l]);
                     }
                     eb = fmaf(cf[ACF_W] * cf[ACF_F + cx], cf[ACF_F + 2 + cy] * cf[ACF_F + 4 + cz], eb);
                     if (++nb == 8) fold();
@@ -824,59 +859,86 @@ __global__ void __launch_bounds__(32 * ACC_WARPS) k_accum_f32(GsProblem P, int l
             __syncwarp();
         };
 
-        if (vm) {
-            for_cell_rows(P, plo, phi, pad, [&](int b, int en) {
-                for (int s = b; s < en; s += 32) {
-                    int i = s + lane;
-                    unsigned m = 0;
-                    if (i < en) {
-                        const float ah[3] = {P.hx[i], P.hy[i], P.hz[i]}, al[3] = {P.lx[i], P.ly[i], P.lz[i]};
-                        float g[3][2];
-                        for (int a = 0; a < 3; a++)
-                            for (int hI = 0; hI < 2; hI++) {
-                                float dlo = (eh[a][hI] - ah[a]) + (el[a][hI] - al[a]);
-                                float dhi = (ah[a] - eh[a][hI + 1]) + (al[a] - el[a][hI + 1]);
-                                g[a][hI] = fmaxf(0.f, fmaxf(dlo, dhi));
-                            }
-                        float R2 = (float)P.aR2[i];
-                        float tol = 1e-5f * R2 + 1e-5f;
-                        for (int cc = 0; cc < 8; cc++) {
-                            if (!((vm >> cc) & 1)) continue;
-                            float d2 = g[0][cc & 1] * g[0][cc & 1] + g[1][(cc >> 1) & 1] * g[1][(cc >> 1) & 1] +
-                                       g[2][cc >> 2] * g[2][cc >> 2];
-                            bool in;
-                            if (d2 < R2 - tol) in = true;
-                            else if (d2 > R2 + tol) in = false;
-                            else {
-                                // near the cutoff sphere: the exact FP64 membership test
-                                double x = P.ax[i], y = P.ay[i], z = P.az[i];
-                                double dx = gs_axis_gap(e[0][cc & 1], e[0][(cc & 1) + 1], x);
-                                double dy = gs_axis_gap(e[1][(cc >> 1) & 1], e[1][((cc >> 1) & 1) + 1], y);
-                                double dz = gs_axis_gap(e[2][cc >> 2], e[2][(cc >> 2) + 1], z);
-                                double dd = __dadd_rn(__dadd_rn(__dmul_rn(dx, dx), __dmul_rn(dy, dy)), __dmul_rn(dz, dz));
-                                in = dd <= P.aR2[i];
-                            }
-                            if (in) m |= 1u << cc;
-                        }
+        // membership of the buffered candidates (lane < ncand takes one):
+        // FP32 box distance with a relative margin, the exact FP64 test inside
+        // the margin; members join the atom queue
+        auto filter = [&](int ncand) {
+            unsigned m = 0;
+            int i = -1;
+            if (lane < ncand) {
+                i = s_cand[wl][lane];
+                const float ah[3] = {P.hx[i], P.hy[i], P.hz[i]}, al[3] = {P.lx[i], P.ly[i], P.lz[i]};
+                float g[3][2];
+                for (int a = 0; a < 3; a++)
+                    for (int hI = 0; hI < 2; hI++) {
+                        float dlo = (eh[a][hI] - ah[a]) + (el[a][hI] - al[a]);
+                        float dhi = (ah[a] - eh[a][hI + 1]) + (al[a] - el[a][hI + 1]);
+                        g[a][hI] = fmaxf(0.f, fmaxf(dlo, dhi));
                     }
-                    my_pairs += __popc(m);
-                    unsigned bal = __ballot_sync(0xffffffffu, m != 0);
-                    int pos = qn + __popc(bal & ((1u << lane) - 1u));
-                    if (m) { s_qi[wl][pos] = i; s_qm[wl][pos] = (uint8_t)m; }
-                    qn += __popc(bal);
+                float R2 = P.fR2[i];
+                float tol = 1e-5f * R2 + 1e-5f;
+                for (int cc = 0; cc < 8; cc++) {
+                    if (!((vm >> cc) & 1)) continue;
+                    float d2 = g[0][cc & 1] * g[0][cc & 1] + g[1][(cc >> 1) & 1] * g[1][(cc >> 1) & 1] +
+                               g[2][cc >> 2] * g[2][cc >> 2];
+                    bool in;
+                    if (d2 < R2 - tol) in = true;
+                    else if (d2 > R2 + tol) in = false;
+                    else {
+                        // near the cutoff sphere: the exact FP64 membership test
+                        double x = P.ax[i], y = P.ay[i], z = P.az[i];
+                        int64_t ix = base[0] + (cc & 1), iy = base[1] + ((cc >> 1) & 1), iz = base[2] + (cc >> 2);
+                        double dx = gs_axis_gap(gs_lat(P, 0, ix, level), gs_lat(P, 0, ix + 1, level), x);
+                        double dy = gs_axis_gap(gs_lat(P, 1, iy, level), gs_lat(P, 1, iy + 1, level), y);
+                        double dz = gs_axis_gap(gs_lat(P, 2, iz, level), gs_lat(P, 2, iz + 1, level), z);
+                        double dd = __dadd_rn(__dadd_rn(__dmul_rn(dx, dx), __dmul_rn(dy, dy)), __dmul_rn(dz, dz));
+                        in = dd <= P.aR2[i];
+                    }
+                    if (in) m |= 1u << cc;
+                }
+            }
+            my_pairs += __popc(m);
+            unsigned bal = __ballot_sync(0xffffffffu, m != 0);
+            int pos = qn + __popc(bal & below);
+            if (m) { s_qi[wl][pos] = i; s_qm[wl][pos] = (uint8_t)m; }
+            qn += __popc(bal);
+            __syncwarp();
+            if (qn >= 32) {
+                process(32);
+                int rest = qn - 32;
+                int mi = 0; uint8_t mm = 0;
+                if (lane < rest) { mi = s_qi[wl][32 + lane]; mm = s_qm[wl][32 + lane]; }
+                __syncwarp();
+                if (lane < rest) { s_qi[wl][lane] = mi; s_qm[wl][lane] = mm; }
+                __syncwarp();
+                qn = rest;
+            }
+        };
+
+        if (vm) {
+            float flo[3] = {eh[0][0], eh[1][0], eh[2][0]}, fhi[3] = {eh[0][2], eh[1][2], eh[2][2]};
+            // rows of the cell list are short; their atoms are merged into a
+            // buffer so that candidates are filtered 32 at a time
+            gs_for_rows(P, flo, fhi, [&](int b, int en, int64_t, int) {
+                for (int s = b; s < en; s += 32) {
+                    int idx = s + lane;
+                    bool v = idx < en;
+                    unsigned bal = __ballot_sync(0xffffffffu, v);
+                    if (v) s_cand[wl][cn + __popc(bal & below)] = idx;
+                    cn += __popc(bal);
                     __syncwarp();
-                    if (qn >= 32) {
-                        process(32);
-                        int rest = qn - 32;
-                        int mi = 0; uint8_t mm = 0;
-                        if (lane < rest) { mi = s_qi[wl][32 + lane]; mm = s_qm[wl][32 + lane]; }
+                    if (cn >= 32) {
+                        filter(32);
+                        int rest = cn - 32;
+                        int mv = lane < rest ? s_cand[wl][32 + lane] : 0;
                         __syncwarp();
-                        if (lane < rest) { s_qi[wl][lane] = mi; s_qm[wl][lane] = mm; }
+                        if (lane < rest) s_cand[wl][lane] = mv;
                         __syncwarp();
-                        qn = rest;
+                        cn = rest;
                     }
                 }
             });
+            if (cn > 0) filter(cn);
             if (qn > 0) process(qn);
             fold();
         }
@@ -900,7 +962,8 @@ int gs_accum_f32(const GsProblem &P, int level, const uint64_t *d_parents, const
     cudaEvent_t e0 = nullptr, e1 = nullptr;
     if (ms) { cudaEventCreate(&e0); cudaEventCreate(&e1); cudaEventRecord(e0, st); }
     GS_LAUNCH(k_accum_f32, grid_for(n_oct, ACC_WARPS), 32 * ACC_WARPS, 0, st)(P, level, d_parents, d_vmask, n_oct, gv,
-                                                                             kGqN[gv], P.pad, d_A, d_err, d_pairs);
+                                                                             kGqN[gv], (float)h, P.lat_exact_f32, d_A,
+                                                                             d_err, d_pairs);
     if (ms) {
         cudaEventRecord(e1, st);
         cudaEventSynchronize(e1);
@@ -915,19 +978,27 @@ int gs_accum_f32(const GsProblem &P, int level, const uint64_t *d_parents, const
 }
 
 // FP32 estimate.  A decision is final when every margin it rests on exceeds
-// the band the FP32 error of A can move it by:
-//   entry error      dA <= MIXED_KAPPA * E   (E = sum w Fx Fy Fz)
-//   singular values  |dsigma| <= ||dA||_F <= 8 dA
-//   bounds L, U      |dL|, |dU| <= 64 dA (2 + 4 s) + FP32 rounding, s = sigma_1 over
-//                    the smallest gap between kept and neighbouring singular values
-//   precision sum    |d sum|high|| <= 64 dA + rounding
-// Otherwise the cube is flagged and its octet is re-evaluated in FP64.
-#define MIXED_KAPPA 3e-6f
+// the band the FP32 error of A and the FP32 estimate can move it by:
+//   entry error      dA = MIXED_KAPPA * E + 1e-7 sum|A|   (E = sum w Fx Fy Fz;
+//                    the largest observed |A32 - A64| / E is 7.7e-7)
+//   bounds L, U      4 (dA + 1e-7 sum|A|)(1 + s), s = sigma_1 over the smallest
+//                    gap between kept and neighbouring singular values (the
+//                    singular vectors' sensitivity); about 9x the largest
+//                    change observed between the FP32 and FP64 estimates
+//   rank rules       a rule within 32 dA of its 99% threshold may flip; then
+//                    a component of at most ~1% of sum(sigma) <= sum|A| may
+//                    move between the main part and R: 0.16 sum|A| is added
+//   precision sum    |d sum|high|| <= 64 dA + rounding (kept cubes only)
+// Otherwise the cube is flagged and its octet is re-evaluated in FP64.  The
+// debug mode (GS debug bit 0) re-runs every cube in FP64 and counts
+// disagreements; the tests require zero.
+#define MIXED_KAPPA 1.5e-6f
 
 __global__ void __launch_bounds__(128) k_estimate_f32(GsProblem P, int level, const float *__restrict__ A,
                                                       const float *__restrict__ E, int64_t n, const uint64_t *parents,
                                                       const uint8_t *vmask, uint8_t *__restrict__ dec,
-                                                      uint8_t *__restrict__ flag, unsigned long long *why_cnt)
+                                                      uint8_t *__restrict__ flag, unsigned long long *why_cnt,
+                                                      float *__restrict__ dbg)
 {
     int64_t q = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (q >= n) return;
@@ -946,7 +1017,11 @@ __global__ void __launch_bounds__(128) k_estimate_f32(GsProblem P, int level, co
     bool f = false;
     int why = 0;
     if (tot > 0.f) {
-        float bLU = 64.f * dA * (2.f + 4.f * fminf(sens, 1e4f)) + 2e-5f * tot;
+        // calibrated: the largest |dL|, |dU| seen between the FP32 and FP64
+        // estimates (debug mode, chain and globular molecules) is 0.45 of
+        // (dA + 1e-7 sum|A|)(1 + s) with kappa = 3e-6; the band takes 4 of
+        // it with kappa = 1.5e-6 (about 9x the largest change seen)
+        float bLU = 4.f * (dA + 1e-7f * tot) * (1.f + fminf(sens, 1e4f));
         // a rank rule within its band may flip: one component of size at
         // most ~1% of sum(sigma) <= tot moves between the main part and R
         if (rm <= 32.f * dA + 1e-5f * tot) bLU += 0.16f * tot;
@@ -962,48 +1037,77 @@ __global__ void __launch_bounds__(128) k_estimate_f32(GsProblem P, int level, co
         why = 3;
     }
     if (why && why_cnt) atomicAdd(&why_cnt[why - 1], 1ull);
+    if (dbg) {
+        float *o = dbg + 6 * q;
+        o[0] = b[0]; o[1] = b[1]; o[2] = sens; o[3] = dA; o[4] = tot;
+        o[5] = (tot > 0.f && rm <= 32.f * dA + 1e-5f * tot) ? 1.f : 0.f;
+    }
     dec[q] = (uint8_t)d;
     flag[q] = f ? 1 : 0;
 }
 
 int gs_estimate_f32(const GsProblem &P, int level, const float *d_A, const float *d_err, int64_t n_cubes,
                     const uint64_t *d_parents, const uint8_t *d_vmask, uint8_t *d_dec, uint8_t *d_flag,
-                    cudaStream_t st, unsigned long long *d_why)
+                    cudaStream_t st, unsigned long long *d_why, float *d_dbg)
 {
     if (n_cubes <= 0) return GS_OK;
     GS_LAUNCH(k_estimate_f32, (unsigned)((n_cubes + 127) / 128), 128, 0, st)(P, level, d_A, d_err, n_cubes, d_parents,
-                                                                            d_vmask, d_dec, d_flag, d_why);
+                                                                            d_vmask, d_dec, d_flag, d_why, d_dbg);
     GS_CHECK(cudaGetLastError());
     return GS_OK;
 }
 
 __global__ void k_add_u64(unsigned long long *dst, const unsigned long long *v) { *dst += *v; }
 
-// octets with a flagged child -> list of octet indices
-__global__ void k_octet_flags(const uint8_t *flag, int64_t n_oct, int64_t *cnt)
+// octets with a flagged child -> list of octet indices; counts flagged children
+__global__ void k_octet_flags(const uint8_t *flag, int64_t n_oct, int64_t *cnt, unsigned long long *nflagged)
 {
     int64_t o = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (o >= n_oct) return;
     uint64_t w = *(const uint64_t *)(flag + 8 * o);
     cnt[o] = w != 0;
+    if (w && nflagged) {
+        int k = 0;
+        for (int c = 0; c < 8; c++) k += ((w >> (8 * c)) & 0xff) != 0;
+        atomicAdd(nflagged, (unsigned long long)k);
+    }
 }
-__global__ void k_octet_gather(const int64_t *off, int64_t n_oct, const uint64_t *parents, uint64_t *sub_par,
-                               int64_t *sub_idx)
+__global__ void k_octet_gather(const int64_t *off, int64_t n_oct, const uint64_t *parents, const uint8_t *flag,
+                               uint64_t *sub_par, int64_t *sub_idx, uint8_t *sub_mask)
 {
     int64_t o = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (o >= n_oct || off[o + 1] == off[o]) return;
     sub_par[off[o]] = parents[o];
     sub_idx[off[o]] = o;
+    uint8_t m = 0;
+    for (int c = 0; c < 8; c++)
+        if (flag[8 * o + c]) m |= (uint8_t)(1u << c);
+    sub_mask[off[o]] = m;
 }
-__global__ void k_octet_scatter(const uint8_t *sub_dec, const int64_t *sub_idx, int64_t n_sub, uint8_t *dec,
-                                unsigned long long *mism)
+// the FP64 decisions replace the flagged children's FP32 ones
+__global__ void k_octet_scatter(const uint8_t *sub_dec, const int64_t *sub_idx, const uint8_t *sub_mask, int64_t n_sub,
+                                uint8_t *dec)
 {
     int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (t >= n_sub * 8) return;
-    int64_t q = sub_idx[t >> 3] * 8 + (t & 7);
-    dec[q] = sub_dec[t];
-    (void)mism;
+    if (!((sub_mask[t >> 3] >> (t & 7)) & 1)) return;
+    dec[sub_idx[t >> 3] * 8 + (t & 7)] = sub_dec[t];
 }
+// debug: largest change of L or U between the FP32 and FP64 estimates,
+// relative to (dA + 1e-7 sum|A|)(1 + s), over cubes whose rank rules are not
+// within their band (those get the rank-flip allowance instead)
+__global__ void k_band_ratio(const float *dbg, const double *b64, const uint8_t *d64, int64_t n, unsigned *maxbits)
+{
+    int64_t q = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (q >= n || d64[q] == DEC_INVALID) return;
+    const float *o = dbg + 6 * q;
+    if (o[4] <= 0.f || o[5] != 0.f) return;
+    double dl = fabs((double)o[0] - b64[6 * q]), du = fabs((double)o[1] - b64[6 * q + 1]);
+    double den = ((double)o[3] + 1e-7 * (double)o[4]) * (1.0 + (double)o[2]);
+    float r = (float)(fmax(dl, du) / den);
+    atomicMax(maxbits, __float_as_uint(r));
+}
+
 // debug: largest |A32 - A64| / E over a chunk, as float bits (non-negative)
 __global__ void k_err_ratio(const float *A32, const float *E, const double *A64, int64_t n, unsigned *maxbits)
 {
@@ -1041,15 +1145,17 @@ int gs_level_mixed(const GsProblem &P, int level, const uint64_t *d_parents, int
     int rc = gs_alloc((void **)&A, sizeof(float) * 64 * 8 * (size_t)n_oct, st);
     if (!rc) rc = gs_alloc((void **)&E, sizeof(float) * 8 * (size_t)n_oct, st);
     if (!rc) rc = gs_alloc((void **)&flag, 8 * (size_t)n_oct, st);
+    float *dbg = nullptr;
+    if (!rc && both) rc = gs_alloc((void **)&dbg, sizeof(float) * 6 * 8 * (size_t)n_oct, st);
     if (!rc) rc = gs_accum_f32(P, level, d_parents, nullptr, n_oct, A, E, d_pairs, d_status, st, ms);
-    if (!rc) rc = gs_estimate_f32(P, level, A, E, n_oct * 8, d_parents, nullptr, d_dec, flag, st, d_why);
+    if (!rc) rc = gs_estimate_f32(P, level, A, E, n_oct * 8, d_parents, nullptr, d_dec, flag, st, d_why, dbg);
     // flagged octets -> FP64
     int64_t *cnt = nullptr, *tot = nullptr;
     if (!rc) rc = gs_alloc((void **)&cnt, sizeof(int64_t) * (size_t)(n_oct + 1), st);
     if (!rc) rc = gs_alloc((void **)&tot, sizeof(int64_t), st);
     if (!rc) {
         cudaMemsetAsync(cnt + n_oct, 0, sizeof(int64_t), st);
-        GS_LAUNCH(k_octet_flags, (unsigned)((n_oct + 255) / 256), 256, 0, st)(flag, n_oct, cnt);
+        GS_LAUNCH(k_octet_flags, (unsigned)((n_oct + 255) / 256), 256, 0, st)(flag, n_oct, cnt, d_rechecked);
         rc = gs_scan_i64(cnt, n_oct + 1, tot, st);
     }
     int64_t nsub = 0;
@@ -1062,49 +1168,44 @@ int gs_level_mixed(const GsProblem &P, int level, const uint64_t *d_parents, int
         uint64_t *sp = nullptr;
         int64_t *si = nullptr;
         double *A64 = nullptr;
-        uint8_t *sd = nullptr;
+        uint8_t *sd = nullptr, *sm = nullptr;
         rc = gs_alloc((void **)&sp, sizeof(uint64_t) * (size_t)nsub, st);
         if (!rc) rc = gs_alloc((void **)&si, sizeof(int64_t) * (size_t)nsub, st);
+        if (!rc) rc = gs_alloc((void **)&sm, (size_t)nsub, st);
         if (!rc) rc = gs_alloc((void **)&A64, sizeof(double) * 64 * 8 * (size_t)nsub, st);
         if (!rc) rc = gs_alloc((void **)&sd, 8 * (size_t)nsub, st);
         if (!rc) {
-            GS_LAUNCH(k_octet_gather, (unsigned)((n_oct + 255) / 256), 256, 0, st)(cnt, n_oct, d_parents, sp, si);
-            rc = gs_accum_f64(P, level, sp, nullptr, nsub, A64, nullptr, d_status, st, nullptr);
+            GS_LAUNCH(k_octet_gather, (unsigned)((n_oct + 255) / 256), 256, 0, st)(cnt, n_oct, d_parents, flag, sp, si,
+                                                                                  sm);
+            // only the flagged children are accumulated and estimated in FP64
+            rc = gs_accum_f64(P, level, sp, sm, nsub, A64, nullptr, d_status, st, nullptr);
         }
-        if (!rc) rc = gs_estimate_f64(P, level, A64, nsub * 8, sp, nullptr, sd, nullptr, st);
-        if (!rc) GS_LAUNCH(k_octet_scatter, (unsigned)((nsub * 8 + 255) / 256), 256, 0, st)(sd, si, nsub, d_dec, nullptr);
-        gs_free(sp, st); gs_free(si, st); gs_free(A64, st); gs_free(sd, st);
-        if (d_rechecked && !rc) {
-            unsigned long long v = (unsigned long long)nsub * 8ull;
-            unsigned long long *tmp = nullptr;
-            // add on the device so the counter stays stream-ordered
-            rc = gs_alloc((void **)&tmp, sizeof(v), st);
-            if (!rc) {
-                cudaMemcpyAsync(tmp, &v, sizeof(v), cudaMemcpyHostToDevice, st);
-                GS_LAUNCH(k_add_u64, 1, 1, 0, st)(d_rechecked, tmp);
-                gs_free(tmp, st);
-            }
-        }
+        if (!rc) rc = gs_estimate_f64(P, level, A64, nsub * 8, sp, sm, sd, nullptr, st);
+        if (!rc) GS_LAUNCH(k_octet_scatter, (unsigned)((nsub * 8 + 255) / 256), 256, 0, st)(sd, si, sm, nsub, d_dec);
+        gs_free(sp, st); gs_free(si, st); gs_free(sm, st); gs_free(A64, st); gs_free(sd, st);
     }
     gs_free(cnt, st); gs_free(tot, st);
     if (!rc && both) {
         // debug: FP64 on every octet; count final decisions that disagree and
         // record the largest |A32 - A64| / E
-        double *A64 = nullptr;
+        double *A64 = nullptr, *b64 = nullptr;
         uint8_t *d64 = nullptr;
         rc = gs_alloc((void **)&A64, sizeof(double) * 64 * 8 * (size_t)n_oct, st);
+        if (!rc) rc = gs_alloc((void **)&b64, sizeof(double) * 6 * 8 * (size_t)n_oct, st);
         if (!rc) rc = gs_alloc((void **)&d64, 8 * (size_t)n_oct, st);
         if (!rc) rc = gs_accum_f64(P, level, d_parents, nullptr, n_oct, A64, nullptr, d_status, st, nullptr);
-        if (!rc) rc = gs_estimate_f64(P, level, A64, n_oct * 8, d_parents, nullptr, d64, nullptr, st);
+        if (!rc) rc = gs_estimate_f64(P, level, A64, n_oct * 8, d_parents, nullptr, d64, b64, st);
         if (!rc) {
-            GS_LAUNCH(k_count_mismatch, (unsigned)((n_oct * 8 + 255) / 256), 256, 0, st)(d_dec, d64, n_oct * 8, d_mism);
-            GS_LAUNCH(k_err_ratio, (unsigned)((n_oct * 8 + 255) / 256), 256, 0, st)(A, E, A64, n_oct * 8,
-                                                                                   (unsigned *)(d_why + 3));
+            unsigned nb = (unsigned)((n_oct * 8 + 255) / 256);
+            GS_LAUNCH(k_count_mismatch, nb, 256, 0, st)(d_dec, d64, n_oct * 8, d_mism);
+            GS_LAUNCH(k_err_ratio, nb, 256, 0, st)(A, E, A64, n_oct * 8, (unsigned *)(d_why + 3));
+            GS_LAUNCH(k_band_ratio, nb, 256, 0, st)(dbg, b64, d64, n_oct * 8, (unsigned *)(d_why + 4));
         }
-        gs_free(A64, st); gs_free(d64, st);
+        gs_free(A64, st); gs_free(b64, st); gs_free(d64, st);
     }
     gs_free(A, st);
     gs_free(E, st);
+    gs_free(dbg, st);
     gs_free(flag, st);
     if (rc) return rc;
     GS_CHECK(cudaGetLastError());

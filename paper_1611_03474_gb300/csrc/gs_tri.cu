@@ -259,23 +259,47 @@ __device__ int tri_cube(const TriCtx &X, int64_t ci, TriOut &o, unsigned long lo
             eid[4 * a + e] = (signed char)id;
         }
     }
-    // fold lines: own (both ends) and the same-size neighbours' ends on shared faces
+    // fold roots of this cube along each axis
+    double rt[3][2][2];
+    int nr[3];
+    for (int a = 0; a < 3; a++) {
+        double ru[2], rv[2];
+        nr[a] = fold_solve(g, a, c, ru, rv);
+        for (int r = 0; r < nr[a]; r++) { rt[a][r][0] = ru[r]; rt[a][r][1] = rv[r]; }
+    }
+    // critical points: an a-fold root and a b-fold root that share the third
+    // axis' coordinate lie on crossing lines; the b-root takes the a-root's
+    // value of that coordinate, so segments along each fold line are exactly
+    // parallel to its axis (pairs in the order (0,1), (0,2), (1,2))
+    signed char xa[12], xi[12], xb[12], xj[12];
+    int nx = 0;
+    for (int a = 0; a < 3; a++)
+        for (int b = a + 1; b < 3; b++) {
+            int cc = 3 - a - b;
+            int ua, va, ub, vb;
+            axes_other(a, ua, va);
+            axes_other(b, ub, vb);
+            for (int i = 0; i < nr[a]; i++)
+                for (int j = 0; j < nr[b]; j++) {
+                    double ca = rt[a][i][cc == ua ? 0 : 1], cb = rt[b][j][cc == ub ? 0 : 1];
+                    if (fabs(ca - cb) > 1e-9) continue;
+                    rt[b][j][cc == ub ? 0 : 1] = ca;
+                    xa[nx] = (signed char)a; xi[nx] = (signed char)i; xb[nx] = (signed char)b; xj[nx] = (signed char)j;
+                    nx++;
+                }
+        }
+    // fold ends: own (both faces) and the same-size neighbours' ends on shared faces
     signed char fpt[6][4];
     int nfp[6] = {0, 0, 0, 0, 0, 0};
-    double rt[3][2][2];
     signed char fend[3][2][2];
-    int nr[3];
     for (int a = 0; a < 3; a++) {
         int ua, va;
         axes_other(a, ua, va);
-        double ru[2], rv[2];
-        nr[a] = fold_solve(g, a, c, ru, rv);
         for (int r = 0; r < nr[a]; r++) {
-            rt[a][r][0] = ru[r]; rt[a][r][1] = rv[r];
             for (int sd = 0; sd < 2; sd++) {
                 int id = (int)add_pt(pts, np, 1);
                 if (id < 0) return 1;
-                pts[id].p[a] = sd; pts[id].p[ua] = ru[r]; pts[id].p[va] = rv[r];
+                pts[id].p[a] = sd; pts[id].p[ua] = rt[a][r][0]; pts[id].p[va] = rt[a][r][1];
                 int64_t L[3] = {C[0] * sc, C[1] * sc, C[2] * sc};
                 L[a] = (C[a] + sd) * sc;
                 pts[id].key = gk_make(L[0], L[1], L[2], 8u + 4u * a + 2u * (sd == 0 ? 1u : 0u) + (unsigned)r, (unsigned)lvl);
@@ -301,46 +325,39 @@ __device__ int tri_cube(const TriCtx &X, int64_t ci, TriOut &o, unsigned long lo
             }
         }
     }
-    // critical points: a-fold i and b-fold j share the coordinate of the third axis
     signed char chain[3][2][4];
     int nch[3][2];
     for (int a = 0; a < 3; a++)
         for (int r = 0; r < nr[a]; r++) { chain[a][r][0] = fend[a][r][0]; nch[a][r] = 1; }
-    for (int a = 0; a < 3; a++)
-        for (int b = a + 1; b < 3; b++) {
-            int cc = 3 - a - b;
-            int ua, va, ub, vb;
-            axes_other(a, ua, va);
-            axes_other(b, ub, vb);
-            for (int i = 0; i < nr[a]; i++)
-                for (int j = 0; j < nr[b]; j++) {
-                    double ca = rt[a][i][cc == ua ? 0 : 1], cb = rt[b][j][cc == ub ? 0 : 1];
-                    if (fabs(ca - cb) > 1e-9) continue;
-                    int id = (int)add_pt(pts, np, 3);
-                    if (id < 0) return 1;
-                    TPt &P = pts[id];
-                    P.p[a] = rt[b][j][a == ub ? 0 : 1];
-                    P.p[b] = rt[a][i][b == ua ? 0 : 1];
-                    P.p[cc] = ca;
-                    P.fa = (signed char)a; P.fb = (signed char)b;
-                    // dg/dx_cc at the point: the outward normal is -sign(dg/dx_cc) e_cc
-                    double dg = 0;
-                    for (int v = 0; v < 8; v++) {
-                        double f = 1.0;
-                        for (int t = 0; t < 3; t++) {
-                            int bit = (v >> t) & 1;
-                            f *= (t == cc) ? (bit ? 1.0 : -1.0) : (bit ? P.p[t] : 1.0 - P.p[t]);
-                        }
-                        dg += f * g[v];
-                    }
-                    bool cyclic = !(a == 0 && b == 2);   // (a,b,cc) an even permutation
-                    P.rh = (signed char)(cyclic == (dg < 0.0) ? 1 : 0);
-                    P.key = gk_make(C[0] * sc, C[1] * sc, C[2] * sc, 20u + 4u * (unsigned)(a + b - 1) + 2u * i + j,
-                                    (unsigned)lvl);
-                    if (nch[a][i] < 3) chain[a][i][nch[a][i]++] = (signed char)id;
-                    if (nch[b][j] < 3) chain[b][j][nch[b][j]++] = (signed char)id;
-                }
+    for (int t = 0; t < nx; t++) {
+        int a = xa[t], i = xi[t], b = xb[t], j = xj[t];
+        int cc = 3 - a - b;
+        int ua, va, ub, vb;
+        axes_other(a, ua, va);
+        axes_other(b, ub, vb);
+        int id = (int)add_pt(pts, np, 3);
+        if (id < 0) return 1;
+        TPt &P = pts[id];
+        P.p[a] = rt[b][j][a == ub ? 0 : 1];
+        P.p[b] = rt[a][i][b == ua ? 0 : 1];
+        P.p[cc] = rt[a][i][cc == ua ? 0 : 1];
+        P.fa = (signed char)a; P.fb = (signed char)b;
+        // dg/dx_cc at the point: the outward normal is -sign(dg/dx_cc) e_cc
+        double dg = 0;
+        for (int v = 0; v < 8; v++) {
+            double f = 1.0;
+            for (int q = 0; q < 3; q++) {
+                int bit = (v >> q) & 1;
+                f *= (q == cc) ? (bit ? 1.0 : -1.0) : (bit ? P.p[q] : 1.0 - P.p[q]);
+            }
+            dg += f * g[v];
         }
+        bool cyclic = !(a == 0 && b == 2);   // (a,b,cc) an even permutation
+        P.rh = (signed char)(cyclic == (dg < 0.0) ? 1 : 0);
+        P.key = gk_make(C[0] * sc, C[1] * sc, C[2] * sc, 20u + 4u * (unsigned)(a + b - 1) + 2u * i + j, (unsigned)lvl);
+        if (nch[a][i] < 3) chain[a][i][nch[a][i]++] = (signed char)id;
+        if (nch[b][j] < 3) chain[b][j][nch[b][j]++] = (signed char)id;
+    }
     for (int a = 0; a < 3; a++)
         for (int r = 0; r < nr[a]; r++) {
             signed char *ch = chain[a][r];
@@ -565,5 +582,111 @@ int gs_triangulate(const TriCtx &X, uint64_t **d_tri_keys, int64_t *ntri_total, 
     GS_CHECK(cudaGetLastError());
     *ntri_total = h[0];
     *npt_total = h[1];
+    return GS_OK;
+}
+
+// ---------------------------------------------------------------- mixed precision marks
+// For a surface cube with FP32 corner values g and bounds e: an edge point
+// moves by at most h (e0 + e1) / |g1 - g0| (first order); a face's saddle
+// decision is safe when |h_s - c| exceeds the bound carried through h_s; a
+// fold root (extreme and critical points) moves by at most the first-order
+// bound from the root's derivative.  Where any bound exceeds tol the corners
+// involved (all eight for a fold) are re-evaluated in FP64.
+__global__ void __launch_bounds__(128) k_tri_marks(TriCtx X, const float *__restrict__ err, double tol,
+                                                   int64_t *__restrict__ mark)
+{
+    int64_t ci = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (ci >= X.ncubes) return;
+    uint64_t ck = X.cubes[ci];
+    int lvl = (int)gk_level(ck);
+    double h = ldexp(X.min_edge, X.max_depth - lvl);
+    double g[8], e[8];
+    int vid[8];
+    for (int v = 0; v < 8; v++) {
+        vid[v] = X.cvid[ci * 8 + v];
+        g[v] = X.phi[vid[v]];
+        e[v] = (double)err[vid[v]];
+    }
+    const double c = X.c;
+    int nin = 0;
+    for (int v = 0; v < 8; v++) nin += g[v] >= c;
+    if (nin == 0 || nin == 8) return;
+    bool all = false;
+    unsigned m = 0;
+    for (int a = 0; a < 3 && !all; a++) {
+        int ua, va;
+        axes_other(a, ua, va);
+        for (int k = 0; k < 4; k++) {
+            int b0[3], b1[3];
+            b0[a] = 0; b1[a] = 1; b0[ua] = b1[ua] = k & 1; b0[va] = b1[va] = k >> 1;
+            int v0 = b0[0] + 2 * b0[1] + 4 * b0[2], v1 = b1[0] + 2 * b1[1] + 4 * b1[2];
+            if ((g[v0] >= c) == (g[v1] >= c)) continue;
+            if (h * (e[v0] + e[v1]) > tol * fabs(g[v1] - g[v0])) m |= (1u << v0) | (1u << v1);
+        }
+        for (int sd = 0; sd < 2; sd++) {
+            double hf[4];
+            int fv[4];
+            for (int k = 0; k < 4; k++) {
+                int b[3];
+                b[a] = sd; b[ua] = k & 1; b[va] = k >> 1;
+                fv[k] = b[0] + 2 * b[1] + 4 * b[2];
+                hf[k] = g[fv[k]];
+            }
+            int around00;
+            double us;
+            if (face_arcs(hf, c, around00, us) == 2) {
+                double den = hf[0] - hf[1] - hf[2] + hf[3];
+                double hs = (hf[0] * hf[3] - hf[1] * hf[2]) / den;
+                double eb = 0;
+                for (int k = 0; k < 4; k++) eb += e[fv[k]];
+                // h_s = (h0 h3 - h1 h2) / den: each value enters with weight <= 2 max|h| / |den|
+                double amp = 2.0 * (fabs(hf[0]) + fabs(hf[1]) + fabs(hf[2]) + fabs(hf[3])) / fabs(den);
+                if (fabs(hs - c) <= 4.0 * amp * eb) for (int k = 0; k < 4; k++) m |= 1u << fv[k];
+            }
+        }
+        double ru[2], rv[2];
+        int nr = fold_solve(g, a, c, ru, rv);
+        if (nr > 0) {
+            // first-order error of the fold roots (u*, v*) of
+            // Q(u) = (a0 + a1 u)(b2 + b3 u) - (a2 + a3 u)(b0 + b1 u), v = -(b0 + b1 u)/(b2 + b3 u):
+            // each monomial coefficient moves by at most 8 max(e) (4 for A, 8 for B = upper - lower)
+            double lo4[4], up4[4], em = 0;
+            for (int k = 0; k < 4; k++) {
+                int b[3];
+                b[a] = 0; b[ua] = k & 1; b[va] = k >> 1;
+                lo4[k] = g[b[0] + 2 * b[1] + 4 * b[2]];
+                em = fmax(em, e[b[0] + 2 * b[1] + 4 * b[2]]);
+                b[a] = 1;
+                up4[k] = g[b[0] + 2 * b[1] + 4 * b[2]];
+                em = fmax(em, e[b[0] + 2 * b[1] + 4 * b[2]]);
+            }
+            double p0 = lo4[0] - c, p1 = lo4[1] - lo4[0], p2 = lo4[2] - lo4[0], p3 = lo4[3] - lo4[1] - lo4[2] + lo4[0];
+            double d0 = up4[0] - lo4[0], d1 = up4[1] - lo4[1], d2 = up4[2] - lo4[2], d3 = up4[3] - lo4[3];
+            double q0 = d0, q1 = d1 - d0, q2 = d2 - d0, q3 = d3 - d1 - d2 + d0;
+            double SA = fabs(p0) + fabs(p1) + fabs(p2) + fabs(p3), SB = fabs(q0) + fabs(q1) + fabs(q2) + fabs(q3);
+            // |dQ| <= 2 (8 em SB + 16 em SA) for u in [0, 1]
+            double dQ = 16.0 * em * (2.0 * SA + SB);
+            for (int r = 0; r < nr && !all; r++) {
+                double u = ru[r], v = rv[r];
+                // |Q'(u)| from the product rule
+                double dQu = p1 * (q2 + q3 * u) + (p0 + p1 * u) * q3 - p3 * (q0 + q1 * u) - (p2 + p3 * u) * q1;
+                double den = q2 + q3 * u;
+                double du = fabs(dQu) > 0 ? dQ / fabs(dQu) : 1e30;
+                double dv = fabs(den) > 0 ? (16.0 * em * (1.0 + fabs(v)) + (fabs(q1) + fabs(q3) * fabs(v)) * du) / fabs(den)
+                                          : 1e30;
+                if (h * (du + dv) > tol) all = true;
+            }
+        }
+    }
+    if (all) m = 0xFF;
+    for (int v = 0; v < 8; v++)
+        if ((m >> v) & 1) mark[vid[v]] = 1;
+}
+
+int gs_tri_marks(const TriCtx &X, const float *d_err, double tol_A, int64_t *d_mark, cudaStream_t st)
+{
+    if (X.ncubes <= 0) return GS_OK;
+    GS_LAUNCH(k_tri_marks, (unsigned)((X.ncubes + 127) / 128), 128, 0, st)(X, d_err, tol_A, d_mark);
+    GS_CHECK(cudaGetLastError());
     return GS_OK;
 }

@@ -151,10 +151,11 @@ def test_mixed_decisions_match_fp64_everywhere(chain100):
                                  min_edge=cfg["min_edge"], precision_mode=gs.GS_PREC_MIXED, debug_flags=1)
     st = m.stats
     print("recheck", st["recheck_cubes"], "of", sum(st["examined"]), "reasons", st["recheck_bounds"],
-          st["recheck_precision"], st["recheck_zero"], "max |A32-A64|/E", st["mixed_err_ratio"])
+          st["recheck_precision"], st["recheck_zero"], "max |A32-A64|/E", st["mixed_err_ratio"],
+          "band ratio", st["mixed_band_ratio"], "vertices rechecked", st["recheck_vertices"])
     assert m.mismatches == 0
-    # the FP32 error stays well inside the band's kappa (3e-6)
-    assert st["mixed_err_ratio"] < 3e-6
+    # the FP32 error stays inside the band's kappa (1.5e-6)
+    assert st["mixed_err_ratio"] < 1.5e-6
     assert st["recheck_cubes"] < 0.2 * sum(st["examined"])
 
 
@@ -173,3 +174,13 @@ def test_field_mixed_close_to_fp64(chain100):
     p32 = gs.gs_eval_field(xyz, r, 0.5, 1.0, pts, precision_mode=gs.GS_PREC_MIXED)
     p64 = oracle.field(xyz, r, 0.5, 1.0, pts)
     assert np.abs(p32 - p64).max() <= 2e-5 * max(1.0, np.abs(p64).max())
+
+
+def test_mixed_decisions_match_fp64_globular():
+    xyz, r = synth.globular(5000, seed=1)
+    m = gs.mesh_gaussian_surface(xyz, r, 0.5, 1.0, 1e-3, 3, precision_mode=gs.GS_PREC_MIXED, debug_flags=1)
+    st = m.stats
+    print("globular5000 recheck", st["recheck_cubes"], "of", sum(st["examined"]), "err ratio",
+          st["mixed_err_ratio"], "band ratio", st["mixed_band_ratio"])
+    assert m.mismatches == 0
+    assert st["mixed_err_ratio"] < 1.5e-6
