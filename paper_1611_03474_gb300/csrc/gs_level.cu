@@ -501,16 +501,17 @@ __device__ __forceinline__ int rank99(const T (&s)[4], T &margin)
 template <typename T>
 __device__ __forceinline__ T gap_sens(const T (&s)[4], int kept)
 {
-    // s[0] / the smallest separation between consecutive values up to the
-    // first dropped one: how far singular vectors can turn per unit change
-    T g = T(1e30);
-    int last = kept < 4 ? kept : 3;
-    for (int i = 0; i < last; i++) {
-        T d = s[i] - s[i + 1];
-        g = d < g ? d : g;
+    // sum over the kept values of s_i / (distance to the nearest other
+    // value): a perturbation E turns the i-th singular pair by about
+    // |E| / gap_i, which moves that term's share of the bounds by about
+    // s_i |E| / gap_i.  Terms far smaller than their gap contribute little.
+    T r = T(0);
+    for (int i = 0; i < kept && i < 4; i++) {
+        T g = T(1e30);
+        if (i > 0) g = s[i - 1] - s[i];
+        if (i < 3) { T d = s[i] - s[i + 1]; g = d < g ? d : g; }
+        r += s[i] / (g > T(0) ? g : T(1e-30));
     }
-    if (last == 0) return T(0);
-    T r = s[0] / (g > T(0) ? g : T(1e-30));
     return r < T(1e6) ? r : T(1e6);
 }
 
@@ -622,10 +623,17 @@ __device__ __forceinline__ int decide(const T *b, T c, T precision, int level, i
 
 __global__ void __launch_bounds__(128) k_estimate_f64(GsProblem P, int level, const double *__restrict__ A,
                                                       int64_t n, const uint64_t *parents, const uint8_t *vmask,
-                                                      uint8_t *__restrict__ dec, double *__restrict__ bounds)
+                                                      uint8_t *__restrict__ dec, double *__restrict__ bounds,
+                                                      const int32_t *__restrict__ list, const unsigned *nlist)
 {
     int64_t q = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    if (q >= n) return;
+    if (list) {
+        // compacted list of the cubes to estimate (the rest keep DEC_INVALID)
+        if (q >= (int64_t)*nlist) return;
+        q = list[q];
+    } else if (q >= n) {
+        return;
+    }
     Octet oc = octet_of(P, level, parents, vmask, q >> 3);
     if (!((oc.vmask >> (q & 7)) & 1)) { dec[q] = DEC_INVALID; return; }
     double a[64];
@@ -643,7 +651,7 @@ int gs_estimate_f64(const GsProblem &P, int level, const double *d_A, int64_t n_
 {
     if (n_cubes <= 0) return GS_OK;
     GS_LAUNCH(k_estimate_f64, (unsigned)((n_cubes + 127) / 128), 128, 0, st)(P, level, d_A, n_cubes, d_parents, d_vmask,
-                                                                     d_dec, d_bounds);
+                                                                     d_dec, d_bounds, nullptr, nullptr);
     GS_CHECK(cudaGetLastError());
     return GS_OK;
 }
@@ -1084,6 +1092,19 @@ __global__ void k_octet_gather(const int64_t *off, int64_t n_oct, const uint64_t
         if (flag[8 * o + c]) m |= (uint8_t)(1u << c);
     sub_mask[off[o]] = m;
 }
+// flagged children of the re-evaluated octets -> a compact list (any order:
+// each entry is estimated on its own), so the FP64 estimate runs full warps
+__global__ void k_child_list(const uint8_t *sub_mask, int64_t n_sub, int32_t *list, unsigned *nlist)
+{
+    int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    bool on = t < n_sub * 8 && ((sub_mask[t >> 3] >> (t & 7)) & 1);
+    unsigned bal = __ballot_sync(0xffffffffu, on);
+    if (!bal) return;
+    unsigned lane = threadIdx.x & 31, base = 0;
+    if (lane == 0) base = atomicAdd(nlist, (unsigned)__popc(bal));
+    base = __shfl_sync(0xffffffffu, base, 0);
+    if (on) list[base + __popc(bal & ((1u << lane) - 1u))] = (int32_t)t;
+}
 // the FP64 decisions replace the flagged children's FP32 ones
 __global__ void k_octet_scatter(const uint8_t *sub_dec, const int64_t *sub_idx, const uint8_t *sub_mask, int64_t n_sub,
                                 uint8_t *dec)
@@ -1180,7 +1201,17 @@ int gs_level_mixed(const GsProblem &P, int level, const uint64_t *d_parents, int
             // only the flagged children are accumulated and estimated in FP64
             rc = gs_accum_f64(P, level, sp, sm, nsub, A64, nullptr, d_status, st, nullptr);
         }
-        if (!rc) rc = gs_estimate_f64(P, level, A64, nsub * 8, sp, sm, sd, nullptr, st);
+        int32_t *lst = nullptr;
+        unsigned *nl = nullptr;
+        if (!rc) rc = gs_alloc((void **)&lst, sizeof(int32_t) * 8 * (size_t)nsub, st);
+        if (!rc) rc = gs_alloc((void **)&nl, sizeof(unsigned), st);
+        if (!rc) {
+            unsigned nb = (unsigned)((nsub * 8 + 127) / 128);
+            cudaMemsetAsync(nl, 0, sizeof(unsigned), st);
+            GS_LAUNCH(k_child_list, nb, 128, 0, st)(sm, nsub, lst, nl);
+            GS_LAUNCH(k_estimate_f64, nb, 128, 0, st)(P, level, A64, nsub * 8, sp, sm, sd, nullptr, lst, nl);
+        }
+        gs_free(lst, st); gs_free(nl, st);
         if (!rc) GS_LAUNCH(k_octet_scatter, (unsigned)((nsub * 8 + 255) / 256), 256, 0, st)(sd, si, sm, nsub, d_dec);
         gs_free(sp, st); gs_free(si, st); gs_free(sm, st); gs_free(A64, st); gs_free(sd, st);
     }

@@ -141,18 +141,25 @@ __device__ __noinline__ int face_arcs(const double *h, double c, int &around00, 
     return 2;
 }
 
+// Where a cube's output goes: triangles are written while fewer than
+// tri_cap have been produced, points only if all of them fit in pt_cap.  The
+// final pass writes at the scanned offsets with unbounded caps; the first
+// pass writes into a fixed per-cube staging slot (caps TRI_STAGE_T,
+// TRI_STAGE_P), so only cubes that overflow it are traced a second time.
 struct TriOut {
     uint64_t *tri_keys;   // [3] per triangle
     uint64_t *pt_keys;
     double *pt_xyz;
     int64_t tri_off, pt_off;
+    int tri_cap, pt_cap;
     int ntri, npt;
-    bool emit;
 };
+#define TRI_STAGE_T 4
+#define TRI_STAGE_P 6
 
 __device__ __forceinline__ void put_tri(TriOut &o, uint64_t a, uint64_t b, uint64_t c)
 {
-    if (o.emit) {
+    if (o.ntri < o.tri_cap) {
         uint64_t *d = o.tri_keys + 3 * (o.tri_off + o.ntri);
         d[0] = a; d[1] = b; d[2] = c;
     }
@@ -499,7 +506,7 @@ __device__ int tri_cube(const TriCtx &X, int64_t ci, TriOut &o, unsigned long lo
         if (n >= 3) clip_piece(pts, poly, n, o, degen);
     }
     // points in world coordinates
-    if (o.emit) {
+    if (np <= o.pt_cap) {
         double h = ldexp(X.min_edge, X.max_depth - lvl);
         for (int i = 0; i < np; i++) {
             double *dst = o.pt_xyz + 3 * (o.pt_off + i);
@@ -517,31 +524,76 @@ __device__ int tri_cube(const TriCtx &X, int64_t ci, TriOut &o, unsigned long lo
     return 0;
 }
 
+// first pass: trace every cube, count its output and stage it when it fits
 __global__ void __launch_bounds__(128) k_tri_count(TriCtx X, int64_t *__restrict__ ntri, int64_t *__restrict__ npt,
-                                                   unsigned long long *errs, unsigned long long *surface)
+                                                   unsigned long long *errs, unsigned long long *surface,
+                                                   uint64_t *st_tri, uint64_t *st_pk, double *st_xyz,
+                                                   unsigned long long *degen)
 {
     int64_t ci = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (ci >= X.ncubes) return;
     TriOut o;
-    o.emit = false; o.ntri = 0; o.npt = 0; o.tri_off = 0; o.pt_off = 0;
-    o.tri_keys = nullptr; o.pt_keys = nullptr; o.pt_xyz = nullptr;
-    int bad = tri_cube(X, ci, o, nullptr);
+    o.ntri = 0; o.npt = 0;
+    o.tri_keys = st_tri; o.pt_keys = st_pk; o.pt_xyz = st_xyz;
+    o.tri_off = ci * TRI_STAGE_T; o.pt_off = ci * TRI_STAGE_P;
+    o.tri_cap = st_tri ? TRI_STAGE_T : 0;
+    o.pt_cap = st_tri ? TRI_STAGE_P : -1;
+    int bad = tri_cube(X, ci, o, st_tri ? degen : nullptr);
     if (bad) { atomicAdd(errs, 1ull); o.ntri = 0; o.npt = 0; }
     if (o.npt > 0) atomicAdd(surface, 1ull);
     ntri[ci] = o.ntri;
     npt[ci] = o.npt;
 }
 
+// staged cubes: copy to the scanned offsets; the others go to the list of
+// cubes traced again by k_tri_emit
+__global__ void __launch_bounds__(128) k_tri_copy(int64_t n, const int64_t *__restrict__ tri_off,
+                                                  const int64_t *__restrict__ pt_off, const uint64_t *__restrict__ st_tri,
+                                                  const uint64_t *__restrict__ st_pk, const double *__restrict__ st_xyz,
+                                                  uint64_t *__restrict__ tri_keys, uint64_t *__restrict__ pt_keys,
+                                                  double *__restrict__ pt_xyz, int64_t *__restrict__ redo,
+                                                  unsigned long long *nredo)
+{
+    int64_t ci = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    bool over = false;
+    if (ci < n) {
+        int64_t t0 = tri_off[ci], nt = tri_off[ci + 1] - t0;
+        int64_t p0 = pt_off[ci], np = pt_off[ci + 1] - p0;
+        if (nt > TRI_STAGE_T || np > TRI_STAGE_P) {
+            over = true;
+        } else {
+            for (int64_t k = 0; k < 3 * nt; k++) tri_keys[3 * t0 + k] = st_tri[3 * ci * TRI_STAGE_T + k];
+            for (int64_t k = 0; k < np; k++) pt_keys[p0 + k] = st_pk[ci * TRI_STAGE_P + k];
+            for (int64_t k = 0; k < 3 * np; k++) pt_xyz[3 * p0 + k] = st_xyz[3 * ci * TRI_STAGE_P + k];
+        }
+    }
+    unsigned bal = __ballot_sync(0xffffffffu, over);
+    if (!bal) return;
+    unsigned lane = threadIdx.x & 31;
+    unsigned long long base = 0;
+    if (lane == 0) base = atomicAdd(nredo, (unsigned long long)__popc(bal));
+    base = __shfl_sync(0xffffffffu, base, 0);
+    if (over) redo[base + __popc(bal & ((1u << lane) - 1u))] = ci;
+}
+
+// final pass over the listed cubes (all cubes when list is null)
 __global__ void __launch_bounds__(128) k_tri_emit(TriCtx X, const int64_t *__restrict__ tri_off,
                                                   const int64_t *__restrict__ pt_off, uint64_t *__restrict__ tri_keys,
                                                   uint64_t *__restrict__ pt_keys, double *__restrict__ pt_xyz,
-                                                  unsigned long long *degen)
+                                                  unsigned long long *degen, const int64_t *__restrict__ list,
+                                                  const unsigned long long *nlist)
 {
     int64_t ci = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    if (ci >= X.ncubes) return;
+    if (list) {
+        if (ci >= (int64_t)*nlist) return;
+        ci = list[ci];
+    } else if (ci >= X.ncubes) {
+        return;
+    }
     if (tri_off[ci + 1] == tri_off[ci] && pt_off[ci + 1] == pt_off[ci]) return;
     TriOut o;
-    o.emit = true; o.ntri = 0; o.npt = 0; o.tri_off = tri_off[ci]; o.pt_off = pt_off[ci];
+    o.ntri = 0; o.npt = 0; o.tri_off = tri_off[ci]; o.pt_off = pt_off[ci];
+    o.tri_cap = 1 << 30; o.pt_cap = 1 << 30;
     o.tri_keys = tri_keys; o.pt_keys = pt_keys; o.pt_xyz = pt_xyz;
     tri_cube(X, ci, o, degen);
 }
@@ -559,10 +611,21 @@ int gs_triangulate(const TriCtx &X, uint64_t **d_tri_keys, int64_t *ntri_total, 
     if (!rc) rc = gs_alloc((void **)&npt, sizeof(int64_t) * (size_t)(n + 1), st);
     if (!rc) rc = gs_alloc((void **)&tot, 2 * sizeof(int64_t), st);
     if (rc) { gs_free(ntri, st); gs_free(npt, st); gs_free(tot, st); return rc; }
+    // staging slots; without room for them every cube is traced twice
+    uint64_t *st_tri = nullptr, *st_pk = nullptr;
+    double *st_xyz = nullptr;
+    if (cudaMallocAsync((void **)&st_tri, sizeof(uint64_t) * 3 * TRI_STAGE_T * (size_t)n, st) != cudaSuccess ||
+        cudaMallocAsync((void **)&st_pk, sizeof(uint64_t) * TRI_STAGE_P * (size_t)n, st) != cudaSuccess ||
+        cudaMallocAsync((void **)&st_xyz, sizeof(double) * 3 * TRI_STAGE_P * (size_t)n, st) != cudaSuccess) {
+        cudaGetLastError();
+        gs_free(st_tri, st); gs_free(st_pk, st); gs_free(st_xyz, st);
+        st_tri = nullptr; st_pk = nullptr; st_xyz = nullptr;
+    }
     unsigned nb = (unsigned)((n + 127) / 128);
     cudaMemsetAsync(ntri + n, 0, sizeof(int64_t), st);
     cudaMemsetAsync(npt + n, 0, sizeof(int64_t), st);
-    GS_LAUNCH(k_tri_count, nb, 128, 0, st)(X, ntri, npt, d_counters + 0, d_counters + 2);
+    GS_LAUNCH(k_tri_count, nb, 128, 0, st)(X, ntri, npt, d_counters + 0, d_counters + 2, st_tri, st_pk, st_xyz,
+                                          d_counters + 1);
     rc = gs_scan_i64(ntri, n + 1, tot, st);
     if (!rc) rc = gs_scan_i64(npt, n + 1, tot + 1, st);
     int64_t h[2] = {0, 0};
@@ -576,7 +639,24 @@ int gs_triangulate(const TriCtx &X, uint64_t **d_tri_keys, int64_t *ntri_total, 
         if (!rc) rc = gs_alloc((void **)d_pt_keys, sizeof(uint64_t) * (size_t)(h[1] + 1), st);
         if (!rc) rc = gs_alloc((void **)d_pt_xyz, sizeof(double) * 3 * (size_t)(h[1] + 1), st);
     }
-    if (!rc) GS_LAUNCH(k_tri_emit, nb, 128, 0, st)(X, ntri, npt, *d_tri_keys, *d_pt_keys, *d_pt_xyz, d_counters + 1);
+    if (!rc && st_tri) {
+        int64_t *redo = nullptr;
+        unsigned long long *nredo = nullptr;
+        rc = gs_alloc((void **)&redo, sizeof(int64_t) * (size_t)n, st);
+        if (!rc) rc = gs_alloc((void **)&nredo, sizeof(unsigned long long), st);
+        if (!rc) {
+            cudaMemsetAsync(nredo, 0, sizeof(unsigned long long), st);
+            GS_LAUNCH(k_tri_copy, nb, 128, 0, st)(n, ntri, npt, st_tri, st_pk, st_xyz, *d_tri_keys, *d_pt_keys,
+                                                 *d_pt_xyz, redo, nredo);
+            GS_LAUNCH(k_tri_emit, nb, 128, 0, st)(X, ntri, npt, *d_tri_keys, *d_pt_keys, *d_pt_xyz, nullptr, redo,
+                                                 nredo);
+        }
+        gs_free(redo, st); gs_free(nredo, st);
+    } else if (!rc) {
+        GS_LAUNCH(k_tri_emit, nb, 128, 0, st)(X, ntri, npt, *d_tri_keys, *d_pt_keys, *d_pt_xyz, d_counters + 1,
+                                             nullptr, nullptr);
+    }
+    gs_free(st_tri, st); gs_free(st_pk, st); gs_free(st_xyz, st);
     gs_free(ntri, st); gs_free(npt, st); gs_free(tot, st);
     if (rc) return rc;
     GS_CHECK(cudaGetLastError());
