@@ -272,7 +272,8 @@ def main():
         "level_ms": st["ms_level"][:4],
         "recheck": {"cubes": st["recheck_cubes"], "vertices": st["recheck_vertices"],
                     "bounds": st["recheck_bounds"], "precision": st["recheck_precision"],
-                    "zero": st["recheck_zero"]},
+                    "zero": st["recheck_zero"], "rank": st["recheck_rank"],
+                    "vertex_mark_cubes": st["vertex_mark_cubes"]},
         "pair_terms": pairs, "vertex_terms": st["vertex_terms"],
         "roofline": roofline,
         "clocks": clk,

@@ -84,6 +84,9 @@ typedef struct {
     int64_t recheck_bounds, recheck_precision, recheck_zero; /* mixed mode: why cubes were re-evaluated */
     double mixed_err_ratio;    /* debug bit 0: largest |A_fp32 - A_fp64| / E observed */
     double mixed_band_ratio;   /* debug bit 0: largest |dL|,|dU| / ((dA + 1e-7 sum|A|)(1 + s)) observed */
+    int64_t recheck_rank;      /* mixed mode: of recheck_bounds, cubes flagged only through a rank rule near its threshold */
+    int64_t vertex_mark_cubes[3]; /* mixed mode: surface cubes whose corners were re-evaluated in FP64 because the
+                                     FP32 bound could move an edge point, flip a face saddle, move a fold root */
 } gs_stats;
 
 typedef struct {

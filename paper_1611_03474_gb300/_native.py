@@ -34,14 +34,16 @@ class Stats(ctypes.Structure):
                 ("n_accum_launches", ctypes.c_int64), ("atom_octets", ctypes.c_int64),
                 ("n_kernel_launches", ctypes.c_int64), ("recheck_bounds", ctypes.c_int64),
                 ("recheck_precision", ctypes.c_int64), ("recheck_zero", ctypes.c_int64),
-                ("mixed_err_ratio", ctypes.c_double), ("mixed_band_ratio", ctypes.c_double)]
+                ("mixed_err_ratio", ctypes.c_double), ("mixed_band_ratio", ctypes.c_double),
+                ("recheck_rank", ctypes.c_int64), ("vertex_mark_cubes", ctypes.c_int64 * 3)]
 
     def as_dict(self, max_depth=20):
         d = {}
         for name, _ in self._fields_:
             v = getattr(self, name)
             if isinstance(v, ctypes.Array):
-                v = [v[i] for i in range(max_depth + 1)]
+                # per-level arrays (21 entries) are cut to the levels used
+                v = [v[i] for i in range(max_depth + 1 if len(v) == 21 else len(v))]
             d[name] = v
         return d
 

@@ -556,7 +556,7 @@ static int mesh_impl(const double *atoms, const double *radii, int64_t n, double
             X.cubes = cubes; X.cvid = cvid; X.phi = phi; X.ncubes = nc; X.c = P.c;
             for (int a3 = 0; a3 < 3; a3++) X.origin[a3] = P.origin[a3];
             X.min_edge = P.min_edge; X.max_depth = P.max_depth;
-            rc = gs_tri_marks(X, err, 8e-6, mark, st);
+            rc = gs_tri_marks(X, err, 8e-6, mark, d_cnt + 21, st);
         }
         if (!rc) rc = gs_field_recompute(P, vkeys, nv, mark, phi, err, &nre2, st);
         nre += nre2;
@@ -581,6 +581,8 @@ static int mesh_impl(const double *atoms, const double *radii, int64_t n, double
     stats->recheck_bounds = (int64_t)h[15];
     stats->recheck_precision = (int64_t)h[16];
     stats->recheck_zero = (int64_t)h[17];
+    stats->recheck_rank = (int64_t)h[20];
+    for (int k = 0; k < 3; k++) stats->vertex_mark_cubes[k] = (int64_t)h[21 + k];
     {
         unsigned bits = (unsigned)(h[18] & 0xffffffffull);
         float r;

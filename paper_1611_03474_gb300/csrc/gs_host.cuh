@@ -81,7 +81,10 @@ struct TriCtx {
 };
 // mixed precision: mark (mark[v] = 1) the corners whose FP32 error could move
 // a surface point by more than tol_A or flip a face or fold decision
-int gs_tri_marks(const TriCtx &X, const float *d_err, double tol_A, int64_t *d_mark, cudaStream_t st);
+// d_why (nullable) counts the cubes marked through an edge point, a face
+// saddle and a fold root
+int gs_tri_marks(const TriCtx &X, const float *d_err, double tol_A, int64_t *d_mark, unsigned long long *d_why,
+                 cudaStream_t st);
 // counters: [0] cubes skipped for an inconsistency, [1] degenerate ears, [2] surface cubes
 int gs_triangulate(const TriCtx &X, uint64_t **d_tri_keys, int64_t *ntri_total, uint64_t **d_pt_keys,
                    double **d_pt_xyz, int64_t *npt_total, unsigned long long *d_counters, cudaStream_t st);

@@ -496,6 +496,41 @@ __device__ __forceinline__ int rank99(const T (&s)[4], T &margin)
     return r;
 }
 
+// Where the 99% rules could go the other way.  A rule j compares
+// sum_{i<=j} s_i with 0.99 sum s; the rules that decide the rank are those up
+// to the chosen one, and the one after it (if the chosen rule flipped, the
+// next one would decide).  RankNear records the rule nearest its threshold,
+// the rank it would give if it flipped, and the second-smallest distance.
+template <typename T>
+struct RankNear {
+    T m1, m2;      // smallest and second-smallest distance of a rule from its threshold
+    int who;       // -1: outer rule; i >= 0: inner rule of kept term i
+    int alt;       // rank that rule gives if it flips (0: none)
+};
+
+template <typename T>
+__device__ __forceinline__ void rank_near(const T (&s)[4], int r, int who, RankNear<T> &rn)
+{
+    T tot = s[0] + s[1] + s[2] + s[3];
+    T acc = 0;
+    T thr = T(0.99) * tot;
+    for (int j = 0; j < 4 && j <= r; j++) {
+        acc += s[j];
+        T m = t_abs(acc - thr);
+        // flipping rule j: below -> rank j+1; at or above -> the next rule decides
+        int alt = acc >= thr ? j + 2 : j + 1;
+        if (j == 3) alt = 0;
+        if (m < rn.m1) {
+            rn.m2 = rn.m1;
+            rn.m1 = m;
+            rn.who = who;
+            rn.alt = alt > 4 ? 0 : alt;
+        } else if (m < rn.m2) {
+            rn.m2 = m;
+        }
+    }
+}
+
 // bounds: out = (L, U, sum|R|, sum|high|, rank, inner ranks); rmargin = the
 // smallest distance of a rank rule from its 99% threshold
 template <typename T>
@@ -515,8 +550,11 @@ __device__ __forceinline__ T gap_sens(const T (&s)[4], int kept)
     return r < T(1e6) ? r : T(1e6);
 }
 
+// fo > 0 forces the outer rank; fi >= 0 forces the inner rank of kept term
+// fi to fj; rn (nullable) collects the rules near their thresholds
 template <typename T>
-__device__ void estimate_bounds_sens(const T *A, T *out, T &rmargin, T &sens);
+__device__ __forceinline__ void estimate_bounds_sens(const T *A, T *out, T &rmargin, T &sens, int fo = 0, int fi = -1,
+                                                     int fj = 0, RankNear<T> *rn = nullptr);
 
 template <typename T>
 __device__ void estimate_bounds(const T *A, T *out, T &rmargin)
@@ -526,7 +564,8 @@ __device__ void estimate_bounds(const T *A, T *out, T &rmargin)
 }
 
 template <typename T>
-__device__ void estimate_bounds_sens(const T *A, T *out, T &rmargin, T &sens)
+__device__ __forceinline__ void estimate_bounds_sens(const T *A, T *out, T &rmargin, T &sens, int fo, int fi, int fj,
+                                                     RankNear<T> *rn)
 {
     T X[4][16];
     T high = 0, tot = 0;
@@ -547,6 +586,12 @@ __device__ void estimate_bounds_sens(const T *A, T *out, T &rmargin, T &sens)
     jacobi4<T, 16>(X, s, u);
     T rm;
     int jr = rank99(s, rm);
+    if (fo > 0) {
+        jr = fo;
+        rm = T(1e30);
+    } else if (rn) {
+        rank_near<T>(s, jr, -1, *rn);
+    }
     rmargin = rm;
     sens = gap_sens<T>(s, jr);
     T At[64];
@@ -563,7 +608,12 @@ __device__ void estimate_bounds_sens(const T *A, T *out, T &rmargin, T &sens)
         jacobi4<T, 4>(V, d, w);
         T rmi;
         int ji = rank99(d, rmi);
-        rmargin = rmi < rmargin ? rmi : rmargin;
+        if (i == fi) {
+            ji = fj;
+        } else {
+            rmargin = rmi < rmargin ? rmi : rmargin;
+            if (rn) rank_near<T>(d, ji, i, *rn);
+        }
         T si = gap_sens<T>(d, ji);
         sens = si > sens ? si : sens;
         inner += ji;
@@ -1018,28 +1068,42 @@ __global__ void __launch_bounds__(128) k_estimate_f32(GsProblem P, int level, co
     for (int t = 0; t < 64; t++) { a[t] = A[q * 64 + t]; tot += fabsf(a[t]); }
     float b[6], rm;
     float sens;
-    estimate_bounds_sens<float>(a, b, rm, sens);
+    RankNear<float> rn;
+    rn.m1 = rn.m2 = 1e30f; rn.who = -1; rn.alt = 0;
+    estimate_bounds_sens<float>(a, b, rm, sens, 0, -1, 0, &rn);
     const float c = (float)P.c, prec = (float)P.precision;
     int d = decide<float>(b, c, prec, level, P.max_depth);
     float dA = MIXED_KAPPA * E[q] + 1e-7f * tot;
     bool f = false;
-    int why = 0;
+    int why = 0, alt = 0;
     if (tot > 0.f) {
         // calibrated: the largest |dL|, |dU| seen between the FP32 and FP64
-        // estimates (debug mode, chain and globular molecules) is 0.45 of
-        // (dA + 1e-7 sum|A|)(1 + s) with kappa = 3e-6; the band takes 4 of
-        // it with kappa = 1.5e-6 (about 9x the largest change seen)
-        float bLU = 4.f * (dA + 1e-7f * tot) * (1.f + fminf(sens, 1e4f));
-        // a rank rule within its band may flip: one component of size at
-        // most ~1% of sum(sigma) <= tot moves between the main part and R
-        if (rm <= 32.f * dA + 1e-5f * tot) bLU += 0.16f * tot;
+        // estimates (debug mode, chain and globular molecules) is 0.85 of
+        // (dA + 1e-7 sum|A|)(1 + s); the band takes 4 of it
+        const float bBase = 4.f * (dA + 1e-7f * tot) * (1.f + fminf(sens, 1e4f));
         float mc = fminf(fabsf(c - b[0]), fabsf(b[1] - c));
         bool keep = b[0] <= c && c <= b[1];
-        if (mc <= bLU) { f = true; why = 1; }
-        else if (keep && level < P.max_depth && fabsf(prec - b[3]) <= 64.f * dA + 1e-6f * b[3] + 1e-7f * tot) {
+        const float near = 32.f * dA + 1e-5f * tot;
+        if (mc <= bBase) {
+            f = true;
+            why = 1;
+        } else if (rn.m1 <= near) {
+            // a rank rule within its band may flip.  With one such rule the
+            // cube is re-estimated under the flipped rank (k_estimate_alt);
+            // with more, FP64 decides.
+            if (rn.m2 > near && rn.alt > 0) {
+                alt = 0x80 | ((rn.who + 1) << 3) | rn.alt;
+            } else {
+                f = true;
+                why = 1;
+                if (why_cnt) atomicAdd(&why_cnt[5], 1ull);   // flagged through a rank rule
+            }
+        }
+        if (!f && keep && level < P.max_depth && fabsf(prec - b[3]) <= 64.f * dA + 1e-6f * b[3] + 1e-7f * tot) {
             f = true;
             why = 2;
         }
+        if (f) alt = 0;
     } else if (E[q] > 0.f) {
         f = true;  // an all-zero FP32 tensor with contributing atoms: let FP64 decide
         why = 3;
@@ -1048,10 +1112,57 @@ __global__ void __launch_bounds__(128) k_estimate_f32(GsProblem P, int level, co
     if (dbg) {
         float *o = dbg + 6 * q;
         o[0] = b[0]; o[1] = b[1]; o[2] = sens; o[3] = dA; o[4] = tot;
-        o[5] = (tot > 0.f && rm <= 32.f * dA + 1e-5f * tot) ? 1.f : 0.f;
+        o[5] = (tot > 0.f && rn.m1 <= 32.f * dA + 1e-5f * tot) ? 1.f : 0.f;
     }
     dec[q] = (uint8_t)d;
-    flag[q] = f ? 1 : 0;
+    flag[q] = f ? 1 : (uint8_t)alt;
+}
+
+// cubes whose FP32 decision rests on one rank rule near its threshold
+// (flag 0x80 | (rule + 1) << 3 | flipped rank) -> a compact list
+__global__ void k_alt_list(const uint8_t *flag, int64_t n, int32_t *list, unsigned *nlist)
+{
+    int64_t q = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    bool on = q < n && (flag[q] & 0x80);
+    unsigned bal = __ballot_sync(0xffffffffu, on);
+    if (!bal) return;
+    unsigned lane = threadIdx.x & 31, base = 0;
+    if (lane == 0) base = atomicAdd(nlist, (unsigned)__popc(bal));
+    base = __shfl_sync(0xffffffffu, base, 0);
+    if (on) list[base + __popc(bal & ((1u << lane) - 1u))] = (int32_t)q;
+}
+
+// the listed cubes re-estimated under the flipped rank: the decision stands
+// (flag 0) when it is the same with a margin outside the band and no other
+// rule of the flipped estimate is near its threshold; otherwise FP64 decides
+__global__ void __launch_bounds__(128) k_estimate_alt(GsProblem P, int level, const float *__restrict__ A,
+                                                      const float *__restrict__ E, const int32_t *__restrict__ list,
+                                                      const unsigned *nlist, const uint8_t *__restrict__ dec,
+                                                      uint8_t *__restrict__ flag, unsigned long long *why_cnt)
+{
+    const int64_t nl = (int64_t)*nlist;
+    for (int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; t < nl; t += (int64_t)gridDim.x * blockDim.x) {
+    int64_t q = list[t];
+    const unsigned code = flag[q];
+    const int who = (int)((code >> 3) & 7u) - 1, altr = (int)(code & 7u);
+    float a[64];
+    float tot = 0.f;
+#pragma unroll
+    for (int k = 0; k < 64; k++) { a[k] = A[q * 64 + k]; tot += fabsf(a[k]); }
+    const float c = (float)P.c, prec = (float)P.precision;
+    const float dA = MIXED_KAPPA * E[q] + 1e-7f * tot;
+    float b2[6], rm2, sens2;
+    estimate_bounds_sens<float>(a, b2, rm2, sens2, who < 0 ? altr : 0, who, who < 0 ? 0 : altr, nullptr);
+    const float bAlt = 4.f * (dA + 1e-7f * tot) * (1.f + fminf(sens2, 1e4f));
+    const float mc2 = fminf(fabsf(c - b2[0]), fabsf(b2[1] - c));
+    const bool ok = rm2 > 32.f * dA + 1e-5f * tot && decide<float>(b2, c, prec, level, P.max_depth) == (int)dec[q] &&
+                    mc2 > bAlt;
+    flag[q] = ok ? 0 : 1;
+    if (!ok && why_cnt) {
+        atomicAdd(&why_cnt[0], 1ull);
+        atomicAdd(&why_cnt[5], 1ull);
+    }
+    }
 }
 
 int gs_estimate_f32(const GsProblem &P, int level, const float *d_A, const float *d_err, int64_t n_cubes,
@@ -1170,6 +1281,20 @@ int gs_level_mixed(const GsProblem &P, int level, const uint64_t *d_parents, int
     if (!rc && both) rc = gs_alloc((void **)&dbg, sizeof(float) * 6 * 8 * (size_t)n_oct, st);
     if (!rc) rc = gs_accum_f32(P, level, d_parents, nullptr, n_oct, A, E, d_pairs, d_status, st, ms);
     if (!rc) rc = gs_estimate_f32(P, level, A, E, n_oct * 8, d_parents, nullptr, d_dec, flag, st, d_why, dbg);
+    if (!rc) {
+        // decisions resting on one rank rule near its threshold
+        int32_t *lst = nullptr;
+        unsigned *nl = nullptr;
+        rc = gs_alloc((void **)&lst, sizeof(int32_t) * 8 * (size_t)n_oct, st);
+        if (!rc) rc = gs_alloc((void **)&nl, sizeof(unsigned), st);
+        if (!rc) {
+            unsigned nb = (unsigned)((n_oct * 8 + 127) / 128);
+            cudaMemsetAsync(nl, 0, sizeof(unsigned), st);
+            GS_LAUNCH(k_alt_list, nb, 128, 0, st)(flag, n_oct * 8, lst, nl);
+            GS_LAUNCH(k_estimate_alt, 152 * 4, 128, 0, st)(P, level, A, E, lst, nl, d_dec, flag, d_why);
+        }
+        gs_free(lst, st); gs_free(nl, st);
+    }
     // flagged octets -> FP64
     int64_t *cnt = nullptr, *tot = nullptr;
     if (!rc) rc = gs_alloc((void **)&cnt, sizeof(int64_t) * (size_t)(n_oct + 1), st);

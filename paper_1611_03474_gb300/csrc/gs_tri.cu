@@ -46,7 +46,9 @@ __device__ __forceinline__ void axes_other(int a, int &u, int &v)
 __device__ __forceinline__ double corner(const double *g, int bx, int by, int bz) { return g[bx + 2 * by + 4 * bz]; }
 
 // roots (u,v) in the open unit square of {B = 0, A = c} for g = A + s B along axis a
-__device__ __noinline__ int fold_solve(const double *g, int a, double c, double *ru, double *rv)
+// roots (u, v) of the fold line of axis a in (0,1)^2 (in (-slack, 1+slack)^2
+// when slack > 0, for the error marks)
+__device__ __noinline__ int fold_solve(const double *g, int a, double c, double *ru, double *rv, double slack = 0.0)
 {
     int ua, va;
     axes_other(a, ua, va);
@@ -93,7 +95,7 @@ __device__ __noinline__ int fold_solve(const double *g, int a, double c, double 
     int nr = 0;
     for (int i = 0; i < nu; i++) {
         double u = us[i];
-        if (!(u > 0.0 && u < 1.0)) continue;
+        if (!(u > -slack && u < 1.0 + slack)) continue;
         double denB = q2 + q3 * u, denA = p2 + p3 * u;
         double cand0, cand1;
         bool h0, h1;
@@ -107,7 +109,7 @@ __device__ __noinline__ int fold_solve(const double *g, int a, double c, double 
         for (int t = 0; t < 2; t++) {
             bool has = t ? h1 : h0;
             double v = t ? cand1 : cand0;
-            if (!has || !(v > 0.0 && v < 1.0)) continue;
+            if (!has || !(v > -slack && v < 1.0 + slack)) continue;
             if (fabs(p0 + p1 * u + p2 * v + p3 * u * v) > 1e-9 * sp) continue;
             if (fabs(q0 + q1 * u + q2 * v + q3 * u * v) > 1e-9 * sq_) continue;
             ru[nr] = u; rv[nr] = v; nr++;
@@ -666,14 +668,15 @@ int gs_triangulate(const TriCtx &X, uint64_t **d_tri_keys, int64_t *ntri_total, 
 }
 
 // ---------------------------------------------------------------- mixed precision marks
-// For a surface cube with FP32 corner values g and bounds e: an edge point
-// moves by at most h (e0 + e1) / |g1 - g0| (first order); a face's saddle
+// For a surface cube with FP32 corner values g and bounds e: an edge point at
+// t = (c - g0) / (g1 - g0) moves by at most h ((1 - t) e0 + t e1) / |g1 - g0|
+// (first order); a face's saddle
 // decision is safe when |h_s - c| exceeds the bound carried through h_s; a
 // fold root (extreme and critical points) moves by at most the first-order
 // bound from the root's derivative.  Where any bound exceeds tol the corners
 // involved (all eight for a fold) are re-evaluated in FP64.
 __global__ void __launch_bounds__(128) k_tri_marks(TriCtx X, const float *__restrict__ err, double tol,
-                                                   int64_t *__restrict__ mark)
+                                                   int64_t *__restrict__ mark, unsigned long long *why)
 {
     int64_t ci = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (ci >= X.ncubes) return;
@@ -691,7 +694,7 @@ __global__ void __launch_bounds__(128) k_tri_marks(TriCtx X, const float *__rest
     int nin = 0;
     for (int v = 0; v < 8; v++) nin += g[v] >= c;
     if (nin == 0 || nin == 8) return;
-    bool all = false;
+    bool all = false, r_edge = false, r_face = false;
     unsigned m = 0;
     for (int a = 0; a < 3 && !all; a++) {
         int ua, va;
@@ -701,7 +704,9 @@ __global__ void __launch_bounds__(128) k_tri_marks(TriCtx X, const float *__rest
             b0[a] = 0; b1[a] = 1; b0[ua] = b1[ua] = k & 1; b0[va] = b1[va] = k >> 1;
             int v0 = b0[0] + 2 * b0[1] + 4 * b0[2], v1 = b1[0] + 2 * b1[1] + 4 * b1[2];
             if ((g[v0] >= c) == (g[v1] >= c)) continue;
-            if (h * (e[v0] + e[v1]) > tol * fabs(g[v1] - g[v0])) m |= (1u << v0) | (1u << v1);
+            // t = (c - g0) / (g1 - g0) moves by ((1 - t) e0 + t e1) / |g1 - g0| to first order
+            double dg = fabs(g[v1] - g[v0]), t = fabs(c - g[v0]) / dg;
+            if (h * ((1.0 - t) * e[v0] + t * e[v1]) > tol * dg) { m |= (1u << v0) | (1u << v1); r_edge = true; }
         }
         for (int sd = 0; sd < 2; sd++) {
             double hf[4];
@@ -721,52 +726,66 @@ __global__ void __launch_bounds__(128) k_tri_marks(TriCtx X, const float *__rest
                 for (int k = 0; k < 4; k++) eb += e[fv[k]];
                 // h_s = (h0 h3 - h1 h2) / den: each value enters with weight <= 2 max|h| / |den|
                 double amp = 2.0 * (fabs(hf[0]) + fabs(hf[1]) + fabs(hf[2]) + fabs(hf[3])) / fabs(den);
-                if (fabs(hs - c) <= 4.0 * amp * eb) for (int k = 0; k < 4; k++) m |= 1u << fv[k];
+                if (fabs(hs - c) <= 4.0 * amp * eb) {
+                    for (int k = 0; k < 4; k++) m |= 1u << fv[k];
+                    r_face = true;
+                }
             }
         }
         double ru[2], rv[2];
-        int nr = fold_solve(g, a, c, ru, rv);
+        int nr = fold_solve(g, a, c, ru, rv, 1e-3);
         if (nr > 0) {
-            // first-order error of the fold roots (u*, v*) of
-            // Q(u) = (a0 + a1 u)(b2 + b3 u) - (a2 + a3 u)(b0 + b1 u), v = -(b0 + b1 u)/(b2 + b3 u):
-            // each monomial coefficient moves by at most 8 max(e) (4 for A, 8 for B = upper - lower)
-            double lo4[4], up4[4], em = 0;
+            // A = lower face - c, B = upper - lower (bilinear in u, v); a root
+            // solves A = B = 0.  Corner errors move A and B at the root by at
+            // most sum_k b_k e_k (bilinear weights b_k summing to 1), and the
+            // root by J^-1 of that (J the Jacobian of (A, B) in (u, v)).
+            double lo4[4], up4[4], elo[4], eup[4];
             for (int k = 0; k < 4; k++) {
                 int b[3];
                 b[a] = 0; b[ua] = k & 1; b[va] = k >> 1;
                 lo4[k] = g[b[0] + 2 * b[1] + 4 * b[2]];
-                em = fmax(em, e[b[0] + 2 * b[1] + 4 * b[2]]);
+                elo[k] = e[b[0] + 2 * b[1] + 4 * b[2]];
                 b[a] = 1;
                 up4[k] = g[b[0] + 2 * b[1] + 4 * b[2]];
-                em = fmax(em, e[b[0] + 2 * b[1] + 4 * b[2]]);
+                eup[k] = e[b[0] + 2 * b[1] + 4 * b[2]];
             }
-            double p0 = lo4[0] - c, p1 = lo4[1] - lo4[0], p2 = lo4[2] - lo4[0], p3 = lo4[3] - lo4[1] - lo4[2] + lo4[0];
+            double p1 = lo4[1] - lo4[0], p2 = lo4[2] - lo4[0], p3 = lo4[3] - lo4[1] - lo4[2] + lo4[0];
             double d0 = up4[0] - lo4[0], d1 = up4[1] - lo4[1], d2 = up4[2] - lo4[2], d3 = up4[3] - lo4[3];
-            double q0 = d0, q1 = d1 - d0, q2 = d2 - d0, q3 = d3 - d1 - d2 + d0;
-            double SA = fabs(p0) + fabs(p1) + fabs(p2) + fabs(p3), SB = fabs(q0) + fabs(q1) + fabs(q2) + fabs(q3);
-            // |dQ| <= 2 (8 em SB + 16 em SA) for u in [0, 1]
-            double dQ = 16.0 * em * (2.0 * SA + SB);
+            double q1 = d1 - d0, q2 = d2 - d0, q3 = d3 - d1 - d2 + d0;
             for (int r = 0; r < nr && !all; r++) {
                 double u = ru[r], v = rv[r];
-                // |Q'(u)| from the product rule
-                double dQu = p1 * (q2 + q3 * u) + (p0 + p1 * u) * q3 - p3 * (q0 + q1 * u) - (p2 + p3 * u) * q1;
-                double den = q2 + q3 * u;
-                double du = fabs(dQu) > 0 ? dQ / fabs(dQu) : 1e30;
-                double dv = fabs(den) > 0 ? (16.0 * em * (1.0 + fabs(v)) + (fabs(q1) + fabs(q3) * fabs(v)) * du) / fabs(den)
-                                          : 1e30;
+                double w[4] = {(1 - u) * (1 - v), u * (1 - v), (1 - u) * v, u * v};
+                double dA = 0, dB = 0;
+                for (int k = 0; k < 4; k++) {
+                    dA += fabs(w[k]) * elo[k];
+                    dB += fabs(w[k]) * (elo[k] + eup[k]);
+                }
+                double J11 = p1 + p3 * v, J12 = p2 + p3 * u, J21 = q1 + q3 * v, J22 = q2 + q3 * u;
+                double det = fabs(J11 * J22 - J12 * J21);
+                double du = det > 0 ? (fabs(J22) * dA + fabs(J12) * dB) / det : 1e30;
+                double dv = det > 0 ? (fabs(J21) * dA + fabs(J11) * dB) / det : 1e30;
+                // the position, and whether the root is inside the face square
                 if (h * (du + dv) > tol) all = true;
+                if (fmin(fabs(u), fabs(1.0 - u)) <= 4.0 * du || fmin(fabs(v), fabs(1.0 - v)) <= 4.0 * dv) all = true;
             }
         }
     }
     if (all) m = 0xFF;
     for (int v = 0; v < 8; v++)
         if ((m >> v) & 1) mark[vid[v]] = 1;
+    if (why) {
+        // cubes marked through an edge point, a face saddle, a fold root
+        if (r_edge) atomicAdd(&why[0], 1ull);
+        if (r_face) atomicAdd(&why[1], 1ull);
+        if (all) atomicAdd(&why[2], 1ull);
+    }
 }
 
-int gs_tri_marks(const TriCtx &X, const float *d_err, double tol_A, int64_t *d_mark, cudaStream_t st)
+int gs_tri_marks(const TriCtx &X, const float *d_err, double tol_A, int64_t *d_mark, unsigned long long *d_why,
+                 cudaStream_t st)
 {
     if (X.ncubes <= 0) return GS_OK;
-    GS_LAUNCH(k_tri_marks, (unsigned)((X.ncubes + 127) / 128), 128, 0, st)(X, d_err, tol_A, d_mark);
+    GS_LAUNCH(k_tri_marks, (unsigned)((X.ncubes + 127) / 128), 128, 0, st)(X, d_err, tol_A, d_mark, d_why);
     GS_CHECK(cudaGetLastError());
     return GS_OK;
 }

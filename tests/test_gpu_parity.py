@@ -151,7 +151,7 @@ def test_mixed_decisions_match_fp64_everywhere(chain100):
                                  min_edge=cfg["min_edge"], precision_mode=gs.GS_PREC_MIXED, debug_flags=1)
     st = m.stats
     print("recheck", st["recheck_cubes"], "of", sum(st["examined"]), "reasons", st["recheck_bounds"],
-          st["recheck_precision"], st["recheck_zero"], "max |A32-A64|/E", st["mixed_err_ratio"],
+          st["recheck_precision"], st["recheck_zero"], "rank", st["recheck_rank"], "max |A32-A64|/E", st["mixed_err_ratio"],
           "band ratio", st["mixed_band_ratio"], "vertices rechecked", st["recheck_vertices"])
     assert m.mismatches == 0
     # the FP32 error stays inside the band's kappa (1.5e-6)
