@@ -24,6 +24,10 @@ __device__ __forceinline__ void point_of(const GsProblem &P, const uint64_t *vke
     }
 }
 
+// FP64 field.  Candidates are screened with the FP32 distance (two-float
+// offsets from the origin) and a relative margin; inside the margin the
+// membership is the exact FP64 test.  t = w exp(-D d^2) with w = exp(D r^2).
+template <bool GRAD>
 __global__ void __launch_bounds__(128) k_field_f64(GsProblem P, const uint64_t *vkeys, const double *pts, int64_t n,
                                                    double *__restrict__ phi, double *__restrict__ grad,
                                                    unsigned long long *terms)
@@ -34,25 +38,36 @@ __global__ void __launch_bounds__(128) k_field_f64(GsProblem P, const uint64_t *
         double p[3];
         point_of(P, vkeys, pts, i, p);
         double s = 0, g0 = 0, g1 = 0, g2 = 0;
-        const double m2D = -2.0 * P.D;
-        float pr[3];
-        for (int a = 0; a < 3; a++) pr[a] = (float)(p[a] - P.origin[a]);
-        gs_for_rows(P, pr, pr, [&](int b, int e, int64_t, int) {
+        const double m2D = -2.0 * P.D, nD = -P.D;
+        float ph[3], pl[3];
+        for (int a = 0; a < 3; a++) {
+            double rel = p[a] - P.origin[a];
+            ph[a] = (float)rel;
+            pl[a] = (float)(rel - (double)ph[a]);
+        }
+        gs_for_rows(P, ph, ph, [&](int b, int e, int64_t, int) {
             for (int k = b; k < e; k++) {
+                float fx = (ph[0] - P.hx[k]) + (pl[0] - P.lx[k]);
+                float fy = (ph[1] - P.hy[k]) + (pl[1] - P.ly[k]);
+                float fz = (ph[2] - P.hz[k]) + (pl[2] - P.lz[k]);
+                float f2 = fx * fx + fy * fy + fz * fz;
+                const float R2 = P.fR2[k];
+                if (f2 > R2 * (1.f + 1e-5f) + 1e-5f) continue;
                 double dx = __dsub_rn(p[0], P.ax[k]), dy = __dsub_rn(p[1], P.ay[k]), dz = __dsub_rn(p[2], P.az[k]);
                 double d2 = __dadd_rn(__dadd_rn(__dmul_rn(dx, dx), __dmul_rn(dy, dy)), __dmul_rn(dz, dz));
                 if (d2 > P.aR2[k]) continue;
-                double r = P.ar[k];
-                double t = exp(-P.D * (d2 - r * r));
+                double t = P.aw[k] * exp(nD * d2);
                 s += t;
-                g0 = fma(m2D * dx, t, g0);
-                g1 = fma(m2D * dy, t, g1);
-                g2 = fma(m2D * dz, t, g2);
+                if (GRAD) {
+                    g0 = fma(m2D * dx, t, g0);
+                    g1 = fma(m2D * dy, t, g1);
+                    g2 = fma(m2D * dz, t, g2);
+                }
                 cnt++;
             }
         });
         phi[i] = s;
-        if (grad) { grad[3 * i] = g0; grad[3 * i + 1] = g1; grad[3 * i + 2] = g2; }
+        if (GRAD) { grad[3 * i] = g0; grad[3 * i + 1] = g1; grad[3 * i + 2] = g2; }
     }
     if (terms) {
         for (int o = 16; o > 0; o >>= 1) cnt += __shfl_xor_sync(0xffffffffu, cnt, o);
@@ -122,7 +137,12 @@ int gs_field_f64(const GsProblem &P, const uint64_t *d_vkeys, const double *d_po
                  double *d_grad, unsigned long long *d_terms, cudaStream_t st)
 {
     if (n <= 0) return GS_OK;
-    GS_LAUNCH(k_field_f64, (unsigned)((n + 127) / 128), 128, 0, st)(P, d_vkeys, d_points, n, d_phi, d_grad, d_terms);
+    if (d_grad)
+        GS_LAUNCH(k_field_f64<true>, (unsigned)((n + 127) / 128), 128, 0, st)(P, d_vkeys, d_points, n, d_phi, d_grad,
+                                                                             d_terms);
+    else
+        GS_LAUNCH(k_field_f64<false>, (unsigned)((n + 127) / 128), 128, 0, st)(P, d_vkeys, d_points, n, d_phi, d_grad,
+                                                                              d_terms);
     GS_CHECK(cudaGetLastError());
     return GS_OK;
 }

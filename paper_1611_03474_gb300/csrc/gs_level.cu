@@ -22,14 +22,14 @@
 
 // ---------------------------------------------------------------- quadrature
 // Gauss-Legendre nodes t_k and folded weights W_kj = (2j+1)/2 * w_k * L_j(t_k),
-// so that alpha_j = sum_k W_kj f(t_k).  Variants with 8, 12, 16, 24 and 6 nodes.
-#define GQ_VARIANTS 5
+// so that alpha_j = sum_k W_kj f(t_k).  Variants with 8, 12, 16, 24, 6 and 5 nodes.
+#define GQ_VARIANTS 6
 #define GQ_MAX 24
 __constant__ double c_gq_t[GQ_VARIANTS][GQ_MAX];
 __constant__ double c_gq_W[GQ_VARIANTS][GQ_MAX][4];
 __constant__ float c_gq_tf[GQ_VARIANTS][GQ_MAX];
 __constant__ float c_gq_Wf[GQ_VARIANTS][GQ_MAX][4];
-static const int kGqN[GQ_VARIANTS] = {8, 12, 16, 24, 6};
+static const int kGqN[GQ_VARIANTS] = {8, 12, 16, 24, 6, 5};
 
 // nodes of P_n as eigen-free Newton iteration in long double, started from
 // Tricomi's asymptotic estimate
@@ -94,8 +94,9 @@ int gs_quadrature_init(void)
 static int gq_variant(double D, double hh, bool fp32)
 {
     double a = sqrt(D) * hh;
-    // FP32: quadrature error below ~1e-7 of the factor's maximum
-    if (fp32) return a <= 0.5 ? 4 : (a <= 1.0 ? 0 : (a <= 1.5 ? 1 : 2));
+    // FP32: quadrature error of each coefficient below 2e-7 of the Gaussian's
+    // peak (5 nodes: 3e-8 up to a = 0.2; 6 nodes: 2e-7 up to 0.5)
+    if (fp32) return a <= 0.2 ? 5 : (a <= 0.5 ? 4 : (a <= 1.0 ? 0 : (a <= 1.5 ? 1 : 2)));
     if (a <= 0.25) return 0;
     if (a <= 0.75) return 1;
     if (a <= 1.0) return 2;
@@ -802,9 +803,14 @@ int gs_root_blocks(const GsProblem &P, uint64_t **d_keys, int64_t *n, cudaStream
 // w * Fx * Fy * Fz (F = the largest value of the atom's 1-D factor on the
 // cube's interval), an upper bound of every term's size from which the
 // error band of the FP32 tensor is derived.
-#define ACF_W 24
-#define ACF_F 25
-#define ACF_STRIDE 36   // 144 B per atom: 16-byte aligned rows for float4 loads
+// Per queued atom the coefficient lane writes the products the update needs:
+// WXY[cx][j][cy][k] = w X_cx[j] Y_cy[k] (64), Z[cz][l] (8) and, per child,
+// w Fx Fy Fz (8); the update of lane (child, j) is then two 16-byte loads and
+// 16 FMA per atom.
+#define ACF_WXY 0
+#define ACF_Z 64
+#define ACF_EB 72
+#define ACF_STRIDE 80   // 320 B per atom, 16-byte aligned rows
 
 __global__ void __launch_bounds__(32 * ACC_WARPS, 4) k_accum_f32(GsProblem P, int level, const uint64_t *parents,
                                                                   const uint8_t *vmask, int64_t n_oct, int gv, int nq,
@@ -821,6 +827,7 @@ __global__ void __launch_bounds__(32 * ACC_WARPS, 4) k_accum_f32(GsProblem P, in
     const unsigned below = (1u << lane) - 1u;
     const int c = lane >> 2, j = lane & 3;
     const int cx = c & 1, cy = (c >> 1) & 1, cz = c >> 2;
+    const int oWXY = ACF_WXY + ((cx * 4 + j) * 2 + cy) * 4, oZ = ACF_Z + 4 * cz, oEB = ACF_EB + c;
     const float nDl2e = (float)(-P.D * 1.4426950408889634);
     const float hh = 0.5f * hf;
     for (int64_t o = (int64_t)blockIdx.x * ACC_WARPS + wl; o < n_oct; o += (int64_t)gridDim.x * ACC_WARPS) {
@@ -861,21 +868,26 @@ __global__ void __launch_bounds__(32 * ACC_WARPS, 4) k_accum_f32(GsProblem P, in
         };
 
         // coefficients of the queued atoms (one lane per atom), then the
-        // rank-one updates (lane = child, x index)
+        // rank-one updates (lane = child, x index); nb and the folds are
+        // warp-uniform
         auto process = [&](int nproc) {
             if (lane < nproc) {
                 int i = s_qi[wl][lane];
                 const float ah[3] = {P.hx[i], P.hy[i], P.hz[i]}, al[3] = {P.lx[i], P.ly[i], P.lz[i]};
-                float *cf = s_cf[wl][lane];
+                float cf[3][2][4], F[3][2];
+#pragma unroll
                 for (int a = 0; a < 3; a++) {
                     float d[3], f[3];
+#pragma unroll
                     for (int t = 0; t < 3; t++) {
                         d[t] = (eh[a][t] - ah[a]) + (el[a][t] - al[a]);   // e_t - x
                         f[t] = exp2f(nDl2e * d[t] * d[t]);
                     }
+#pragma unroll
                     for (int hI = 0; hI < 2; hI++) {
                         float m = d[hI] + hh;   // interval centre - x
                         float a0 = 0.f, a1 = 0.f, a2 = 0.f, a3 = 0.f;
+#pragma unroll 1
                         for (int k = 0; k < nq; k++) {
                             float dk = fmaf(hh, c_gq_tf[gv][k], m);
                             float fk = exp2f(nDl2e * dk * dk);
@@ -886,33 +898,56 @@ __global__ void __launch_bounds__(32 * ACC_WARPS, 4) k_accum_f32(GsProblem P, in
                         }
                         float fa = f[hI], fb = f[hI + 1];
                         float eR = fb - (a0 + a1 + a2 + a3), eL = fa - (a0 - a1 + a2 - a3);
-                        cf[8 * a + 4 * hI + 0] = a0;
-                        cf[8 * a + 4 * hI + 1] = a1;
-                        cf[8 * a + 4 * hI + 2] = a2 + 0.5f * (eR + eL);
-                        cf[8 * a + 4 * hI + 3] = a3 + 0.5f * (eR - eL);
+                        cf[a][hI][0] = a0;
+                        cf[a][hI][1] = a1;
+                        cf[a][hI][2] = a2 + 0.5f * (eR + eL);
+                        cf[a][hI][3] = a3 + 0.5f * (eR - eL);
                         bool inside = d[hI] <= 0.f && d[hI + 1] >= 0.f;
-                        cf[ACF_F + 2 * a + hI] = inside ? 1.f : fmaxf(fa, fb);
+                        F[a][hI] = inside ? 1.f : fmaxf(fa, fb);
                     }
                 }
-                cf[ACF_W] = P.fw[i];
+                const float w = P.fw[i];
+                float *rec = s_cf[wl][lane];
+#pragma unroll
+                for (int x = 0; x < 2; x++)
+#pragma unroll
+                    for (int jj = 0; jj < 4; jj++) {
+                        float wx = w * cf[0][x][jj];
+#pragma unroll
+                        for (int y = 0; y < 2; y++) {
+                            float4 v = make_float4(wx * cf[1][y][0], wx * cf[1][y][1], wx * cf[1][y][2], wx * cf[1][y][3]);
+                            *reinterpret_cast<float4 *>(rec + ACF_WXY + ((x * 4 + jj) * 2 + y) * 4) = v;
+                        }
+                    }
+#pragma unroll
+                for (int z = 0; z < 2; z++)
+                    *reinterpret_cast<float4 *>(rec + ACF_Z + 4 * z) =
+                        make_float4(cf[2][z][0], cf[2][z][1], cf[2][z][2], cf[2][z][3]);
+                float e8[8];
+#pragma unroll
+                for (int cc = 0; cc < 8; cc++) e8[cc] = w * F[0][cc & 1] * F[1][(cc >> 1) & 1] * F[2][cc >> 2];
+                *reinterpret_cast<float4 *>(rec + ACF_EB) = make_float4(e8[0], e8[1], e8[2], e8[3]);
+                *reinterpret_cast<float4 *>(rec + ACF_EB + 4) = make_float4(e8[4], e8[5], e8[6], e8[7]);
             }
             __syncwarp();
             for (int t = 0; t < nproc; t++) {
-                if ((s_qm[wl][t] >> c) & 1) {
-                    const float *cf = s_cf[wl][t];
-                    float wa = cf[ACF_W] * cf[4 * cx + j];
-                    const float4 by = *reinterpret_cast<const float4 *>(cf + 8 + 4 * cy);
-                    const float4 gz = *reinterpret_cast<const float4 *>(cf + 16 + 4 * cz);
-                    const float bv[4] = {by.x, by.y, by.z, by.w}, gv4[4] = {gz.x, gz.y, gz.z, gz.w};
-#pragma unroll
-                    for (int k = 0; k < 4; k++) {
-                        float wb = wa * bv[k];
-#pragma unroll
-                        for (int l = 0; l < 4; l++) part[4 * k + l] = fmaf(wb, gv4[l], part[4 * k + l]);
-                    }
-                    eb = fmaf(cf[ACF_W] * cf[ACF_F + cx], cf[ACF_F + 2 + cy] * cf[ACF_F + 4 + cz], eb);
-                    if (++nb == 8) fold();
+                const unsigned mt = s_qm[wl][t];
+                const float *rec = s_cf[wl][t];
+                float4 xy = *reinterpret_cast<const float4 *>(rec + oWXY);
+                const float4 z = *reinterpret_cast<const float4 *>(rec + oZ);
+                float e1 = rec[oEB];
+                if (mt != 0xFFu && !((mt >> c) & 1u)) {
+                    // this atom does not reach this lane's child
+                    xy = make_float4(0.f, 0.f, 0.f, 0.f);
+                    e1 = 0.f;
                 }
+                const float xv[4] = {xy.x, xy.y, xy.z, xy.w}, zv[4] = {z.x, z.y, z.z, z.w};
+#pragma unroll
+                for (int k = 0; k < 4; k++)
+#pragma unroll
+                    for (int l = 0; l < 4; l++) part[4 * k + l] = fmaf(xv[k], zv[l], part[4 * k + l]);
+                eb += e1;
+                if (++nb == 8) fold();
             }
             __syncwarp();
         };
