@@ -78,6 +78,10 @@ struct TriCtx {
     double origin[3];
     double min_edge;
     int max_depth;
+    // fold roots per cube, filled by gs_triangulate before the tracing passes:
+    // fcount[4 ci + a] roots of axis a at froot[12 ci + 4 a + 2 r + (0: u, 1: v)]
+    const uint8_t *fcount = nullptr;
+    const double *froot = nullptr;
 };
 // mixed precision: mark (mark[v] = 1) the corners whose FP32 error could move
 // a surface point by more than tol_A or flip a face or fold decision

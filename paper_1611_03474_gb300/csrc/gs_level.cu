@@ -804,13 +804,15 @@ int gs_root_blocks(const GsProblem &P, uint64_t **d_keys, int64_t *n, cudaStream
 // cube's interval), an upper bound of every term's size from which the
 // error band of the FP32 tensor is derived.
 // Per queued atom the coefficient lane writes the products the update needs:
-// WXY[cx][j][cy][k] = w X_cx[j] Y_cy[k] (64), Z[cz][l] (8) and, per child,
+// WXY[cy][cx][j][k] = w X_cx[j] Y_cy[k] (64), Z[cz][l] (8) and, per child,
 // w Fx Fy Fz (8); the update of lane (child, j) is then two 16-byte loads and
-// 16 FMA per atom.
+// 16 FMA per atom.  The eight lanes of a quarter warp read eight consecutive
+// 16-byte words; the record stride (21 words of 16 bytes) spreads the
+// coefficient lanes' stores over all banks.
 #define ACF_WXY 0
 #define ACF_Z 64
 #define ACF_EB 72
-#define ACF_STRIDE 80   // 320 B per atom, 16-byte aligned rows
+#define ACF_STRIDE 84
 
 __global__ void __launch_bounds__(32 * ACC_WARPS, 4) k_accum_f32(GsProblem P, int level, const uint64_t *parents,
                                                                   const uint8_t *vmask, int64_t n_oct, int gv, int nq,
@@ -827,7 +829,7 @@ __global__ void __launch_bounds__(32 * ACC_WARPS, 4) k_accum_f32(GsProblem P, in
     const unsigned below = (1u << lane) - 1u;
     const int c = lane >> 2, j = lane & 3;
     const int cx = c & 1, cy = (c >> 1) & 1, cz = c >> 2;
-    const int oWXY = ACF_WXY + ((cx * 4 + j) * 2 + cy) * 4, oZ = ACF_Z + 4 * cz, oEB = ACF_EB + c;
+    const int oWXY = ACF_WXY + ((cy * 2 + cx) * 4 + j) * 4, oZ = ACF_Z + 4 * cz, oEB = ACF_EB + c;
     const float nDl2e = (float)(-P.D * 1.4426950408889634);
     const float hh = 0.5f * hf;
     for (int64_t o = (int64_t)blockIdx.x * ACC_WARPS + wl; o < n_oct; o += (int64_t)gridDim.x * ACC_WARPS) {
@@ -916,7 +918,7 @@ __global__ void __launch_bounds__(32 * ACC_WARPS, 4) k_accum_f32(GsProblem P, in
 #pragma unroll
                         for (int y = 0; y < 2; y++) {
                             float4 v = make_float4(wx * cf[1][y][0], wx * cf[1][y][1], wx * cf[1][y][2], wx * cf[1][y][3]);
-                            *reinterpret_cast<float4 *>(rec + ACF_WXY + ((x * 4 + jj) * 2 + y) * 4) = v;
+                            *reinterpret_cast<float4 *>(rec + ACF_WXY + ((y * 2 + x) * 4 + jj) * 4) = v;
                         }
                     }
 #pragma unroll

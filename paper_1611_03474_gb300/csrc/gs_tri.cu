@@ -273,7 +273,15 @@ __device__ int tri_cube(const TriCtx &X, int64_t ci, TriOut &o, unsigned long lo
     int nr[3];
     for (int a = 0; a < 3; a++) {
         double ru[2], rv[2];
-        nr[a] = fold_solve(g, a, c, ru, rv);
+        if (X.fcount) {
+            nr[a] = X.fcount[ci * 4 + a];
+            for (int r = 0; r < nr[a]; r++) {
+                ru[r] = X.froot[ci * 12 + 4 * a + 2 * r];
+                rv[r] = X.froot[ci * 12 + 4 * a + 2 * r + 1];
+            }
+        } else {
+            nr[a] = fold_solve(g, a, c, ru, rv);
+        }
         for (int r = 0; r < nr[a]; r++) { rt[a][r][0] = ru[r]; rt[a][r][1] = rv[r]; }
     }
     // critical points: an a-fold root and a b-fold root that share the third
@@ -319,10 +327,19 @@ __device__ int tri_cube(const TriCtx &X, int64_t ci, TriOut &o, unsigned long lo
         for (int sd = 0; sd < 2; sd++) {
             int nb = X.nbr[ci * 6 + 2 * a + sd];
             if (nb < 0) continue;
-            double gn[8];
-            for (int v = 0; v < 8; v++) gn[v] = X.phi[X.cvid[(int64_t)nb * 8 + v]];
             double nu_[2], nv_[2];
-            int nn = fold_solve(gn, a, c, nu_, nv_);
+            int nn;
+            if (X.fcount) {
+                nn = X.fcount[(int64_t)nb * 4 + a];
+                for (int r = 0; r < nn; r++) {
+                    nu_[r] = X.froot[(int64_t)nb * 12 + 4 * a + 2 * r];
+                    nv_[r] = X.froot[(int64_t)nb * 12 + 4 * a + 2 * r + 1];
+                }
+            } else {
+                double gn[8];
+                for (int v = 0; v < 8; v++) gn[v] = X.phi[X.cvid[(int64_t)nb * 8 + v]];
+                nn = fold_solve(gn, a, c, nu_, nv_);
+            }
             for (int r = 0; r < nn; r++) {
                 int id = (int)add_pt(pts, np, 2);
                 if (id < 0) return 1;
@@ -526,6 +543,27 @@ __device__ int tri_cube(const TriCtx &X, int64_t ci, TriOut &o, unsigned long lo
     return 0;
 }
 
+// fold roots of every cube (own ends and, across faces, the neighbours'
+// ends are read from this table instead of being solved again)
+__global__ void __launch_bounds__(128) k_fold_table(TriCtx X, uint8_t *__restrict__ fcount, double *__restrict__ froot)
+{
+    int64_t ci = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (ci >= X.ncubes) return;
+    double g[8];
+    for (int v = 0; v < 8; v++) g[v] = X.phi[X.cvid[ci * 8 + v]];
+    uint32_t cnt = 0;
+    for (int a = 0; a < 3; a++) {
+        double ru[2], rv[2];
+        int nr = fold_solve(g, a, X.c, ru, rv);
+        cnt |= (uint32_t)nr << (8 * a);
+        for (int r = 0; r < nr; r++) {
+            froot[ci * 12 + 4 * a + 2 * r] = ru[r];
+            froot[ci * 12 + 4 * a + 2 * r + 1] = rv[r];
+        }
+    }
+    *reinterpret_cast<uint32_t *>(fcount + ci * 4) = cnt;
+}
+
 // first pass: trace every cube, count its output and stage it when it fits
 __global__ void __launch_bounds__(128) k_tri_count(TriCtx X, int64_t *__restrict__ ntri, int64_t *__restrict__ npt,
                                                    unsigned long long *errs, unsigned long long *surface,
@@ -601,9 +639,10 @@ __global__ void __launch_bounds__(128) k_tri_emit(TriCtx X, const int64_t *__res
 }
 
 // ---------------------------------------------------------------- host
-int gs_triangulate(const TriCtx &X, uint64_t **d_tri_keys, int64_t *ntri_total, uint64_t **d_pt_keys,
+int gs_triangulate(const TriCtx &X0, uint64_t **d_tri_keys, int64_t *ntri_total, uint64_t **d_pt_keys,
                    double **d_pt_xyz, int64_t *npt_total, unsigned long long *d_counters, cudaStream_t st)
 {
+    TriCtx X = X0;
     int64_t n = X.ncubes;
     *d_tri_keys = nullptr; *d_pt_keys = nullptr; *d_pt_xyz = nullptr;
     *ntri_total = 0; *npt_total = 0;
@@ -624,6 +663,19 @@ int gs_triangulate(const TriCtx &X, uint64_t **d_tri_keys, int64_t *ntri_total, 
         st_tri = nullptr; st_pk = nullptr; st_xyz = nullptr;
     }
     unsigned nb = (unsigned)((n + 127) / 128);
+    // fold-root table; without room for it each cube solves its neighbours' roots
+    uint8_t *fcount = nullptr;
+    double *froot = nullptr;
+    if (cudaMallocAsync((void **)&fcount, 4 * (size_t)n, st) != cudaSuccess ||
+        cudaMallocAsync((void **)&froot, sizeof(double) * 12 * (size_t)n, st) != cudaSuccess) {
+        cudaGetLastError();
+        gs_free(fcount, st); gs_free(froot, st);
+        fcount = nullptr; froot = nullptr;
+    } else {
+        GS_LAUNCH(k_fold_table, nb, 128, 0, st)(X, fcount, froot);
+        X.fcount = fcount;
+        X.froot = froot;
+    }
     cudaMemsetAsync(ntri + n, 0, sizeof(int64_t), st);
     cudaMemsetAsync(npt + n, 0, sizeof(int64_t), st);
     GS_LAUNCH(k_tri_count, nb, 128, 0, st)(X, ntri, npt, d_counters + 0, d_counters + 2, st_tri, st_pk, st_xyz,
@@ -659,6 +711,7 @@ int gs_triangulate(const TriCtx &X, uint64_t **d_tri_keys, int64_t *ntri_total, 
                                              nullptr, nullptr);
     }
     gs_free(st_tri, st); gs_free(st_pk, st); gs_free(st_xyz, st);
+    gs_free(fcount, st); gs_free(froot, st);
     gs_free(ntri, st); gs_free(npt, st); gs_free(tot, st);
     if (rc) return rc;
     GS_CHECK(cudaGetLastError());
