@@ -274,7 +274,7 @@ def main():
                     "bounds": st["recheck_bounds"], "precision": st["recheck_precision"],
                     "zero": st["recheck_zero"], "rank": st["recheck_rank"],
                     "vertex_mark_cubes": st["vertex_mark_cubes"]},
-        "pair_terms": pairs, "vertex_terms": st["vertex_terms"],
+        "pair_terms": pairs, "atom_octets": st["atom_octets"], "vertex_terms": st["vertex_terms"],
         "roofline": roofline,
         "clocks": clk,
         "e2e": {"value": e2e_ms, "unit": "ms", "h2d_bytes_per_step": int(xyz_h.nbytes + r_h.nbytes),

@@ -593,6 +593,7 @@ static int mesh_impl(const double *atoms, const double *radii, int64_t n, double
         stats->mixed_band_ratio = r;
     }
     stats->pair_terms = (int64_t)h[8];
+    stats->atom_octets = (int64_t)h[24];
     stats->vertex_terms = (int64_t)h[9];
     stats->recheck_cubes = (int64_t)h[13];
     out->mismatches = (int64_t)h[14];

@@ -29,7 +29,7 @@ int gs_estimate_f64(const GsProblem &P, int level, const double *d_A, int64_t n_
 // mixed precision: FP32 accumulate (Kahan) + error bound, FP32 estimate with margins
 int gs_accum_f32(const GsProblem &P, int level, const uint64_t *d_parents, const uint8_t *d_vmask, int64_t n_oct,
                  float *d_A, float *d_err, unsigned long long *d_pairs, unsigned *d_status, cudaStream_t st,
-                 float *ms = nullptr);
+                 float *ms = nullptr, unsigned long long *d_atom_octets = nullptr);
 int gs_estimate_f32(const GsProblem &P, int level, const float *d_A, const float *d_err, int64_t n_cubes,
                     const uint64_t *d_parents, const uint8_t *d_vmask, uint8_t *d_dec, uint8_t *d_flag,
                     cudaStream_t st, unsigned long long *d_why = nullptr, float *d_dbg = nullptr);

@@ -128,6 +128,71 @@ __device__ __forceinline__ void gs_for_rows(const GsProblem &P, const float *lo,
     }
 }
 
+// Warp-cooperative form of gs_for_rows: the lanes compute the (y, z) rows in
+// parallel (32 at a time), a warp scan concatenates their atom ranges, and
+// chunk(i) is called by all lanes with one candidate atom index per lane
+// (-1 past the end), 32 candidates per call.  Same rows and ranges as
+// gs_for_rows; all lanes must call it with the same box.
+template <typename F>
+__device__ __forceinline__ void gs_warp_candidates(const GsProblem &P, const float *lo, const float *hi, int lane,
+                                                   F chunk)
+{
+    const unsigned full = 0xffffffffu;
+    const float cs = P.cell_f, inv = P.inv_cell_f, pad = P.pad_f + 1e-3f;
+    int c0[3], c1[3];
+    for (int a = 0; a < 3; a++) {
+        float f0 = floorf((lo[a] - pad) * inv), f1 = floorf((hi[a] + pad) * inv);
+        f0 = fminf(fmaxf(f0, 0.f), (float)(P.cdim[a] - 1));
+        f1 = fminf(fmaxf(f1, 0.f), (float)(P.cdim[a] - 1));
+        c0[a] = (int)f0;
+        c1[a] = (int)f1;
+    }
+    const float pad2 = pad * pad;
+    const int ny = c1[1] - c0[1] + 1, nz = c1[2] - c0[2] + 1, nrows = ny * nz;
+    for (int r0 = 0; r0 < nrows; r0 += 32) {
+        const int r = r0 + lane;
+        int b = 0, len = 0;
+        if (r < nrows) {
+            const int cy = c0[1] + r % ny, cz = c0[2] + r / ny;
+            float zlo = cz * cs;
+            float gz = fmaxf(0.f, fmaxf(zlo - hi[2], lo[2] - (zlo + cs)));
+            float ylo = cy * cs;
+            float gy = fmaxf(0.f, fmaxf(ylo - hi[1], lo[1] - (ylo + cs)));
+            float rem2 = pad2 - gy * gy - gz * gz;
+            if (gz * gz <= pad2 && rem2 >= 0.f) {
+                float rem = sqrtf(rem2) + 1e-3f;
+                float f0 = fmaxf(floorf((lo[0] - rem) * inv), (float)c0[0]);
+                float f1 = fminf(floorf((hi[0] + rem) * inv), (float)c1[0]);
+                int x0 = (int)f0, x1 = (int)f1;
+                if (x0 <= x1) {
+                    int64_t row = (int64_t)P.cdim[0] * (cy + (int64_t)P.cdim[1] * cz);
+                    b = P.cell_start[row + x0];
+                    len = P.cell_start[row + x1 + 1] - b;
+                }
+            }
+        }
+        int incl = len;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            int v = __shfl_up_sync(full, incl, o);
+            if (lane >= o) incl += v;
+        }
+        const int total = __shfl_sync(full, incl, 31), excl = incl - len;
+        for (int g0 = 0; g0 < total; g0 += 32) {
+            const int g = g0 + lane;
+            // the last row whose range starts at or before g
+            int src = 0;
+#pragma unroll
+            for (int step = 16; step > 0; step >>= 1) {
+                int e = __shfl_sync(full, excl, src + step);
+                if (e <= g) src += step;
+            }
+            const int bs = __shfl_sync(full, b, src), es = __shfl_sync(full, excl, src);
+            chunk(g < total ? bs + (g - es) : -1);
+        }
+    }
+}
+
 // ---------------------------------------------------------------- hashing
 #define GS_EMPTY 0xFFFFFFFFFFFFFFFFull
 __host__ __device__ __forceinline__ uint64_t gs_mix(uint64_t k)

@@ -814,17 +814,20 @@ int gs_root_blocks(const GsProblem &P, uint64_t **d_keys, int64_t *n, cudaStream
 #define ACF_EB 72
 #define ACF_STRIDE 84
 
+// GV: quadrature variant (a compile-time constant, so the node loop unrolls
+// and the nodes and weights are immediate constant-bank operands)
+template <int GV, int NQ>
 __global__ void __launch_bounds__(32 * ACC_WARPS, 4) k_accum_f32(GsProblem P, int level, const uint64_t *parents,
-                                                                  const uint8_t *vmask, int64_t n_oct, int gv, int nq,
+                                                                  const uint8_t *vmask, int64_t n_oct,
                                                                   float hf, int lat_exact, float *__restrict__ A_out,
                                                                   float *__restrict__ E_out,
-                                                                  unsigned long long *pairs)
+                                                                  unsigned long long *pairs,
+                                                                  unsigned long long *atom_octets)
 {
-    unsigned long long my_pairs = 0;
+    unsigned long long my_pairs = 0, my_atoms = 0;
     __shared__ __align__(16) float s_cf[ACC_WARPS][32][ACF_STRIDE];
     __shared__ int s_qi[ACC_WARPS][ACC_Q];
     __shared__ uint8_t s_qm[ACC_WARPS][ACC_Q];
-    __shared__ int s_cand[ACC_WARPS][64];
     const int lane = threadIdx.x & 31, wl = threadIdx.x >> 5;
     const unsigned below = (1u << lane) - 1u;
     const int c = lane >> 2, j = lane & 3;
@@ -854,7 +857,7 @@ __global__ void __launch_bounds__(32 * ACC_WARPS, 4) k_accum_f32(GsProblem P, in
 #pragma unroll
         for (int t = 0; t < 16; t++) { acc[t] = 0.f; comp[t] = 0.f; part[t] = 0.f; }
         float eb = 0.f;
-        int nb = 0, qn = 0, cn = 0;
+        int nb = 0, qn = 0;
         const uint8_t vm = q.vmask;
 
         auto fold = [&]() {
@@ -889,14 +892,14 @@ __global__ void __launch_bounds__(32 * ACC_WARPS, 4) k_accum_f32(GsProblem P, in
                     for (int hI = 0; hI < 2; hI++) {
                         float m = d[hI] + hh;   // interval centre - x
                         float a0 = 0.f, a1 = 0.f, a2 = 0.f, a3 = 0.f;
-#pragma unroll 1
-                        for (int k = 0; k < nq; k++) {
-                            float dk = fmaf(hh, c_gq_tf[gv][k], m);
+#pragma unroll
+                        for (int k = 0; k < NQ; k++) {
+                            float dk = fmaf(hh, c_gq_tf[GV][k], m);
                             float fk = exp2f(nDl2e * dk * dk);
-                            a0 = fmaf(c_gq_Wf[gv][k][0], fk, a0);
-                            a1 = fmaf(c_gq_Wf[gv][k][1], fk, a1);
-                            a2 = fmaf(c_gq_Wf[gv][k][2], fk, a2);
-                            a3 = fmaf(c_gq_Wf[gv][k][3], fk, a3);
+                            a0 = fmaf(c_gq_Wf[GV][k][0], fk, a0);
+                            a1 = fmaf(c_gq_Wf[GV][k][1], fk, a1);
+                            a2 = fmaf(c_gq_Wf[GV][k][2], fk, a2);
+                            a3 = fmaf(c_gq_Wf[GV][k][3], fk, a3);
                         }
                         float fa = f[hI], fb = f[hI + 1];
                         float eR = fb - (a0 + a1 + a2 + a3), eL = fa - (a0 - a1 + a2 - a3);
@@ -932,7 +935,7 @@ __global__ void __launch_bounds__(32 * ACC_WARPS, 4) k_accum_f32(GsProblem P, in
                 *reinterpret_cast<float4 *>(rec + ACF_EB + 4) = make_float4(e8[4], e8[5], e8[6], e8[7]);
             }
             __syncwarp();
-            for (int t = 0; t < nproc; t++) {
+            auto upd = [&](int t) {
                 const unsigned mt = s_qm[wl][t];
                 const float *rec = s_cf[wl][t];
                 float4 xy = *reinterpret_cast<const float4 *>(rec + oWXY);
@@ -949,51 +952,65 @@ __global__ void __launch_bounds__(32 * ACC_WARPS, 4) k_accum_f32(GsProblem P, in
 #pragma unroll
                     for (int l = 0; l < 4; l++) part[4 * k + l] = fmaf(xv[k], zv[l], part[4 * k + l]);
                 eb += e1;
-                if (++nb == 8) fold();
+            };
+            int t = 0;
+            for (; t + 2 <= nproc; t += 2) {
+                upd(t);
+                upd(t + 1);
+                nb += 2;
+                if (nb >= 8) fold();
+            }
+            if (t < nproc) {
+                upd(t);
+                if (++nb >= 8) fold();
             }
             __syncwarp();
         };
 
-        // membership of the buffered candidates (lane < ncand takes one):
-        // FP32 box distance with a relative margin, the exact FP64 test inside
-        // the margin; members join the atom queue
-        auto filter = [&](int ncand) {
+        // membership of one candidate per lane (i < 0: none): FP32 box
+        // distance with a relative margin, the exact FP64 test inside the
+        // margin; members join the atom queue
+        auto filter = [&](int i) {
             unsigned m = 0;
-            int i = -1;
-            if (lane < ncand) {
-                i = s_cand[wl][lane];
+            if (i >= 0) {
                 const float ah[3] = {P.hx[i], P.hy[i], P.hz[i]}, al[3] = {P.lx[i], P.ly[i], P.lz[i]};
-                float g[3][2];
+                float g2[3][2];
+#pragma unroll
                 for (int a = 0; a < 3; a++)
+#pragma unroll
                     for (int hI = 0; hI < 2; hI++) {
                         float dlo = (eh[a][hI] - ah[a]) + (el[a][hI] - al[a]);
                         float dhi = (ah[a] - eh[a][hI + 1]) + (al[a] - el[a][hI + 1]);
-                        g[a][hI] = fmaxf(0.f, fmaxf(dlo, dhi));
+                        float g = fmaxf(0.f, fmaxf(dlo, dhi));
+                        g2[a][hI] = g * g;
                     }
-                float R2 = P.fR2[i];
-                float tol = 1e-5f * R2 + 1e-5f;
+                const float R2 = P.fR2[i];
+                const float tol = 1e-5f * R2 + 1e-5f;
+                unsigned nearm = 0;
+#pragma unroll
                 for (int cc = 0; cc < 8; cc++) {
-                    if (!((vm >> cc) & 1)) continue;
-                    float d2 = g[0][cc & 1] * g[0][cc & 1] + g[1][(cc >> 1) & 1] * g[1][(cc >> 1) & 1] +
-                               g[2][cc >> 2] * g[2][cc >> 2];
-                    bool in;
-                    if (d2 < R2 - tol) in = true;
-                    else if (d2 > R2 + tol) in = false;
-                    else {
-                        // near the cutoff sphere: the exact FP64 membership test
-                        double x = P.ax[i], y = P.ay[i], z = P.az[i];
-                        int64_t ix = base[0] + (cc & 1), iy = base[1] + ((cc >> 1) & 1), iz = base[2] + (cc >> 2);
-                        double dx = gs_axis_gap(gs_lat(P, 0, ix, level), gs_lat(P, 0, ix + 1, level), x);
-                        double dy = gs_axis_gap(gs_lat(P, 1, iy, level), gs_lat(P, 1, iy + 1, level), y);
-                        double dz = gs_axis_gap(gs_lat(P, 2, iz, level), gs_lat(P, 2, iz + 1, level), z);
-                        double dd = __dadd_rn(__dadd_rn(__dmul_rn(dx, dx), __dmul_rn(dy, dy)), __dmul_rn(dz, dz));
-                        in = dd <= P.aR2[i];
-                    }
-                    if (in) m |= 1u << cc;
+                    float d2 = g2[0][cc & 1] + g2[1][(cc >> 1) & 1] + g2[2][cc >> 2];
+                    if (d2 < R2 - tol) m |= 1u << cc;
+                    else if (d2 <= R2 + tol) nearm |= 1u << cc;
+                }
+                m &= vm;
+                nearm &= vm;
+                // near the cutoff sphere: the exact FP64 membership test
+                while (nearm) {
+                    const int cc = __ffs(nearm) - 1;
+                    nearm &= nearm - 1;
+                    double x = P.ax[i], y = P.ay[i], z = P.az[i];
+                    int64_t ix = base[0] + (cc & 1), iy = base[1] + ((cc >> 1) & 1), iz = base[2] + (cc >> 2);
+                    double dx = gs_axis_gap(gs_lat(P, 0, ix, level), gs_lat(P, 0, ix + 1, level), x);
+                    double dy = gs_axis_gap(gs_lat(P, 1, iy, level), gs_lat(P, 1, iy + 1, level), y);
+                    double dz = gs_axis_gap(gs_lat(P, 2, iz, level), gs_lat(P, 2, iz + 1, level), z);
+                    double dd = __dadd_rn(__dadd_rn(__dmul_rn(dx, dx), __dmul_rn(dy, dy)), __dmul_rn(dz, dz));
+                    if (dd <= P.aR2[i]) m |= 1u << cc;
                 }
             }
             my_pairs += __popc(m);
             unsigned bal = __ballot_sync(0xffffffffu, m != 0);
+            if (lane == 0) my_atoms += __popc(bal);
             int pos = qn + __popc(bal & below);
             if (m) { s_qi[wl][pos] = i; s_qm[wl][pos] = (uint8_t)m; }
             qn += __popc(bal);
@@ -1012,28 +1029,7 @@ __global__ void __launch_bounds__(32 * ACC_WARPS, 4) k_accum_f32(GsProblem P, in
 
         if (vm) {
             float flo[3] = {eh[0][0], eh[1][0], eh[2][0]}, fhi[3] = {eh[0][2], eh[1][2], eh[2][2]};
-            // rows of the cell list are short; their atoms are merged into a
-            // buffer so that candidates are filtered 32 at a time
-            gs_for_rows(P, flo, fhi, [&](int b, int en, int64_t, int) {
-                for (int s = b; s < en; s += 32) {
-                    int idx = s + lane;
-                    bool v = idx < en;
-                    unsigned bal = __ballot_sync(0xffffffffu, v);
-                    if (v) s_cand[wl][cn + __popc(bal & below)] = idx;
-                    cn += __popc(bal);
-                    __syncwarp();
-                    if (cn >= 32) {
-                        filter(32);
-                        int rest = cn - 32;
-                        int mv = lane < rest ? s_cand[wl][32 + lane] : 0;
-                        __syncwarp();
-                        if (lane < rest) s_cand[wl][lane] = mv;
-                        __syncwarp();
-                        cn = rest;
-                    }
-                }
-            });
-            if (cn > 0) filter(cn);
+            gs_warp_candidates(P, flo, fhi, lane, filter);
             if (qn > 0) process(qn);
             fold();
         }
@@ -1046,19 +1042,30 @@ __global__ void __launch_bounds__(32 * ACC_WARPS, 4) k_accum_f32(GsProblem P, in
         for (int off = 16; off > 0; off >>= 1) my_pairs += __shfl_xor_sync(0xffffffffu, my_pairs, off);
         if (lane == 0 && my_pairs) atomicAdd(pairs, my_pairs);
     }
+    if (atom_octets && lane == 0 && my_atoms) atomicAdd(atom_octets, my_atoms);
 }
 
 int gs_accum_f32(const GsProblem &P, int level, const uint64_t *d_parents, const uint8_t *d_vmask, int64_t n_oct,
-                 float *d_A, float *d_err, unsigned long long *d_pairs, unsigned *d_status, cudaStream_t st, float *ms)
+                 float *d_A, float *d_err, unsigned long long *d_pairs, unsigned *d_status, cudaStream_t st, float *ms,
+                 unsigned long long *d_atom_octets)
 {
     if (n_oct <= 0) return GS_OK;
     double h = gs_h(P, level);
     int gv = gq_variant(P.D, 0.5 * h, true);
     cudaEvent_t e0 = nullptr, e1 = nullptr;
     if (ms) { cudaEventCreate(&e0); cudaEventCreate(&e1); cudaEventRecord(e0, st); }
-    GS_LAUNCH(k_accum_f32, grid_for(n_oct, ACC_WARPS), 32 * ACC_WARPS, 0, st)(P, level, d_parents, d_vmask, n_oct, gv,
-                                                                             kGqN[gv], (float)h, P.lat_exact_f32, d_A,
-                                                                             d_err, d_pairs);
+    const unsigned grid = grid_for(n_oct, ACC_WARPS);
+#define GS_ACC32(V, N)                                                                                              \
+    GS_LAUNCH((k_accum_f32<V, N>), grid, 32 * ACC_WARPS, 0, st)(P, level, d_parents, d_vmask, n_oct, (float)h,      \
+                                                               P.lat_exact_f32, d_A, d_err, d_pairs, d_atom_octets)
+    switch (gv) {
+    case 5: GS_ACC32(5, 5); break;
+    case 4: GS_ACC32(4, 6); break;
+    case 0: GS_ACC32(0, 8); break;
+    case 1: GS_ACC32(1, 12); break;
+    default: GS_ACC32(2, 16); break;
+    }
+#undef GS_ACC32
     if (ms) {
         cudaEventRecord(e1, st);
         cudaEventSynchronize(e1);
@@ -1316,7 +1323,8 @@ int gs_level_mixed(const GsProblem &P, int level, const uint64_t *d_parents, int
     if (!rc) rc = gs_alloc((void **)&flag, 8 * (size_t)n_oct, st);
     float *dbg = nullptr;
     if (!rc && both) rc = gs_alloc((void **)&dbg, sizeof(float) * 6 * 8 * (size_t)n_oct, st);
-    if (!rc) rc = gs_accum_f32(P, level, d_parents, nullptr, n_oct, A, E, d_pairs, d_status, st, ms);
+    // the counter block holds the atom-octet count 16 slots after the pair count
+    if (!rc) rc = gs_accum_f32(P, level, d_parents, nullptr, n_oct, A, E, d_pairs, d_status, st, ms, d_pairs + 16);
     if (!rc) rc = gs_estimate_f32(P, level, A, E, n_oct * 8, d_parents, nullptr, d_dec, flag, st, d_why, dbg);
     if (!rc) {
         // decisions resting on one rank rule near its threshold
