@@ -56,7 +56,7 @@ __global__ void __launch_bounds__(128) k_field_f64(GsProblem P, const uint64_t *
                 double dx = __dsub_rn(p[0], P.ax[k]), dy = __dsub_rn(p[1], P.ay[k]), dz = __dsub_rn(p[2], P.az[k]);
                 double d2 = __dadd_rn(__dadd_rn(__dmul_rn(dx, dx), __dmul_rn(dy, dy)), __dmul_rn(dz, dz));
                 if (d2 > P.aR2[k]) continue;
-                double t = P.aw[k] * exp(nD * d2);
+                double t = P.aw[k] * gs_exp(nD * d2);
                 s += t;
                 if (GRAD) {
                     g0 = fma(m2D * dx, t, g0);

@@ -193,6 +193,43 @@ __device__ __forceinline__ void gs_warp_candidates(const GsProblem &P, const flo
     }
 }
 
+// ---------------------------------------------------------------- exp (FP64)
+// exp(x) for |x| <= 700 by Tang's table-driven method (ACM TOMS 15, 1989):
+// x = (32 m + j) ln2/32 + r with |r| <= ln2/64 (Cody-Waite reduction, ln2/32
+// split so that k * GS_L1 is exact for |k| < 2^15), exp(r) - 1 by its degree-6
+// Taylor polynomial (truncation below 4e-18), then 2^(j/32) from a table and
+// 2^m into the exponent field.  Error within 2 ulp; no special cases.
+static __device__ const double gs_exp_tab[32] = {
+    0x1.0000000000000p+0, 0x1.059b0d3158574p+0, 0x1.0b5586cf9890fp+0, 0x1.11301d0125b51p+0,
+    0x1.172b83c7d517bp+0, 0x1.1d4873168b9aap+0, 0x1.2387a6e756238p+0, 0x1.29e9df51fdee1p+0,
+    0x1.306fe0a31b715p+0, 0x1.371a7373aa9cbp+0, 0x1.3dea64c123422p+0, 0x1.44e086061892dp+0,
+    0x1.4bfdad5362a27p+0, 0x1.5342b569d4f82p+0, 0x1.5ab07dd485429p+0, 0x1.6247eb03a5585p+0,
+    0x1.6a09e667f3bcdp+0, 0x1.71f75e8ec5f74p+0, 0x1.7a11473eb0187p+0, 0x1.82589994cce13p+0,
+    0x1.8ace5422aa0dbp+0, 0x1.93737b0cdc5e5p+0, 0x1.9c49182a3f090p+0, 0x1.a5503b23e255dp+0,
+    0x1.ae89f995ad3adp+0, 0x1.b7f76f2fb5e47p+0, 0x1.c199bdd85529cp+0, 0x1.cb720dcef9069p+0,
+    0x1.d5818dcfba487p+0, 0x1.dfc97337b9b5fp+0, 0x1.ea4afa2a490dap+0, 0x1.f50765b6e4540p+0};
+
+__device__ __forceinline__ double gs_exp(double x)
+{
+    const double inv = 0x1.71547652b82fep+5;      // 32 / ln 2
+    const double L1 = 0x1.62e42fefa0000p-6;       // ln 2 / 32, leading 37 bits
+    const double L2 = 0x1.cf79abc9e3b3ap-45;      // ln 2 / 32 - L1
+    const double shifter = 0x1.8p+52;             // rounds to an integer in the low word
+    double t = fma(x, inv, shifter);
+    const int k = __double2loint(t);
+    const double kd = t - shifter;
+    double r = fma(-kd, L1, x);
+    r = fma(-kd, L2, r);
+    double p = fma(r, 1.0 / 720.0, 1.0 / 120.0);
+    p = fma(r, p, 1.0 / 24.0);
+    p = fma(r, p, 1.0 / 6.0);
+    p = fma(r, p, 0.5);
+    p = fma(r * r, p, r);                         // exp(r) - 1
+    const double s = __ldg(&gs_exp_tab[k & 31]);
+    const double y = fma(s, p, s);
+    return __hiloint2double(__double2hiint(y) + ((k >> 5) << 20), __double2loint(y));
+}
+
 // ---------------------------------------------------------------- hashing
 #define GS_EMPTY 0xFFFFFFFFFFFFFFFFull
 __host__ __device__ __forceinline__ uint64_t gs_mix(uint64_t k)

@@ -147,21 +147,24 @@ __device__ __forceinline__ Octet octet_of(const GsProblem &P, int level, const u
 // one axis: C0-corrected Legendre coefficients of exp(-D (x - xi)^2) on
 // [e0,e1] and [e1,e2] (the two child intervals), FP64; `need` selects the
 // intervals (bit 0: [e0,e1], bit 1: [e1,e2]) some accumulated child uses
-__device__ __forceinline__ void axis_coeffs_f64(double xi, double e0, double e1, double e2, double D, int gv, int nq,
+template <int GV, int NQ>
+__device__ __forceinline__ void axis_coeffs_f64(double xi, double e0, double e1, double e2, double D,
                                                 double *out /* [2][4] */, int need = 3)
 {
-    double f0 = (need & 1) ? exp(-D * (e0 - xi) * (e0 - xi)) : 0.0;
-    double f1 = exp(-D * (e1 - xi) * (e1 - xi));
-    double f2 = (need & 2) ? exp(-D * (e2 - xi) * (e2 - xi)) : 0.0;
+    const int gv = GV, nq = NQ;
+    double f0 = (need & 1) ? gs_exp(-D * (e0 - xi) * (e0 - xi)) : 0.0;
+    double f1 = gs_exp(-D * (e1 - xi) * (e1 - xi));
+    double f2 = (need & 2) ? gs_exp(-D * (e2 - xi) * (e2 - xi)) : 0.0;
 #pragma unroll
     for (int h = 0; h < 2; h++) {
         if (!((need >> h) & 1)) continue;
         double lo = h ? e1 : e0, hi = h ? e2 : e1;
         double m = __dmul_rn(0.5, __dadd_rn(lo, hi)) - xi, hh = __dmul_rn(0.5, __dsub_rn(hi, lo));
         double a0 = 0, a1 = 0, a2 = 0, a3 = 0;
+#pragma unroll
         for (int k = 0; k < nq; k++) {
             double d = fma(hh, c_gq_t[gv][k], m);
-            double f = exp(-D * d * d);
+            double f = gs_exp(-D * d * d);
             a0 = fma(c_gq_W[gv][k][0], f, a0);
             a1 = fma(c_gq_W[gv][k][1], f, a1);
             a2 = fma(c_gq_W[gv][k][2], f, a2);
@@ -177,15 +180,15 @@ __device__ __forceinline__ void axis_coeffs_f64(double xi, double e0, double e1,
     }
 }
 
+template <int GV, int NQ>
 __global__ void __launch_bounds__(32 * ACC_WARPS) k_accum_f64(GsProblem P, int level, const uint64_t *parents,
-                                                               const uint8_t *vmask, int64_t n_oct, int gv, int nq,
+                                                               const uint8_t *vmask, int64_t n_oct,
                                                                double pad, double *__restrict__ A_out,
                                                                unsigned long long *pairs, unsigned *status)
 {
     __shared__ double s_cf[ACC_WARPS][32][25];   // per queued atom: 3 axes x 2 intervals x 4, then w
     __shared__ int s_qi[ACC_WARPS][ACC_Q];
     __shared__ uint8_t s_qm[ACC_WARPS][ACC_Q];
-    __shared__ int s_cand[ACC_WARPS][64];
     const int lane = threadIdx.x & 31, wl = threadIdx.x >> 5;
     const unsigned below = (1u << lane) - 1u;
     const int c = lane >> 2, j = lane & 3;
@@ -206,7 +209,7 @@ __global__ void __launch_bounds__(32 * ACC_WARPS) k_accum_f64(GsProblem P, int l
         double acc[16];
 #pragma unroll
         for (int t = 0; t < 16; t++) acc[t] = 0.0;
-        int qn = 0, cn = 0;
+        int qn = 0;
         const uint8_t vm = q.vmask;
 
         // intervals used by the selected children, per axis
@@ -222,7 +225,7 @@ __global__ void __launch_bounds__(32 * ACC_WARPS) k_accum_f64(GsProblem P, int l
                 int i = s_qi[wl][lane];
                 double xs[3] = {P.ax[i], P.ay[i], P.az[i]};
                 for (int a = 0; a < 3; a++)
-                    axis_coeffs_f64(xs[a], e[a][0], e[a][1], e[a][2], P.D, gv, nq, &s_cf[wl][lane][8 * a], need[a]);
+                    axis_coeffs_f64<GV, NQ>(xs[a], e[a][0], e[a][1], e[a][2], P.D, &s_cf[wl][lane][8 * a], need[a]);
                 s_cf[wl][lane][24] = P.aw[i];
             }
             __syncwarp();
@@ -241,39 +244,43 @@ __global__ void __launch_bounds__(32 * ACC_WARPS) k_accum_f64(GsProblem P, int l
             __syncwarp();
         };
 
-        // membership: FP32 box distance with a margin, the exact FP64 test
-        // (the definition) inside the margin
-        auto filter = [&](int ncand) {
+        // membership of one candidate per lane (i < 0: none): FP32 box
+        // distance with a margin, the exact FP64 test (the definition) inside
+        // the margin
+        auto filter = [&](int i) {
             unsigned m = 0;
-            int i = -1;
-            if (lane < ncand) {
-                i = s_cand[wl][lane];
+            if (i >= 0) {
                 const float ah[3] = {P.hx[i], P.hy[i], P.hz[i]}, al[3] = {P.lx[i], P.ly[i], P.lz[i]};
-                float g[3][2];
+                float g2[3][2];
+#pragma unroll
                 for (int a = 0; a < 3; a++)
+#pragma unroll
                     for (int hI = 0; hI < 2; hI++) {
                         float dlo = (eh[a][hI] - ah[a]) + (el[a][hI] - al[a]);
                         float dhi = (ah[a] - eh[a][hI + 1]) + (al[a] - el[a][hI + 1]);
-                        g[a][hI] = fmaxf(0.f, fmaxf(dlo, dhi));
+                        float g = fmaxf(0.f, fmaxf(dlo, dhi));
+                        g2[a][hI] = g * g;
                     }
-                float R2 = P.fR2[i];
-                float tol = 1e-5f * R2 + 1e-5f;
+                const float R2 = P.fR2[i];
+                const float tol = 1e-5f * R2 + 1e-5f;
+                unsigned nearm = 0;
+#pragma unroll
                 for (int cc = 0; cc < 8; cc++) {
-                    if (!((vm >> cc) & 1)) continue;
-                    float d2 = g[0][cc & 1] * g[0][cc & 1] + g[1][(cc >> 1) & 1] * g[1][(cc >> 1) & 1] +
-                               g[2][cc >> 2] * g[2][cc >> 2];
-                    bool in;
-                    if (d2 < R2 - tol) in = true;
-                    else if (d2 > R2 + tol) in = false;
-                    else {
-                        double x = P.ax[i], y = P.ay[i], z = P.az[i];
-                        double dx = gs_axis_gap(e[0][cc & 1], e[0][(cc & 1) + 1], x);
-                        double dy = gs_axis_gap(e[1][(cc >> 1) & 1], e[1][((cc >> 1) & 1) + 1], y);
-                        double dz = gs_axis_gap(e[2][cc >> 2], e[2][(cc >> 2) + 1], z);
-                        double dd = __dadd_rn(__dadd_rn(__dmul_rn(dx, dx), __dmul_rn(dy, dy)), __dmul_rn(dz, dz));
-                        in = dd <= P.aR2[i];
-                    }
-                    if (in) m |= 1u << cc;
+                    float d2 = g2[0][cc & 1] + g2[1][(cc >> 1) & 1] + g2[2][cc >> 2];
+                    if (d2 < R2 - tol) m |= 1u << cc;
+                    else if (d2 <= R2 + tol) nearm |= 1u << cc;
+                }
+                m &= vm;
+                nearm &= vm;
+                while (nearm) {
+                    const int cc = __ffs(nearm) - 1;
+                    nearm &= nearm - 1;
+                    double x = P.ax[i], y = P.ay[i], z = P.az[i];
+                    double dx = gs_axis_gap(e[0][cc & 1], e[0][(cc & 1) + 1], x);
+                    double dy = gs_axis_gap(e[1][(cc >> 1) & 1], e[1][((cc >> 1) & 1) + 1], y);
+                    double dz = gs_axis_gap(e[2][cc >> 2], e[2][(cc >> 2) + 1], z);
+                    double dd = __dadd_rn(__dadd_rn(__dmul_rn(dx, dx), __dmul_rn(dy, dy)), __dmul_rn(dz, dz));
+                    if (dd <= P.aR2[i]) m |= 1u << cc;
                 }
             }
             my_pairs += __popc(m);
@@ -296,26 +303,7 @@ __global__ void __launch_bounds__(32 * ACC_WARPS) k_accum_f64(GsProblem P, int l
 
         if (vm) {
             float flo[3] = {eh[0][0], eh[1][0], eh[2][0]}, fhi[3] = {eh[0][2], eh[1][2], eh[2][2]};
-            gs_for_rows(P, flo, fhi, [&](int b, int en, int64_t, int) {
-                for (int s = b; s < en; s += 32) {
-                    int idx = s + lane;
-                    bool v = idx < en;
-                    unsigned bal = __ballot_sync(0xffffffffu, v);
-                    if (v) s_cand[wl][cn + __popc(bal & below)] = idx;
-                    cn += __popc(bal);
-                    __syncwarp();
-                    if (cn >= 32) {
-                        filter(32);
-                        int rest = cn - 32;
-                        int mv = lane < rest ? s_cand[wl][32 + lane] : 0;
-                        __syncwarp();
-                        if (lane < rest) s_cand[wl][lane] = mv;
-                        __syncwarp();
-                        cn = rest;
-                    }
-                }
-            });
-            if (cn > 0) filter(cn);
+            gs_warp_candidates(P, flo, fhi, lane, filter);
             if (qn > 0) process(qn);
         }
         double *dst = A_out + ((size_t)o * 8 + c) * 64 + 16 * j;
@@ -346,8 +334,17 @@ int gs_accum_f64(const GsProblem &P, int level, const uint64_t *d_parents, const
     int gv = gq_variant(P.D, 0.5 * h, false);
     cudaEvent_t e0 = nullptr, e1 = nullptr;
     if (ms) { cudaEventCreate(&e0); cudaEventCreate(&e1); cudaEventRecord(e0, st); }
-    GS_LAUNCH(k_accum_f64, grid_for(n_oct, ACC_WARPS), 32 * ACC_WARPS, 0, st)(P, level, d_parents, d_vmask, n_oct, gv,
-                                                                             kGqN[gv], P.pad, d_A, d_pairs, d_status);
+    const unsigned grid = grid_for(n_oct, ACC_WARPS);
+#define GS_ACC64(V, N)                                                                                              \
+    GS_LAUNCH((k_accum_f64<V, N>), grid, 32 * ACC_WARPS, 0, st)(P, level, d_parents, d_vmask, n_oct, P.pad, d_A,    \
+                                                               d_pairs, d_status)
+    switch (gv) {
+    case 0: GS_ACC64(0, 8); break;
+    case 1: GS_ACC64(1, 12); break;
+    case 2: GS_ACC64(2, 16); break;
+    default: GS_ACC64(3, 24); break;
+    }
+#undef GS_ACC64
     if (ms) {
         cudaEventRecord(e1, st);
         cudaEventSynchronize(e1);
@@ -369,7 +366,9 @@ template <> __device__ __forceinline__ float t_sqrt<float>(float x) { return sqr
 template <typename T> __device__ __forceinline__ T t_abs(T x) { return x < T(0) ? -x : x; }
 template <typename T> struct Eps;
 template <> struct Eps<double> { static __device__ __forceinline__ double v() { return 1e-15; } };
-template <> struct Eps<float> { static __device__ __forceinline__ float v() { return 1e-7f; } };
+// FP32: the rounding noise of a 16-term dot product is ~1e-6 of |p||q|, so a
+// tighter rotation threshold would keep rotating noise until the sweep limit
+template <> struct Eps<float> { static __device__ __forceinline__ float v() { return 1e-6f; } };
 
 // one-sided Jacobi on the 4 rows of X (4 x N): afterwards the rows are
 // orthogonal and X_in = Q^T X_out.  Returns singular values sorted

@@ -50,6 +50,28 @@ def test_field_fp64_parity(chain100):
     assert np.allclose(g, rg, rtol=1e-12, atol=1e-14 * np.abs(rg).max())
 
 
+def test_field_single_atom_exp():
+    """One atom: phi(p) = exp(-D (|p - x|^2 - r^2)) exactly (Eq. 1).  Points
+    at distances spanning the whole cutoff radius exercise the FP64 exponential
+    over its full argument range; the bound is a few ulp."""
+    rng = np.random.default_rng(7)
+    D, c, r0 = 0.5, 1.0, 1.7
+    xyz = np.array([[12.25, -3.5, 40.125]])
+    R = np.sqrt(r0 * r0 - np.log(1e-8 * c) / D)
+    dirs = rng.normal(size=(20000, 3))
+    dirs /= np.linalg.norm(dirs, axis=1)[:, None]
+    pts = xyz + dirs * (rng.random(20000)[:, None] * 0.999 * R)
+    phi = gs.gs_eval_field(xyz, np.array([r0]), D, c, pts)
+    d2 = ((pts - xyz) ** 2).sum(1)
+    ref = np.exp(-D * (d2 - r0 * r0))
+    # the two arguments, -D d^2 (plus log w) and -D (d^2 - r^2), round
+    # differently by up to half an ulp each; the exponentials, w and the
+    # product add a few ulp
+    u = 2.0 ** -53
+    tol = (D * d2 + np.abs(D * (d2 - r0 * r0))) * u + 8 * u
+    assert np.all(np.abs(phi - ref) <= tol * ref)
+
+
 def _sample_cubes(cfg, rng, n_per_level=200):
     o, nroot, pad = oracle.root_grid(cfg["xyz"], cfg["r"], cfg["D"], cfg["c"], cfg["min_edge"], cfg["max_depth"])
     keys = []
