@@ -594,9 +594,10 @@ __device__ __forceinline__ void estimate_bounds_sens(const T *A, T *out, T &rmar
     }
     rmargin = rm;
     sens = gap_sens<T>(s, jr);
-    T At[64];
+    // R = A minus the kept rank-one terms, subtracted in place
+    T R[64];
 #pragma unroll
-    for (int t = 0; t < 64; t++) At[t] = 0;
+    for (int t = 0; t < 64; t++) R[t] = A[t];
     T M = 0, m = 0;
     int inner = 0;
     for (int i = 0; i < jr; i++) {
@@ -637,7 +638,7 @@ __device__ __forceinline__ void estimate_bounds_sens(const T *A, T *out, T &rmar
                 for (int b = 0; b < 4; b++) {
                     T sab = sa * w[k][b];
 #pragma unroll
-                    for (int cc = 0; cc < 4; cc++) At[16 * a + 4 * b + cc] += sab * V[k][cc];
+                    for (int cc = 0; cc < 4; cc++) R[16 * a + 4 * b + cc] -= sab * V[k][cc];
                 }
             }
         }
@@ -653,7 +654,7 @@ __device__ __forceinline__ void estimate_bounds_sens(const T *A, T *out, T &rmar
     }
     T sr = 0;
 #pragma unroll
-    for (int t = 0; t < 64; t++) sr += t_abs(A[t] - At[t]);
+    for (int t = 0; t < 64; t++) sr += t_abs(R[t]);
     out[0] = m - sr;
     out[1] = M + sr;
     out[2] = sr;
