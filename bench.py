@@ -242,6 +242,14 @@ def main():
             ft.append(e0.elapsed_time(e1))
         fp64 = {"ms_per_mesh": float(np.mean(ft)), "pair_terms": mf.stats["pair_terms"],
                 "ms_accum": mf.stats["ms_accum"], "n_triangles": mf.stats["n_triangles"]}
+        # FP32-vs-FP64 vertex error: the mixed mesh of the end-to-end step
+        # against an (untimed) FP64 mesh with host outputs
+        mfh = run(xyz_h, r_h, gs.GS_PREC_FP64, device_output=False)
+        same = (np.array_equal(mh.vertex_keys, mfh.vertex_keys) and np.array_equal(mh.triangles, mfh.triangles)
+                and np.array_equal(mh.cube_keys, mfh.cube_keys))
+        fp64["same_cubes_and_topology"] = bool(same)
+        fp64["max_vertex_diff_A"] = float(np.abs(mh.vertices - mfh.vertices).max()) if same else None
+        del mfh
 
     st = stats[-1]
     pairs = st["pair_terms"]
