@@ -214,6 +214,42 @@ int gs_cube_decisions(const double *atoms, const double *radii, int64_t n_atoms,
 int gs_triangulate_grid(int64_t nx, int64_t ny, int64_t nz, const double *values, double c,
                         const gs_options *opt, gs_mesh *out);
 
+/*
+ * gs_mesh_backward -- adjoint of mesh_gaussian_surface: given dL/dp for every
+ * vertex of the mesh that mesh_gaussian_surface returns for the same
+ * arguments, accumulate dL/d(atom centres), dL/d(radii) and dL/dD.  The cube
+ * set and the topology are held fixed (the derivative of the piecewise
+ * smooth map); every vertex is differentiated through the corner values it
+ * is computed from -- edge points through eq intersection, extreme points
+ * through the fold equations eq fold1 by implicit differentiation, critical
+ * points (eq critical) through the two fold roots that define them -- and
+ * the corner values through eq Gaussian1 (terms recomputed, not stored).
+ * The paper defines no derivatives; this is the chain rule applied to its
+ * construction.  The mesh is recomputed inside the call.
+ *   grad_vertices [n_vertices][3] (host or device), in the mesh's vertex order;
+ *   n_vertices must equal the mesh's vertex count (else GS_ERR_ARG).
+ *   grad_atoms [n_atoms][3], grad_radii [n_atoms], grad_D [1] (host or device,
+ *   each nullable), overwritten.  FP64 atomics: sums are reproducible only up
+ *   to rounding order.  Errors as mesh_gaussian_surface; GS_ERR_DEVICE_STATUS
+ *   if a vertex key does not resolve to its cube or edge.
+ */
+int gs_mesh_backward(const double *atoms, const double *radii, int64_t n_atoms, double D, double c,
+                     double precision, int max_depth, const gs_options *opt, const double *grad_vertices,
+                     int64_t n_vertices, double *grad_atoms, double *grad_radii, double *grad_D);
+
+/*
+ * gs_volume_area -- enclosed volume sum p0.(p1 x p2)/6 and surface area
+ * sum |(p1 - p0) x (p2 - p0)|/2 of a closed mesh with outward (counter-
+ * clockwise seen from outside) triangles, the two measures the paper
+ * reports for its meshes (section 3.4), with their gradients per vertex.
+ *   vertices [n_vertices][3], triangles [n_triangles][3] int32 (host or
+ *   device); volume_area [2] out; grad_volume, grad_area [n_vertices][3]
+ *   (nullable) overwritten.  GS_ERR_ARG if a triangle index is outside
+ *   [0, n_vertices).  opt: only the stream is used (NULL: a private stream).
+ */
+int gs_volume_area(const double *vertices, int64_t n_vertices, const int32_t *triangles, int64_t n_triangles,
+                   double *volume_area, double *grad_volume, double *grad_area, const gs_options *opt);
+
 #ifdef __cplusplus
 }
 #endif

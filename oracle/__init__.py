@@ -94,6 +94,10 @@ def lib():
         L.or_partition.restype = i32
         L.or_mesh_free.argtypes = [ctypes.POINTER(MeshOut)]
         L.or_mesh_grid.argtypes = [i64, i64, i64, p, d, ctypes.POINTER(MeshOut)]
+        L.or_mesh_grad.argtypes = [i64, p, p, d, d, d, d, d, i32, i64, p, p, p, p]
+        L.or_mesh_grad.restype = i32
+        L.or_volume_area.argtypes = [i64, p, i64, p, p]
+        L.or_volume_area.restype = None
         L.or_mesh_grid.restype = i32
         _lib = L
     return _lib
@@ -233,6 +237,28 @@ def mesh(xyz, r, D, c, precision, min_edge, max_depth, cutoff_rel=CUTOFF_REL):
     finally:
         L.or_mesh_free(ctypes.byref(out))
     return res
+
+
+def mesh_grad(xyz, r, D, c, precision, min_edge, max_depth, dLdp, cutoff_rel=CUTOFF_REL):
+    """(dL/dxyz [n,3], dL/dr [n], dL/dD) from dL/dp [nv,3] in the order of
+    mesh()'s vertices (sorted keys); cube set and topology held fixed."""
+    xyz, r = _f64(xyz), _f64(r)
+    g = _f64(dLdp).reshape(-1, 3)
+    gx, gr, gD = np.zeros((len(r), 3)), np.zeros(len(r)), np.zeros(1)
+    e = lib().or_mesh_grad(len(r), _ptr(xyz), _ptr(r), D, c, cutoff_rel, precision, min_edge, max_depth, len(g),
+                           _ptr(g), _ptr(gx), _ptr(gr), _ptr(gD))
+    if e:
+        raise ValueError("oracle status %d" % e)
+    return gx, gr, float(gD[0])
+
+
+def volume_area(vertices, triangles):
+    """(volume, area) of a closed outward mesh (plain sums)."""
+    v = _f64(vertices).reshape(-1, 3)
+    t = np.ascontiguousarray(triangles, dtype=np.int32)
+    out = np.zeros(2)
+    lib().or_volume_area(len(v), _ptr(v), len(t), _ptr(t), _ptr(out))
+    return out[0], out[1]
 
 
 def partition(xyz, r, D, c, precision, min_edge, max_depth, cutoff_rel=CUTOFF_REL):

@@ -1506,3 +1506,187 @@ int or_mesh_grid(int64_t nx, int64_t ny, int64_t nz, const double *values, doubl
 
 int or_sizeof_mesh_out(void) { return (int)sizeof(or_mesh_out); }
 int or_sizeof_stats(void) { return (int)sizeof(ostats); }
+
+/* ================================================================== */
+/* Derivatives of the mesh.  The paper defines none; these are the chain */
+/* rule applied to its construction, with the cube set and the topology  */
+/* held fixed.  A vertex is a function of the lattice values it is        */
+/* computed from (eqs intersection, fold1, critical); the lattice values  */
+/* are functions of the atoms (eq Gaussian1).                             */
+/* ================================================================== */
+
+/* Fold equations of axis a at (u,v): A = bilinear(lower face) - c,
+ * B = bilinear(upper face) - bilinear(lower face), their partials in (u,v)
+ * and in each corner value. */
+static void fold_eqs(const double *g, int a, double c, double u, double v, double *A, double *B, double dA[2],
+                     double dB[2], double dAg[8], double dBg[8])
+{
+    int ua, va;
+    other_axes(a, &ua, &va);
+    *A = -c; *B = 0.0;
+    dA[0] = dA[1] = dB[0] = dB[1] = 0.0;
+    for (int k = 0; k < 8; k++) dAg[k] = dBg[k] = 0.0;
+    for (int k = 0; k < 4; k++) {
+        int ku = k & 1, kv = k >> 1;
+        double wu = ku ? u : 1.0 - u, wv = kv ? v : 1.0 - v, w = wu * wv;
+        double dwdu = (ku ? 1.0 : -1.0) * wv, dwdv = wu * (kv ? 1.0 : -1.0);
+        int b[3];
+        b[a] = 0; b[ua] = ku; b[va] = kv;
+        int il = b[0] | (b[1] << 1) | (b[2] << 2);
+        b[a] = 1;
+        int iu = b[0] | (b[1] << 1) | (b[2] << 2);
+        double dlt = g[iu] - g[il];
+        *A += w * g[il];
+        *B += w * dlt;
+        dA[0] += dwdu * g[il]; dA[1] += dwdv * g[il];
+        dB[0] += dwdu * dlt;   dB[1] += dwdv * dlt;
+        dAg[il] += w;
+        dBg[iu] += w;
+        dBg[il] -= w;
+    }
+}
+
+/* d(u,v)/dg_k of a fold root of axis a: the 2x2 system
+ * [dA/du dA/dv; dB/du dB/dv] (du, dv) = -(dA/dg_k, dB/dg_k), by Cramer's rule */
+static void fold_root_derivs(const double *g, int a, double c, double u, double v, double du[8], double dv[8])
+{
+    double A, B, dA[2], dB[2], dAg[8], dBg[8];
+    fold_eqs(g, a, c, u, v, &A, &B, dA, dB, dAg, dBg);
+    double det = dA[0] * dB[1] - dA[1] * dB[0];
+    for (int k = 0; k < 8; k++) {
+        double r1 = -dAg[k], r2 = -dBg[k];
+        du[k] = det != 0.0 ? (r1 * dB[1] - dA[1] * r2) / det : 0.0;
+        dv[k] = det != 0.0 ? (dA[0] * r2 - r1 * dB[0]) / det : 0.0;
+    }
+}
+
+static int64_t lattice_index(const or_mesh_out *m, int64_t X, int64_t Y, int64_t Z)
+{
+    return find_u64(m->lattice_keys, m->n_lattice, okey((uint64_t)X, (uint64_t)Y, (uint64_t)Z, T_VERT, 0));
+}
+
+/* dL/d(atom centres [n,3]), dL/d(radii [n]), dL/dD from dL/dp [nv,3] given in
+ * the order of or_mesh's vertices (sorted keys).  Outputs overwritten. */
+int or_mesh_grad(int64_t n, const double *xyz, const double *r, double D, double c, double cutoff_rel,
+                 double precision, double min_edge, int max_depth, int64_t nv, const double *dLdp, double *g_xyz,
+                 double *g_r, double *g_D)
+{
+    or_mesh_out m;
+    int e = or_mesh(n, xyz, r, D, c, cutoff_rel, precision, min_edge, max_depth, &m);
+    if (e) return e;
+    if (nv != m.n_vertices) { or_mesh_free(&m); return OR_ERR_ARG; }
+    oprob P;
+    e = oprob_init(&P, n, xyz, r, D, c, cutoff_rel, precision, min_edge, max_depth);
+    if (e) { or_mesh_free(&m); return e; }
+    double *lam = (double *)calloc((size_t)(m.n_lattice ? m.n_lattice : 1), sizeof(double));
+    omesh_ctx M = {&P, m.cube_keys, m.n_cubes, m.lattice_keys, m.lattice_phi, m.n_lattice};
+    for (int64_t i = 0; i < nv && !e; i++) {
+        const double *G = dLdp + 3 * i;
+        uint64_t K = m.vkeys[i];
+        unsigned type = (unsigned)((K >> 54) & 31u);
+        int l = (int)okey_level(K);
+        int64_t L[3];
+        okey_xyz(K, &L[0], &L[1], &L[2]);
+        int64_t s = (int64_t)1 << (max_depth - l);
+        double h = lvl_h(&P, l);
+        if (type <= 2) {
+            /* edge point (eq intersection): t = (c - g0)/(g1 - g0) along axis a */
+            int a = (int)type;
+            int64_t L1[3] = {L[0], L[1], L[2]};
+            L1[a] += s;
+            int64_t i0 = lattice_index(&m, L[0], L[1], L[2]), i1 = lattice_index(&m, L1[0], L1[1], L1[2]);
+            if (i0 < 0 || i1 < 0) { e = OR_ERR_CAP; break; }
+            double g0 = m.lattice_phi[i0], g1 = m.lattice_phi[i1];
+            double t = (c - g0) / (g1 - g0);
+            lam[i0] += G[a] * h * (-(1.0 - t) / (g1 - g0));
+            lam[i1] += G[a] * h * (-t / (g1 - g0));
+            continue;
+        }
+        /* extreme point (fold end on a face) or critical point: the cube */
+        int64_t C[3] = {L[0] / s, L[1] / s, L[2] / s};
+        int fa, fr, fb = -1, fj = 0;
+        if (type >= 8 && type < 20) {
+            int code = (int)type - 8;
+            fa = code >> 2;
+            fr = code & 1;
+            if (!((code >> 1) & 1)) C[fa] -= 1;   /* the end on the owner's upper face */
+        } else if (type >= 20 && type < 32) {
+            int code = (int)type - 20, pr = code >> 2;
+            fa = pr == 2 ? 1 : 0;
+            fb = pr == 0 ? 1 : 2;
+            fr = (code >> 1) & 1;
+            fj = code & 1;
+        } else {
+            continue;
+        }
+        double g[8];
+        if (!cube_values(&M, l, C[0], C[1], C[2], g)) { e = OR_ERR_CAP; break; }
+        int64_t li[8];
+        for (int v = 0; v < 8; v++) {
+            li[v] = lattice_index(&m, (C[0] + (v & 1)) * s, (C[1] + ((v >> 1) & 1)) * s, (C[2] + ((v >> 2) & 1)) * s);
+            if (li[v] < 0) { e = OR_ERR_CAP; break; }
+        }
+        if (e) break;
+        double ru[2], rv[2], du[8], dv[8], dp[3][8];
+        memset(dp, 0, sizeof(dp));
+        int ua, va;
+        other_axes(fa, &ua, &va);
+        if (fold_roots(g, fa, c, ru, rv) <= fr) { e = OR_ERR_CAP; break; }
+        fold_root_derivs(g, fa, c, ru[fr], rv[fr], du, dv);
+        if (fb < 0) {
+            for (int v = 0; v < 8; v++) { dp[ua][v] = du[v]; dp[va][v] = dv[v]; }
+        } else {
+            /* eq critical: coordinate fa from the b-root, the others from the a-root */
+            int cc = 3 - fa - fb, ub, vb;
+            for (int v = 0; v < 8; v++) {
+                dp[fb][v] = fb == ua ? du[v] : dv[v];
+                dp[cc][v] = cc == ua ? du[v] : dv[v];
+            }
+            other_axes(fb, &ub, &vb);
+            if (fold_roots(g, fb, c, ru, rv) <= fj) { e = OR_ERR_CAP; break; }
+            fold_root_derivs(g, fb, c, ru[fj], rv[fj], du, dv);
+            for (int v = 0; v < 8; v++) dp[fa][v] = fa == ub ? du[v] : dv[v];
+        }
+        for (int v = 0; v < 8; v++) lam[li[v]] += h * (G[0] * dp[0][v] + G[1] * dp[1][v] + G[2] * dp[2][v]);
+    }
+    /* the field (eq Gaussian1, truncated): dt/dx_i = 2D t (p - x_i),
+     * dt/dr_i = 2D t r_i, dt/dD = -t (|p - x_i|^2 - r_i^2), all atoms */
+    for (int64_t i = 0; i < n; i++) { g_xyz[3 * i] = g_xyz[3 * i + 1] = g_xyz[3 * i + 2] = 0.0; g_r[i] = 0.0; }
+    *g_D = 0.0;
+    for (int64_t k = 0; k < m.n_lattice && !e; k++) {
+        if (lam[k] == 0.0) continue;
+        int64_t x, y, z;
+        okey_xyz(m.lattice_keys[k], &x, &y, &z);
+        double p[3] = {lat_x(&P, 0, x, max_depth), lat_x(&P, 1, y, max_depth), lat_x(&P, 2, z, max_depth)};
+        for (int64_t i = 0; i < n; i++) {
+            double d[3] = {p[0] - xyz[3 * i], p[1] - xyz[3 * i + 1], p[2] - xyz[3 * i + 2]};
+            double d2 = d[0] * d[0] + d[1] * d[1] + d[2] * d[2];
+            if (d2 > P.R2[i]) continue;
+            double t = exp(-D * (d2 - r[i] * r[i]));
+            for (int q = 0; q < 3; q++) g_xyz[3 * i + q] += lam[k] * 2.0 * D * t * d[q];
+            g_r[i] += lam[k] * 2.0 * D * t * r[i];
+            *g_D -= lam[k] * t * (d2 - r[i] * r[i]);
+        }
+    }
+    free(lam);
+    oprob_free(&P);
+    or_mesh_free(&m);
+    return e;
+}
+
+/* enclosed volume and area of a closed outward mesh (plain sums) */
+void or_volume_area(int64_t nv, const double *v, int64_t nt, const int32_t *t, double *out2)
+{
+    (void)nv;
+    double vol = 0.0, area = 0.0;
+    for (int64_t i = 0; i < nt; i++) {
+        const double *p0 = v + 3 * t[3 * i], *p1 = v + 3 * t[3 * i + 1], *p2 = v + 3 * t[3 * i + 2];
+        double c12[3] = {p1[1] * p2[2] - p1[2] * p2[1], p1[2] * p2[0] - p1[0] * p2[2], p1[0] * p2[1] - p1[1] * p2[0]};
+        vol += (p0[0] * c12[0] + p0[1] * c12[1] + p0[2] * c12[2]) / 6.0;
+        double e1[3] = {p1[0] - p0[0], p1[1] - p0[1], p1[2] - p0[2]}, e2[3] = {p2[0] - p0[0], p2[1] - p0[1], p2[2] - p0[2]};
+        double n[3] = {e1[1] * e2[2] - e1[2] * e2[1], e1[2] * e2[0] - e1[0] * e2[2], e1[0] * e2[1] - e1[1] * e2[0]};
+        area += 0.5 * sqrt(n[0] * n[0] + n[1] * n[1] + n[2] * n[2]);
+    }
+    out2[0] = vol;
+    out2[1] = area;
+}

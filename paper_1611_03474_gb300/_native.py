@@ -97,6 +97,10 @@ def load():
     L.gs_bin_atoms_static.restype = i32
     L.gs_struct_size.argtypes = [i32]
     L.gs_struct_size.restype = i64
+    L.gs_mesh_backward.argtypes = [p, p, i64, d, d, d, i32, ctypes.POINTER(Options), p, i64, p, p, p]
+    L.gs_mesh_backward.restype = i32
+    L.gs_volume_area.argtypes = [p, i64, p, i64, p, p, p, ctypes.POINTER(Options)]
+    L.gs_volume_area.restype = i32
     for which, cls in ((0, Stats), (1, Options), (2, MeshC)):
         if L.gs_struct_size(which) != ctypes.sizeof(cls):
             raise GsError(-1, "ABI struct %s: library %d bytes, binding %d" % (cls.__name__, L.gs_struct_size(which),
@@ -271,3 +275,39 @@ def gs_bin_atoms_static(atoms, cell_size, origin, dims, cell_start, atom_perm, s
     dims = np.ascontiguousarray(dims, dtype=np.int64)
     _check(L.gs_bin_atoms_static(_ptr(atoms), int(atoms.shape[0]), cell_size, _ptr(origin), _ptr(dims),
                                  _ptr(cell_start), _ptr(atom_perm), _stream_ptr(stream)))
+
+
+def gs_mesh_backward(atoms, radii, D, c, precision, max_depth, grad_vertices, min_edge=0.25,
+                     precision_mode=GS_PREC_FP64, cutoff_rel=1e-8, stream=None):
+    """dL/d(atoms [n,3], radii [n], D) from dL/d(vertices) [nv,3] of the mesh
+    mesh_gaussian_surface returns for the same arguments (numpy arrays)."""
+    L = load()
+    atoms = _host64(atoms, (-1, 3))
+    radii = _host64(radii)
+    gv = _host64(grad_vertices, (-1, 3))
+    n = atoms.shape[0]
+    ga, gr, gD = np.zeros((n, 3)), np.zeros(n), np.zeros(1)
+    o = L.gs_default_options()
+    o.min_edge = min_edge
+    o.precision_mode = precision_mode
+    o.cutoff_rel = cutoff_rel
+    o.cuda_stream = _stream_ptr(stream)
+    _check(L.gs_mesh_backward(_ptr(atoms), _ptr(radii), n, D, c, precision, max_depth, ctypes.byref(o), _ptr(gv),
+                              gv.shape[0], _ptr(ga), _ptr(gr), _ptr(gD)))
+    return ga, gr, float(gD[0])
+
+
+def gs_volume_area(vertices, triangles, grad=False, stream=None):
+    """(volume, area) of a closed outward mesh, and with grad=True their
+    gradients per vertex ([nv,3] each)."""
+    L = load()
+    v = _host64(vertices, (-1, 3))
+    t = triangles if hasattr(triangles, "data_ptr") else np.ascontiguousarray(triangles, dtype=np.int32)
+    nv, nt = v.shape[0], t.shape[0]
+    va = np.zeros(2)
+    gV = np.zeros((nv, 3)) if grad else None
+    gA = np.zeros((nv, 3)) if grad else None
+    o = L.gs_default_options()
+    o.cuda_stream = _stream_ptr(stream)
+    _check(L.gs_volume_area(_ptr(v), nv, _ptr(t), nt, _ptr(va), _ptr(gV), _ptr(gA), ctypes.byref(o)))
+    return (va[0], va[1], gV, gA) if grad else (va[0], va[1])

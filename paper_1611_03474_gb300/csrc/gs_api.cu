@@ -166,6 +166,7 @@ struct Prepared {
     GsProblem P;
     GsAtomsSoA soa;
     int32_t *cell_start;
+    int32_t *perm;   // cell-ordered atom -> input index
 };
 
 // upload, prep, cell list; buffers registered in B
@@ -257,6 +258,7 @@ static int prepare(const double *atoms, const double *radii, int64_t n, double D
     if (!rc) rc = B.get(&S.fR2, (size_t)n);
     if (!rc) rc = B.get(&S.fr2, (size_t)n);
     if (rc) return rc;
+    out->perm = perm;
     rc = gs_gather_atoms(perm, n, d_xyz, d_r, d_R2, d_w, P.origin, P.cell, P.cdim, &S, st);
     if (rc) return rc;
     P.ax = S.x; P.ay = S.y; P.az = S.z; P.ar = S.r; P.aR2 = S.R2; P.aw = S.w;
@@ -442,8 +444,17 @@ __global__ void k_grid_cubes(int64_t nx, int64_t ny, int64_t nz, uint64_t *cubes
     cubes[i] = gk_make(i % nx, (i / nx) % ny, i / (nx * ny), GT_CUBE, 0);
 }
 
+// backward request: dL/d(mesh vertices) in, dL/d(atoms, radii, D) out
+struct BackReq {
+    const double *gv;   // [nv, 3], host or device
+    int64_t nv;
+    double *g_atoms, *g_radii, *g_D;   // host or device
+};
+
+static int put_out(void *dst, const void *src, size_t bytes, cudaStream_t st);
+
 static int mesh_impl(const double *atoms, const double *radii, int64_t n, double D, double c, double precision,
-                     int max_depth, const gs_options &o, gs_mesh *out, cudaStream_t st)
+                     int max_depth, const gs_options &o, gs_mesh *out, cudaStream_t st, const BackReq *bw = nullptr)
 {
     gs_stats local;
     gs_stats *stats = o.stats ? o.stats : &local;
@@ -572,8 +583,42 @@ static int mesh_impl(const double *atoms, const double *radii, int64_t n, double
     rc = surface_from_values(P, cubes, nc, cvid, phi, B, d_status, d_cnt + 10, M, stats, T);
     if (rc) return rc;
     int tw1 = T.mark();
-    rc = finish_output(M, o, out, st);
-    if (rc) return rc;
+    if (bw) {
+        // adjoint: dL/dp -> dL/dphi at the lattice vertices -> dL/d(atoms, radii, D)
+        if (bw->nv != M.nv)
+            return gs_fail(GS_ERR_ARG, "grad_vertices has %lld rows, the mesh %lld vertices", (long long)bw->nv,
+                           (long long)M.nv);
+        const double *gv = bw->gv;
+        if (M.nv > 0 && !on_device(gv)) {
+            double *tmp = nullptr;
+            rc = B.get(&tmp, 3 * (size_t)M.nv);
+            if (rc) return rc;
+            GS_CHECK(cudaMemcpyAsync(tmp, gv, sizeof(double) * 3 * (size_t)M.nv, cudaMemcpyHostToDevice, st));
+            gv = tmp;
+        }
+        double *lambda = nullptr, *g = nullptr;
+        rc = B.get(&lambda, (size_t)nv + 1);
+        if (!rc) rc = B.get(&g, 4 * (size_t)n + 1);
+        if (rc) return rc;
+        GS_CHECK(cudaMemsetAsync(g, 0, sizeof(double) * (4 * (size_t)n + 1), st));
+        TriCtx X;
+        memset(&X, 0, sizeof(X));
+        X.cubes = cubes; X.cvid = cvid; X.phi = phi; X.ncubes = nc; X.c = P.c;
+        for (int a3 = 0; a3 < 3; a3++) X.origin[a3] = P.origin[a3];
+        X.min_edge = P.min_edge; X.max_depth = P.max_depth;
+        rc = gs_vertex_adjoint(X, vkeys, nv, M.vkeys, gv, M.nv, lambda, d_status, st);
+        if (!rc) rc = gs_field_adjoint(P, PR.perm, vkeys, lambda, nv, g, g + 3 * n, g + 4 * n, st);
+        if (!rc) rc = check_status(d_status, st, "adjoint");
+        if (!rc && bw->g_atoms) rc = put_out(bw->g_atoms, g, sizeof(double) * 3 * (size_t)n, st);
+        if (!rc && bw->g_radii) rc = put_out(bw->g_radii, g + 3 * n, sizeof(double) * (size_t)n, st);
+        if (!rc && bw->g_D) rc = put_out(bw->g_D, g + 4 * n, sizeof(double), st);
+        if (rc) return rc;
+        GS_CHECK(cudaStreamSynchronize(st));
+    }
+    if (out) {
+        rc = finish_output(M, o, out, st);
+        if (rc) return rc;
+    }
     int tend = T.mark();
     GS_CHECK(cudaStreamSynchronize(st));
     unsigned long long h[32];
@@ -596,7 +641,7 @@ static int mesh_impl(const double *atoms, const double *radii, int64_t n, double
     stats->atom_octets = (int64_t)h[24];
     stats->vertex_terms = (int64_t)h[9];
     stats->recheck_cubes = (int64_t)h[13];
-    out->mismatches = (int64_t)h[14];
+    if (out) out->mismatches = (int64_t)h[14];
     stats->conformity_splits = splits;
     stats->n_cubes_final = nc;
     stats->n_lattice_vertices = nv;
@@ -611,12 +656,9 @@ static int mesh_impl(const double *atoms, const double *radii, int64_t n, double
     return GS_OK;
 }
 
-extern "C" int mesh_gaussian_surface(const double *atoms, const double *radii, int64_t n_atoms, double D, double c,
-                                     double precision, int max_depth, const gs_options *opt, gs_mesh *out)
+static int check_mesh_args(const double *atoms, const double *radii, int64_t n_atoms, double D, double c,
+                           double precision, int max_depth, const gs_options &o)
 {
-    if (!out) return gs_fail(GS_ERR_ARG, "out is NULL");
-    memset(out, 0, sizeof(*out));
-    gs_options o = opt ? *opt : gs_default_options();
     if (!atoms || !radii || n_atoms <= 0 || n_atoms > ((int64_t)1 << 31) - 1)
         return gs_fail(GS_ERR_ARG, "need 1 <= n_atoms < 2^31 and non-NULL inputs");
     if (!(D > 0) || !std::isfinite(D) || !(c > 0) || !std::isfinite(c) || !(precision > 0) || !std::isfinite(precision))
@@ -626,7 +668,18 @@ extern "C" int mesh_gaussian_surface(const double *atoms, const double *radii, i
     if (!(o.cutoff_rel > 0 && o.cutoff_rel < 1)) return gs_fail(GS_ERR_ARG, "cutoff_rel must be in (0,1)");
     if (o.precision_mode != GS_PREC_FP64 && o.precision_mode != GS_PREC_MIXED)
         return gs_fail(GS_ERR_ARG, "unknown precision mode");
-    int rc = device_setup();
+    return GS_OK;
+}
+
+extern "C" int mesh_gaussian_surface(const double *atoms, const double *radii, int64_t n_atoms, double D, double c,
+                                     double precision, int max_depth, const gs_options *opt, gs_mesh *out)
+{
+    if (!out) return gs_fail(GS_ERR_ARG, "out is NULL");
+    memset(out, 0, sizeof(*out));
+    gs_options o = opt ? *opt : gs_default_options();
+    int rc = check_mesh_args(atoms, radii, n_atoms, D, c, precision, max_depth, o);
+    if (rc) return rc;
+    rc = device_setup();
     if (rc) return rc;
     cudaStream_t st = (cudaStream_t)o.cuda_stream;
     bool own = false;
@@ -639,6 +692,111 @@ extern "C" int mesh_gaussian_surface(const double *atoms, const double *radii, i
     if (own) cudaStreamDestroy(st);
     if (!rc && e != cudaSuccess) rc = gs_fail_cuda(e, "stream", __FILE__, __LINE__);
     if (rc) mesh_free(out);
+    return rc;
+}
+
+extern "C" int gs_mesh_backward(const double *atoms, const double *radii, int64_t n_atoms, double D, double c,
+                                double precision, int max_depth, const gs_options *opt, const double *grad_vertices,
+                                int64_t n_vertices, double *grad_atoms, double *grad_radii, double *grad_D)
+{
+    gs_options o = opt ? *opt : gs_default_options();
+    int rc = check_mesh_args(atoms, radii, n_atoms, D, c, precision, max_depth, o);
+    if (rc) return rc;
+    if (n_vertices < 0 || (n_vertices > 0 && !grad_vertices))
+        return gs_fail(GS_ERR_ARG, "grad_vertices is NULL");
+    rc = device_setup();
+    if (rc) return rc;
+    cudaStream_t st = (cudaStream_t)o.cuda_stream;
+    bool own = false;
+    if (!st) {
+        GS_CHECK(cudaStreamCreateWithFlags(&st, cudaStreamNonBlocking));
+        own = true;
+    }
+    BackReq bw;
+    bw.gv = grad_vertices;
+    bw.nv = n_vertices;
+    bw.g_atoms = grad_atoms;
+    bw.g_radii = grad_radii;
+    bw.g_D = grad_D;
+    rc = mesh_impl(atoms, radii, n_atoms, D, c, precision, max_depth, o, nullptr, st, &bw);
+    cudaError_t e = cudaStreamSynchronize(st);
+    if (own) cudaStreamDestroy(st);
+    if (!rc && e != cudaSuccess) rc = gs_fail_cuda(e, "stream", __FILE__, __LINE__);
+    return rc;
+}
+
+static int put_in(void *dst, const void *src, size_t bytes, cudaStream_t st)
+{
+    GS_CHECK(cudaMemcpyAsync(dst, src, bytes, cudaMemcpyHostToDevice, st));
+    return GS_OK;
+}
+
+__global__ void k_check_tri(const int32_t *t, int64_t n3, int64_t nv, unsigned *status)
+{
+    int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < n3 && (t[i] < 0 || t[i] >= nv)) atomicOr(status, 1u);
+}
+
+// every triangle index must name a vertex (the kernels read without checks)
+static int check_tri_ids(const int32_t *d_t, int64_t nt, int64_t nv, unsigned *d_status, cudaStream_t st)
+{
+    GS_CHECK(cudaMemsetAsync(d_status, 0, sizeof(unsigned), st));
+    GS_LAUNCH(k_check_tri, (unsigned)((3 * nt + 255) / 256), 256, 0, st)(d_t, 3 * nt, nv, d_status);
+    unsigned h = 0;
+    GS_CHECK(cudaMemcpyAsync(&h, d_status, sizeof(h), cudaMemcpyDeviceToHost, st));
+    GS_CHECK(cudaStreamSynchronize(st));
+    return h ? gs_fail(GS_ERR_ARG, "a triangle index is outside [0, n_vertices)") : GS_OK;
+}
+
+extern "C" int gs_volume_area(const double *vertices, int64_t n_vertices, const int32_t *triangles,
+                              int64_t n_triangles, double *volume_area, double *grad_volume, double *grad_area,
+                              const gs_options *opt)
+{
+    gs_options o = opt ? *opt : gs_default_options();
+    if (n_vertices < 0 || n_triangles < 0 || !volume_area || (n_vertices > 0 && !vertices) ||
+        (n_triangles > 0 && !triangles) || n_vertices > ((int64_t)1 << 31))
+        return gs_fail(GS_ERR_ARG, "bad arguments");
+    int rc = device_setup();
+    if (rc) return rc;
+    cudaStream_t st = (cudaStream_t)o.cuda_stream;
+    bool own = false;
+    if (!st) {
+        GS_CHECK(cudaStreamCreateWithFlags(&st, cudaStreamNonBlocking));
+        own = true;
+    }
+    {
+        DevBufs B(st);
+        const double *v = vertices;
+        const int32_t *t = triangles;
+        double *acc = nullptr, *gV = nullptr, *gA = nullptr;
+        unsigned *d_status = nullptr;
+        rc = B.get(&acc, 2);
+        if (!rc) rc = B.get(&d_status, 1);
+        if (!rc && n_vertices && !on_device(vertices)) {
+            double *tv = nullptr;
+            rc = B.get(&tv, 3 * (size_t)n_vertices);
+            if (!rc) rc = put_in(tv, vertices, sizeof(double) * 3 * (size_t)n_vertices, st);
+            v = tv;
+        }
+        if (!rc && n_triangles && !on_device(triangles)) {
+            int32_t *tt = nullptr;
+            rc = B.get(&tt, 3 * (size_t)n_triangles);
+            if (!rc) rc = put_in(tt, triangles, sizeof(int32_t) * 3 * (size_t)n_triangles, st);
+            t = tt;
+        }
+        if (!rc && n_triangles) rc = check_tri_ids(t, n_triangles, n_vertices, d_status, st);
+        if (!rc && grad_volume) rc = B.get(&gV, 3 * (size_t)n_vertices + 1);
+        if (!rc && grad_area) rc = B.get(&gA, 3 * (size_t)n_vertices + 1);
+        if (!rc && gV) GS_CHECK(cudaMemsetAsync(gV, 0, sizeof(double) * 3 * (size_t)n_vertices, st));
+        if (!rc && gA) GS_CHECK(cudaMemsetAsync(gA, 0, sizeof(double) * 3 * (size_t)n_vertices, st));
+        if (!rc) rc = gs_volume_area_dev(v, t, n_triangles, acc, gV, gA, st);
+        if (!rc) rc = put_out(volume_area, acc, 2 * sizeof(double), st);
+        if (!rc && gV) rc = put_out(grad_volume, gV, sizeof(double) * 3 * (size_t)n_vertices, st);
+        if (!rc && gA) rc = put_out(grad_area, gA, sizeof(double) * 3 * (size_t)n_vertices, st);
+        cudaError_t e = cudaStreamSynchronize(st);
+        if (!rc && e != cudaSuccess) rc = gs_fail_cuda(e, "stream", __FILE__, __LINE__);
+    }
+    if (own) cudaStreamDestroy(st);
     return rc;
 }
 

@@ -270,3 +270,61 @@ int gs_field_recompute(const GsProblem &P, const uint64_t *d_vkeys, int64_t n, i
     *n_recomputed = m;
     return GS_OK;
 }
+
+// ---------------------------------------------------------------- adjoint
+// dL/dtheta = sum_v lambda_v dphi(v)/dtheta with the field's terms
+// recomputed (not stored): for t = exp(-D (|v - x_i|^2 - r_i^2)),
+//   dt/dx_i = 2 D t (v - x_i),  dt/dr_i = 2 D t r_i,  dt/dD = -t (|v - x_i|^2 - r_i^2).
+// The cutoff sphere moves with r_i and D; its terms are ~cutoff_rel c and
+// their jump is not differentiated.
+__global__ void __launch_bounds__(128) k_field_adjoint(GsProblem P, const int32_t *__restrict__ perm,
+                                                       const uint64_t *vkeys, const double *__restrict__ lambda,
+                                                       int64_t n, double *gx, double *gr, double *gD)
+{
+    int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    double dD = 0.0;
+    const double lam = i < n ? lambda[i] : 0.0;
+    if (lam != 0.0) {
+        double p[3];
+        point_of(P, vkeys, nullptr, i, p);
+        const double D = P.D, nD = -P.D;
+        float ph[3], pl[3];
+        for (int a = 0; a < 3; a++) {
+            double rel = p[a] - P.origin[a];
+            ph[a] = (float)rel;
+            pl[a] = (float)(rel - (double)ph[a]);
+        }
+        gs_for_rows(P, ph, ph, [&](int b, int e, int64_t, int) {
+            for (int k = b; k < e; k++) {
+                float fx = (ph[0] - P.hx[k]) + (pl[0] - P.lx[k]);
+                float fy = (ph[1] - P.hy[k]) + (pl[1] - P.ly[k]);
+                float fz = (ph[2] - P.hz[k]) + (pl[2] - P.lz[k]);
+                float f2 = fx * fx + fy * fy + fz * fz;
+                if (f2 > P.fR2[k] * (1.f + 1e-5f) + 1e-5f) continue;
+                double dx = __dsub_rn(p[0], P.ax[k]), dy = __dsub_rn(p[1], P.ay[k]), dz = __dsub_rn(p[2], P.az[k]);
+                double d2 = __dadd_rn(__dadd_rn(__dmul_rn(dx, dx), __dmul_rn(dy, dy)), __dmul_rn(dz, dz));
+                if (d2 > P.aR2[k]) continue;
+                const double t = P.aw[k] * gs_exp(nD * d2), r = P.ar[k];
+                const double s = lam * 2.0 * D * t;
+                const int64_t o = perm[k];
+                atomicAdd(&gx[3 * o], s * dx);
+                atomicAdd(&gx[3 * o + 1], s * dy);
+                atomicAdd(&gx[3 * o + 2], s * dz);
+                atomicAdd(&gr[o], s * r);
+                dD -= lam * t * (d2 - r * r);
+            }
+        });
+    }
+    for (int o = 16; o > 0; o >>= 1) dD += __shfl_xor_sync(0xffffffffu, dD, o);
+    if ((threadIdx.x & 31) == 0 && dD != 0.0) atomicAdd(gD, dD);
+}
+
+int gs_field_adjoint(const GsProblem &P, const int32_t *d_perm, const uint64_t *d_vkeys, const double *d_lambda,
+                     int64_t nv, double *d_gx, double *d_gr, double *d_gD, cudaStream_t st)
+{
+    if (nv <= 0) return GS_OK;
+    GS_LAUNCH(k_field_adjoint, (unsigned)((nv + 127) / 128), 128, 0, st)(P, d_perm, d_vkeys, d_lambda, nv, d_gx, d_gr,
+                                                                        d_gD);
+    GS_CHECK(cudaGetLastError());
+    return GS_OK;
+}

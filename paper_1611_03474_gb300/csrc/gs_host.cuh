@@ -85,6 +85,17 @@ struct TriCtx {
 };
 // mixed precision: mark (mark[v] = 1) the corners whose FP32 error could move
 // a surface point by more than tol_A or flip a face or fold decision
+// adjoint of the triangulation: dL/dp per mesh vertex -> dL/dphi per lattice
+// vertex (d_lambda [nlat], overwritten)
+int gs_vertex_adjoint(const TriCtx &X, const uint64_t *d_lat_keys, int64_t nlat, const uint64_t *d_mkeys,
+                      const double *d_gv, int64_t nm, double *d_lambda, unsigned *d_status, cudaStream_t st);
+// volume and area of a closed mesh (d_acc[2]) and their vertex gradients (nullable, accumulated)
+int gs_volume_area_dev(const double *d_v, const int32_t *d_tri, int64_t nt, double *d_acc, double *d_gV, double *d_gA,
+                       cudaStream_t st);
+// adjoint of the field: lambda per lattice vertex -> dL/d(atom centre, radius, D), accumulated
+int gs_field_adjoint(const GsProblem &P, const int32_t *d_perm, const uint64_t *d_vkeys, const double *d_lambda,
+                     int64_t nv, double *d_gx, double *d_gr, double *d_gD, cudaStream_t st);
+__global__ void k_hash_index(GsHash H, const uint64_t *keys, int64_t n, unsigned *status);
 // d_why (nullable) counts the cubes marked through an edge point, a face
 // saddle and a fold root
 int gs_tri_marks(const TriCtx &X, const float *d_err, double tol_A, int64_t *d_mark, unsigned long long *d_why,

@@ -842,3 +842,234 @@ int gs_tri_marks(const TriCtx &X, const float *d_err, double tol_A, int64_t *d_m
     GS_CHECK(cudaGetLastError());
     return GS_OK;
 }
+
+// ---------------------------------------------------------------- adjoint
+// With the cube set and the topology held fixed, every mesh vertex is a
+// function of the lattice values of one cube: an edge point of its edge's
+// two end values (eq intersection), an extreme point of its owner cube's
+// eight corners through the fold equations A = B = 0 (eq fold1), a critical
+// point of the two fold roots that define it.  k_vertex_adjoint pulls
+// dL/dp back to dL/dphi at the lattice vertices (lambda).
+
+// derivatives of a fold root (u, v) of axis a with respect to the eight
+// corner values: J (du, dv) = -(dA, dB), with A the bilinear interpolant of
+// the lower face minus c and B that of upper minus lower, J their Jacobian
+__device__ void fold_root_grad(const double *g, int a, double u, double v, double du[8], double dv[8])
+{
+    int ua, va;
+    axes_other(a, ua, va);
+    double lo[4], up[4];
+    int ilo[4], iup[4];
+    for (int k = 0; k < 4; k++) {
+        int b[3];
+        b[a] = 0; b[ua] = k & 1; b[va] = k >> 1;
+        ilo[k] = b[0] + 2 * b[1] + 4 * b[2];
+        b[a] = 1;
+        iup[k] = b[0] + 2 * b[1] + 4 * b[2];
+        lo[k] = g[ilo[k]];
+        up[k] = g[iup[k]];
+    }
+    double p1 = lo[1] - lo[0], p2 = lo[2] - lo[0], p3 = lo[3] - lo[1] - lo[2] + lo[0];
+    double d0 = up[0] - lo[0], d1 = up[1] - lo[1], d2 = up[2] - lo[2], d3 = up[3] - lo[3];
+    double q1 = d1 - d0, q2 = d2 - d0, q3 = d3 - d1 - d2 + d0;
+    double J11 = p1 + p3 * v, J12 = p2 + p3 * u, J21 = q1 + q3 * v, J22 = q2 + q3 * u;
+    double det = J11 * J22 - J12 * J21;
+    double inv = det != 0.0 ? 1.0 / det : 0.0;
+    double w[4] = {(1 - u) * (1 - v), u * (1 - v), (1 - u) * v, u * v};
+    for (int k = 0; k < 8; k++) { du[k] = 0; dv[k] = 0; }
+    for (int k = 0; k < 4; k++) {
+        // lower corner: dA = w, dB = -w; upper corner: dA = 0, dB = w
+        du[ilo[k]] = -w[k] * (J22 + J12) * inv;
+        dv[ilo[k]] = w[k] * (J21 + J11) * inv;
+        du[iup[k]] = J12 * w[k] * inv;
+        dv[iup[k]] = -J11 * w[k] * inv;
+    }
+}
+
+struct AdjCtx {
+    TriCtx X;
+    GsHash lat;                 // lattice vertex key -> id
+    GsHash cub;                 // cube key -> index
+    const uint64_t *mkeys;      // mesh vertex keys
+    const double *gv;           // dL/dp per mesh vertex [n, 3]
+    int64_t nm;
+    double *lambda;             // dL/dphi per lattice vertex
+};
+
+__device__ __forceinline__ int64_t adj_lat(const AdjCtx &C, int64_t x, int64_t y, int64_t z)
+{
+    int64_t s = gs_hash_find(C.lat, gk_make(x, y, z, GT_VERT, 0));
+    return s < 0 ? -1 : (int64_t)C.lat.vals[s];
+}
+
+__global__ void __launch_bounds__(128) k_vertex_adjoint(AdjCtx C, unsigned *status)
+{
+    int64_t m = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (m >= C.nm) return;
+    const double G[3] = {C.gv[3 * m], C.gv[3 * m + 1], C.gv[3 * m + 2]};
+    if (G[0] == 0.0 && G[1] == 0.0 && G[2] == 0.0) return;
+    const uint64_t K = C.mkeys[m];
+    const unsigned type = gk_type(K), lvl = gk_level(K);
+    const int64_t L[3] = {gk_x(K), gk_y(K), gk_z(K)};
+    const int64_t sc = (int64_t)1 << (C.X.max_depth - (int)lvl);
+    const double h = ldexp(C.X.min_edge, C.X.max_depth - (int)lvl);
+    const double c = C.X.c;
+    if (type <= 2) {
+        // edge point: t = (c - g0) / (g1 - g0) along axis a
+        const int a = (int)type;
+        int64_t L1[3] = {L[0], L[1], L[2]};
+        L1[a] += sc;
+        int64_t i0 = adj_lat(C, L[0], L[1], L[2]), i1 = adj_lat(C, L1[0], L1[1], L1[2]);
+        if (i0 < 0 || i1 < 0) { atomicOr(status, GS_ST_LOOKUP); return; }
+        double g0 = C.X.phi[i0], g1 = C.X.phi[i1], dg = g1 - g0;
+        if (dg == 0.0) return;
+        double t = (c - g0) / dg;
+        atomicAdd(&C.lambda[i0], G[a] * h * (-(1.0 - t) / dg));
+        atomicAdd(&C.lambda[i1], G[a] * h * (-t / dg));
+        return;
+    }
+    // extreme (8 + 4a + 2 side + rank) or critical (20 + 4 (a + b - 1) + 2 i + j) point
+    int64_t cube[3] = {L[0], L[1], L[2]};
+    int fa = -1, fr = 0, fb = -1, fj = 0;
+    if (type >= 8 && type < 20) {
+        const int code = (int)type - 8;
+        fa = code >> 2;
+        fr = code & 1;
+        if (!((code >> 1) & 1)) cube[fa] -= sc;   // the end on the owner's upper face
+    } else if (type >= 20 && type < 32) {
+        const int code = (int)type - 20, pr = code >> 2;
+        fa = pr == 2 ? 1 : 0;
+        fb = pr == 0 ? 1 : 2;
+        fr = (code >> 1) & 1;
+        fj = code & 1;
+    } else {
+        return;
+    }
+    int64_t s = gs_hash_find(C.cub, gk_make(cube[0] / sc, cube[1] / sc, cube[2] / sc, GT_CUBE, lvl));
+    if (s < 0) { atomicOr(status, GS_ST_LOOKUP); return; }
+    const int64_t ci = (int64_t)C.cub.vals[s];
+    double g[8];
+    int64_t vid[8];
+    for (int v = 0; v < 8; v++) {
+        vid[v] = C.X.cvid[ci * 8 + v];
+        g[v] = C.X.phi[vid[v]];
+    }
+    double dp[3][8];
+    for (int q = 0; q < 3; q++)
+        for (int v = 0; v < 8; v++) dp[q][v] = 0.0;
+    double ru[2], rv[2], du[8], dv[8];
+    int ua, va;
+    int nr = fold_solve(g, fa, c, ru, rv);
+    if (fr >= nr) { atomicOr(status, GS_ST_LOOKUP); return; }
+    axes_other(fa, ua, va);
+    fold_root_grad(g, fa, ru[fr], rv[fr], du, dv);
+    if (fb < 0) {
+        for (int v = 0; v < 8; v++) { dp[ua][v] = du[v]; dp[va][v] = dv[v]; }
+    } else {
+        // coordinate fa from the b-root, the other two from the a-root (the
+        // shared coordinate is the a-root's)
+        const int cc = 3 - fa - fb;
+        for (int v = 0; v < 8; v++) {
+            dp[fb][v] = fb == ua ? du[v] : dv[v];
+            dp[cc][v] = cc == ua ? du[v] : dv[v];
+        }
+        int ub, vb;
+        axes_other(fb, ub, vb);
+        int nb = fold_solve(g, fb, c, ru, rv);
+        if (fj >= nb) { atomicOr(status, GS_ST_LOOKUP); return; }
+        fold_root_grad(g, fb, ru[fj], rv[fj], du, dv);
+        for (int v = 0; v < 8; v++) dp[fa][v] = fa == ub ? du[v] : dv[v];
+    }
+    for (int v = 0; v < 8; v++) {
+        double lam = h * (G[0] * dp[0][v] + G[1] * dp[1][v] + G[2] * dp[2][v]);
+        if (lam != 0.0) atomicAdd(&C.lambda[vid[v]], lam);
+    }
+}
+
+// volume sum p0.(p1 x p2)/6 and area sum |(p1-p0) x (p2-p0)|/2 of a closed,
+// outward-oriented mesh, with their gradients per vertex (nullable)
+__global__ void __launch_bounds__(256) k_volume_area(const double *__restrict__ v, const int32_t *__restrict__ tri,
+                                                     int64_t nt, double *acc, double *gV, double *gA)
+{
+    int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    double vol = 0.0, area = 0.0;
+    if (t < nt) {
+        const int32_t i[3] = {tri[3 * t], tri[3 * t + 1], tri[3 * t + 2]};
+        double p[3][3];
+        for (int k = 0; k < 3; k++)
+            for (int q = 0; q < 3; q++) p[k][q] = v[3 * (int64_t)i[k] + q];
+        auto cross = [](const double *x, const double *y, double *o) {
+            o[0] = x[1] * y[2] - x[2] * y[1];
+            o[1] = x[2] * y[0] - x[0] * y[2];
+            o[2] = x[0] * y[1] - x[1] * y[0];
+        };
+        double c12[3], c20[3], c01[3];
+        cross(p[1], p[2], c12);
+        cross(p[2], p[0], c20);
+        cross(p[0], p[1], c01);
+        vol = (p[0][0] * c12[0] + p[0][1] * c12[1] + p[0][2] * c12[2]) / 6.0;
+        double e1[3], e2[3], n[3];
+        for (int q = 0; q < 3; q++) { e1[q] = p[1][q] - p[0][q]; e2[q] = p[2][q] - p[0][q]; }
+        cross(e1, e2, n);
+        double nn = sqrt(n[0] * n[0] + n[1] * n[1] + n[2] * n[2]);
+        area = 0.5 * nn;
+        if (gV)
+            for (int q = 0; q < 3; q++) {
+                atomicAdd(&gV[3 * (int64_t)i[0] + q], c12[q] / 6.0);
+                atomicAdd(&gV[3 * (int64_t)i[1] + q], c20[q] / 6.0);
+                atomicAdd(&gV[3 * (int64_t)i[2] + q], c01[q] / 6.0);
+            }
+        if (gA && nn > 0.0) {
+            double nh[3] = {n[0] / nn, n[1] / nn, n[2] / nn};
+            // d area / d p_k = n_hat x (p_{k+2} - p_{k+1}) / 2
+            for (int k = 0; k < 3; k++) {
+                double d[3], o[3];
+                for (int q = 0; q < 3; q++) d[q] = p[(k + 2) % 3][q] - p[(k + 1) % 3][q];
+                cross(nh, d, o);
+                for (int q = 0; q < 3; q++) atomicAdd(&gA[3 * (int64_t)i[k] + q], 0.5 * o[q]);
+            }
+        }
+    }
+    for (int o = 16; o > 0; o >>= 1) {
+        vol += __shfl_xor_sync(0xffffffffu, vol, o);
+        area += __shfl_xor_sync(0xffffffffu, area, o);
+    }
+    if ((threadIdx.x & 31) == 0) {
+        atomicAdd(&acc[0], vol);
+        atomicAdd(&acc[1], area);
+    }
+}
+
+int gs_vertex_adjoint(const TriCtx &X, const uint64_t *d_lat_keys, int64_t nlat, const uint64_t *d_mkeys,
+                      const double *d_gv, int64_t nm, double *d_lambda, unsigned *d_status, cudaStream_t st)
+{
+    AdjCtx C;
+    C.X = X;
+    C.mkeys = d_mkeys;
+    C.gv = d_gv;
+    C.nm = nm;
+    C.lambda = d_lambda;
+    int rc = gs_hash_make(&C.lat, nlat, st);
+    if (rc) return rc;
+    rc = gs_hash_make(&C.cub, X.ncubes, st);
+    if (rc) { gs_hash_free(&C.lat, st); return rc; }
+    GS_CHECK(cudaMemsetAsync(d_lambda, 0, sizeof(double) * (size_t)(nlat + 1), st));
+    if (nlat > 0) GS_LAUNCH(k_hash_index, (unsigned)((nlat + 255) / 256), 256, 0, st)(C.lat, d_lat_keys, nlat, d_status);
+    if (X.ncubes > 0)
+        GS_LAUNCH(k_hash_index, (unsigned)((X.ncubes + 255) / 256), 256, 0, st)(C.cub, X.cubes, X.ncubes, d_status);
+    if (nm > 0) GS_LAUNCH(k_vertex_adjoint, (unsigned)((nm + 127) / 128), 128, 0, st)(C, d_status);
+    gs_hash_free(&C.lat, st);
+    gs_hash_free(&C.cub, st);
+    GS_CHECK(cudaGetLastError());
+    return GS_OK;
+}
+
+int gs_volume_area_dev(const double *d_v, const int32_t *d_tri, int64_t nt, double *d_acc, double *d_gV, double *d_gA,
+                       cudaStream_t st)
+{
+    GS_CHECK(cudaMemsetAsync(d_acc, 0, 2 * sizeof(double), st));
+    if (nt > 0)
+        GS_LAUNCH(k_volume_area, (unsigned)((nt + 255) / 256), 256, 0, st)(d_v, d_tri, nt, d_acc, d_gV, d_gA);
+    GS_CHECK(cudaGetLastError());
+    return GS_OK;
+}

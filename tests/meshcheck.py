@@ -118,3 +118,51 @@ def canonical_triangles(keys, F):
 def check_closed_manifold(V, F):
     assert directed_edge_defects(F) == 0, "edge not shared by exactly two oppositely oriented triangles"
     assert link_defects(F, len(V)) == 0, "vertex link is not a single loop"
+
+
+# ---------------------------------------------------------------- differentiation
+def key_normal_weights(keys, seed=0):
+    """w_v ~ N(0,1)^3 per vertex, drawn from a counter-based hash of the
+    vertex key (so that two meshes with the same keys get the same weights
+    whatever their vertex order): splitmix64 of (key, seed, axis), Box-Muller."""
+    k = np.asarray(keys, dtype=np.uint64)
+    M = np.uint64(0xFFFFFFFFFFFFFFFF)
+
+    def mix(x):
+        x = (x + np.uint64(0x9E3779B97F4A7C15)) & M
+        x = ((x ^ (x >> np.uint64(30))) * np.uint64(0xBF58476D1CE4E5B9)) & M
+        x = ((x ^ (x >> np.uint64(27))) * np.uint64(0x94D049BB133111EB)) & M
+        return x ^ (x >> np.uint64(31))
+
+    out = np.zeros((len(k), 3))
+    with np.errstate(over="ignore"):
+        for q in range(3):
+            a = mix(k ^ mix(np.uint64(seed * 6 + 2 * q)))
+            b = mix(k ^ mix(np.uint64(seed * 6 + 2 * q + 1)))
+            u1 = ((a >> np.uint64(11)).astype(np.float64) + 0.5) / 2.0 ** 53
+            u2 = ((b >> np.uint64(11)).astype(np.float64) + 0.5) / 2.0 ** 53
+            out[:, q] = np.sqrt(-2.0 * np.log(u1)) * np.cos(2.0 * np.pi * u2)
+    return out
+
+
+def surface_loss(vertices, triangles, W):
+    """L = sum_v W_v . p_v + enclosed volume + surface area (plain numpy)."""
+    v, t = np.asarray(vertices), np.asarray(triangles)
+    p0, p1, p2 = v[t[:, 0]], v[t[:, 1]], v[t[:, 2]]
+    vol = np.einsum("ij,ij->", p0, np.cross(p1, p2)) / 6.0
+    area = 0.5 * np.linalg.norm(np.cross(p1 - p0, p2 - p0), axis=1).sum()
+    return float((W * v).sum() + vol + area)
+
+
+def surface_loss_grad(vertices, triangles, W):
+    """dL/dp of surface_loss: W + sum over triangles of (p_{k+1} x p_{k+2})/6
+    + n_hat x (p_{k+2} - p_{k+1})/2 at each corner k."""
+    v, t = np.asarray(vertices), np.asarray(triangles)
+    g = np.array(W, dtype=np.float64, copy=True)
+    p0, p1, p2 = v[t[:, 0]], v[t[:, 1]], v[t[:, 2]]
+    n = np.cross(p1 - p0, p2 - p0)
+    nh = n / np.linalg.norm(n, axis=1)[:, None]
+    for k in range(3):
+        a, b = v[t[:, (k + 1) % 3]], v[t[:, (k + 2) % 3]]
+        np.add.at(g, t[:, k], np.cross(a, b) / 6.0 + 0.5 * np.cross(nh, b - a))
+    return g
