@@ -149,6 +149,7 @@ def main():
     ap.add_argument("--ref-sample", type=int, default=300)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--fp64-steps", type=int, default=1, help="extra FP64-form steps timed for comparison")
+    ap.add_argument("--diff-steps", type=int, default=2, help="differentiation-form steps (10k atoms) to time")
     args = ap.parse_args()
     ws, rank, local = dist_env()
     if args.impl == "reference":
@@ -251,6 +252,32 @@ def main():
         fp64["max_vertex_diff_A"] = float(np.abs(mh.vertices - mfh.vertices).max()) if same else None
         del mfh
 
+    # differentiation form on the 10,000-atom globular molecule: forward mesh,
+    # loss gradient per vertex, adjoint (gs_mesh_backward recomputes the mesh)
+    diff = None
+    if args.diff_steps > 0 and ws == 1:
+        dcfg = synth.config("globular10k")
+        dx, dr = dcfg["xyz"], dcfg["r"]
+        tf, tb = [], []
+        for it in range(args.diff_steps + 1):
+            barrier()
+            t0 = time.perf_counter()
+            dm = gs.mesh_gaussian_surface(dx, dr, dcfg["D"], dcfg["c"], dcfg["precision"], dcfg["max_depth"],
+                                          min_edge=dcfg["min_edge"], stream=stream)
+            t1 = time.perf_counter()
+            vol, area, gV, gA = gs.gs_volume_area(dm.vertices, dm.triangles, grad=True, stream=stream)
+            gv = gV + gA
+            t2 = time.perf_counter()
+            gs.gs_mesh_backward(dx, dr, dcfg["D"], dcfg["c"], dcfg["precision"], dcfg["max_depth"], gv,
+                                min_edge=dcfg["min_edge"], stream=stream)
+            t3 = time.perf_counter()
+            if it > 0:
+                tf.append((t1 - t0) * 1e3)
+                tb.append((t3 - t1) * 1e3)
+        diff = {"workload": "globular10k: 10,000 atoms, D=0.5, c=1, L = volume + area, host buffers",
+                "ms_forward": float(np.mean(tf)), "ms_backward": float(np.mean(tb)),
+                "n_vertices": int(dm.vertices.shape[0]), "volume_A3": float(vol), "area_A2": float(area)}
+
     st = stats[-1]
     pairs = st["pair_terms"]
     acc_ms = float(np.mean([s["ms_accum"] for s in stats]))
@@ -289,6 +316,7 @@ def main():
                 "d2h_bytes_per_step": int(nbytes_out)},
         "gpu_launches": int(st["n_kernel_launches"]),
         "fp64_form": fp64,
+        "diff_form": diff,
     }
     if rank == 0 and ws == 1 and not args.no_cpu_baseline:
         line["cpu_baseline"] = cpu_baseline(cfg)
