@@ -48,10 +48,25 @@ __device__ __forceinline__ double corner(const double *g, int bx, int by, int bz
 // roots (u,v) in the open unit square of {B = 0, A = c} for g = A + s B along axis a
 // roots (u, v) of the fold line of axis a in (0,1)^2 (in (-slack, 1+slack)^2
 // when slack > 0, for the error marks)
-__device__ __noinline__ int fold_solve(const double *g, int a, double c, double *ru, double *rv, double slack = 0.0)
+// sgn: bit v = (g[v] >= c), or -1 to compare here
+__device__ __noinline__ int fold_solve(const double *g, int a, double c, double *ru, double *rv, double slack = 0.0,
+                                       int sgn = -1)
 {
     int ua, va;
     axes_other(a, ua, va);
+    if (sgn < 0) {
+        sgn = 0;
+        for (int v = 0; v < 8; v++) sgn |= (g[v] >= c ? 1 : 0) << v;
+    }
+    int nlo = 0, nup = 0;
+    for (int k = 0; k < 4; k++) {
+        int b[3];
+        b[a] = 0; b[ua] = k & 1; b[va] = k >> 1;
+        nlo += (sgn >> (b[0] + 2 * b[1] + 4 * b[2])) & 1;
+        b[a] = 1;
+        nup += (sgn >> (b[0] + 2 * b[1] + 4 * b[2])) & 1;
+    }
+    if (nlo == 0 || nlo == 4 || nup == 0 || nup == 4) return 0;
     double lo[4], up[4];  // face s=0 and s=1 values at (u,v) = (0,0),(1,0),(0,1),(1,1)
     for (int k = 0; k < 4; k++) {
         int b[3];
@@ -60,9 +75,6 @@ __device__ __noinline__ int fold_solve(const double *g, int a, double c, double 
         b[a] = 1;
         up[k] = corner(g, b[0], b[1], b[2]);
     }
-    int nlo = 0, nup = 0;
-    for (int k = 0; k < 4; k++) { nlo += lo[k] >= c; nup += up[k] >= c; }
-    if (nlo == 0 || nlo == 4 || nup == 0 || nup == 4) return 0;
     // A - c = p0 + p1 u + p2 v + p3 uv ; B = q0 + q1 u + q2 v + q3 uv
     // monomial coefficients, summed left to right (the face's corner order)
     double p0 = lo[0] - c, p1 = lo[1] - lo[0], p2 = lo[2] - lo[0], p3 = lo[3] - lo[1] - lo[2] + lo[0];
@@ -126,18 +138,20 @@ __device__ __noinline__ int fold_solve(const double *g, int a, double c, double 
 // face decision in the face's (u,v) frame from h[u + 2v]: returns the number
 // of arcs (0,1,2); for two arcs sets around00 (arcs cut off corners 00 and
 // 11) and the saddle's u coordinate
-__device__ __noinline__ int face_arcs(const double *h, double c, int &around00, double &us)
+// fs: bit k = (h[k] >= c), or -1 to compare here
+__device__ __noinline__ int face_arcs(const double *h, double c, int &around00, double &us, int fs = -1)
 {
-    int nin = (h[0] >= c) + (h[1] >= c) + (h[2] >= c) + (h[3] >= c);
+    if (fs < 0) fs = (h[0] >= c ? 1 : 0) | (h[1] >= c ? 2 : 0) | (h[2] >= c ? 4 : 0) | (h[3] >= c ? 8 : 0);
+    int nin = __popc(fs);
     around00 = 0;
     us = 0.0;
     if (nin == 0 || nin == 4) return 0;
-    bool diag = ((h[0] >= c) == (h[3] >= c)) && ((h[1] >= c) == (h[2] >= c)) && ((h[0] >= c) != (h[1] >= c));
-    if (!diag) return 1;
+    // diagonal pattern: corners 0 and 3 on one side, 1 and 2 on the other
+    if (fs != 9 && fs != 6) return 1;
     double den = h[0] - h[1] - h[2] + h[3];
     double hs = (h[0] * h[3] - h[1] * h[2]) / den;
     us = (h[0] - h[2]) / den;
-    bool in00 = h[0] >= c;
+    bool in00 = fs & 1;
     bool sep = hs < c;
     around00 = (in00 == sep) ? 1 : 0;
     return 2;
@@ -192,6 +206,25 @@ __device__ void clip_piece(const TPt *pts, const unsigned char *poly, int n, Tri
     double sg = Nk >= 0 ? 1.0 : -1.0;
     unsigned char v[POLY_MAX];
     for (int i = 0; i < n; i++) v[i] = poly[i];
+    // Orientation signs, filtered in FP32: the points' local coordinates lie
+    // in [0,1], so rounding them to float moves each difference by at most
+    // 1.8e-7 and each product by 1.8e-7 times the other factor; when the
+    // FP32 value exceeds that bound (with margin) its sign is the exact sign
+    // and the FP64 predicate's.  Otherwise the FP64 predicate decides.
+    float qa[TP_MAX], qb[TP_MAX];
+    for (int i = 0; i < n; i++) {
+        qa[poly[i]] = (float)pts[poly[i]].p[ia];
+        qb[poly[i]] = (float)pts[poly[i]].p[ib];
+    }
+    auto osign = [&](int a, int b, int c) -> int {
+        float d1 = qa[b] - qa[a], d2 = qb[c] - qb[a], d3 = qb[b] - qb[a], d4 = qa[c] - qa[a];
+        float p1 = d1 * d2, p2 = d3 * d4, vv = p1 - p2;
+        float err = 4e-7f * (fabsf(d1) + fabsf(d2) + fabsf(d3) + fabsf(d4)) + 3e-7f * (fabsf(p1) + fabsf(p2)) + 1e-13f;
+        int s32 = vv > err ? 1 : (vv < -err ? -1 : 0);
+        if (s32 != 0) return sg > 0 ? s32 : -s32;
+        double o = sg * orient(pts[a].p, pts[b].p, pts[c].p, ia, ib);
+        return o > 0 ? 1 : (o < 0 ? -1 : 0);
+    };
     int m = n;
     int guard = 0;
     while (m > 3 && guard++ < POLY_MAX) {
@@ -199,15 +232,12 @@ __device__ void clip_piece(const TPt *pts, const unsigned char *poly, int n, Tri
         for (int i = 0; i < m; i++) {
             int a = v[i == 0 ? m - 1 : i - 1], b = v[i], c = v[i + 1 == m ? 0 : i + 1];
             if (fall < 0 || pts[b].key < pts[v[fall]].key) fall = i;
-            if (!(sg * orient(pts[a].p, pts[b].p, pts[c].p, ia, ib) > 0)) continue;
+            if (!(osign(a, b, c) > 0)) continue;
             bool empty = true;
             for (int jx = 0; jx < m && empty; jx++) {
                 int d = v[jx];
                 if (d == a || d == b || d == c) continue;
-                const double *pd = pts[d].p;
-                if (sg * orient(pts[a].p, pts[b].p, pd, ia, ib) >= 0 && sg * orient(pts[b].p, pts[c].p, pd, ia, ib) >= 0 &&
-                    sg * orient(pts[c].p, pts[a].p, pd, ia, ib) >= 0)
-                    empty = false;
+                if (osign(a, b, d) >= 0 && osign(b, c, d) >= 0 && osign(c, a, d) >= 0) empty = false;
             }
             if (!empty) continue;
             if (pick < 0 || pts[b].key < pts[v[pick]].key) pick = i;
@@ -241,9 +271,10 @@ __device__ int tri_cube(const TriCtx &X, int64_t ci, TriOut &o, unsigned long lo
     double g[8];
     for (int v = 0; v < 8; v++) g[v] = X.phi[X.cvid[ci * 8 + v]];
     const double c = X.c;
-    int nin = 0;
-    for (int v = 0; v < 8; v++) nin += g[v] >= c;
-    if (nin == 0 || nin == 8) return 0;
+    // inside bits, compared once: bit v = (g[v] >= c)
+    int sg = 0;
+    for (int v = 0; v < 8; v++) sg |= (g[v] >= c ? 1 : 0) << v;
+    if (sg == 0 || sg == 0xFF) return 0;
 
     TPt pts[TP_MAX];
     int np = 0;
@@ -255,9 +286,10 @@ __device__ int tri_cube(const TriCtx &X, int64_t ci, TriOut &o, unsigned long lo
             int o1 = e & 1, o2 = e >> 1;
             int b0[3], b1[3];
             b0[a] = 0; b1[a] = 1; b0[ua] = b1[ua] = o1; b0[va] = b1[va] = o2;
-            double g0 = corner(g, b0[0], b0[1], b0[2]), g1 = corner(g, b1[0], b1[1], b1[2]);
+            const int v0 = b0[0] + 2 * b0[1] + 4 * b0[2], v1 = b1[0] + 2 * b1[1] + 4 * b1[2];
             eid[4 * a + e] = -1;
-            if ((g0 >= c) == (g1 >= c)) continue;
+            if (((sg >> v0) & 1) == ((sg >> v1) & 1)) continue;
+            double g0 = g[v0], g1 = g[v1];
             int id = (int)add_pt(pts, np, 0);
             pts[id].p[a] = __ddiv_rn(__dsub_rn(c, g0), __dsub_rn(g1, g0));
             pts[id].p[ua] = o1;
@@ -280,7 +312,7 @@ __device__ int tri_cube(const TriCtx &X, int64_t ci, TriOut &o, unsigned long lo
                 rv[r] = X.froot[ci * 12 + 4 * a + 2 * r + 1];
             }
         } else {
-            nr[a] = fold_solve(g, a, c, ru, rv);
+            nr[a] = fold_solve(g, a, c, ru, rv, 0.0, sg);
         }
         for (int r = 0; r < nr[a]; r++) { rt[a][r][0] = ru[r]; rt[a][r][1] = rv[r]; }
     }
@@ -406,10 +438,13 @@ __device__ int tri_cube(const TriCtx &X, int64_t ci, TriOut &o, unsigned long lo
         axes_other(a, ua, va);
         for (int sd = 0; sd < 2; sd++) {
             double h[4];
+            int fs = 0;
             for (int k = 0; k < 4; k++) {
                 int b[3];
                 b[a] = sd; b[ua] = k & 1; b[va] = k >> 1;
-                h[k] = corner(g, b[0], b[1], b[2]);
+                const int vk = b[0] + 2 * b[1] + 4 * b[2];
+                h[k] = g[vk];
+                fs |= ((sg >> vk) & 1) << k;
             }
             // face edges in the (u,v) frame: 0 v=0, 1 u=1, 2 v=1, 3 u=0
             int ep[4];
@@ -425,7 +460,7 @@ __device__ int tri_cube(const TriCtx &X, int64_t ci, TriOut &o, unsigned long lo
             }
             int around00;
             double us;
-            int narc = face_arcs(h, c, around00, us);
+            int narc = face_arcs(h, c, around00, us, fs);
             int fid = 2 * a + sd;
             if (narc == 0) {
                 if (nfp[fid] > 0) return 1;
@@ -551,10 +586,12 @@ __global__ void __launch_bounds__(128) k_fold_table(TriCtx X, uint8_t *__restric
     if (ci >= X.ncubes) return;
     double g[8];
     for (int v = 0; v < 8; v++) g[v] = X.phi[X.cvid[ci * 8 + v]];
+    int sg = 0;
+    for (int v = 0; v < 8; v++) sg |= (g[v] >= X.c ? 1 : 0) << v;
     uint32_t cnt = 0;
-    for (int a = 0; a < 3; a++) {
+    for (int a = 0; a < 3 && sg != 0 && sg != 0xFF; a++) {
         double ru[2], rv[2];
-        int nr = fold_solve(g, a, X.c, ru, rv);
+        int nr = fold_solve(g, a, X.c, ru, rv, 0.0, sg);
         cnt |= (uint32_t)nr << (8 * a);
         for (int r = 0; r < nr; r++) {
             froot[ci * 12 + 4 * a + 2 * r] = ru[r];
