@@ -365,10 +365,44 @@ template <> __device__ __forceinline__ double t_sqrt<double>(double x) { return 
 template <> __device__ __forceinline__ float t_sqrt<float>(float x) { return sqrtf(x); }
 template <typename T> __device__ __forceinline__ T t_abs(T x) { return x < T(0) ? -x : x; }
 template <typename T> struct Eps;
+// Jacobi rotation zeroing the inner product ga of two rows with squared
+// norms al, be; false when the rows are already orthogonal to within Eps
+template <typename T> __device__ __forceinline__ bool jac_rot(T al, T be, T ga, T &cs, T &sn);
 template <> struct Eps<double> { static __device__ __forceinline__ double v() { return 1e-15; } };
 // FP32: the rounding noise of a 16-term dot product is ~1e-6 of |p||q|, so a
 // tighter rotation threshold would keep rotating noise until the sweep limit
 template <> struct Eps<float> { static __device__ __forceinline__ float v() { return 1e-6f; } };
+
+template <> __device__ __forceinline__ bool jac_rot<double>(double al, double be, double ga, double &cs, double &sn)
+{
+    if (ga == 0.0 || fabs(ga) <= Eps<double>::v() * sqrt(al * be)) return false;
+    double tau = (be - al) / (2.0 * ga);
+    double t = (tau >= 0.0 ? 1.0 : -1.0) / (fabs(tau) + sqrt(1.0 + tau * tau));
+    cs = 1.0 / sqrt(1.0 + t * t);
+    sn = cs * t;
+    return true;
+}
+// FP32: the rotation only has to reduce ga (the sweep repeats until the
+// threshold holds), so the approximate reciprocal, divide and square roots
+// of the SFU suffice
+template <> __device__ __forceinline__ bool jac_rot<float>(float al, float be, float ga, float &cs, float &sn)
+{
+    const float e = Eps<float>::v();
+    if (ga == 0.f || ga * ga <= e * e * (al * be)) return false;
+    float tau = __fdividef(be - al, 2.f * ga);
+    const float at = fabsf(tau);
+    float t;
+    if (at > 1e18f) {
+        t = 0.5f / at;   // 1 / (|tau| + sqrt(1 + tau^2)) without overflowing tau^2
+    } else {
+        const float q = 1.f + at * at;
+        t = __fdividef(1.f, at + q * rsqrtf(q));
+    }
+    t = copysignf(t, tau);
+    cs = rsqrtf(1.f + t * t);
+    sn = cs * t;
+    return true;
+}
 
 // one-sided Jacobi on the 4 rows of X (4 x N): afterwards the rows are
 // orthogonal and X_in = Q^T X_out.  Returns singular values sorted
@@ -395,11 +429,9 @@ __device__ void jacobi4(T (&X)[4][N], T (&s)[4], T (&u)[4][4])
                     be += X[q][k] * X[q][k];
                     ga += X[p][k] * X[q][k];
                 }
-                if (ga == T(0) || t_abs(ga) <= Eps<T>::v() * t_sqrt(al * be)) continue;
+                T cs, sn;
+                if (!jac_rot<T>(al, be, ga, cs, sn)) continue;
                 any = true;
-                T tau = (be - al) / (T(2) * ga);
-                T t = (tau >= T(0) ? T(1) : T(-1)) / (t_abs(tau) + t_sqrt(T(1) + tau * tau));
-                T cs = T(1) / t_sqrt(T(1) + t * t), sn = cs * t;
 #pragma unroll
                 for (int k = 0; k < N; k++) {
                     T xp = X[p][k], xq = X[q][k];
@@ -424,21 +456,55 @@ __device__ void jacobi4(T (&X)[4][N], T (&s)[4], T (&u)[4][4])
         for (int k = 0; k < N; k++) n2 += X[p][k] * X[p][k];
         sv[p] = t_sqrt(n2);
     }
-    // stable sort of 4 indices by descending value
-    for (int i = 1; i < 4; i++) {
-        int o = ord[i], k = i - 1;
-        while (k >= 0 && sv[ord[k]] < sv[o]) { ord[k + 1] = ord[k]; k--; }
-        ord[k + 1] = o;
-    }
     T Y[4][N];
-    for (int i = 0; i < 4; i++) {
-        int p = ord[i];
-        s[i] = sv[p];
-        T inv = sv[p] > T(0) ? T(1) / sv[p] : T(0);
+    if constexpr (sizeof(T) == 4) {
+        // stable sort by descending value: row p goes to position pos[p] (the
+        // number of rows before it in that order); moves with static indices
+        // only, so that X, Q stay in registers
+        int pos[4];
 #pragma unroll
-        for (int k = 0; k < 4; k++) u[i][k] = Q[p][k];
+        for (int p = 0; p < 4; p++) {
+            int r = 0;
 #pragma unroll
-        for (int k = 0; k < N; k++) Y[i][k] = X[p][k] * inv;
+            for (int q = 0; q < 4; q++) r += (sv[q] > sv[p] || (sv[q] == sv[p] && q < p)) ? 1 : 0;
+            pos[p] = r;
+        }
+        (void)ord;
+#pragma unroll
+        for (int p = 0; p < 4; p++) {
+            T inv = sv[p] > T(0) ? T(1) / sv[p] : T(0);
+#pragma unroll
+            for (int k = 0; k < N; k++) X[p][k] *= inv;
+        }
+#pragma unroll
+        for (int i = 0; i < 4; i++) {
+#pragma unroll
+            for (int p = 0; p < 4; p++) {
+                if (pos[p] != i) continue;
+                s[i] = sv[p];
+#pragma unroll
+                for (int k = 0; k < 4; k++) u[i][k] = Q[p][k];
+#pragma unroll
+                for (int k = 0; k < N; k++) Y[i][k] = X[p][k];
+            }
+        }
+
+    } else {
+        // stable insertion sort of 4 indices by descending value
+        for (int i = 1; i < 4; i++) {
+            int o = ord[i], k = i - 1;
+            while (k >= 0 && sv[ord[k]] < sv[o]) { ord[k + 1] = ord[k]; k--; }
+            ord[k + 1] = o;
+        }
+        for (int i = 0; i < 4; i++) {
+            int p = ord[i];
+            s[i] = sv[p];
+            T inv = sv[p] > T(0) ? T(1) / sv[p] : T(0);
+#pragma unroll
+            for (int k = 0; k < 4; k++) u[i][k] = Q[p][k];
+#pragma unroll
+            for (int k = 0; k < N; k++) Y[i][k] = X[p][k] * inv;
+        }
     }
 #pragma unroll
     for (int i = 0; i < 4; i++)
