@@ -93,6 +93,23 @@ class ClockSampler:
                 "reasons": sorted(reasons), "samples": len(sm)}
 
 
+def _batch_molecule(spec):
+    import synth
+    i, n, D = spec
+    xyz, r = synth.globular(n, seed=1000 + i)
+    return xyz, r, D
+
+
+def make_batch_molecules(count=64):
+    """The batch workload: 64 globular molecules, atom counts log-uniform in
+    [500, 50000], D in {0.5, 0.9} (seeded)."""
+    import multiprocessing as mp
+    import synth
+    specs = [(i, n, D) for i, (n, D) in enumerate(synth.batch_specs(count=count, seed=0))]
+    with mp.get_context("spawn").Pool(processes=max(1, min(16, os.cpu_count() or 1))) as pool:
+        return pool.map(_batch_molecule, specs, chunksize=1)
+
+
 def cpu_baseline(cfg, n_sample=300):
     """The oracle, as it stands, on a cut-out of the workload: the n_sample
     atoms nearest to the outermost atom of the first unit.  Scaled to a whole
@@ -150,11 +167,18 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--fp64-steps", type=int, default=1, help="extra FP64-form steps timed for comparison")
     ap.add_argument("--diff-steps", type=int, default=2, help="differentiation-form steps (10k atoms) to time")
+    ap.add_argument("--batch-steps", type=int, default=1, help="batch-form steps (64 molecules) to time")
     args = ap.parse_args()
     ws, rank, local = dist_env()
     if args.impl == "reference":
         run_reference(args, ws, rank)
         return
+
+    # batch-form molecules: generated on the host cores by a spawn pool before
+    # any GPU call (the generator is a per-step Python random walk)
+    batch_mols = None
+    if args.batch_steps > 0 and rank == 0 and ws == 1:
+        batch_mols = make_batch_molecules()
 
     import torch
 
@@ -278,6 +302,31 @@ def main():
                 "ms_forward": float(np.mean(tf)), "ms_backward": float(np.mean(tb)),
                 "n_vertices": int(dm.vertices.shape[0]), "volume_A3": float(vol), "area_A2": float(area)}
 
+    # batch form: 64 molecules, one call, worker threads with a stream each,
+    # against the same molecules meshed one call at a time
+    batch = None
+    if batch_mols is not None:
+        kwb = dict(precision_mode=mode, device_output=True)
+        res = {}
+        for label, nw in (("sequential", 1), ("concurrent", 8)):
+            ts = []
+            for it in range(args.batch_steps + 1):
+                flush.zero_()
+                barrier()
+                t0 = time.perf_counter()
+                bm = gs.mesh_gaussian_surface_batch(batch_mols, cfg["c"], cfg["precision"], cfg["max_depth"],
+                                                    n_workers=nw, **kwb)
+                t1 = time.perf_counter()
+                if it > 0:
+                    ts.append((t1 - t0) * 1e3)
+            res[label] = float(np.mean(ts))
+        natoms = sum(len(m[1]) for m in batch_mols)
+        batch = {"workload": "64 globular molecules, %d atoms in all, n log-uniform in [500, 50000], D in {0.5, 0.9}, "
+                             "host inputs, device outputs" % natoms,
+                 "ms_per_batch_concurrent": res["concurrent"], "ms_per_batch_sequential": res["sequential"],
+                 "molecules_per_s": 64 * 1e3 / res["concurrent"], "n_workers": 8,
+                 "n_triangles": int(sum(m.n_triangles for m in bm))}
+
     st = stats[-1]
     pairs = st["pair_terms"]
     acc_ms = float(np.mean([s["ms_accum"] for s in stats]))
@@ -317,6 +366,7 @@ def main():
         "gpu_launches": int(st["n_kernel_launches"]),
         "fp64_form": fp64,
         "diff_form": diff,
+        "batch_form": batch,
     }
     if rank == 0 and ws == 1 and not args.no_cpu_baseline:
         line["cpu_baseline"] = cpu_baseline(cfg)

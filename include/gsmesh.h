@@ -133,6 +133,24 @@ gs_options gs_default_options(void);
 int mesh_gaussian_surface(const double *atoms, const double *radii, int64_t n_atoms, double D, double c,
                           double precision, int max_depth, const gs_options *opt, gs_mesh *out);
 
+/*
+ * mesh_gaussian_surface_batch -- mesh n_mols independent molecules (the
+ * method applies to each molecule on its own; the paper meshes one at a
+ * time).  Molecule m is atoms[offsets[m] .. offsets[m+1]) with decay rate
+ * D[m]; c, precision, max_depth and opt are shared (opt->stats and
+ * opt->cuda_stream are ignored).  n_workers host threads, each with its own
+ * CUDA stream, take the molecules largest first, so small molecules overlap
+ * on the GPU.  out [n_mols] receives one mesh per molecule (release each with
+ * mesh_free); stats [n_mols] (nullable) one record per molecule.
+ *   offsets [n_mols + 1] host int64, offsets[0] = 0, strictly increasing;
+ *   D [n_mols] host.  Atoms and radii host or device.
+ * Errors: as mesh_gaussian_surface for any molecule (the message names it);
+ * on error every out[m] is released and zeroed.
+ */
+int mesh_gaussian_surface_batch(const double *atoms, const double *radii, const int64_t *offsets, int64_t n_mols,
+                                const double *D, double c, double precision, int max_depth, const gs_options *opt,
+                                int n_workers, gs_mesh *out, gs_stats *stats);
+
 /* release the arrays of a gs_mesh (host or device) and zero it; NULL-safe */
 void mesh_free(gs_mesh *m);
 

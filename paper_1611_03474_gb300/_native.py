@@ -101,6 +101,8 @@ def load():
     L.gs_mesh_backward.restype = i32
     L.gs_volume_area.argtypes = [p, i64, p, i64, p, p, p, ctypes.POINTER(Options)]
     L.gs_volume_area.restype = i32
+    L.mesh_gaussian_surface_batch.argtypes = [p, p, p, i64, p, d, d, i32, ctypes.POINTER(Options), i32, p, p]
+    L.mesh_gaussian_surface_batch.restype = i32
     for which, cls in ((0, Stats), (1, Options), (2, MeshC)):
         if L.gs_struct_size(which) != ctypes.sizeof(cls):
             raise GsError(-1, "ABI struct %s: library %d bytes, binding %d" % (cls.__name__, L.gs_struct_size(which),
@@ -311,3 +313,39 @@ def gs_volume_area(vertices, triangles, grad=False, stream=None):
     o.cuda_stream = _stream_ptr(stream)
     _check(L.gs_volume_area(_ptr(v), nv, _ptr(t), nt, _ptr(va), _ptr(gV), _ptr(gA), ctypes.byref(o)))
     return (va[0], va[1], gV, gA) if grad else (va[0], va[1])
+
+
+def mesh_gaussian_surface_batch(molecules, c, precision, max_depth, min_edge=0.25, precision_mode=GS_PREC_FP64,
+                                cutoff_rel=1e-8, n_workers=8, device_output=False):
+    """Mesh several molecules concurrently: molecules is a list of (atoms
+    [n,3], radii [n], D).  Returns a list of Mesh (host arrays unless
+    device_output, as in mesh_gaussian_surface)."""
+    L = load()
+    xs = [np.ascontiguousarray(m[0], dtype=np.float64).reshape(-1, 3) for m in molecules]
+    rs = [np.ascontiguousarray(m[1], dtype=np.float64).reshape(-1) for m in molecules]
+    Ds = np.ascontiguousarray([float(m[2]) for m in molecules], dtype=np.float64)
+    offsets = np.zeros(len(molecules) + 1, dtype=np.int64)
+    offsets[1:] = np.cumsum([len(r) for r in rs])
+    atoms = np.ascontiguousarray(np.concatenate(xs))
+    radii = np.ascontiguousarray(np.concatenate(rs))
+    nm = len(molecules)
+    outs = (MeshC * nm)()
+    stats = (Stats * nm)()
+    o = L.gs_default_options()
+    o.min_edge = min_edge
+    o.precision_mode = precision_mode
+    o.cutoff_rel = cutoff_rel
+    o.device_output = 1 if device_output else 0
+    _check(L.mesh_gaussian_surface_batch(_ptr(atoms), _ptr(radii), _ptr(offsets), nm, _ptr(Ds), c, precision,
+                                         max_depth, ctypes.byref(o), n_workers, ctypes.cast(outs, ctypes.c_void_p),
+                                         ctypes.cast(stats, ctypes.c_void_p)))
+    res = []
+    for m in range(nm):
+        if device_output:
+            r = Mesh(None, None, None, None, stats[m].as_dict(max_depth), outs[m].mismatches)
+            r.n_vertices, r.n_triangles, r.n_cubes = outs[m].n_vertices, outs[m].n_triangles, outs[m].n_cubes
+            L.mesh_free(ctypes.byref(outs[m]))
+            res.append(r)
+        else:
+            res.append(_mesh_from_c(outs[m], L, stats[m], max_depth))
+    return res

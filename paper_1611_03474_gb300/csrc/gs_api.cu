@@ -15,6 +15,12 @@
 
 #include "gs_host.cuh"
 
+#include <algorithm>
+#include <atomic>
+#include <string>
+#include <thread>
+#include <vector>
+
 extern "C" gs_options gs_default_options(void)
 {
     gs_options o;
@@ -693,6 +699,73 @@ extern "C" int mesh_gaussian_surface(const double *atoms, const double *radii, i
     if (!rc && e != cudaSuccess) rc = gs_fail_cuda(e, "stream", __FILE__, __LINE__);
     if (rc) mesh_free(out);
     return rc;
+}
+
+extern "C" int mesh_gaussian_surface_batch(const double *atoms, const double *radii, const int64_t *offsets,
+                                           int64_t n_mols, const double *D, double c, double precision, int max_depth,
+                                           const gs_options *opt, int n_workers, gs_mesh *out, gs_stats *stats)
+{
+    if (!out || n_mols <= 0 || !offsets || !D) return gs_fail(GS_ERR_ARG, "need n_mols >= 1, offsets, D and out");
+    for (int64_t m = 0; m < n_mols; m++) memset(&out[m], 0, sizeof(gs_mesh));
+    gs_options base = opt ? *opt : gs_default_options();
+    if (offsets[0] != 0) return gs_fail(GS_ERR_ARG, "offsets[0] must be 0");
+    for (int64_t m = 0; m < n_mols; m++) {
+        if (offsets[m + 1] <= offsets[m]) return gs_fail(GS_ERR_ARG, "molecule %lld is empty", (long long)m);
+        gs_options o = base;
+        int rc = check_mesh_args(atoms, radii, offsets[m + 1] - offsets[m], D[m], c, precision, max_depth, o);
+        if (rc) return rc;
+    }
+    int rc = device_setup();
+    if (rc) return rc;
+    int dev = 0;
+    GS_CHECK(cudaGetDevice(&dev));
+    // largest molecules first, taken by the workers as they free up
+    std::vector<int64_t> order((size_t)n_mols);
+    for (int64_t m = 0; m < n_mols; m++) order[(size_t)m] = m;
+    std::stable_sort(order.begin(), order.end(), [&](int64_t a, int64_t b) {
+        return offsets[a + 1] - offsets[a] > offsets[b + 1] - offsets[b];
+    });
+    std::atomic<int64_t> next{0};
+    std::mutex mu;
+    int first_rc = 0;
+    int64_t first_mol = -1;
+    std::string first_msg;
+    auto worker = [&]() {
+        if (cudaSetDevice(dev) != cudaSuccess) return;
+        cudaStream_t st = nullptr;
+        if (cudaStreamCreateWithFlags(&st, cudaStreamNonBlocking) != cudaSuccess) {
+            std::lock_guard<std::mutex> lk(mu);
+            if (!first_rc) { first_rc = GS_ERR_CUDA; first_msg = "stream creation failed"; }
+            return;
+        }
+        for (;;) {
+            int64_t t = next.fetch_add(1);
+            if (t >= n_mols) break;
+            const int64_t m = order[(size_t)t], o0 = offsets[m], n = offsets[m + 1] - o0;
+            gs_options o = base;
+            o.cuda_stream = st;
+            o.stats = stats ? &stats[m] : nullptr;
+            int r = mesh_impl(atoms + 3 * o0, radii + o0, n, D[m], c, precision, max_depth, o, &out[m], st);
+            cudaError_t e = cudaStreamSynchronize(st);
+            if (!r && e != cudaSuccess) r = gs_fail_cuda(e, "stream", __FILE__, __LINE__);
+            if (r) {
+                std::lock_guard<std::mutex> lk(mu);
+                if (!first_rc) { first_rc = r; first_mol = m; first_msg = gs_last_error(); }
+            }
+        }
+        cudaStreamDestroy(st);
+    };
+    int nw = n_workers < 1 ? 1 : n_workers;
+    if (nw > n_mols) nw = (int)n_mols;
+    std::vector<std::thread> pool;
+    for (int w = 1; w < nw; w++) pool.emplace_back(worker);
+    worker();
+    for (auto &th : pool) th.join();
+    if (first_rc) {
+        for (int64_t m = 0; m < n_mols; m++) mesh_free(&out[m]);
+        return gs_fail(first_rc, "molecule %lld: %s", (long long)first_mol, first_msg.c_str());
+    }
+    return GS_OK;
 }
 
 extern "C" int gs_mesh_backward(const double *atoms, const double *radii, int64_t n_atoms, double D, double c,

@@ -27,10 +27,11 @@ int gs_fail_cuda(cudaError_t e, const char *what, const char *file, int line)
 
 extern "C" const char *gs_last_error(void) { return g_last_error; }
 
-#include <atomic>
-static std::atomic<long long> g_launches{0};
-void gs_count_launch(void) { g_launches.fetch_add(1, std::memory_order_relaxed); }
-long long gs_launch_count(void) { return g_launches.load(std::memory_order_relaxed); }
+// per host thread: a call runs on one thread, so the difference over the
+// call counts exactly its own launches even when calls run concurrently
+static thread_local long long g_launches = 0;
+void gs_count_launch(void) { g_launches++; }
+long long gs_launch_count(void) { return g_launches; }
 
 int gs_alloc(void **p, size_t bytes, cudaStream_t st)
 {

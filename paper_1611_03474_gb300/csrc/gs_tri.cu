@@ -781,9 +781,9 @@ __global__ void __launch_bounds__(128) k_tri_marks(TriCtx X, const float *__rest
         e[v] = (double)err[vid[v]];
     }
     const double c = X.c;
-    int nin = 0;
-    for (int v = 0; v < 8; v++) nin += g[v] >= c;
-    if (nin == 0 || nin == 8) return;
+    int sg = 0;
+    for (int v = 0; v < 8; v++) sg |= (g[v] >= c ? 1 : 0) << v;
+    if (sg == 0 || sg == 0xFF) return;
     bool all = false, r_edge = false, r_face = false;
     unsigned m = 0;
     for (int a = 0; a < 3 && !all; a++) {
@@ -793,23 +793,24 @@ __global__ void __launch_bounds__(128) k_tri_marks(TriCtx X, const float *__rest
             int b0[3], b1[3];
             b0[a] = 0; b1[a] = 1; b0[ua] = b1[ua] = k & 1; b0[va] = b1[va] = k >> 1;
             int v0 = b0[0] + 2 * b0[1] + 4 * b0[2], v1 = b1[0] + 2 * b1[1] + 4 * b1[2];
-            if ((g[v0] >= c) == (g[v1] >= c)) continue;
+            if (((sg >> v0) & 1) == ((sg >> v1) & 1)) continue;
             // t = (c - g0) / (g1 - g0) moves by ((1 - t) e0 + t e1) / |g1 - g0| to first order
             double dg = fabs(g[v1] - g[v0]), t = fabs(c - g[v0]) / dg;
             if (h * ((1.0 - t) * e[v0] + t * e[v1]) > tol * dg) { m |= (1u << v0) | (1u << v1); r_edge = true; }
         }
         for (int sd = 0; sd < 2; sd++) {
             double hf[4];
-            int fv[4];
+            int fv[4], fs = 0;
             for (int k = 0; k < 4; k++) {
                 int b[3];
                 b[a] = sd; b[ua] = k & 1; b[va] = k >> 1;
                 fv[k] = b[0] + 2 * b[1] + 4 * b[2];
                 hf[k] = g[fv[k]];
+                fs |= ((sg >> fv[k]) & 1) << k;
             }
             int around00;
             double us;
-            if (face_arcs(hf, c, around00, us) == 2) {
+            if (face_arcs(hf, c, around00, us, fs) == 2) {
                 double den = hf[0] - hf[1] - hf[2] + hf[3];
                 double hs = (hf[0] * hf[3] - hf[1] * hf[2]) / den;
                 double eb = 0;
@@ -823,7 +824,7 @@ __global__ void __launch_bounds__(128) k_tri_marks(TriCtx X, const float *__rest
             }
         }
         double ru[2], rv[2];
-        int nr = fold_solve(g, a, c, ru, rv, 1e-3);
+        int nr = fold_solve(g, a, c, ru, rv, 1e-3, sg);
         if (nr > 0) {
             // A = lower face - c, B = upper - lower (bilinear in u, v); a root
             // solves A = B = 0.  Corner errors move A and B at the root by at
