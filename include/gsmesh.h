@@ -268,6 +268,17 @@ int gs_mesh_backward(const double *atoms, const double *radii, int64_t n_atoms, 
 int gs_volume_area(const double *vertices, int64_t n_vertices, const int32_t *triangles, int64_t n_triangles,
                    double *volume_area, double *grad_volume, double *grad_area, const gs_options *opt);
 
+/*
+ * gs_mesh_intersections -- number of pairs of triangles that share no vertex
+ * and overlap by more than tol (A) along every separating axis of the pair
+ * (the paper's count of intersecting triangle pairs, section 3.2, which it
+ * reports as zero for its meshes).  vertices [n_vertices][3], triangles
+ * [n_triangles][3] int32, host or device.  GS_ERR_ARG if a triangle index
+ * is outside [0, n_vertices) or tol < 0.
+ */
+int gs_mesh_intersections(const double *vertices, int64_t n_vertices, const int32_t *triangles,
+                          int64_t n_triangles, double tol, int64_t *n_pairs, const gs_options *opt);
+
 #ifdef __cplusplus
 }
 #endif

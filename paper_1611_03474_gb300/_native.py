@@ -103,6 +103,8 @@ def load():
     L.gs_volume_area.restype = i32
     L.mesh_gaussian_surface_batch.argtypes = [p, p, p, i64, p, d, d, i32, ctypes.POINTER(Options), i32, p, p]
     L.mesh_gaussian_surface_batch.restype = i32
+    L.gs_mesh_intersections.argtypes = [p, i64, p, i64, d, p, ctypes.POINTER(Options)]
+    L.gs_mesh_intersections.restype = i32
     for which, cls in ((0, Stats), (1, Options), (2, MeshC)):
         if L.gs_struct_size(which) != ctypes.sizeof(cls):
             raise GsError(-1, "ABI struct %s: library %d bytes, binding %d" % (cls.__name__, L.gs_struct_size(which),
@@ -349,3 +351,15 @@ def mesh_gaussian_surface_batch(molecules, c, precision, max_depth, min_edge=0.2
         else:
             res.append(_mesh_from_c(outs[m], L, stats[m], max_depth))
     return res
+
+
+def gs_mesh_intersections(vertices, triangles, tol=1e-9, stream=None):
+    """Number of vertex-disjoint triangle pairs that overlap by more than tol."""
+    L = load()
+    v = _host64(vertices, (-1, 3))
+    t = triangles if hasattr(triangles, "data_ptr") else np.ascontiguousarray(triangles, dtype=np.int32)
+    n = ctypes.c_int64(0)
+    o = L.gs_default_options()
+    o.cuda_stream = _stream_ptr(stream)
+    _check(L.gs_mesh_intersections(_ptr(v), v.shape[0], _ptr(t), t.shape[0], tol, ctypes.byref(n), ctypes.byref(o)))
+    return int(n.value)

@@ -821,6 +821,49 @@ static int check_tri_ids(const int32_t *d_t, int64_t nt, int64_t nv, unsigned *d
     return h ? gs_fail(GS_ERR_ARG, "a triangle index is outside [0, n_vertices)") : GS_OK;
 }
 
+extern "C" int gs_mesh_intersections(const double *vertices, int64_t n_vertices, const int32_t *triangles,
+                                     int64_t n_triangles, double tol, int64_t *n_pairs, const gs_options *opt)
+{
+    gs_options o = opt ? *opt : gs_default_options();
+    if (!n_pairs || n_vertices < 0 || n_triangles < 0 || (n_vertices > 0 && !vertices) ||
+        (n_triangles > 0 && !triangles) || n_vertices > ((int64_t)1 << 31) || !(tol >= 0.0))
+        return gs_fail(GS_ERR_ARG, "bad arguments");
+    *n_pairs = 0;
+    int rc = device_setup();
+    if (rc) return rc;
+    cudaStream_t st = (cudaStream_t)o.cuda_stream;
+    bool own = false;
+    if (!st) {
+        GS_CHECK(cudaStreamCreateWithFlags(&st, cudaStreamNonBlocking));
+        own = true;
+    }
+    {
+        DevBufs B(st);
+        const double *v = vertices;
+        const int32_t *t = triangles;
+        unsigned *d_status = nullptr;
+        rc = B.get(&d_status, 1);
+        if (!rc && n_vertices && !on_device(vertices)) {
+            double *tv = nullptr;
+            rc = B.get(&tv, 3 * (size_t)n_vertices);
+            if (!rc) rc = put_in(tv, vertices, sizeof(double) * 3 * (size_t)n_vertices, st);
+            v = tv;
+        }
+        if (!rc && n_triangles && !on_device(triangles)) {
+            int32_t *tt = nullptr;
+            rc = B.get(&tt, 3 * (size_t)n_triangles);
+            if (!rc) rc = put_in(tt, triangles, sizeof(int32_t) * 3 * (size_t)n_triangles, st);
+            t = tt;
+        }
+        if (!rc && n_triangles) rc = check_tri_ids(t, n_triangles, n_vertices, d_status, st);
+        if (!rc) rc = gs_count_intersections(v, n_vertices, t, n_triangles, tol, n_pairs, st);
+        cudaError_t e = cudaStreamSynchronize(st);
+        if (!rc && e != cudaSuccess) rc = gs_fail_cuda(e, "stream", __FILE__, __LINE__);
+    }
+    if (own) cudaStreamDestroy(st);
+    return rc;
+}
+
 extern "C" int gs_volume_area(const double *vertices, int64_t n_vertices, const int32_t *triangles,
                               int64_t n_triangles, double *volume_area, double *grad_volume, double *grad_area,
                               const gs_options *opt)

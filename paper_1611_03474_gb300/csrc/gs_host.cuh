@@ -96,6 +96,9 @@ int gs_volume_area_dev(const double *d_v, const int32_t *d_tri, int64_t nt, doub
 int gs_field_adjoint(const GsProblem &P, const int32_t *d_perm, const uint64_t *d_vkeys, const double *d_lambda,
                      int64_t nv, double *d_gx, double *d_gr, double *d_gD, cudaStream_t st);
 __global__ void k_hash_index(GsHash H, const uint64_t *keys, int64_t n, unsigned *status);
+// pairs of triangles sharing no vertex that overlap by more than tol (A)
+int gs_count_intersections(const double *d_v, int64_t nv, const int32_t *d_t, int64_t nt, double tol,
+                           int64_t *n_pairs, cudaStream_t st);
 // d_why (nullable) counts the cubes marked through an edge point, a face
 // saddle and a fold root
 int gs_tri_marks(const TriCtx &X, const float *d_err, double tol_A, int64_t *d_mark, unsigned long long *d_why,

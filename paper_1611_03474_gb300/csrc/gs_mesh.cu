@@ -11,6 +11,9 @@
 //     and remapping of the triangles' keys to vertex ids.
 #include "gs_host.cuh"
 
+#include <cmath>
+#include <vector>
+
 __global__ void k_hash_clear(uint64_t *keys, uint64_t *vals, uint64_t cap, uint64_t vinit)
 {
     for (uint64_t i = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; i < cap; i += (uint64_t)gridDim.x * blockDim.x) {
@@ -342,5 +345,200 @@ int gs_weld(const uint64_t *d_pk, const double *d_pxyz, int64_t npt, const uint6
     }
     GS_CHECK(cudaGetLastError());
     *nv = total;
+    return GS_OK;
+}
+
+// ---------------------------------------------------------------- mesh check
+// Pairs of triangles that share no vertex and intersect (the paper reports
+// none for its meshes).  Triangles are binned by their centroid on a grid
+// whose cell is at least the largest triangle extent, so any intersecting
+// pair lies in the same or in neighbouring cells; each pair is tested once
+// (by its lower index) with the separating-axis test on the 11 candidate
+// axes (2 normals, 9 edge cross products), FP64, counting only pairs with no
+// separating gap larger than tol.
+__global__ void k_tri_bins(const double *v, const int32_t *t, int64_t nt, const double *lo, double inv, const int *dims,
+                           int32_t *cell)
+{
+    int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= nt) return;
+    int cc[3];
+    for (int a = 0; a < 3; a++) {
+        double m = (v[3 * (int64_t)t[3 * i] + a] + v[3 * (int64_t)t[3 * i + 1] + a] + v[3 * (int64_t)t[3 * i + 2] + a]) / 3.0;
+        int k = (int)floor((m - lo[a]) * inv);
+        cc[a] = k < 0 ? 0 : (k >= dims[a] ? dims[a] - 1 : k);
+    }
+    cell[i] = cc[0] + dims[0] * (cc[1] + dims[1] * cc[2]);
+}
+
+__device__ __forceinline__ void tri_project(const double (*p)[3], const double *ax, double &mn, double &mx)
+{
+    double d0 = p[0][0] * ax[0] + p[0][1] * ax[1] + p[0][2] * ax[2];
+    double d1 = p[1][0] * ax[0] + p[1][1] * ax[1] + p[1][2] * ax[2];
+    double d2 = p[2][0] * ax[0] + p[2][1] * ax[1] + p[2][2] * ax[2];
+    mn = fmin(d0, fmin(d1, d2));
+    mx = fmax(d0, fmax(d1, d2));
+}
+
+// true when the triangles overlap by more than tol along every candidate
+// separating axis (a separating gap, or an overlap of at most tol, on any
+// axis means no intersection)
+__device__ bool tris_intersect(const double (*P)[3], const double (*Q)[3], double tol)
+{
+    double eP[3][3], eQ[3][3];
+    for (int k = 0; k < 3; k++)
+        for (int a = 0; a < 3; a++) {
+            eP[k][a] = P[(k + 1) % 3][a] - P[k][a];
+            eQ[k][a] = Q[(k + 1) % 3][a] - Q[k][a];
+        }
+    auto cross = [](const double *x, const double *y, double *o) {
+        o[0] = x[1] * y[2] - x[2] * y[1];
+        o[1] = x[2] * y[0] - x[0] * y[2];
+        o[2] = x[0] * y[1] - x[1] * y[0];
+    };
+    auto separated = [&](const double *axis) {
+        double n2 = axis[0] * axis[0] + axis[1] * axis[1] + axis[2] * axis[2];
+        if (n2 <= 1e-30) return false;   // degenerate axis
+        double inv = 1.0 / sqrt(n2), ax[3] = {axis[0] * inv, axis[1] * inv, axis[2] * inv};
+        double a0, a1, b0, b1;
+        tri_project(P, ax, a0, a1);
+        tri_project(Q, ax, b0, b1);
+        return a1 <= b0 + tol || b1 <= a0 + tol;
+    };
+    double nP[3], nQ[3];
+    cross(eP[0], eP[1], nP);
+    cross(eQ[0], eQ[1], nQ);
+    double lP = sqrt(nP[0] * nP[0] + nP[1] * nP[1] + nP[2] * nP[2]);
+    bool coplanar = lP > 0.0;
+    for (int k = 0; k < 3 && coplanar; k++) {
+        double d = (nP[0] * (Q[k][0] - P[0][0]) + nP[1] * (Q[k][1] - P[0][1]) + nP[2] * (Q[k][2] - P[0][2])) / lP;
+        coplanar = fabs(d) <= tol;
+    }
+    if (coplanar) {
+        // in the common plane: the in-plane normals of the six edges
+        for (int s = 0; s < 2; s++)
+            for (int k = 0; k < 3; k++) {
+                double ax[3];
+                cross(s ? eQ[k] : eP[k], nP, ax);
+                if (separated(ax)) return false;
+            }
+        return true;
+    }
+    if (separated(nP) || separated(nQ)) return false;
+    for (int i = 0; i < 3; i++)
+        for (int j = 0; j < 3; j++) {
+            double ax[3];
+            cross(eP[i], eQ[j], ax);
+            if (separated(ax)) return false;
+        }
+    return true;
+}
+
+__global__ void k_tri_pairs(const double *v, const int32_t *t, int64_t nt, const int32_t *order,
+                            const int32_t *cell_start, const int32_t *cell, const int *dims, double tol,
+                            unsigned long long *count)
+{
+    int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    unsigned long long found = 0;
+    if (i < nt) {
+        int32_t ti[3] = {t[3 * i], t[3 * i + 1], t[3 * i + 2]};
+        double P[3][3];
+        for (int k = 0; k < 3; k++)
+            for (int a = 0; a < 3; a++) P[k][a] = v[3 * (int64_t)ti[k] + a];
+        int c = cell[i];
+        int cx = c % dims[0], cy = (c / dims[0]) % dims[1], cz = c / (dims[0] * dims[1]);
+        for (int dz = -1; dz <= 1; dz++)
+            for (int dy = -1; dy <= 1; dy++)
+                for (int dx = -1; dx <= 1; dx++) {
+                    int x = cx + dx, y = cy + dy, z = cz + dz;
+                    if (x < 0 || y < 0 || z < 0 || x >= dims[0] || y >= dims[1] || z >= dims[2]) continue;
+                    int nc = x + dims[0] * (y + dims[1] * z);
+                    for (int s = cell_start[nc]; s < cell_start[nc + 1]; s++) {
+                        int64_t j = order[s];
+                        if (j <= i) continue;
+                        int32_t tj[3] = {t[3 * j], t[3 * j + 1], t[3 * j + 2]};
+                        bool shared = false;
+                        for (int a = 0; a < 3; a++)
+                            for (int b = 0; b < 3; b++) shared |= ti[a] == tj[b];
+                        if (shared) continue;
+                        double Q[3][3];
+                        for (int k = 0; k < 3; k++)
+                            for (int a = 0; a < 3; a++) Q[k][a] = v[3 * (int64_t)tj[k] + a];
+                        if (tris_intersect(P, Q, tol)) found++;
+                    }
+                }
+    }
+    for (int o = 16; o > 0; o >>= 1) found += __shfl_xor_sync(0xffffffffu, found, o);
+    if ((threadIdx.x & 31) == 0 && found) atomicAdd(count, found);
+}
+
+int gs_count_intersections(const double *d_v, int64_t nv, const int32_t *d_t, int64_t nt, double tol,
+                           int64_t *n_pairs, cudaStream_t st)
+{
+    *n_pairs = 0;
+    if (nt <= 1) return GS_OK;
+    // bounding box and largest triangle extent on the host (one pass over a
+    // copy would do; the vertices are read back once here for simplicity)
+    std::vector<double> hv((size_t)nv * 3);
+    std::vector<int32_t> ht((size_t)nt * 3);
+    GS_CHECK(cudaMemcpyAsync(hv.data(), d_v, sizeof(double) * hv.size(), cudaMemcpyDeviceToHost, st));
+    GS_CHECK(cudaMemcpyAsync(ht.data(), d_t, sizeof(int32_t) * ht.size(), cudaMemcpyDeviceToHost, st));
+    GS_CHECK(cudaStreamSynchronize(st));
+    double lo[3] = {1e300, 1e300, 1e300}, hi[3] = {-1e300, -1e300, -1e300}, ext = 0.0;
+    for (int64_t i = 0; i < nv; i++)
+        for (int a = 0; a < 3; a++) { lo[a] = fmin(lo[a], hv[3 * i + a]); hi[a] = fmax(hi[a], hv[3 * i + a]); }
+    for (int64_t i = 0; i < nt; i++)
+        for (int a = 0; a < 3; a++) {
+            double x0 = hv[3 * (int64_t)ht[3 * i] + a], x1 = hv[3 * (int64_t)ht[3 * i + 1] + a],
+                   x2 = hv[3 * (int64_t)ht[3 * i + 2] + a];
+            ext = fmax(ext, fmax(x0, fmax(x1, x2)) - fmin(x0, fmin(x1, x2)));
+        }
+    // two intersecting triangles of extent <= ext have centroids within 4/3 ext
+    // per axis, so a cell of that size puts them in the same or adjacent cells;
+    // larger cells when that would exceed ~4 cells per triangle
+    double cellsz = fmax(4.0 / 3.0 * ext * (1.0 + 1e-9), 1e-6);
+    double vol = 1.0;
+    for (int a = 0; a < 3; a++) vol *= fmax(hi[a] - lo[a], cellsz);
+    cellsz = fmax(cellsz, cbrt(vol / (4.0 * (double)nt)));
+    int dims[3];
+    for (int a = 0; a < 3; a++) dims[a] = (int)((int64_t)floor((hi[a] - lo[a]) / cellsz) + 1);
+    const int64_t ncell = (int64_t)dims[0] * dims[1] * dims[2];
+    double *d_lo = nullptr;
+    int *d_dims = nullptr;
+    int32_t *cell = nullptr, *order = nullptr, *start = nullptr;
+    unsigned long long *cnt = nullptr;
+    int rc = gs_alloc((void **)&d_lo, 3 * sizeof(double), st);
+    if (!rc) rc = gs_alloc((void **)&d_dims, 3 * sizeof(int), st);
+    if (!rc) rc = gs_alloc((void **)&cell, sizeof(int32_t) * (size_t)nt, st);
+    if (!rc) rc = gs_alloc((void **)&cnt, sizeof(unsigned long long), st);
+    if (rc) { gs_free(d_lo, st); gs_free(d_dims, st); gs_free(cell, st); gs_free(cnt, st); return rc; }
+    GS_CHECK(cudaMemcpyAsync(d_lo, lo, 3 * sizeof(double), cudaMemcpyHostToDevice, st));
+    GS_CHECK(cudaMemcpyAsync(d_dims, dims, 3 * sizeof(int), cudaMemcpyHostToDevice, st));
+    GS_LAUNCH(k_tri_bins, (unsigned)((nt + 255) / 256), 256, 0, st)(d_v, d_t, nt, d_lo, 1.0 / cellsz, d_dims, cell);
+    // counting sort of the triangles by cell on the host (cell array read back)
+    std::vector<int32_t> hc((size_t)nt), hs((size_t)ncell + 1, 0), ho((size_t)nt);
+    GS_CHECK(cudaMemcpyAsync(hc.data(), cell, sizeof(int32_t) * (size_t)nt, cudaMemcpyDeviceToHost, st));
+    GS_CHECK(cudaStreamSynchronize(st));
+    for (int64_t i = 0; i < nt; i++) hs[(size_t)hc[i] + 1]++;
+    for (int64_t k = 0; k < ncell; k++) hs[(size_t)k + 1] += hs[(size_t)k];
+    {
+        std::vector<int32_t> fill(hs.begin(), hs.end() - 1);
+        for (int64_t i = 0; i < nt; i++) ho[(size_t)fill[(size_t)hc[i]]++] = (int32_t)i;
+    }
+    rc = gs_alloc((void **)&order, sizeof(int32_t) * (size_t)nt, st);
+    if (!rc) rc = gs_alloc((void **)&start, sizeof(int32_t) * (size_t)(ncell + 1), st);
+    if (!rc) {
+        GS_CHECK(cudaMemcpyAsync(order, ho.data(), sizeof(int32_t) * (size_t)nt, cudaMemcpyHostToDevice, st));
+        GS_CHECK(cudaMemcpyAsync(start, hs.data(), sizeof(int32_t) * (size_t)(ncell + 1), cudaMemcpyHostToDevice, st));
+        GS_CHECK(cudaMemsetAsync(cnt, 0, sizeof(unsigned long long), st));
+        GS_LAUNCH(k_tri_pairs, (unsigned)((nt + 127) / 128), 128, 0, st)(d_v, d_t, nt, order, start, cell, d_dims, tol,
+                                                                         cnt);
+        unsigned long long h = 0;
+        GS_CHECK(cudaMemcpyAsync(&h, cnt, sizeof(h), cudaMemcpyDeviceToHost, st));
+        GS_CHECK(cudaStreamSynchronize(st));
+        *n_pairs = (int64_t)h;
+    }
+    gs_free(d_lo, st); gs_free(d_dims, st); gs_free(cell, st); gs_free(cnt, st); gs_free(order, st); gs_free(start, st);
+    if (rc) return rc;
+    GS_CHECK(cudaGetLastError());
     return GS_OK;
 }

@@ -211,3 +211,54 @@ def test_autograd_function(gs):
     assert np.abs(x.grad.numpy() - ga).max() <= 1e-10 * scale
     assert np.abs(r.grad.numpy() - gr).max() <= 1e-10 * scale
     assert abs(D.grad.item() - gD) <= 1e-10 * max(1.0, abs(gD))
+
+
+def _sat_pairs(v, t, tol=1e-9):
+    """Brute-force count of vertex-disjoint intersecting triangle pairs
+    (separating-axis test on the 11 axes, coplanar pairs in their plane)."""
+    P = v[t]
+    n = len(t)
+    count = 0
+    for i in range(n):
+        for j in range(i + 1, n):
+            if set(t[i]) & set(t[j]):
+                continue
+            A, B = P[i], P[j]
+            if np.any(A.max(0) < B.min(0) - tol) or np.any(B.max(0) < A.min(0) - tol):
+                continue
+            eA, eB = np.roll(A, -1, 0) - A, np.roll(B, -1, 0) - B
+            nA = np.cross(eA[0], eA[1])
+            axes = [nA, np.cross(eB[0], eB[1])] + [np.cross(a, b) for a in eA for b in eB]
+            lA = np.linalg.norm(nA)
+            if lA > 0 and np.all(np.abs((B - A[0]) @ nA) / lA <= tol):
+                axes = [np.cross(e, nA) for e in list(eA) + list(eB)]
+            sep = False
+            for ax in axes:
+                l = np.linalg.norm(ax)
+                if l <= 1e-15:
+                    continue
+                ax = ax / l
+                a, b = A @ ax, B @ ax
+                if a.max() <= b.min() + tol or b.max() <= a.min() + tol:
+                    sep = True
+                    break
+            if not sep:
+                count += 1
+    return count
+
+
+@pytest.mark.gpu
+def test_gpu_intersections(gs):
+    """The chain mesh has no intersecting triangle pairs; two single-atom
+    meshes pushed into each other have as many as a brute-force check finds."""
+    cfg = synth.config("chain100")
+    m = gs.mesh_gaussian_surface(cfg["xyz"], cfg["r"], cfg["D"], ARGS["c"], ARGS["precision"], ARGS["max_depth"],
+                                 min_edge=1.0)
+    assert gs.gs_mesh_intersections(m.vertices, m.triangles) == 0
+    a = gs.mesh_gaussian_surface(np.zeros((1, 3)), np.array([1.3]), 0.5, 1.0, 1e-3, 2, min_edge=0.5)
+    b = gs.mesh_gaussian_surface(np.array([[1.7, 0.3, 0.1]]), np.array([1.2]), 0.5, 1.0, 1e-3, 2, min_edge=0.5)
+    v = np.vstack([a.vertices, b.vertices])
+    t = np.vstack([a.triangles, b.triangles + len(a.vertices)]).astype(np.int32)
+    n_gpu = gs.gs_mesh_intersections(v, t)
+    assert n_gpu > 0
+    assert n_gpu == _sat_pairs(v, t)
