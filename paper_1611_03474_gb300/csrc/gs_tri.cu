@@ -784,7 +784,7 @@ __global__ void __launch_bounds__(128) k_tri_marks(TriCtx X, const float *__rest
     int sg = 0;
     for (int v = 0; v < 8; v++) sg |= (g[v] >= c ? 1 : 0) << v;
     if (sg == 0 || sg == 0xFF) return;
-    bool all = false, r_edge = false, r_face = false;
+    bool all = false, r_edge = false, r_face = false, r_fold = false;
     unsigned m = 0;
     for (int a = 0; a < 3 && !all; a++) {
         int ua, va;
@@ -796,7 +796,15 @@ __global__ void __launch_bounds__(128) k_tri_marks(TriCtx X, const float *__rest
             if (((sg >> v0) & 1) == ((sg >> v1) & 1)) continue;
             // t = (c - g0) / (g1 - g0) moves by ((1 - t) e0 + t e1) / |g1 - g0| to first order
             double dg = fabs(g[v1] - g[v0]), t = fabs(c - g[v0]) / dg;
-            if (h * ((1.0 - t) * e[v0] + t * e[v1]) > tol * dg) { m |= (1u << v0) | (1u << v1); r_edge = true; }
+            // an FP64 corner has no error: re-evaluate the larger contributor,
+            // and the other one too if it alone still exceeds the bound
+            const double c0 = h * (1.0 - t) * e[v0], c1 = h * t * e[v1], lim = tol * dg;
+            if (c0 + c1 > lim) {
+                const int big = c0 >= c1 ? v0 : v1, small = c0 >= c1 ? v1 : v0;
+                m |= 1u << big;
+                if (fmin(c0, c1) > lim) m |= 1u << small;
+                r_edge = true;
+            }
         }
         for (int sd = 0; sd < 2; sd++) {
             double hf[4];
@@ -831,14 +839,17 @@ __global__ void __launch_bounds__(128) k_tri_marks(TriCtx X, const float *__rest
             // most sum_k b_k e_k (bilinear weights b_k summing to 1), and the
             // root by J^-1 of that (J the Jacobian of (A, B) in (u, v)).
             double lo4[4], up4[4], elo[4], eup[4];
+            int ilo4[4], iup4[4];
             for (int k = 0; k < 4; k++) {
                 int b[3];
                 b[a] = 0; b[ua] = k & 1; b[va] = k >> 1;
-                lo4[k] = g[b[0] + 2 * b[1] + 4 * b[2]];
-                elo[k] = e[b[0] + 2 * b[1] + 4 * b[2]];
+                ilo4[k] = b[0] + 2 * b[1] + 4 * b[2];
+                lo4[k] = g[ilo4[k]];
+                elo[k] = e[ilo4[k]];
                 b[a] = 1;
-                up4[k] = g[b[0] + 2 * b[1] + 4 * b[2]];
-                eup[k] = e[b[0] + 2 * b[1] + 4 * b[2]];
+                iup4[k] = b[0] + 2 * b[1] + 4 * b[2];
+                up4[k] = g[iup4[k]];
+                eup[k] = e[iup4[k]];
             }
             double p1 = lo4[1] - lo4[0], p2 = lo4[2] - lo4[0], p3 = lo4[3] - lo4[1] - lo4[2] + lo4[0];
             double d0 = up4[0] - lo4[0], d1 = up4[1] - lo4[1], d2 = up4[2] - lo4[2], d3 = up4[3] - lo4[3];
@@ -846,18 +857,40 @@ __global__ void __launch_bounds__(128) k_tri_marks(TriCtx X, const float *__rest
             for (int r = 0; r < nr && !all; r++) {
                 double u = ru[r], v = rv[r];
                 double w[4] = {(1 - u) * (1 - v), u * (1 - v), (1 - u) * v, u * v};
-                double dA = 0, dB = 0;
-                for (int k = 0; k < 4; k++) {
-                    dA += fabs(w[k]) * elo[k];
-                    dB += fabs(w[k]) * (elo[k] + eup[k]);
-                }
                 double J11 = p1 + p3 * v, J12 = p2 + p3 * u, J21 = q1 + q3 * v, J22 = q2 + q3 * u;
                 double det = fabs(J11 * J22 - J12 * J21);
-                double du = det > 0 ? (fabs(J22) * dA + fabs(J12) * dB) / det : 1e30;
-                double dv = det > 0 ? (fabs(J21) * dA + fabs(J11) * dB) / det : 1e30;
-                // the position, and whether the root is inside the face square
-                if (h * (du + dv) > tol) all = true;
-                if (fmin(fabs(u), fabs(1.0 - u)) <= 4.0 * du || fmin(fabs(v), fabs(1.0 - v)) <= 4.0 * dv) all = true;
+                if (!(det > 0)) { all = true; break; }
+                // a lower corner moves A by w and B by -w, an upper corner B by
+                // w: its share of the root's first-order error (du + dv)
+                double share[8], tot = 0.0, bu = 0.0, bv = 0.0;
+                for (int q = 0; q < 4; q++) {
+                    double slo = w[q] * elo[q], sup = w[q] * eup[q];
+                    double dul = (fabs(J22) + fabs(J12)) * slo / det, dvl = (fabs(J21) + fabs(J11)) * slo / det;
+                    double duu = fabs(J12) * sup / det, dvu = fabs(J11) * sup / det;
+                    share[ilo4[q]] = dul + dvl;
+                    share[iup4[q]] = duu + dvu;
+                    bu += dul + duu;
+                    bv += dvl + dvu;
+                }
+                for (int q = 0; q < 8; q++) tot += share[q];
+                // inside the face square (a root near its boundary may cross it)
+                const bool edge_risk = fmin(fabs(u), fabs(1.0 - u)) <= 4.0 * bu ||
+                                       fmin(fabs(v), fabs(1.0 - v)) <= 4.0 * bv;
+                if (edge_risk) { all = true; break; }
+                if (h * tot > tol) {
+                    // re-evaluate the largest contributors until the rest is within tol
+                    unsigned done = 0;
+                    double rest = tot;
+                    for (int it = 0; it < 8 && h * rest > tol; it++) {
+                        int best = -1;
+                        for (int q = 0; q < 8; q++)
+                            if (!((done >> q) & 1) && (best < 0 || share[q] > share[best])) best = q;
+                        done |= 1u << best;
+                        rest -= share[best];
+                    }
+                    m |= done;
+                    r_fold = true;
+                }
             }
         }
     }
@@ -868,7 +901,7 @@ __global__ void __launch_bounds__(128) k_tri_marks(TriCtx X, const float *__rest
         // cubes marked through an edge point, a face saddle, a fold root
         if (r_edge) atomicAdd(&why[0], 1ull);
         if (r_face) atomicAdd(&why[1], 1ull);
-        if (all) atomicAdd(&why[2], 1ull);
+        if (all || r_fold) atomicAdd(&why[2], 1ull);
     }
 }
 
