@@ -772,18 +772,24 @@ __global__ void __launch_bounds__(128) k_tri_marks(TriCtx X, const float *__rest
     if (ci >= X.ncubes) return;
     uint64_t ck = X.cubes[ci];
     int lvl = (int)gk_level(ck);
-    double h = ldexp(X.min_edge, X.max_depth - lvl);
-    double g[8], e[8];
+    const float h = (float)ldexp(X.min_edge, X.max_depth - lvl);
+    double g[8];
+    float gc[8], e[8];
     int vid[8];
+    const double c = X.c;
+    int sg = 0;
     for (int v = 0; v < 8; v++) {
         vid[v] = X.cvid[ci * 8 + v];
         g[v] = X.phi[vid[v]];
-        e[v] = (double)err[vid[v]];
+        e[v] = err[vid[v]];
+        gc[v] = (float)(g[v] - c);
+        sg |= (g[v] >= c ? 1 : 0) << v;
     }
-    const double c = X.c;
-    int sg = 0;
-    for (int v = 0; v < 8; v++) sg |= (g[v] >= c ? 1 : 0) << v;
     if (sg == 0 || sg == 0xFF) return;
+    // The bounds below are first-order estimates evaluated in FP32 from the
+    // corner values minus c; they are inflated by 1% (and tol lowered by
+    // 0.1%) so that their own rounding only ever marks more corners.
+    const float tolf = (float)tol * 0.999f, infl = 1.01f;
     bool all = false, r_edge = false, r_face = false, r_fold = false;
     unsigned m = 0;
     for (int a = 0; a < 3 && !all; a++) {
@@ -794,103 +800,122 @@ __global__ void __launch_bounds__(128) k_tri_marks(TriCtx X, const float *__rest
             b0[a] = 0; b1[a] = 1; b0[ua] = b1[ua] = k & 1; b0[va] = b1[va] = k >> 1;
             int v0 = b0[0] + 2 * b0[1] + 4 * b0[2], v1 = b1[0] + 2 * b1[1] + 4 * b1[2];
             if (((sg >> v0) & 1) == ((sg >> v1) & 1)) continue;
-            // t = (c - g0) / (g1 - g0) moves by ((1 - t) e0 + t e1) / |g1 - g0| to first order
-            double dg = fabs(g[v1] - g[v0]), t = fabs(c - g[v0]) / dg;
-            // an FP64 corner has no error: re-evaluate the larger contributor,
-            // and the other one too if it alone still exceeds the bound
-            const double c0 = h * (1.0 - t) * e[v0], c1 = h * t * e[v1], lim = tol * dg;
+            // t = (c - g0) / (g1 - g0) moves by ((1 - t) e0 + t e1) / |g1 - g0|
+            // to first order; an FP64 corner has no error: re-evaluate the
+            // larger contributor, and the other one if it alone exceeds the bound
+            float dg = fabsf(gc[v1] - gc[v0]), t = fminf(fabsf(gc[v0]) / dg, 1.f);
+            const float c0 = infl * h * (1.f - t) * e[v0], c1 = infl * h * t * e[v1], lim = tolf * dg;
             if (c0 + c1 > lim) {
                 const int big = c0 >= c1 ? v0 : v1, small = c0 >= c1 ? v1 : v0;
                 m |= 1u << big;
-                if (fmin(c0, c1) > lim) m |= 1u << small;
+                if (fminf(c0, c1) > lim) m |= 1u << small;
                 r_edge = true;
             }
         }
         for (int sd = 0; sd < 2; sd++) {
-            double hf[4];
             int fv[4], fs = 0;
             for (int k = 0; k < 4; k++) {
                 int b[3];
                 b[a] = sd; b[ua] = k & 1; b[va] = k >> 1;
                 fv[k] = b[0] + 2 * b[1] + 4 * b[2];
-                hf[k] = g[fv[k]];
                 fs |= ((sg >> fv[k]) & 1) << k;
             }
-            int around00;
-            double us;
-            if (face_arcs(hf, c, around00, us, fs) == 2) {
-                double den = hf[0] - hf[1] - hf[2] + hf[3];
-                double hs = (hf[0] * hf[3] - hf[1] * hf[2]) / den;
-                double eb = 0;
-                for (int k = 0; k < 4; k++) eb += e[fv[k]];
-                // h_s = (h0 h3 - h1 h2) / den: each value enters with weight <= 2 max|h| / |den|
-                double amp = 2.0 * (fabs(hf[0]) + fabs(hf[1]) + fabs(hf[2]) + fabs(hf[3])) / fabs(den);
-                if (fabs(hs - c) <= 4.0 * amp * eb) {
-                    for (int k = 0; k < 4; k++) m |= 1u << fv[k];
-                    r_face = true;
-                }
+            if (fs != 6 && fs != 9) continue;   // only a diagonal pattern has a saddle decision
+            double hf[4] = {g[fv[0]], g[fv[1]], g[fv[2]], g[fv[3]]};
+            double den = hf[0] - hf[1] - hf[2] + hf[3];
+            double hs = (hf[0] * hf[3] - hf[1] * hf[2]) / den;
+            double eb = 0;
+            for (int k = 0; k < 4; k++) eb += e[fv[k]];
+            // h_s = (h0 h3 - h1 h2) / den: each value enters with weight <= 2 max|h| / |den|
+            double amp = 2.0 * (fabs(hf[0]) + fabs(hf[1]) + fabs(hf[2]) + fabs(hf[3])) / fabs(den);
+            if (fabs(hs - c) <= 4.0 * amp * eb) {
+                for (int k = 0; k < 4; k++) m |= 1u << fv[k];
+                r_face = true;
             }
         }
-        double ru[2], rv[2];
-        int nr = fold_solve(g, a, c, ru, rv, 1e-3, sg);
-        if (nr > 0) {
-            // A = lower face - c, B = upper - lower (bilinear in u, v); a root
-            // solves A = B = 0.  Corner errors move A and B at the root by at
-            // most sum_k b_k e_k (bilinear weights b_k summing to 1), and the
-            // root by J^-1 of that (J the Jacobian of (A, B) in (u, v)).
-            double lo4[4], up4[4], elo[4], eup[4];
-            int ilo4[4], iup4[4];
-            for (int k = 0; k < 4; k++) {
-                int b[3];
-                b[a] = 0; b[ua] = k & 1; b[va] = k >> 1;
-                ilo4[k] = b[0] + 2 * b[1] + 4 * b[2];
-                lo4[k] = g[ilo4[k]];
-                elo[k] = e[ilo4[k]];
-                b[a] = 1;
-                iup4[k] = b[0] + 2 * b[1] + 4 * b[2];
-                up4[k] = g[iup4[k]];
-                eup[k] = e[iup4[k]];
+        // fold roots of axis a: A = lower face - c, B = upper - lower
+        // (bilinear in the face coordinates u, v); a root solves A = B = 0
+        float lo4[4], up4[4], elo[4], eup[4];
+        int ilo4[4], iup4[4], nlo = 0, nup = 0;
+        for (int k = 0; k < 4; k++) {
+            int b[3];
+            b[a] = 0; b[ua] = k & 1; b[va] = k >> 1;
+            ilo4[k] = b[0] + 2 * b[1] + 4 * b[2];
+            b[a] = 1;
+            iup4[k] = b[0] + 2 * b[1] + 4 * b[2];
+            lo4[k] = gc[ilo4[k]]; elo[k] = e[ilo4[k]];
+            up4[k] = gc[iup4[k]]; eup[k] = e[iup4[k]];
+            nlo += (sg >> ilo4[k]) & 1;
+            nup += (sg >> iup4[k]) & 1;
+        }
+        if (nlo == 0 || nlo == 4 || nup == 0 || nup == 4) continue;
+        const float p0 = lo4[0], p1 = lo4[1] - lo4[0], p2 = lo4[2] - lo4[0], p3 = lo4[3] - lo4[1] - lo4[2] + lo4[0];
+        const float d0 = up4[0] - lo4[0], d1 = up4[1] - lo4[1], d2 = up4[2] - lo4[2], d3 = up4[3] - lo4[3];
+        const float q0 = d0, q1 = d1 - d0, q2 = d2 - d0, q3 = d3 - d1 - d2 + d0;
+        if (q0 == 0.f && q1 == 0.f && q2 == 0.f && q3 == 0.f) continue;
+        // (p0 + p1 u)(q2 + q3 u) - (p2 + p3 u)(q0 + q1 u) = 0
+        const float A2 = p1 * q3 - p3 * q1, A1 = p0 * q3 + p1 * q2 - p2 * q1 - p3 * q0, A0 = p0 * q2 - p2 * q0;
+        const float slack = 2e-3f;
+        float us[2];
+        int nu = 0;
+        const float scale = A1 * A1 + 4.f * fabsf(A2 * A0);
+        if (A2 == 0.f) {
+            if (A1 != 0.f) us[nu++] = -A0 / A1;
+        } else {
+            const float disc = A1 * A1 - 4.f * A2 * A0;
+            if (fabsf(disc) <= 1e-4f * scale) {
+                // a double root within FP32 noise: two roots may merge or part
+                const float u2 = -A1 / (2.f * A2);
+                if (u2 > -0.01f && u2 < 1.01f) { all = true; break; }
+            } else if (disc > 0.f) {
+                const float sq = sqrtf(disc), w = A1 >= 0.f ? -0.5f * (A1 + sq) : -0.5f * (A1 - sq);
+                if (w != 0.f) { us[nu++] = w / A2; us[nu++] = A0 / w; }
             }
-            double p1 = lo4[1] - lo4[0], p2 = lo4[2] - lo4[0], p3 = lo4[3] - lo4[1] - lo4[2] + lo4[0];
-            double d0 = up4[0] - lo4[0], d1 = up4[1] - lo4[1], d2 = up4[2] - lo4[2], d3 = up4[3] - lo4[3];
-            double q1 = d1 - d0, q2 = d2 - d0, q3 = d3 - d1 - d2 + d0;
-            for (int r = 0; r < nr && !all; r++) {
-                double u = ru[r], v = rv[r];
-                double w[4] = {(1 - u) * (1 - v), u * (1 - v), (1 - u) * v, u * v};
-                double J11 = p1 + p3 * v, J12 = p2 + p3 * u, J21 = q1 + q3 * v, J22 = q2 + q3 * u;
-                double det = fabs(J11 * J22 - J12 * J21);
-                if (!(det > 0)) { all = true; break; }
-                // a lower corner moves A by w and B by -w, an upper corner B by
-                // w: its share of the root's first-order error (du + dv)
-                double share[8], tot = 0.0, bu = 0.0, bv = 0.0;
-                for (int q = 0; q < 4; q++) {
-                    double slo = w[q] * elo[q], sup = w[q] * eup[q];
-                    double dul = (fabs(J22) + fabs(J12)) * slo / det, dvl = (fabs(J21) + fabs(J11)) * slo / det;
-                    double duu = fabs(J12) * sup / det, dvu = fabs(J11) * sup / det;
-                    share[ilo4[q]] = dul + dvl;
-                    share[iup4[q]] = duu + dvu;
-                    bu += dul + duu;
-                    bv += dvl + dvu;
+        }
+        for (int r = 0; r < nu && !all; r++) {
+            const float u = us[r];
+            if (!(u > -slack && u < 1.f + slack)) continue;
+            const float denB = q2 + q3 * u, denA = p2 + p3 * u;
+            const bool useB = fabsf(denB) >= fabsf(denA);
+            const float den = useB ? denB : denA;
+            if (den == 0.f) { all = true; break; }
+            const float v = useB ? -(q0 + q1 * u) / denB : -(p0 + p1 * u) / denA;
+            if (!(v > -slack && v < 1.f + slack)) continue;
+            // corner errors move A and B at the root by the bilinear weights
+            // times the errors, and the root by J^-1 of that
+            const float w4[4] = {(1 - u) * (1 - v), u * (1 - v), (1 - u) * v, u * v};
+            const float J11 = p1 + p3 * v, J12 = p2 + p3 * u, J21 = q1 + q3 * v, J22 = q2 + q3 * u;
+            const float det = fabsf(J11 * J22 - J12 * J21);
+            if (!(det > 0.f)) { all = true; break; }
+            float share[8], tot = 0.f, bu = 0.f, bv = 0.f;
+            for (int q = 0; q < 4; q++) {
+                const float slo = infl * fabsf(w4[q]) * elo[q], sup = infl * fabsf(w4[q]) * eup[q];
+                const float dul = (fabsf(J22) + fabsf(J12)) * slo / det, dvl = (fabsf(J21) + fabsf(J11)) * slo / det;
+                const float duu = fabsf(J12) * sup / det, dvu = fabsf(J11) * sup / det;
+                share[ilo4[q]] = dul + dvl;
+                share[iup4[q]] = duu + dvu;
+                bu += dul + duu;
+                bv += dvl + dvu;
+            }
+            for (int q = 0; q < 8; q++) tot += share[q];
+            // a root near the face square's boundary may cross it
+            if (fminf(fabsf(u), fabsf(1.f - u)) <= 4.f * bu + 1e-5f || fminf(fabsf(v), fabsf(1.f - v)) <= 4.f * bv + 1e-5f) {
+                all = true;
+                break;
+            }
+            if (h * tot > tolf) {
+                // re-evaluate the largest contributors until the rest is within tol
+                unsigned done = 0;
+                float rest = tot;
+                for (int it = 0; it < 8 && h * rest > tolf; it++) {
+                    int best = -1;
+                    for (int q = 0; q < 8; q++)
+                        if (!((done >> q) & 1) && (best < 0 || share[q] > share[best])) best = q;
+                    done |= 1u << best;
+                    rest -= share[best];
                 }
-                for (int q = 0; q < 8; q++) tot += share[q];
-                // inside the face square (a root near its boundary may cross it)
-                const bool edge_risk = fmin(fabs(u), fabs(1.0 - u)) <= 4.0 * bu ||
-                                       fmin(fabs(v), fabs(1.0 - v)) <= 4.0 * bv;
-                if (edge_risk) { all = true; break; }
-                if (h * tot > tol) {
-                    // re-evaluate the largest contributors until the rest is within tol
-                    unsigned done = 0;
-                    double rest = tot;
-                    for (int it = 0; it < 8 && h * rest > tol; it++) {
-                        int best = -1;
-                        for (int q = 0; q < 8; q++)
-                            if (!((done >> q) & 1) && (best < 0 || share[q] > share[best])) best = q;
-                        done |= 1u << best;
-                        rest -= share[best];
-                    }
-                    m |= done;
-                    r_fold = true;
-                }
+                m |= done;
+                r_fold = true;
             }
         }
     }
