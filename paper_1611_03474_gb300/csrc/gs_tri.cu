@@ -602,13 +602,65 @@ __global__ void __launch_bounds__(128) k_fold_table(TriCtx X, uint8_t *__restric
 }
 
 // first pass: trace every cube, count its output and stage it when it fits
+// Cube classes for the tracing order: cubes of one class take the same
+// branches (crossing edges, fold roots), so warps diverge less.  Class
+// 13 * min(roots, 3) + crossing edges; cubes without a surface go last.
+#define TRI_CLASSES 64
+__global__ void k_tri_class(TriCtx X, int32_t *__restrict__ cls, unsigned *__restrict__ hist)
+{
+    __shared__ unsigned sh[TRI_CLASSES];
+    for (int k = threadIdx.x; k < TRI_CLASSES; k += blockDim.x) sh[k] = 0;
+    __syncthreads();
+    int64_t ci = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (ci < X.ncubes) {
+        int sg = 0;
+        for (int v = 0; v < 8; v++) sg |= (X.phi[X.cvid[ci * 8 + v]] >= X.c ? 1 : 0) << v;
+        int k = TRI_CLASSES - 1;
+        if (sg != 0 && sg != 0xFF) {
+            int ne = 0;
+            for (int a = 0; a < 3; a++) {
+                int ua, va;
+                axes_other(a, ua, va);
+                for (int e = 0; e < 4; e++) {
+                    int b0[3];
+                    b0[a] = 0; b0[ua] = e & 1; b0[va] = e >> 1;
+                    int v0 = b0[0] + 2 * b0[1] + 4 * b0[2], v1 = v0 + (1 << a);
+                    ne += ((sg >> v0) ^ (sg >> v1)) & 1;
+                }
+            }
+            int nr = 0;
+            if (X.fcount) {
+                uint32_t f = *reinterpret_cast<const uint32_t *>(X.fcount + ci * 4);
+                nr = (int)(f & 0xFF) + (int)((f >> 8) & 0xFF) + (int)((f >> 16) & 0xFF);
+            }
+            k = 13 * (nr < 3 ? nr : 3) + ne;
+        }
+        cls[ci] = k;
+        atomicAdd(&sh[k], 1u);
+    }
+    __syncthreads();
+    for (int k = threadIdx.x; k < TRI_CLASSES; k += blockDim.x)
+        if (sh[k]) atomicAdd(&hist[k], sh[k]);
+}
+
+// order[pos] = cube: classes in turn (any order within a class)
+__global__ void k_tri_order(const int32_t *__restrict__ cls, int64_t n, unsigned *__restrict__ cursor,
+                            int32_t *__restrict__ order)
+{
+    int64_t ci = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (ci >= n) return;
+    unsigned pos = atomicAdd(&cursor[cls[ci]], 1u);
+    order[pos] = (int32_t)ci;
+}
+
 __global__ void __launch_bounds__(128) k_tri_count(TriCtx X, int64_t *__restrict__ ntri, int64_t *__restrict__ npt,
                                                    unsigned long long *errs, unsigned long long *surface,
                                                    uint64_t *st_tri, uint64_t *st_pk, double *st_xyz,
-                                                   unsigned long long *degen)
+                                                   unsigned long long *degen, const int32_t *__restrict__ order)
 {
     int64_t ci = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (ci >= X.ncubes) return;
+    if (order) ci = order[ci];
     TriOut o;
     o.ntri = 0; o.npt = 0;
     o.tri_keys = st_tri; o.pt_keys = st_pk; o.pt_xyz = st_xyz;
@@ -715,8 +767,29 @@ int gs_triangulate(const TriCtx &X0, uint64_t **d_tri_keys, int64_t *ntri_total,
     }
     cudaMemsetAsync(ntri + n, 0, sizeof(int64_t), st);
     cudaMemsetAsync(npt + n, 0, sizeof(int64_t), st);
+    // tracing order by cube class (fewer divergent branches per warp)
+    int32_t *cls = nullptr, *order = nullptr;
+    unsigned *hist = nullptr;
+    if (n < ((int64_t)1 << 31) && !gs_alloc((void **)&cls, sizeof(int32_t) * (size_t)n, st) &&
+        !gs_alloc((void **)&order, sizeof(int32_t) * (size_t)n, st) &&
+        !gs_alloc((void **)&hist, sizeof(unsigned) * TRI_CLASSES, st)) {
+        cudaMemsetAsync(hist, 0, sizeof(unsigned) * TRI_CLASSES, st);
+        GS_LAUNCH(k_tri_class, nb, 128, 0, st)(X, cls, hist);
+        unsigned hh[TRI_CLASSES];
+        cudaMemcpyAsync(hh, hist, sizeof(hh), cudaMemcpyDeviceToHost, st);
+        cudaStreamSynchronize(st);
+        unsigned acc = 0;
+        for (int k = 0; k < TRI_CLASSES; k++) { unsigned c = hh[k]; hh[k] = acc; acc += c; }
+        cudaMemcpyAsync(hist, hh, sizeof(hh), cudaMemcpyHostToDevice, st);
+        GS_LAUNCH(k_tri_order, nb, 128, 0, st)(cls, n, hist, order);
+    } else {
+        cudaGetLastError();
+        gs_free(order, st);
+        order = nullptr;
+    }
     GS_LAUNCH(k_tri_count, nb, 128, 0, st)(X, ntri, npt, d_counters + 0, d_counters + 2, st_tri, st_pk, st_xyz,
-                                          d_counters + 1);
+                                          d_counters + 1, order);
+    gs_free(cls, st); gs_free(order, st); gs_free(hist, st);
     rc = gs_scan_i64(ntri, n + 1, tot, st);
     if (!rc) rc = gs_scan_i64(npt, n + 1, tot + 1, st);
     int64_t h[2] = {0, 0};
