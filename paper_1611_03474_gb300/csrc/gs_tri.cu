@@ -578,6 +578,55 @@ __device__ int tri_cube(const TriCtx &X, int64_t ci, TriOut &o, unsigned long lo
     return 0;
 }
 
+// both faces normal to axis a are cut by the surface (needed for a fold root)
+__device__ __forceinline__ bool fold_faces_straddle(int sg, int a)
+{
+    int ua, va;
+    axes_other(a, ua, va);
+    int nlo = 0, nup = 0;
+    for (int k = 0; k < 4; k++) {
+        int b[3];
+        b[a] = 0; b[ua] = k & 1; b[va] = k >> 1;
+        nlo += (sg >> (b[0] + 2 * b[1] + 4 * b[2])) & 1;
+        b[a] = 1;
+        nup += (sg >> (b[0] + 2 * b[1] + 4 * b[2])) & 1;
+    }
+    return nlo != 0 && nlo != 4 && nup != 0 && nup != 4;
+}
+
+// FP32 screen for the fold roots of axis a: false only when the quadratic
+// in u certainly has no root in (0,1) (its FP32 coefficients are within
+// ~1e-6 of their size; the margins below are 1e-3 of it), so the FP64
+// solver runs only where it may find a root
+__device__ __forceinline__ bool fold_may_have_roots(const float *gc, int a)
+{
+    int ua, va;
+    axes_other(a, ua, va);
+    float lo[4], up[4];
+    for (int k = 0; k < 4; k++) {
+        int b[3];
+        b[a] = 0; b[ua] = k & 1; b[va] = k >> 1;
+        lo[k] = gc[b[0] + 2 * b[1] + 4 * b[2]];
+        b[a] = 1;
+        up[k] = gc[b[0] + 2 * b[1] + 4 * b[2]];
+    }
+    const float p0 = lo[0], p1 = lo[1] - lo[0], p2 = lo[2] - lo[0], p3 = lo[3] - lo[1] - lo[2] + lo[0];
+    const float d0 = up[0] - lo[0], d1 = up[1] - lo[1], d2 = up[2] - lo[2], d3 = up[3] - lo[3];
+    const float q0 = d0, q1 = d1 - d0, q2 = d2 - d0, q3 = d3 - d1 - d2 + d0;
+    const float A2 = p1 * q3 - p3 * q1, A1 = p0 * q3 + p1 * q2 - p2 * q1 - p3 * q0, A0 = p0 * q2 - p2 * q0;
+    const float mag = fabsf(p1 * q3) + fabsf(p3 * q1) + fabsf(p0 * q3) + fabsf(p1 * q2) + fabsf(p2 * q1) +
+                      fabsf(p3 * q0) + fabsf(p0 * q2) + fabsf(p2 * q0);
+    if (!(mag > 1e-30f)) return true;                      // degenerate: let FP64 decide
+    if (fabsf(A2) <= 1e-3f * mag) return true;             // near linear
+    const float disc = A1 * A1 - 4.f * A2 * A0, scale = A1 * A1 + 4.f * fabsf(A2 * A0);
+    if (disc < -1e-3f * scale) return false;               // no real root
+    if (disc <= 1e-3f * scale) return true;                // near a double root
+    const float sq = sqrtf(disc), w = A1 >= 0.f ? -0.5f * (A1 + sq) : -0.5f * (A1 - sq);
+    if (w == 0.f) return true;
+    const float u1 = w / A2, u2 = A0 / w;
+    return (u1 > -0.01f && u1 < 1.01f) || (u2 > -0.01f && u2 < 1.01f);
+}
+
 // fold roots of every cube (own ends and, across faces, the neighbours'
 // ends are read from this table instead of being solved again)
 __global__ void __launch_bounds__(128) k_fold_table(TriCtx X, uint8_t *__restrict__ fcount, double *__restrict__ froot)
@@ -587,11 +636,15 @@ __global__ void __launch_bounds__(128) k_fold_table(TriCtx X, uint8_t *__restric
     double g[8];
     for (int v = 0; v < 8; v++) g[v] = X.phi[X.cvid[ci * 8 + v]];
     int sg = 0;
-    for (int v = 0; v < 8; v++) sg |= (g[v] >= X.c ? 1 : 0) << v;
+    float gc[8];
+    for (int v = 0; v < 8; v++) {
+        sg |= (g[v] >= X.c ? 1 : 0) << v;
+        gc[v] = (float)(g[v] - X.c);
+    }
     uint32_t cnt = 0;
     for (int a = 0; a < 3 && sg != 0 && sg != 0xFF; a++) {
         double ru[2], rv[2];
-        int nr = fold_solve(g, a, X.c, ru, rv, 0.0, sg);
+        int nr = fold_faces_straddle(sg, a) && fold_may_have_roots(gc, a) ? fold_solve(g, a, X.c, ru, rv, 0.0, sg) : 0;
         cnt |= (uint32_t)nr << (8 * a);
         for (int r = 0; r < nr; r++) {
             froot[ci * 12 + 4 * a + 2 * r] = ru[r];
