@@ -778,19 +778,31 @@ int gs_estimate_f64(const GsProblem &P, int level, const double *d_A, int64_t n_
 // low half is the cube's slot among the next level's parents, the high half
 // its slot among the accepted cubes.  counters: examined, discarded,
 // accepted, forced, split.
-__global__ void k_level_count(const uint8_t *__restrict__ dec, int64_t n, int64_t *__restrict__ packed,
-                              unsigned long long *counters)
+__global__ void __launch_bounds__(256) k_level_count(const uint8_t *__restrict__ dec, int64_t n,
+                                                     int64_t *__restrict__ packed, unsigned long long *counters)
 {
-    int64_t q = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    unsigned d = q < n ? dec[q] : DEC_INVALID;
-    if (q < n) packed[q] = (int64_t)(d == DEC_SPLIT) | ((int64_t)(d == DEC_ACCEPT || d == DEC_FORCED) << 32);
-    unsigned lane = threadIdx.x & 31;
-    unsigned b[5] = {__ballot_sync(0xffffffffu, d != DEC_INVALID), __ballot_sync(0xffffffffu, d == DEC_DISCARD),
-                     __ballot_sync(0xffffffffu, d == DEC_ACCEPT), __ballot_sync(0xffffffffu, d == DEC_FORCED),
-                     __ballot_sync(0xffffffffu, d == DEC_SPLIT)};
-    if (lane == 0)
-        for (int k = 0; k < 5; k++)
-            if (b[k]) atomicAdd(&counters[k], (unsigned long long)__popc(b[k]));
+    // grid-stride; counts kept per thread and reduced once per block, so the
+    // five global counters see one atomic per block
+    unsigned cnt[5] = {0, 0, 0, 0, 0};
+    for (int64_t q = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; q < n; q += (int64_t)gridDim.x * blockDim.x) {
+        unsigned d = dec[q];
+        packed[q] = (int64_t)(d == DEC_SPLIT) | ((int64_t)(d == DEC_ACCEPT || d == DEC_FORCED) << 32);
+        cnt[0] += d != DEC_INVALID;
+        cnt[1] += d == DEC_DISCARD;
+        cnt[2] += d == DEC_ACCEPT;
+        cnt[3] += d == DEC_FORCED;
+        cnt[4] += d == DEC_SPLIT;
+    }
+    __shared__ unsigned long long sh[5];
+    if (threadIdx.x < 5) sh[threadIdx.x] = 0;
+    __syncthreads();
+    for (int k = 0; k < 5; k++) {
+        unsigned v = cnt[k];
+        for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+        if ((threadIdx.x & 31) == 0 && v) atomicAdd(&sh[k], (unsigned long long)v);
+    }
+    __syncthreads();
+    if (threadIdx.x < 5 && sh[threadIdx.x]) atomicAdd(&counters[threadIdx.x], sh[threadIdx.x]);
 }
 
 __global__ void k_level_emit(GsProblem P, int level, const uint64_t *parents, const uint8_t *vmask,
@@ -821,7 +833,10 @@ int gs_level_compact(const GsProblem &P, int level, const uint64_t *d_parents, c
     if (!rc) rc = gs_alloc((void **)&tot, sizeof(int64_t), st);
     if (rc) { gs_free(packed, st); return rc; }
     cudaMemsetAsync(packed + n, 0, sizeof(int64_t), st);
-    GS_LAUNCH(k_level_count, (unsigned)((n + 255) / 256), 256, 0, st)(d_dec, n, packed, d_counters);
+    {
+        int64_t nb = (n + 255) / 256;
+        GS_LAUNCH(k_level_count, (unsigned)(nb < 152 * 16 ? nb : 152 * 16), 256, 0, st)(d_dec, n, packed, d_counters);
+    }
     rc = gs_scan_i64(packed, n + 1, tot, st);
     int64_t h = 0;
     if (!rc) {

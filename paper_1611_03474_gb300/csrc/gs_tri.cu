@@ -722,7 +722,11 @@ __global__ void __launch_bounds__(128) k_tri_count(TriCtx X, int64_t *__restrict
     o.pt_cap = st_tri ? TRI_STAGE_P : -1;
     int bad = tri_cube(X, ci, o, st_tri ? degen : nullptr);
     if (bad) { atomicAdd(errs, 1ull); o.ntri = 0; o.npt = 0; }
-    if (o.npt > 0) atomicAdd(surface, 1ull);
+    {
+        // one atomic per warp for the surface-cube count
+        const unsigned act = __activemask(), bal = __ballot_sync(act, o.npt > 0);
+        if ((int)(threadIdx.x & 31) == __ffs(act) - 1 && bal) atomicAdd(surface, (unsigned long long)__popc(bal));
+    }
     ntri[ci] = o.ntri;
     npt[ci] = o.npt;
 }
@@ -1049,10 +1053,16 @@ __global__ void __launch_bounds__(128) k_tri_marks(TriCtx X, const float *__rest
     for (int v = 0; v < 8; v++)
         if ((m >> v) & 1) mark[vid[v]] = 1;
     if (why) {
-        // cubes marked through an edge point, a face saddle, a fold root
-        if (r_edge) atomicAdd(&why[0], 1ull);
-        if (r_face) atomicAdd(&why[1], 1ull);
-        if (all || r_fold) atomicAdd(&why[2], 1ull);
+        // cubes marked through an edge point, a face saddle, a fold root (one
+        // atomic per warp and counter)
+        const unsigned act = __activemask();
+        const unsigned b0 = __ballot_sync(act, r_edge), b1 = __ballot_sync(act, r_face),
+                       b2 = __ballot_sync(act, all || r_fold);
+        if ((int)(threadIdx.x & 31) == __ffs(act) - 1) {
+            if (b0) atomicAdd(&why[0], (unsigned long long)__popc(b0));
+            if (b1) atomicAdd(&why[1], (unsigned long long)__popc(b1));
+            if (b2) atomicAdd(&why[2], (unsigned long long)__popc(b2));
+        }
     }
 }
 
