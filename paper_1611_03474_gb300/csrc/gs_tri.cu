@@ -696,14 +696,27 @@ __global__ void k_tri_class(TriCtx X, int32_t *__restrict__ cls, unsigned *__res
         if (sh[k]) atomicAdd(&hist[k], sh[k]);
 }
 
-// order[pos] = cube: classes in turn (any order within a class)
+// order[pos] = cube: classes in turn (any order within a class).  Each block
+// counts its cubes per class in shared memory and reserves one range per
+// class with a single global atomic.
 __global__ void k_tri_order(const int32_t *__restrict__ cls, int64_t n, unsigned *__restrict__ cursor,
                             int32_t *__restrict__ order)
 {
+    __shared__ unsigned cnt[TRI_CLASSES], base[TRI_CLASSES];
+    for (int k = threadIdx.x; k < TRI_CLASSES; k += blockDim.x) cnt[k] = 0;
+    __syncthreads();
     int64_t ci = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    if (ci >= n) return;
-    unsigned pos = atomicAdd(&cursor[cls[ci]], 1u);
-    order[pos] = (int32_t)ci;
+    int k = -1;
+    unsigned local = 0;
+    if (ci < n) {
+        k = cls[ci];
+        local = atomicAdd(&cnt[k], 1u);
+    }
+    __syncthreads();
+    for (int q = threadIdx.x; q < TRI_CLASSES; q += blockDim.x)
+        if (cnt[q]) base[q] = atomicAdd(&cursor[q], cnt[q]);
+    __syncthreads();
+    if (k >= 0) order[base[k] + local] = (int32_t)ci;
 }
 
 __global__ void __launch_bounds__(128) k_tri_count(TriCtx X, int64_t *__restrict__ ntri, int64_t *__restrict__ npt,
