@@ -156,36 +156,35 @@ __global__ void k_vert_claim(GsHash H, const uint64_t *cubes, int64_t n, int max
     if (s >= 0) atomicMin((unsigned long long *)&H.vals[s], (unsigned long long)t);
 }
 
-__global__ void k_vert_owner(GsHash H, const uint64_t *cubes, int64_t n, int max_depth, int64_t *flag)
+// owner flag per corner, and the corner's hash slot (kept so that the later
+// passes index the table directly instead of probing it again)
+__global__ void k_vert_owner(GsHash H, const uint64_t *cubes, int64_t n, int max_depth, int64_t *flag,
+                             int64_t *slot, unsigned *status)
 {
     int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (t >= n * 8) return;
     uint64_t key = corner_key(cubes[t >> 3], (int)(t & 7), max_depth);
     int64_t s = gs_hash_find(H, key);
+    if (s < 0) atomicOr(status, GS_ST_LOOKUP);
+    slot[t] = s;
     flag[t] = (s >= 0 && H.vals[s] == (uint64_t)t) ? 1 : 0;
 }
 
-__global__ void k_vert_write(GsHash H, const uint64_t *cubes, int64_t n, int max_depth, const int64_t *off,
+__global__ void k_vert_write(const uint64_t *cubes, int64_t n, int max_depth, const int64_t *off, const int64_t *slot,
                              uint64_t *vkeys, uint64_t *slot_id)
 {
     int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (t >= n * 8) return;
     if (off[t + 1] == off[t]) return;
-    uint64_t key = corner_key(cubes[t >> 3], (int)(t & 7), max_depth);
-    int64_t s = gs_hash_find(H, key);
-    vkeys[off[t]] = key;
-    if (s >= 0) slot_id[s] = (uint64_t)off[t];
+    vkeys[off[t]] = corner_key(cubes[t >> 3], (int)(t & 7), max_depth);
+    if (slot[t] >= 0) slot_id[slot[t]] = (uint64_t)off[t];
 }
 
-__global__ void k_vert_cvid(GsHash H, const uint64_t *cubes, int64_t n, int max_depth, const uint64_t *slot_id,
-                            int32_t *cvid, unsigned *status)
+__global__ void k_vert_cvid(int64_t n, const int64_t *slot, const uint64_t *slot_id, int32_t *cvid)
 {
     int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (t >= n * 8) return;
-    uint64_t key = corner_key(cubes[t >> 3], (int)(t & 7), max_depth);
-    int64_t s = gs_hash_find(H, key);
-    if (s < 0) { atomicOr(status, GS_ST_LOOKUP); cvid[t] = 0; return; }
-    cvid[t] = (int32_t)slot_id[s];
+    cvid[t] = slot[t] >= 0 ? (int32_t)slot_id[slot[t]] : 0;
 }
 
 int gs_lattice_vertices(const uint64_t *d_cubes, int64_t n, int max_depth, uint64_t **d_vkeys, int64_t *nv,
@@ -197,16 +196,17 @@ int gs_lattice_vertices(const uint64_t *d_cubes, int64_t n, int max_depth, uint6
     GsHash H;
     int rc = gs_hash_make(&H, m / 2 + 8, st);
     if (rc) return rc;
-    int64_t *flag = nullptr, *tot = nullptr;
+    int64_t *flag = nullptr, *tot = nullptr, *slot = nullptr;
     uint64_t *slot_id = nullptr;
     rc = gs_alloc((void **)&flag, sizeof(int64_t) * (size_t)(m + 1), st);
     if (!rc) rc = gs_alloc((void **)&tot, sizeof(int64_t), st);
+    if (!rc) rc = gs_alloc((void **)&slot, sizeof(int64_t) * (size_t)m, st);
     if (!rc) rc = gs_alloc((void **)&slot_id, sizeof(uint64_t) * (size_t)(H.mask + 1), st);
     unsigned nb = (unsigned)((m + 255) / 256);
     if (!rc) {
         GS_LAUNCH(k_vert_claim, nb, 256, 0, st)(H, d_cubes, n, max_depth, d_status);
         cudaMemsetAsync(flag + m, 0, sizeof(int64_t), st);
-        GS_LAUNCH(k_vert_owner, nb, 256, 0, st)(H, d_cubes, n, max_depth, flag);
+        GS_LAUNCH(k_vert_owner, nb, 256, 0, st)(H, d_cubes, n, max_depth, flag, slot, d_status);
         rc = gs_scan_i64(flag, m + 1, tot, st);
     }
     int64_t total = 0;
@@ -218,10 +218,10 @@ int gs_lattice_vertices(const uint64_t *d_cubes, int64_t n, int max_depth, uint6
     if (!rc) rc = gs_alloc((void **)d_vkeys, sizeof(uint64_t) * (size_t)(total + 1), st);
     if (!rc) rc = gs_alloc((void **)d_cvid, sizeof(int32_t) * (size_t)m, st);
     if (!rc) {
-        GS_LAUNCH(k_vert_write, nb, 256, 0, st)(H, d_cubes, n, max_depth, flag, *d_vkeys, slot_id);
-        GS_LAUNCH(k_vert_cvid, nb, 256, 0, st)(H, d_cubes, n, max_depth, slot_id, *d_cvid, d_status);
+        GS_LAUNCH(k_vert_write, nb, 256, 0, st)(d_cubes, n, max_depth, flag, slot, *d_vkeys, slot_id);
+        GS_LAUNCH(k_vert_cvid, nb, 256, 0, st)(n, slot, slot_id, *d_cvid);
     }
-    gs_free(flag, st); gs_free(tot, st); gs_free(slot_id, st);
+    gs_free(flag, st); gs_free(tot, st); gs_free(slot, st); gs_free(slot_id, st);
     gs_hash_free(&H, st);
     if (rc) { gs_free(*d_vkeys, st); gs_free(*d_cvid, st); *d_vkeys = nullptr; *d_cvid = nullptr; return rc; }
     GS_CHECK(cudaGetLastError());
@@ -271,14 +271,15 @@ __global__ void k_weld_claim(GsHash H, const uint64_t *pk, int64_t n, unsigned *
     int64_t s = gs_hash_insert(H, pk[t], status);
     if (s >= 0) atomicMin((unsigned long long *)&H.vals[s], (unsigned long long)t);
 }
-__global__ void k_weld_owner(GsHash H, const uint64_t *pk, int64_t n, int64_t *flag)
+__global__ void k_weld_owner(GsHash H, const uint64_t *pk, int64_t n, int64_t *flag, int64_t *slot)
 {
     int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (t >= n) return;
     int64_t s = gs_hash_find(H, pk[t]);
+    slot[t] = s;
     flag[t] = (s >= 0 && H.vals[s] == (uint64_t)t) ? 1 : 0;
 }
-__global__ void k_weld_write(GsHash H, const uint64_t *pk, const double *pxyz, int64_t n, const int64_t *off,
+__global__ void k_weld_write(const uint64_t *pk, const double *pxyz, int64_t n, const int64_t *off, const int64_t *slot,
                              uint64_t *vkeys, double *vxyz, uint64_t *slot_id)
 {
     int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
@@ -289,8 +290,7 @@ __global__ void k_weld_write(GsHash H, const uint64_t *pk, const double *pxyz, i
     vxyz[3 * id] = pxyz[3 * t];
     vxyz[3 * id + 1] = pxyz[3 * t + 1];
     vxyz[3 * id + 2] = pxyz[3 * t + 2];
-    int64_t s = gs_hash_find(H, pk[t]);
-    if (s >= 0) slot_id[s] = (uint64_t)id;
+    if (slot[t] >= 0) slot_id[slot[t]] = (uint64_t)id;
 }
 __global__ void k_weld_tris(GsHash H, const uint64_t *slot_id, const uint64_t *tk, int64_t ntri, int32_t *tri,
                             unsigned *status)
@@ -310,16 +310,17 @@ int gs_weld(const uint64_t *d_pk, const double *d_pxyz, int64_t npt, const uint6
     GsHash H;
     int rc = gs_hash_make(&H, npt / 2 + 8, st);
     if (rc) return rc;
-    int64_t *flag = nullptr, *tot = nullptr;
+    int64_t *flag = nullptr, *tot = nullptr, *slot = nullptr;
     uint64_t *slot_id = nullptr;
     rc = gs_alloc((void **)&flag, sizeof(int64_t) * (size_t)(npt + 1), st);
     if (!rc) rc = gs_alloc((void **)&tot, sizeof(int64_t), st);
+    if (!rc) rc = gs_alloc((void **)&slot, sizeof(int64_t) * (size_t)npt, st);
     if (!rc) rc = gs_alloc((void **)&slot_id, sizeof(uint64_t) * (size_t)(H.mask + 1), st);
     unsigned nb = (unsigned)((npt + 255) / 256);
     if (!rc) {
         GS_LAUNCH(k_weld_claim, nb, 256, 0, st)(H, d_pk, npt, d_status);
         cudaMemsetAsync(flag + npt, 0, sizeof(int64_t), st);
-        GS_LAUNCH(k_weld_owner, nb, 256, 0, st)(H, d_pk, npt, flag);
+        GS_LAUNCH(k_weld_owner, nb, 256, 0, st)(H, d_pk, npt, flag, slot);
         rc = gs_scan_i64(flag, npt + 1, tot, st);
     }
     int64_t total = 0;
@@ -332,11 +333,11 @@ int gs_weld(const uint64_t *d_pk, const double *d_pxyz, int64_t npt, const uint6
     if (!rc) rc = gs_alloc((void **)d_vxyz, sizeof(double) * 3 * (size_t)(total + 1), st);
     if (!rc) rc = gs_alloc((void **)d_tri, sizeof(int32_t) * 3 * (size_t)(ntri + 1), st);
     if (!rc) {
-        GS_LAUNCH(k_weld_write, nb, 256, 0, st)(H, d_pk, d_pxyz, npt, flag, *d_vkeys, *d_vxyz, slot_id);
+        GS_LAUNCH(k_weld_write, nb, 256, 0, st)(d_pk, d_pxyz, npt, flag, slot, *d_vkeys, *d_vxyz, slot_id);
         if (ntri > 0)
             GS_LAUNCH(k_weld_tris, (unsigned)((3 * ntri + 255) / 256), 256, 0, st)(H, slot_id, d_tk, ntri, *d_tri, d_status);
     }
-    gs_free(flag, st); gs_free(tot, st); gs_free(slot_id, st);
+    gs_free(slot, st); gs_free(flag, st); gs_free(tot, st); gs_free(slot_id, st);
     gs_hash_free(&H, st);
     if (rc) {
         gs_free(*d_vkeys, st); gs_free(*d_vxyz, st); gs_free(*d_tri, st);
