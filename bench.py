@@ -28,6 +28,19 @@ sys.path.insert(0, ROOT)
 
 METRIC = "ms per surface mesh (1M atoms), mixed vs FP64 GPU; Gaussian evals/s, % peak"
 WORKLOAD = dict(name="assembly1m", atoms=1000020, D=0.5, c=1.0, precision=1e-3, min_edge=0.25, max_depth=3)
+
+
+def workload_desc(name):
+    """The config string of a named workload (both arms report the same)."""
+    params = "D=0.5, c=1, precision 1e-3, min edge 0.25 A, max_depth 3"
+    if name == "assembly1m":
+        return ("assembly1m: 1,000,020 atoms (60 x 16,667-atom globular unit on a 250 A icosahedral shell), "
+                + params)
+    if name.startswith("globular"):
+        return "%s: %s-atom globular molecule (0.1 atoms/A^3), %s" % (name, name[len("globular"):], params)
+    if name == "chain100":
+        return "chain100: 100-atom random-walk chain, " + params
+    return name
 # plain-ALU peaks (FLOP/s) from the unit counts and clocks: 152 SMs at 2070 MHz;
 # FP32: 128 FMA lanes/SM/clk; FP64: 2 FMA/SM/clk (1.25 TFLOP/s nominal);
 # an FMA counts 2 flops
@@ -148,8 +161,8 @@ def run_reference(args, ws, rank):
     line = {"impl": "reference", "metric": METRIC, "value": v, "unit": "ms", "n_gpus": args.gpus,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": v, "higher_is_better": False,
             "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-            "config": {"workload": "assembly1m: 1,000,020 atoms, D=0.5, c=1, precision 1e-3, min edge 0.25 A, "
-                                   "max_depth 3", "sample_atoms": args.ref_sample},
+            "config": {"workload": workload_desc(WORKLOAD["name"]), "mode": "fp64 CPU oracle",
+                       "parallelism": "single", "sample_atoms": args.ref_sample},
             "cpu_baseline": dict(b, value=v),
             "e2e": {"value": v, "unit": "ms", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)
@@ -344,8 +357,7 @@ def main():
         "metric": METRIC, "value": ms * (1.0 / ws), "unit": "ms", "n_gpus": ws, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": False, "scaling": "weak",
         "vs_baseline": None, "dtype": "f32+f64" if fp32 else "f64", "data": "synthetic",
-        "config": {"workload": "assembly1m: 1,000,020 atoms (60 x 16,667-atom globular unit on a 250 A "
-                               "icosahedral shell), D=0.5, c=1, precision 1e-3, min edge 0.25 A, max_depth 3",
+        "config": {"workload": workload_desc(args.workload),
                    "mode": args.mode, "parallelism": "replicas" if ws > 1 else "single",
                    "l2": "256 MB flush between timed steps"},
         "gaussian_evals_per_s": evals / (ms * 1e-3),
