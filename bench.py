@@ -168,6 +168,62 @@ def run_reference(args, ws, rank):
     print(json.dumps(line), flush=True)
 
 
+def open_edges(tris):
+    """Directed edges without exactly one oppositely oriented partner (0 for a
+    closed, consistently oriented mesh)."""
+    t = np.asarray(tris, dtype=np.int64)
+    if len(t) == 0:
+        return 0
+    n = int(t.max()) + 1
+    e = t[:, [0, 1, 1, 2, 2, 0]].reshape(-1, 2)
+    fwd = e[:, 0] * n + e[:, 1]
+    rev = e[:, 1] * n + e[:, 0]
+    u, cnt = np.unique(fwd, return_counts=True)
+    dup = int((cnt - 1).sum())
+    return dup + int((~np.isin(rev, u)).sum())
+
+
+READINGS = (("default: re-projected children, bounds first, sum norm", {}),
+            ("child re-expansion", {"child_mode": 1}),
+            ("literal step-3 order", {"decision_order": 1}),
+            ("max-norm precision test", {"precision_norm": 1}),
+            ("euclidean-norm precision test", {"precision_norm": 2}))
+
+
+def readings_form(gs, synth, torch, dev, stream, steps, barrier):
+    cfg = synth.config("globular20k")
+    x = torch.from_numpy(cfg["xyz"]).to(dev)
+    r = torch.from_numpy(cfg["r"]).to(dev)
+    out = {"workload": workload_desc("globular20k") + ", FP64 form; also at precision 1e-2, where cubes are "
+                       "accepted above the finest level", "fidelity": "phi at triangle centroids"}
+    rows = []
+    for (label, kw), prec in [(rd, p) for p in (cfg["precision"], 1e-2) for rd in READINGS]:
+        args = (cfg["D"], cfg["c"], prec, cfg["max_depth"])
+        ts = []
+        for it in range(steps + 1):
+            barrier()
+            t0 = time.perf_counter()
+            m = gs.mesh_gaussian_surface(x, r, *args, min_edge=cfg["min_edge"], stream=stream, device_output=True,
+                                         **kw)
+            torch.cuda.synchronize()
+            if it > 0:
+                ts.append((time.perf_counter() - t0) * 1e3)
+        m = gs.mesh_gaussian_surface(x, r, *args, min_edge=cfg["min_edge"], stream=stream, **kw)
+        st = m.stats
+        cen = m.vertices[m.triangles].mean(1)
+        phi = gs.gs_eval_field(cfg["xyz"], cfg["r"], cfg["D"], cfg["c"], cen, stream=stream)
+        dev_rel = np.abs(phi - cfg["c"]) / cfg["c"]
+        rows.append({"reading": label, "precision": prec, "ms_per_mesh": float(np.mean(ts)),
+                     "ms_levels": st["ms_levels"], "accepted": st["accepted"][:cfg["max_depth"] + 1],
+                     "pair_terms": st["pair_terms"], "examined": st["examined"][:cfg["max_depth"] + 1],
+                     "n_cubes_final": st["n_cubes_final"], "n_triangles": st["n_triangles"],
+                     "open_edges": open_edges(m.triangles),
+                     "centroid_phi_err_max": float(dev_rel.max()) if len(dev_rel) else 0.0,
+                     "centroid_phi_err_mean": float(dev_rel.mean()) if len(dev_rel) else 0.0})
+    out["rows"] = rows
+    return out
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -181,6 +237,8 @@ def main():
     ap.add_argument("--fp64-steps", type=int, default=1, help="extra FP64-form steps timed for comparison")
     ap.add_argument("--diff-steps", type=int, default=2, help="differentiation-form steps (10k atoms) to time")
     ap.add_argument("--batch-steps", type=int, default=1, help="batch-form steps (64 molecules) to time")
+    ap.add_argument("--readings-steps", type=int, default=1,
+                    help="steps per alternative reading (20k atoms, FP64 form) timed and compared")
     args = ap.parse_args()
     ws, rank, local = dist_env()
     if args.impl == "reference":
@@ -340,6 +398,12 @@ def main():
                  "molecules_per_s": 64 * 1e3 / res["concurrent"], "n_workers": 8,
                  "n_triangles": int(sum(m.n_triangles for m in bm))}
 
+    # the alternative readings of section 2.2 on the 20,000-atom globular
+    # molecule, FP64 form: cube counts, work, time and mesh fidelity
+    readings = None
+    if args.readings_steps > 0 and ws == 1:
+        readings = readings_form(gs, synth, torch, dev, stream, args.readings_steps, barrier)
+
     st = stats[-1]
     pairs = st["pair_terms"]
     acc_ms = float(np.mean([s["ms_accum"] for s in stats]))
@@ -379,6 +443,7 @@ def main():
         "fp64_form": fp64,
         "diff_form": diff,
         "batch_form": batch,
+        "readings_form": readings,
     }
     if rank == 0 and ws == 1 and not args.no_cpu_baseline:
         line["cpu_baseline"] = cpu_baseline(cfg)

@@ -55,6 +55,21 @@ extern "C" {
 #define GS_PREC_FP64 0   /* every field sum and estimate in FP64 (the reference form) */
 #define GS_PREC_MIXED 1  /* FP32 compensated sums, FP64 re-evaluation near thresholds */
 
+/* gs_options.child_mode */
+#define GS_CHILD_REPROJECT 0
+#define GS_CHILD_REEXPAND 1
+
+/* gs_options.decision_order (steps 2 and 3 of section 2.2) */
+#define GS_ORDER_BOUNDS_FIRST 0  /* every cube: bound test, then the precision test, then split */
+#define GS_ORDER_LITERAL 1       /* a child meeting the precision test is accepted before its bound test; root
+                                    cubes that pass the bound test are always divided */
+
+/* gs_options.precision_norm: the size of the higher-than-linear coefficients
+   compared with the precision bound (section 2.2.3 leaves the norm open) */
+#define GS_NORM_SUM 0  /* sum of their magnitudes (bounds the sup-norm of that part of the polynomial) */
+#define GS_NORM_MAX 1  /* largest magnitude */
+#define GS_NORM_RSS 2  /* square root of the sum of squares */
+
 /* decisions reported by gs_cube_decisions */
 #define GS_DEC_DISCARD 0
 #define GS_DEC_ACCEPT 1
@@ -97,6 +112,11 @@ typedef struct {
     int device_output;      /* 1: out arrays stay on the device (free with mesh_free) */
     int debug_flags;        /* bit 0: mixed mode also runs FP64 on every cube and counts disagreements */
     gs_stats *stats;        /* nullable: filled on success */
+    int child_mode;         /* child tensors: GS_CHILD_REPROJECT (default: projected from the atoms on each
+                               child box) or GS_CHILD_REEXPAND (the parent's polynomial re-expanded on the
+                               child; the other reading of eq childtensor; FP64 form only) */
+    int decision_order;     /* GS_ORDER_BOUNDS_FIRST (default) or GS_ORDER_LITERAL (FP64 form only) */
+    int precision_norm;     /* GS_NORM_SUM (default), GS_NORM_MAX or GS_NORM_RSS (FP64 form only) */
 } gs_options;
 
 typedef struct {

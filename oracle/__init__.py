@@ -80,6 +80,10 @@ def lib():
         L.or_bounds.argtypes = [p, p]
         L.or_decide.argtypes = [p, d, d, i32, i32, p]
         L.or_decide.restype = i32
+        L.or_decide_ex.argtypes = [p, d, d, i32, i32, i32, i32, p]
+        L.or_decide_ex.restype = i32
+        L.or_high_norm.argtypes = [p, i32]
+        L.or_high_norm.restype = d
         L.or_root_grid.argtypes = [i64, p, p, d, d, d, d, i32, p, p, p]
         L.or_root_grid.restype = i32
         L.or_field.argtypes = [i64, p, p, d, d, d, i64, p, p, p]
@@ -94,6 +98,10 @@ def lib():
         L.or_partition.restype = i32
         L.or_mesh_free.argtypes = [ctypes.POINTER(MeshOut)]
         L.or_mesh_grid.argtypes = [i64, i64, i64, p, d, ctypes.POINTER(MeshOut)]
+        L.or_mesh_ex.argtypes = [i64, p, p, d, d, d, d, d, i32, i32, i32, i32, ctypes.POINTER(MeshOut)]
+        L.or_mesh_ex.restype = i32
+        L.or_child_reexpand.argtypes = [p, i32, p]
+        L.or_child_reexpand.restype = None
         L.or_mesh_grad.argtypes = [i64, p, p, d, d, d, d, d, i32, i64, p, p, p, p]
         L.or_mesh_grad.restype = i32
         L.or_volume_area.argtypes = [i64, p, i64, p, p]
@@ -150,11 +158,18 @@ def bounds(A):
     return out
 
 
-def decide(A, c, precision, level, max_depth):
+def decide(A, c, precision, level, max_depth, order=0, norm=0):
+    """Decision for one cube; order 1 is the literal order of steps 2-3,
+    norm 1/2 measure the high-order coefficients by max |.| / Euclidean norm."""
     A = _f64(A, (64,))
     out = np.zeros(6)
-    d = lib().or_decide(_ptr(A), c, precision, level, max_depth, _ptr(out))
+    d = lib().or_decide_ex(_ptr(A), c, precision, level, max_depth, order, norm, _ptr(out))
     return d, out
+
+
+def high_norm(A, norm):
+    A = _f64(A, (64,))
+    return lib().or_high_norm(_ptr(A), int(norm))
 
 
 def root_grid(xyz, r, D, c, min_edge, max_depth, cutoff_rel=CUTOFF_REL):
@@ -215,13 +230,24 @@ def _arr(ptr, n, dtype, shape=None):
     return a if shape is None else a.reshape(shape)
 
 
-def mesh(xyz, r, D, c, precision, min_edge, max_depth, cutoff_rel=CUTOFF_REL):
-    """Whole path; returns dict(vertices, vkeys, triangles, cube_keys, pre_keys, stats, ...)."""
+def child_reexpand(A, c8):
+    """Coefficients on child c8 of the polynomial with coefficients A[4,4,4]."""
+    A = _f64(A, (64,))
+    B = np.zeros(64)
+    lib().or_child_reexpand(_ptr(A), int(c8), _ptr(B))
+    return B.reshape(4, 4, 4)
+
+
+def mesh(xyz, r, D, c, precision, min_edge, max_depth, cutoff_rel=CUTOFF_REL, child_mode=0, order=0, norm=0):
+    """Whole path; returns dict(vertices, vkeys, triangles, cube_keys, pre_keys, stats, ...).
+    child_mode 1: child tensors by re-expansion of the parent's polynomial;
+    order 1: literal order of steps 2-3; norm 1/2: max |.| / Euclidean norm
+    of the high-order coefficients in the precision test."""
     xyz, r = _f64(xyz), _f64(r)
     out = MeshOut()
     L = lib()
-    e = L.or_mesh(len(r), _ptr(xyz), _ptr(r), D, c, cutoff_rel, precision, min_edge, max_depth,
-                  ctypes.byref(out))
+    e = L.or_mesh_ex(len(r), _ptr(xyz), _ptr(r), D, c, cutoff_rel, precision, min_edge, max_depth, child_mode,
+                     order, norm, ctypes.byref(out))
     if e:
         raise ValueError("oracle status %d" % e)
     try:

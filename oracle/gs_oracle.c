@@ -81,6 +81,9 @@ typedef struct {
     double origin[3];
     int64_t nroot[3];
     double h0;
+    int child_mode;   /* 0: children re-projected from the atoms; 1: re-expansion of the parent's P~ */
+    int order;        /* 0: bound test, then precision test; 1: literal order of steps 2 and 3 */
+    int norm;         /* size of the high-order coefficients: 0 sum of |.|, 1 max |.|, 2 sqrt of sum of squares */
 } oprob;
 
 /* Terms exp(-D(|x-xi|^2 - ri^2)) below cutoff_rel*c are dropped:
@@ -467,6 +470,55 @@ int or_decide(const double *A, double c, double precision, int level, int max_de
     return DEC_SPLIT;
 }
 
+/* The alternative readings of section 2.2.3 and of steps 2-3 of section 2.2.
+ * norm: the size of the coefficients A_jkl with max(j,k,l) >= 2 measured as
+ * the sum of magnitudes (0), the largest magnitude (1) or the Euclidean norm
+ * (2).  order 1 takes steps 2 and 3 as printed: a root cube goes through the
+ * bound test (step 2) and, when kept, is divided (step 3); each child's
+ * polynomial is then computed and, if its higher-order coefficients are under
+ * the bound, the child is accepted as trilinear; otherwise it returns to
+ * step 2 (bound test, then division).  A child without atoms (A = 0) has no
+ * surface and is discarded under both orders. */
+double or_high_norm(const double *A, int norm)
+{
+    double sum = 0, mx = 0, sq = 0;
+    for (int j = 0; j < 4; j++)
+        for (int k = 0; k < 4; k++)
+            for (int l = 0; l < 4; l++) {
+                if (j < 2 && k < 2 && l < 2) continue;
+                double v = A[16 * j + 4 * k + l];
+                sum += fabs(v);
+                if (fabs(v) > mx) mx = fabs(v);
+                sq += v * v;
+            }
+    if (norm == 1) return mx;
+    if (norm == 2) return sqrt(sq);
+    return sum;
+}
+
+int or_decide_ex(const double *A, double c, double precision, int level, int max_depth, int order, int norm,
+                 double *out6)
+{
+    if (order == 0 && norm == 0) return or_decide(A, c, precision, level, max_depth, out6);
+    or_bounds(A, out6);
+    out6[3] = or_high_norm(A, norm);
+    double L = out6[0], U = out6[1];
+    int has_atoms = out6[4] != 0;
+    int trilinear = out6[3] <= precision;
+    int straddles = L <= c && c <= U;
+    if (!has_atoms) return DEC_DISCARD;
+    if (order == 1) {
+        if (level > 0 && trilinear) return DEC_ACCEPT;   /* step 3 on a child */
+        if (!straddles) return DEC_DISCARD;               /* step 2 */
+        if (level >= max_depth) return DEC_FORCED;
+        return DEC_SPLIT;                                 /* step 3: divide */
+    }
+    if (!straddles) return DEC_DISCARD;
+    if (trilinear) return DEC_ACCEPT;
+    if (level >= max_depth) return DEC_FORCED;
+    return DEC_SPLIT;
+}
+
 /* ================================================================== */
 /* Field at points (eq Gaussian1, same truncation, point distance).      */
 /* ================================================================== */
@@ -558,6 +610,37 @@ static void cube_box(const oprob *P, uint64_t key, double *lo, double *hi)
     }
 }
 
+/* Child tensor by re-expansion (the other reading of the child tensor, eq
+ * childtensor): the Legendre coefficients, on child box c8, of the parent's
+ * polynomial P~ = sum A_jkl L_j(s_x) L_k(s_y) L_l(s_z).  On the child's
+ * local coordinates t in [-1,1]^3 the parent coordinate is s = (t + sigma)/2,
+ * sigma = -1 for the lower half and +1 for the upper.  Coefficient
+ * B_pqr = prod (2p+1)/2 times the integral of P~(s(t)) L_p L_q L_r over the
+ * child cube, by 4-point Gauss-Legendre per axis (exact: degree <= 6). */
+void or_child_reexpand(const double *A, int c8, double *B)
+{
+    double t4[4], w4[4];
+    gauss_legendre(4, t4, w4);
+    double sg[3] = {(c8 & 1) ? 1.0 : -1.0, ((c8 >> 1) & 1) ? 1.0 : -1.0, ((c8 >> 2) & 1) ? 1.0 : -1.0};
+    for (int q = 0; q < 64; q++) B[q] = 0.0;
+    for (int ix = 0; ix < 4; ix++)
+        for (int iy = 0; iy < 4; iy++)
+            for (int iz = 0; iz < 4; iz++) {
+                double tx = t4[ix], ty = t4[iy], tz = t4[iz];
+                double sx = (tx + sg[0]) / 2.0, sy = (ty + sg[1]) / 2.0, sz = (tz + sg[2]) / 2.0;
+                double f = 0.0;
+                for (int j = 0; j < 4; j++)
+                    for (int k = 0; k < 4; k++)
+                        for (int l = 0; l < 4; l++) f += A[16 * j + 4 * k + l] * leg(j, sx) * leg(k, sy) * leg(l, sz);
+                double w = w4[ix] * w4[iy] * w4[iz];
+                for (int p = 0; p < 4; p++)
+                    for (int q = 0; q < 4; q++)
+                        for (int r = 0; r < 4; r++)
+                            B[16 * p + 4 * q + r] += (2 * p + 1) / 2.0 * (2 * q + 1) / 2.0 * (2 * r + 1) / 2.0 * w * f *
+                                                     leg(p, tx) * leg(q, ty) * leg(r, tz);
+            }
+}
+
 static int partition(const oprob *P, vec64 *accepted, ostats *st, uint8_t *dec_log_unused)
 {
     (void)dec_log_unused;
@@ -567,14 +650,19 @@ static int partition(const oprob *P, vec64 *accepted, ostats *st, uint8_t *dec_l
             for (int64_t x = 0; x < P->nroot[0]; x++)
                 if (v_push(&cur, okey((uint64_t)x, (uint64_t)y, (uint64_t)z, T_CUBE, 0))) return OR_ERR_OOM;
     st->min_margin = INFINITY;
+    /* child_mode 1: the tensors of the current cubes (children of the split
+     * cubes of the previous level, in the order of cur) */
+    double *curA = NULL, *nxtA = NULL;
+    int64_t nxt_cap = 0;
     for (int l = 0; l <= P->max_depth && cur.n > 0; l++) {
         st->examined[l] = cur.n;
         nxt.n = 0;
         for (int64_t q = 0; q < cur.n; q++) {
             double lo[3], hi[3], A[64], o6[6];
             cube_box(P, cur.a[q], lo, hi);
-            st->pair_terms += cube_tensor(P, lo, hi, A);
-            int d = or_decide(A, P->c, P->precision, l, P->max_depth, o6);
+            if (P->child_mode == 1 && l > 0) memcpy(A, curA + 64 * q, sizeof(A));
+            else st->pair_terms += cube_tensor(P, lo, hi, A);
+            int d = or_decide_ex(A, P->c, P->precision, l, P->max_depth, P->order, P->norm, o6);
             if (o6[4] > 0) {
                 double scale = fabs(P->c) + fabs(o6[0]) + fabs(o6[1]);
                 double mg = fmin(fabs(P->c - o6[0]), fabs(o6[1] - P->c)) / scale;
@@ -590,14 +678,31 @@ static int partition(const oprob *P, vec64 *accepted, ostats *st, uint8_t *dec_l
             st->split[l]++;
             int64_t x, y, zz;
             okey_xyz(cur.a[q], &x, &y, &zz);
-            for (int c8 = 0; c8 < 8; c8++)
+            for (int c8 = 0; c8 < 8; c8++) {
                 if (v_push(&nxt, okey((uint64_t)(2 * x + (c8 & 1)), (uint64_t)(2 * y + ((c8 >> 1) & 1)),
-                                      (uint64_t)(2 * zz + ((c8 >> 2) & 1)), T_CUBE, (unsigned)(l + 1))))
+                                      (uint64_t)(2 * zz + ((c8 >> 2) & 1)), T_CUBE, (unsigned)(l + 1)))) {
+                    free(curA); free(nxtA);
                     return OR_ERR_OOM;
+                }
+                if (P->child_mode == 1) {
+                    if (nxt.n > nxt_cap) {
+                        nxt_cap = 2 * nxt.n + 64;
+                        double *g = (double *)realloc(nxtA, sizeof(double) * 64 * (size_t)nxt_cap);
+                        if (!g) { free(curA); free(nxtA); return OR_ERR_OOM; }
+                        nxtA = g;
+                    }
+                    or_child_reexpand(A, c8, nxtA + 64 * (nxt.n - 1));
+                }
+            }
         }
         vec64 t = cur; cur = nxt; nxt = t;
+        free(curA);
+        curA = nxtA;
+        nxtA = NULL;
+        nxt_cap = 0;
     }
     free(cur.a); free(nxt.a);
+    free(curA); free(nxtA);
     return OR_OK;
 }
 
@@ -1332,13 +1437,20 @@ int or_cube_batch(int64_t n, const double *xyz, const double *r, double D, doubl
 }
 
 /* the whole path: partition, conformity, vertex field, triangulation, weld */
-int or_mesh(int64_t n, const double *xyz, const double *r, double D, double c, double cutoff_rel,
-            double precision, double min_edge, int max_depth, or_mesh_out *out)
+int or_mesh_ex(int64_t n, const double *xyz, const double *r, double D, double c, double cutoff_rel,
+               double precision, double min_edge, int max_depth, int child_mode, int order, int norm,
+               or_mesh_out *out)
 {
     memset(out, 0, sizeof(*out));
     oprob P;
     int e = oprob_init(&P, n, xyz, r, D, c, cutoff_rel, precision, min_edge, max_depth);
     if (e) return e;
+    if (child_mode != 0 && child_mode != 1) { oprob_free(&P); return OR_ERR_ARG; }
+    if (order != 0 && order != 1) { oprob_free(&P); return OR_ERR_ARG; }
+    if (norm < 0 || norm > 2) { oprob_free(&P); return OR_ERR_ARG; }
+    P.child_mode = child_mode;
+    P.order = order;
+    P.norm = norm;
     ostats *st = &out->st;
     vec64 acc = {0};
     e = partition(&P, &acc, st, NULL);
@@ -1417,6 +1529,12 @@ done:
 }
 
 /* partition only (level loop), returns the accepted cubes (sorted) */
+int or_mesh(int64_t n, const double *xyz, const double *r, double D, double c, double cutoff_rel,
+            double precision, double min_edge, int max_depth, or_mesh_out *out)
+{
+    return or_mesh_ex(n, xyz, r, D, c, cutoff_rel, precision, min_edge, max_depth, 0, 0, 0, out);
+}
+
 int or_partition(int64_t n, const double *xyz, const double *r, double D, double c, double cutoff_rel,
                  double precision, double min_edge, int max_depth, or_mesh_out *out)
 {

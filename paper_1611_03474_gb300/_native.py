@@ -51,7 +51,8 @@ class Stats(ctypes.Structure):
 class Options(ctypes.Structure):
     _fields_ = [("min_edge", ctypes.c_double), ("precision_mode", ctypes.c_int), ("cutoff_rel", ctypes.c_double),
                 ("cuda_stream", ctypes.c_void_p), ("device_output", ctypes.c_int), ("debug_flags", ctypes.c_int),
-                ("stats", ctypes.POINTER(Stats))]
+                ("stats", ctypes.POINTER(Stats)), ("child_mode", ctypes.c_int),
+                ("decision_order", ctypes.c_int), ("precision_norm", ctypes.c_int)]
 
 
 class MeshC(ctypes.Structure):
@@ -178,8 +179,15 @@ def _mesh_from_c(m, L, stats, max_depth):
     return res
 
 
+GS_CHILD_REPROJECT, GS_CHILD_REEXPAND = 0, 1
+GS_ORDER_BOUNDS_FIRST, GS_ORDER_LITERAL = 0, 1
+GS_NORM_SUM, GS_NORM_MAX, GS_NORM_RSS = 0, 1, 2
+
+
 def mesh_gaussian_surface(atoms, radii, D, c, precision, max_depth, min_edge=0.25, precision_mode=GS_PREC_FP64,
-                          cutoff_rel=1e-8, stream=None, debug_flags=0, device_output=False):
+                          cutoff_rel=1e-8, stream=None, debug_flags=0, device_output=False,
+                          child_mode=GS_CHILD_REPROJECT, decision_order=GS_ORDER_BOUNDS_FIRST,
+                          precision_norm=GS_NORM_SUM):
     """Mesh {phi = c}; see include/gsmesh.h.  With device_output the mesh
     stays in device memory and only its sizes and stats are returned (the
     arrays are released)."""
@@ -195,6 +203,9 @@ def mesh_gaussian_surface(atoms, radii, D, c, precision, max_depth, min_edge=0.2
     o.cuda_stream = _stream_ptr(stream)
     o.device_output = 1 if device_output else 0
     o.debug_flags = debug_flags
+    o.child_mode = child_mode
+    o.decision_order = decision_order
+    o.precision_norm = precision_norm
     o.stats = ctypes.pointer(st)
     m = MeshC()
     rc = L.mesh_gaussian_surface(_ptr(atoms), _ptr(radii), n, D, c, precision, max_depth, ctypes.byref(o),

@@ -281,18 +281,23 @@ static int prepare(const double *atoms, const double *radii, int64_t n, double D
 }
 
 // process one level in chunks of parents; appends accepted keys; returns the next parents
+// d_parA (re-expansion only): the parents' tensors [n_oct][64]; *d_nextA
+// receives the split cubes' tensors for the next level
 static int run_level(const GsProblem &P, int level, const uint64_t *d_parents, int64_t n_oct, int mode,
                      DevBufs &B, std::vector<uint64_t *> &acc_parts, std::vector<int64_t> &acc_counts,
                      uint64_t **d_next, int64_t *n_next, unsigned long long *d_counters, unsigned long long *d_pairs,
                      unsigned long long *d_rechecked, unsigned long long *d_mism, bool both, unsigned *d_status,
-                     gs_stats *stats)
+                     gs_stats *stats, bool reexpand = false, const double *d_parA = nullptr,
+                     double **d_nextA = nullptr)
 {
     cudaStream_t st = B.st;
     const int64_t CH = 1 << 21;  // octets per chunk (8 GB of FP64 tensors)
     std::vector<uint64_t *> nexts;
+    std::vector<double *> nextAs;
     std::vector<int64_t> ncnt;
     *d_next = nullptr;
     *n_next = 0;
+    if (d_nextA) *d_nextA = nullptr;
     for (int64_t o0 = 0; o0 < n_oct; o0 += CH) {
         int64_t m = n_oct - o0 < CH ? n_oct - o0 : CH;
         const uint64_t *par = d_parents + o0;
@@ -303,39 +308,51 @@ static int run_level(const GsProblem &P, int level, const uint64_t *d_parents, i
         if (mode == GS_PREC_MIXED) {
             rc = gs_level_mixed(P, level, par, m, dec, d_pairs, d_rechecked, d_mism, both, d_status, st,
                                 stats ? &tacc : nullptr, d_mism + 1);
-        } else {
-            double *dA = nullptr;
+        }
+        double *dA = nullptr;
+        if (mode != GS_PREC_MIXED) {
             rc = gs_alloc((void **)&dA, sizeof(double) * 64 * 8 * (size_t)m, st);
             if (rc) { gs_free(dec, st); return rc; }
-            rc = gs_accum_f64(P, level, par, nullptr, m, dA, d_pairs, d_status, st, stats ? &tacc : nullptr);
+            if (reexpand && d_parA) rc = gs_reexpand(d_parA + 64 * o0, m, dA, st);
+            else rc = gs_accum_f64(P, level, par, nullptr, m, dA, d_pairs, d_status, st, stats ? &tacc : nullptr);
             if (!rc) rc = gs_estimate_f64(P, level, dA, m * 8, par, nullptr, dec, nullptr, st);
-            gs_free(dA, st);
         }
         if (stats) { stats->ms_accum += tacc; stats->n_accum_launches++; }
         uint64_t *acc = nullptr;
         if (!rc) rc = gs_alloc((void **)&acc, sizeof(uint64_t) * (size_t)m * 8, st);
         uint64_t *nx = nullptr;
+        double *nA = nullptr;
         int64_t nn = 0, na = 0;
-        if (!rc) rc = gs_level_compact(P, level, par, nullptr, m, dec, &nx, &nn, acc, m * 8, &na, d_counters, st);
+        if (!rc)
+            rc = gs_level_compact(P, level, par, nullptr, m, dec, &nx, &nn, acc, m * 8, &na, d_counters, st,
+                                  reexpand ? dA : nullptr, reexpand ? &nA : nullptr);
         gs_free(dec, st);
-        if (rc) { gs_free(acc, st); gs_free(nx, st); return rc; }
+        gs_free(dA, st);
+        if (rc) { gs_free(acc, st); gs_free(nx, st); gs_free(nA, st); return rc; }
         acc_parts.push_back(acc);
         acc_counts.push_back(na);
-        if (nx) { nexts.push_back(nx); ncnt.push_back(nn); }
+        if (nx) { nexts.push_back(nx); nextAs.push_back(nA); ncnt.push_back(nn); }
     }
     int64_t total = 0;
     for (auto v : ncnt) total += v;
     if (nexts.size() == 1) {
         *d_next = nexts[0];
+        if (d_nextA) *d_nextA = nextAs[0];
+        else gs_free(nextAs[0], st);
     } else if (total > 0) {
         int rc = gs_alloc((void **)d_next, sizeof(uint64_t) * (size_t)total, st);
+        if (!rc && reexpand && d_nextA) rc = gs_alloc((void **)d_nextA, sizeof(double) * 64 * (size_t)total, st);
         if (rc) return rc;
         int64_t off = 0;
         for (size_t i = 0; i < nexts.size(); i++) {
             GS_CHECK(cudaMemcpyAsync(*d_next + off, nexts[i], sizeof(uint64_t) * (size_t)ncnt[i],
                                      cudaMemcpyDeviceToDevice, st));
+            if (reexpand && d_nextA && nextAs[i])
+                GS_CHECK(cudaMemcpyAsync(*d_nextA + 64 * off, nextAs[i], sizeof(double) * 64 * (size_t)ncnt[i],
+                                         cudaMemcpyDeviceToDevice, st));
             off += ncnt[i];
             gs_free(nexts[i], st);
+            gs_free(nextAs[i], st);
         }
     }
     *n_next = total;
@@ -481,6 +498,8 @@ static int mesh_impl(const double *atoms, const double *radii, int64_t n, double
     Prepared PR;
     rc = prepare(atoms, radii, n, D, c, o.cutoff_rel, precision, o.min_edge, max_depth, B, d_status, &PR, stats, T);
     if (rc) return rc;
+    PR.P.order = o.decision_order;
+    PR.P.norm = o.precision_norm;
     const GsProblem &P = PR.P;
 
     // ---- level loop (section 2.2, steps 1-3)
@@ -488,6 +507,8 @@ static int mesh_impl(const double *atoms, const double *radii, int64_t n, double
     std::vector<uint64_t *> acc_all;
     std::vector<int64_t> acc_cnt;
     uint64_t *parents = nullptr;
+    double *parentA = nullptr;   // re-expansion: the parents' tensors
+    const bool reexpand = o.child_mode == GS_CHILD_REEXPAND;
     int64_t n_oct = 0;
     rc = gs_root_blocks(P, &parents, &n_oct, st);
     if (rc) return rc;
@@ -499,8 +520,13 @@ static int mesh_impl(const double *atoms, const double *radii, int64_t n, double
         int64_t nn = 0;
         std::vector<uint64_t *> parts;
         std::vector<int64_t> cnts;
+        double *nextA = nullptr;
         rc = run_level(P, l, parents, n_oct, o.precision_mode, B, parts, cnts, &next, &nn, d_cnt, d_cnt + 8,
-                       d_cnt + 13, d_cnt + 14, (o.debug_flags & 1) != 0, d_status, stats);
+                       d_cnt + 13, d_cnt + 14, (o.debug_flags & 1) != 0, d_status, stats, reexpand, parentA,
+                       reexpand ? &nextA : nullptr);
+        if (parentA) B.release(parentA);
+        parentA = nextA;
+        if (parentA) B.keep(parentA);
         for (size_t i = 0; i < parts.size(); i++) { B.keep(parts[i]); acc_all.push_back(parts[i]); acc_cnt.push_back(cnts[i]); }
         if (parents) B.release(parents);
         if (rc) { gs_free(next, st); return rc; }
@@ -516,6 +542,7 @@ static int mesh_impl(const double *atoms, const double *radii, int64_t n, double
         stats->ms_level[l] = T.ms(ta, tb);
     }
     if (parents) B.release(parents);
+    if (parentA) B.release(parentA);
     rc = check_status(d_status, st, "levels");
     if (rc) return rc;
     int64_t nc = 0;
@@ -674,6 +701,17 @@ static int check_mesh_args(const double *atoms, const double *radii, int64_t n_a
     if (!(o.cutoff_rel > 0 && o.cutoff_rel < 1)) return gs_fail(GS_ERR_ARG, "cutoff_rel must be in (0,1)");
     if (o.precision_mode != GS_PREC_FP64 && o.precision_mode != GS_PREC_MIXED)
         return gs_fail(GS_ERR_ARG, "unknown precision mode");
+    if (o.child_mode != GS_CHILD_REPROJECT && o.child_mode != GS_CHILD_REEXPAND)
+        return gs_fail(GS_ERR_ARG, "unknown child mode");
+    if (o.child_mode == GS_CHILD_REEXPAND && o.precision_mode != GS_PREC_FP64)
+        return gs_fail(GS_ERR_ARG, "child re-expansion is implemented in the FP64 form only");
+    if (o.decision_order != GS_ORDER_BOUNDS_FIRST && o.decision_order != GS_ORDER_LITERAL)
+        return gs_fail(GS_ERR_ARG, "unknown decision order");
+    if (o.precision_norm != GS_NORM_SUM && o.precision_norm != GS_NORM_MAX && o.precision_norm != GS_NORM_RSS)
+        return gs_fail(GS_ERR_ARG, "unknown precision norm");
+    if ((o.decision_order != GS_ORDER_BOUNDS_FIRST || o.precision_norm != GS_NORM_SUM) &&
+        o.precision_mode != GS_PREC_FP64)
+        return gs_fail(GS_ERR_ARG, "the alternative decision order and norms are implemented in the FP64 form only");
     return GS_OK;
 }
 

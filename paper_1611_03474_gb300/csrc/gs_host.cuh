@@ -47,9 +47,14 @@ int gs_field_mixed(const GsProblem &P, const uint64_t *d_vkeys, int64_t n, doubl
                    int64_t *n_rechecked, cudaStream_t st);
 int gs_field_f32(const GsProblem &P, const uint64_t *d_vkeys, const double *d_points, int64_t n, double *d_phi,
                  double *d_grad, float *d_err, unsigned long long *d_terms, cudaStream_t st);
+// d_A / d_nextA (optional): the level's tensors in, the split cubes' tensors
+// out in the order of the next level's parents (for re-expansion)
 int gs_level_compact(const GsProblem &P, int level, const uint64_t *d_parents, const uint8_t *d_vmask, int64_t n_oct,
                      const uint8_t *d_dec, uint64_t **d_next, int64_t *n_next, uint64_t *d_acc_base,
-                     int64_t acc_cap, int64_t *n_acc, unsigned long long *d_counters, cudaStream_t st);
+                     int64_t acc_cap, int64_t *n_acc, unsigned long long *d_counters, cudaStream_t st,
+                     const double *d_A = nullptr, double **d_nextA = nullptr);
+// child tensors [n_oct][8][64] re-expanded from the parents' tensors [n_oct][64]
+int gs_reexpand(const double *d_Apar, int64_t n_oct, double *d_A, cudaStream_t st);
 
 int gs_level_mixed(const GsProblem &P, int level, const uint64_t *d_parents, int64_t n_oct, uint8_t *d_dec,
                    unsigned long long *d_pairs, unsigned long long *d_rechecked, unsigned long long *d_mism,

@@ -45,6 +45,8 @@ struct GsProblem {
     double precision;
     double min_edge;
     int max_depth;
+    int order;           // GS_ORDER_*: decision order of steps 2 and 3 (FP64 form)
+    int norm;            // GS_NORM_*: size of the higher-order coefficients (FP64 form)
     double origin[3];
     int64_t nroot[3];
     double pad;          // largest cutoff radius

@@ -57,6 +57,12 @@ static void gl_rule(int n, long double *t, long double *w)
     }
 }
 
+// Re-expansion of a cubic Legendre series on a half interval: for the lower
+// (h = 0) or upper (h = 1) half of [-1,1], R[h][p][j] = (2p+1)/2 times the
+// integral of L_j((t + sigma)/2) L_p(t) over [-1,1] (sigma = -1 or +1), so
+// that the child's coefficients are R times the parent's.
+__constant__ double c_reexp[2][4][4];
+
 static bool g_gq_ready[64];
 
 int gs_quadrature_init(void)
@@ -80,6 +86,28 @@ int gs_quadrature_init(void)
                 Wf[v][k][j] = (float)W[v][k][j];
             }
         }
+    }
+    {
+        // 4-point Gauss-Legendre integrates the degree-6 products exactly
+        long double t4[4], w4[4];
+        gl_rule(4, t4, w4);
+        auto L = [](int j, long double x) -> long double {
+            switch (j) {
+            case 0: return 1.0L;
+            case 1: return x;
+            case 2: return (3.0L * x * x - 1.0L) / 2.0L;
+            default: return (5.0L * x * x * x - 3.0L * x) / 2.0L;
+            }
+        };
+        static double R[2][4][4];
+        for (int h = 0; h < 2; h++)
+            for (int p = 0; p < 4; p++)
+                for (int j = 0; j < 4; j++) {
+                    long double acc = 0.0L, sg = h ? 1.0L : -1.0L;
+                    for (int q = 0; q < 4; q++) acc += w4[q] * L(j, (t4[q] + sg) / 2.0L) * L(p, t4[q]);
+                    R[h][p][j] = (double)((2.0L * p + 1.0L) / 2.0L * acc);
+                }
+        GS_CHECK(cudaMemcpyToSymbol(c_reexp, R, sizeof(R)));
     }
     GS_CHECK(cudaMemcpyToSymbol(c_gq_t, t, sizeof(t)));
     GS_CHECK(cudaMemcpyToSymbol(c_gq_W, W, sizeof(W)));
@@ -738,6 +766,34 @@ __device__ __forceinline__ int decide(const T *b, T c, T precision, int level, i
     return DEC_SPLIT;
 }
 
+// Literal order of steps 2 and 3: a child whose higher-order coefficients
+// meet the bound is accepted before its bounds are tested; a root cube that
+// passes the bound test is divided.
+__device__ __forceinline__ int decide_literal(const double *b, double c, double precision, int level, int max_depth)
+{
+    if (b[4] == 0.0) return DEC_DISCARD;
+    if (level > 0 && b[3] <= precision) return DEC_ACCEPT;
+    if (!(b[0] <= c && c <= b[1])) return DEC_DISCARD;
+    if (level >= max_depth) return DEC_FORCED;
+    return DEC_SPLIT;
+}
+
+// size of the higher-than-linear coefficients: largest magnitude (GS_NORM_MAX)
+// or root sum of squares (GS_NORM_RSS); the sum of magnitudes is b[3] already
+__device__ __forceinline__ double high_norm(const double *a, int norm)
+{
+    double mx = 0.0, ss = 0.0;
+    for (int j = 0; j < 4; j++)
+        for (int k = 0; k < 4; k++)
+            for (int l = 0; l < 4; l++)
+                if (j >= 2 || k >= 2 || l >= 2) {
+                    const double v = a[16 * j + 4 * k + l];
+                    mx = fmax(mx, fabs(v));
+                    ss = fma(v, v, ss);
+                }
+    return norm == GS_NORM_MAX ? mx : sqrt(ss);
+}
+
 __global__ void __launch_bounds__(128) k_estimate_f64(GsProblem P, int level, const double *__restrict__ A,
                                                       int64_t n, const uint64_t *parents, const uint8_t *vmask,
                                                       uint8_t *__restrict__ dec, double *__restrict__ bounds,
@@ -758,7 +814,9 @@ __global__ void __launch_bounds__(128) k_estimate_f64(GsProblem P, int level, co
     for (int t = 0; t < 64; t++) a[t] = A[q * 64 + t];
     double b[6], rm;
     estimate_bounds<double>(a, b, rm);
-    dec[q] = (uint8_t)decide<double>(b, P.c, P.precision, level, P.max_depth);
+    if (P.norm != GS_NORM_SUM) b[3] = high_norm(a, P.norm);
+    dec[q] = (uint8_t)(P.order == GS_ORDER_LITERAL ? decide_literal(b, P.c, P.precision, level, P.max_depth)
+                                                   : decide<double>(b, P.c, P.precision, level, P.max_depth));
     if (bounds)
         for (int t = 0; t < 6; t++) bounds[q * 6 + t] = b[t];
 }
@@ -771,6 +829,60 @@ int gs_estimate_f64(const GsProblem &P, int level, const double *d_A, int64_t n_
                                                                      d_dec, d_bounds, nullptr, nullptr);
     GS_CHECK(cudaGetLastError());
     return GS_OK;
+}
+
+// ---------------------------------------------------------------- re-expansion
+// child tensors from the parents' (one thread per child): the parent's
+// polynomial re-expanded on the child box, axis by axis
+__global__ void k_reexpand(const double *__restrict__ Apar, int64_t n_oct, double *__restrict__ A_out)
+{
+    int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (t >= n_oct * 8) return;
+    const int c = (int)(t & 7), hx = c & 1, hy = (c >> 1) & 1, hz = c >> 2;
+    const double *P = Apar + (t >> 3) * 64;
+    double B[64], C[64];
+    // along x (first index)
+    for (int p = 0; p < 4; p++)
+        for (int kl = 0; kl < 16; kl++) {
+            double acc = 0.0;
+            for (int j = 0; j < 4; j++) acc = fma(c_reexp[hx][p][j], P[16 * j + kl], acc);
+            B[16 * p + kl] = acc;
+        }
+    // along y
+    for (int p = 0; p < 4; p++)
+        for (int q = 0; q < 4; q++)
+            for (int l = 0; l < 4; l++) {
+                double acc = 0.0;
+                for (int k = 0; k < 4; k++) acc = fma(c_reexp[hy][q][k], B[16 * p + 4 * k + l], acc);
+                C[16 * p + 4 * q + l] = acc;
+            }
+    // along z
+    double *out = A_out + t * 64;
+    for (int pq = 0; pq < 16; pq++)
+        for (int r = 0; r < 4; r++) {
+            double acc = 0.0;
+            for (int l = 0; l < 4; l++) acc = fma(c_reexp[hz][r][l], C[4 * pq + l], acc);
+            out[4 * pq + r] = acc;
+        }
+}
+
+int gs_reexpand(const double *d_Apar, int64_t n_oct, double *d_A, cudaStream_t st)
+{
+    if (n_oct <= 0) return GS_OK;
+    GS_LAUNCH(k_reexpand, (unsigned)((n_oct * 8 + 127) / 128), 128, 0, st)(d_Apar, n_oct, d_A);
+    GS_CHECK(cudaGetLastError());
+    return GS_OK;
+}
+
+// tensors of the split cubes, in the order of the next level's parents
+__global__ void k_split_tensors(const uint8_t *__restrict__ dec, int64_t n, const int64_t *__restrict__ off,
+                                const double *__restrict__ A, double *__restrict__ Anext)
+{
+    int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (t >= n * 64) return;
+    const int64_t q = t >> 6;
+    if (dec[q] != DEC_SPLIT) return;
+    Anext[(off[q] & 0xffffffffll) * 64 + (t & 63)] = A[t];
 }
 
 // ---------------------------------------------------------------- compaction
@@ -823,8 +935,10 @@ __global__ void k_level_emit(GsProblem P, int level, const uint64_t *parents, co
 
 int gs_level_compact(const GsProblem &P, int level, const uint64_t *d_parents, const uint8_t *d_vmask, int64_t n_oct,
                      const uint8_t *d_dec, uint64_t **d_next, int64_t *n_next, uint64_t *d_acc_base,
-                     int64_t acc_cap, int64_t *n_acc, unsigned long long *d_counters, cudaStream_t st)
+                     int64_t acc_cap, int64_t *n_acc, unsigned long long *d_counters, cudaStream_t st,
+                     const double *d_A, double **d_nextA)
 {
+    if (d_nextA) *d_nextA = nullptr;
     int64_t n = n_oct * 8;
     *d_next = nullptr; *n_next = 0; *n_acc = 0;
     if (n <= 0) return GS_OK;
@@ -849,6 +963,11 @@ int gs_level_compact(const GsProblem &P, int level, const uint64_t *d_parents, c
     if (!rc && ns > 0) rc = gs_alloc((void **)d_next, sizeof(uint64_t) * (size_t)ns, st);
     if (!rc) GS_LAUNCH(k_level_emit, (unsigned)((n + 255) / 256), 256, 0, st)(P, level, d_parents, d_vmask, d_dec, n, packed,
                                                                       *d_next, d_acc_base);
+    if (!rc && d_A && d_nextA && ns > 0) {
+        rc = gs_alloc((void **)d_nextA, sizeof(double) * 64 * (size_t)ns, st);
+        if (!rc)
+            GS_LAUNCH(k_split_tensors, (unsigned)((n * 64 + 255) / 256), 256, 0, st)(d_dec, n, packed, d_A, *d_nextA);
+    }
     gs_free(packed, st); gs_free(tot, st);
     if (rc) return rc;
     GS_CHECK(cudaGetLastError());

@@ -8,7 +8,7 @@ import pytest
 
 import oracle
 import synth
-from meshcheck import canonical_triangles, check_closed_manifold
+from meshcheck import canonical_triangles, check_closed_manifold, directed_edge_defects
 
 pytestmark = pytest.mark.gpu
 
@@ -206,3 +206,56 @@ def test_mixed_decisions_match_fp64_globular():
           st["mixed_err_ratio"], "band ratio", st["mixed_band_ratio"])
     assert m.mismatches == 0
     assert st["mixed_err_ratio"] < 1.5e-6
+
+
+def test_child_reexpansion_parity_chain100(chain100):
+    """Re-expansion reading of the child tensor (FP64 form) against the oracle
+    taking the same reading: same cube sets, surface points and topology."""
+    cfg = chain100
+    m = gs.mesh_gaussian_surface(cfg["xyz"], cfg["r"], cfg["D"], cfg["c"], cfg["precision"], cfg["max_depth"],
+                                 min_edge=cfg["min_edge"], child_mode=gs.GS_CHILD_REEXPAND)
+    ref = oracle.mesh(cfg["xyz"], cfg["r"], cfg["D"], cfg["c"], cfg["precision"], cfg["min_edge"], cfg["max_depth"],
+                      child_mode=1)
+    for l in range(cfg["max_depth"] + 1):
+        assert m.stats["examined"][l] == ref["stats"]["examined"][l]
+        assert m.stats["split"][l] == ref["stats"]["split"][l]
+    _assert_mesh_parity(m, ref)
+    # the holes this reading leaves (a re-expanded child's bounds describe the
+    # parent's polynomial, not the field) are the oracle's too
+    assert directed_edge_defects(m.triangles) == directed_edge_defects(ref["triangles"])
+    with pytest.raises(gs.GsError):
+        gs.mesh_gaussian_surface(cfg["xyz"], cfg["r"], cfg["D"], cfg["c"], cfg["precision"], cfg["max_depth"],
+                                 min_edge=cfg["min_edge"], child_mode=gs.GS_CHILD_REEXPAND,
+                                 precision_mode=gs.GS_PREC_MIXED)
+
+
+@pytest.mark.parametrize("order,norm", [(1, 0), (0, 1), (0, 2), (1, 2)])
+def test_alternative_readings_parity(chain100, order, norm):
+    """Literal order of steps 2-3 and the other precision-test norms (FP64
+    form) against the oracle taking the same reading.  precision 0.01 makes
+    the norms matter at level 2."""
+    cfg = dict(chain100, precision=0.01)
+    m = gs.mesh_gaussian_surface(cfg["xyz"], cfg["r"], cfg["D"], cfg["c"], cfg["precision"], cfg["max_depth"],
+                                 min_edge=cfg["min_edge"], decision_order=order, precision_norm=norm)
+    ref = oracle.mesh(cfg["xyz"], cfg["r"], cfg["D"], cfg["c"], cfg["precision"], cfg["min_edge"], cfg["max_depth"],
+                      order=order, norm=norm)
+    for key in ("examined", "split", "accepted", "forced"):
+        assert list(m.stats[key][:cfg["max_depth"] + 1]) == list(ref["stats"][key][:cfg["max_depth"] + 1]), key
+    assert m.stats["conformity_splits"] == ref["stats"]["conformity_splits"]
+    _assert_mesh_parity(m, ref)
+    check_closed_manifold(m.vertices, m.triangles)
+
+
+def test_alternative_readings_rejected_in_mixed_form(chain100):
+    """The alternative readings exist in the FP64 form only; unknown values
+    are argument errors."""
+    cfg = chain100
+    cases = [(gs.GS_PREC_MIXED, dict(decision_order=gs.GS_ORDER_LITERAL)),
+             (gs.GS_PREC_MIXED, dict(precision_norm=gs.GS_NORM_MAX)),
+             (gs.GS_PREC_FP64, dict(precision_norm=7)),
+             (gs.GS_PREC_FP64, dict(decision_order=3))]
+    for mode, kw in cases:
+        with pytest.raises(gs.GsError) as e:
+            gs.mesh_gaussian_surface(cfg["xyz"], cfg["r"], cfg["D"], cfg["c"], cfg["precision"], cfg["max_depth"],
+                                     min_edge=cfg["min_edge"], precision_mode=mode, **kw)
+        assert e.value.code == -1

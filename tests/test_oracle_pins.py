@@ -374,3 +374,103 @@ def test_chain100_closed_manifold_and_level_invariants():
     phi = oracle.field(cfg["xyz"], cfg["r"], cfg["D"], cfg["c"], V)
     assert np.abs(phi - cfg["c"]).max() < 0.05
     assert volume(V, F) > 0
+
+
+@pytest.mark.parametrize("c8", range(8))
+def test_child_reexpansion_reproduces_parent_polynomial(c8):
+    """Re-expansion reading of the child tensor (section 2.2): a cubic in each
+    variable restricted to a half box is again such a cubic, so the child's
+    coefficients must reproduce the parent's P~ at every point of the child
+    box (t_parent = (t_child + s) / 2 with s = -1 for the lower half)."""
+    rng = np.random.default_rng(40 + c8)
+    A = rng.standard_normal((4, 4, 4)) * np.exp(-np.add.outer(np.add.outer(np.arange(4), np.arange(4)), np.arange(4)))
+    B = oracle.child_reexpand(A, c8)
+    s = np.array([1.0 if (c8 >> a) & 1 else -1.0 for a in range(3)])
+    t = rng.uniform(-1, 1, (500, 3))
+    ref = _ptilde(A, (t + s) / 2)
+    assert np.abs(_ptilde(B, t) - ref).max() < 1e-13 * np.abs(A).sum()
+    # the constant alone stays a constant; x alone halves its slope on the child
+    E = np.zeros((4, 4, 4))
+    E[1, 0, 0] = 1.0
+    Bx = oracle.child_reexpand(E, c8)
+    expect = np.zeros((4, 4, 4))
+    expect[0, 0, 0], expect[1, 0, 0] = s[0] / 2, 0.5
+    assert np.abs(Bx - expect).max() < 1e-15
+
+
+def test_child_reexpansion_reading_leaves_holes():
+    """The two readings of the child tensor (section 2.2) differ in kind: with
+    the children re-projected from the atoms the chain mesh is closed; with
+    the parent's polynomial re-expanded, a child's bounds describe that
+    polynomial rather than phi, some surface cubes are discarded as empty and
+    the mesh has open edges.  This is why the projection reading is the
+    default."""
+    cfg = synth.config("chain100")
+    args = (cfg["xyz"], cfg["r"], cfg["D"], cfg["c"], cfg["precision"], cfg["min_edge"], cfg["max_depth"])
+    a = oracle.mesh(*args, child_mode=0)
+    b = oracle.mesh(*args, child_mode=1)
+    assert directed_edge_defects(a["triangles"]) == 0
+    assert directed_edge_defects(b["triangles"]) > 0
+    assert b["stats"]["pair_terms"] < a["stats"]["pair_terms"]
+
+
+def test_precision_norms_match_numpy():
+    """The three sizes of the higher-than-linear coefficients (section 2.2.3
+    leaves the norm open) against numpy's own norms of the same entries."""
+    rng = np.random.default_rng(9)
+    A = rng.standard_normal((4, 4, 4))
+    high = A[np.maximum.outer(np.maximum.outer(np.arange(4), np.arange(4)), np.arange(4)) >= 2]
+    assert high.size == 56
+    assert np.isclose(oracle.high_norm(A, 0), np.linalg.norm(high, 1), rtol=1e-15)
+    assert oracle.high_norm(A, 1) == np.linalg.norm(high, np.inf)
+    assert np.isclose(oracle.high_norm(A, 2), np.linalg.norm(high), rtol=1e-15)
+    # a trilinear tensor has no higher-order part under any norm
+    T = np.zeros((4, 4, 4))
+    T[:2, :2, :2] = rng.standard_normal((2, 2, 2))
+    assert all(oracle.high_norm(T, n) == 0 for n in range(3))
+
+
+def test_literal_decision_order():
+    """Steps 2-3 of section 2.2 as printed: a child whose polynomial is
+    (near) trilinear is accepted without its bound test; a root cube that
+    passes the bound test is divided; a cube without atoms is discarded."""
+    c, prec = 1.0, 1e-3
+    A = np.zeros((4, 4, 4))
+    A[0, 0, 0] = 0.2          # constant 0.2: bounds [0.2, 0.2] miss c = 1
+    assert oracle.decide(A, c, prec, 1, 3)[0] == 0             # bounds first: discard
+    assert oracle.decide(A, c, prec, 1, 3, order=1)[0] == 1    # literal: trilinear child, accept
+    assert oracle.decide(A, c, prec, 0, 3, order=1)[0] == 0    # root: bound test
+    A[1, 0, 0] = 1.0          # 0.2 + x spans [-0.8, 1.2]: straddles c
+    assert oracle.decide(A, c, prec, 0, 3)[0] == 1
+    assert oracle.decide(A, c, prec, 0, 3, order=1)[0] == 2    # a kept root is divided
+    assert oracle.decide(A, c, prec, 2, 3, order=1)[0] == 1
+    A[2, 2, 2] = 0.5          # high part over the bound: bound test, then divide or force
+    assert oracle.decide(A, c, prec, 2, 3, order=1)[0] == 2
+    assert oracle.decide(A, c, prec, 3, 3, order=1)[0] == 3
+    assert oracle.decide(np.zeros((4, 4, 4)), c, prec, 2, 3, order=1)[0] == 0
+
+
+def test_precision_norm_split_sets_are_nested():
+    """max |.| <= Euclidean <= sum of |.|, so a cube split under a smaller
+    norm is split under every larger one: the examined and split counts are
+    ordered level by level, and each mesh stays a closed manifold."""
+    cfg = dict(synth.config("chain100"), precision=0.01)
+    args = (cfg["xyz"], cfg["r"], cfg["D"], cfg["c"], cfg["precision"], cfg["min_edge"], cfg["max_depth"])
+    ms = [oracle.mesh(*args, norm=n) for n in (1, 2, 0)]
+    for lo, hi in zip(ms, ms[1:]):
+        assert np.all(np.asarray(lo["stats"]["split"]) <= np.asarray(hi["stats"]["split"]))
+        assert np.all(np.asarray(lo["stats"]["examined"]) <= np.asarray(hi["stats"]["examined"]))
+    assert sum(ms[0]["stats"]["split"]) < sum(ms[2]["stats"]["split"])
+    for m in ms:
+        check_closed_manifold(m["vertices"], m["triangles"])
+
+
+def test_literal_order_mesh_closed():
+    """Under the literal order the extra cubes are trilinear children that
+    miss the surface: the surface cubes and the mesh stay closed."""
+    cfg = dict(synth.config("chain100"), precision=0.01)
+    args = (cfg["xyz"], cfg["r"], cfg["D"], cfg["c"], cfg["precision"], cfg["min_edge"], cfg["max_depth"])
+    a = oracle.mesh(*args)
+    b = oracle.mesh(*args, order=1)
+    check_closed_manifold(b["vertices"], b["triangles"])
+    assert sum(b["stats"]["accepted"][1:]) >= sum(a["stats"]["accepted"][1:])
