@@ -433,7 +433,7 @@ def main():
         "recheck": {"cubes": st["recheck_cubes"], "vertices": st["recheck_vertices"],
                     "bounds": st["recheck_bounds"], "precision": st["recheck_precision"],
                     "zero": st["recheck_zero"], "rank": st["recheck_rank"],
-                    "vertex_mark_cubes": st["vertex_mark_cubes"]},
+                    "vertex_mark_cubes": st["vertex_mark_cubes"], "estimate_fast_cubes": st["estimate_fast_cubes"]},
         "pair_terms": pairs, "atom_octets": st["atom_octets"], "vertex_terms": st["vertex_terms"],
         "roofline": roofline,
         "clocks": clk,

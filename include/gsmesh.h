@@ -102,6 +102,8 @@ typedef struct {
     int64_t recheck_rank;      /* mixed mode: of recheck_bounds, cubes flagged only through a rank rule near its threshold */
     int64_t vertex_mark_cubes[3]; /* mixed mode: surface cubes whose corners were re-evaluated in FP64 because the
                                      FP32 bound could move an edge point, flip a face saddle, move a fold root */
+    int64_t estimate_fast_cubes; /* mixed mode: cubes kept because the corner values of P~ straddle c, decided
+                                    without the SVD bounds */
 } gs_stats;
 
 typedef struct {

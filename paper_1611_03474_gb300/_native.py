@@ -35,7 +35,8 @@ class Stats(ctypes.Structure):
                 ("n_kernel_launches", ctypes.c_int64), ("recheck_bounds", ctypes.c_int64),
                 ("recheck_precision", ctypes.c_int64), ("recheck_zero", ctypes.c_int64),
                 ("mixed_err_ratio", ctypes.c_double), ("mixed_band_ratio", ctypes.c_double),
-                ("recheck_rank", ctypes.c_int64), ("vertex_mark_cubes", ctypes.c_int64 * 3)]
+                ("recheck_rank", ctypes.c_int64), ("vertex_mark_cubes", ctypes.c_int64 * 3),
+                ("estimate_fast_cubes", ctypes.c_int64)]
 
     def as_dict(self, max_depth=20):
         d = {}

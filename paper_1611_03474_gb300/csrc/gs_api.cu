@@ -661,6 +661,7 @@ static int mesh_impl(const double *atoms, const double *radii, int64_t n, double
     stats->recheck_zero = (int64_t)h[17];
     stats->recheck_rank = (int64_t)h[20];
     for (int k = 0; k < 3; k++) stats->vertex_mark_cubes[k] = (int64_t)h[21 + k];
+    stats->estimate_fast_cubes = (int64_t)h[25];
     {
         unsigned bits = (unsigned)(h[18] & 0xffffffffull);
         float r;

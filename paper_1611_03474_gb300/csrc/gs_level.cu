@@ -1296,20 +1296,101 @@ int gs_accum_f32(const GsProblem &P, int level, const uint64_t *d_parents, const
 // disagreements; the tests require zero.
 #define MIXED_KAPPA 1.5e-6f
 
-__global__ void __launch_bounds__(128) k_estimate_f32(GsProblem P, int level, const float *__restrict__ A,
-                                                      const float *__restrict__ E, int64_t n, const uint64_t *parents,
-                                                      const uint8_t *vmask, uint8_t *__restrict__ dec,
-                                                      uint8_t *__restrict__ flag, unsigned long long *why_cnt,
-                                                      float *__restrict__ dbg)
+// one cube's 64 coefficients (256 B, 16-byte aligned) in 16-byte loads
+__device__ __forceinline__ void load_tensor_f32(const float *__restrict__ src, float *a)
 {
-    int64_t q = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    if (q >= n) return;
+    const float4 *s4 = reinterpret_cast<const float4 *>(src);
+#pragma unroll
+    for (int t = 0; t < 16; t++) {
+        const float4 v = __ldg(s4 + t);
+        a[4 * t] = v.x; a[4 * t + 1] = v.y; a[4 * t + 2] = v.z; a[4 * t + 3] = v.w;
+    }
+}
+
+// P~ at the 8 cube corners: L_n(+-1) = (+-1)^n, so each corner value is a
+// signed sum of the coefficients; lo and hi receive the smallest and largest
+__device__ __forceinline__ void corner_range(const float *a, float &lo, float &hi)
+{
+    lo = 3.0e38f;
+    hi = -3.0e38f;
+#pragma unroll
+    for (int sx = 0; sx < 2; sx++) {
+        float bx[16];
+#pragma unroll
+        for (int kl = 0; kl < 16; kl++) {
+            const float e = a[kl] + a[32 + kl], o = a[16 + kl] + a[48 + kl];
+            bx[kl] = sx ? e + o : e - o;
+        }
+#pragma unroll
+        for (int sy = 0; sy < 2; sy++) {
+            float cz[4];
+#pragma unroll
+            for (int l = 0; l < 4; l++) {
+                const float e = bx[l] + bx[8 + l], o = bx[4 + l] + bx[12 + l];
+                cz[l] = sy ? e + o : e - o;
+            }
+            const float e = cz[0] + cz[2], o = cz[1] + cz[3];
+            lo = fminf(lo, fminf(e - o, e + o));
+            hi = fmaxf(hi, fmaxf(e - o, e + o));
+        }
+    }
+}
+
+// Cubes whose corner values of P~ straddle c by more than the FP32 error of
+// those sums are kept by the FP64 estimate whatever its SVD gives: L <= min P~
+// and max P~ <= U hold for any factorisation, since R = A - A~ is taken
+// exactly and the 1-D and product bounds are enclosures.  Their decision needs
+// only the precision sum.  Returns false for the cubes that need the bounds.
+__device__ __forceinline__ bool estimate_fast_f32(const GsProblem &P, int level, const float *__restrict__ A,
+                                                  const float *__restrict__ E, int64_t q, const uint64_t *parents,
+                                                  const uint8_t *vmask, uint8_t *__restrict__ dec,
+                                                  uint8_t *__restrict__ flag, unsigned long long *why_cnt,
+                                                  float *__restrict__ dbg)
+{
     Octet oc = octet_of(P, level, parents, vmask, q >> 3);
-    if (!((oc.vmask >> (q & 7)) & 1)) { dec[q] = DEC_INVALID; flag[q] = 0; return; }
+    if (!((oc.vmask >> (q & 7)) & 1)) { dec[q] = DEC_INVALID; flag[q] = 0; return true; }
     float a[64];
+    load_tensor_f32(A + q * 64, a);
+    float tot = 0.f, high = 0.f;
+#pragma unroll
+    for (int t = 0; t < 64; t++) {
+        tot += fabsf(a[t]);
+        if ((t >> 4) >= 2 || ((t >> 2) & 3) >= 2 || (t & 3) >= 2) high += fabsf(a[t]);
+    }
+    const float c = (float)P.c, prec = (float)P.precision;
+    const float dA = MIXED_KAPPA * E[q] + 1e-7f * tot;
+    float lo, hi;
+    corner_range(a, lo, hi);
+    // each corner sum moves by at most sum|dA_t| <= 64 dA, plus its own FP32
+    // rounding (6 additions deep, < 4e-7 sum|A|)
+    const float cm = 64.f * dA + 4e-6f * tot;
+    if (!(hi - c > cm && c - lo > cm)) return false;
+    const int d = high <= prec ? DEC_ACCEPT : (level >= P.max_depth ? DEC_FORCED : DEC_SPLIT);
+    if (why_cnt) atomicAdd(&why_cnt[10], 1ull);   // decided without the SVD
+    const bool f = level < P.max_depth && fabsf(prec - high) <= 64.f * dA + 1e-6f * high + 1e-7f * tot;
+    if (f && why_cnt) atomicAdd(&why_cnt[1], 1ull);
+    if (dbg) {
+        float *o = dbg + 6 * q;
+        o[0] = lo; o[1] = hi; o[2] = 0.f; o[3] = dA; o[4] = tot;
+        o[5] = 2.f;   // no SVD bounds: the band check skips the cube
+    }
+    dec[q] = (uint8_t)d;
+    flag[q] = f ? 1 : 0;
+    return true;
+}
+
+// the full FP32 estimate of one valid cube: two-level SVD bounds, rank rules
+// and the bands below
+__device__ __forceinline__ void estimate_full_f32(const GsProblem &P, int level, const float *__restrict__ A,
+                                                  const float *__restrict__ E, int64_t q, uint8_t *__restrict__ dec,
+                                                  uint8_t *__restrict__ flag, unsigned long long *why_cnt,
+                                                  float *__restrict__ dbg)
+{
+    float a[64];
+    load_tensor_f32(A + q * 64, a);
     float tot = 0.f;
 #pragma unroll
-    for (int t = 0; t < 64; t++) { a[t] = A[q * 64 + t]; tot += fabsf(a[t]); }
+    for (int t = 0; t < 64; t++) tot += fabsf(a[t]);
     float b[6], rm;
     float sens;
     RankNear<float> rn;
@@ -1359,7 +1440,38 @@ __global__ void __launch_bounds__(128) k_estimate_f32(GsProblem P, int level, co
         o[5] = (tot > 0.f && rn.m1 <= 32.f * dA + 1e-5f * tot) ? 1.f : 0.f;
     }
     dec[q] = (uint8_t)d;
-    flag[q] = f ? 1 : (uint8_t)alt;
+    flag[q] = f ? 1 : (uint8_t)alt;}
+
+// first pass: invalid and straddling cubes are decided here (one light thread
+// per cube); the others go to a list that the SVD estimate runs over in full
+// warps
+__global__ void __launch_bounds__(256) k_estimate_pre(GsProblem P, int level, const float *__restrict__ A,
+                                                      const float *__restrict__ E, int64_t n, const uint64_t *parents,
+                                                      const uint8_t *vmask, uint8_t *__restrict__ dec,
+                                                      uint8_t *__restrict__ flag, unsigned long long *why_cnt,
+                                                      float *__restrict__ dbg, int32_t *__restrict__ list,
+                                                      unsigned *nlist)
+{
+    const int64_t q = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    const bool slow = q < n && !estimate_fast_f32(P, level, A, E, q, parents, vmask, dec, flag, why_cnt, dbg);
+    const unsigned bal = __ballot_sync(0xffffffffu, slow);
+    if (!bal) return;
+    const unsigned lane = threadIdx.x & 31;
+    unsigned wb = 0;
+    if (lane == 0) wb = atomicAdd(nlist, (unsigned)__popc(bal));
+    wb = __shfl_sync(0xffffffffu, wb, 0);
+    if (slow) list[wb + __popc(bal & ((1u << lane) - 1u))] = (int32_t)q;
+}
+
+__global__ void __launch_bounds__(128) k_estimate_f32(GsProblem P, int level, const float *__restrict__ A,
+                                                      const float *__restrict__ E, uint8_t *__restrict__ dec,
+                                                      uint8_t *__restrict__ flag, unsigned long long *why_cnt,
+                                                      float *__restrict__ dbg, const int32_t *__restrict__ list,
+                                                      const unsigned *nlist)
+{
+    const int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (t >= (int64_t)*nlist) return;
+    estimate_full_f32(P, level, A, E, (int64_t)list[t], dec, flag, why_cnt, dbg);
 }
 
 // cubes whose FP32 decision rests on one rank rule near its threshold
@@ -1414,8 +1526,19 @@ int gs_estimate_f32(const GsProblem &P, int level, const float *d_A, const float
                     cudaStream_t st, unsigned long long *d_why, float *d_dbg)
 {
     if (n_cubes <= 0) return GS_OK;
-    GS_LAUNCH(k_estimate_f32, (unsigned)((n_cubes + 127) / 128), 128, 0, st)(P, level, d_A, d_err, n_cubes, d_parents,
-                                                                            d_vmask, d_dec, d_flag, d_why, d_dbg);
+    int32_t *list = nullptr;
+    unsigned *nlist = nullptr;
+    int rc = gs_alloc((void **)&list, sizeof(int32_t) * (size_t)n_cubes, st);
+    if (!rc) rc = gs_alloc((void **)&nlist, sizeof(unsigned), st);
+    if (rc) { gs_free(list, st); return rc; }
+    GS_CHECK(cudaMemsetAsync(nlist, 0, sizeof(unsigned), st));
+    GS_LAUNCH(k_estimate_pre, (unsigned)((n_cubes + 255) / 256), 256, 0, st)(P, level, d_A, d_err, n_cubes, d_parents,
+                                                                            d_vmask, d_dec, d_flag, d_why, d_dbg,
+                                                                            list, nlist);
+    GS_LAUNCH(k_estimate_f32, (unsigned)((n_cubes + 127) / 128), 128, 0, st)(P, level, d_A, d_err, d_dec, d_flag,
+                                                                            d_why, d_dbg, list, nlist);
+    gs_free(list, st);
+    gs_free(nlist, st);
     GS_CHECK(cudaGetLastError());
     return GS_OK;
 }
@@ -1511,7 +1634,8 @@ __global__ void k_count_mismatch(const uint8_t *a, const uint8_t *b, int64_t n, 
 
 // one chunk of a level in mixed precision; dec receives the final decisions
 // d_why: [0..2] flag reasons (bounds band, precision band, zero tensor), [3] low 32 bits = float bits of
-// the largest |A32 - A64| / E seen in debug mode
+// the largest |A32 - A64| / E seen in debug mode, [4] the same for the band ratio, [5] flags through a rank
+// rule, [10] cubes decided without the SVD (corner values straddle c)
 int gs_level_mixed(const GsProblem &P, int level, const uint64_t *d_parents, int64_t n_oct, uint8_t *d_dec,
                    unsigned long long *d_pairs, unsigned long long *d_rechecked, unsigned long long *d_mism,
                    bool both, unsigned *d_status, cudaStream_t st, float *ms, unsigned long long *d_why)
