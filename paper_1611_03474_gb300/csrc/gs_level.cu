@@ -1004,15 +1004,17 @@ int gs_root_blocks(const GsProblem &P, uint64_t **d_keys, int64_t *n, cudaStream
 // cube's interval), an upper bound of every term's size from which the
 // error band of the FP32 tensor is derived.
 // Per queued atom the coefficient lane writes the products the update needs:
-// WXY[cy][cx][j][k] = w X_cx[j] Y_cy[k] (64), Z[cz][l] (8) and, per child,
-// w Fx Fy Fz (8); the update of lane (child, j) is then two 16-byte loads and
-// 16 FMA per atom.  The eight lanes of a quarter warp read eight consecutive
-// 16-byte words; the record stride (21 words of 16 bytes) spreads the
-// coefficient lanes' stores over all banks.
+// WXY[cy][cx][j][k] = w X_cx[j] Y_cy[k] (64), Z[cz][l] with each value twice
+// (16) and, per child, w Fx Fy Fz (8); the update of lane (child, j) is then
+// three 16-byte loads and 8 paired FMA (f32x2) per atom: the pairs run over
+// k = (0,1) and (2,3) against (Z[l], Z[l]).  Paired operations round each
+// element as the scalar ones do.  The eight lanes of a quarter warp read
+// eight consecutive 16-byte words; the record stride (23 words of 16 bytes)
+// spreads the coefficient lanes' stores over all banks.
 #define ACF_WXY 0
 #define ACF_Z 64
-#define ACF_EB 72
-#define ACF_STRIDE 84
+#define ACF_EB 80
+#define ACF_STRIDE 92
 
 // GV: quadrature variant (a compile-time constant, so the node loop unrolls
 // and the nodes and weights are immediate constant-bank operands)
@@ -1032,7 +1034,7 @@ __global__ void __launch_bounds__(32 * ACC_WARPS, 4) k_accum_f32(GsProblem P, in
     const unsigned below = (1u << lane) - 1u;
     const int c = lane >> 2, j = lane & 3;
     const int cx = c & 1, cy = (c >> 1) & 1, cz = c >> 2;
-    const int oWXY = ACF_WXY + ((cy * 2 + cx) * 4 + j) * 4, oZ = ACF_Z + 4 * cz, oEB = ACF_EB + c;
+    const int oWXY = ACF_WXY + ((cy * 2 + cx) * 4 + j) * 4, oZ = ACF_Z + 8 * cz, oEB = ACF_EB + c;
     const float nDl2e = (float)(-P.D * 1.4426950408889634);
     const float hh = 0.5f * hf;
     for (int64_t o = (int64_t)blockIdx.x * ACC_WARPS + wl; o < n_oct; o += (int64_t)gridDim.x * ACC_WARPS) {
@@ -1053,22 +1055,36 @@ __global__ void __launch_bounds__(32 * ACC_WARPS, 4) k_accum_f32(GsProblem P, in
                     el[a][t] = (float)(rel - (double)eh[a][t]);
                 }
             }
-        float acc[16], comp[16], part[16];
+        // [kp][l] holds the entries (k, l) = (2 kp, l) and (2 kp + 1, l);
+        // ncomp is the negated Kahan compensation
+        float2 acc[2][4], ncomp[2][4], part[2][4];
 #pragma unroll
-        for (int t = 0; t < 16; t++) { acc[t] = 0.f; comp[t] = 0.f; part[t] = 0.f; }
+        for (int kp = 0; kp < 2; kp++)
+#pragma unroll
+            for (int l = 0; l < 4; l++) {
+                acc[kp][l] = make_float2(0.f, 0.f);
+                ncomp[kp][l] = make_float2(0.f, 0.f);
+                part[kp][l] = make_float2(0.f, 0.f);
+            }
         float eb = 0.f;
         int nb = 0, qn = 0;
         const uint8_t vm = q.vmask;
 
+        // Kahan step y = part - comp, s = acc + y, comp = (s - acc) - y; each
+        // subtraction is an FMA with -1, which rounds as the subtraction does
         auto fold = [&]() {
+            const float2 m1 = make_float2(-1.f, -1.f);
 #pragma unroll
-            for (int t = 0; t < 16; t++) {
-                float y = part[t] - comp[t];
-                float s = acc[t] + y;
-                comp[t] = (s - acc[t]) - y;
-                acc[t] = s;
-                part[t] = 0.f;
-            }
+            for (int kp = 0; kp < 2; kp++)
+#pragma unroll
+                for (int l = 0; l < 4; l++) {
+                    const float2 y = __fadd2_rn(part[kp][l], ncomp[kp][l]);
+                    const float2 sm = __fadd2_rn(acc[kp][l], y);
+                    const float2 t = __ffma2_rn(acc[kp][l], m1, sm);
+                    ncomp[kp][l] = __ffma2_rn(t, m1, y);
+                    acc[kp][l] = sm;
+                    part[kp][l] = make_float2(0.f, 0.f);
+                }
             nb = 0;
         };
 
@@ -1125,9 +1141,12 @@ __global__ void __launch_bounds__(32 * ACC_WARPS, 4) k_accum_f32(GsProblem P, in
                         }
                     }
 #pragma unroll
-                for (int z = 0; z < 2; z++)
-                    *reinterpret_cast<float4 *>(rec + ACF_Z + 4 * z) =
-                        make_float4(cf[2][z][0], cf[2][z][1], cf[2][z][2], cf[2][z][3]);
+                for (int z = 0; z < 2; z++) {
+                    *reinterpret_cast<float4 *>(rec + ACF_Z + 8 * z) =
+                        make_float4(cf[2][z][0], cf[2][z][0], cf[2][z][1], cf[2][z][1]);
+                    *reinterpret_cast<float4 *>(rec + ACF_Z + 8 * z + 4) =
+                        make_float4(cf[2][z][2], cf[2][z][2], cf[2][z][3], cf[2][z][3]);
+                }
                 float e8[8];
 #pragma unroll
                 for (int cc = 0; cc < 8; cc++) e8[cc] = w * F[0][cc & 1] * F[1][(cc >> 1) & 1] * F[2][cc >> 2];
@@ -1139,18 +1158,21 @@ __global__ void __launch_bounds__(32 * ACC_WARPS, 4) k_accum_f32(GsProblem P, in
                 const unsigned mt = s_qm[wl][t];
                 const float *rec = s_cf[wl][t];
                 float4 xy = *reinterpret_cast<const float4 *>(rec + oWXY);
-                const float4 z = *reinterpret_cast<const float4 *>(rec + oZ);
+                const float4 za = *reinterpret_cast<const float4 *>(rec + oZ);
+                const float4 zb = *reinterpret_cast<const float4 *>(rec + oZ + 4);
                 float e1 = rec[oEB];
                 if (mt != 0xFFu && !((mt >> c) & 1u)) {
                     // this atom does not reach this lane's child
                     xy = make_float4(0.f, 0.f, 0.f, 0.f);
                     e1 = 0.f;
                 }
-                const float xv[4] = {xy.x, xy.y, xy.z, xy.w}, zv[4] = {z.x, z.y, z.z, z.w};
+                const float2 xk[2] = {make_float2(xy.x, xy.y), make_float2(xy.z, xy.w)};
+                const float2 zl[4] = {make_float2(za.x, za.y), make_float2(za.z, za.w), make_float2(zb.x, zb.y),
+                                      make_float2(zb.z, zb.w)};
 #pragma unroll
-                for (int k = 0; k < 4; k++)
+                for (int kp = 0; kp < 2; kp++)
 #pragma unroll
-                    for (int l = 0; l < 4; l++) part[4 * k + l] = fmaf(xv[k], zv[l], part[4 * k + l]);
+                    for (int l = 0; l < 4; l++) part[kp][l] = __ffma2_rn(xk[kp], zl[l], part[kp][l]);
                 eb += e1;
             };
             int t = 0;
@@ -1235,7 +1257,13 @@ __global__ void __launch_bounds__(32 * ACC_WARPS, 4) k_accum_f32(GsProblem P, in
         }
         float *dst = A_out + ((size_t)o * 8 + c) * 64 + 16 * j;
 #pragma unroll
-        for (int t = 0; t < 16; t++) dst[t] = acc[t] - comp[t];
+        for (int kp = 0; kp < 2; kp++) {
+            float2 v[4];
+#pragma unroll
+            for (int l = 0; l < 4; l++) v[l] = __fadd2_rn(acc[kp][l], ncomp[kp][l]);   // acc - comp
+            *reinterpret_cast<float4 *>(dst + 4 * (2 * kp)) = make_float4(v[0].x, v[1].x, v[2].x, v[3].x);
+            *reinterpret_cast<float4 *>(dst + 4 * (2 * kp + 1)) = make_float4(v[0].y, v[1].y, v[2].y, v[3].y);
+        }
         if (j == 0) E_out[(size_t)o * 8 + c] = eb;
     }
     if (pairs) {
