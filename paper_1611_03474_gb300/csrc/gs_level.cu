@@ -600,6 +600,7 @@ struct RankNear {
     T m1, m2;      // smallest and second-smallest distance of a rule from its threshold
     int who;       // -1: outer rule; i >= 0: inner rule of kept term i
     int alt;       // rank that rule gives if it flips (0: none)
+    T ssum;        // sum of the outer singular values
 };
 
 template <typename T>
@@ -684,6 +685,7 @@ __device__ __forceinline__ void estimate_bounds_sens(const T *A, T *out, T &rmar
         jr = fo;
         rm = T(1e30);
     } else if (rn) {
+        rn->ssum = s[0] + s[1] + s[2] + s[3];
         rank_near<T>(s, jr, -1, *rn);
     }
     rmargin = rm;
@@ -1315,14 +1317,27 @@ int gs_accum_f32(const GsProblem &P, int level, const uint64_t *d_parents, const
 //                    gap between kept and neighbouring singular values (the
 //                    singular vectors' sensitivity); about 9x the largest
 //                    change observed between the FP32 and FP64 estimates
-//   rank rules       a rule within 32 dA of its 99% threshold may flip; then
-//                    a component of at most ~1% of sum(sigma) <= sum|A| may
-//                    move between the main part and R: 0.16 sum|A| is added
+//   rank rules       a rule within 32 dA of its 99% threshold may flip and
+//                    move terms between the main part and R; the decision is
+//                    final when its margin also exceeds RANK_FLIP_ALLOW times
+//                    the sum of the singular values; otherwise one such rule
+//                    is settled by re-estimating under the flipped rank, more
+//                    by FP64
 //   precision sum    |d sum|high|| <= 64 dA + rounding (kept cubes only)
 // Otherwise the cube is flagged and its octet is re-evaluated in FP64.  The
 // debug mode (GS debug bit 0) re-runs every cube in FP64 and counts
 // disagreements; the tests require zero.
 #define MIXED_KAPPA 1.5e-6f
+
+// Largest change of L or U, relative to the sum of the outer singular values
+// S, when rank rules near their 99% thresholds flip.  A flipping rule moves
+// terms whose singular values sum to at most ~1% of S (the rule sits at the
+// threshold); per unit of singular value, a term adds at most 16 to the
+// product bound (|u| <= sum|u_a| <= 2, sum d_k <= 2, |w z| <= 4) and at most 8
+// to sum|R|.  Outer rules move <= 16 (0.011 S); inner rules of term i move
+// <= 8 (0.011 sigma_i) sum_k d_k <= 16 (0.011 sigma_i), <= 16 (0.011 S) over
+// all terms; together <= 0.36 S.
+#define RANK_FLIP_ALLOW 0.4f
 
 // one cube's 64 coefficients (256 B, 16-byte aligned) in 16-byte loads
 __device__ __forceinline__ void load_tensor_f32(const float *__restrict__ src, float *a)
@@ -1422,7 +1437,7 @@ __device__ __forceinline__ void estimate_full_f32(const GsProblem &P, int level,
     float b[6], rm;
     float sens;
     RankNear<float> rn;
-    rn.m1 = rn.m2 = 1e30f; rn.who = -1; rn.alt = 0;
+    rn.m1 = rn.m2 = 1e30f; rn.who = -1; rn.alt = 0; rn.ssum = 0.f;
     estimate_bounds_sens<float>(a, b, rm, sens, 0, -1, 0, &rn);
     const float c = (float)P.c, prec = (float)P.precision;
     int d = decide<float>(b, c, prec, level, P.max_depth);
@@ -1440,6 +1455,9 @@ __device__ __forceinline__ void estimate_full_f32(const GsProblem &P, int level,
         if (mc <= bBase) {
             f = true;
             why = 1;
+        } else if (rn.m1 <= near && mc > bBase + RANK_FLIP_ALLOW * rn.ssum) {
+            // rank rules within their band may flip, but no flip can move L
+            // or U across c (see RANK_FLIP_ALLOW)
         } else if (rn.m1 <= near) {
             // a rank rule within its band may flip.  With one such rule the
             // cube is re-estimated under the flipped rank (k_estimate_alt);
