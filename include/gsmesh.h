@@ -53,7 +53,8 @@ extern "C" {
 
 /* precision modes */
 #define GS_PREC_FP64 0   /* every field sum and estimate in FP64 (the reference form) */
-#define GS_PREC_MIXED 1  /* FP32 compensated sums, FP64 re-evaluation near thresholds */
+#define GS_PREC_MIXED 1  /* FP32 compensated sums, FP64 re-evaluation near thresholds; needs D R^2 <= 80
+                            for the largest cutoff radius R (R^2 = r^2 - ln(cutoff_rel c)/D), else GS_ERR_ARG */
 
 /* gs_options.child_mode */
 #define GS_CHILD_REPROJECT 0

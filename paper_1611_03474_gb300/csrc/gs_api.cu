@@ -176,6 +176,17 @@ struct Prepared {
 };
 
 // upload, prep, cell list; buffers registered in B
+// The FP32 form keeps every weight exp(D r^2) finite and every factor of a
+// term inside the cutoff above the FP32 flush-to-zero range when D R^2 <= 80
+// for the largest cutoff radius R (R^2 = r^2 + K/D)
+static int check_fp32_range(const GsProblem &P)
+{
+    if (P.D * P.pad * P.pad > 80.0)
+        return gs_fail(GS_ERR_ARG, "D r^2 plus the cutoff exponent exceeds 80: outside the FP32 range of the mixed "
+                                   "form; use the FP64 form");
+    return GS_OK;
+}
+
 static int prepare(const double *atoms, const double *radii, int64_t n, double D, double c, double cutoff_rel,
                    double precision, double min_edge, int max_depth, DevBufs &B, unsigned *d_status, Prepared *out,
                    gs_stats *stats, Timer &T)
@@ -501,6 +512,10 @@ static int mesh_impl(const double *atoms, const double *radii, int64_t n, double
     PR.P.order = o.decision_order;
     PR.P.norm = o.precision_norm;
     const GsProblem &P = PR.P;
+    if (o.precision_mode == GS_PREC_MIXED) {
+        rc = check_fp32_range(P);
+        if (rc) return rc;
+    }
 
     // ---- level loop (section 2.2, steps 1-3)
     int tl0 = T.mark();
@@ -1049,6 +1064,7 @@ extern "C" int gs_eval_field(const double *atoms, const double *radii, int64_t n
         if (!rc) { cudaMemsetAsync(d_status, 0, sizeof(unsigned), st); }
         Prepared PR;
         if (!rc) rc = prepare(atoms, radii, n_atoms, D, c, cutoff_rel, 1.0, 0.25, 0, B, d_status, &PR, nullptr, T);
+        if (!rc && precision_mode == GS_PREC_MIXED) rc = check_fp32_range(PR.P);
         const double *d_pts = points;
         double *d_phi = nullptr, *d_grad = nullptr;
         if (!rc && n_points > 0) {

@@ -8,7 +8,7 @@
 // form sums exp(-D (d^2 - r^2)) directly.  The FP32 form takes each atom's
 // offset from its cell corner (FP32) and the point's offset from the same
 // corner (formed in FP64 once per cell), evaluates the exponential with
-// exp2f, sums with Kahan compensation and returns an error bound per point.
+// gs_ex2, sums with Kahan compensation and returns an error bound per point.
 #include "gs_host.cuh"
 
 __device__ __forceinline__ void point_of(const GsProblem &P, const uint64_t *vkeys, const double *pts, int64_t i,
@@ -106,12 +106,12 @@ __global__ void __launch_bounds__(128) k_field_f32(GsProblem P, const uint64_t *
                 // sphere, where a term is ~cutoff_rel * c and inside the bound
                 if (d2 > P.fR2[k]) continue;
                 float r2 = P.fr2[k];
-                float t = exp2f(nDl2e * (d2 - r2));
+                float t = gs_ex2(nDl2e * (d2 - r2));
                 float y = t - comp;
                 float u = s + y;
                 comp = (u - s) - y;
                 s = u;
-                // this term's error: exp2f (2 ulp) and the rounding of its
+                // this term's error: ex2 (2 ulp) and the rounding of its
                 // argument, about 3 ulp of d^2 and r^2 times D
                 eacc = fmaf(t, 3e-7f + 2.5e-7f * Df * (d2 + r2), eacc);
                 g0 = fmaf(m2D * dx, t, g0);

@@ -196,6 +196,18 @@ __device__ __forceinline__ void gs_warp_candidates(const GsProblem &P, const flo
 }
 
 // ---------------------------------------------------------------- exp (FP64)
+// 2^x by the hardware approximation (ex2.approx, relative error <= 2^-22,
+// results below 2^-126 flushed to zero).  The FP32 factors and terms it
+// serves stay far above that range: their arguments are bounded by the
+// cutoff, and a weight exp(D r^2) large enough to reach it overflows FP32
+// first.
+__device__ __forceinline__ float gs_ex2(float x)
+{
+    float y;
+    asm("ex2.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
+    return y;
+}
+
 // exp(x) for |x| <= 700 by Tang's table-driven method (ACM TOMS 15, 1989):
 // x = (32 m + j) ln2/32 + r with |r| <= ln2/64 (Cody-Waite reduction, ln2/32
 // split so that k * GS_L1 is exact for |k| < 2^15), exp(r) - 1 by its degree-6

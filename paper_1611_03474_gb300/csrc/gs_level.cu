@@ -1000,7 +1000,7 @@ int gs_root_blocks(const GsProblem &P, uint64_t **d_keys, int64_t *n, cudaStream
 // ================================================================ mixed precision
 // FP32 accumulation.  Atom centres and lattice coordinates are taken relative
 // to the origin as two-float sums, so differences x - e keep ~1e-7 A; the
-// 1-D factors use exp2f; each lane sums 8 atoms plainly and folds the batch
+// 1-D factors use gs_ex2; each lane sums 8 atoms plainly and folds the batch
 // into a Kahan-compensated accumulator.  Per cube it also sums
 // w * Fx * Fy * Fz (F = the largest value of the atom's 1-D factor on the
 // cube's interval), an upper bound of every term's size from which the
@@ -1104,7 +1104,7 @@ __global__ void __launch_bounds__(32 * ACC_WARPS, 4) k_accum_f32(GsProblem P, in
 #pragma unroll
                     for (int t = 0; t < 3; t++) {
                         d[t] = (eh[a][t] - ah[a]) + (el[a][t] - al[a]);   // e_t - x
-                        f[t] = exp2f(nDl2e * d[t] * d[t]);
+                        f[t] = gs_ex2(nDl2e * d[t] * d[t]);
                     }
 #pragma unroll
                     for (int hI = 0; hI < 2; hI++) {
@@ -1113,7 +1113,7 @@ __global__ void __launch_bounds__(32 * ACC_WARPS, 4) k_accum_f32(GsProblem P, in
 #pragma unroll
                         for (int k = 0; k < NQ; k++) {
                             float dk = fmaf(hh, c_gq_tf[GV][k], m);
-                            float fk = exp2f(nDl2e * dk * dk);
+                            float fk = gs_ex2(nDl2e * dk * dk);
                             a0 = fmaf(c_gq_Wf[GV][k][0], fk, a0);
                             a1 = fmaf(c_gq_Wf[GV][k][1], fk, a1);
                             a2 = fmaf(c_gq_Wf[GV][k][2], fk, a2);

@@ -259,3 +259,17 @@ def test_alternative_readings_rejected_in_mixed_form(chain100):
             gs.mesh_gaussian_surface(cfg["xyz"], cfg["r"], cfg["D"], cfg["c"], cfg["precision"], cfg["max_depth"],
                                      min_edge=cfg["min_edge"], precision_mode=mode, **kw)
         assert e.value.code == -1
+
+
+def test_mixed_form_range_guard():
+    """The FP32 form rejects inputs whose weights exp(D r^2) or cutoff factors
+    leave the FP32 range (D R^2 > 80); the FP64 form meshes them."""
+    xyz, r = np.array([[0.0, 0.0, 0.0], [1.0, 0.5, 0.0]]), np.array([5.0, 5.0])
+    D = 3.0   # D r^2 = 75, plus the cutoff exponent 18.4
+    with pytest.raises(gs.GsError) as e:
+        gs.mesh_gaussian_surface(xyz, r, D, 1.0, 1e-3, 2, min_edge=1.0, precision_mode=gs.GS_PREC_MIXED)
+    assert e.value.code == -1
+    with pytest.raises(gs.GsError):
+        gs.gs_eval_field(xyz, r, D, 1.0, xyz, precision_mode=gs.GS_PREC_MIXED)
+    m = gs.mesh_gaussian_surface(xyz, r, D, 1.0, 1e-3, 2, min_edge=1.0)
+    check_closed_manifold(m.vertices, m.triangles)
