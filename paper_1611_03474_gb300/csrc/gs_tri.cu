@@ -187,23 +187,50 @@ __device__ __forceinline__ double orient(const double *a, const double *b, const
     return (b[i] - a[i]) * (c[j] - a[j]) - (b[j] - a[j]) * (c[i] - a[i]);
 }
 
-// ear clipping of one piece (indices into pts), CCW seen from outside
-__device__ void clip_piece(const TPt *pts, const unsigned char *poly, int n, TriOut &o, unsigned long long *degen)
+// ear clipping of one piece (indices into pts), CCW seen from outside; pf
+// holds the points' coordinates rounded to FP32
+__device__ void clip_piece(const TPt *pts, const float (*pf)[3], const unsigned char *poly, int n, TriOut &o,
+                           unsigned long long *degen)
 {
-    double N0 = 0, N1 = 0, N2 = 0;
+    // Newell normal; the piece is projected along its largest component.
+    // FP32 first: with coordinates in [0,1] each term is at most 2 and carries
+    // at most 7.2e-7 of rounding, the partial sums at most 2n * 6e-8 each, so
+    // every component lies within errM of its exact value.  When the largest
+    // leads the others by more than 2 errM, the axis and the sign are those of
+    // the exact (and the FP64) normal; otherwise FP64 decides.
+    float M0 = 0.f, M1 = 0.f, M2 = 0.f;
     for (int i = 0; i < n; i++) {
-        const double *p = pts[poly[i]].p, *q = pts[poly[i + 1 == n ? 0 : i + 1]].p;
-        N0 += (p[1] - q[1]) * (p[2] + q[2]);
-        N1 += (p[2] - q[2]) * (p[0] + q[0]);
-        N2 += (p[0] - q[0]) * (p[1] + q[1]);
+        const float *p = pf[poly[i]], *q = pf[poly[i + 1 == n ? 0 : i + 1]];
+        M0 += (p[1] - q[1]) * (p[2] + q[2]);
+        M1 += (p[2] - q[2]) * (p[0] + q[0]);
+        M2 += (p[0] - q[0]) * (p[1] + q[1]);
     }
-    int k = 0;
-    double best = fabs(N0);
-    if (fabs(N1) > best) { k = 1; best = fabs(N1); }
-    if (fabs(N2) > best) k = 2;
-    double Nk = k == 0 ? N0 : (k == 1 ? N1 : N2);
+    const float errM = (float)n * (1e-6f + 1.5e-7f * (float)n);
+    const float b0 = fabsf(M0), b1 = fabsf(M1), b2 = fabsf(M2);
+    int k;
+    double sg;
+    const int kf = b0 >= b1 ? (b0 >= b2 ? 0 : 2) : (b1 >= b2 ? 1 : 2);
+    const float top = kf == 0 ? b0 : (kf == 1 ? b1 : b2);
+    const float second = kf == 0 ? fmaxf(b1, b2) : (kf == 1 ? fmaxf(b0, b2) : fmaxf(b0, b1));
+    if (top - second > 2.f * errM && top > errM) {
+        k = kf;
+        sg = (kf == 0 ? M0 : (kf == 1 ? M1 : M2)) >= 0.f ? 1.0 : -1.0;
+    } else {
+        double N0 = 0, N1 = 0, N2 = 0;
+        for (int i = 0; i < n; i++) {
+            const double *p = pts[poly[i]].p, *q = pts[poly[i + 1 == n ? 0 : i + 1]].p;
+            N0 += (p[1] - q[1]) * (p[2] + q[2]);
+            N1 += (p[2] - q[2]) * (p[0] + q[0]);
+            N2 += (p[0] - q[0]) * (p[1] + q[1]);
+        }
+        k = 0;
+        double best = fabs(N0);
+        if (fabs(N1) > best) { k = 1; best = fabs(N1); }
+        if (fabs(N2) > best) k = 2;
+        double Nk = k == 0 ? N0 : (k == 1 ? N1 : N2);
+        sg = Nk >= 0 ? 1.0 : -1.0;
+    }
     int ia = (k + 1) % 3, ib = (k + 2) % 3;
-    double sg = Nk >= 0 ? 1.0 : -1.0;
     unsigned char v[POLY_MAX];
     for (int i = 0; i < n; i++) v[i] = poly[i];
     // Orientation signs, filtered in FP32: the points' local coordinates lie
@@ -213,8 +240,8 @@ __device__ void clip_piece(const TPt *pts, const unsigned char *poly, int n, Tri
     // and the FP64 predicate's.  Otherwise the FP64 predicate decides.
     float qa[TP_MAX], qb[TP_MAX];
     for (int i = 0; i < n; i++) {
-        qa[poly[i]] = (float)pts[poly[i]].p[ia];
-        qb[poly[i]] = (float)pts[poly[i]].p[ib];
+        qa[poly[i]] = pf[poly[i]][ia];
+        qb[poly[i]] = pf[poly[i]][ib];
     }
     auto osign = [&](int a, int b, int c) -> int {
         float d1 = qa[b] - qa[a], d2 = qb[c] - qb[a], d3 = qb[b] - qb[a], d4 = qa[c] - qa[a];
@@ -467,9 +494,19 @@ __device__ int tri_cube(const TriCtx &X, int64_t ci, TriOut &o, unsigned long lo
                 continue;
             }
             // start test: the curve leaves the boundary point into the face,
-            // with the inside on its right seen from outside the cube
-            double hs = (sd ? 1.0 : -1.0) * (a == 1 ? -1.0 : 1.0);
-            double st[4] = {hs * (h[1] - h[0]), hs * (h[3] - h[1]), -hs * (h[3] - h[2]), -hs * (h[2] - h[0])};
+            // with the inside on its right seen from outside the cube.  With
+            // hs = +-1 (sd ? 1 : -1)(a == 1 ? -1 : 1) the test values are
+            // hs (h1 - h0), hs (h3 - h1), -hs (h3 - h2), -hs (h2 - h0); the
+            // sign of a difference of doubles is that of their comparison
+            const bool hp = (sd != 0) == (a != 1);
+            auto st_pos = [&](int e) -> bool {
+                switch (e) {
+                case 0: return hp ? h[1] > h[0] : h[1] < h[0];
+                case 1: return hp ? h[3] > h[1] : h[3] < h[1];
+                case 2: return hp ? h[3] < h[2] : h[3] > h[2];
+                default: return hp ? h[2] < h[0] : h[2] > h[0];
+                }
+            };
             int pr[2][2];
             if (narc == 1) {
                 int k = 0;
@@ -483,7 +520,7 @@ __device__ int tri_cube(const TriCtx &X, int64_t ci, TriOut &o, unsigned long lo
             for (int ai = 0; ai < narc; ai++) {
                 int e1 = pr[ai][0], e2 = pr[ai][1];
                 if (ep[e1] < 0 || ep[e2] < 0) return 1;
-                bool s1 = st[e1] > 0, s2 = st[e2] > 0;
+                bool s1 = st_pos(e1), s2 = st_pos(e2);
                 if (s1 == s2) return 1;
                 int S = s1 ? ep[e1] : ep[e2], T = s1 ? ep[e2] : ep[e1];
                 int mid[8], nm = 0;
@@ -496,9 +533,13 @@ __device__ int tri_cube(const TriCtx &X, int64_t ci, TriOut &o, unsigned long lo
                     }
                     if (nm < 8) mid[nm++] = id;
                 }
-                double du = pts[T].p[ua] - pts[S].p[ua], dv = pts[T].p[va] - pts[S].p[va];
-                int ax = fabs(du) >= fabs(dv) ? ua : va;
-                double sg = (ax == ua ? du : dv) >= 0 ? 1.0 : -1.0;
+                int ax = ua;
+                double sg = 1.0;
+                if (nm > 1) {
+                    double du = pts[T].p[ua] - pts[S].p[ua], dv = pts[T].p[va] - pts[S].p[va];
+                    ax = fabs(du) >= fabs(dv) ? ua : va;
+                    sg = (ax == ua ? du : dv) >= 0 ? 1.0 : -1.0;
+                }
                 for (int i1 = 1; i1 < nm; i1++) {
                     int x = mid[i1], j = i1 - 1;
                     while (j >= 0) {
@@ -521,6 +562,9 @@ __device__ int tri_cube(const TriCtx &X, int64_t ci, TriOut &o, unsigned long lo
     for (int i = 0; i < np; i++)
         if (pts[i].kind != 3 && nxt[i] < 0) return 1;
 
+    float pf[TP_MAX][3];
+    for (int i = 0; i < np; i++)
+        for (int a = 0; a < 3; a++) pf[i][a] = (float)pts[i].p[a];
     // pieces: faces of the graph of loops and fold segments, traced with the
     // face on the left; at a critical point take the next segment clockwise
     unsigned long long used_loop = 0ull;
@@ -557,19 +601,26 @@ __device__ int tri_cube(const TriCtx &X, int64_t ci, TriOut &o, unsigned long lo
             if (slot >= 0 && ((used_fold[cur] >> slot) & 1u)) { ok = false; break; }
         }
         if (!ok) return 1;
-        if (n >= 3) clip_piece(pts, poly, n, o, degen);
+        if (n >= 3) clip_piece(pts, pf, poly, n, o, degen);
     }
     // points in world coordinates
     if (np <= o.pt_cap) {
         double h = ldexp(X.min_edge, X.max_depth - lvl);
+        double lo[3], hi[3];
+        for (int a = 0; a < 3; a++) {
+            lo[a] = __dadd_rn(X.origin[a], __dmul_rn((double)(C[a] * sc), X.min_edge));
+            hi[a] = __dadd_rn(X.origin[a], __dmul_rn((double)((C[a] + 1) * sc), X.min_edge));
+        }
         for (int i = 0; i < np; i++) {
             double *dst = o.pt_xyz + 3 * (o.pt_off + i);
             for (int a = 0; a < 3; a++) {
+                // the cube's own faces (local 0 or 1, read from the bits)
+                // take the lattice coordinates; lo + (-0) h is lo as well
                 double f = pts[i].p[a];
-                double lo = __dadd_rn(X.origin[a], __dmul_rn((double)(C[a] * sc), X.min_edge));
-                if (f == 0.0) dst[a] = lo;
-                else if (f == 1.0) dst[a] = __dadd_rn(X.origin[a], __dmul_rn((double)((C[a] + 1) * sc), X.min_edge));
-                else dst[a] = __dadd_rn(lo, __dmul_rn(f, h));
+                const unsigned long long fb = (unsigned long long)__double_as_longlong(f);
+                if ((fb << 1) == 0ull) dst[a] = lo[a];
+                else if (fb == 0x3FF0000000000000ull) dst[a] = hi[a];
+                else dst[a] = __dadd_rn(lo[a], __dmul_rn(f, h));
             }
             o.pt_keys[o.pt_off + i] = pts[i].key;
         }
