@@ -451,26 +451,67 @@ __device__ void jacobi4(T (&X)[4][N], T (&s)[4], T (&u)[4][4])
 #pragma unroll
             for (int q = p + 1; q < 4; q++) {
                 T al = 0, be = 0, ga = 0;
+                if constexpr (sizeof(T) == 4 && N % 4 == 0) {
+                    // FP32: paired (f32x2) products over k = (2m, 2m+1), two
+                    // partial sums each to shorten the dependency chains
+                    float2 a2[2] = {make_float2(0.f, 0.f), make_float2(0.f, 0.f)};
+                    float2 b2[2] = {a2[0], a2[0]}, g2[2] = {a2[0], a2[0]};
 #pragma unroll
-                for (int k = 0; k < N; k++) {
-                    al += X[p][k] * X[p][k];
-                    be += X[q][k] * X[q][k];
-                    ga += X[p][k] * X[q][k];
+                    for (int m = 0; m < N / 2; m++) {
+                        const float2 xp = make_float2(X[p][2 * m], X[p][2 * m + 1]);
+                        const float2 xq = make_float2(X[q][2 * m], X[q][2 * m + 1]);
+                        a2[m & 1] = __ffma2_rn(xp, xp, a2[m & 1]);
+                        b2[m & 1] = __ffma2_rn(xq, xq, b2[m & 1]);
+                        g2[m & 1] = __ffma2_rn(xp, xq, g2[m & 1]);
+                    }
+                    const float2 a = __fadd2_rn(a2[0], a2[1]), b = __fadd2_rn(b2[0], b2[1]), g = __fadd2_rn(g2[0], g2[1]);
+                    al = a.x + a.y;
+                    be = b.x + b.y;
+                    ga = g.x + g.y;
+                } else {
+#pragma unroll
+                    for (int k = 0; k < N; k++) {
+                        al += X[p][k] * X[p][k];
+                        be += X[q][k] * X[q][k];
+                        ga += X[p][k] * X[q][k];
+                    }
                 }
                 T cs, sn;
                 if (!jac_rot<T>(al, be, ga, cs, sn)) continue;
                 any = true;
+                if constexpr (sizeof(T) == 4 && N % 2 == 0) {
+                    const float2 c2 = make_float2(cs, cs), s2 = make_float2(sn, sn), ns2 = make_float2(-sn, -sn);
 #pragma unroll
-                for (int k = 0; k < N; k++) {
-                    T xp = X[p][k], xq = X[q][k];
-                    X[p][k] = cs * xp - sn * xq;
-                    X[q][k] = sn * xp + cs * xq;
-                }
+                    for (int m = 0; m < N / 2; m++) {
+                        const float2 xp = make_float2(X[p][2 * m], X[p][2 * m + 1]);
+                        const float2 xq = make_float2(X[q][2 * m], X[q][2 * m + 1]);
+                        const float2 np2 = __ffma2_rn(c2, xp, __fmul2_rn(ns2, xq));
+                        const float2 nq2 = __ffma2_rn(s2, xp, __fmul2_rn(c2, xq));
+                        X[p][2 * m] = np2.x; X[p][2 * m + 1] = np2.y;
+                        X[q][2 * m] = nq2.x; X[q][2 * m + 1] = nq2.y;
+                    }
 #pragma unroll
-                for (int k = 0; k < 4; k++) {
-                    T qp = Q[p][k], qq = Q[q][k];
-                    Q[p][k] = cs * qp - sn * qq;
-                    Q[q][k] = sn * qp + cs * qq;
+                    for (int m = 0; m < 2; m++) {
+                        const float2 qp = make_float2(Q[p][2 * m], Q[p][2 * m + 1]);
+                        const float2 qq = make_float2(Q[q][2 * m], Q[q][2 * m + 1]);
+                        const float2 np2 = __ffma2_rn(c2, qp, __fmul2_rn(ns2, qq));
+                        const float2 nq2 = __ffma2_rn(s2, qp, __fmul2_rn(c2, qq));
+                        Q[p][2 * m] = np2.x; Q[p][2 * m + 1] = np2.y;
+                        Q[q][2 * m] = nq2.x; Q[q][2 * m + 1] = nq2.y;
+                    }
+                } else {
+#pragma unroll
+                    for (int k = 0; k < N; k++) {
+                        T xp = X[p][k], xq = X[q][k];
+                        X[p][k] = cs * xp - sn * xq;
+                        X[q][k] = sn * xp + cs * xq;
+                    }
+#pragma unroll
+                    for (int k = 0; k < 4; k++) {
+                        T qp = Q[p][k], qq = Q[q][k];
+                        Q[p][k] = cs * qp - sn * qq;
+                        Q[q][k] = sn * qp + cs * qq;
+                    }
                 }
             }
         if (!any) break;
