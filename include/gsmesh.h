@@ -156,6 +156,32 @@ gs_options gs_default_options(void);
 int mesh_gaussian_surface(const double *atoms, const double *radii, int64_t n_atoms, double D, double c,
                           double precision, int max_depth, const gs_options *opt, gs_mesh *out);
 
+/* Output buffers owned by the caller (host memory, pinned or pageable, or
+ * device memory, told apart by the CUDA runtime): the mesh is copied into
+ * them directly, so buffers kept across calls (pinned host memory for a
+ * host consumer) avoid a per-call allocation and staging copy. */
+typedef struct {
+    double *vertices;       /* [cap_vertices][3] */
+    int32_t *triangles;     /* [cap_triangles][3] */
+    uint64_t *vertex_keys;  /* [cap_vertices] or NULL (not wanted) */
+    uint64_t *cube_keys;    /* [cap_cubes] or NULL (not wanted) */
+    int64_t cap_vertices, cap_triangles, cap_cubes;
+    int64_t n_vertices, n_triangles, n_cubes;   /* out: the mesh's sizes (also on GS_ERR_CAPACITY) */
+} gs_mesh_buffers;
+
+/*
+ * mesh_gaussian_surface_into -- mesh_gaussian_surface with the result copied
+ * into caller-owned buffers (layout and order as in gs_mesh).  On success the
+ * n_* fields hold the sizes.  When a buffer is smaller than the mesh the call
+ * writes nothing into the buffers, sets the n_* fields to the sizes needed
+ * and returns GS_ERR_CAPACITY; the caller may grow the buffers and call
+ * again.  Other errors as mesh_gaussian_surface; GS_ERR_ARG also for a
+ * negative capacity or a NULL vertices/triangles buffer with a positive
+ * capacity.
+ */
+int mesh_gaussian_surface_into(const double *atoms, const double *radii, int64_t n_atoms, double D, double c,
+                               double precision, int max_depth, const gs_options *opt, gs_mesh_buffers *out);
+
 /*
  * mesh_gaussian_surface_batch -- mesh n_mols independent molecules (the
  * method applies to each molecule on its own; the paper meshes one at a

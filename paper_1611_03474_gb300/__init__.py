@@ -11,10 +11,11 @@ from ._native import (GS_CHILD_REEXPAND, GS_CHILD_REPROJECT, GS_NORM_MAX, GS_NOR
                       GS_ORDER_LITERAL, GS_PREC_FP64, GS_PREC_MIXED, GsError, Mesh, Stats,
                       gs_bin_atoms, gs_bin_atoms_static, gs_cube_decisions, gs_eval_field, gs_mesh_backward,
                       gs_mesh_intersections, gs_triangulate_grid, gs_volume_area, library_path, load,
-                      mesh_gaussian_surface, mesh_gaussian_surface_batch)
+                      mesh_gaussian_surface, mesh_gaussian_surface_batch, mesh_gaussian_surface_into)
 
 __all__ = ["GS_CHILD_REEXPAND", "GS_CHILD_REPROJECT", "GS_NORM_MAX", "GS_NORM_RSS", "GS_NORM_SUM",
            "GS_ORDER_BOUNDS_FIRST", "GS_ORDER_LITERAL", "GS_PREC_FP64", "GS_PREC_MIXED", "GsError", "Mesh", "Stats",
            "gs_bin_atoms", "gs_bin_atoms_static", "gs_cube_decisions", "gs_eval_field", "gs_mesh_backward",
            "gs_mesh_intersections", "gs_triangulate_grid", "gs_volume_area", "library_path", "load",
-           "mesh_gaussian_surface", "mesh_gaussian_surface_batch"]
+           "mesh_gaussian_surface", "mesh_gaussian_surface_batch",
+           "mesh_gaussian_surface_into"]

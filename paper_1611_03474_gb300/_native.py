@@ -56,6 +56,13 @@ class Options(ctypes.Structure):
                 ("decision_order", ctypes.c_int), ("precision_norm", ctypes.c_int)]
 
 
+class MeshBuffers(ctypes.Structure):
+    _fields_ = [("vertices", ctypes.c_void_p), ("triangles", ctypes.c_void_p), ("vertex_keys", ctypes.c_void_p),
+                ("cube_keys", ctypes.c_void_p), ("cap_vertices", ctypes.c_int64), ("cap_triangles", ctypes.c_int64),
+                ("cap_cubes", ctypes.c_int64), ("n_vertices", ctypes.c_int64), ("n_triangles", ctypes.c_int64),
+                ("n_cubes", ctypes.c_int64)]
+
+
 class MeshC(ctypes.Structure):
     _fields_ = [("vertices", ctypes.POINTER(ctypes.c_double)), ("n_vertices", ctypes.c_int64),
                 ("triangles", ctypes.POINTER(ctypes.c_int32)), ("n_triangles", ctypes.c_int64),
@@ -81,6 +88,9 @@ def load():
     p, d, i64, i32 = ctypes.c_void_p, ctypes.c_double, ctypes.c_int64, ctypes.c_int
     L.mesh_gaussian_surface.argtypes = [p, p, i64, d, d, d, i32, ctypes.POINTER(Options), ctypes.POINTER(MeshC)]
     L.mesh_gaussian_surface.restype = i32
+    L.mesh_gaussian_surface_into.argtypes = [p, p, i64, d, d, d, i32, ctypes.POINTER(Options),
+                                             ctypes.POINTER(MeshBuffers)]
+    L.mesh_gaussian_surface_into.restype = i32
     L.mesh_free.argtypes = [ctypes.POINTER(MeshC)]
     L.mesh_free.restype = None
     L.gs_status_string.argtypes = [i32]
@@ -218,6 +228,43 @@ def mesh_gaussian_surface(atoms, radii, D, c, precision, max_depth, min_edge=0.2
         L.mesh_free(ctypes.byref(m))
         return res
     return _mesh_from_c(m, L, st, max_depth)
+
+
+def mesh_gaussian_surface_into(atoms, radii, D, c, precision, max_depth, vertices, triangles, vertex_keys=None,
+                               cube_keys=None, min_edge=0.25, precision_mode=GS_PREC_FP64, cutoff_rel=1e-8,
+                               stream=None, stats=False):
+    """Mesh {phi = c} into caller-owned buffers (torch tensors on the host,
+    pinned or not, or on the device, or numpy arrays): vertices float64
+    [cap, 3], triangles int32 [cap, 3], vertex_keys / cube_keys uint64 (or
+    int64) or None.  Returns (n_vertices, n_triangles, n_cubes), plus the
+    stats dict when stats=True.  Buffers too small raise GsError with code
+    GS_ERR_CAPACITY (-3) and the sizes needed in its .needed attribute."""
+    L = load()
+    atoms = _host64(atoms, (-1, 3))
+    radii = _host64(radii)
+    st = Stats()
+    o = L.gs_default_options()
+    o.min_edge = min_edge
+    o.precision_mode = precision_mode
+    o.cutoff_rel = cutoff_rel
+    o.cuda_stream = _stream_ptr(stream)
+    o.stats = ctypes.pointer(st)
+    b = MeshBuffers()
+    b.vertices, b.triangles = _ptr(vertices), _ptr(triangles)
+    b.vertex_keys, b.cube_keys = _ptr(vertex_keys), _ptr(cube_keys)
+    b.cap_vertices, b.cap_triangles = int(vertices.shape[0]), int(triangles.shape[0])
+    b.cap_cubes = int(cube_keys.shape[0]) if cube_keys is not None else 0
+    if vertex_keys is not None and int(vertex_keys.shape[0]) < b.cap_vertices:
+        b.cap_vertices = int(vertex_keys.shape[0])
+    rc = L.mesh_gaussian_surface_into(_ptr(atoms), _ptr(radii), atoms.shape[0], D, c, precision, max_depth,
+                                      ctypes.byref(o), ctypes.byref(b))
+    try:
+        _check(rc)
+    except GsError as e:
+        e.needed = (b.n_vertices, b.n_triangles, b.n_cubes)
+        raise
+    sizes = (b.n_vertices, b.n_triangles, b.n_cubes)
+    return (sizes + (st.as_dict(max_depth),)) if stats else sizes
 
 
 def gs_triangulate_grid(values, c, stream=None):

@@ -419,6 +419,27 @@ static int finish_output(MeshDev &M, const gs_options &o, gs_mesh *out, cudaStre
     return GS_OK;
 }
 
+// the mesh into caller-owned buffers (cudaMemcpyDefault: host or device)
+static int finish_into(MeshDev &M, gs_mesh_buffers *b, cudaStream_t st)
+{
+    b->n_vertices = M.nv;
+    b->n_triangles = M.nt;
+    b->n_cubes = M.nc;
+    if (M.nv > b->cap_vertices || M.nt > b->cap_triangles || (b->cube_keys && M.nc > b->cap_cubes))
+        return gs_fail(GS_ERR_CAPACITY, "output buffers too small: the mesh has %lld vertices, %lld triangles, %lld cubes",
+                       (long long)M.nv, (long long)M.nt, (long long)M.nc);
+    if (M.nv) {
+        GS_CHECK(cudaMemcpyAsync(b->vertices, M.vxyz, sizeof(double) * 3 * (size_t)M.nv, cudaMemcpyDefault, st));
+        if (b->vertex_keys)
+            GS_CHECK(cudaMemcpyAsync(b->vertex_keys, M.vkeys, sizeof(uint64_t) * (size_t)M.nv, cudaMemcpyDefault, st));
+    }
+    if (M.nt) GS_CHECK(cudaMemcpyAsync(b->triangles, M.tri, sizeof(int32_t) * 3 * (size_t)M.nt, cudaMemcpyDefault, st));
+    if (M.nc && b->cube_keys)
+        GS_CHECK(cudaMemcpyAsync(b->cube_keys, M.cubes, sizeof(uint64_t) * (size_t)M.nc, cudaMemcpyDefault, st));
+    GS_CHECK(cudaStreamSynchronize(st));
+    return GS_OK;
+}
+
 // triangulate the final cubes given lattice vertex values; shared by the
 // molecule path and the grid entry point
 static int surface_from_values(const GsProblem &P, const uint64_t *d_cubes, int64_t nc, const int32_t *d_cvid,
@@ -488,7 +509,8 @@ struct BackReq {
 static int put_out(void *dst, const void *src, size_t bytes, cudaStream_t st);
 
 static int mesh_impl(const double *atoms, const double *radii, int64_t n, double D, double c, double precision,
-                     int max_depth, const gs_options &o, gs_mesh *out, cudaStream_t st, const BackReq *bw = nullptr)
+                     int max_depth, const gs_options &o, gs_mesh *out, cudaStream_t st, const BackReq *bw = nullptr,
+                     gs_mesh_buffers *into = nullptr)
 {
     gs_stats local;
     gs_stats *stats = o.stats ? o.stats : &local;
@@ -664,7 +686,7 @@ static int mesh_impl(const double *atoms, const double *radii, int64_t n, double
         GS_CHECK(cudaStreamSynchronize(st));
     }
     if (out) {
-        rc = finish_output(M, o, out, st);
+        rc = into ? finish_into(M, into, st) : finish_output(M, o, out, st);
         if (rc) return rc;
     }
     int tend = T.mark();
@@ -752,6 +774,36 @@ extern "C" int mesh_gaussian_surface(const double *atoms, const double *radii, i
     if (own) cudaStreamDestroy(st);
     if (!rc && e != cudaSuccess) rc = gs_fail_cuda(e, "stream", __FILE__, __LINE__);
     if (rc) mesh_free(out);
+    return rc;
+}
+
+extern "C" int mesh_gaussian_surface_into(const double *atoms, const double *radii, int64_t n_atoms, double D,
+                                          double c, double precision, int max_depth, const gs_options *opt,
+                                          gs_mesh_buffers *out)
+{
+    if (!out) return gs_fail(GS_ERR_ARG, "out is NULL");
+    out->n_vertices = out->n_triangles = out->n_cubes = 0;
+    if (out->cap_vertices < 0 || out->cap_triangles < 0 || out->cap_cubes < 0 ||
+        (out->cap_vertices > 0 && !out->vertices) || (out->cap_triangles > 0 && !out->triangles))
+        return gs_fail(GS_ERR_ARG, "negative capacity or missing vertices/triangles buffer");
+    gs_options o = opt ? *opt : gs_default_options();
+    o.device_output = 1;   // the mesh stays on the device until it is copied into the buffers
+    int rc = check_mesh_args(atoms, radii, n_atoms, D, c, precision, max_depth, o);
+    if (rc) return rc;
+    rc = device_setup();
+    if (rc) return rc;
+    cudaStream_t st = (cudaStream_t)o.cuda_stream;
+    bool own = false;
+    if (!st) {
+        GS_CHECK(cudaStreamCreateWithFlags(&st, cudaStreamNonBlocking));
+        own = true;
+    }
+    gs_mesh unused;
+    memset(&unused, 0, sizeof(unused));
+    rc = mesh_impl(atoms, radii, n_atoms, D, c, precision, max_depth, o, &unused, st, nullptr, out);
+    cudaError_t e = cudaStreamSynchronize(st);
+    if (own) cudaStreamDestroy(st);
+    if (!rc && e != cudaSuccess) rc = gs_fail_cuda(e, "stream", __FILE__, __LINE__);
     return rc;
 }
 

@@ -29,7 +29,7 @@ def test_header_declares_the_boundary():
     for n in ("mesh_gaussian_surface", "mesh_free", "gs_status_string", "gs_last_error", "gs_bin_atoms",
               "gs_eval_field", "gs_cube_decisions", "gs_triangulate_grid", "gs_default_options",
               "gs_mesh_backward", "gs_volume_area", "mesh_gaussian_surface_batch",
-              "gs_mesh_intersections"):
+              "gs_mesh_intersections", "mesh_gaussian_surface_into"):
         assert n in names
 
 

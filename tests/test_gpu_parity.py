@@ -273,3 +273,36 @@ def test_mixed_form_range_guard():
         gs.gs_eval_field(xyz, r, D, 1.0, xyz, precision_mode=gs.GS_PREC_MIXED)
     m = gs.mesh_gaussian_surface(xyz, r, D, 1.0, 1e-3, 2, min_edge=1.0)
     check_closed_manifold(m.vertices, m.triangles)
+
+
+def test_mesh_into_caller_buffers(chain100):
+    """The caller-buffer entry point gives the library-allocated mesh bit for
+    bit, into pinned host and into device buffers; buffers too small raise
+    GS_ERR_CAPACITY with the sizes needed and receive nothing."""
+    torch = pytest.importorskip("torch")
+    cfg = chain100
+    args = (cfg["xyz"], cfg["r"], cfg["D"], cfg["c"], cfg["precision"], cfg["max_depth"])
+    ref = gs.mesh_gaussian_surface(*args, min_edge=cfg["min_edge"], precision_mode=gs.GS_PREC_MIXED)
+    nv, nt, nc = len(ref.vertices), len(ref.triangles), len(ref.cube_keys)
+    for dev in ("cpu", "cuda"):
+        pin = dev == "cpu"
+        V = torch.full((nv + 5, 3), -1.0, dtype=torch.float64, device=dev)
+        T = torch.full((nt + 5, 3), -1, dtype=torch.int32, device=dev)
+        K = torch.zeros(nv + 5, dtype=torch.int64, device=dev)
+        C = torch.zeros(nc, dtype=torch.int64, device=dev)
+        if pin:
+            V, T, K, C = V.pin_memory(), T.pin_memory(), K.pin_memory(), C.pin_memory()
+        sizes = gs.mesh_gaussian_surface_into(*args, V, T, K, C, min_edge=cfg["min_edge"],
+                                              precision_mode=gs.GS_PREC_MIXED)
+        assert sizes == (nv, nt, nc)
+        assert np.array_equal(V[:nv].cpu().numpy(), ref.vertices)
+        assert np.array_equal(T[:nt].cpu().numpy(), ref.triangles)
+        assert np.array_equal(K[:nv].cpu().numpy().view(np.uint64), ref.vertex_keys)
+        assert np.array_equal(C.cpu().numpy().view(np.uint64), ref.cube_keys)
+        assert (V[nv:] == -1.0).all() and (T[nt:] == -1).all()
+    small = torch.full((nv - 1, 3), -1.0, dtype=torch.float64)
+    tri = torch.zeros((nt, 3), dtype=torch.int32)
+    with pytest.raises(gs.GsError) as e:
+        gs.mesh_gaussian_surface_into(*args, small, tri, min_edge=cfg["min_edge"])
+    assert e.value.code == -3 and e.value.needed[:2] == (nv, nt)
+    assert (small == -1.0).all()
