@@ -705,6 +705,70 @@ __global__ void __launch_bounds__(128) k_fold_table(TriCtx X, uint8_t *__restric
     *reinterpret_cast<uint32_t *>(fcount + ci * 4) = cnt;
 }
 
+// The same table in two passes: an FP32 screen over every cube lists the
+// (cube, axis) pairs whose fold roots may exist and zeroes every count; the
+// FP64 solver then runs over the list in full warps (a warp of the one-pass
+// kernel runs the solver whenever any of its cubes needs it).  List entry:
+// cube << 2 | axis.
+__global__ void __launch_bounds__(256) k_fold_screen(TriCtx X, uint8_t *__restrict__ fcount,
+                                                     uint32_t *__restrict__ list, unsigned *nlist)
+{
+    const int64_t ci = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    unsigned need = 0;
+    if (ci < X.ncubes) {
+        int sg = 0;
+        float gc[8];
+        for (int v = 0; v < 8; v++) {
+            const double g = X.phi[X.cvid[ci * 8 + v]];
+            sg |= (g >= X.c ? 1 : 0) << v;
+            gc[v] = (float)(g - X.c);
+        }
+        if (sg != 0 && sg != 0xFF)
+            for (int a = 0; a < 3; a++)
+                if (fold_faces_straddle(sg, a) && fold_may_have_roots(gc, a)) need |= 1u << a;
+        *reinterpret_cast<uint32_t *>(fcount + ci * 4) = 0u;
+    }
+    const unsigned lane = threadIdx.x & 31;
+    const unsigned cntv = (unsigned)__popc(need);
+    unsigned incl = cntv;
+    for (int o = 1; o < 32; o <<= 1) {
+        const unsigned t = __shfl_up_sync(0xffffffffu, incl, o);
+        if (lane >= (unsigned)o) incl += t;
+    }
+    const unsigned tot = __shfl_sync(0xffffffffu, incl, 31);
+    if (tot == 0) return;
+    unsigned base = 0;
+    if (lane == 31) base = atomicAdd(nlist, tot);
+    base = __shfl_sync(0xffffffffu, base, 31);
+    unsigned pos = base + incl - cntv;
+    for (int a = 0; a < 3; a++)
+        if ((need >> a) & 1u) list[pos++] = ((uint32_t)ci << 2) | (uint32_t)a;
+}
+
+__global__ void __launch_bounds__(128) k_fold_solve(TriCtx X, const uint32_t *__restrict__ list,
+                                                    const unsigned *__restrict__ nlist, uint8_t *__restrict__ fcount,
+                                                    double *__restrict__ froot)
+{
+    const int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (t >= (int64_t)*nlist) return;
+    const uint32_t e = list[t];
+    const int64_t ci = (int64_t)(e >> 2);
+    const int a = (int)(e & 3u);
+    double g[8];
+    int sg = 0;
+    for (int v = 0; v < 8; v++) {
+        g[v] = X.phi[X.cvid[ci * 8 + v]];
+        sg |= (g[v] >= X.c ? 1 : 0) << v;
+    }
+    double ru[2], rv[2];
+    const int nr = fold_solve(g, a, X.c, ru, rv, 0.0, sg);
+    fcount[ci * 4 + a] = (uint8_t)nr;
+    for (int r = 0; r < nr; r++) {
+        froot[ci * 12 + 4 * a + 2 * r] = ru[r];
+        froot[ci * 12 + 4 * a + 2 * r + 1] = rv[r];
+    }
+}
+
 // first pass: trace every cube, count its output and stage it when it fits
 // Cube classes for the tracing order: cubes of one class take the same
 // branches (crossing edges, fold roots), so warps diverge less.  Class
@@ -882,7 +946,21 @@ int gs_triangulate(const TriCtx &X0, uint64_t **d_tri_keys, int64_t *ntri_total,
         gs_free(fcount, st); gs_free(froot, st);
         fcount = nullptr; froot = nullptr;
     } else {
-        GS_LAUNCH(k_fold_table, nb, 128, 0, st)(X, fcount, froot);
+        uint32_t *flist = nullptr;
+        unsigned *nflist = nullptr;
+        const bool screened = n < ((int64_t)1 << 30) &&
+                              cudaMallocAsync((void **)&flist, sizeof(uint32_t) * 3 * (size_t)n, st) == cudaSuccess &&
+                              cudaMallocAsync((void **)&nflist, sizeof(unsigned), st) == cudaSuccess;
+        if (screened) {
+            cudaMemsetAsync(nflist, 0, sizeof(unsigned), st);
+            GS_LAUNCH(k_fold_screen, (unsigned)((n + 255) / 256), 256, 0, st)(X, fcount, flist, nflist);
+            GS_LAUNCH(k_fold_solve, (unsigned)((3 * n + 127) / 128), 128, 0, st)(X, flist, nflist, fcount, froot);
+        } else {
+            cudaGetLastError();
+            GS_LAUNCH(k_fold_table, nb, 128, 0, st)(X, fcount, froot);
+        }
+        gs_free(flist, st);
+        gs_free(nflist, st);
         X.fcount = fcount;
         X.froot = froot;
     }
