@@ -809,6 +809,36 @@ __device__ __forceinline__ int decide(const T *b, T c, T precision, int level, i
     return DEC_SPLIT;
 }
 
+// P~ at the 8 cube corners: L_n(+-1) = (+-1)^n, so each corner value is a
+// signed sum of the coefficients; lo and hi receive the smallest and largest
+template <typename T>
+__device__ __forceinline__ void corner_range(const T *a, T &lo, T &hi)
+{
+    lo = T(3.0e38);
+    hi = T(-3.0e38);
+#pragma unroll
+    for (int sx = 0; sx < 2; sx++) {
+        T bx[16];
+#pragma unroll
+        for (int kl = 0; kl < 16; kl++) {
+            const T e = a[kl] + a[32 + kl], o = a[16 + kl] + a[48 + kl];
+            bx[kl] = sx ? e + o : e - o;
+        }
+#pragma unroll
+        for (int sy = 0; sy < 2; sy++) {
+            T cz[4];
+#pragma unroll
+            for (int l = 0; l < 4; l++) {
+                const T e = bx[l] + bx[8 + l], o = bx[4 + l] + bx[12 + l];
+                cz[l] = sy ? e + o : e - o;
+            }
+            const T e = cz[0] + cz[2], o = cz[1] + cz[3];
+            lo = fmin(lo, fmin(e - o, e + o));
+            hi = fmax(hi, fmax(e - o, e + o));
+        }
+    }
+}
+
 // Literal order of steps 2 and 3: a child whose higher-order coefficients
 // meet the bound is accepted before its bounds are tested; a root cube that
 // passes the bound test is divided.
@@ -864,10 +894,70 @@ __global__ void __launch_bounds__(128) k_estimate_f64(GsProblem P, int level, co
         for (int t = 0; t < 6; t++) bounds[q * 6 + t] = b[t];
 }
 
+// FP64 first pass (default decision order and norm, no bounds wanted):
+// invalid cubes and cubes whose corner values of P~ straddle c by more than
+// the rounding of those sums (1e-12 sum|A|) are decided here; the FP64 bounds
+// enclose P~ up to rounding, so the SVD estimate would keep them too, and
+// the precision sum is taken in the same order as there.  The rest go to a
+// list for the SVD estimate.
+__global__ void __launch_bounds__(256) k_estimate_pre64(GsProblem P, int level, const double *__restrict__ A, int64_t n,
+                                                        const uint64_t *parents, const uint8_t *vmask,
+                                                        uint8_t *__restrict__ dec, int32_t *__restrict__ list,
+                                                        unsigned *nlist)
+{
+    const int64_t q = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    bool slow = false;
+    if (q < n) {
+        Octet oc = octet_of(P, level, parents, vmask, q >> 3);
+        if (!((oc.vmask >> (q & 7)) & 1)) {
+            dec[q] = DEC_INVALID;
+        } else {
+            double a[64];
+            double tot = 0.0, high = 0.0;
+#pragma unroll
+            for (int t = 0; t < 64; t++) {
+                a[t] = A[q * 64 + t];
+                tot += fabs(a[t]);
+                if ((t >> 4) >= 2 || ((t >> 2) & 3) >= 2 || (t & 3) >= 2) high += fabs(a[t]);
+            }
+            double lo, hi;
+            corner_range<double>(a, lo, hi);
+            const double cm = 1e-12 * tot;
+            if (hi - P.c > cm && P.c - lo > cm)
+                dec[q] = (uint8_t)(high <= P.precision ? DEC_ACCEPT : (level >= P.max_depth ? DEC_FORCED : DEC_SPLIT));
+            else
+                slow = true;
+        }
+    }
+    const unsigned bal = __ballot_sync(0xffffffffu, slow);
+    if (!bal) return;
+    const unsigned lane = threadIdx.x & 31;
+    unsigned wb = 0;
+    if (lane == 0) wb = atomicAdd(nlist, (unsigned)__popc(bal));
+    wb = __shfl_sync(0xffffffffu, wb, 0);
+    if (slow) list[wb + __popc(bal & ((1u << lane) - 1u))] = (int32_t)q;
+}
+
 int gs_estimate_f64(const GsProblem &P, int level, const double *d_A, int64_t n_cubes, const uint64_t *d_parents,
                     const uint8_t *d_vmask, uint8_t *d_dec, double *d_bounds, cudaStream_t st)
 {
     if (n_cubes <= 0) return GS_OK;
+    if (!d_bounds && P.order == GS_ORDER_BOUNDS_FIRST && P.norm == GS_NORM_SUM && n_cubes < ((int64_t)1 << 31)) {
+        int32_t *list = nullptr;
+        unsigned *nlist = nullptr;
+        int rc = gs_alloc((void **)&list, sizeof(int32_t) * (size_t)n_cubes, st);
+        if (!rc) rc = gs_alloc((void **)&nlist, sizeof(unsigned), st);
+        if (rc) { gs_free(list, st); return rc; }
+        GS_CHECK(cudaMemsetAsync(nlist, 0, sizeof(unsigned), st));
+        GS_LAUNCH(k_estimate_pre64, (unsigned)((n_cubes + 255) / 256), 256, 0, st)(P, level, d_A, n_cubes, d_parents,
+                                                                                d_vmask, d_dec, list, nlist);
+        GS_LAUNCH(k_estimate_f64, (unsigned)((n_cubes + 127) / 128), 128, 0, st)(P, level, d_A, n_cubes, d_parents,
+                                                                         d_vmask, d_dec, nullptr, list, nlist);
+        gs_free(list, st);
+        gs_free(nlist, st);
+        GS_CHECK(cudaGetLastError());
+        return GS_OK;
+    }
     GS_LAUNCH(k_estimate_f64, (unsigned)((n_cubes + 127) / 128), 128, 0, st)(P, level, d_A, n_cubes, d_parents, d_vmask,
                                                                      d_dec, d_bounds, nullptr, nullptr);
     GS_CHECK(cudaGetLastError());
@@ -1391,34 +1481,6 @@ __device__ __forceinline__ void load_tensor_f32(const float *__restrict__ src, f
     }
 }
 
-// P~ at the 8 cube corners: L_n(+-1) = (+-1)^n, so each corner value is a
-// signed sum of the coefficients; lo and hi receive the smallest and largest
-__device__ __forceinline__ void corner_range(const float *a, float &lo, float &hi)
-{
-    lo = 3.0e38f;
-    hi = -3.0e38f;
-#pragma unroll
-    for (int sx = 0; sx < 2; sx++) {
-        float bx[16];
-#pragma unroll
-        for (int kl = 0; kl < 16; kl++) {
-            const float e = a[kl] + a[32 + kl], o = a[16 + kl] + a[48 + kl];
-            bx[kl] = sx ? e + o : e - o;
-        }
-#pragma unroll
-        for (int sy = 0; sy < 2; sy++) {
-            float cz[4];
-#pragma unroll
-            for (int l = 0; l < 4; l++) {
-                const float e = bx[l] + bx[8 + l], o = bx[4 + l] + bx[12 + l];
-                cz[l] = sy ? e + o : e - o;
-            }
-            const float e = cz[0] + cz[2], o = cz[1] + cz[3];
-            lo = fminf(lo, fminf(e - o, e + o));
-            hi = fmaxf(hi, fmaxf(e - o, e + o));
-        }
-    }
-}
 
 // Cubes whose corner values of P~ straddle c by more than the FP32 error of
 // those sums are kept by the FP64 estimate whatever its SVD gives: L <= min P~
@@ -1444,7 +1506,7 @@ __device__ __forceinline__ bool estimate_fast_f32(const GsProblem &P, int level,
     const float c = (float)P.c, prec = (float)P.precision;
     const float dA = MIXED_KAPPA * E[q] + 1e-7f * tot;
     float lo, hi;
-    corner_range(a, lo, hi);
+    corner_range<float>(a, lo, hi);
     // each corner sum moves by at most sum|dA_t| <= 64 dA, plus its own FP32
     // rounding (6 additions deep, < 4e-7 sum|A|)
     const float cm = 64.f * dA + 4e-6f * tot;
