@@ -599,9 +599,13 @@ static int mesh_impl(const double *atoms, const double *radii, int64_t n, double
     }
     int tl1 = T.mark();
 
-    // ---- conformity across faces and edges (section 2.3, neighbouring cubes)
+    // ---- conformity across faces and edges (section 2.3, neighbouring cubes):
+    // a cube is split only next to a finer one, so with every accepted cube
+    // on one level there is nothing to do
     int64_t splits = 0;
-    rc = gs_conformity(&cubes, &nc, max_depth, &splits, d_status, st);
+    int acc_levels = 0;
+    for (int l = 0; l <= max_depth; l++) acc_levels += (stats->accepted[l] + stats->forced[l]) > 0 ? 1 : 0;
+    if (acc_levels > 1) rc = gs_conformity(&cubes, &nc, max_depth, &splits, d_status, st);
     B.keep(cubes);
     if (rc) return rc;
     int tc1 = T.mark();

@@ -147,26 +147,26 @@ __device__ __forceinline__ uint64_t corner_key(uint64_t ck, int v, int max_depth
     return gk_make((gk_x(ck) + (v & 1)) * s, (gk_y(ck) + ((v >> 1) & 1)) * s, (gk_z(ck) + (v >> 2)) * s, GT_VERT, 0);
 }
 
-__global__ void k_vert_claim(GsHash H, const uint64_t *cubes, int64_t n, int max_depth, unsigned *status)
+// every corner claims its key's slot (the smallest corner index wins) and
+// keeps the slot, so the later passes index the table without probing it
+__global__ void k_vert_claim(GsHash H, const uint64_t *cubes, int64_t n, int max_depth, int64_t *slot,
+                             unsigned *status)
 {
     int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (t >= n * 8) return;
     uint64_t key = corner_key(cubes[t >> 3], (int)(t & 7), max_depth);
     int64_t s = gs_hash_insert(H, key, status);
+    slot[t] = s;
     if (s >= 0) atomicMin((unsigned long long *)&H.vals[s], (unsigned long long)t);
 }
 
-// owner flag per corner, and the corner's hash slot (kept so that the later
-// passes index the table directly instead of probing it again)
-__global__ void k_vert_owner(GsHash H, const uint64_t *cubes, int64_t n, int max_depth, int64_t *flag,
-                             int64_t *slot, unsigned *status)
+// owner flag per corner (the corner that won its slot)
+__global__ void k_vert_owner(GsHash H, int64_t n, int64_t *flag, const int64_t *slot, unsigned *status)
 {
     int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (t >= n * 8) return;
-    uint64_t key = corner_key(cubes[t >> 3], (int)(t & 7), max_depth);
-    int64_t s = gs_hash_find(H, key);
+    const int64_t s = slot[t];
     if (s < 0) atomicOr(status, GS_ST_LOOKUP);
-    slot[t] = s;
     flag[t] = (s >= 0 && H.vals[s] == (uint64_t)t) ? 1 : 0;
 }
 
@@ -204,9 +204,9 @@ int gs_lattice_vertices(const uint64_t *d_cubes, int64_t n, int max_depth, uint6
     if (!rc) rc = gs_alloc((void **)&slot_id, sizeof(uint64_t) * (size_t)(H.mask + 1), st);
     unsigned nb = (unsigned)((m + 255) / 256);
     if (!rc) {
-        GS_LAUNCH(k_vert_claim, nb, 256, 0, st)(H, d_cubes, n, max_depth, d_status);
+        GS_LAUNCH(k_vert_claim, nb, 256, 0, st)(H, d_cubes, n, max_depth, slot, d_status);
         cudaMemsetAsync(flag + m, 0, sizeof(int64_t), st);
-        GS_LAUNCH(k_vert_owner, nb, 256, 0, st)(H, d_cubes, n, max_depth, flag, slot, d_status);
+        GS_LAUNCH(k_vert_owner, nb, 256, 0, st)(H, n, flag, slot, d_status);
         rc = gs_scan_i64(flag, m + 1, tot, st);
     }
     int64_t total = 0;
