@@ -264,19 +264,21 @@ int gs_neighbours(const uint64_t *d_cubes, int64_t n, int32_t **d_nbr, unsigned 
 }
 
 // ---------------------------------------------------------------- weld
-__global__ void k_weld_claim(GsHash H, const uint64_t *pk, int64_t n, unsigned *status)
+// every point claims its key's slot (the smallest point index wins) and
+// keeps the slot for the owner and write passes
+__global__ void k_weld_claim(GsHash H, const uint64_t *pk, int64_t n, int64_t *slot, unsigned *status)
 {
     int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (t >= n) return;
     int64_t s = gs_hash_insert(H, pk[t], status);
+    slot[t] = s;
     if (s >= 0) atomicMin((unsigned long long *)&H.vals[s], (unsigned long long)t);
 }
-__global__ void k_weld_owner(GsHash H, const uint64_t *pk, int64_t n, int64_t *flag, int64_t *slot)
+__global__ void k_weld_owner(GsHash H, int64_t n, int64_t *flag, const int64_t *slot)
 {
     int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (t >= n) return;
-    int64_t s = gs_hash_find(H, pk[t]);
-    slot[t] = s;
+    const int64_t s = slot[t];
     flag[t] = (s >= 0 && H.vals[s] == (uint64_t)t) ? 1 : 0;
 }
 __global__ void k_weld_write(const uint64_t *pk, const double *pxyz, int64_t n, const int64_t *off, const int64_t *slot,
@@ -318,9 +320,9 @@ int gs_weld(const uint64_t *d_pk, const double *d_pxyz, int64_t npt, const uint6
     if (!rc) rc = gs_alloc((void **)&slot_id, sizeof(uint64_t) * (size_t)(H.mask + 1), st);
     unsigned nb = (unsigned)((npt + 255) / 256);
     if (!rc) {
-        GS_LAUNCH(k_weld_claim, nb, 256, 0, st)(H, d_pk, npt, d_status);
+        GS_LAUNCH(k_weld_claim, nb, 256, 0, st)(H, d_pk, npt, slot, d_status);
         cudaMemsetAsync(flag + npt, 0, sizeof(int64_t), st);
-        GS_LAUNCH(k_weld_owner, nb, 256, 0, st)(H, d_pk, npt, flag, slot);
+        GS_LAUNCH(k_weld_owner, nb, 256, 0, st)(H, npt, flag, slot);
         rc = gs_scan_i64(flag, npt + 1, tot, st);
     }
     int64_t total = 0;
