@@ -52,6 +52,10 @@ PEAK_FP64 = SM_COUNT * 2 * 2 * SM_MHZ * 1e6
 # algorithmic work of one (cube, atom) term of the tensor accumulation:
 # the rank-one update of the 4x4x4 tensor (64 FMA) and its 16 y-z products
 FLOPS_PER_PAIR = 64 * 2 + 16
+# DRAM bytes per cube of k_accum_f32: 394.7 MB for the 1,723,336 cubes of one
+# launch in the ncu capture on the 20,000-atom molecule (writes of the 256 B
+# tensor and 4 B bound per cube; atoms and cell list stay in L2)
+ACCUM_F32_DRAM_BYTES_PER_CUBE = 394.7e6 / 1723336
 
 
 def dist_env():
@@ -425,9 +429,15 @@ def main():
     fp32 = mode == gs.GS_PREC_MIXED and st.get("recheck_cubes", 0) >= 0 and args.mode == "mixed"
     peak = PEAK_FP32 if fp32 else PEAK_FP64
     achieved = pairs * FLOPS_PER_PAIR / (acc_ms * 1e-3) if acc_ms > 0 else 0.0
+    # DRAM traffic per launch: bytes per accumulated cube from the ncu capture
+    # of the FP32 kernel on the 20,000-atom molecule (the kernel writes each
+    # cube's tensor and bound and reads almost nothing), times the cubes one
+    # launch accumulates here
+    traffic = (ACCUM_F32_DRAM_BYTES_PER_CUBE * sum(st["examined"]) / launches) if fp32 else None
     roofline = {"bound": "alu", "kernel": "k_accum_f32" if fp32 else "k_accum_f64",
                 "achieved": achieved / 1e12, "peak": peak / 1e12, "unit": "TFLOP/s", "frac": achieved / peak,
-                "traffic": None, "launches_per_step": launches, "ms_per_launch": acc_ms / launches,
+                "traffic": traffic, "traffic_unit": "bytes per launch",
+                "launches_per_step": launches, "ms_per_launch": acc_ms / launches,
                 "peak_source": "152 SMs x 2070 MHz x (%s) FMA/SM/clk x 2 (unit counts and clocks)"
                                % ("128 FP32" if fp32 else "2 FP64")}
     evals = pairs + st["vertex_terms"]
