@@ -62,3 +62,37 @@ def test_argument_errors_without_gpu(lib):
     with pytest.raises(gs.GsError) as e:
         gs.mesh_gaussian_surface(np.zeros((1, 3)), np.ones(1), 0.5, 1.0, 1e-3, 21)
     assert e.value.code == -1
+
+
+def test_option_and_buffer_errors_without_gpu(lib):
+    """Argument errors of the mesh entry points are found on the host, before
+    any device work: unknown readings, readings outside the FP64 form, and
+    malformed caller-owned buffers all return GS_ERR_ARG (-1)."""
+    import numpy as np
+    import paper_1611_03474_gb300 as gs
+    from paper_1611_03474_gb300 import _native as nat
+    xyz, r = np.zeros((1, 3)), np.ones(1)
+    bad = [dict(child_mode=5), dict(decision_order=3), dict(precision_norm=9),
+           dict(child_mode=gs.GS_CHILD_REEXPAND, precision_mode=gs.GS_PREC_MIXED),
+           dict(decision_order=gs.GS_ORDER_LITERAL, precision_mode=gs.GS_PREC_MIXED),
+           dict(precision_norm=gs.GS_NORM_RSS, precision_mode=gs.GS_PREC_MIXED),
+           dict(min_edge=0.0), dict(cutoff_rel=1.5)]
+    for kw in bad:
+        with pytest.raises(gs.GsError) as e:
+            gs.mesh_gaussian_surface(xyz, r, 0.5, 1.0, 1e-3, 2, **kw)
+        assert e.value.code == -1, kw
+    for args in ((xyz, r, 0.0, 1.0, 1e-3, 2), (xyz, r, 0.5, 1.0, 1e-3, 21), (xyz, r, 0.5, -1.0, 1e-3, 2)):
+        with pytest.raises(gs.GsError) as e:
+            gs.mesh_gaussian_surface(*args)
+        assert e.value.code == -1
+    L = nat.load()
+    opt = L.gs_default_options()
+    for caps, ptrs in (((-1, 4, 0), (True, True)), ((4, 4, 0), (False, True)), ((4, 4, 0), (True, False))):
+        b = nat.MeshBuffers()
+        V, T = np.zeros((4, 3)), np.zeros((4, 3), np.int32)
+        b.vertices = V.ctypes.data if ptrs[0] else None
+        b.triangles = T.ctypes.data if ptrs[1] else None
+        b.cap_vertices, b.cap_triangles, b.cap_cubes = caps
+        rc = L.mesh_gaussian_surface_into(nat._ptr(xyz), nat._ptr(r), 1, 0.5, 1.0, 1e-3, 2, ctypes.byref(opt),
+                                          ctypes.byref(b))
+        assert rc == -1 and (b.n_vertices, b.n_triangles, b.n_cubes) == (0, 0, 0)
