@@ -148,16 +148,28 @@ __device__ __forceinline__ uint64_t corner_key(uint64_t ck, int v, int max_depth
 }
 
 // every corner claims its key's slot (the smallest corner index wins) and
-// keeps the slot, so the later passes index the table without probing it
+// keeps the slot, so the later passes index the table without probing it.
+// A warp holds the corners of 4 consecutive cubes (usually children of one
+// octet), many of them shared: lanes with equal keys insert once, through
+// their lowest lane, which also has the group's smallest corner index.
 __global__ void k_vert_claim(GsHash H, const uint64_t *cubes, int64_t n, int max_depth, int64_t *slot,
                              unsigned *status)
 {
-    int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    if (t >= n * 8) return;
-    uint64_t key = corner_key(cubes[t >> 3], (int)(t & 7), max_depth);
-    int64_t s = gs_hash_insert(H, key, status);
-    slot[t] = s;
-    if (s >= 0) atomicMin((unsigned long long *)&H.vals[s], (unsigned long long)t);
+    const int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    const bool valid = t < n * 8;
+    const unsigned lane = threadIdx.x & 31;
+    // corner keys have level 0 (top bits clear): a lane past the end takes a
+    // key no corner has, so it matches only itself
+    const uint64_t key = valid ? corner_key(cubes[t >> 3], (int)(t & 7), max_depth) : ((1ull << 63) | lane);
+    const unsigned grp = __match_any_sync(0xffffffffu, (unsigned long long)key);
+    const int leader = __ffs(grp) - 1;
+    long long s = -1;
+    if (valid && (int)lane == leader) {
+        s = gs_hash_insert(H, key, status);
+        if (s >= 0) atomicMin((unsigned long long *)&H.vals[s], (unsigned long long)t);
+    }
+    s = __shfl_sync(0xffffffffu, s, leader);
+    if (valid) slot[t] = (int64_t)s;
 }
 
 // owner flag per corner (the corner that won its slot)
