@@ -474,3 +474,17 @@ def test_literal_order_mesh_closed():
     b = oracle.mesh(*args, order=1)
     check_closed_manifold(b["vertices"], b["triangles"])
     assert sum(b["stats"]["accepted"][1:]) >= sum(a["stats"]["accepted"][1:])
+
+
+def test_child_reexpansion_composes_over_levels():
+    """Re-expanding to child c1 and then to its child c2 gives the parent's
+    polynomial on that grandchild box, t_parent = ((t + s2)/2 + s1)/2."""
+    rng = np.random.default_rng(77)
+    A = rng.standard_normal((4, 4, 4))
+    t = rng.uniform(-1, 1, (300, 3))
+    for c1, c2 in ((0, 7), (5, 2), (3, 3)):
+        B = oracle.child_reexpand(oracle.child_reexpand(A, c1), c2)
+        s1 = np.array([1.0 if (c1 >> a) & 1 else -1.0 for a in range(3)])
+        s2 = np.array([1.0 if (c2 >> a) & 1 else -1.0 for a in range(3)])
+        ref = _ptilde(A, ((t + s2) / 2 + s1) / 2)
+        assert np.abs(_ptilde(B, t) - ref).max() < 1e-13 * np.abs(A).sum()
