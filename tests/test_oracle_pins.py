@@ -488,3 +488,40 @@ def test_child_reexpansion_composes_over_levels():
         s2 = np.array([1.0 if (c2 >> a) & 1 else -1.0 for a in range(3)])
         ref = _ptilde(A, ((t + s2) / 2 + s1) / 2)
         assert np.abs(_ptilde(B, t) - ref).max() < 1e-13 * np.abs(A).sum()
+
+
+def test_corner_straddle_implies_keep():
+    """The first passes of the estimate rest on the bounds enclosing P~: a cube
+    whose corner values of P~ (L_n(+-1) = (+-1)^n, so signed coefficient
+    sums) straddle c has L <= min corner and max corner <= U, so the bound
+    test keeps it.  Checked on the oracle's tensors, bounds and decisions for
+    cubes of every level around the chain."""
+    cfg = synth.config("chain100")
+    rng = np.random.default_rng(5)
+    o, nroot, pad = oracle.root_grid(cfg["xyz"], cfg["r"], cfg["D"], cfg["c"], cfg["min_edge"], cfg["max_depth"])
+    keys = []
+    for l in range(cfg["max_depth"] + 1):
+        h = cfg["min_edge"] * 2 ** (cfg["max_depth"] - l)
+        centres = cfg["xyz"][rng.integers(0, len(cfg["r"]), 400)] + rng.normal(0, 1.5, (400, 3))
+        idx = np.clip(np.floor((centres - o) / h).astype(np.int64), 0, (nroot << l) - 1)
+        keys += [int(x) | (int(y) << 18) | (int(z) << 36) | (30 << 54) | (l << 59) for x, y, z in idx]
+    keys = np.unique(np.array(keys, dtype=np.uint64))
+    A, b, d = oracle.cube_batch(cfg["xyz"], cfg["r"], cfg["D"], cfg["c"], cfg["precision"], cfg["min_edge"],
+                                cfg["max_depth"], keys)
+    s = np.array([[1.0 if (v >> a) & 1 else -1.0 for a in range(3)] for v in range(8)])
+    j = np.arange(4)
+    corners = np.einsum("qjkl,vj,vk,vl->qv", A.reshape(-1, 4, 4, 4), s[:, :1] ** j, s[:, 1:2] ** j, s[:, 2:] ** j)
+    lo, hi = corners.min(1), corners.max(1)
+    tot = np.abs(A).sum(1)
+    straddle = (hi - cfg["c"] > 1e-12 * tot) & (cfg["c"] - lo > 1e-12 * tot)
+    assert straddle.sum() > 100 and (~straddle).sum() > 100
+    assert np.all(d[straddle] != 0)                                   # never discarded
+    assert np.all(b[straddle, 0] <= lo[straddle] + 1e-12 * tot[straddle])
+    assert np.all(hi[straddle] <= b[straddle, 1] + 1e-12 * tot[straddle])
+    # and the decision is the one the first passes take without the SVD
+    t = np.arange(64)
+    high_mask = ((t >> 4) >= 2) | (((t >> 2) & 3) >= 2) | ((t & 3) >= 2)
+    high = np.abs(A[:, high_mask]).sum(1)
+    level = (keys >> np.uint64(59)).astype(int)
+    expect = np.where(high <= cfg["precision"], 1, np.where(level >= cfg["max_depth"], 3, 2))
+    assert np.array_equal(d[straddle], expect[straddle])
