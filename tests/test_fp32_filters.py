@@ -5,6 +5,8 @@ operations (one rounding each) reproduce their arithmetic.
 - Orientation (ear clipping, section 2.3): when the FP32 value of
   (b-a)_i (c-a)_j - (b-a)_j (c-a)_i clears its bound, its sign is the FP64
   predicate's.
+- Fold-root screen: the FP32 screen of a fold quadratic answers "no root"
+  only where the FP64 solver finds none.
 - Newell normal of a piece (its projection axis): every FP32 component lies
   within n (1e-6 + 1.5e-7 n) of the FP64 one, so the axis and sign chosen
   when the largest leads by twice that are the FP64 choice."""
@@ -78,3 +80,116 @@ def test_newell_normal_fp32_bound(seed):
                   (pd[0] - qd[0]) * (pd[1] + qd[1])]
         errM = n * (1e-6 + 1.5e-7 * n)
         assert np.all(np.abs(M.astype(np.float64) - N) <= errM)
+
+
+def _faces(g, a):
+    ua, va = (1, 2) if a == 0 else ((0, 2) if a == 1 else (0, 1))
+    lo, up = [], []
+    for k in range(4):
+        b = [0, 0, 0]
+        b[ua], b[va] = k & 1, k >> 1
+        b[a] = 0
+        lo.append(g[b[0] + 2 * b[1] + 4 * b[2]])
+        b[a] = 1
+        up.append(g[b[0] + 2 * b[1] + 4 * b[2]])
+    return lo, up
+
+
+def _coeffs(lo, up, c, T):
+    lo = [T(x) for x in lo]
+    up = [T(x) for x in up]
+    p0 = T(lo[0] - c) if c is not None else lo[0]
+    p1, p2 = T(lo[1] - lo[0]), T(lo[2] - lo[0])
+    p3 = T(T(T(lo[3] - lo[1]) - lo[2]) + lo[0])
+    d = [T(up[k] - lo[k]) for k in range(4)]
+    q0, q1, q2 = d[0], T(d[1] - d[0]), T(d[2] - d[0])
+    q3 = T(T(T(d[3] - d[1]) - d[2]) + d[0])
+    A2 = T(T(p1 * q3) - T(p3 * q1))
+    A1 = T(T(T(T(p0 * q3) + T(p1 * q2)) - T(p2 * q1)) - T(p3 * q0))
+    A0 = T(T(p0 * q2) - T(p2 * q0))
+    return (p0, p1, p2, p3), (q0, q1, q2, q3), (A2, A1, A0)
+
+
+def screen32(g, c, a):
+    gc = [f32(x - c) for x in g]
+    lo, up = _faces(gc, a)
+    (p0, p1, p2, p3), (q0, q1, q2, q3), (A2, A1, A0) = _coeffs(lo, up, None, f32)
+    terms = [p1 * q3, p3 * q1, p0 * q3, p1 * q2, p2 * q1, p3 * q0, p0 * q2, p2 * q0]
+    mag = f32(0)
+    for t in terms:
+        mag = f32(mag + abs(f32(t)))
+    if not mag > 1e-30:
+        return True
+    if abs(A2) <= f32(1e-3) * mag:
+        return True
+    disc = f32(f32(A1 * A1) - f32(f32(f32(4) * A2) * A0))
+    scale = f32(f32(A1 * A1) + f32(4) * abs(f32(A2 * A0)))
+    if disc < f32(-1e-3) * scale:
+        return False
+    if disc <= f32(1e-3) * scale:
+        return True
+    sq = np.sqrt(disc, dtype=f32)
+    w = f32(f32(-0.5) * f32(A1 + sq)) if A1 >= 0 else f32(f32(-0.5) * f32(A1 - sq))
+    if w == 0:
+        return True
+    u1, u2 = f32(w / A2), f32(A0 / w)
+    return (-0.01 < u1 < 1.01) or (-0.01 < u2 < 1.01)
+
+
+def solve64_has_root(g, c, a):
+    """The FP64 fold solver's root test (roots u, v in [0,1] satisfying both
+    fold equations), restated in numpy."""
+    lo, up = _faces(g, a)
+    (p0, p1, p2, p3), (q0, q1, q2, q3), (A2, A1, A0) = _coeffs(lo, up, c, np.float64)
+    if q0 == q1 == q2 == q3 == 0:
+        return False
+    us = []
+    if A2 == 0:
+        if A1 != 0:
+            us.append(-A0 / A1)
+    else:
+        disc = A1 * A1 - 4 * A2 * A0
+        if disc >= 0:
+            sq = np.sqrt(disc)
+            w = -0.5 * (A1 + sq) if A1 >= 0 else -0.5 * (A1 - sq)
+            us += [w / A2, A0 / w] if w != 0 else [0.0]
+    sp, sq_ = abs(p0) + abs(p1) + abs(p2) + abs(p3), abs(q0) + abs(q1) + abs(q2) + abs(q3)
+    for u in us:
+        if not (0 < u < 1):
+            continue
+        for num, den in ((q0 + q1 * u, q2 + q3 * u), (p0 + p1 * u, p2 + p3 * u)):
+            if den == 0:
+                continue
+            v = -num / den
+            if 0 < v < 1 and abs(p0 + p1 * u + p2 * v + p3 * u * v) <= 1e-9 * sp and \
+                    abs(q0 + q1 * u + q2 * v + q3 * u * v) <= 1e-9 * sq_:
+                return True
+    return False
+
+
+@pytest.mark.parametrize("seed", range(3))
+def test_fold_screen_never_misses_a_root(seed):
+    """The FP32 screen answers 'no root' only where the FP64 solver finds
+    none: random corner values, corner values differing by 1e-6 of their
+    size, and cubes built around a fold root of chosen position."""
+    rng = np.random.default_rng(200 + seed)
+    c, found = 1.0, 0
+    for k in range(6000):
+        kind = k % 3
+        if kind == 0:
+            g = c + rng.uniform(-1, 1, 8)
+        elif kind == 1:
+            g = c + 1e-6 * rng.uniform(-1, 1, 8) * 10 ** rng.uniform(-2, 2)
+        else:
+            # g = A(u,v) + s B(u,v) with B = (u - u0)(...) style zero near (u0, v0)
+            u0, v0, s0 = rng.random(3)
+            g = np.empty(8)
+            cu, cv, cs = rng.standard_normal(3)
+            for v in range(8):
+                x, y, z = v & 1, (v >> 1) & 1, v >> 2
+                g[v] = c + cu * (x - u0) + cv * (y - v0) * (z - s0) * rng.uniform(0.5, 2) + cs * (x - u0) * (y - v0)
+        for a in range(3):
+            if solve64_has_root(g, c, a):
+                found += 1
+                assert screen32(g, c, a), (g.tolist(), a)
+    assert found > 100
