@@ -9,7 +9,10 @@ operations (one rounding each) reproduce their arithmetic.
   only where the FP64 solver finds none.
 - Newell normal of a piece (its projection axis): every FP32 component lies
   within n (1e-6 + 1.5e-7 n) of the FP64 one, so the axis and sign chosen
-  when the largest leads by twice that are the FP64 choice."""
+  when the largest leads by twice that are the FP64 choice.
+- The estimate's FP32 first pass (additions only, so no contraction can
+  apply): its corner values of P~ lie within 64 dA + 4e-6 sum|A| of the
+  FP64 ones."""
 import numpy as np
 import pytest
 
@@ -193,3 +196,43 @@ def test_fold_screen_never_misses_a_root(seed):
                 found += 1
                 assert screen32(g, c, a), (g.tolist(), a)
     assert found > 100
+
+
+def _corner_range(a, T):
+    """Corner values of P~ as the estimate's first pass sums them
+    (x pairs, then y pairs, then z pairs), in type T."""
+    a = [T(x) for x in a]
+    lo, hi = None, None
+    for sx in (0, 1):
+        bx = []
+        for kl in range(16):
+            e, o = T(a[kl] + a[32 + kl]), T(a[16 + kl] + a[48 + kl])
+            bx.append(T(e + o) if sx else T(e - o))
+        for sy in (0, 1):
+            cz = []
+            for l in range(4):
+                e, o = T(bx[l] + bx[8 + l]), T(bx[4 + l] + bx[12 + l])
+                cz.append(T(e + o) if sy else T(e - o))
+            e, o = T(cz[0] + cz[2]), T(cz[1] + cz[3])
+            for v in (T(e - o), T(e + o)):
+                lo = v if lo is None else min(lo, v)
+                hi = v if hi is None else max(hi, v)
+    return lo, hi
+
+
+@pytest.mark.parametrize("seed", range(3))
+def test_corner_sums_within_the_first_pass_margin(seed):
+    """The FP32 first pass keeps a cube when its FP32 corner values straddle
+    c by 64 dA + 4e-6 sum|A|: with every FP32 entry within dA of the FP64
+    one, the FP32 corner range lies within that margin of the FP64 range."""
+    rng = np.random.default_rng(300 + seed)
+    for _ in range(3000):
+        A = rng.standard_normal(64) * np.exp(-rng.uniform(0, 6, 64))
+        tot = np.abs(A).sum()
+        dA = 1.6e-6 * tot * rng.uniform(0.01, 1)
+        A32 = (A + rng.uniform(-1, 1, 64) * dA).astype(f32)   # entries off by <= dA (+ their rounding)
+        dA_eff = dA + 6e-8 * np.abs(A).max()
+        lo32, hi32 = _corner_range(A32, f32)
+        lo64, hi64 = _corner_range(A, np.float64)
+        m = 64 * dA_eff + 4e-6 * tot
+        assert abs(float(lo32) - lo64) <= m and abs(float(hi32) - hi64) <= m
