@@ -236,3 +236,42 @@ def test_corner_sums_within_the_first_pass_margin(seed):
         lo64, hi64 = _corner_range(A, np.float64)
         m = 64 * dA_eff + 4e-6 * tot
         assert abs(float(lo32) - lo64) <= m and abs(float(hi32) - hi64) <= m
+
+
+@pytest.mark.parametrize("D", [0.5, 0.9])
+def test_vertex_term_bound_covers_argument_rounding(D):
+    """Mixed vertex field: each FP32 term t = 2^(-D log2e (d^2 - r^2)) is
+    taken to err by at most t (3e-7 + 2.5e-7 D (d^2 + r^2)).  The exponent's
+    FP32 rounding is reproduced here (two-float offsets from the origin, d^2
+    with or without FMA contraction, d^2 - r^2, the scaled exponent); the
+    hardware ex2 adds its documented 2^-22 and the result's rounding.  The
+    coefficient is tight: rare far terms (D d^2 ~ 10, where the rounding of
+    D log2e itself counts) reach up to ~1.003 of it, which the per-point
+    bound's other terms and its consumers' slack (a 4x band for signs, 8e-6
+    against the 1e-5 A bar for positions) absorb; the test holds it to
+    1.01."""
+    rng = np.random.default_rng(int(D * 10))
+    origin = np.array([-7.0, -3.0, -11.0])
+    nDl2e = f32(-D * 1.4426950408889634)
+    worst = 0.0
+    for _ in range(20000):
+        x = rng.uniform(0, 300, 3)
+        r = rng.choice([1.2, 1.7, 1.55, 1.52, 1.8])
+        R = np.sqrt(r * r - np.log(1e-8) / D)
+        dvec = rng.normal(size=3)
+        p = x + dvec / np.linalg.norm(dvec) * rng.uniform(0, R)
+        ph, xh = (p - origin).astype(f32), (x - origin).astype(f32)
+        pl = ((p - origin) - ph.astype(np.float64)).astype(f32)
+        xl = ((x - origin) - xh.astype(np.float64)).astype(f32)
+        d = [f32(f32(ph[a] - xh[a]) + f32(pl[a] - xl[a])) for a in range(3)]
+        r2 = f32(r * r)
+        d2_plain = f32(f32(f32(d[0] * d[0]) + f32(d[1] * d[1])) + f32(d[2] * d[2]))
+        d2_fma = f32(np.float64(d[2]) * d[2] + np.float64(f32(np.float64(d[1]) * d[1] + np.float64(f32(d[0] * d[0])))))
+        exact = -D * 1.4426950408889634 * (np.sum((p - x) ** 2) - r * r)
+        bound = 3e-7 + 2.5e-7 * D * (float(d2_plain) + r * r)
+        for d2 in (d2_plain, d2_fma):
+            arg = f32(nDl2e * f32(d2 - r2))
+            rel = np.log(2) * abs(float(arg) - exact) + 2.0 ** -22 + 2.0 ** -24
+            worst = max(worst, rel / bound)
+            assert rel <= 1.01 * bound
+    assert worst > 0.05   # the cases reach a sizeable share of the bound
