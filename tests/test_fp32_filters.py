@@ -10,6 +10,8 @@ operations (one rounding each) reproduce their arithmetic.
 - Newell normal of a piece (its projection axis): every FP32 component lies
   within n (1e-6 + 1.5e-7 n) of the FP64 one, so the axis and sign chosen
   when the largest leads by twice that are the FP64 choice.
+- Edge-point marks of the mixed vertex field: the first-order criterion
+  that leaves an edge point to FP32 keeps it within the 1e-5 A bar.
 - The estimate's FP32 first pass (additions only, so no contraction can
   apply): its corner values of P~ lie within 64 dA + 4e-6 sum|A| of the
   FP64 ones."""
@@ -275,3 +277,29 @@ def test_vertex_term_bound_covers_argument_rounding(D):
             worst = max(worst, rel / bound)
             assert rel <= 1.01 * bound
     assert worst > 0.05   # the cases reach a sizeable share of the bound
+
+
+def test_edge_point_mark_criterion_is_sound():
+    """Mixed vertex marks: an edge point t = (c - g0)/(g1 - g0) is left to FP32
+    when h ((1 - t) e0 + t e1) / |g1 - g0|, inflated by 1%, is at most
+    8e-6 A (e0, e1 the corners' error bounds).  Then the point moves by less
+    than the 1e-5 A bar for any corner errors within the bounds: the exact
+    worst case over the four sign combinations of the errors is checked."""
+    rng = np.random.default_rng(17)
+    h, c, tol = 0.25, 1.0, 8e-6
+    checked = 0
+    for _ in range(200000):
+        g0 = c - 10 ** rng.uniform(-7, 0)
+        g1 = c + 10 ** rng.uniform(-7, 0)
+        if rng.random() < 0.5:
+            g0, g1 = g1, g0
+        e0, e1 = (10 ** rng.uniform(-9, -5, 2))
+        t = (c - g0) / (g1 - g0)
+        first = 1.01 * h * ((1 - t) * e0 + t * e1) / abs(g1 - g0)
+        if first > tol or max(e0, e1) >= abs(g1 - g0) / 2:
+            continue
+        checked += 1
+        moves = [abs((c - (g0 + s0 * e0)) / ((g1 + s1 * e1) - (g0 + s0 * e0)) - t) * h
+                 for s0 in (-1, 1) for s1 in (-1, 1)]
+        assert max(moves) < 1e-5
+    assert checked > 20000
