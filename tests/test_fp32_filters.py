@@ -10,8 +10,8 @@ operations (one rounding each) reproduce their arithmetic.
 - Newell normal of a piece (its projection axis): every FP32 component lies
   within n (1e-6 + 1.5e-7 n) of the FP64 one, so the axis and sign chosen
   when the largest leads by twice that are the FP64 choice.
-- Edge-point marks of the mixed vertex field: the first-order criterion
-  that leaves an edge point to FP32 keeps it within the 1e-5 A bar.
+- Edge-point and fold-root marks of the mixed vertex field: the first-order
+  criteria that leave a surface point to FP32 keep it within the 1e-5 A bar.
 - The estimate's FP32 first pass (additions only, so no contraction can
   apply): its corner values of P~ lie within 64 dA + 4e-6 sum|A| of the
   FP64 ones."""
@@ -303,3 +303,72 @@ def test_edge_point_mark_criterion_is_sound():
                  for s0 in (-1, 1) for s1 in (-1, 1)]
         assert max(moves) < 1e-5
     assert checked > 20000
+
+
+def _fold_roots64(g, c, a):
+    """(u, v) fold roots of axis a in the open face square, FP64."""
+    lo, up = _faces(g, a)
+    (p0, p1, p2, p3), (q0, q1, q2, q3), (A2, A1, A0) = _coeffs(lo, up, c, np.float64)
+    us = []
+    if A2 == 0:
+        if A1 != 0:
+            us.append(-A0 / A1)
+    else:
+        disc = A1 * A1 - 4 * A2 * A0
+        if disc >= 0:
+            sq = np.sqrt(disc)
+            w = -0.5 * (A1 + sq) if A1 >= 0 else -0.5 * (A1 - sq)
+            us += [w / A2, A0 / w] if w != 0 else [0.0]
+    out = []
+    for u in us:
+        if not 0 < u < 1:
+            continue
+        denB, denA = q2 + q3 * u, p2 + p3 * u
+        den, num = (denB, q0 + q1 * u) if abs(denB) >= abs(denA) else (denA, p0 + p1 * u)
+        if den != 0 and 0 < -num / den < 1:
+            out.append((u, -num / den))
+    return out, (p0, p1, p2, p3), (q0, q1, q2, q3), (A2, A1, A0)
+
+
+def test_fold_root_mark_criterion_is_sound():
+    """Mixed vertex marks for fold roots: when the first-order bound
+    h (|du| + |dv|) from J^-1 of the corner errors (inflated 1%) is within
+    8e-6 A, the root is at least 4 error radii inside the face square and not
+    a near-double root, corner errors within their bounds move the root by
+    less than 1e-5 A (checked over random sign patterns, root re-solved in
+    FP64)."""
+    rng = np.random.default_rng(23)
+    h, c, tol, a = 0.25, 1.0, 8e-6, 0
+    checked = 0
+    for _ in range(4000):
+        g = c + rng.uniform(-1, 1, 8) * 10 ** rng.uniform(-2, 0)
+        roots, (p0, p1, p2, p3), (q0, q1, q2, q3), (A2, A1, A0) = _fold_roots64(g, c, a)
+        if not roots:
+            continue
+        scale = A1 * A1 + 4 * abs(A2 * A0)
+        if A2 != 0 and abs(A1 * A1 - 4 * A2 * A0) <= 1e-4 * scale:
+            continue   # near-double root: every corner goes to FP64
+        e = 10 ** rng.uniform(-10, -6, 8)
+        lo_i = [0, 2, 4, 6]   # axis 0: corner index of (u, v) = (y, z) on the x = 0 face
+        up_i = [1, 3, 5, 7]
+        for u, v in roots:
+            w4 = [(1 - u) * (1 - v), u * (1 - v), (1 - u) * v, u * v]
+            J11, J12, J21, J22 = p1 + p3 * v, p2 + p3 * u, q1 + q3 * v, q2 + q3 * u
+            det = abs(J11 * J22 - J12 * J21)
+            if det == 0:
+                continue
+            bu = bv = 0.0
+            for q in range(4):
+                slo, sup = 1.01 * w4[q] * e[lo_i[q]], 1.01 * w4[q] * e[up_i[q]]
+                bu += ((abs(J22) + abs(J12)) * slo + abs(J12) * sup) / det
+                bv += ((abs(J21) + abs(J11)) * slo + abs(J11) * sup) / det
+            if h * (bu + bv) > tol or min(u, 1 - u) <= 4 * bu + 1e-5 or min(v, 1 - v) <= 4 * bv + 1e-5:
+                continue
+            checked += 1
+            for _ in range(24):
+                gp = g + rng.choice([-1.0, 1.0], 8) * e
+                rp, *_ = _fold_roots64(gp, c, a)
+                assert rp, "the root vanished"
+                move = min(np.hypot(up_ - u, vp - v) for up_, vp in rp) * h
+                assert move < 1e-5
+    assert checked > 300
