@@ -11,7 +11,8 @@ operations (one rounding each) reproduce their arithmetic.
   within n (1e-6 + 1.5e-7 n) of the FP64 one, so the axis and sign chosen
   when the largest leads by twice that are the FP64 choice.
 - Edge-point and fold-root marks of the mixed vertex field: the first-order
-  criteria that leave a surface point to FP32 keep it within the 1e-5 A bar.
+  criteria that leave a surface point to FP32 keep it within the 1e-5 A bar;
+  the face-saddle criterion keeps the saddle decision.
 - The estimate's FP32 first pass (additions only, so no contraction can
   apply): its corner values of P~ lie within 64 dA + 4e-6 sum|A| of the
   FP64 ones."""
@@ -372,3 +373,30 @@ def test_fold_root_mark_criterion_is_sound():
                 move = min(np.hypot(up_ - u, vp - v) for up_, vp in rp) * h
                 assert move < 1e-5
     assert checked > 300
+
+
+def test_face_saddle_mark_criterion_is_sound():
+    """Mixed vertex marks for diagonal faces: when |h_s - c| exceeds
+    4 amp sum(e), amp = 2 sum|h| / |h0 - h1 - h2 + h3|, the saddle decision
+    h_s < c is the same for every set of corner errors within e (corner
+    signs themselves are settled by the first recheck round)."""
+    rng = np.random.default_rng(29)
+    c, checked = 1.0, 0
+    for _ in range(100000):
+        s = rng.choice([-1.0, 1.0])
+        h = c + s * np.array([1, -1, -1, 1]) * 10 ** rng.uniform(-6, 0, 4)   # diagonal pattern
+        e = 10 ** rng.uniform(-10, -5, 4)
+        if np.any(np.abs(h - c) <= 2 * e):
+            continue
+        den = h[0] - h[1] - h[2] + h[3]
+        hs = (h[0] * h[3] - h[1] * h[2]) / den
+        amp = 2 * np.abs(h).sum() / abs(den)
+        if abs(hs - c) <= 4 * amp * e.sum():
+            continue
+        checked += 1
+        for _ in range(8):
+            hp = h + rng.choice([-1.0, 1.0], 4) * e
+            denp = hp[0] - hp[1] - hp[2] + hp[3]
+            hsp = (hp[0] * hp[3] - hp[1] * hp[2]) / denp
+            assert (hsp < c) == (hs < c)
+    assert checked > 20000
