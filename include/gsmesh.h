@@ -113,7 +113,9 @@ typedef struct {
     double cutoff_rel;      /* default 1e-8 */
     void *cuda_stream;      /* cudaStream_t or NULL */
     int device_output;      /* 1: out arrays stay on the device (free with mesh_free) */
-    int debug_flags;        /* bit 0: mixed mode also runs FP64 on every cube and counts disagreements */
+    int debug_flags;        /* bit 0: mixed mode also runs FP64 on every cube and counts disagreements;
+                               bit 1: process each level in chunks of 1000 parent octets (instead of 2^21),
+                               so that small inputs take the multi-chunk path of large ones */
     gs_stats *stats;        /* nullable: filled on success */
     int child_mode;         /* child tensors: GS_CHILD_REPROJECT (default: projected from the atoms on each
                                child box) or GS_CHILD_REEXPAND (the parent's polynomial re-expanded on the

@@ -21,6 +21,27 @@
 #include <stdint.h>
 #include <stdlib.h>
 #include <string.h>
+#ifdef _OPENMP
+#include <omp.h>
+#endif
+
+/* Threads: the loops over cubes and points run in parallel when built with
+ * OpenMP.  Every cube's and point's result depends on that cube or point
+ * alone, and results are collected in input order, so the output does not
+ * depend on the thread count. */
+static int g_threads = 0; /* 0: OpenMP's default */
+int or_set_threads(int n)
+{
+    g_threads = n < 0 ? 0 : n;
+#ifdef _OPENMP
+    return g_threads ? g_threads : omp_get_max_threads();
+#else
+    return 1;
+#endif
+}
+#ifdef _OPENMP
+#define OR_NT (g_threads ? g_threads : omp_get_max_threads())
+#endif
 
 /* ------------------------------------------------------------------ */
 /* Key format (shared *format*, not code, with the CUDA library):      */
@@ -89,6 +110,7 @@ typedef struct {
 /* Terms exp(-D(|x-xi|^2 - ri^2)) below cutoff_rel*c are dropped:
  *   term >= cutoff_rel*c  <=>  |x-xi|^2 <= ri^2 + K/D,  K = -ln(cutoff_rel*c). */
 static double cut_K(double cutoff_rel, double c) { return -log(cutoff_rel * c); }
+static void gl_init(void);
 
 static int oprob_init(oprob *P, int64_t n, const double *xyz, const double *r, double D, double c,
                       double cutoff_rel, double precision, double min_edge, int max_depth)
@@ -97,6 +119,7 @@ static int oprob_init(oprob *P, int64_t n, const double *xyz, const double *r, d
         max_depth > 20 || !(cutoff_rel > 0) || !(cutoff_rel < 1))
         return OR_ERR_ARG;
     memset(P, 0, sizeof(*P));
+    gl_init(); /* before any parallel loop reads the nodes */
     P->n = n; P->xyz = xyz; P->r = r; P->D = D; P->c = c; P->cutoff_rel = cutoff_rel;
     P->precision = precision; P->min_edge = min_edge; P->max_depth = max_depth;
     P->R2 = (double *)malloc(sizeof(double) * (size_t)n);
@@ -654,47 +677,73 @@ static int partition(const oprob *P, vec64 *accepted, ostats *st, uint8_t *dec_l
      * cubes of the previous level, in the order of cur) */
     double *curA = NULL, *nxtA = NULL;
     int64_t nxt_cap = 0;
+    int e = OR_OK;
     for (int l = 0; l <= P->max_depth && cur.n > 0; l++) {
         st->examined[l] = cur.n;
         nxt.n = 0;
+        /* each cube's tensor and decision depend on that cube alone: computed
+         * in parallel, then taken in order */
+        uint8_t *dec = (uint8_t *)malloc((size_t)cur.n);
+        double *marg = (double *)malloc(sizeof(double) * (size_t)cur.n);
+        int64_t *pairs = (int64_t *)malloc(sizeof(int64_t) * (size_t)cur.n);
+        double *keepA = P->child_mode == 1 ? (double *)malloc(sizeof(double) * 64 * (size_t)cur.n) : NULL;
+        if (!dec || !marg || !pairs || (P->child_mode == 1 && !keepA)) {
+            free(dec); free(marg); free(pairs); free(keepA);
+            e = OR_ERR_OOM;
+            break;
+        }
+#ifdef _OPENMP
+#pragma omp parallel for schedule(dynamic, 64) num_threads(OR_NT)
+#endif
         for (int64_t q = 0; q < cur.n; q++) {
             double lo[3], hi[3], A[64], o6[6];
             cube_box(P, cur.a[q], lo, hi);
+            pairs[q] = 0;
             if (P->child_mode == 1 && l > 0) memcpy(A, curA + 64 * q, sizeof(A));
-            else st->pair_terms += cube_tensor(P, lo, hi, A);
+            else pairs[q] = cube_tensor(P, lo, hi, A);
             int d = or_decide_ex(A, P->c, P->precision, l, P->max_depth, P->order, P->norm, o6);
+            double mg = INFINITY;
             if (o6[4] > 0) {
                 double scale = fabs(P->c) + fabs(o6[0]) + fabs(o6[1]);
-                double mg = fmin(fabs(P->c - o6[0]), fabs(o6[1] - P->c)) / scale;
+                mg = fmin(fabs(P->c - o6[0]), fabs(o6[1] - P->c)) / scale;
                 if (d != DEC_DISCARD) mg = fmin(mg, fabs(P->precision - o6[3]) / (P->precision + o6[3]));
-                if (mg < st->min_margin) st->min_margin = mg;
             }
+            dec[q] = (uint8_t)d;
+            marg[q] = mg;
+            if (keepA) memcpy(keepA + 64 * q, A, sizeof(A));
+        }
+        for (int64_t q = 0; q < cur.n && !e; q++) {
+            int d = dec[q];
+            st->pair_terms += pairs[q];
+            if (marg[q] < st->min_margin) st->min_margin = marg[q];
             if (d == DEC_DISCARD) { st->discarded[l]++; continue; }
             if (d == DEC_ACCEPT || d == DEC_FORCED) {
                 if (d == DEC_ACCEPT) st->accepted[l]++; else st->forced[l]++;
-                if (v_push(accepted, cur.a[q])) return OR_ERR_OOM;
+                if (v_push(accepted, cur.a[q])) e = OR_ERR_OOM;
                 continue;
             }
             st->split[l]++;
             int64_t x, y, zz;
             okey_xyz(cur.a[q], &x, &y, &zz);
-            for (int c8 = 0; c8 < 8; c8++) {
+            for (int c8 = 0; c8 < 8 && !e; c8++) {
                 if (v_push(&nxt, okey((uint64_t)(2 * x + (c8 & 1)), (uint64_t)(2 * y + ((c8 >> 1) & 1)),
                                       (uint64_t)(2 * zz + ((c8 >> 2) & 1)), T_CUBE, (unsigned)(l + 1)))) {
-                    free(curA); free(nxtA);
-                    return OR_ERR_OOM;
+                    e = OR_ERR_OOM;
+                    break;
                 }
                 if (P->child_mode == 1) {
                     if (nxt.n > nxt_cap) {
                         nxt_cap = 2 * nxt.n + 64;
                         double *g = (double *)realloc(nxtA, sizeof(double) * 64 * (size_t)nxt_cap);
-                        if (!g) { free(curA); free(nxtA); return OR_ERR_OOM; }
+                        if (!g) { e = OR_ERR_OOM; break; }
                         nxtA = g;
                     }
-                    or_child_reexpand(A, c8, nxtA + 64 * (nxt.n - 1));
+                    or_child_reexpand(keepA + 64 * q, c8, nxtA + 64 * (nxt.n - 1));
                 }
             }
         }
+        free(dec); free(marg); free(pairs); free(keepA);
+        if (e) break;
         vec64 t = cur; cur = nxt; nxt = t;
         free(curA);
         curA = nxtA;
@@ -703,7 +752,7 @@ static int partition(const oprob *P, vec64 *accepted, ostats *st, uint8_t *dec_l
     }
     free(cur.a); free(nxt.a);
     free(curA); free(nxtA);
-    return OR_OK;
+    return e;
 }
 
 /* ================================================================== */
@@ -1351,6 +1400,63 @@ static int triangulate_cube(const omesh_ctx *M, uint64_t ckey, vtri *tris, vvert
     return OR_OK;
 }
 
+/* Triangulate every listed cube.  Cubes are independent (each reads only the
+ * shared, read-only field and cube set), so blocks of cubes run in parallel
+ * into their own buffers, which are then appended in cube order with the
+ * piece numbers offset: the result is that of the sequential loop. */
+static int triangulate_all(const omesh_ctx *M, const uint64_t *cubes, int64_t n, vtri *tris, vvert *verts,
+                           ostats *st)
+{
+    const int64_t BS = 2048;
+    int64_t nb = (n + BS - 1) / BS;
+    if (nb == 0) return OR_OK;
+    vtri *bt = (vtri *)calloc((size_t)nb, sizeof(vtri));
+    vvert *bv = (vvert *)calloc((size_t)nb, sizeof(vvert));
+    ostats *bs = (ostats *)calloc((size_t)nb, sizeof(ostats));
+    int *be = (int *)calloc((size_t)nb, sizeof(int));
+    if (!bt || !bv || !bs || !be) { free(bt); free(bv); free(bs); free(be); return OR_ERR_OOM; }
+#ifdef _OPENMP
+#pragma omp parallel for schedule(dynamic, 1) num_threads(OR_NT)
+#endif
+    for (int64_t b = 0; b < nb; b++) {
+        int64_t i1 = (b + 1) * BS < n ? (b + 1) * BS : n;
+        for (int64_t i = b * BS; i < i1 && !be[b]; i++) be[b] = triangulate_cube(M, cubes[i], &bt[b], &bv[b], &bs[b]);
+    }
+    int e = OR_OK;
+    for (int64_t b = 0; b < nb; b++) {
+        if (be[b] && !e) e = be[b];
+        st->n_cubes_surface += bs[b].n_cubes_surface;
+        st->degenerate_ears += bs[b].degenerate_ears;
+        st->loop_errors += bs[b].loop_errors;
+        for (int64_t i = 0; i < bt[b].n && !e; i++) {
+            otri *t = &bt[b].t[i];
+            if (t_push(tris, t->k[0], t->k[1], t->k[2])) { e = OR_ERR_OOM; break; }
+            tris->t[tris->n - 1].piece = t->piece + tris->piece;
+        }
+        tris->piece += bt[b].piece;
+        for (int64_t i = 0; i < bv[b].n && !e; i++)
+            if (p_push(verts, bv[b].p[i].key, bv[b].p[i].x)) e = OR_ERR_OOM;
+        free(bt[b].t);
+        free(bv[b].p);
+    }
+    free(bt); free(bv); free(bs); free(be);
+    return e;
+}
+
+/* phi at lattice-vertex keys (finest lattice), one point at a time */
+static void lattice_field(const oprob *P, const uint64_t *vk, int64_t n, double *vphi)
+{
+#ifdef _OPENMP
+#pragma omp parallel for schedule(dynamic, 256) num_threads(OR_NT)
+#endif
+    for (int64_t i = 0; i < n; i++) {
+        int64_t x, y, z;
+        okey_xyz(vk[i], &x, &y, &z);
+        double p[3] = {lat_x(P, 0, x, P->max_depth), lat_x(P, 1, y, P->max_depth), lat_x(P, 2, z, P->max_depth)};
+        vphi[i] = phi_at(P, p, NULL);
+    }
+}
+
 static int cmp_vert(const void *a, const void *b)
 {
     uint64_t x = ((const overt *)a)->key, y = ((const overt *)b)->key;
@@ -1399,6 +1505,9 @@ int or_field(int64_t n, const double *xyz, const double *r, double D, double c, 
     oprob P;
     int e = oprob_init(&P, n, xyz, r, D, c, cutoff_rel, 1.0, 1.0, 0);
     if (e) return e;
+#ifdef _OPENMP
+#pragma omp parallel for schedule(dynamic, 256) num_threads(OR_NT)
+#endif
     for (int64_t i = 0; i < npts; i++) phi[i] = phi_at(&P, pts + 3 * i, grad ? grad + 3 * i : NULL);
     oprob_free(&P);
     return OR_OK;
@@ -1424,6 +1533,9 @@ int or_cube_batch(int64_t n, const double *xyz, const double *r, double D, doubl
     oprob P;
     int e = oprob_init(&P, n, xyz, r, D, c, cutoff_rel, precision, min_edge, max_depth);
     if (e) return e;
+#ifdef _OPENMP
+#pragma omp parallel for schedule(dynamic, 16) num_threads(OR_NT)
+#endif
     for (int64_t q = 0; q < ncubes; q++) {
         double lo[3], hi[3], A[64], o6[6];
         cube_box(&P, keys[q], lo, hi);
@@ -1476,12 +1588,8 @@ int or_mesh_ex(int64_t n, const double *xyz, const double *r, double D, double c
         }
         vk.n = sort_unique(vk.a, vk.n);
         double *vphi = (double *)malloc(sizeof(double) * (size_t)(vk.n ? vk.n : 1));
-        for (int64_t i = 0; i < vk.n; i++) {
-            int64_t x, y, z;
-            okey_xyz(vk.a[i], &x, &y, &z);
-            double p[3] = {lat_x(&P, 0, x, max_depth), lat_x(&P, 1, y, max_depth), lat_x(&P, 2, z, max_depth)};
-            vphi[i] = phi_at(&P, p, NULL);
-        }
+        if (!vphi) { free(vk.a); e = OR_ERR_OOM; goto done; }
+        lattice_field(&P, vk.a, vk.n, vphi);
         st->n_vertices_lattice = vk.n;
         out->n_lattice = vk.n;
         out->lattice_keys = vk.a;
@@ -1489,10 +1597,8 @@ int or_mesh_ex(int64_t n, const double *xyz, const double *r, double D, double c
         omesh_ctx M = {&P, acc.a, acc.n, vk.a, vphi, vk.n};
         vtri tris = {0};
         vvert verts = {0};
-        for (int64_t i = 0; i < acc.n; i++) {
-            e = triangulate_cube(&M, acc.a[i], &tris, &verts, st);
-            if (e) goto done;
-        }
+        e = triangulate_all(&M, acc.a, acc.n, &tris, &verts, st);
+        if (e) { free(tris.t); free(verts.p); goto done; }
         /* weld: unique keys (sorted), triangles remapped to indices */
         if (verts.n) qsort(verts.p, (size_t)verts.n, sizeof(overt), cmp_vert);
         int64_t m = 0;
@@ -1589,8 +1695,7 @@ int or_mesh_grid(int64_t nx, int64_t ny, int64_t nz, const double *values, doubl
     omesh_ctx M = {&P, cubes, nc, vk, vp, nv};
     vtri tris = {0};
     vvert verts = {0};
-    int e = OR_OK;
-    for (int64_t i = 0; i < nc && !e; i++) e = triangulate_cube(&M, cubes[i], &tris, &verts, &out->st);
+    int e = triangulate_all(&M, cubes, nc, &tris, &verts, &out->st);
     if (!e) {
         if (verts.n) qsort(verts.p, (size_t)verts.n, sizeof(overt), cmp_vert);
         int64_t m = 0;

@@ -299,10 +299,12 @@ static int run_level(const GsProblem &P, int level, const uint64_t *d_parents, i
                      uint64_t **d_next, int64_t *n_next, unsigned long long *d_counters, unsigned long long *d_pairs,
                      unsigned long long *d_rechecked, unsigned long long *d_mism, bool both, unsigned *d_status,
                      gs_stats *stats, bool reexpand = false, const double *d_parA = nullptr,
-                     double **d_nextA = nullptr)
+                     double **d_nextA = nullptr, bool small_chunks = false)
 {
     cudaStream_t st = B.st;
-    const int64_t CH = 1 << 21;  // octets per chunk (8 GB of FP64 tensors)
+    // octets per chunk (8 GB of FP64 tensors); debug: 1000, so that small
+    // inputs run the multi-chunk path
+    const int64_t CH = small_chunks ? 1000 : ((int64_t)1 << 21);
     std::vector<uint64_t *> nexts;
     std::vector<double *> nextAs;
     std::vector<int64_t> ncnt;
@@ -560,7 +562,7 @@ static int mesh_impl(const double *atoms, const double *radii, int64_t n, double
         double *nextA = nullptr;
         rc = run_level(P, l, parents, n_oct, o.precision_mode, B, parts, cnts, &next, &nn, d_cnt, d_cnt + 8,
                        d_cnt + 13, d_cnt + 14, (o.debug_flags & 1) != 0, d_status, stats, reexpand, parentA,
-                       reexpand ? &nextA : nullptr);
+                       reexpand ? &nextA : nullptr, (o.debug_flags & 2) != 0);
         if (parentA) B.release(parentA);
         parentA = nextA;
         if (parentA) B.keep(parentA);

@@ -166,3 +166,88 @@ def surface_loss_grad(vertices, triangles, W):
         a, b = v[t[:, (k + 1) % 3]], v[t[:, (k + 2) % 3]]
         np.add.at(g, t[:, k], np.cross(a, b) / 6.0 + 0.5 * np.cross(nh, b - a))
     return g
+
+
+# ---------------------------------------------------------------- windows
+TYPE_CUBE = 30
+
+
+def key_shift(keys, shift, max_depth):
+    """Keys of a sub-problem moved to the full problem's lattice: shift is the
+    difference of the two root origins in finest-lattice units (a multiple of
+    2^max_depth).  Cube keys hold coordinates at their own level, point keys
+    finest-lattice coordinates."""
+    k = np.asarray(keys, dtype=np.uint64).astype(np.int64)
+    x, y, z = k & 0x3FFFF, (k >> 18) & 0x3FFFF, (k >> 36) & 0x3FFFF
+    typ, lvl = (k >> 54) & 31, (k >> 59) & 31
+    sh = np.where(typ == TYPE_CUBE, max_depth - lvl, 0)
+    x = x + (shift[0] >> sh)
+    y = y + (shift[1] >> sh)
+    z = z + (shift[2] >> sh)
+    assert (x < (1 << 18)).all() and (y < (1 << 18)).all() and (z < (1 << 18)).all()
+    return (x | (y << 18) | (z << 36) | (typ << 54) | (lvl << 59)).astype(np.uint64)
+
+
+def cube_boxes(keys, origin, min_edge, max_depth):
+    k = np.asarray(keys, dtype=np.uint64).astype(np.int64)
+    xyz = np.stack([k & 0x3FFFF, (k >> 18) & 0x3FFFF, (k >> 36) & 0x3FFFF], 1).astype(np.float64)
+    h = min_edge * 2.0 ** (max_depth - ((k >> 59) & 31)).astype(np.float64)
+    lo = origin + xyz * h[:, None]
+    return lo, lo + h[:, None]
+
+
+def window_compare(full, cfg, centre, half=6.0, inner=5.0, margin=10.0, min_cubes=100, min_tris=500):
+    """Locality check (section 3.1: every cube decision and field value reads
+    only atoms within the cutoff radius): the oracle meshes the atoms within
+    `margin` of the window [centre - half, centre + half]^3 and must give the
+    same cubes inside the window, and inside the inner window [centre -
+    inner, centre + inner]^3 the same surface-point keys, positions within
+    1e-5 A and triangles, as `full` (dict cube_keys, vkeys, vertices,
+    triangles: the whole problem's mesh).  margin >= root cube edge +
+    largest cutoff radius covers every ancestor's and neighbour's atoms.
+    Returns the number of triangles compared."""
+    import oracle
+    md, me = cfg["max_depth"], cfg["min_edge"]
+    o_full, _, _ = oracle.root_grid(cfg["xyz"], cfg["r"], cfg["D"], cfg["c"], me, md)
+    lo_w, hi_w = centre - half, centre + half
+    sel = np.all((cfg["xyz"] >= lo_w - margin) & (cfg["xyz"] <= hi_w + margin), axis=1)
+    sx, sr = np.ascontiguousarray(cfg["xyz"][sel]), np.ascontiguousarray(cfg["r"][sel])
+    ref = oracle.mesh(sx, sr, cfg["D"], cfg["c"], cfg["precision"], me, md)
+    assert ref["stats"]["loop_errors"] == 0
+    o_sub, _, _ = oracle.root_grid(sx, sr, cfg["D"], cfg["c"], me, md)
+    shift = np.round((o_sub - o_full) / me).astype(np.int64)
+    assert np.all(shift % (1 << md) == 0) and np.all(shift >= 0)
+    # cubes inside the window
+    glo, ghi = cube_boxes(full["cube_keys"], o_full, me, md)
+    ginside = np.all((glo >= lo_w) & (ghi <= hi_w), axis=1)
+    rkeys = key_shift(ref["cube_keys"], shift, md)
+    rlo, rhi = cube_boxes(rkeys, o_full, me, md)
+    rinside = np.all((rlo >= lo_w) & (rhi <= hi_w), axis=1)
+    assert ginside.sum() >= min_cubes
+    assert np.array_equal(np.sort(full["cube_keys"][ginside]), np.sort(rkeys[rinside])), "cubes differ"
+    # surface points inside the inner window
+    gv, gkeys = full["vertices"], np.asarray(full["vkeys"], dtype=np.uint64)
+    gin = np.all((gv > centre - inner) & (gv < centre + inner), axis=1)
+    rvk = key_shift(ref["vkeys"], shift, md)
+    rin = np.all((ref["vertices"] > centre - inner) & (ref["vertices"] < centre + inner), axis=1)
+    gk, rk = gkeys[gin], rvk[rin]
+    only = np.setxor1d(gk, rk)
+    if len(only):  # allowed only on the inner window's boundary
+        pos = np.concatenate([gv[np.isin(gkeys, only)], ref["vertices"][np.isin(rvk, only)]])
+        d = np.minimum(np.abs(pos - (centre - inner)), np.abs(pos - (centre + inner))).min(1)
+        assert d.max() < 1e-5, "surface points differ inside the window"
+    common = np.intersect1d(gk, rk)
+    go = np.argsort(gkeys, kind="stable")
+    gi = go[np.searchsorted(gkeys[go], common)]
+    ro = np.argsort(rvk, kind="stable")
+    ri = ro[np.searchsorted(rvk[ro], common)]
+    assert np.array_equal(gkeys[gi], common) and np.array_equal(rvk[ri], common)
+    assert np.abs(gv[gi] - ref["vertices"][ri]).max() < 1e-5
+    # triangles whose three points lie in the common inner set
+    gct = canonical_triangles(gkeys, full["triangles"])
+    rct = canonical_triangles(rvk, ref["triangles"])
+    gct = gct[np.all(np.isin(gct, common), axis=1)]
+    rct = rct[np.all(np.isin(rct, common), axis=1)]
+    assert len(gct) >= min_tris
+    assert np.array_equal(gct, rct), "triangles differ inside the window"
+    return len(gct)

@@ -525,3 +525,23 @@ def test_corner_straddle_implies_keep():
     level = (keys >> np.uint64(59)).astype(int)
     expect = np.where(high <= cfg["precision"], 1, np.where(level >= cfg["max_depth"], 3, 2))
     assert np.array_equal(d[straddle], expect[straddle])
+
+
+def test_threaded_oracle_equals_single_thread():
+    """The oracle's parallel loops (cube tensors and decisions, lattice
+    values, per-cube triangulation) give the same mesh, cube set and
+    statistics on 1 thread and on several: each cube's or point's result
+    depends on it alone and results are collected in input order."""
+    cfg = synth.config("chain100")
+    args = (cfg["xyz"], cfg["r"], cfg["D"], cfg["c"], 0.05, cfg["min_edge"], cfg["max_depth"])
+    try:
+        oracle.set_threads(1)
+        one = oracle.mesh(*args)
+        if oracle.set_threads(4) < 2:
+            pytest.skip("oracle built without OpenMP")
+        many = oracle.mesh(*args)
+    finally:
+        oracle.set_threads(0)
+    for k in ("vertices", "vkeys", "triangles", "cube_keys", "pre_keys", "lattice_keys", "lattice_phi"):
+        assert np.array_equal(one[k], many[k]), k
+    assert one["stats"] == many["stats"]
