@@ -55,7 +55,8 @@ class Stats(ctypes.Structure):
                 ("n_vertices_lattice", ctypes.c_int64), ("n_cubes_final", ctypes.c_int64),
                 ("n_cubes_surface", ctypes.c_int64), ("open_faces", ctypes.c_int64),
                 ("degenerate_ears", ctypes.c_int64), ("loop_errors", ctypes.c_int64),
-                ("min_margin", ctypes.c_double)]
+                ("min_margin", ctypes.c_double), ("constrained_vertices", ctypes.c_int64),
+                ("agreement_splits", ctypes.c_int64)]
 
 
 class MeshOut(ctypes.Structure):
@@ -70,6 +71,7 @@ class MeshOut(ctypes.Structure):
                 ("n_lattice", ctypes.c_int64),
                 ("lattice_keys", ctypes.POINTER(ctypes.c_uint64)),
                 ("lattice_phi", ctypes.POINTER(ctypes.c_double)),
+                ("lattice_psi", ctypes.POINTER(ctypes.c_double)),
                 ("st", Stats)]
 
 
@@ -108,7 +110,7 @@ def lib():
         L.or_partition.restype = i32
         L.or_mesh_free.argtypes = [ctypes.POINTER(MeshOut)]
         L.or_mesh_grid.argtypes = [i64, i64, i64, p, d, ctypes.POINTER(MeshOut)]
-        L.or_mesh_ex.argtypes = [i64, p, p, d, d, d, d, d, i32, i32, i32, i32, ctypes.POINTER(MeshOut)]
+        L.or_mesh_ex.argtypes = [i64, p, p, d, d, d, d, d, i32, i32, i32, i32, i32, ctypes.POINTER(MeshOut)]
         L.or_mesh_ex.restype = i32
         L.or_child_reexpand.argtypes = [p, i32, p]
         L.or_child_reexpand.restype = None
@@ -231,7 +233,8 @@ def _stats_dict(st, max_depth):
                 n_vertices_lattice=int(st.n_vertices_lattice), n_cubes_final=int(st.n_cubes_final),
                 n_cubes_surface=int(st.n_cubes_surface), open_faces=int(st.open_faces),
                 degenerate_ears=int(st.degenerate_ears), loop_errors=int(st.loop_errors),
-                min_margin=float(st.min_margin))
+                min_margin=float(st.min_margin), constrained_vertices=int(st.constrained_vertices),
+                agreement_splits=int(st.agreement_splits))
 
 
 def _arr(ptr, n, dtype, shape=None):
@@ -250,16 +253,19 @@ def child_reexpand(A, c8):
     return B.reshape(4, 4, 4)
 
 
-def mesh(xyz, r, D, c, precision, min_edge, max_depth, cutoff_rel=CUTOFF_REL, child_mode=0, order=0, norm=0):
+def mesh(xyz, r, D, c, precision, min_edge, max_depth, cutoff_rel=CUTOFF_REL, child_mode=0, order=0, norm=0,
+         conform=0):
     """Whole path; returns dict(vertices, vkeys, triangles, cube_keys, pre_keys, stats, ...).
     child_mode 1: child tensors by re-expansion of the parent's polynomial;
     order 1: literal order of steps 2-3; norm 1/2: max |.| / Euclidean norm
-    of the high-order coefficients in the precision test."""
+    of the high-order coefficients in the precision test; conform 1: cubes
+    sharing a face or an edge are split to one size (instead of constrained
+    vertex values with at most one level between them)."""
     xyz, r = _f64(xyz), _f64(r)
     out = MeshOut()
     L = lib()
     e = L.or_mesh_ex(len(r), _ptr(xyz), _ptr(r), D, c, cutoff_rel, precision, min_edge, max_depth, child_mode,
-                     order, norm, ctypes.byref(out))
+                     order, norm, conform, ctypes.byref(out))
     if e:
         raise ValueError("oracle status %d" % e)
     try:
@@ -271,6 +277,7 @@ def mesh(xyz, r, D, c, precision, min_edge, max_depth, cutoff_rel=CUTOFF_REL, ch
             pre_keys=_arr(out.pre_keys, out.n_accepted_pre, np.uint64),
             lattice_keys=_arr(out.lattice_keys, out.n_lattice, np.uint64),
             lattice_phi=_arr(out.lattice_phi, out.n_lattice, np.float64),
+            lattice_psi=_arr(out.lattice_psi, out.n_lattice, np.float64),
             stats=_stats_dict(out.st, max_depth))
     finally:
         L.or_mesh_free(ctypes.byref(out))

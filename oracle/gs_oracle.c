@@ -105,6 +105,8 @@ typedef struct {
     int child_mode;   /* 0: children re-projected from the atoms; 1: re-expansion of the parent's P~ */
     int order;        /* 0: bound test, then precision test; 1: literal order of steps 2 and 3 */
     int norm;         /* size of the high-order coefficients: 0 sum of |.|, 1 max |.|, 2 sqrt of sum of squares */
+    int conform;      /* mixed-size neighbours: 0 constrained vertex values with at most one level between
+                         cubes that share a face or an edge; 1 equal sizes across every shared face and edge */
 } oprob;
 
 /* Terms exp(-D(|x-xi|^2 - ri^2)) below cutoff_rel*c are dropped:
@@ -159,6 +161,14 @@ static void oprob_free(oprob *P) { free(P->R2); P->R2 = NULL; }
 static double lvl_h(const oprob *P, int l) { return ldexp(P->min_edge, P->max_depth - l); }
 /* world coordinate of lattice index i at level l along axis a */
 static double lat_x(const oprob *P, int a, int64_t i, int l) { return P->origin[a] + (double)i * lvl_h(P, l); }
+/* world coordinate at fraction f of the level-l edge that starts at lattice
+ * index i (the index's own lattice coordinate when f is 0 or 1) */
+static double wfrac(const oprob *P, int a, int64_t i, int l, double f)
+{
+    if (f == 0) return lat_x(P, a, i, l);
+    if (f == 1) return lat_x(P, a, i + 1, l);
+    return lat_x(P, a, i, l) + f * lvl_h(P, l);
+}
 
 /* ================================================================== */
 /* Gauss-Legendre rule (nodes by Newton iteration on P_n).              */
@@ -619,6 +629,8 @@ typedef struct {
     int64_t n_cubes_final, n_cubes_surface;
     int64_t open_faces, degenerate_ears, loop_errors;
     double min_margin;        /* smallest |c-L|,|U-c|,|precision-high| seen (relative) */
+    int64_t constrained_vertices; /* lattice vertices whose value is a coarser cube's interpolant */
+    int64_t agreement_splits;     /* cubes split because a constrained value fell on the other side of c */
 } ostats;
 
 static void cube_box(const oprob *P, uint64_t key, double *lo, double *hi)
@@ -756,20 +768,31 @@ static int partition(const oprob *P, vec64 *accepted, ostats *st, uint8_t *dec_l
 }
 
 /* ================================================================== */
-/* Mixed-size neighbours (section 2.3: points of neighbouring cubes     */
-/* inside the current cube must be considered).  Reading: an accepted   */
-/* cube that touches a finer accepted cube along a face or an edge is    */
-/* split into 8 accepted children, until no such contact remains; all    */
-/* surface points on shared faces and edges then come from cubes of one  */
-/* size.                                                                 */
+/* Mixed-size neighbours (section 2.3: the points of the neighbouring   */
+/* cubes that lie in the current cube are taken into its loops, so that  */
+/* cubes of different sizes join without cracks).                       */
+/*                                                                       */
+/* Reading (conform = 0): the accepted cubes keep their sizes, except    */
+/* that a cube touching a cube two or more levels finer along a face or  */
+/* an edge is split (to a fixpoint), so cubes that share a face or an    */
+/* edge differ by at most one level.  A lattice vertex on a face or an   */
+/* edge of a coarser final cube takes that cube's interpolant there      */
+/* (constrain_values below), which makes the piecewise trilinear g       */
+/* continuous; the triangulation then takes the finer neighbours' points */
+/* on a shared face into the coarser cube's face curve, and the coarser  */
+/* cube's extreme points into the finer cubes' curves.                   */
+/* Reading conform = 1: every accepted cube touching any finer one is    */
+/* split, until all cubes sharing a face or an edge have one size.       */
 /* ================================================================== */
 
-static int touches_finer(const uint64_t *S, int64_t n, uint64_t key, int max_depth)
+/* does the cube touch, along a face or an edge, a cube at least min_gap
+ * levels finer? */
+static int touches_finer(const uint64_t *S, int64_t n, uint64_t key, int max_depth, int min_gap)
 {
     int64_t x, y, z;
     okey_xyz(key, &x, &y, &z);
     int l = (int)okey_level(key);
-    for (int lf = l + 1; lf <= max_depth; lf++) {
+    for (int lf = l + min_gap; lf <= max_depth; lf++) {
         int64_t s = (int64_t)1 << (lf - l);
         int64_t I0[3] = {x * s, y * s, z * s};
         for (int64_t a = -1; a <= s; a++)
@@ -795,7 +818,7 @@ static int conformity(const oprob *P, vec64 *S, ostats *st)
         for (int64_t i = 0; i < S->n; i++) {
             uint64_t k = S->a[i];
             int l = (int)okey_level(k);
-            if (l < P->max_depth && touches_finer(S->a, S->n, k, P->max_depth)) {
+            if (l < P->max_depth && touches_finer(S->a, S->n, k, P->max_depth, P->conform ? 1 : 2)) {
                 int64_t x, y, z;
                 okey_xyz(k, &x, &y, &z);
                 for (int c8 = 0; c8 < 8; c8++)
@@ -813,6 +836,163 @@ static int conformity(const oprob *P, vec64 *S, ostats *st)
     return OR_ERR_CAP;
 }
 
+/* replace the cubes listed in R (sorted, unique, all members of S) by their
+ * eight children */
+static int split_listed(vec64 *S, const uint64_t *R, int64_t nr, int64_t *nsplit)
+{
+    vec64 out = {0};
+    *nsplit = 0;
+    for (int64_t i = 0; i < S->n; i++) {
+        uint64_t k = S->a[i];
+        if (find_u64(R, nr, k) < 0) {
+            if (v_push(&out, k)) { free(out.a); return OR_ERR_OOM; }
+            continue;
+        }
+        int64_t x, y, z;
+        okey_xyz(k, &x, &y, &z);
+        unsigned l = okey_level(k);
+        for (int c8 = 0; c8 < 8; c8++)
+            if (v_push(&out, okey((uint64_t)(2 * x + (c8 & 1)), (uint64_t)(2 * y + ((c8 >> 1) & 1)),
+                                  (uint64_t)(2 * z + ((c8 >> 2) & 1)), T_CUBE, l + 1))) {
+                free(out.a);
+                return OR_ERR_OOM;
+            }
+        (*nsplit)++;
+    }
+    free(S->a);
+    *S = out;
+    S->n = sort_unique(S->a, S->n);
+    return OR_OK;
+}
+
+/* Constrained vertex values.  A lattice vertex that lies on a face or an
+ * edge of a coarser final cube without being one of its corners takes the
+ * bilinear (face) or linear (edge) interpolant of that cube's corner values;
+ * the coarsest cube touching the vertex decides, and the values are set
+ * coarse to fine, so the corners it reads are final.  With these values the
+ * trilinear functions of two cubes sharing a face agree on the whole face
+ * (conforming hanging-node constraints of octree finite elements), so their
+ * level curves there coincide.  Every other vertex keeps its field value.
+ * The interpolant depends only on the face or edge (its corners in global
+ * axis order and the vertex's fractions along it), not on which cube holds
+ * it. */
+typedef struct {
+    int lev;          /* level of the constraining face or edge; -1: free (psi = phi) */
+    int nsrc;         /* 2 (edge) or 4 (face) */
+    int64_t src[4];   /* vertex indices: edge lower, upper; face (u0,w0) (u1,w0) (u0,w1) (u1,w1) */
+    double t[2];      /* fractions along the edge, or along u and w on the face */
+} ocons;
+
+static int64_t vert_index(const uint64_t *vk, int64_t nv, int64_t X, int64_t Y, int64_t Z)
+{
+    if (X < 0 || Y < 0 || Z < 0) return -1;
+    return find_u64(vk, nv, okey((uint64_t)X, (uint64_t)Y, (uint64_t)Z, T_VERT, 0));
+}
+
+static int constrain_values(const oprob *P, const uint64_t *cubes, int64_t nc, const uint64_t *vk, int64_t nv,
+                            const double *phi, double *psi, ocons *cons)
+{
+    const int md = P->max_depth;
+    for (int64_t i = 0; i < nv; i++) {
+        ocons *K = &cons[i];
+        K->lev = -1;
+        K->nsrc = 0;
+        psi[i] = phi[i];
+        if (P->conform) continue;
+        int64_t X[3];
+        okey_xyz(vk[i], &X[0], &X[1], &X[2]);
+        for (int l = 0; l < md; l++) {
+            int64_t s = (int64_t)1 << (md - l);
+            int al[3], na = 0;
+            for (int a = 0; a < 3; a++) { al[a] = X[a] % s == 0; na += al[a]; }
+            if (na == 0) continue;
+            /* level-l cubes whose closed box holds the vertex */
+            int found = 0;
+            for (int c8 = 0; c8 < 8 && !found; c8++) {
+                int64_t Q[3];
+                int ok = 1;
+                for (int a = 0; a < 3; a++) {
+                    int bit = (c8 >> a) & 1;
+                    if (!al[a] && bit) { ok = 0; break; }
+                    Q[a] = X[a] / s - (al[a] && bit ? 1 : 0);
+                    if (Q[a] < 0) { ok = 0; break; }
+                }
+                if (ok && find_u64(cubes, nc, okey((uint64_t)Q[0], (uint64_t)Q[1], (uint64_t)Q[2], T_CUBE,
+                                                   (unsigned)l)) >= 0)
+                    found = 1;
+            }
+            if (!found) continue;
+            if (na == 3) break; /* a corner of the coarsest cube touching it: free */
+            /* the face (one aligned axis) or edge (two) of level l holding it */
+            int un[2], nu = 0;
+            for (int a = 0; a < 3; a++)
+                if (!al[a]) un[nu++] = a;
+            int64_t base[3];
+            for (int a = 0; a < 3; a++) base[a] = al[a] ? X[a] : (X[a] / s) * s;
+            K->lev = l;
+            K->nsrc = nu == 1 ? 2 : 4;
+            for (int k = 0; k < nu; k++) K->t[k] = (double)(X[un[k]] - base[un[k]]) / (double)s;
+            for (int q = 0; q < K->nsrc; q++) {
+                int64_t Y[3] = {base[0], base[1], base[2]};
+                for (int k = 0; k < nu; k++) Y[un[k]] += ((q >> k) & 1) ? s : 0;
+                K->src[q] = vert_index(vk, nv, Y[0], Y[1], Y[2]);
+                if (K->src[q] < 0) return OR_ERR_CAP;
+            }
+            break;
+        }
+    }
+    /* coarse to fine: a source's own constraint is of a coarser level */
+    for (int l = 0; l < md; l++)
+        for (int64_t i = 0; i < nv; i++) {
+            const ocons *K = &cons[i];
+            if (K->lev != l) continue;
+            if (K->nsrc == 2) {
+                double a = psi[K->src[0]], b = psi[K->src[1]];
+                psi[i] = a + K->t[0] * (b - a);
+            } else {
+                double q00 = psi[K->src[0]], q10 = psi[K->src[1]], q01 = psi[K->src[2]], q11 = psi[K->src[3]];
+                double e0 = q00 + K->t[0] * (q10 - q00);
+                double e1 = q01 + K->t[0] * (q11 - q01);
+                psi[i] = e0 + K->t[1] * (e1 - e0);
+            }
+        }
+    return OR_OK;
+}
+
+/* Disagreement (the split rule for cubes of different sizes): a vertex
+ * whose constrained value and field value lie on different sides of c
+ * would put the surface where the finer cubes, or the cubes discarded next
+ * to them, have none.  Every final cube of the constraining level that
+ * holds such a vertex on its boundary is listed for splitting. */
+static int disagreeing_cubes(const oprob *P, const uint64_t *cubes, int64_t nc, const uint64_t *vk, int64_t nv,
+                             const double *phi, const double *psi, const ocons *cons, vec64 *R)
+{
+    const int md = P->max_depth;
+    const double c = P->c;
+    for (int64_t i = 0; i < nv; i++) {
+        if (cons[i].lev < 0 || (psi[i] >= c) == (phi[i] >= c)) continue;
+        int l = cons[i].lev;
+        int64_t s = (int64_t)1 << (md - l);
+        int64_t X[3];
+        okey_xyz(vk[i], &X[0], &X[1], &X[2]);
+        for (int c8 = 0; c8 < 8; c8++) {
+            int64_t Q[3];
+            int ok = 1;
+            for (int a = 0; a < 3; a++) {
+                int al = X[a] % s == 0, bit = (c8 >> a) & 1;
+                if (!al && bit) { ok = 0; break; }
+                Q[a] = X[a] / s - (al && bit ? 1 : 0);
+                if (Q[a] < 0) { ok = 0; break; }
+            }
+            if (!ok) continue;
+            uint64_t k = okey((uint64_t)Q[0], (uint64_t)Q[1], (uint64_t)Q[2], T_CUBE, (unsigned)l);
+            if (find_u64(cubes, nc, k) >= 0 && v_push(R, k)) return OR_ERR_OOM;
+        }
+    }
+    R->n = sort_unique(R->a, R->n);
+    return OR_OK;
+}
+
 /* ================================================================== */
 /* Per-cube trilinear surface (eq linear1) and its triangulation         */
 /* (section 2.3, eqs intersection, curve, fold1, critical).              */
@@ -821,6 +1001,7 @@ static int conformity(const oprob *P, vec64 *S, ostats *st)
 
 typedef struct {
     double p[3];   /* local coords */
+    double w[3];   /* world coords, computed in the frame of the cube (or edge) the point belongs to */
     uint64_t key;
     int kind;      /* 0 edge point, 1 own extreme point, 2 neighbour's extreme point, 3 critical point */
     int nb[4];     /* fold neighbours: extreme point -> nb[0]; critical point -> +a, -a, +b, -b */
@@ -829,6 +1010,7 @@ typedef struct {
 } opoint;
 
 #define MAXP 64
+#define FPMAX 20 /* points inserted into one face curve */
 #ifdef OR_DEBUG
 #include <stdio.h>
 #define LOOPERR(site) do { st->loop_errors++; fprintf(stderr, "looperr site %d cube %llx\n", site, (unsigned long long)ckey); } while (0)
@@ -1071,8 +1253,12 @@ static int triangulate_cube(const omesh_ctx *M, uint64_t ckey, vtri *tris, vvert
 
     opoint pts[MAXP];
     int np = 0;
+    const int fine_ok = P->conform == 0 && l < P->max_depth;
+    const int64_t s2 = s / 2; /* the finer level's step (with fine_ok) */
     /* edge points (eq intersection): eid[a][o1][o2], o1/o2 = bits of the
-     * other two axes in increasing axis order */
+     * other two axes in increasing axis order.  An edge that a finer cube
+     * touches is halved (its midpoint is a lattice vertex): the point is the
+     * crossing on the half where the sign changes, keyed by that half. */
     int eid[3][2][2];
     for (int a = 0; a < 3; a++) {
         int ua, va;
@@ -1085,11 +1271,30 @@ static int triangulate_cube(const omesh_ctx *M, uint64_t ckey, vtri *tris, vvert
                 eid[a][o1][o2] = -1;
                 if ((g0 >= c) == (g1 >= c)) continue;
                 int id = new_point(pts, &np, 0);
+                if (id < 0) { LOOPERR(9); return OR_OK; }
                 opoint *p = &pts[id];
-                p->p[a] = (c - g0) / (g1 - g0); p->p[ua] = o1; p->p[va] = o2;
                 int64_t L[3];
                 L[a] = C[a] * s; L[ua] = (C[ua] + o1) * s; L[va] = (C[va] + o2) * s;
-                p->key = okey((uint64_t)L[0], (uint64_t)L[1], (uint64_t)L[2], (unsigned)a, (unsigned)l);
+                double gm;
+                int64_t Lm[3] = {L[0], L[1], L[2]};
+                Lm[a] += s2;
+                if (fine_ok && lookup_phi(M, Lm[0], Lm[1], Lm[2], &gm)) {
+                    int half = (g0 >= c) == (gm >= c); /* 0: first half, 1: second */
+                    double ga = half ? gm : g0, gb = half ? g1 : gm;
+                    double t = (c - ga) / (gb - ga);
+                    p->p[a] = (half + t) * 0.5;
+                    L[a] += half * s2;
+                    p->key = okey((uint64_t)L[0], (uint64_t)L[1], (uint64_t)L[2], (unsigned)a, (unsigned)(l + 1));
+                    p->w[a] = wfrac(P, a, 2 * C[a] + half, l + 1, t);
+                } else {
+                    double t = (c - g0) / (g1 - g0);
+                    p->p[a] = t;
+                    p->key = okey((uint64_t)L[0], (uint64_t)L[1], (uint64_t)L[2], (unsigned)a, (unsigned)l);
+                    p->w[a] = wfrac(P, a, C[a], l, t);
+                }
+                p->p[ua] = o1; p->p[va] = o2;
+                p->w[ua] = lat_x(P, ua, L[ua], P->max_depth);
+                p->w[va] = lat_x(P, va, L[va], P->max_depth);
                 eid[a][o1][o2] = id;
             }
     }
@@ -1097,7 +1302,7 @@ static int triangulate_cube(const omesh_ctx *M, uint64_t ckey, vtri *tris, vvert
      * whose ends on the two faces normal to the axis are extreme points
      * (eq curve).  A neighbour's folds end on the face it shares with this
      * cube; they become further points of that face curve. */
-    int fp[3][2][4];
+    int fp[3][2][FPMAX];
     int nfp[3][2] = {{0, 0}, {0, 0}, {0, 0}};
     double fr[3][2][2];   /* own roots: fr[a][r] = (u, v) */
     int fend[3][2][2];    /* own fold ends: fend[a][r][side] */
@@ -1136,7 +1341,7 @@ static int triangulate_cube(const omesh_ctx *M, uint64_t ckey, vtri *tris, vvert
         for (int r = 0; r < nfr[a]; r++) {
             for (int sd = 0; sd < 2; sd++) {
                 int id = new_point(pts, &np, 1);
-                if (id < 0) return OR_ERR_CAP;
+                if (id < 0) { LOOPERR(9); return OR_OK; }
                 opoint *p = &pts[id];
                 p->p[a] = sd; p->p[ua] = fr[a][r][0]; p->p[va] = fr[a][r][1];
                 int64_t L[3] = {C[0] * s, C[1] * s, C[2] * s};
@@ -1144,31 +1349,147 @@ static int triangulate_cube(const omesh_ctx *M, uint64_t ckey, vtri *tris, vvert
                 /* face at sd=0: this cube lies on its + side; sd=1: - side */
                 unsigned type = 8u + 4u * (unsigned)a + 2u * (unsigned)(sd == 0) + (unsigned)r;
                 p->key = okey((uint64_t)L[0], (uint64_t)L[1], (uint64_t)L[2], type, (unsigned)l);
+                for (int q = 0; q < 3; q++) p->w[q] = wfrac(P, q, C[q], l, p->p[q]);
                 fend[a][r][sd] = id;
                 fp[a][sd][nfp[a][sd]++] = id;
             }
         }
+        /* Across each face normal to a: the points of the neighbouring cubes
+         * that lie on it (section 2.3).  A neighbour of the same size adds its
+         * a-fold ends; finer neighbours (four tiles of the face) add their
+         * a-fold ends and the points on the face's inner half-lines, which
+         * are their edges; a coarser neighbour adds those of its a-fold ends
+         * that fall in this face (the quarter of its face that this cube
+         * covers, halves taken as [0, 1/2) and [1/2, 1]).  All of them lie
+         * on this face's level curve: the tiles' and this face's values are
+         * one bilinear function (constrained vertex values). */
         for (int sd = 0; sd < 2; sd++) {
             int64_t N[3] = {C[0], C[1], C[2]};
             N[a] += sd ? 1 : -1;
             if (N[a] < 0) continue;
             uint64_t nk = okey((uint64_t)N[0], (uint64_t)N[1], (uint64_t)N[2], T_CUBE, (unsigned)l);
-            if (find_u64(M->cubes, M->ncubes, nk) < 0) continue;
-            double gn[8];
-            if (!cube_values(M, l, N[0], N[1], N[2], gn)) return OR_ERR_CAP;
-            double nu_[2], nv_[2];
-            int nn = fold_roots(gn, a, c, nu_, nv_);
-            for (int r = 0; r < nn; r++) {
-                int id = new_point(pts, &np, 2);
-                if (id < 0) return OR_ERR_CAP;
-                opoint *p = &pts[id];
-                p->p[a] = sd; p->p[ua] = nu_[r]; p->p[va] = nv_[r];
-                int64_t L[3] = {C[0] * s, C[1] * s, C[2] * s};
-                L[a] = (C[a] + sd) * s;
-                /* the neighbour lies on the + side of the shared face iff sd = 1 */
-                unsigned type = 8u + 4u * (unsigned)a + 2u * (unsigned)(sd == 1) + (unsigned)r;
-                p->key = okey((uint64_t)L[0], (uint64_t)L[1], (uint64_t)L[2], type, (unsigned)l);
-                fp[a][sd][nfp[a][sd]++] = id;
+            if (find_u64(M->cubes, M->ncubes, nk) >= 0) {
+                double gn[8];
+                if (!cube_values(M, l, N[0], N[1], N[2], gn)) return OR_ERR_CAP;
+                double nu_[2], nv_[2];
+                int nn = fold_roots(gn, a, c, nu_, nv_);
+                for (int r = 0; r < nn; r++) {
+                    int id = new_point(pts, &np, 2);
+                    if (id < 0 || nfp[a][sd] >= FPMAX) { LOOPERR(9); return OR_OK; }
+                    opoint *p = &pts[id];
+                    p->p[a] = sd; p->p[ua] = nu_[r]; p->p[va] = nv_[r];
+                    int64_t L[3] = {C[0] * s, C[1] * s, C[2] * s};
+                    L[a] = (C[a] + sd) * s;
+                    /* the neighbour lies on the + side of the shared face iff sd = 1 */
+                    unsigned type = 8u + 4u * (unsigned)a + 2u * (unsigned)(sd == 1) + (unsigned)r;
+                    p->key = okey((uint64_t)L[0], (uint64_t)L[1], (uint64_t)L[2], type, (unsigned)l);
+                    for (int q = 0; q < 3; q++) p->w[q] = wfrac(P, q, C[q], l, p->p[q]);
+                    fp[a][sd][nfp[a][sd]++] = id;
+                }
+                continue;
+            }
+            if (P->conform) continue;
+            /* the neighbouring cube's side of the shared plane */
+            const int side_n = sd ? 0 : 1;
+            const int64_t plane = (C[a] + sd) * s; /* finest-lattice coordinate of the face */
+            if (fine_ok) {
+                int tex[2][2];
+                int64_t T[2][2][3];
+                int ntile = 0;
+                for (int iv = 0; iv < 2; iv++)
+                    for (int iu = 0; iu < 2; iu++) {
+                        int64_t *t3 = T[iu][iv];
+                        t3[a] = 2 * N[a] + side_n; t3[ua] = 2 * C[ua] + iu; t3[va] = 2 * C[va] + iv;
+                        tex[iu][iv] = find_u64(M->cubes, M->ncubes,
+                                               okey((uint64_t)t3[0], (uint64_t)t3[1], (uint64_t)t3[2], T_CUBE,
+                                                    (unsigned)(l + 1))) >= 0;
+                        ntile += tex[iu][iv];
+                    }
+                if (ntile > 0) {
+                    /* the tiles' fold ends on this face */
+                    for (int iv = 0; iv < 2; iv++)
+                        for (int iu = 0; iu < 2; iu++) {
+                            if (!tex[iu][iv]) continue;
+                            const int64_t *t3 = T[iu][iv];
+                            double gt[8];
+                            if (!cube_values(M, l + 1, t3[0], t3[1], t3[2], gt)) return OR_ERR_CAP;
+                            double tu[2], tv[2];
+                            int nn = fold_roots(gt, a, c, tu, tv);
+                            for (int r = 0; r < nn; r++) {
+                                int id = new_point(pts, &np, 2);
+                                if (id < 0 || nfp[a][sd] >= FPMAX) { LOOPERR(9); return OR_OK; }
+                                opoint *p = &pts[id];
+                                p->p[a] = sd; p->p[ua] = (iu + tu[r]) * 0.5; p->p[va] = (iv + tv[r]) * 0.5;
+                                int64_t L[3] = {t3[0] * s2, t3[1] * s2, t3[2] * s2};
+                                L[a] = plane;
+                                unsigned type = 8u + 4u * (unsigned)a + 2u * (unsigned)(side_n == 0) + (unsigned)r;
+                                p->key = okey((uint64_t)L[0], (uint64_t)L[1], (uint64_t)L[2], type, (unsigned)(l + 1));
+                                p->w[a] = lat_x(P, a, plane, P->max_depth);
+                                p->w[ua] = wfrac(P, ua, t3[ua], l + 1, tu[r]);
+                                p->w[va] = wfrac(P, va, t3[va], l + 1, tv[r]);
+                                fp[a][sd][nfp[a][sd]++] = id;
+                            }
+                        }
+                    /* the inner half-lines: along u at v = 1/2 (halves k),
+                     * then along v at u = 1/2; a half-line is an edge of the
+                     * tiles on either side of it */
+                    for (int dir = 0; dir < 2; dir++)
+                        for (int k = 0; k < 2; k++) {
+                            int along = dir ? va : ua, across = dir ? ua : va;
+                            int has = dir ? (tex[0][k] || tex[1][k]) : (tex[k][0] || tex[k][1]);
+                            if (!has) continue;
+                            int64_t L0[3];
+                            L0[a] = plane;
+                            L0[along] = C[along] * s + k * s2;
+                            L0[across] = C[across] * s + s2;
+                            int64_t L1[3] = {L0[0], L0[1], L0[2]};
+                            L1[along] += s2;
+                            double ga, gb;
+                            if (!lookup_phi(M, L0[0], L0[1], L0[2], &ga) || !lookup_phi(M, L1[0], L1[1], L1[2], &gb)) {
+                                LOOPERR(10);
+                                return OR_OK;
+                            }
+                            if ((ga >= c) == (gb >= c)) continue;
+                            int id = new_point(pts, &np, 2);
+                            if (id < 0 || nfp[a][sd] >= FPMAX) { LOOPERR(9); return OR_OK; }
+                            opoint *p = &pts[id];
+                            double t = (c - ga) / (gb - ga);
+                            p->p[a] = sd; p->p[along] = (k + t) * 0.5; p->p[across] = 0.5;
+                            p->key = okey((uint64_t)L0[0], (uint64_t)L0[1], (uint64_t)L0[2], (unsigned)along,
+                                          (unsigned)(l + 1));
+                            p->w[a] = lat_x(P, a, plane, P->max_depth);
+                            p->w[along] = wfrac(P, along, 2 * C[along] + k, l + 1, t);
+                            p->w[across] = lat_x(P, across, L0[across], P->max_depth);
+                            fp[a][sd][nfp[a][sd]++] = id;
+                        }
+                    continue;
+                }
+            }
+            if (l > 0) {
+                int64_t Q[3] = {N[0] >> 1, N[1] >> 1, N[2] >> 1};
+                if (find_u64(M->cubes, M->ncubes,
+                             okey((uint64_t)Q[0], (uint64_t)Q[1], (uint64_t)Q[2], T_CUBE, (unsigned)(l - 1))) < 0)
+                    continue;
+                double gq[8];
+                if (!cube_values(M, l - 1, Q[0], Q[1], Q[2], gq)) return OR_ERR_CAP;
+                double qu_[2], qv_[2];
+                int nn = fold_roots(gq, a, c, qu_, qv_);
+                const int64_t su = C[ua] - 2 * Q[ua], sv = C[va] - 2 * Q[va]; /* this face's quarter */
+                for (int r = 0; r < nn; r++) {
+                    if ((qu_[r] >= 0.5) != (su == 1) || (qv_[r] >= 0.5) != (sv == 1)) continue;
+                    int id = new_point(pts, &np, 2);
+                    if (id < 0 || nfp[a][sd] >= FPMAX) { LOOPERR(9); return OR_OK; }
+                    opoint *p = &pts[id];
+                    p->p[a] = sd; p->p[ua] = 2.0 * qu_[r] - (double)su; p->p[va] = 2.0 * qv_[r] - (double)sv;
+                    int64_t L[3] = {Q[0] * 2 * s, Q[1] * 2 * s, Q[2] * 2 * s};
+                    L[a] = plane;
+                    unsigned type = 8u + 4u * (unsigned)a + 2u * (unsigned)(side_n == 0) + (unsigned)r;
+                    p->key = okey((uint64_t)L[0], (uint64_t)L[1], (uint64_t)L[2], type, (unsigned)(l - 1));
+                    p->w[a] = lat_x(P, a, plane, P->max_depth);
+                    p->w[ua] = wfrac(P, ua, Q[ua], l - 1, qu_[r]);
+                    p->w[va] = wfrac(P, va, Q[va], l - 1, qv_[r]);
+                    fp[a][sd][nfp[a][sd]++] = id;
+                }
             }
         }
     }
@@ -1183,11 +1504,12 @@ static int triangulate_cube(const omesh_ctx *M, uint64_t ckey, vtri *tris, vvert
         other_axes(a, &ua, &va);
         other_axes(b, &ub, &vb);
         int id = new_point(pts, &np, 3);
-        if (id < 0) return OR_ERR_CAP;
+        if (id < 0) { LOOPERR(9); return OR_OK; }
         opoint *p = &pts[id];
         p->p[a] = fr[b][j][a == ub ? 0 : 1];
         p->p[b] = fr[a][i][b == ua ? 0 : 1];
         p->p[cc] = fr[a][i][cc == ua ? 0 : 1];
+        for (int q = 0; q < 3; q++) p->w[q] = wfrac(P, q, C[q], l, p->p[q]);
         p->fa = a; p->fb = b;
         /* outward normal = -grad g = -(dg/dx_cc) e_cc at the point */
         double w[3] = {p->p[0], p->p[1], p->p[2]};
@@ -1297,7 +1619,7 @@ static int triangulate_cube(const omesh_ctx *M, uint64_t ckey, vtri *tris, vvert
                 int st1 = stq[e1] > 0, st2 = stq[e2] > 0;
                 if (st1 == st2) { LOOPERR(4); continue; }
                 int S = st1 ? P1 : P2, T = st1 ? P2 : P1;
-                int mid[8], nm = 0;
+                int mid[FPMAX], nm = 0;
                 for (int t = 0; t < nfp[a][sd]; t++) {
                     int id = fp[a][sd][t];
                     if (narc == 2) {
@@ -1305,7 +1627,7 @@ static int triangulate_cube(const omesh_ctx *M, uint64_t ckey, vtri *tris, vvert
                         int arc_lowu = (ai == 0) ? around00 : !around00;
                         if (branch_lowu != arc_lowu) continue;
                     }
-                    if (nm < 8) mid[nm++] = id;
+                    mid[nm++] = id;
                 }
                 double du = pts[T].p[ua] - pts[S].p[ua], dv = pts[T].p[va] - pts[S].p[va];
                 int ax = fabs(du) >= fabs(dv) ? ua : va;
@@ -1319,7 +1641,7 @@ static int triangulate_cube(const omesh_ctx *M, uint64_t ckey, vtri *tris, vvert
                     }
                     mid[j + 1] = x;
                 }
-                int seq[12], ns = 0;
+                int seq[FPMAX + 2], ns = 0;
                 seq[ns++] = S;
                 for (int i1 = 0; i1 < nm; i1++) seq[ns++] = mid[i1];
                 seq[ns++] = T;
@@ -1383,20 +1705,9 @@ static int triangulate_cube(const omesh_ctx *M, uint64_t ckey, vtri *tris, vvert
             if (r) return r;
         } else if (n > MAXP) LOOPERR(8);
     }
-    /* world positions */
-    double lo[3];
-    for (int a = 0; a < 3; a++) lo[a] = lat_x(P, a, C[a], l);
-    double h = lvl_h(P, l);
-    for (int i = 0; i < np; i++) {
-        double x[3];
-        for (int a = 0; a < 3; a++) {
-            double f = pts[i].p[a];
-            if (f == 0) x[a] = lo[a];
-            else if (f == 1) x[a] = lat_x(P, a, C[a] + 1, l);
-            else x[a] = lo[a] + f * h;
-        }
-        if (p_push(verts, pts[i].key, x)) return OR_ERR_OOM;
-    }
+    /* world positions, each computed in its owner's frame */
+    for (int i = 0; i < np; i++)
+        if (p_push(verts, pts[i].key, pts[i].w)) return OR_ERR_OOM;
     return OR_OK;
 }
 
@@ -1477,13 +1788,14 @@ typedef struct {
     uint64_t *pre_keys;   /* accepted cubes before conformity, sorted */
     int64_t n_lattice;
     uint64_t *lattice_keys; double *lattice_phi; /* vertex field at cube corners */
+    double *lattice_psi;  /* the values the trilinear functions take: phi, or the constrained interpolant */
     ostats st;
 } or_mesh_out;
 
 void or_mesh_free(or_mesh_out *o)
 {
     free(o->vertices); free(o->vkeys); free(o->triangles); free(o->tri_piece); free(o->cube_keys); free(o->pre_keys);
-    free(o->lattice_keys); free(o->lattice_phi);
+    free(o->lattice_keys); free(o->lattice_phi); free(o->lattice_psi);
     memset(o, 0, sizeof(*o));
 }
 
@@ -1550,7 +1862,7 @@ int or_cube_batch(int64_t n, const double *xyz, const double *r, double D, doubl
 
 /* the whole path: partition, conformity, vertex field, triangulation, weld */
 int or_mesh_ex(int64_t n, const double *xyz, const double *r, double D, double c, double cutoff_rel,
-               double precision, double min_edge, int max_depth, int child_mode, int order, int norm,
+               double precision, double min_edge, int max_depth, int child_mode, int order, int norm, int conform,
                or_mesh_out *out)
 {
     memset(out, 0, sizeof(*out));
@@ -1560,6 +1872,8 @@ int or_mesh_ex(int64_t n, const double *xyz, const double *r, double D, double c
     if (child_mode != 0 && child_mode != 1) { oprob_free(&P); return OR_ERR_ARG; }
     if (order != 0 && order != 1) { oprob_free(&P); return OR_ERR_ARG; }
     if (norm < 0 || norm > 2) { oprob_free(&P); return OR_ERR_ARG; }
+    if (conform != 0 && conform != 1) { oprob_free(&P); return OR_ERR_ARG; }
+    P.conform = conform;
     P.child_mode = child_mode;
     P.order = order;
     P.norm = norm;
@@ -1573,28 +1887,55 @@ int or_mesh_ex(int64_t n, const double *xyz, const double *r, double D, double c
     if (acc.n) memcpy(out->pre_keys, acc.a, sizeof(uint64_t) * (size_t)acc.n);
     e = conformity(&P, &acc, st);
     if (e) goto done;
-    st->n_cubes_final = acc.n;
-    /* lattice vertices of accepted cubes and their field values */
+    /* lattice vertices of the final cubes, their field values, and the
+     * constrained values; cubes of different sizes that disagree are split
+     * and the whole repeated (to a fixpoint) */
     {
         vec64 vk = {0};
-        for (int64_t i = 0; i < acc.n; i++) {
-            int64_t x, y, z;
-            okey_xyz(acc.a[i], &x, &y, &z);
-            int l = (int)okey_level(acc.a[i]);
-            int64_t s = (int64_t)1 << (max_depth - l);
-            for (int v = 0; v < 8; v++)
-                if (v_push(&vk, okey((uint64_t)((x + (v & 1)) * s), (uint64_t)((y + ((v >> 1) & 1)) * s),
-                                     (uint64_t)((z + ((v >> 2) & 1)) * s), T_VERT, 0))) { e = OR_ERR_OOM; goto done; }
+        double *vphi = NULL, *vpsi = NULL;
+        for (int iter = 0;; iter++) {
+            free(vk.a); free(vphi); free(vpsi);
+            vk.a = NULL; vk.n = vk.cap = 0; vphi = vpsi = NULL;
+            if (iter > 64) { e = OR_ERR_CAP; goto done; }
+            for (int64_t i = 0; i < acc.n; i++) {
+                int64_t x, y, z;
+                okey_xyz(acc.a[i], &x, &y, &z);
+                int l = (int)okey_level(acc.a[i]);
+                int64_t s = (int64_t)1 << (max_depth - l);
+                for (int v = 0; v < 8; v++)
+                    if (v_push(&vk, okey((uint64_t)((x + (v & 1)) * s), (uint64_t)((y + ((v >> 1) & 1)) * s),
+                                         (uint64_t)((z + ((v >> 2) & 1)) * s), T_VERT, 0))) { e = OR_ERR_OOM; goto done; }
+            }
+            vk.n = sort_unique(vk.a, vk.n);
+            vphi = (double *)malloc(sizeof(double) * (size_t)(vk.n ? vk.n : 1));
+            vpsi = (double *)malloc(sizeof(double) * (size_t)(vk.n ? vk.n : 1));
+            ocons *cons = (ocons *)malloc(sizeof(ocons) * (size_t)(vk.n ? vk.n : 1));
+            if (!vphi || !vpsi || !cons) { free(cons); free(vk.a); free(vphi); free(vpsi); e = OR_ERR_OOM; goto done; }
+            lattice_field(&P, vk.a, vk.n, vphi);
+            e = constrain_values(&P, acc.a, acc.n, vk.a, vk.n, vphi, vpsi, cons);
+            vec64 R = {0};
+            if (!e) e = disagreeing_cubes(&P, acc.a, acc.n, vk.a, vk.n, vphi, vpsi, cons, &R);
+            int64_t ncons = 0;
+            for (int64_t i = 0; i < vk.n; i++) ncons += cons[i].lev >= 0;
+            free(cons);
+            if (!e && R.n > 0) {
+                int64_t ns = 0;
+                e = split_listed(&acc, R.a, R.n, &ns);
+                st->agreement_splits += ns;
+                if (!e) e = conformity(&P, &acc, st);
+            }
+            int64_t nr = R.n;
+            free(R.a);
+            if (e) { free(vk.a); free(vphi); free(vpsi); goto done; }
+            if (nr == 0) { st->constrained_vertices = ncons; break; }
         }
-        vk.n = sort_unique(vk.a, vk.n);
-        double *vphi = (double *)malloc(sizeof(double) * (size_t)(vk.n ? vk.n : 1));
-        if (!vphi) { free(vk.a); e = OR_ERR_OOM; goto done; }
-        lattice_field(&P, vk.a, vk.n, vphi);
+        st->n_cubes_final = acc.n;
         st->n_vertices_lattice = vk.n;
         out->n_lattice = vk.n;
         out->lattice_keys = vk.a;
         out->lattice_phi = vphi;
-        omesh_ctx M = {&P, acc.a, acc.n, vk.a, vphi, vk.n};
+        out->lattice_psi = vpsi;
+        omesh_ctx M = {&P, acc.a, acc.n, vk.a, vpsi, vk.n};
         vtri tris = {0};
         vvert verts = {0};
         e = triangulate_all(&M, acc.a, acc.n, &tris, &verts, st);
@@ -1638,7 +1979,7 @@ done:
 int or_mesh(int64_t n, const double *xyz, const double *r, double D, double c, double cutoff_rel,
             double precision, double min_edge, int max_depth, or_mesh_out *out)
 {
-    return or_mesh_ex(n, xyz, r, D, c, cutoff_rel, precision, min_edge, max_depth, 0, 0, 0, out);
+    return or_mesh_ex(n, xyz, r, D, c, cutoff_rel, precision, min_edge, max_depth, 0, 0, 0, 0, out);
 }
 
 int or_partition(int64_t n, const double *xyz, const double *r, double D, double c, double cutoff_rel,
@@ -1802,7 +2143,12 @@ int or_mesh_grad(int64_t n, const double *xyz, const double *r, double D, double
     e = oprob_init(&P, n, xyz, r, D, c, cutoff_rel, precision, min_edge, max_depth);
     if (e) { or_mesh_free(&m); return e; }
     double *lam = (double *)calloc((size_t)(m.n_lattice ? m.n_lattice : 1), sizeof(double));
-    omesh_ctx M = {&P, m.cube_keys, m.n_cubes, m.lattice_keys, m.lattice_phi, m.n_lattice};
+    ocons *cons = (ocons *)malloc(sizeof(ocons) * (size_t)(m.n_lattice ? m.n_lattice : 1));
+    double *psi = (double *)malloc(sizeof(double) * (size_t)(m.n_lattice ? m.n_lattice : 1));
+    if (!lam || !cons || !psi) e = OR_ERR_OOM;
+    if (!e) e = constrain_values(&P, m.cube_keys, m.n_cubes, m.lattice_keys, m.n_lattice, m.lattice_phi, psi, cons);
+    /* the vertices are functions of the values the trilinear functions take (psi) */
+    omesh_ctx M = {&P, m.cube_keys, m.n_cubes, m.lattice_keys, psi, m.n_lattice};
     for (int64_t i = 0; i < nv && !e; i++) {
         const double *G = dLdp + 3 * i;
         uint64_t K = m.vkeys[i];
@@ -1819,7 +2165,7 @@ int or_mesh_grad(int64_t n, const double *xyz, const double *r, double D, double
             L1[a] += s;
             int64_t i0 = lattice_index(&m, L[0], L[1], L[2]), i1 = lattice_index(&m, L1[0], L1[1], L1[2]);
             if (i0 < 0 || i1 < 0) { e = OR_ERR_CAP; break; }
-            double g0 = m.lattice_phi[i0], g1 = m.lattice_phi[i1];
+            double g0 = psi[i0], g1 = psi[i1];
             double t = (c - g0) / (g1 - g0);
             lam[i0] += G[a] * h * (-(1.0 - t) / (g1 - g0));
             lam[i1] += G[a] * h * (-t / (g1 - g0));
@@ -1872,6 +2218,24 @@ int or_mesh_grad(int64_t n, const double *xyz, const double *r, double D, double
         }
         for (int v = 0; v < 8; v++) lam[li[v]] += h * (G[0] * dp[0][v] + G[1] * dp[1][v] + G[2] * dp[2][v]);
     }
+    /* constrained values are interpolants of their sources: fine to coarse,
+     * each passes its adjoint on with the interpolation weights */
+    for (int l = max_depth - 1; l >= 0 && !e; l--)
+        for (int64_t k = 0; k < m.n_lattice; k++) {
+            const ocons *K = &cons[k];
+            if (K->lev != l || lam[k] == 0.0) continue;
+            if (K->nsrc == 2) {
+                lam[K->src[0]] += lam[k] * (1.0 - K->t[0]);
+                lam[K->src[1]] += lam[k] * K->t[0];
+            } else {
+                double tu = K->t[0], tw = K->t[1];
+                lam[K->src[0]] += lam[k] * (1.0 - tu) * (1.0 - tw);
+                lam[K->src[1]] += lam[k] * tu * (1.0 - tw);
+                lam[K->src[2]] += lam[k] * (1.0 - tu) * tw;
+                lam[K->src[3]] += lam[k] * tu * tw;
+            }
+            lam[k] = 0.0;
+        }
     /* the field (eq Gaussian1, truncated): dt/dx_i = 2D t (p - x_i),
      * dt/dr_i = 2D t r_i, dt/dD = -t (|p - x_i|^2 - r_i^2), all atoms */
     for (int64_t i = 0; i < n; i++) { g_xyz[3 * i] = g_xyz[3 * i + 1] = g_xyz[3 * i + 2] = 0.0; g_r[i] = 0.0; }
@@ -1892,6 +2256,8 @@ int or_mesh_grad(int64_t n, const double *xyz, const double *r, double D, double
         }
     }
     free(lam);
+    free(cons);
+    free(psi);
     oprob_free(&P);
     or_mesh_free(&m);
     return e;
