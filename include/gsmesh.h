@@ -71,6 +71,16 @@ extern "C" {
 #define GS_NORM_MAX 1  /* largest magnitude */
 #define GS_NORM_RSS 2  /* square root of the sum of squares */
 
+/* gs_options.conform_mode: how accepted cubes of different sizes join (section 2.3: the points of the
+   neighbouring cubes that lie in the current cube are considered) */
+#define GS_CONFORM_CONSTRAIN 0  /* cubes sharing a face or an edge differ by at most one level; a lattice vertex
+                                   on a coarser cube's face or edge takes that cube's interpolant, so the
+                                   finer and coarser face curves coincide and each takes the other's points;
+                                   a vertex whose interpolant and field value lie on different sides of c
+                                   splits the coarser cube */
+#define GS_CONFORM_EQUAL 1      /* every cube touching a finer one is split until cubes sharing a face or an
+                                   edge have one size */
+
 /* decisions reported by gs_cube_decisions */
 #define GS_DEC_DISCARD 0
 #define GS_DEC_ACCEPT 1
@@ -105,6 +115,11 @@ typedef struct {
                                      FP32 bound could move an edge point, flip a face saddle, move a fold root */
     int64_t estimate_fast_cubes; /* mixed mode: cubes kept because the corner values of P~ straddle c, decided
                                     without the SVD bounds */
+    int64_t constrained_vertices; /* lattice vertices on a coarser cube's face or edge, whose value is that
+                                     cube's interpolant (GS_CONFORM_CONSTRAIN) */
+    int64_t agreement_splits;     /* cubes split because such an interpolant and the field value lay on
+                                     different sides of c */
+    int64_t mixed_cubes;          /* final cubes with a neighbour of another size across a face or an edge */
 } gs_stats;
 
 typedef struct {
@@ -122,6 +137,7 @@ typedef struct {
                                child; the other reading of eq childtensor; FP64 form only) */
     int decision_order;     /* GS_ORDER_BOUNDS_FIRST (default) or GS_ORDER_LITERAL (FP64 form only) */
     int precision_norm;     /* GS_NORM_SUM (default), GS_NORM_MAX or GS_NORM_RSS (FP64 form only) */
+    int conform_mode;       /* cubes of different sizes: GS_CONFORM_CONSTRAIN (default) or GS_CONFORM_EQUAL */
 } gs_options;
 
 typedef struct {

@@ -36,7 +36,8 @@ class Stats(ctypes.Structure):
                 ("recheck_precision", ctypes.c_int64), ("recheck_zero", ctypes.c_int64),
                 ("mixed_err_ratio", ctypes.c_double), ("mixed_band_ratio", ctypes.c_double),
                 ("recheck_rank", ctypes.c_int64), ("vertex_mark_cubes", ctypes.c_int64 * 3),
-                ("estimate_fast_cubes", ctypes.c_int64)]
+                ("estimate_fast_cubes", ctypes.c_int64), ("constrained_vertices", ctypes.c_int64),
+                ("agreement_splits", ctypes.c_int64), ("mixed_cubes", ctypes.c_int64)]
 
     def as_dict(self, max_depth=20):
         d = {}
@@ -53,7 +54,7 @@ class Options(ctypes.Structure):
     _fields_ = [("min_edge", ctypes.c_double), ("precision_mode", ctypes.c_int), ("cutoff_rel", ctypes.c_double),
                 ("cuda_stream", ctypes.c_void_p), ("device_output", ctypes.c_int), ("debug_flags", ctypes.c_int),
                 ("stats", ctypes.POINTER(Stats)), ("child_mode", ctypes.c_int),
-                ("decision_order", ctypes.c_int), ("precision_norm", ctypes.c_int)]
+                ("decision_order", ctypes.c_int), ("precision_norm", ctypes.c_int), ("conform_mode", ctypes.c_int)]
 
 
 class MeshBuffers(ctypes.Structure):
@@ -193,12 +194,13 @@ def _mesh_from_c(m, L, stats, max_depth):
 GS_CHILD_REPROJECT, GS_CHILD_REEXPAND = 0, 1
 GS_ORDER_BOUNDS_FIRST, GS_ORDER_LITERAL = 0, 1
 GS_NORM_SUM, GS_NORM_MAX, GS_NORM_RSS = 0, 1, 2
+GS_CONFORM_CONSTRAIN, GS_CONFORM_EQUAL = 0, 1
 
 
 def mesh_gaussian_surface(atoms, radii, D, c, precision, max_depth, min_edge=0.25, precision_mode=GS_PREC_FP64,
                           cutoff_rel=1e-8, stream=None, debug_flags=0, device_output=False,
                           child_mode=GS_CHILD_REPROJECT, decision_order=GS_ORDER_BOUNDS_FIRST,
-                          precision_norm=GS_NORM_SUM):
+                          precision_norm=GS_NORM_SUM, conform_mode=GS_CONFORM_CONSTRAIN):
     """Mesh {phi = c}; see include/gsmesh.h.  With device_output the mesh
     stays in device memory and only its sizes and stats are returned (the
     arrays are released)."""
@@ -217,6 +219,7 @@ def mesh_gaussian_surface(atoms, radii, D, c, precision, max_depth, min_edge=0.2
     o.child_mode = child_mode
     o.decision_order = decision_order
     o.precision_norm = precision_norm
+    o.conform_mode = conform_mode
     o.stats = ctypes.pointer(st)
     m = MeshC()
     rc = L.mesh_gaussian_surface(_ptr(atoms), _ptr(radii), n, D, c, precision, max_depth, ctypes.byref(o),

@@ -16,7 +16,7 @@ LIB = os.path.join(BUILD, "libgsmesh.so")
 INCLUDE = os.path.join(os.path.dirname(HERE), "include")
 
 # geometric predicates of the triangulation round every product and sum once
-PER_FILE_FLAGS = {"gs_tri.cu": ["-fmad=false"]}
+PER_FILE_FLAGS = {"gs_tri.cu": ["-fmad=false"], "gs_cons.cu": ["-fmad=false"]}
 
 NVCC_FLAGS = ["-gencode", "arch=compute_103a,code=sm_103a", "-O3", "-lineinfo", "-std=c++17",
               "--extended-lambda", "-Xcompiler", "-fPIC", "-I", INCLUDE]

@@ -108,8 +108,16 @@ struct DevBufs {
     void keep(void *p) { if (p) ptrs.push_back(p); }
     void release(void *p)
     {
+        if (!p) return;
         for (auto &q : ptrs)
             if (q == p) { gs_free(q, st); q = nullptr; }
+    }
+    // stop tracking p without freeing it (a callee frees or replaces it)
+    void forget(void *p)
+    {
+        if (!p) return;
+        for (auto &q : ptrs)
+            if (q == p) q = nullptr;
     }
     ~DevBufs()
     {
@@ -444,9 +452,16 @@ static int finish_into(MeshDev &M, gs_mesh_buffers *b, cudaStream_t st)
 
 // triangulate the final cubes given lattice vertex values; shared by the
 // molecule path and the grid entry point
+// cubes of different sizes in the final set (constrained vertex values)
+struct MixInfo {
+    const uint8_t *mixed;       // per cube, or null when no cube has a neighbour of another size
+    GsHash hc, hv;              // cube key -> index; lattice-vertex key -> slot
+    const uint64_t *vslot_id;   // slot -> lattice vertex id
+};
+
 static int surface_from_values(const GsProblem &P, const uint64_t *d_cubes, int64_t nc, const int32_t *d_cvid,
                                const double *d_phi, DevBufs &B, unsigned *d_status, unsigned long long *d_tcount,
-                               MeshDev &M, gs_stats *stats, Timer &T)
+                               MeshDev &M, gs_stats *stats, Timer &T, const MixInfo *mx = nullptr)
 {
     cudaStream_t st = B.st;
     int t0 = T.mark();
@@ -455,6 +470,9 @@ static int surface_from_values(const GsProblem &P, const uint64_t *d_cubes, int6
     if (rc) return rc;
     B.keep(nbr);
     TriCtx X;
+    if (mx && mx->mixed) {
+        X.mixed = mx->mixed; X.hc = mx->hc; X.hv = mx->hv; X.vslot_id = mx->vslot_id;
+    }
     X.cubes = d_cubes; X.cvid = d_cvid; X.nbr = nbr; X.phi = d_phi; X.ncubes = nc; X.c = P.c;
     for (int a = 0; a < 3; a++) X.origin[a] = P.origin[a];
     X.min_edge = P.min_edge; X.max_depth = P.max_depth;
@@ -601,52 +619,121 @@ static int mesh_impl(const double *atoms, const double *radii, int64_t n, double
     }
     int tl1 = T.mark();
 
-    // ---- conformity across faces and edges (section 2.3, neighbouring cubes):
-    // a cube is split only next to a finer one, so with every accepted cube
-    // on one level there is nothing to do
-    int64_t splits = 0;
+    // ---- cubes of different sizes (section 2.3, the points of neighbouring
+    // cubes inside the current cube): with every accepted cube on one level
+    // there is nothing to do
+    int64_t splits = 0, agree_splits = 0;
     int acc_levels = 0;
     for (int l = 0; l <= max_depth; l++) acc_levels += (stats->accepted[l] + stats->forced[l]) > 0 ? 1 : 0;
-    if (acc_levels > 1) rc = gs_conformity(&cubes, &nc, max_depth, &splits, d_status, st);
-    B.keep(cubes);
-    if (rc) return rc;
+    const bool constrain = acc_levels > 1 && o.conform_mode == GS_CONFORM_CONSTRAIN;
+    if (acc_levels > 1) rc = gs_conformity(&cubes, &nc, max_depth, constrain ? 2 : 1, &splits, d_status, st);
+    if (rc) { gs_free(cubes, st); return rc; }
     int tc1 = T.mark();
 
-    // ---- lattice vertices and the field there (eq linear1's corner values)
+    // ---- lattice vertices, the field there (eq linear1's corner values)
+    // and, for cubes of different sizes, the constrained values; a sign
+    // disagreement splits the coarser cubes and the whole is rebuilt
     uint64_t *vkeys = nullptr;
     int32_t *cvid = nullptr;
     int64_t nv = 0;
-    rc = gs_lattice_vertices(cubes, nc, max_depth, &vkeys, &nv, &cvid, d_status, st);
-    B.keep(vkeys); B.keep(cvid);
-    if (rc) return rc;
     double *phi = nullptr;
-    rc = B.get(&phi, (size_t)nv + 1);
-    if (rc) return rc;
-    if (o.precision_mode == GS_PREC_FP64) {
-        rc = gs_field_f64(P, vkeys, nullptr, nv, phi, nullptr, d_cnt + 9, st);
-    } else {
-        // FP32 values; FP64 where the inside test, a surface point's position
-        // (first-order bound 8e-6 A) or a face or fold decision could depend on
-        // the FP32 error:
-        // first the values near c, then, with those exact, the sensitive corners
-        float *err = nullptr;
-        int64_t *mark = nullptr;
-        rc = B.get(&err, (size_t)nv + 1);
-        if (!rc) rc = B.get(&mark, (size_t)nv + 1);
-        if (!rc) rc = gs_field_f32_marked(P, vkeys, nv, phi, err, mark, d_cnt + 9, st);
-        int64_t nre = 0, nre2 = 0;
-        if (!rc) rc = gs_field_recompute(P, vkeys, nv, mark, phi, err, &nre, st);
-        if (!rc) {
-            GS_CHECK(cudaMemsetAsync(mark, 0, sizeof(int64_t) * (size_t)(nv + 1), st));
-            TriCtx X;
-            memset(&X, 0, sizeof(X));
-            X.cubes = cubes; X.cvid = cvid; X.phi = phi; X.ncubes = nc; X.c = P.c;
-            for (int a3 = 0; a3 < 3; a3++) X.origin[a3] = P.origin[a3];
-            X.min_edge = P.min_edge; X.max_depth = P.max_depth;
-            rc = gs_tri_marks(X, err, 8e-6, mark, d_cnt + 21, st);
+    float *err = nullptr;
+    int64_t *mark = nullptr;
+    GsHash hv{nullptr, nullptr, 0}, hc{nullptr, nullptr, 0};
+    uint64_t *vslot = nullptr;
+    GsCons K{nullptr, nullptr, nullptr, 0, 0};
+    uint8_t *mixed = nullptr;
+    int64_t n_mixed = 0, nre = 0;
+    auto release_round = [&]() {
+        B.release(vkeys); B.release(cvid); B.release(phi); B.release(err); B.release(mark);
+        B.release(hv.keys); B.release(hv.vals); B.release(vslot); B.release(hc.keys); B.release(hc.vals);
+        B.release(K.lev); B.release(K.src); B.release(K.t); B.release(mixed);
+        vkeys = nullptr; cvid = nullptr; phi = nullptr; err = nullptr; mark = nullptr; vslot = nullptr;
+        hv = GsHash{nullptr, nullptr, 0}; hc = GsHash{nullptr, nullptr, 0};
+        K = GsCons{nullptr, nullptr, nullptr, 0, 0}; mixed = nullptr;
+    };
+    B.keep(cubes);
+    for (int iter = 0;; iter++) {
+        if (iter > 64) return gs_fail(GS_ERR_CAPACITY, "cube sizes did not settle");
+        rc = gs_lattice_vertices(cubes, nc, max_depth, &vkeys, &nv, &cvid, d_status, st, constrain ? &hv : nullptr,
+                                 constrain ? &vslot : nullptr);
+        B.keep(vkeys); B.keep(cvid); B.keep(hv.keys); B.keep(hv.vals); B.keep(vslot);
+        if (rc) return rc;
+        rc = B.get(&phi, (size_t)nv + 1);
+        if (rc) return rc;
+        if (o.precision_mode == GS_PREC_FP64) {
+            rc = gs_field_f64(P, vkeys, nullptr, nv, phi, nullptr, d_cnt + 9, st);
+        } else {
+            // FP32 values; FP64 where the inside test could depend on the FP32 error
+            rc = B.get(&err, (size_t)nv + 1);
+            if (!rc) rc = B.get(&mark, (size_t)nv + 1);
+            if (!rc) rc = gs_field_f32_marked(P, vkeys, nv, phi, err, mark, d_cnt + 9, st);
+            int64_t n1 = 0;
+            if (!rc) rc = gs_field_recompute(P, vkeys, nv, mark, phi, err, &n1, st);
+            nre += n1;
         }
-        if (!rc) rc = gs_field_recompute(P, vkeys, nv, mark, phi, err, &nre2, st);
-        nre += nre2;
+        if (rc) return rc;
+        if (!constrain) break;
+        rc = gs_hash_make(&hc, nc, st);
+        if (rc) return rc;
+        B.keep(hc.keys); B.keep(hc.vals);
+        GS_LAUNCH(k_hash_index, (unsigned)((nc + 255) / 256), 256, 0, st)(hc, cubes, nc, d_status);
+        rc = gs_cons_alloc(&K, nv, st);
+        if (rc) return rc;
+        B.keep(K.lev); B.keep(K.src); B.keep(K.t);
+        if (mark) GS_CHECK(cudaMemsetAsync(mark, 0, sizeof(int64_t) * (size_t)(nv + 1), st));
+        rc = gs_cons_find(&K, hc, hv, vslot, vkeys, max_depth, mark, d_cnt + 26, d_status, st);
+        if (!rc && mark) {
+            // the constrained values and their sources in FP64: exact interpolants
+            int64_t n1 = 0;
+            rc = gs_field_recompute(P, vkeys, nv, mark, phi, err, &n1, st);
+            nre += n1;
+        }
+        int64_t *split = nullptr;
+        if (!rc) rc = B.get(&split, (size_t)nc + 1);
+        if (!rc) rc = gs_fill_i64(split, nc, 1, st);
+        int64_t nflip = 0;
+        if (!rc) rc = gs_cons_apply(K, hc, vkeys, max_depth, P.c, phi, split, &nflip, d_cnt + 27, st);
+        if (!rc) rc = check_status(d_status, st, "constrained values");
+        if (rc) return rc;
+        if (nflip > 0) {
+            int64_t ns = 0, ns2 = 0;
+            B.forget(cubes);   // replaced (and freed) by the split
+            rc = gs_split_counted(&cubes, &nc, split, &ns, st);
+            B.release(split);
+            if (!rc) rc = gs_conformity(&cubes, &nc, max_depth, 2, &ns2, d_status, st);
+            B.keep(cubes);
+            if (rc) return rc;
+            agree_splits += ns;
+            splits += ns2;
+            release_round();
+            continue;
+        }
+        B.release(split);
+        rc = B.get(&mixed, (size_t)nc + 1);
+        if (!rc) rc = gs_mixed_flags(K, cubes, nc, cvid, hv, vslot, max_depth, mixed, &n_mixed, d_cnt + 28, st);
+        if (rc) return rc;
+        break;
+    }
+    stats->constrained_vertices = K.ncons;
+    stats->agreement_splits = agree_splits;
+    stats->mixed_cubes = n_mixed;
+    if (o.precision_mode == GS_PREC_MIXED) {
+        // FP64 where a surface point's position (first-order bound 8e-6 A)
+        // or a face or fold decision could depend on the FP32 error; every
+        // corner of a cube with neighbours of another size
+        GS_CHECK(cudaMemsetAsync(mark, 0, sizeof(int64_t) * (size_t)(nv + 1), st));
+        TriCtx X;
+        memset(&X, 0, sizeof(X));
+        X.cubes = cubes; X.cvid = cvid; X.phi = phi; X.ncubes = nc; X.c = P.c;
+        for (int a3 = 0; a3 < 3; a3++) X.origin[a3] = P.origin[a3];
+        X.min_edge = P.min_edge; X.max_depth = P.max_depth;
+        X.mixed = n_mixed > 0 ? mixed : nullptr;
+        rc = gs_tri_marks(X, err, 8e-6, mark, d_cnt + 21, st);
+        if (!rc && constrain) rc = gs_cons_unmark(K, mark, st);
+        int64_t n2 = 0;
+        if (!rc) rc = gs_field_recompute(P, vkeys, nv, mark, phi, err, &n2, st);
+        nre += n2;
         stats->recheck_vertices = nre;
     }
     if (rc) return rc;
@@ -656,7 +743,8 @@ static int mesh_impl(const double *atoms, const double *radii, int64_t n, double
     MeshDev M;
     M.cubes = cubes;
     M.nc = nc;
-    rc = surface_from_values(P, cubes, nc, cvid, phi, B, d_status, d_cnt + 10, M, stats, T);
+    MixInfo mx{n_mixed > 0 ? mixed : nullptr, hc, hv, vslot};
+    rc = surface_from_values(P, cubes, nc, cvid, phi, B, d_status, d_cnt + 10, M, stats, T, &mx);
     if (rc) return rc;
     int tw1 = T.mark();
     if (bw) {
@@ -683,6 +771,8 @@ static int mesh_impl(const double *atoms, const double *radii, int64_t n, double
         for (int a3 = 0; a3 < 3; a3++) X.origin[a3] = P.origin[a3];
         X.min_edge = P.min_edge; X.max_depth = P.max_depth;
         rc = gs_vertex_adjoint(X, vkeys, nv, M.vkeys, gv, M.nv, lambda, d_status, st);
+        // a constrained value passes its adjoint on to the corners it interpolates
+        if (!rc && constrain) rc = gs_cons_adjoint(K, max_depth, lambda, st);
         if (!rc) rc = gs_field_adjoint(P, PR.perm, vkeys, lambda, nv, g, g + 3 * n, g + 4 * n, st);
         if (!rc) rc = check_status(d_status, st, "adjoint");
         if (!rc && bw->g_atoms) rc = put_out(bw->g_atoms, g, sizeof(double) * 3 * (size_t)n, st);
@@ -753,6 +843,8 @@ static int check_mesh_args(const double *atoms, const double *radii, int64_t n_a
         return gs_fail(GS_ERR_ARG, "unknown decision order");
     if (o.precision_norm != GS_NORM_SUM && o.precision_norm != GS_NORM_MAX && o.precision_norm != GS_NORM_RSS)
         return gs_fail(GS_ERR_ARG, "unknown precision norm");
+    if (o.conform_mode != GS_CONFORM_CONSTRAIN && o.conform_mode != GS_CONFORM_EQUAL)
+        return gs_fail(GS_ERR_ARG, "unknown conform mode");
     if ((o.decision_order != GS_ORDER_BOUNDS_FIRST || o.precision_norm != GS_NORM_SUM) &&
         o.precision_mode != GS_PREC_FP64)
         return gs_fail(GS_ERR_ARG, "the alternative decision order and norms are implemented in the FP64 form only");

@@ -65,12 +65,46 @@ int gs_root_blocks(const GsProblem &P, uint64_t **d_keys, int64_t *n, cudaStream
 // gs_mesh.cu
 int gs_hash_make(GsHash *H, int64_t n, cudaStream_t st);
 void gs_hash_free(GsHash *H, cudaStream_t st);
-int gs_conformity(uint64_t **d_cubes, int64_t *n, int max_depth, int64_t *splits, unsigned *d_status, cudaStream_t st);
+// min_gap: split a cube that touches one at least this many levels finer
+int gs_conformity(uint64_t **d_cubes, int64_t *n, int max_depth, int min_gap, int64_t *splits, unsigned *d_status,
+                  cudaStream_t st);
+int gs_split_counted(uint64_t **d_cubes, int64_t *n, int64_t *cnt, int64_t *splits, cudaStream_t st);
+// keep_hash (nullable): the key -> slot table of the vertices is handed over
+// (free with gs_hash_free), with *keep_slot_id mapping a slot to the vertex id
 int gs_lattice_vertices(const uint64_t *d_cubes, int64_t n, int max_depth, uint64_t **d_vkeys, int64_t *nv,
-                        int32_t **d_cvid, unsigned *d_status, cudaStream_t st);
-int gs_neighbours(const uint64_t *d_cubes, int64_t n, int32_t **d_nbr, unsigned *d_status, cudaStream_t st);
+                        int32_t **d_cvid, unsigned *d_status, cudaStream_t st, GsHash *keep_hash = nullptr,
+                        uint64_t **keep_slot_id = nullptr);
+// keep_hash (nullable): the cube key -> index table is handed over
+int gs_neighbours(const uint64_t *d_cubes, int64_t n, int32_t **d_nbr, unsigned *d_status, cudaStream_t st,
+                  GsHash *keep_hash = nullptr);
 int gs_weld(const uint64_t *d_pk, const double *d_pxyz, int64_t npt, const uint64_t *d_tk, int64_t ntri,
             uint64_t **d_vkeys, double **d_vxyz, int64_t *nv, int32_t **d_tri, unsigned *d_status, cudaStream_t st);
+
+// gs_cons.cu: constrained vertex values for cubes of different sizes
+struct GsCons {
+    int8_t *lev;     // [nv] level of the constraining face or edge, -1 free
+    int32_t *src;    // [nv][4] source vertex ids (-1 unused)
+    double *t;       // [nv][2] fractions along the edge, or along the face's axes
+    int64_t nv;
+    int64_t ncons;   // constrained vertices (after gs_cons_find)
+};
+int gs_cons_alloc(GsCons *K, int64_t nv, cudaStream_t st);
+void gs_cons_free(GsCons *K, cudaStream_t st);
+// d_mark (nullable): marks every constrained vertex and its sources;
+// d_scratch: one device counter
+int gs_cons_find(GsCons *K, const GsHash &hc, const GsHash &hv, const uint64_t *d_slot_id, const uint64_t *d_vkeys,
+                 int md, int64_t *d_mark, unsigned long long *d_scratch, unsigned *d_status, cudaStream_t st);
+// replaces the constrained values in d_phi (coarse to fine); with d_split
+// (n + 1 entries per cube, preset to 1) counts the sign disagreements and sets
+// 8 for the cubes to split
+int gs_cons_apply(const GsCons &K, const GsHash &hc, const uint64_t *d_vkeys, int md, double c, double *d_phi,
+                  int64_t *d_split, int64_t *n_flip, unsigned long long *d_scratch, cudaStream_t st);
+int gs_mixed_flags(const GsCons &K, const uint64_t *d_cubes, int64_t n, const int32_t *d_cvid, const GsHash &hv,
+                   const uint64_t *d_slot_id, int md, uint8_t *d_mixed, int64_t *n_mixed,
+                   unsigned long long *d_scratch, cudaStream_t st);
+int gs_cons_unmark(const GsCons &K, int64_t *d_mark, cudaStream_t st);
+int gs_cons_adjoint(const GsCons &K, int md, double *d_lambda, cudaStream_t st);
+int gs_fill_i64(int64_t *d_a, int64_t n, int64_t v, cudaStream_t st);
 
 // gs_tri.cu
 struct TriCtx {
@@ -87,6 +121,13 @@ struct TriCtx {
     // fcount[4 ci + a] roots of axis a at froot[12 ci + 4 a + 2 r + (0: u, 1: v)]
     const uint8_t *fcount = nullptr;
     const double *froot = nullptr;
+    // cubes of different sizes: per-cube flag of a mixed-size contact (null:
+    // all cubes that share a face or an edge have one size), the cube key ->
+    // index table and the lattice-vertex key -> slot table with slot -> id
+    const uint8_t *mixed = nullptr;
+    GsHash hc{nullptr, nullptr, 0};
+    GsHash hv{nullptr, nullptr, 0};
+    const uint64_t *vslot_id = nullptr;
 };
 // mixed precision: mark (mark[v] = 1) the corners whose FP32 error could move
 // a surface point by more than tol_A or flip a face or fold decision

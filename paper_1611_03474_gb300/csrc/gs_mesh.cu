@@ -1,9 +1,12 @@
 // gs_mesh.cu -- hash-table passes around the triangulation:
-//   * conformity: an accepted cube touching a finer accepted cube along a
-//     face or an edge is split into 8 accepted children until no such
-//     contact remains (the paper's rule that points of neighbouring cubes
-//     inside the current cube are considered, section 2.3, realised by
-//     equalising sizes across every shared face and edge);
+//   * conformity for cubes of different sizes (section 2.3: points of the
+//     neighbouring cubes inside the current cube are considered): an
+//     accepted cube touching, along a face or an edge, a cube at least
+//     min_gap levels finer is split into 8 accepted children until no such
+//     contact remains (min_gap 2: at most one level between cubes sharing a
+//     face or an edge, whose points the constrained vertex values of
+//     gs_cons.cu then join; min_gap 1: one size across every shared face and
+//     edge);
 //   * lattice vertices of the accepted cubes with deterministic ids (owner =
 //     smallest (cube, corner) index, then a prefix sum in cube order);
 //   * same-size face neighbours of each cube;
@@ -53,10 +56,10 @@ __global__ void k_hash_index(GsHash H, const uint64_t *keys, int64_t n, unsigned
 }
 
 // ---------------------------------------------------------------- conformity
-// Each accepted cube F marks every coarser accepted cube C that contains one
-// of F's 18 face or edge neighbour cells: exactly the cubes that touch a
-// finer accepted cube along a face or an edge.
-__global__ void k_conform_mark(GsHash H, const uint64_t *cubes, int64_t n, int64_t *cnt)
+// Each accepted cube F marks every accepted cube C at least min_gap levels
+// coarser that contains one of F's 18 face or edge neighbour cells: exactly
+// the cubes that touch a cube that much finer along a face or an edge.
+__global__ void k_conform_mark(GsHash H, const uint64_t *cubes, int64_t n, int64_t *cnt, int min_gap)
 {
     int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= n) return;
@@ -70,7 +73,7 @@ __global__ void k_conform_mark(GsHash H, const uint64_t *cubes, int64_t n, int64
         if (nz_ == 0 || nz_ == 3) continue;
         int64_t X = x + dx, Y = y + dy, Z = z + dz;
         if (X < 0 || Y < 0 || Z < 0) continue;
-        for (int l = lf - 1; l >= 0; l--) {
+        for (int l = lf - min_gap; l >= 0; l--) {
             int sh = lf - l;
             int64_t s = gs_hash_find(H, gk_make(X >> sh, Y >> sh, Z >> sh, GT_CUBE, (unsigned)l));
             if (s >= 0) {
@@ -99,10 +102,44 @@ __global__ void k_conform_emit(const uint64_t *cubes, int64_t n, const int64_t *
     for (int c = 0; c < 8; c++) out[o + c] = gk_make(2 * x + (c & 1), 2 * y + ((c >> 1) & 1), 2 * z + (c >> 2), GT_CUBE, l);
 }
 
+// cnt[i] = 8 splits cube i into its children, 1 keeps it (n + 1 entries,
+// scanned in place); in/out: *d_cubes (replaced when any cube splits), *n
+int gs_split_counted(uint64_t **d_cubes, int64_t *n, int64_t *cnt, int64_t *splits, cudaStream_t st)
+{
+    const int64_t m = *n;
+    *splits = 0;
+    if (m == 0) return GS_OK;
+    int64_t *tot = nullptr;
+    int rc = gs_alloc((void **)&tot, sizeof(int64_t), st);
+    if (rc) return rc;
+    cudaMemsetAsync(cnt + m, 0, sizeof(int64_t), st);
+    rc = gs_scan_i64(cnt, m + 1, tot, st);
+    int64_t total = 0;
+    if (!rc) {
+        cudaError_t e = cudaMemcpyAsync(&total, tot, sizeof(int64_t), cudaMemcpyDeviceToHost, st);
+        if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+        if (e != cudaSuccess) rc = gs_fail_cuda(e, "split count", __FILE__, __LINE__);
+    }
+    gs_free(tot, st);
+    if (rc || total == m) return rc;
+    uint64_t *out = nullptr;
+    rc = gs_alloc((void **)&out, sizeof(uint64_t) * (size_t)total, st);
+    if (rc) return rc;
+    GS_LAUNCH(k_conform_emit, (unsigned)((m + 255) / 256), 256, 0, st)(*d_cubes, m, cnt, out);
+    gs_free(*d_cubes, st);
+    *d_cubes = out;
+    *splits = (total - m) / 7;
+    *n = total;
+    GS_CHECK(cudaGetLastError());
+    return GS_OK;
+}
+
 // in/out: *d_cubes (replaced when split), *n
-int gs_conformity(uint64_t **d_cubes, int64_t *n, int max_depth, int64_t *splits, unsigned *d_status, cudaStream_t st)
+int gs_conformity(uint64_t **d_cubes, int64_t *n, int max_depth, int min_gap, int64_t *splits, unsigned *d_status,
+                  cudaStream_t st)
 {
     *splits = 0;
+    (void)max_depth;
     for (int pass = 0; pass < 64; pass++) {
         int64_t m = *n;
         if (m == 0) return GS_OK;
@@ -117,25 +154,15 @@ int gs_conformity(uint64_t **d_cubes, int64_t *n, int max_depth, int64_t *splits
         if (rc) { gs_hash_free(&H, st); gs_free(cnt, st); return rc; }
         cudaMemsetAsync(cnt + m, 0, sizeof(int64_t), st);
         GS_LAUNCH(k_fill_one, nb, 256, 0, st)(cnt, m);
-        GS_LAUNCH(k_conform_mark, nb, 256, 0, st)(H, *d_cubes, m, cnt);
+        GS_LAUNCH(k_conform_mark, nb, 256, 0, st)(H, *d_cubes, m, cnt, min_gap);
         gs_hash_free(&H, st);
-        rc = gs_scan_i64(cnt, m + 1, tot, st);
-        int64_t total = 0;
-        if (!rc) {
-            cudaError_t e = cudaMemcpyAsync(&total, tot, sizeof(int64_t), cudaMemcpyDeviceToHost, st);
-            if (e == cudaSuccess) e = cudaStreamSynchronize(st);
-            if (e != cudaSuccess) rc = gs_fail_cuda(e, "conformity count", __FILE__, __LINE__);
-        }
-        if (rc || total == m) { gs_free(cnt, st); gs_free(tot, st); return rc; }
-        uint64_t *out = nullptr;
-        rc = gs_alloc((void **)&out, sizeof(uint64_t) * (size_t)total, st);
-        if (rc) { gs_free(cnt, st); gs_free(tot, st); return rc; }
-        GS_LAUNCH(k_conform_emit, nb, 256, 0, st)(*d_cubes, m, cnt, out);
-        gs_free(cnt, st); gs_free(tot, st);
-        gs_free(*d_cubes, st);
-        *d_cubes = out;
-        *splits += (total - m) / 7;
-        *n = total;
+        gs_free(tot, st);
+        int64_t ns = 0;
+        rc = gs_split_counted(d_cubes, n, cnt, &ns, st);
+        gs_free(cnt, st);
+        if (rc) return rc;
+        if (ns == 0) return GS_OK;
+        *splits += ns;
     }
     return gs_fail(GS_ERR_CAPACITY, "conformity did not converge");
 }
@@ -200,9 +227,11 @@ __global__ void k_vert_cvid(int64_t n, const int64_t *slot, const uint64_t *slot
 }
 
 int gs_lattice_vertices(const uint64_t *d_cubes, int64_t n, int max_depth, uint64_t **d_vkeys, int64_t *nv,
-                        int32_t **d_cvid, unsigned *d_status, cudaStream_t st)
+                        int32_t **d_cvid, unsigned *d_status, cudaStream_t st, GsHash *keep_hash,
+                        uint64_t **keep_slot_id)
 {
     *d_vkeys = nullptr; *d_cvid = nullptr; *nv = 0;
+    if (keep_hash) { keep_hash->keys = keep_hash->vals = nullptr; keep_hash->mask = 0; *keep_slot_id = nullptr; }
     if (n <= 0) return GS_OK;
     int64_t m = n * 8;
     GsHash H;
@@ -233,8 +262,15 @@ int gs_lattice_vertices(const uint64_t *d_cubes, int64_t n, int max_depth, uint6
         GS_LAUNCH(k_vert_write, nb, 256, 0, st)(d_cubes, n, max_depth, flag, slot, *d_vkeys, slot_id);
         GS_LAUNCH(k_vert_cvid, nb, 256, 0, st)(n, slot, slot_id, *d_cvid);
     }
-    gs_free(flag, st); gs_free(tot, st); gs_free(slot, st); gs_free(slot_id, st);
-    gs_hash_free(&H, st);
+    gs_free(flag, st); gs_free(tot, st); gs_free(slot, st);
+    if (!rc && keep_hash) {
+        // key -> slot stays; slot -> vertex id through slot_id
+        *keep_hash = H;
+        *keep_slot_id = slot_id;
+    } else {
+        gs_free(slot_id, st);
+        gs_hash_free(&H, st);
+    }
     if (rc) { gs_free(*d_vkeys, st); gs_free(*d_cvid, st); *d_vkeys = nullptr; *d_cvid = nullptr; return rc; }
     GS_CHECK(cudaGetLastError());
     *nv = total;
@@ -259,9 +295,11 @@ __global__ void k_neighbours(GsHash H, const uint64_t *cubes, int64_t n, int32_t
     nbr[t] = r;
 }
 
-int gs_neighbours(const uint64_t *d_cubes, int64_t n, int32_t **d_nbr, unsigned *d_status, cudaStream_t st)
+int gs_neighbours(const uint64_t *d_cubes, int64_t n, int32_t **d_nbr, unsigned *d_status, cudaStream_t st,
+                  GsHash *keep_hash)
 {
     *d_nbr = nullptr;
+    if (keep_hash) { keep_hash->keys = keep_hash->vals = nullptr; keep_hash->mask = 0; }
     if (n <= 0) return GS_OK;
     GsHash H;
     int rc = gs_hash_make(&H, n, st);
@@ -269,7 +307,8 @@ int gs_neighbours(const uint64_t *d_cubes, int64_t n, int32_t **d_nbr, unsigned 
     GS_LAUNCH(k_hash_index, (unsigned)((n + 255) / 256), 256, 0, st)(H, d_cubes, n, d_status);
     rc = gs_alloc((void **)d_nbr, sizeof(int32_t) * 6 * (size_t)n, st);
     if (!rc) GS_LAUNCH(k_neighbours, (unsigned)((6 * n + 255) / 256), 256, 0, st)(H, d_cubes, n, *d_nbr);
-    gs_hash_free(&H, st);
+    if (!rc && keep_hash) *keep_hash = H;
+    else gs_hash_free(&H, st);
     if (rc) return rc;
     GS_CHECK(cudaGetLastError());
     return GS_OK;

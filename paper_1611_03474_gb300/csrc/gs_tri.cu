@@ -26,7 +26,9 @@
 // exactly degenerate configurations are recognised as such.
 #include "gs_host.cuh"
 
-#define TP_MAX 48
+#define TP_MAX 48      // points of a cube whose neighbours across faces and edges have its size
+#define TP_MIX 64      // points of a cube with neighbours of another size
+#define FP_MIX 20      // points inserted into one face curve (another size)
 #define POLY_MAX 96
 
 struct TPt {
@@ -238,7 +240,7 @@ __device__ void clip_piece(const TPt *pts, const float (*pf)[3], const unsigned 
     // 1.8e-7 and each product by 1.8e-7 times the other factor; when the
     // FP32 value exceeds that bound (with margin) its sign is the exact sign
     // and the FP64 predicate's.  Otherwise the FP64 predicate decides.
-    float qa[TP_MAX], qb[TP_MAX];
+    float qa[TP_MIX], qb[TP_MIX];
     for (int i = 0; i < n; i++) {
         qa[poly[i]] = pf[poly[i]][ia];
         qb[poly[i]] = pf[poly[i]][ib];
@@ -278,9 +280,10 @@ __device__ void clip_piece(const TPt *pts, const float (*pf)[3], const unsigned 
     if (m == 3 && v[0] != v[1] && v[1] != v[2] && v[0] != v[2]) put_tri(o, pts[v[0]].key, pts[v[1]].key, pts[v[2]].key);
 }
 
+template <int CAP>
 __device__ __forceinline__ int64_t add_pt(TPt *pts, int &np, int kind)
 {
-    if (np >= TP_MAX) return -1;
+    if (np >= CAP) return -1;
     TPt &p = pts[np];
     p.kind = (signed char)kind;
     p.nb[0] = p.nb[1] = p.nb[2] = p.nb[3] = -1;
@@ -288,9 +291,172 @@ __device__ __forceinline__ int64_t add_pt(TPt *pts, int &np, int kind)
     return np++;
 }
 
-// returns 0 on success, 1 on an inconsistency (cube skipped)
+// world coordinate at fraction f of the level-lvl edge starting at lattice
+// index i on axis a (the index's lattice coordinate when f is 0 or 1)
+__device__ __forceinline__ double wfrac(const TriCtx &X, int a, int64_t i, int lvl, double f)
+{
+    const int64_t s = (int64_t)1 << (X.max_depth - lvl);
+    const double lo = __dadd_rn(X.origin[a], __dmul_rn((double)(i * s), X.min_edge));
+    if (f == 0.0) return lo;
+    if (f == 1.0) return __dadd_rn(X.origin[a], __dmul_rn((double)((i + 1) * s), X.min_edge));
+    return __dadd_rn(lo, __dmul_rn(f, ldexp(X.min_edge, X.max_depth - lvl)));
+}
+// world coordinate of finest-lattice index L on axis a
+__device__ __forceinline__ double wlat(const TriCtx &X, int a, int64_t L)
+{
+    return __dadd_rn(X.origin[a], __dmul_rn((double)L, X.min_edge));
+}
+__device__ __forceinline__ int64_t tri_vert(const TriCtx &X, int64_t x, int64_t y, int64_t z)
+{
+    if (x < 0 || y < 0 || z < 0) return -1;
+    const int64_t s = gs_hash_find(X.hv, gk_make((uint64_t)x, (uint64_t)y, (uint64_t)z, GT_VERT, 0));
+    return s < 0 ? -1 : (int64_t)X.vslot_id[s];
+}
+__device__ __forceinline__ int64_t tri_cube_at(const TriCtx &X, int64_t x, int64_t y, int64_t z, int lvl)
+{
+    if (x < 0 || y < 0 || z < 0) return -1;
+    const int64_t s = gs_hash_find(X.hc, gk_make((uint64_t)x, (uint64_t)y, (uint64_t)z, GT_CUBE, (unsigned)lvl));
+    return s < 0 ? -1 : (int64_t)X.hc.vals[s];
+}
+// fold roots of axis a of cube q (from the table when there is one)
+__device__ __forceinline__ int cube_fold_roots(const TriCtx &X, int64_t q, int a, double *ru, double *rv)
+{
+    if (X.fcount) {
+        const int nn = X.fcount[q * 4 + a];
+        for (int r = 0; r < nn; r++) {
+            ru[r] = X.froot[q * 12 + 4 * a + 2 * r];
+            rv[r] = X.froot[q * 12 + 4 * a + 2 * r + 1];
+        }
+        return nn;
+    }
+    double gq[8];
+    for (int v = 0; v < 8; v++) gq[v] = X.phi[X.cvid[q * 8 + v]];
+    return fold_solve(gq, a, X.c, ru, rv);
+}
+
+// Points across face (a, sd) of cube C (level lvl) that has no neighbour of
+// its own size there: the finer neighbours' fold ends and inner half-line
+// points, or the coarser neighbour's fold ends inside this face.  All of
+// them lie on this face's level curve (constrained vertex values make the
+// finer faces' and this face's values one bilinear function).  Returns 1 on
+// an inconsistency.
+__device__ __noinline__ int tri_mixed_face(const TriCtx &X, const int64_t *C, int lvl, int a, int sd, bool fine_ok,
+                                           TPt *pts, double (*pw)[3], int &np, signed char *fp, int &nfp)
+{
+    int ua, va;
+    axes_other(a, ua, va);
+    const double c = X.c;
+    const int64_t sc = (int64_t)1 << (X.max_depth - lvl), s2 = sc >> 1;
+    int64_t N[3] = {C[0], C[1], C[2]};
+    N[a] += sd ? 1 : -1;
+    if (N[a] < 0) return 0;
+    const int side_n = sd ? 0 : 1;          // the neighbour's side of the shared plane
+    const int64_t plane = (C[a] + sd) * sc; // finest-lattice coordinate of the face
+    if (fine_ok) {
+        int64_t tq[4], T[4][3];
+        int ntile = 0;
+        for (int iv = 0; iv < 2; iv++)
+            for (int iu = 0; iu < 2; iu++) {
+                const int q = iu + 2 * iv;
+                T[q][a] = 2 * N[a] + side_n; T[q][ua] = 2 * C[ua] + iu; T[q][va] = 2 * C[va] + iv;
+                tq[q] = tri_cube_at(X, T[q][0], T[q][1], T[q][2], lvl + 1);
+                ntile += tq[q] >= 0;
+            }
+        if (ntile > 0) {
+            for (int iv = 0; iv < 2; iv++)
+                for (int iu = 0; iu < 2; iu++) {
+                    const int q = iu + 2 * iv;
+                    if (tq[q] < 0) continue;
+                    double tu[2], tv[2];
+                    const int nn = cube_fold_roots(X, tq[q], a, tu, tv);
+                    for (int r = 0; r < nn; r++) {
+                        const int id = (int)add_pt<TP_MIX>(pts, np, 2);
+                        if (id < 0 || nfp >= FP_MIX) return 1;
+                        pts[id].p[a] = sd;
+                        pts[id].p[ua] = __dmul_rn(__dadd_rn((double)iu, tu[r]), 0.5);
+                        pts[id].p[va] = __dmul_rn(__dadd_rn((double)iv, tv[r]), 0.5);
+                        int64_t L[3] = {T[q][0] * s2, T[q][1] * s2, T[q][2] * s2};
+                        L[a] = plane;
+                        pts[id].key = gk_make(L[0], L[1], L[2], 8u + 4u * a + 2u * (side_n == 0 ? 1u : 0u) + (unsigned)r,
+                                              (unsigned)(lvl + 1));
+                        pw[id][a] = wlat(X, a, plane);
+                        pw[id][ua] = wfrac(X, ua, T[q][ua], lvl + 1, tu[r]);
+                        pw[id][va] = wfrac(X, va, T[q][va], lvl + 1, tv[r]);
+                        fp[nfp++] = (signed char)id;
+                    }
+                }
+            // inner half-lines: along u at v = 1/2 (halves k), then along v at
+            // u = 1/2; each is an edge of the tiles on either side of it
+            for (int dir = 0; dir < 2; dir++)
+                for (int k = 0; k < 2; k++) {
+                    const int along = dir ? va : ua, across = dir ? ua : va;
+                    const bool has = dir ? (tq[2 * k] >= 0 || tq[1 + 2 * k] >= 0) : (tq[k] >= 0 || tq[k + 2] >= 0);
+                    if (!has) continue;
+                    int64_t L0[3];
+                    L0[a] = plane;
+                    L0[along] = C[along] * sc + k * s2;
+                    L0[across] = C[across] * sc + s2;
+                    int64_t L1[3] = {L0[0], L0[1], L0[2]};
+                    L1[along] += s2;
+                    const int64_t ia = tri_vert(X, L0[0], L0[1], L0[2]), ib = tri_vert(X, L1[0], L1[1], L1[2]);
+                    if (ia < 0 || ib < 0) return 1;
+                    const double ga = X.phi[ia], gb = X.phi[ib];
+                    if ((ga >= c) == (gb >= c)) continue;
+                    const int id = (int)add_pt<TP_MIX>(pts, np, 2);
+                    if (id < 0 || nfp >= FP_MIX) return 1;
+                    const double t = __ddiv_rn(__dsub_rn(c, ga), __dsub_rn(gb, ga));
+                    pts[id].p[a] = sd;
+                    pts[id].p[along] = __dmul_rn(__dadd_rn((double)k, t), 0.5);
+                    pts[id].p[across] = 0.5;
+                    pts[id].key = gk_make(L0[0], L0[1], L0[2], (unsigned)along, (unsigned)(lvl + 1));
+                    pw[id][a] = wlat(X, a, plane);
+                    pw[id][along] = wfrac(X, along, 2 * C[along] + k, lvl + 1, t);
+                    pw[id][across] = wlat(X, across, L0[across]);
+                    fp[nfp++] = (signed char)id;
+                }
+            return 0;
+        }
+    }
+    if (lvl > 0) {
+        const int64_t Q[3] = {N[0] >> 1, N[1] >> 1, N[2] >> 1};
+        const int64_t q = tri_cube_at(X, Q[0], Q[1], Q[2], lvl - 1);
+        if (q < 0) return 0;
+        double qu[2], qv[2];
+        const int nn = cube_fold_roots(X, q, a, qu, qv);
+        const int64_t su = C[ua] - 2 * Q[ua], sv = C[va] - 2 * Q[va];  // this face's quarter
+        for (int r = 0; r < nn; r++) {
+            if ((qu[r] >= 0.5) != (su == 1) || (qv[r] >= 0.5) != (sv == 1)) continue;
+            const int id = (int)add_pt<TP_MIX>(pts, np, 2);
+            if (id < 0 || nfp >= FP_MIX) return 1;
+            pts[id].p[a] = sd;
+            pts[id].p[ua] = __dsub_rn(__dmul_rn(2.0, qu[r]), (double)su);
+            pts[id].p[va] = __dsub_rn(__dmul_rn(2.0, qv[r]), (double)sv);
+            int64_t L[3] = {Q[0] * 2 * sc, Q[1] * 2 * sc, Q[2] * 2 * sc};
+            L[a] = plane;
+            pts[id].key = gk_make(L[0], L[1], L[2], 8u + 4u * a + 2u * (side_n == 0 ? 1u : 0u) + (unsigned)r,
+                                  (unsigned)(lvl - 1));
+            pw[id][a] = wlat(X, a, plane);
+            pw[id][ua] = wfrac(X, ua, Q[ua], lvl - 1, qu[r]);
+            pw[id][va] = wfrac(X, va, Q[va], lvl - 1, qv[r]);
+            fp[nfp++] = (signed char)id;
+        }
+    }
+    return 0;
+}
+
+// returns 0 on success, 1 on an inconsistency (cube skipped).  MIX: the cube
+// has neighbours of another size (cubes of different sizes, section 2.3):
+// halved edges take the crossing of the half where the sign changes; across
+// a face with finer neighbours the face curve takes their fold ends and the
+// points on the face's inner half-lines; across a face of a coarser
+// neighbour it takes that cube's fold ends falling in this face.  Every
+// point's world position is computed in the frame of the cube or edge it
+// belongs to.
+template <bool MIX>
 __device__ int tri_cube(const TriCtx &X, int64_t ci, TriOut &o, unsigned long long *degen)
 {
+    constexpr int NP = MIX ? TP_MIX : TP_MAX;
+    constexpr int FP = MIX ? FP_MIX : 4;
     uint64_t ck = X.cubes[ci];
     int lvl = (int)gk_level(ck);
     int64_t C[3] = {gk_x(ck), gk_y(ck), gk_z(ck)};
@@ -303,8 +469,11 @@ __device__ int tri_cube(const TriCtx &X, int64_t ci, TriOut &o, unsigned long lo
     for (int v = 0; v < 8; v++) sg |= (g[v] >= c ? 1 : 0) << v;
     if (sg == 0 || sg == 0xFF) return 0;
 
-    TPt pts[TP_MAX];
+    TPt pts[NP];
+    double pw[MIX ? NP : 1][3];   // world coordinates (MIX)
     int np = 0;
+    const bool fine_ok = MIX && lvl < X.max_depth;
+    const int64_t s2 = sc >> 1;
     signed char eid[12];
     for (int a = 0; a < 3; a++) {
         int ua, va;
@@ -317,13 +486,33 @@ __device__ int tri_cube(const TriCtx &X, int64_t ci, TriOut &o, unsigned long lo
             eid[4 * a + e] = -1;
             if (((sg >> v0) & 1) == ((sg >> v1) & 1)) continue;
             double g0 = g[v0], g1 = g[v1];
-            int id = (int)add_pt(pts, np, 0);
-            pts[id].p[a] = __ddiv_rn(__dsub_rn(c, g0), __dsub_rn(g1, g0));
-            pts[id].p[ua] = o1;
-            pts[id].p[va] = o2;
+            int id = (int)add_pt<NP>(pts, np, 0);
             int64_t L[3];
             L[a] = C[a] * sc; L[ua] = (C[ua] + o1) * sc; L[va] = (C[va] + o2) * sc;
-            pts[id].key = gk_make(L[0], L[1], L[2], (unsigned)a, (unsigned)lvl);
+            int64_t mid = -1;
+            if (fine_ok) {
+                int64_t Lm[3] = {L[0], L[1], L[2]};
+                Lm[a] += s2;
+                mid = tri_vert(X, Lm[0], Lm[1], Lm[2]);
+            }
+            if (MIX && mid >= 0) {
+                // halved edge: the half where the sign changes
+                const double gm = X.phi[mid];
+                const int half = ((g0 >= c) == (gm >= c)) ? 1 : 0;
+                const double ga = half ? gm : g0, gb = half ? g1 : gm;
+                const double t = __ddiv_rn(__dsub_rn(c, ga), __dsub_rn(gb, ga));
+                pts[id].p[a] = __dmul_rn(__dadd_rn((double)half, t), 0.5);
+                L[a] += half * s2;
+                pts[id].key = gk_make(L[0], L[1], L[2], (unsigned)a, (unsigned)(lvl + 1));
+                if (MIX) pw[id][a] = wfrac(X, a, 2 * C[a] + half, lvl + 1, t);
+            } else {
+                pts[id].p[a] = __ddiv_rn(__dsub_rn(c, g0), __dsub_rn(g1, g0));
+                pts[id].key = gk_make(L[0], L[1], L[2], (unsigned)a, (unsigned)lvl);
+                if (MIX) pw[id][a] = wfrac(X, a, C[a], lvl, pts[id].p[a]);
+            }
+            pts[id].p[ua] = o1;
+            pts[id].p[va] = o2;
+            if (MIX) { pw[id][ua] = wlat(X, ua, L[ua]); pw[id][va] = wlat(X, va, L[va]); }
             eid[4 * a + e] = (signed char)id;
         }
     }
@@ -365,7 +554,7 @@ __device__ int tri_cube(const TriCtx &X, int64_t ci, TriOut &o, unsigned long lo
                 }
         }
     // fold ends: own (both faces) and the same-size neighbours' ends on shared faces
-    signed char fpt[6][4];
+    signed char fpt[6][FP];
     int nfp[6] = {0, 0, 0, 0, 0, 0};
     signed char fend[3][2][2];
     for (int a = 0; a < 3; a++) {
@@ -373,18 +562,25 @@ __device__ int tri_cube(const TriCtx &X, int64_t ci, TriOut &o, unsigned long lo
         axes_other(a, ua, va);
         for (int r = 0; r < nr[a]; r++) {
             for (int sd = 0; sd < 2; sd++) {
-                int id = (int)add_pt(pts, np, 1);
+                int id = (int)add_pt<NP>(pts, np, 1);
                 if (id < 0) return 1;
                 pts[id].p[a] = sd; pts[id].p[ua] = rt[a][r][0]; pts[id].p[va] = rt[a][r][1];
                 int64_t L[3] = {C[0] * sc, C[1] * sc, C[2] * sc};
                 L[a] = (C[a] + sd) * sc;
                 pts[id].key = gk_make(L[0], L[1], L[2], 8u + 4u * a + 2u * (sd == 0 ? 1u : 0u) + (unsigned)r, (unsigned)lvl);
+                if (MIX)
+                    for (int q = 0; q < 3; q++) pw[id][q] = wfrac(X, q, C[q], lvl, pts[id].p[q]);
                 fend[a][r][sd] = (signed char)id;
                 fpt[2 * a + sd][nfp[2 * a + sd]++] = (signed char)id;
             }
         }
         for (int sd = 0; sd < 2; sd++) {
             int nb = X.nbr[ci * 6 + 2 * a + sd];
+            if (MIX && nb < 0) {
+                if (tri_mixed_face(X, C, lvl, a, sd, fine_ok, pts, pw, np, fpt[2 * a + sd], nfp[2 * a + sd]))
+                    return 1;
+                continue;
+            }
             if (nb < 0) continue;
             double nu_[2], nv_[2];
             int nn;
@@ -400,12 +596,14 @@ __device__ int tri_cube(const TriCtx &X, int64_t ci, TriOut &o, unsigned long lo
                 nn = fold_solve(gn, a, c, nu_, nv_);
             }
             for (int r = 0; r < nn; r++) {
-                int id = (int)add_pt(pts, np, 2);
-                if (id < 0) return 1;
+                int id = (int)add_pt<NP>(pts, np, 2);
+                if (id < 0 || nfp[2 * a + sd] >= FP) return 1;
                 pts[id].p[a] = sd; pts[id].p[ua] = nu_[r]; pts[id].p[va] = nv_[r];
                 int64_t L[3] = {C[0] * sc, C[1] * sc, C[2] * sc};
                 L[a] = (C[a] + sd) * sc;
                 pts[id].key = gk_make(L[0], L[1], L[2], 8u + 4u * a + 2u * (sd == 1 ? 1u : 0u) + (unsigned)r, (unsigned)lvl);
+                if (MIX)
+                    for (int q = 0; q < 3; q++) pw[id][q] = wfrac(X, q, C[q], lvl, pts[id].p[q]);
                 fpt[2 * a + sd][nfp[2 * a + sd]++] = (signed char)id;
             }
         }
@@ -420,12 +618,14 @@ __device__ int tri_cube(const TriCtx &X, int64_t ci, TriOut &o, unsigned long lo
         int ua, va, ub, vb;
         axes_other(a, ua, va);
         axes_other(b, ub, vb);
-        int id = (int)add_pt(pts, np, 3);
+        int id = (int)add_pt<NP>(pts, np, 3);
         if (id < 0) return 1;
         TPt &P = pts[id];
         P.p[a] = rt[b][j][a == ub ? 0 : 1];
         P.p[b] = rt[a][i][b == ua ? 0 : 1];
         P.p[cc] = rt[a][i][cc == ua ? 0 : 1];
+        if (MIX)
+            for (int q = 0; q < 3; q++) pw[id][q] = wfrac(X, q, C[q], lvl, P.p[q]);
         P.fa = (signed char)a; P.fb = (signed char)b;
         // dg/dx_cc at the point: the outward normal is -sign(dg/dx_cc) e_cc
         double dg = 0;
@@ -458,7 +658,7 @@ __device__ int tri_cube(const TriCtx &X, int64_t ci, TriOut &o, unsigned long lo
             }
         }
     // face arcs -> successor along the loops
-    signed char nxt[TP_MAX];
+    signed char nxt[NP];
     for (int i = 0; i < np; i++) nxt[i] = -1;
     for (int a = 0; a < 3; a++) {
         int ua, va;
@@ -523,7 +723,7 @@ __device__ int tri_cube(const TriCtx &X, int64_t ci, TriOut &o, unsigned long lo
                 bool s1 = st_pos(e1), s2 = st_pos(e2);
                 if (s1 == s2) return 1;
                 int S = s1 ? ep[e1] : ep[e2], T = s1 ? ep[e2] : ep[e1];
-                int mid[8], nm = 0;
+                int mid[FP], nm = 0;
                 for (int t = 0; t < nfp[fid]; t++) {
                     int id = fpt[fid][t];
                     if (narc == 2) {
@@ -531,7 +731,7 @@ __device__ int tri_cube(const TriCtx &X, int64_t ci, TriOut &o, unsigned long lo
                         bool arc_low = ai == 0 ? (around00 != 0) : (around00 == 0);
                         if (low != arc_low) continue;
                     }
-                    if (nm < 8) mid[nm++] = id;
+                    mid[nm++] = id;
                 }
                 int ax = ua;
                 double sg = 1.0;
@@ -562,13 +762,13 @@ __device__ int tri_cube(const TriCtx &X, int64_t ci, TriOut &o, unsigned long lo
     for (int i = 0; i < np; i++)
         if (pts[i].kind != 3 && nxt[i] < 0) return 1;
 
-    float pf[TP_MAX][3];
+    float pf[NP][3];
     for (int i = 0; i < np; i++)
         for (int a = 0; a < 3; a++) pf[i][a] = (float)pts[i].p[a];
     // pieces: faces of the graph of loops and fold segments, traced with the
     // face on the left; at a critical point take the next segment clockwise
     unsigned long long used_loop = 0ull;
-    unsigned char used_fold[TP_MAX];
+    unsigned char used_fold[NP];
     for (int i = 0; i < np; i++) used_fold[i] = 0;
     const int cw_r[4] = {3, 2, 0, 1}, cw_l[4] = {2, 3, 1, 0};
     for (int i0 = 0; i0 < np; i0++) {
@@ -604,7 +804,13 @@ __device__ int tri_cube(const TriCtx &X, int64_t ci, TriOut &o, unsigned long lo
         if (n >= 3) clip_piece(pts, pf, poly, n, o, degen);
     }
     // points in world coordinates
-    if (np <= o.pt_cap) {
+    if (MIX && np <= o.pt_cap) {
+        for (int i = 0; i < np; i++) {
+            double *dst = o.pt_xyz + 3 * (o.pt_off + i);
+            for (int a = 0; a < 3; a++) dst[a] = pw[i][a];
+            o.pt_keys[o.pt_off + i] = pts[i].key;
+        }
+    } else if (np <= o.pt_cap) {
         double h = ldexp(X.min_edge, X.max_depth - lvl);
         double lo[3], hi[3];
         for (int a = 0; a < 3; a++) {
@@ -834,21 +1040,32 @@ __global__ void k_tri_order(const int32_t *__restrict__ cls, int64_t n, unsigned
     if (k >= 0) order[base[k] + local] = (int32_t)ci;
 }
 
+// MIX: over the list of cubes with neighbours of another size (count only);
+// otherwise over all cubes, skipping those
+template <bool MIX>
 __global__ void __launch_bounds__(128) k_tri_count(TriCtx X, int64_t *__restrict__ ntri, int64_t *__restrict__ npt,
                                                    unsigned long long *errs, unsigned long long *surface,
                                                    uint64_t *st_tri, uint64_t *st_pk, double *st_xyz,
-                                                   unsigned long long *degen, const int32_t *__restrict__ order)
+                                                   unsigned long long *degen, const int32_t *__restrict__ order,
+                                                   const int64_t *__restrict__ mlist, const unsigned long long *nmlist)
 {
     int64_t ci = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    if (ci >= X.ncubes) return;
-    if (order) ci = order[ci];
+    if (MIX) {
+        if (ci >= (int64_t)*nmlist) return;
+        ci = mlist[ci];
+        st_tri = nullptr;
+    } else {
+        if (ci >= X.ncubes) return;
+        if (order) ci = order[ci];
+        if (X.mixed && X.mixed[ci]) return;
+    }
     TriOut o;
     o.ntri = 0; o.npt = 0;
     o.tri_keys = st_tri; o.pt_keys = st_pk; o.pt_xyz = st_xyz;
     o.tri_off = ci * TRI_STAGE_T; o.pt_off = ci * TRI_STAGE_P;
     o.tri_cap = st_tri ? TRI_STAGE_T : 0;
     o.pt_cap = st_tri ? TRI_STAGE_P : -1;
-    int bad = tri_cube(X, ci, o, st_tri ? degen : nullptr);
+    int bad = tri_cube<MIX>(X, ci, o, st_tri ? degen : nullptr);
     if (bad) { atomicAdd(errs, 1ull); o.ntri = 0; o.npt = 0; }
     {
         // one atomic per warp for the surface-cube count
@@ -866,11 +1083,11 @@ __global__ void __launch_bounds__(128) k_tri_copy(int64_t n, const int64_t *__re
                                                   const uint64_t *__restrict__ st_pk, const double *__restrict__ st_xyz,
                                                   uint64_t *__restrict__ tri_keys, uint64_t *__restrict__ pt_keys,
                                                   double *__restrict__ pt_xyz, int64_t *__restrict__ redo,
-                                                  unsigned long long *nredo)
+                                                  unsigned long long *nredo, const uint8_t *__restrict__ mixed)
 {
     int64_t ci = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     bool over = false;
-    if (ci < n) {
+    if (ci < n && !(mixed && mixed[ci])) {
         int64_t t0 = tri_off[ci], nt = tri_off[ci + 1] - t0;
         int64_t p0 = pt_off[ci], np = pt_off[ci + 1] - p0;
         if (nt > TRI_STAGE_T || np > TRI_STAGE_P) {
@@ -890,7 +1107,9 @@ __global__ void __launch_bounds__(128) k_tri_copy(int64_t n, const int64_t *__re
     if (over) redo[base + __popc(bal & ((1u << lane) - 1u))] = ci;
 }
 
-// final pass over the listed cubes (all cubes when list is null)
+// final pass over the listed cubes (all cubes when list is null); MIX: the
+// cubes with neighbours of another size, which the other passes skip
+template <bool MIX>
 __global__ void __launch_bounds__(128) k_tri_emit(TriCtx X, const int64_t *__restrict__ tri_off,
                                                   const int64_t *__restrict__ pt_off, uint64_t *__restrict__ tri_keys,
                                                   uint64_t *__restrict__ pt_keys, double *__restrict__ pt_xyz,
@@ -904,12 +1123,21 @@ __global__ void __launch_bounds__(128) k_tri_emit(TriCtx X, const int64_t *__res
     } else if (ci >= X.ncubes) {
         return;
     }
+    if (!MIX && X.mixed && X.mixed[ci]) return;
     if (tri_off[ci + 1] == tri_off[ci] && pt_off[ci + 1] == pt_off[ci]) return;
     TriOut o;
     o.ntri = 0; o.npt = 0; o.tri_off = tri_off[ci]; o.pt_off = pt_off[ci];
     o.tri_cap = 1 << 30; o.pt_cap = 1 << 30;
     o.tri_keys = tri_keys; o.pt_keys = pt_keys; o.pt_xyz = pt_xyz;
-    tri_cube(X, ci, o, degen);
+    tri_cube<MIX>(X, ci, o, degen);
+}
+
+// list of the cubes flagged mixed (any order)
+__global__ void k_mixed_list(const uint8_t *__restrict__ mixed, int64_t n, int64_t *__restrict__ list,
+                             unsigned long long *nlist)
+{
+    const int64_t ci = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (ci < n && mixed[ci]) list[atomicAdd(nlist, 1ull)] = ci;
 }
 
 // ---------------------------------------------------------------- host
@@ -986,8 +1214,20 @@ int gs_triangulate(const TriCtx &X0, uint64_t **d_tri_keys, int64_t *ntri_total,
         gs_free(order, st);
         order = nullptr;
     }
-    GS_LAUNCH(k_tri_count, nb, 128, 0, st)(X, ntri, npt, d_counters + 0, d_counters + 2, st_tri, st_pk, st_xyz,
-                                          d_counters + 1, order);
+    GS_LAUNCH(k_tri_count<false>, nb, 128, 0, st)(X, ntri, npt, d_counters + 0, d_counters + 2, st_tri, st_pk, st_xyz,
+                                                 d_counters + 1, order, nullptr, nullptr);
+    int64_t *mlist = nullptr;
+    unsigned long long *nmlist = nullptr;
+    if (X.mixed) {
+        rc = gs_alloc((void **)&mlist, sizeof(int64_t) * (size_t)n, st);
+        if (!rc) rc = gs_alloc((void **)&nmlist, sizeof(unsigned long long), st);
+        if (!rc) {
+            cudaMemsetAsync(nmlist, 0, sizeof(unsigned long long), st);
+            GS_LAUNCH(k_mixed_list, (unsigned)((n + 255) / 256), 256, 0, st)(X.mixed, n, mlist, nmlist);
+            GS_LAUNCH(k_tri_count<true>, nb, 128, 0, st)(X, ntri, npt, d_counters + 0, d_counters + 2, nullptr, nullptr,
+                                                        nullptr, d_counters + 1, nullptr, mlist, nmlist);
+        }
+    }
     gs_free(cls, st); gs_free(order, st); gs_free(hist, st);
     rc = gs_scan_i64(ntri, n + 1, tot, st);
     if (!rc) rc = gs_scan_i64(npt, n + 1, tot + 1, st);
@@ -1010,15 +1250,19 @@ int gs_triangulate(const TriCtx &X0, uint64_t **d_tri_keys, int64_t *ntri_total,
         if (!rc) {
             cudaMemsetAsync(nredo, 0, sizeof(unsigned long long), st);
             GS_LAUNCH(k_tri_copy, nb, 128, 0, st)(n, ntri, npt, st_tri, st_pk, st_xyz, *d_tri_keys, *d_pt_keys,
-                                                 *d_pt_xyz, redo, nredo);
-            GS_LAUNCH(k_tri_emit, nb, 128, 0, st)(X, ntri, npt, *d_tri_keys, *d_pt_keys, *d_pt_xyz, nullptr, redo,
-                                                 nredo);
+                                                 *d_pt_xyz, redo, nredo, X.mixed);
+            GS_LAUNCH(k_tri_emit<false>, nb, 128, 0, st)(X, ntri, npt, *d_tri_keys, *d_pt_keys, *d_pt_xyz, nullptr,
+                                                        redo, nredo);
         }
         gs_free(redo, st); gs_free(nredo, st);
     } else if (!rc) {
-        GS_LAUNCH(k_tri_emit, nb, 128, 0, st)(X, ntri, npt, *d_tri_keys, *d_pt_keys, *d_pt_xyz, d_counters + 1,
-                                             nullptr, nullptr);
+        GS_LAUNCH(k_tri_emit<false>, nb, 128, 0, st)(X, ntri, npt, *d_tri_keys, *d_pt_keys, *d_pt_xyz, d_counters + 1,
+                                                    nullptr, nullptr);
     }
+    if (!rc && X.mixed)
+        GS_LAUNCH(k_tri_emit<true>, nb, 128, 0, st)(X, ntri, npt, *d_tri_keys, *d_pt_keys, *d_pt_xyz, d_counters + 1,
+                                                   mlist, nmlist);
+    gs_free(mlist, st); gs_free(nmlist, st);
     gs_free(st_tri, st); gs_free(st_pk, st); gs_free(st_xyz, st);
     gs_free(fcount, st); gs_free(froot, st);
     gs_free(ntri, st); gs_free(npt, st); gs_free(tot, st);
@@ -1042,6 +1286,11 @@ __global__ void __launch_bounds__(128) k_tri_marks(TriCtx X, const float *__rest
 {
     int64_t ci = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (ci >= X.ncubes) return;
+    if (X.mixed && X.mixed[ci]) {
+        // neighbours of another size: every corner in FP64
+        for (int v = 0; v < 8; v++) mark[X.cvid[ci * 8 + v]] = 1;
+        return;
+    }
     uint64_t ck = X.cubes[ci];
     int lvl = (int)gk_level(ck);
     const float h = (float)ldexp(X.min_edge, X.max_depth - lvl);

@@ -196,16 +196,10 @@ def cube_boxes(keys, origin, min_edge, max_depth):
     return lo, lo + h[:, None]
 
 
-def window_compare(full, cfg, centre, half=6.0, inner=5.0, margin=10.0, min_cubes=100, min_tris=500):
-    """Locality check (section 3.1: every cube decision and field value reads
-    only atoms within the cutoff radius): the oracle meshes the atoms within
-    `margin` of the window [centre - half, centre + half]^3 and must give the
-    same cubes inside the window, and inside the inner window [centre -
-    inner, centre + inner]^3 the same surface-point keys, positions within
-    1e-5 A and triangles, as `full` (dict cube_keys, vkeys, vertices,
-    triangles: the whole problem's mesh).  margin >= root cube edge +
-    largest cutoff radius covers every ancestor's and neighbour's atoms.
-    Returns the number of triangles compared."""
+def window_oracle(cfg, centre, half=6.0, margin=10.0):
+    """The oracle's mesh of the atoms within `margin` of the window
+    [centre - half, centre + half]^3, with the shift of its root origin to
+    the whole problem's (finest-lattice units)."""
     import oracle
     md, me = cfg["max_depth"], cfg["min_edge"]
     o_full, _, _ = oracle.root_grid(cfg["xyz"], cfg["r"], cfg["D"], cfg["c"], me, md)
@@ -217,6 +211,23 @@ def window_compare(full, cfg, centre, half=6.0, inner=5.0, margin=10.0, min_cube
     o_sub, _, _ = oracle.root_grid(sx, sr, cfg["D"], cfg["c"], me, md)
     shift = np.round((o_sub - o_full) / me).astype(np.int64)
     assert np.all(shift % (1 << md) == 0) and np.all(shift >= 0)
+    return dict(ref=ref, shift=shift, origin=o_full, centre=centre, half=half)
+
+
+def window_compare(full, cfg, win, inner=5.0, min_cubes=100, min_tris=500):
+    """Locality check (section 3.1: every cube decision and field value reads
+    only atoms within the cutoff radius): the oracle's mesh of a window's
+    atoms plus a margin (window_oracle) must give the same cubes inside the
+    window, and inside the inner window [centre - inner, centre + inner]^3
+    the same surface-point keys, positions within 1e-5 A and triangles, as
+    `full` (dict cube_keys, vkeys, vertices, triangles: the whole problem's
+    mesh).  A margin >= root cube edge + largest cutoff radius covers every
+    ancestor's and neighbour's atoms.  Returns the number of triangles
+    compared."""
+    md, me = cfg["max_depth"], cfg["min_edge"]
+    ref, shift, o_full = win["ref"], win["shift"], win["origin"]
+    centre, half = win["centre"], win["half"]
+    lo_w, hi_w = centre - half, centre + half
     # cubes inside the window
     glo, ghi = cube_boxes(full["cube_keys"], o_full, me, md)
     ginside = np.all((glo >= lo_w) & (ghi <= hi_w), axis=1)

@@ -18,7 +18,7 @@ import pytest
 
 import oracle
 import synth
-from meshcheck import canonical_triangles, check_closed_manifold, window_compare
+from meshcheck import canonical_triangles, check_closed_manifold, window_compare, window_oracle
 
 pytestmark = pytest.mark.gpu
 
@@ -101,23 +101,20 @@ def _window_centres(cfg, count=4, seed=3):
     return out
 
 
-@pytest.fixture(scope="module")
-def c3_meshes():
+def test_window_parity_assembly1m():
+    """Both precision forms of the full-size assembly against the oracle's
+    meshes of three windows (each computed once)."""
     cfg = synth.config("assembly1m")
     args = (cfg["xyz"], cfg["r"], cfg["D"], cfg["c"], cfg["precision"], cfg["max_depth"])
-    out = {}
+    full = {}
     for mode in ("mixed", "fp64"):
-        out[mode] = gs.mesh_gaussian_surface(*args, min_edge=cfg["min_edge"], precision_mode=_mode(mode))
-    return cfg, out
-
-
-@pytest.mark.parametrize("mode", ["mixed", "fp64"])
-def test_window_parity_assembly1m(c3_meshes, mode):
-    cfg, meshes = c3_meshes
-    m = meshes[mode]
-    full = dict(cube_keys=m.cube_keys, vkeys=m.vertex_keys, vertices=m.vertices, triangles=m.triangles)
+        m = gs.mesh_gaussian_surface(*args, min_edge=cfg["min_edge"], precision_mode=_mode(mode))
+        full[mode] = dict(cube_keys=m.cube_keys, vkeys=m.vertex_keys, vertices=m.vertices, triangles=m.triangles)
+        del m
     oracle.set_threads(0)
-    tris = 0
-    for centre in _window_centres(cfg):
-        tris += window_compare(full, cfg, centre)
-    print("assembly1m windows (%s): %d triangles compared" % (mode, tris))
+    tris = {"mixed": 0, "fp64": 0}
+    for centre in _window_centres(cfg, count=3):
+        win = window_oracle(cfg, centre)
+        for mode in tris:
+            tris[mode] += window_compare(full[mode], cfg, win)
+    print("assembly1m windows: triangles compared", tris)
