@@ -141,28 +141,38 @@ def make_batch_molecules(count=64):
         return pool.map(_batch_molecule, specs, chunksize=1)
 
 
-def cpu_baseline(cfg, n_sample=300):
-    """The oracle, as it stands, on a cut-out of the workload: the n_sample
-    atoms nearest to the outermost atom of the first unit.  Scaled to a whole
-    mesh by atom count (the method is O(N); the oracle's brute-force atom scan
-    makes the real full-size figure larger still)."""
+def cpu_baseline(cfg, half=6.0, margin=10.0, examined_full=None):
+    """The oracle, as it stands, on a window of the workload: the atoms within
+    `margin` of the cube of half-width `half` around the outermost atom of
+    the first unit (the window's surface is the assembly's), meshed on every
+    host core the oracle's threads can use.  The whole-mesh figure is an
+    extrapolation, labelled as such: the window's time per examined cube
+    times the examined cubes of the whole mesh (the GPU run's count when
+    given).  The oracle scans every atom of its input for every cube, so the
+    oracle run on the whole assembly at once would take longer still; this
+    figure is what meshing it window by window would cost."""
     import oracle
     xyz, r = cfg["xyz"], cfg["r"]
     unit = xyz[:16667]
     cen = unit.mean(0)
     p0 = unit[np.argmax(((unit - cen) ** 2).sum(1))]
-    idx = np.argsort(((xyz - p0) ** 2).sum(1))[:n_sample]
-    sx, sr = np.ascontiguousarray(xyz[idx]), np.ascontiguousarray(r[idx])
+    sel = np.all((xyz >= p0 - half - margin) & (xyz <= p0 + half + margin), axis=1)
+    sx, sr = np.ascontiguousarray(xyz[sel]), np.ascontiguousarray(r[sel])
     oracle.build()
+    threads = oracle.set_threads(0)
     t0 = time.perf_counter()
     m = oracle.mesh(sx, sr, cfg["D"], cfg["c"], cfg["precision"], cfg["min_edge"], cfg["max_depth"])
     dt = time.perf_counter() - t0
-    scale = len(r) / n_sample
-    return {"value": dt * 1e3 * scale, "unit": "ms", "cores": 1, "kind": "oracle",
-            "sample": "oracle.mesh (FP64, single thread) on the %d atoms of the assembly nearest the outermost atom "
-                      "of unit 0 (%d triangles, %.1f s), scaled x%.0f by atom count"
-                      % (n_sample, len(m["triangles"]), dt, scale),
-            "sample_seconds": dt}
+    ex_win = sum(m["stats"]["examined"])
+    if examined_full is None:
+        examined_full = len(r) / len(sr) * ex_win
+    scale = examined_full / ex_win
+    return {"value": dt * 1e3 * scale, "unit": "ms", "cores": threads, "kind": "oracle",
+            "sample": "oracle.mesh (FP64, %d threads) on a window of the assembly: %d atoms within %.0f A of the "
+                      "%.0f A cube around the outermost atom of unit 0 (%d examined cubes, %d triangles, %.1f s); "
+                      "extrapolated x%.0f by examined cubes to the whole mesh (not measured)"
+                      % (threads, len(sr), margin, 2 * half, ex_win, len(m["triangles"]), dt, scale),
+            "sample_seconds": dt, "extrapolated": True}
 
 
 def run_reference(args, ws, rank):
@@ -172,7 +182,7 @@ def run_reference(args, ws, rank):
     cfg = synth.config(WORKLOAD["name"])
     vals = []
     for i in range(args.warmup + args.steps):
-        b = cpu_baseline(cfg, n_sample=args.ref_sample)
+        b = cpu_baseline(cfg, half=args.ref_half)
         if i >= args.warmup:
             vals.append(b["value"])
     v = float(np.mean(vals))
@@ -180,7 +190,7 @@ def run_reference(args, ws, rank):
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": v, "higher_is_better": False,
             "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
             "config": {"workload": workload_desc(WORKLOAD["name"]), "mode": "fp64 CPU oracle",
-                       "parallelism": "single", "sample_atoms": args.ref_sample},
+                       "parallelism": "single", "window_half_A": args.ref_half},
             "cpu_baseline": dict(b, value=v),
             "e2e": {"value": v, "unit": "ms", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)
@@ -201,21 +211,25 @@ def open_edges(tris):
     return dup + int((~np.isin(rev, u)).sum())
 
 
-READINGS = (("default: re-projected children, bounds first, sum norm", {}),
+READINGS = (("default: re-projected children, bounds first, sum norm, constrained values", {}),
             ("child re-expansion", {"child_mode": 1}),
             ("literal step-3 order", {"decision_order": 1}),
             ("max-norm precision test", {"precision_norm": 1}),
-            ("euclidean-norm precision test", {"precision_norm": 2}))
+            ("euclidean-norm precision test", {"precision_norm": 2}),
+            ("equal sizes across shared faces and edges", {"conform_mode": 1}))
+# precisions at which the readings are compared; at 5e-2 cubes are accepted
+# on two levels, where the readings for cubes of different sizes differ
+READING_PRECISIONS = (1e-3, 1e-2, 5e-2)
 
 
 def readings_form(gs, synth, torch, dev, stream, steps, barrier):
     cfg = synth.config("globular20k")
     x = torch.from_numpy(cfg["xyz"]).to(dev)
     r = torch.from_numpy(cfg["r"]).to(dev)
-    out = {"workload": workload_desc("globular20k") + ", FP64 form; also at precision 1e-2, where cubes are "
-                       "accepted above the finest level", "fidelity": "phi at triangle centroids"}
+    out = {"workload": workload_desc("globular20k") + ", FP64 form; also at precisions 1e-2 and 5e-2, where "
+                       "cubes are accepted above the finest level", "fidelity": "phi at triangle centroids"}
     rows = []
-    for (label, kw), prec in [(rd, p) for p in (cfg["precision"], 1e-2) for rd in READINGS]:
+    for (label, kw), prec in [(rd, p) for p in READING_PRECISIONS for rd in READINGS]:
         args = (cfg["D"], cfg["c"], prec, cfg["max_depth"])
         ts = []
         for it in range(steps + 1):
@@ -235,6 +249,10 @@ def readings_form(gs, synth, torch, dev, stream, steps, barrier):
                      "ms_levels": st["ms_levels"], "accepted": st["accepted"][:cfg["max_depth"] + 1],
                      "pair_terms": st["pair_terms"], "examined": st["examined"][:cfg["max_depth"] + 1],
                      "n_cubes_final": st["n_cubes_final"], "n_triangles": st["n_triangles"],
+                     "final_levels": np.bincount(np.asarray(m.cube_keys).astype(np.int64) >> 59,
+                                                 minlength=cfg["max_depth"] + 1).tolist(),
+                     "conformity_splits": st["conformity_splits"], "agreement_splits": st["agreement_splits"],
+                     "constrained_vertices": st["constrained_vertices"], "loop_errors": st["loop_errors"],
                      "open_edges": open_edges(m.triangles),
                      "centroid_phi_err_max": float(dev_rel.max()) if len(dev_rel) else 0.0,
                      "centroid_phi_err_mean": float(dev_rel.mean()) if len(dev_rel) else 0.0})
@@ -250,8 +268,12 @@ def main():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--mode", default="mixed", choices=["mixed", "fp64"])
     ap.add_argument("--workload", default="assembly1m")
-    ap.add_argument("--ref-sample", type=int, default=300)
+    ap.add_argument("--ref-half", type=float, default=6.0, help="half-width (A) of the oracle's window")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--e2e-warmup", type=int, default=2, help="untimed end-to-end calls before the timed ones")
+    ap.add_argument("--e2e-steps", type=int, default=5, help="timed end-to-end calls (host buffers, copies inside)")
+    ap.add_argument("--adaptive-steps", type=int, default=2,
+                    help="mixed-form steps of the same assembly at precision 5e-2 (cubes on two levels)")
     ap.add_argument("--fp64-steps", type=int, default=1, help="extra FP64-form steps timed for comparison")
     ap.add_argument("--diff-steps", type=int, default=2, help="differentiation-form steps (10k atoms) to time")
     ap.add_argument("--batch-steps", type=int, default=1, help="batch-form steps (64 molecules) to time")
@@ -334,7 +356,7 @@ def main():
             torch.empty((nt0, 3), dtype=torch.int32).pin_memory(),
             torch.empty(nv0, dtype=torch.int64).pin_memory(), torch.empty(nc0, dtype=torch.int64).pin_memory())
     e2e_times = []
-    for _ in range(max(1, min(args.steps, 2))):
+    for it in range(args.e2e_warmup + args.e2e_steps):
         flush.zero_()
         barrier()
         t0 = time.perf_counter()
@@ -342,7 +364,8 @@ def main():
                                                    cfg["max_depth"], *outs, min_edge=cfg["min_edge"],
                                                    precision_mode=mode, stream=stream)
         t1 = time.perf_counter()
-        e2e_times.append((t1 - t0) * 1e3)
+        if it >= args.e2e_warmup:
+            e2e_times.append((t1 - t0) * 1e3)
     nbytes_out = 24 * nv + 12 * nt + 8 * nv + 8 * nc
     mh = types.SimpleNamespace(vertices=outs[0][:nv].numpy(), triangles=outs[1][:nt].numpy(),
                                vertex_keys=outs[2][:nv].numpy().view(np.uint64),
@@ -372,6 +395,33 @@ def main():
         fp64["same_cubes_and_topology"] = bool(same)
         fp64["max_vertex_diff_A"] = float(np.abs(mh.vertices - mfh.vertices).max()) if same else None
         del mfh
+
+    # the adaptive path at full size: the same assembly in the same form at
+    # precision 5e-2, where surface cubes are accepted on two levels and
+    # cubes of different sizes join through constrained values
+    adaptive = None
+    if args.adaptive_steps > 0:
+        at = []
+        for _ in range(args.adaptive_steps):
+            flush.zero_()
+            barrier()
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            ma = gs.mesh_gaussian_surface(xyz_d, r_d, cfg["D"], cfg["c"], 5e-2, cfg["max_depth"], precision_mode=mode,
+                                          device_output=True, **kw)
+            e1.record(stream)
+            barrier()
+            at.append(e0.elapsed_time(e1))
+        sa = ma.stats
+        adaptive = {"workload": workload_desc(args.workload).replace("precision 1e-3", "precision 5e-2"),
+                    "mode": args.mode, "ms_per_mesh": float(np.mean(at)),
+                    "accepted": sa["accepted"][:4], "forced": sa["forced"][:4], "examined": sa["examined"][:4],
+                    "n_cubes_final": sa["n_cubes_final"], "n_triangles": sa["n_triangles"],
+                    "constrained_vertices": sa["constrained_vertices"], "agreement_splits": sa["agreement_splits"],
+                    "conformity_splits": sa["conformity_splits"], "mixed_cubes": sa["mixed_cubes"],
+                    "loop_errors": sa["loop_errors"], "stage_ms": {k: sa[k] for k in ("ms_levels", "ms_conformity",
+                                                                                      "ms_field", "ms_triangulate",
+                                                                                      "ms_weld")}}
 
     # differentiation form on the 10,000-atom globular molecule: forward mesh,
     # loss gradient per vertex, adjoint (gs_mesh_backward recomputes the mesh)
@@ -470,15 +520,19 @@ def main():
         "roofline": roofline,
         "clocks": clk,
         "e2e": {"value": e2e_ms, "unit": "ms", "h2d_bytes_per_step": int(xyz_h.nbytes + r_h.nbytes),
-                "d2h_bytes_per_step": int(nbytes_out)},
+                "d2h_bytes_per_step": int(nbytes_out), "runs": len(e2e_times), "warmup_runs": args.e2e_warmup,
+                "min_ms": float(np.min(e2e_times)), "max_ms": float(np.max(e2e_times)),
+                "copy_GBps_est": float(nbytes_out / ((e2e_ms - ms_per_mesh) * 1e-3) / 1e9)
+                if e2e_ms > ms_per_mesh else None},
         "gpu_launches": int(st["n_kernel_launches"]),
         "fp64_form": fp64,
+        "adaptive_form": adaptive,
         "diff_form": diff,
         "batch_form": batch,
         "readings_form": readings,
     }
     if rank == 0 and ws == 1 and not args.no_cpu_baseline:
-        line["cpu_baseline"] = cpu_baseline(cfg)
+        line["cpu_baseline"] = cpu_baseline(cfg, examined_full=sum(st["examined"]))
     if rank == 0:
         print(json.dumps(line), flush=True)
     if ws > 1:

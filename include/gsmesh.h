@@ -238,7 +238,8 @@ int64_t gs_struct_size(int which);
  *   linear index x + dims[0] * (y + dims[1] * z).
  *   cell_start [dims0*dims1*dims2 + 1] int32: atoms of cell k are
  *   atom_perm[cell_start[k] .. cell_start[k+1]), in ascending atom index.
- *   All arrays host or device; outputs are written where they live.
+ *   All arrays host or device; outputs are written where they live.  The
+ *   time is bounded by n_atoms however the atoms crowd into cells.
  */
 int gs_bin_atoms(const double *atoms, int64_t n_atoms, double cell_size, const double *origin,
                  const int64_t *dims, int32_t *cell_start, int32_t *atom_perm, void *stream);
@@ -254,9 +255,13 @@ int gs_bin_atoms(const double *atoms, int64_t n_atoms, double cell_size, const d
  *   [n_atoms] must be device memory on the current device; origin [3] and
  *   dims [3] are host arrays.  Same results as gs_bin_atoms.
  *   Limits: n_atoms <= GS_STATIC_MAX_ATOMS, cells <= GS_STATIC_MAX_CELLS;
- *   larger requests, host pointers or NULLs return GS_ERR_ARG.
+ *   larger requests, host pointers, memory of another device or NULLs
+ *   return GS_ERR_ARG.  Buffer lengths cannot be checked through plain
+ *   pointers: shorter buffers than the above are the caller's error (the
+ *   Python binding checks them).  The time is bounded by n_atoms however
+ *   the atoms crowd into cells (stable radix passes, no per-cell sort).
  *   No cudaMalloc, cudaFree or allocating library call is made: the
- *   temporaries live in one fixed device array (about 12.6 MB, reserved on
+ *   temporaries live in one fixed device array (about 18 MB, reserved on
  *   every GPU that loads the library until the process exits).  Every call
  *   shares that array; calls whose work overlaps on the GPU race and give
  *   wrong results.  The first call on a device looks up the array's address

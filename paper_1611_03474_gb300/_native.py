@@ -332,13 +332,41 @@ def gs_bin_atoms(atoms, cell_size, origin, dims, stream=None):
     return cs, pm
 
 
+def _require_device_tensor(name, t, dtype, min_numel, device):
+    """t must be a contiguous torch tensor of dtype on `device` with at least
+    min_numel elements (checked before the call: nothing reaches the GPU)."""
+    import torch
+    if not isinstance(t, torch.Tensor):
+        raise GsError(-1, "%s must be a torch tensor in device memory" % name)
+    if t.dtype != dtype:
+        raise GsError(-1, "%s must be %s, not %s" % (name, dtype, t.dtype))
+    if t.device.type != "cuda" or t.device.index != device:
+        raise GsError(-1, "%s must be on cuda:%d (the current device), not %s" % (name, device, t.device))
+    if not t.is_contiguous():
+        raise GsError(-1, "%s must be contiguous" % name)
+    if t.numel() < min_numel:
+        raise GsError(-1, "%s has %d elements, needs at least %d" % (name, t.numel(), min_numel))
+
+
 def gs_bin_atoms_static(atoms, cell_size, origin, dims, cell_start, atom_perm, stream=None):
     """Allocation-free cell list into caller-provided device buffers (torch
-    CUDA tensors: atoms float64 [n,3], cell_start int32 [ncell+1], atom_perm
-    int32 [n]); see include/gsmesh.h for the limits and the sharing rules."""
+    CUDA tensors on the current device: atoms float64 [n,3], cell_start int32
+    with at least prod(dims)+1 elements, atom_perm int32 with at least n);
+    see include/gsmesh.h for the limits and the sharing rules.  Wrong types,
+    shapes, sizes or devices raise GsError before any GPU work."""
+    import torch
     L = load()
     origin = np.ascontiguousarray(origin, dtype=np.float64)
     dims = np.ascontiguousarray(dims, dtype=np.int64)
+    if origin.shape != (3,) or dims.shape != (3,):
+        raise GsError(-1, "origin and dims must have 3 entries")
+    dev = torch.cuda.current_device()
+    if not isinstance(atoms, torch.Tensor) or atoms.dim() != 2 or atoms.shape[1] != 3:
+        raise GsError(-1, "atoms must be a torch tensor of shape [n, 3]")
+    _require_device_tensor("atoms", atoms, torch.float64, 3 * atoms.shape[0], dev)
+    ncell = int(np.prod(dims)) if np.all(dims > 0) else 0
+    _require_device_tensor("cell_start", cell_start, torch.int32, ncell + 1, dev)
+    _require_device_tensor("atom_perm", atom_perm, torch.int32, atoms.shape[0], dev)
     _check(L.gs_bin_atoms_static(_ptr(atoms), int(atoms.shape[0]), cell_size, _ptr(origin), _ptr(dims),
                                  _ptr(cell_start), _ptr(atom_perm), _stream_ptr(stream)))
 

@@ -1,7 +1,11 @@
-// gs_bin.cu -- atom preparation and the uniform cell list (stable counting
-// sort).  The cell list drives the neighbourhood truncation of section
-// 2.2.1: only atoms whose cutoff sphere meets a cube (a point) are summed.
+// gs_bin.cu -- atom preparation and the uniform cell list: per-cell counts
+// and their exclusive scan give the cell offsets, and stable radix passes on
+// the cell index (gs_radix.cuh) order the atoms by cell, ascending atom index
+// within a cell, in time bounded by the number of atoms.  The cell list
+// drives the neighbourhood truncation of section 2.2.1: only atoms whose
+// cutoff sphere meets a cube (a point) are summed.
 #include "gs_host.cuh"
+#include "gs_radix.cuh"
 
 // order-preserving map of doubles to unsigned integers (for atomic min/max)
 __device__ __forceinline__ unsigned long long dbl_ord(double v)
@@ -78,33 +82,10 @@ __global__ void k_cell_count(const double *__restrict__ xyz, int64_t n, double o
     atomicAdd((unsigned long long *)&counts[k], 1ull);
 }
 
-__global__ void k_cell_scatter(const int32_t *__restrict__ cell_of_atom, int64_t n, const int64_t *__restrict__ start,
-                               int32_t *__restrict__ fill, int32_t *__restrict__ perm)
-{
-    int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    if (i >= n) return;
-    int k = cell_of_atom[i];
-    int pos = (int)start[k] + atomicAdd(&fill[k], 1);
-    perm[pos] = (int32_t)i;
-}
-
-// restore ascending atom order inside each cell (the scatter's atomics are
-// unordered); insertion sort, cells are small
-__global__ void k_cell_sort(const int64_t *__restrict__ start, int64_t ncell, int64_t n, int32_t *__restrict__ perm,
-                            int32_t *__restrict__ cell_start)
+__global__ void k_cell_starts(const int64_t *__restrict__ start, int64_t ncell, int32_t *__restrict__ cell_start)
 {
     int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    if (k > ncell) return;
-    int64_t s = start[k];
-    cell_start[k] = (int32_t)s;
-    if (k == ncell) return;
-    int64_t e = start[k + 1];
-    for (int64_t i = s + 1; i < e; i++) {
-        int32_t v = perm[i];
-        int64_t j = i - 1;
-        while (j >= s && perm[j] > v) { perm[j + 1] = perm[j]; j--; }
-        perm[j + 1] = v;
-    }
+    if (k <= ncell) cell_start[k] = (int32_t)start[k];
 }
 
 __global__ void k_gather_atoms(const int32_t *__restrict__ perm, int64_t n, const double *__restrict__ xyz,
@@ -168,23 +149,45 @@ int gs_build_cells(const double *d_xyz, int64_t n, const double origin[3], doubl
 {
     int64_t ncell = (int64_t)cdim[0] * cdim[1] * cdim[2];
     int64_t *counts = nullptr;
-    int32_t *coa = nullptr, *fill = nullptr;
+    int32_t *coa = nullptr;
     int rc = gs_alloc((void **)&counts, sizeof(int64_t) * (size_t)(ncell + 1), st);
     if (!rc) rc = gs_alloc((void **)&coa, sizeof(int32_t) * (size_t)n, st);
-    if (!rc) rc = gs_alloc((void **)&fill, sizeof(int32_t) * (size_t)ncell, st);
-    if (rc) { gs_free(counts, st); gs_free(coa, st); gs_free(fill, st); return rc; }
+    if (rc) { gs_free(counts, st); gs_free(coa, st); return rc; }
     cudaMemsetAsync(counts, 0, sizeof(int64_t) * (size_t)(ncell + 1), st);
-    cudaMemsetAsync(fill, 0, sizeof(int32_t) * (size_t)ncell, st);
     double inv = 1.0 / cell;
     unsigned nb = (unsigned)((n + 255) / 256);
     GS_LAUNCH(k_cell_count, nb, 256, 0, st)(d_xyz, n, origin[0], origin[1], origin[2], inv, cdim[0], cdim[1], cdim[2], coa,
                                      counts);
     rc = gs_scan_i64(counts, ncell + 1, nullptr, st);
-    if (!rc) {
-        GS_LAUNCH(k_cell_scatter, nb, 256, 0, st)(coa, n, counts, fill, d_perm);
-        GS_LAUNCH(k_cell_sort, (unsigned)((ncell + 1 + 255) / 256), 256, 0, st)(counts, ncell, n, d_perm, d_cell_start);
+    if (!rc) GS_LAUNCH(k_cell_starts, (unsigned)((ncell + 1 + 255) / 256), 256, 0, st)(counts, ncell, d_cell_start);
+    // atoms grouped by cell, ascending atom index within a cell: stable radix
+    // passes on the cell index (time bounded by n whatever the cell sizes)
+    const int passes = rs_passes(ncell);
+    const int64_t nblk = (n + RS_TILE - 1) / RS_TILE;
+    int64_t *hist = nullptr;
+    int32_t *kb = nullptr, *vb = nullptr;
+    if (!rc && passes > 0) {
+        rc = gs_alloc((void **)&hist, sizeof(int64_t) * (size_t)(256 * nblk + 1), st);
+        if (!rc) rc = gs_alloc((void **)&kb, sizeof(int32_t) * (size_t)n, st);
+        if (!rc) rc = gs_alloc((void **)&vb, sizeof(int32_t) * (size_t)n, st);
     }
-    gs_free(counts, st); gs_free(coa, st); gs_free(fill, st);
+    if (!rc && passes == 0) GS_LAUNCH(k_rs_iota, nb, 256, 0, st)(d_perm, n);
+    int32_t *kbuf[2] = {kb, coa};
+    int32_t *vbuf[2];
+    vbuf[(passes - 1) & 1] = d_perm;   // the last pass writes the output
+    vbuf[passes & 1] = vb;
+    for (int p = 0; p < passes && !rc; p++) {
+        const int32_t *kin = p == 0 ? coa : kbuf[(p - 1) & 1];
+        int32_t *kout = p == passes - 1 ? nullptr : kbuf[p & 1];
+        const int32_t *vin = p == 0 ? nullptr : vbuf[(p - 1) & 1];
+        GS_LAUNCH(k_rs_hist<int64_t>, (unsigned)nblk, RS_THREADS, 0, st)(kin, n, 8 * p, hist, nblk);
+        rc = gs_scan_i64(hist, 256 * nblk, nullptr, st);
+        if (!rc)
+            GS_LAUNCH(k_rs_scatter<int64_t>, (unsigned)nblk, RS_THREADS, 0, st)(kin, vin, n, 8 * p, hist, nblk, kout,
+                                                                              vbuf[p & 1]);
+    }
+    gs_free(counts, st); gs_free(coa, st);
+    gs_free(hist, st); gs_free(kb, st); gs_free(vb, st);
     if (rc) return rc;
     GS_CHECK(cudaGetLastError());
     return GS_OK;

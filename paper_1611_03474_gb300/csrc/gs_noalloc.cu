@@ -10,8 +10,12 @@
 // inputs and outputs; the temporaries live in g_bin_scratch below.
 //
 // Limits: at most GS_STATIC_MAX_ATOMS atoms and GS_STATIC_MAX_CELLS cells.
-// The array (GS_STATIC_SCRATCH_BYTES, about 12.6 MB) is reserved on every
-// GPU that loads the library, until the process exits.
+// The array (GS_STATIC_SCRATCH_BYTES, about 18 MB) is reserved on every GPU
+// that loads the library, until the process exits.
+//
+// The atoms are ordered by cell with the same stable radix passes as the
+// allocating entry point (gs_radix.cuh), so the time is bounded by the
+// number of atoms however they crowd into cells.
 //
 // Sharing: every call uses the same array and it keeps the previous call's
 // contents; the counters that must start at zero are cleared by each call.
@@ -24,13 +28,17 @@
 #include <mutex>
 
 #include "gs_internal.cuh"
+#include "gs_radix.cuh"
 
 #define GS_STATIC_SCAN_THREADS 512
 #define GS_STATIC_SCAN_TILE (GS_STATIC_SCAN_THREADS * 4)
-// counts [cells+1] + fill [cells] + cell of each atom [atoms] + tile sums, all int32
+// int32 words: counts [cells+1], cell of each atom [atoms], radix key and
+// value buffers [atoms] each, digit histograms [256 * radix blocks] and the
+// scan's tile sums (for the longer of counts and histograms)
+#define GS_STATIC_RS_BLOCKS ((GS_STATIC_MAX_ATOMS + RS_TILE - 1) / RS_TILE)
 #define GS_STATIC_TILES ((GS_STATIC_MAX_CELLS + 1 + GS_STATIC_SCAN_TILE - 1) / GS_STATIC_SCAN_TILE)
 #define GS_STATIC_SCRATCH_WORDS \
-    ((GS_STATIC_MAX_CELLS + 1) + GS_STATIC_MAX_CELLS + GS_STATIC_MAX_ATOMS + GS_STATIC_TILES + 64)
+    ((GS_STATIC_MAX_CELLS + 1) + 3 * GS_STATIC_MAX_ATOMS + 256 * GS_STATIC_RS_BLOCKS + GS_STATIC_TILES + 64)
 #define GS_STATIC_SCRATCH_BYTES (4ull * GS_STATIC_SCRATCH_WORDS)
 
 static __device__ __align__(256) int32_t g_bin_scratch[GS_STATIC_SCRATCH_WORDS];
@@ -147,38 +155,27 @@ __global__ void k_static_tile_apply(int32_t *__restrict__ v, int64_t n, const in
     }
 }
 
-__global__ void k_static_scatter(const int32_t *__restrict__ cell_of_atom, int64_t n, const int32_t *__restrict__ start,
-                                 int32_t *__restrict__ fill, int32_t *__restrict__ perm)
-{
-    int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    if (i >= n) return;
-    int k = cell_of_atom[i];
-    perm[start[k] + atomicAdd(&fill[k], 1)] = (int32_t)i;
-}
-
-// ascending atom order inside each cell; copies the offsets to the output
-__global__ void k_static_sort(const int32_t *__restrict__ start, int64_t ncell, int32_t *__restrict__ perm,
-                              int32_t *__restrict__ cell_start)
+__global__ void k_static_starts(const int32_t *__restrict__ start, int64_t ncell, int32_t *__restrict__ cell_start)
 {
     int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    if (k > ncell) return;
-    int32_t s = start[k];
-    cell_start[k] = s;
-    if (k == ncell) return;
-    int32_t e = start[k + 1];
-    for (int32_t i = s + 1; i < e; i++) {
-        int32_t v = perm[i];
-        int32_t j = i - 1;
-        while (j >= s && perm[j] > v) { perm[j + 1] = perm[j]; j--; }
-        perm[j + 1] = v;
-    }
+    if (k <= ncell) cell_start[k] = start[k];
 }
 
-static bool is_device_ptr(const void *p)
+// exclusive scan of m int32 values in place (tile sums in sums)
+static void static_scan(int32_t *v, int64_t m, int32_t *sums, cudaStream_t st)
+{
+    int64_t tiles = (m + GS_STATIC_SCAN_TILE - 1) / GS_STATIC_SCAN_TILE;
+    k_static_tile_sums<<<(unsigned)tiles, GS_STATIC_SCAN_THREADS, 0, st>>>(v, m, sums);
+    k_static_scan_sums<<<1, GS_STATIC_SCAN_THREADS, 0, st>>>(sums, tiles);
+    k_static_tile_apply<<<(unsigned)tiles, GS_STATIC_SCAN_THREADS, 0, st>>>(v, m, sums);
+}
+
+// device (or managed) memory of the current device
+static bool is_device_ptr(const void *p, int dev)
 {
     cudaPointerAttributes a;
     if (cudaPointerGetAttributes(&a, p) != cudaSuccess) { cudaGetLastError(); return false; }
-    return a.type == cudaMemoryTypeDevice || a.type == cudaMemoryTypeManaged;
+    return (a.type == cudaMemoryTypeDevice || a.type == cudaMemoryTypeManaged) && a.device == dev;
 }
 
 extern "C" int gs_bin_atoms_static(const double *atoms, int64_t n_atoms, double cell_size, const double *origin,
@@ -192,33 +189,52 @@ extern "C" int gs_bin_atoms_static(const double *atoms, int64_t n_atoms, double 
     int cd[3];
     for (int a = 0; a < 3; a++) {
         if (dims[a] <= 0 || dims[a] > GS_STATIC_MAX_CELLS)
-            return gs_fail(GS_ERR_ARG, "gs_bin_atoms_static: dims must be positive");
+            return gs_fail(GS_ERR_ARG, "gs_bin_atoms_static: each of dims must be in [1, %d]", GS_STATIC_MAX_CELLS);
         cd[a] = (int)dims[a];
         ncell *= dims[a];
         if (ncell > GS_STATIC_MAX_CELLS)
             return gs_fail(GS_ERR_ARG, "gs_bin_atoms_static: at most %d cells", GS_STATIC_MAX_CELLS);
     }
-    if (!is_device_ptr(atoms) || !is_device_ptr(cell_start) || !is_device_ptr(atom_perm))
-        return gs_fail(GS_ERR_ARG, "gs_bin_atoms_static: atoms, cell_start and atom_perm must be device memory");
+    int dev = 0;
+    cudaError_t de = cudaGetDevice(&dev);
+    if (de != cudaSuccess) return gs_fail_cuda(de, "cudaGetDevice", __FILE__, __LINE__);
+    if (!is_device_ptr(atoms, dev) || !is_device_ptr(cell_start, dev) || !is_device_ptr(atom_perm, dev))
+        return gs_fail(GS_ERR_ARG, "gs_bin_atoms_static: atoms, cell_start and atom_perm must be device memory of "
+                                   "the current device");
     int32_t *scr = nullptr;
     int rc = static_scratch(&scr);
     if (rc) return rc;
+    const int64_t nblk = (n_atoms + RS_TILE - 1) / RS_TILE;
     int32_t *counts = scr;                       // [ncell + 1]
-    int32_t *fill = counts + (ncell + 1);        // [ncell]
-    int32_t *coa = fill + ncell;                 // [n_atoms]
-    int32_t *sums = coa + n_atoms;               // [tiles]
+    int32_t *coa = counts + (ncell + 1);         // [n_atoms]
+    int32_t *kb = coa + n_atoms;                 // [n_atoms]
+    int32_t *vb = kb + n_atoms;                  // [n_atoms]
+    int32_t *hist = vb + n_atoms;                // [256 * nblk]
+    int32_t *sums = hist + 256 * nblk;           // [tiles]
     cudaStream_t st = (cudaStream_t)stream;
-    int64_t nz = 2 * ncell + 1;
+    const unsigned nb = (unsigned)((n_atoms + 255) / 256);
+    int64_t nz = ncell + 1;
     k_static_zero<<<(unsigned)((nz + 255) / 256 < 4096 ? (nz + 255) / 256 : 4096), 256, 0, st>>>(counts, nz);
-    k_static_count<<<(unsigned)((n_atoms + 255) / 256), 256, 0, st>>>(atoms, n_atoms, origin[0], origin[1], origin[2],
-                                                                      1.0 / cell_size, cd[0], cd[1], cd[2], coa, counts);
-    int64_t m = ncell + 1;
-    int64_t tiles = (m + GS_STATIC_SCAN_TILE - 1) / GS_STATIC_SCAN_TILE;
-    k_static_tile_sums<<<(unsigned)tiles, GS_STATIC_SCAN_THREADS, 0, st>>>(counts, m, sums);
-    k_static_scan_sums<<<1, GS_STATIC_SCAN_THREADS, 0, st>>>(sums, tiles);
-    k_static_tile_apply<<<(unsigned)tiles, GS_STATIC_SCAN_THREADS, 0, st>>>(counts, m, sums);
-    k_static_scatter<<<(unsigned)((n_atoms + 255) / 256), 256, 0, st>>>(coa, n_atoms, counts, fill, atom_perm);
-    k_static_sort<<<(unsigned)((ncell + 1 + 255) / 256), 256, 0, st>>>(counts, ncell, atom_perm, cell_start);
+    k_static_count<<<nb, 256, 0, st>>>(atoms, n_atoms, origin[0], origin[1], origin[2], 1.0 / cell_size, cd[0], cd[1],
+                                       cd[2], coa, counts);
+    static_scan(counts, ncell + 1, sums, st);
+    k_static_starts<<<(unsigned)((ncell + 1 + 255) / 256), 256, 0, st>>>(counts, ncell, cell_start);
+    // stable radix passes on the cell index; the last writes atom_perm
+    const int passes = rs_passes(ncell);
+    if (passes == 0) k_rs_iota<<<nb, 256, 0, st>>>(atom_perm, n_atoms);
+    int32_t *kbuf[2] = {kb, coa};
+    int32_t *vbuf[2];
+    vbuf[(passes - 1) & 1] = atom_perm;
+    vbuf[passes & 1] = vb;
+    for (int p = 0; p < passes; p++) {
+        const int32_t *kin = p == 0 ? coa : kbuf[(p - 1) & 1];
+        int32_t *kout = p == passes - 1 ? nullptr : kbuf[p & 1];
+        const int32_t *vin = p == 0 ? nullptr : vbuf[(p - 1) & 1];
+        k_rs_hist<int32_t><<<(unsigned)nblk, RS_THREADS, 0, st>>>(kin, n_atoms, 8 * p, hist, nblk);
+        static_scan(hist, 256 * nblk, sums, st);
+        k_rs_scatter<int32_t><<<(unsigned)nblk, RS_THREADS, 0, st>>>(kin, vin, n_atoms, 8 * p, hist, nblk, kout,
+                                                                    vbuf[p & 1]);
+    }
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return gs_fail_cuda(e, "gs_bin_atoms_static launch", __FILE__, __LINE__);
     e = cudaStreamSynchronize(st);

@@ -254,8 +254,11 @@ def window_compare(full, cfg, win, inner=5.0, min_cubes=100, min_tris=500):
     ri = ro[np.searchsorted(rvk[ro], common)]
     assert np.array_equal(gkeys[gi], common) and np.array_equal(rvk[ri], common)
     assert np.abs(gv[gi] - ref["vertices"][ri]).max() < 1e-5
-    # triangles whose three points lie in the common inner set
-    gct = canonical_triangles(gkeys, full["triangles"])
+    # triangles whose three points lie in the common inner set (the whole
+    # mesh's triangles are cut to the inner window first)
+    gt = np.asarray(full["triangles"])
+    gt = gt[gin[gt].all(axis=1)]
+    gct = canonical_triangles(gkeys, gt)
     rct = canonical_triangles(rvk, ref["triangles"])
     gct = gct[np.all(np.isin(gct, common), axis=1)]
     rct = rct[np.all(np.isin(rct, common), axis=1)]

@@ -306,3 +306,21 @@ def test_mesh_into_caller_buffers(chain100):
         gs.mesh_gaussian_surface_into(*args, small, tri, min_edge=cfg["min_edge"])
     assert e.value.code == -3 and e.value.needed[:2] == (nv, nt)
     assert (small == -1.0).all()
+
+
+@pytest.mark.parametrize("case", ["one_cell", "clamped_outliers"])
+def test_cell_list_crowded_cells(case):
+    """The cell list's time does not depend on how atoms crowd into cells
+    (stable radix passes, no per-cell sort): 10^5 atoms in a single cell,
+    and clamped outliers piling into the edge cells, bit-exact against the
+    oracle's cell list."""
+    rng = np.random.default_rng(7)
+    if case == "one_cell":
+        xyz = rng.uniform(0, 1, (100000, 3))
+        origin, cell, dims = np.zeros(3), 2.0, np.array([1, 1, 1])
+    else:
+        xyz = np.concatenate([rng.uniform(-5, 5, (50000, 3)), rng.uniform(-500, 500, (60001, 3))])
+        origin, cell, dims = np.array([-5.0, -5.0, -5.0]), 0.7, np.array([15, 15, 15])
+    cs, pm = gs.gs_bin_atoms(xyz, cell, origin, dims)
+    rs, rp = oracle.cell_list(xyz, cell, origin, dims)
+    assert np.array_equal(cs, rs) and np.array_equal(pm, rp)

@@ -21,7 +21,8 @@ def _case(seed, n, cell, dims):
 
 def test_static_binning_matches_allocating_entry_point():
     assert torch.cuda.is_available()
-    cases = [(_case(21, 200003, 1.7, (40, 45, 50)), 1.7), (_case(22, 777, 3.1, (9, 7, 5)), 3.1)]
+    cases = [(_case(21, 200003, 1.7, (40, 45, 50)), 1.7), (_case(22, 777, 3.1, (9, 7, 5)), 3.1),
+             (_case(23, 5000, 2.0, (1, 1, 1)), 2.0)]
     for (xyz, origin, dims), cell in cases:
         ref_cs, ref_pm = gs.gs_bin_atoms(xyz, cell, origin, dims)
         ncell = int(np.prod(dims))
@@ -44,3 +45,18 @@ def test_static_binning_rejects_oversized_requests():
     with pytest.raises(gs.GsError) as e:
         gs.gs_bin_atoms_static(np.zeros((4, 3)), 1.0, np.zeros(3), np.array([1, 1, 1]), cs, pm)
     assert e.value.code == -1
+
+
+def test_static_binning_rejects_wrong_buffers():
+    """Wrong dtype, short buffers and host tensors are refused before any GPU
+    work (GsError, code -1)."""
+    n, dims = 100, np.array([4, 4, 4])
+    x_d = torch.zeros((n, 3), dtype=torch.float64, device="cuda")
+    ok_cs = torch.zeros(65, dtype=torch.int32, device="cuda")
+    ok_pm = torch.zeros(n, dtype=torch.int32, device="cuda")
+    bad = [(x_d.float(), ok_cs, ok_pm), (x_d, ok_cs[:64], ok_pm), (x_d, ok_cs, ok_pm[:99]),
+           (x_d, ok_cs.long(), ok_pm), (x_d.cpu(), ok_cs, ok_pm), (x_d, ok_cs, ok_pm.cpu())]
+    for a, cs, pm in bad:
+        with pytest.raises(gs.GsError) as e:
+            gs.gs_bin_atoms_static(a, 1.0, np.zeros(3), dims, cs, pm)
+        assert e.value.code == -1
