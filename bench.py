@@ -355,18 +355,47 @@ def main():
     outs = (torch.empty((nv0, 3), dtype=torch.float64).pin_memory(),
             torch.empty((nt0, 3), dtype=torch.int32).pin_memory(),
             torch.empty(nv0, dtype=torch.int64).pin_memory(), torch.empty(nc0, dtype=torch.int64).pin_memory())
-    e2e_times = []
+    e2e_times, e2e_stage = [], None
     for it in range(args.e2e_warmup + args.e2e_steps):
         flush.zero_()
         barrier()
         t0 = time.perf_counter()
-        nv, nt, nc = gs.mesh_gaussian_surface_into(xyz_h, r_h, cfg["D"], cfg["c"], cfg["precision"],
-                                                   cfg["max_depth"], *outs, min_edge=cfg["min_edge"],
-                                                   precision_mode=mode, stream=stream)
+        nv, nt, nc, est = gs.mesh_gaussian_surface_into(xyz_h, r_h, cfg["D"], cfg["c"], cfg["precision"],
+                                                        cfg["max_depth"], *outs, min_edge=cfg["min_edge"],
+                                                        precision_mode=mode, stream=stream, stats=True)
         t1 = time.perf_counter()
         if it >= args.e2e_warmup:
             e2e_times.append((t1 - t0) * 1e3)
+            e2e_stage = {k: est[k] for k in ("ms_total", "ms_upload", "ms_bin", "ms_levels", "ms_field",
+                                             "ms_triangulate", "ms_weld", "ms_download")}
     nbytes_out = 24 * nv + 12 * nt + 8 * nv + 8 * nc
+    # the host link itself: one 1 GiB device-to-host copy into pinned memory
+    # (best of 5), the bound on the end-to-end step's copies; and one copy of
+    # the vertex array's size into the step's own pinned vertex buffer
+    link = None
+    try:
+        vsrc = torch.empty(outs[0].numel(), dtype=torch.float64, device=dev)
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        outs[0].view(-1).copy_(vsrc, non_blocking=True)
+        torch.cuda.synchronize()
+        out_gbps = float(outs[0].numel() * 8 / (time.perf_counter() - t0) / 1e9)
+        del vsrc
+        src = torch.empty(1 << 28, dtype=torch.float32, device=dev)
+        dst = torch.empty(1 << 28, dtype=torch.float32).pin_memory()
+        bt = []
+        for _ in range(5):
+            torch.cuda.synchronize()
+            t0 = time.perf_counter()
+            dst.copy_(src, non_blocking=True)
+            torch.cuda.synchronize()
+            bt.append(time.perf_counter() - t0)
+        link = {"d2h_GBps": float((1 << 30) / min(bt) / 1e9), "bytes": 1 << 30,
+                "how": "torch copy of 1 GiB from device to pinned host memory, best of 5",
+                "into_vertex_buffer_GBps": out_gbps}
+        del src, dst
+    except Exception as e:  # noqa: BLE001 (reported, not fatal)
+        link = {"error": str(e)[:200]}
     mh = types.SimpleNamespace(vertices=outs[0][:nv].numpy(), triangles=outs[1][:nt].numpy(),
                                vertex_keys=outs[2][:nv].numpy().view(np.uint64),
                                cube_keys=outs[3][:nc].numpy().view(np.uint64))
@@ -523,7 +552,7 @@ def main():
                 "d2h_bytes_per_step": int(nbytes_out), "runs": len(e2e_times), "warmup_runs": args.e2e_warmup,
                 "min_ms": float(np.min(e2e_times)), "max_ms": float(np.max(e2e_times)),
                 "copy_GBps_est": float(nbytes_out / ((e2e_ms - ms_per_mesh) * 1e-3) / 1e9)
-                if e2e_ms > ms_per_mesh else None},
+                if e2e_ms > ms_per_mesh else None, "link": link, "stage_ms_last": e2e_stage},
         "gpu_launches": int(st["n_kernel_launches"]),
         "fp64_form": fp64,
         "adaptive_form": adaptive,

@@ -18,6 +18,16 @@
  *  - Return value 0 on success, a negative GS_ERR_* code otherwise; nothing
  *    is thrown across the ABI.  gs_last_error() gives a message for the
  *    calling thread's last failure.  Output structs are zeroed on error.
+ *  - Host waits poll with a deadline (environment GS_WAIT_TIMEOUT_S,
+ *    seconds, default 600) and return GS_ERR_TIMEOUT after it; every device
+ *    loop is bounded.  A mesh call whose level loop runs out of device
+ *    memory or of an internal table is run once more with smaller level
+ *    chunks (gs_stats.retries).  For testing these paths, the environment
+ *    variable GS_FAULT injects a failure on the host, read at each call:
+ *    "alloc@K" (the K-th device allocation fails: GS_ERR_OOM), "capacity@L"
+ *    (level L reports a full table on the first attempt: the retry runs),
+ *    "timeout" (the first host wait times out: GS_ERR_TIMEOUT).  Nothing is
+ *    injected on the device.
  *  - Terms below cutoff_rel * c are dropped: atom i contributes at a point
  *    (a cube) iff the squared distance to the point (to the box) is at most
  *    R_i^2 = r_i^2 - ln(cutoff_rel * c) / D (section 2.2.1, the
@@ -47,7 +57,7 @@ extern "C" {
 #define GS_ERR_ARG (-1)           /* invalid argument (sizes, non-finite values, ranges) */
 #define GS_ERR_OOM (-2)           /* device or host allocation failed */
 #define GS_ERR_CAPACITY (-3)      /* an internal bound was exceeded (hash full, too many points) */
-#define GS_ERR_TIMEOUT (-4)       /* a bounded device loop or host wait gave up */
+#define GS_ERR_TIMEOUT (-4)       /* a host wait passed its deadline (GS_WAIT_TIMEOUT_S seconds, default 600) */
 #define GS_ERR_CUDA (-5)          /* a CUDA runtime call failed */
 #define GS_ERR_DEVICE_STATUS (-6) /* a kernel reported an inconsistency through its status word */
 
@@ -120,6 +130,8 @@ typedef struct {
     int64_t agreement_splits;     /* cubes split because such an interpolant and the field value lay on
                                      different sides of c */
     int64_t mixed_cubes;          /* final cubes with a neighbour of another size across a face or an edge */
+    int64_t retries;              /* 1 when the level loop ran out of device memory or of an internal table and
+                                     the call was run again with smaller level chunks */
 } gs_stats;
 
 typedef struct {

@@ -37,7 +37,7 @@ class Stats(ctypes.Structure):
                 ("mixed_err_ratio", ctypes.c_double), ("mixed_band_ratio", ctypes.c_double),
                 ("recheck_rank", ctypes.c_int64), ("vertex_mark_cubes", ctypes.c_int64 * 3),
                 ("estimate_fast_cubes", ctypes.c_int64), ("constrained_vertices", ctypes.c_int64),
-                ("agreement_splits", ctypes.c_int64), ("mixed_cubes", ctypes.c_int64)]
+                ("agreement_splits", ctypes.c_int64), ("mixed_cubes", ctypes.c_int64), ("retries", ctypes.c_int64)]
 
     def as_dict(self, max_depth=20):
         d = {}
@@ -233,6 +233,61 @@ def mesh_gaussian_surface(atoms, radii, D, c, precision, max_depth, min_edge=0.2
     return _mesh_from_c(m, L, st, max_depth)
 
 
+class _DeviceArray:
+    """A view of library-owned device memory for torch.as_tensor (the CUDA
+    array interface); the caller copies it before the memory is released."""
+
+    def __init__(self, ptr, shape, typestr):
+        self.__cuda_array_interface__ = {"data": (int(ptr) if ptr else 0, False), "shape": tuple(shape),
+                                         "typestr": typestr, "strides": None, "version": 3}
+
+
+def mesh_gaussian_surface_device(atoms, radii, D, c, precision, max_depth, min_edge=0.25, precision_mode=GS_PREC_FP64,
+                                 cutoff_rel=1e-8, stream=None, debug_flags=0, conform_mode=GS_CONFORM_CONSTRAIN):
+    """Mesh {phi = c} with the result in device memory owned by torch:
+    atoms [n,3] and radii [n] (float64 torch tensors, CUDA or host) in;
+    returns (vertices [nv,3] float64, triangles [nt,3] int32, vertex_keys
+    [nv] int64 (the uint64 keys' bits), cube_keys [nc] int64, stats) as
+    tensors on the current CUDA device.  The mesh never visits the host: the
+    library's device arrays are copied into torch's (device to device) and
+    released."""
+    import torch
+    L = load()
+    atoms = _host64(atoms, (-1, 3))
+    radii = _host64(radii)
+    n = atoms.shape[0]
+    st = Stats()
+    o = L.gs_default_options()
+    o.min_edge = min_edge
+    o.precision_mode = precision_mode
+    o.cutoff_rel = cutoff_rel
+    o.cuda_stream = _stream_ptr(stream)
+    o.device_output = 1
+    o.debug_flags = debug_flags
+    o.conform_mode = conform_mode
+    o.stats = ctypes.pointer(st)
+    m = MeshC()
+    _check(L.mesh_gaussian_surface(_ptr(atoms), _ptr(radii), n, D, c, precision, max_depth, ctypes.byref(o),
+                                   ctypes.byref(m)))
+    try:
+        dev = torch.device("cuda", torch.cuda.current_device())
+
+        def grab(ptr, shape, typestr, dtype):
+            if int(np.prod(shape)) == 0:
+                return torch.empty(shape, dtype=dtype, device=dev)
+            addr = ctypes.cast(ptr, ctypes.c_void_p).value
+            return torch.as_tensor(_DeviceArray(addr, shape, typestr), device=dev).clone()
+
+        v = grab(m.vertices, (m.n_vertices, 3), "<f8", torch.float64)
+        t = grab(m.triangles, (m.n_triangles, 3), "<i4", torch.int32)
+        k = grab(m.vertex_keys, (m.n_vertices,), "<i8", torch.int64)
+        ck = grab(m.cube_keys, (m.n_cubes,), "<i8", torch.int64)
+        torch.cuda.synchronize(dev)
+    finally:
+        L.mesh_free(ctypes.byref(m))
+    return v, t, k, ck, st.as_dict(max_depth)
+
+
 def mesh_gaussian_surface_into(atoms, radii, D, c, precision, max_depth, vertices, triangles, vertex_keys=None,
                                cube_keys=None, min_edge=0.25, precision_mode=GS_PREC_FP64, cutoff_rel=1e-8,
                                stream=None, stats=False):
@@ -380,7 +435,14 @@ def gs_mesh_backward(atoms, radii, D, c, precision, max_depth, grad_vertices, mi
     radii = _host64(radii)
     gv = _host64(grad_vertices, (-1, 3))
     n = atoms.shape[0]
-    ga, gr, gD = np.zeros((n, 3)), np.zeros(n), np.zeros(1)
+    if hasattr(atoms, "is_cuda") and atoms.is_cuda:
+        # device tensors in, device tensors out (no host round trip)
+        import torch
+        ga = torch.zeros((n, 3), dtype=torch.float64, device=atoms.device)
+        gr = torch.zeros(n, dtype=torch.float64, device=atoms.device)
+        gD = torch.zeros(1, dtype=torch.float64, device=atoms.device)
+    else:
+        ga, gr, gD = np.zeros((n, 3)), np.zeros(n), np.zeros(1)
     o = L.gs_default_options()
     o.min_edge = min_edge
     o.precision_mode = precision_mode
@@ -388,6 +450,8 @@ def gs_mesh_backward(atoms, radii, D, c, precision, max_depth, grad_vertices, mi
     o.cuda_stream = _stream_ptr(stream)
     _check(L.gs_mesh_backward(_ptr(atoms), _ptr(radii), n, D, c, precision, max_depth, ctypes.byref(o), _ptr(gv),
                               gv.shape[0], _ptr(ga), _ptr(gr), _ptr(gD)))
+    if not isinstance(ga, np.ndarray):
+        return ga, gr, gD[0]
     return ga, gr, float(gD[0])
 
 
@@ -398,9 +462,16 @@ def gs_volume_area(vertices, triangles, grad=False, stream=None):
     v = _host64(vertices, (-1, 3))
     t = triangles if hasattr(triangles, "data_ptr") else np.ascontiguousarray(triangles, dtype=np.int32)
     nv, nt = v.shape[0], t.shape[0]
-    va = np.zeros(2)
-    gV = np.zeros((nv, 3)) if grad else None
-    gA = np.zeros((nv, 3)) if grad else None
+    if hasattr(v, "is_cuda") and v.is_cuda:
+        # device tensors in, device tensors out
+        import torch
+        va = torch.zeros(2, dtype=torch.float64, device=v.device)
+        gV = torch.zeros((nv, 3), dtype=torch.float64, device=v.device) if grad else None
+        gA = torch.zeros((nv, 3), dtype=torch.float64, device=v.device) if grad else None
+    else:
+        va = np.zeros(2)
+        gV = np.zeros((nv, 3)) if grad else None
+        gA = np.zeros((nv, 3)) if grad else None
     o = L.gs_default_options()
     o.cuda_stream = _stream_ptr(stream)
     _check(L.gs_volume_area(_ptr(v), nv, _ptr(t), nt, _ptr(va), _ptr(gV), _ptr(gA), ctypes.byref(o)))

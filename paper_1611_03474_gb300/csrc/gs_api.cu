@@ -15,7 +15,10 @@
 
 #include "gs_host.cuh"
 
+#include <nvtx3/nvToolsExt.h>
+
 #include <algorithm>
+#include <initializer_list>
 #include <atomic>
 #include <string>
 #include <thread>
@@ -78,6 +81,7 @@ static std::mutex g_init_mu;
 static bool g_dev_ready[64];
 static int device_setup(void)
 {
+    gs_guard_begin();   // every API call starts here: the call's fault-injection state
     int dev = 0;
     GS_CHECK(cudaGetDevice(&dev));
     std::lock_guard<std::mutex> lk(g_init_mu);
@@ -93,6 +97,19 @@ static int device_setup(void)
     if (dev >= 0 && dev < 64) g_dev_ready[dev] = true;
     return GS_OK;
 }
+
+// NVTX range for the lifetime of a scope (a phase or a level), visible in
+// timeline profilers; a no-op without one attached
+struct NvtxRange {
+    bool on = true;
+    explicit NvtxRange(const char *name) { nvtxRangePushA(name); }
+    void end()
+    {
+        if (on) nvtxRangePop();
+        on = false;
+    }
+    ~NvtxRange() { end(); }
+};
 
 // a simple scope guard for stream-ordered device buffers
 struct DevBufs {
@@ -153,7 +170,7 @@ static int check_status(unsigned *d_status, cudaStream_t st, const char *stage)
 {
     unsigned h = 0;
     GS_CHECK(cudaMemcpyAsync(&h, d_status, sizeof(unsigned), cudaMemcpyDeviceToHost, st));
-    GS_CHECK(cudaStreamSynchronize(st));
+    GS_CHECK(gs_sync(st));
     if (h & GS_ST_INPUT) return gs_fail(GS_ERR_ARG, "non-finite or negative atom data");
     if (h & GS_ST_CAPACITY) return gs_fail(GS_ERR_CAPACITY, "%s: internal table full", stage);
     if (h) return gs_fail(GS_ERR_DEVICE_STATUS, "%s: device status 0x%x", stage, h);
@@ -292,7 +309,7 @@ static int prepare(const double *atoms, const double *radii, int64_t n, double D
     P.cell_start = out->cell_start;
     int t2 = T.mark();
     if (stats) {
-        GS_CHECK(cudaStreamSynchronize(st));
+        GS_CHECK(gs_sync(st));
         stats->ms_upload = T.ms(t0, t1);
         stats->ms_bin = T.ms(t1, t2);
     }
@@ -307,12 +324,14 @@ static int run_level(const GsProblem &P, int level, const uint64_t *d_parents, i
                      uint64_t **d_next, int64_t *n_next, unsigned long long *d_counters, unsigned long long *d_pairs,
                      unsigned long long *d_rechecked, unsigned long long *d_mism, bool both, unsigned *d_status,
                      gs_stats *stats, bool reexpand = false, const double *d_parA = nullptr,
-                     double **d_nextA = nullptr, bool small_chunks = false)
+                     double **d_nextA = nullptr, int64_t CH = (int64_t)1 << 21)
 {
     cudaStream_t st = B.st;
-    // octets per chunk (8 GB of FP64 tensors); debug: 1000, so that small
-    // inputs run the multi-chunk path
-    const int64_t CH = small_chunks ? 1000 : ((int64_t)1 << 21);
+    // CH: octets per chunk (2^21: 8 GB of FP64 tensors; smaller after an
+    // allocation or capacity failure, and 1000 in a debug mode, so that small
+    // inputs run the multi-chunk path)
+    if (gs_fault_capacity(level)) return gs_fail(GS_ERR_CAPACITY, "level %d: internal table full (injected by GS_FAULT)",
+                                                 level);
     std::vector<uint64_t *> nexts;
     std::vector<double *> nextAs;
     std::vector<int64_t> ncnt;
@@ -425,7 +444,7 @@ static int finish_output(MeshDev &M, const gs_options &o, gs_mesh *out, cudaStre
         if (M.nc)
             GS_CHECK(cudaMemcpyAsync(out->cube_keys, M.cubes, sizeof(uint64_t) * (size_t)M.nc, cudaMemcpyDeviceToHost, st));
     }
-    GS_CHECK(cudaStreamSynchronize(st));
+    GS_CHECK(gs_sync(st));
     return GS_OK;
 }
 
@@ -446,7 +465,7 @@ static int finish_into(MeshDev &M, gs_mesh_buffers *b, cudaStream_t st)
     if (M.nt) GS_CHECK(cudaMemcpyAsync(b->triangles, M.tri, sizeof(int32_t) * 3 * (size_t)M.nt, cudaMemcpyDefault, st));
     if (M.nc && b->cube_keys)
         GS_CHECK(cudaMemcpyAsync(b->cube_keys, M.cubes, sizeof(uint64_t) * (size_t)M.nc, cudaMemcpyDefault, st));
-    GS_CHECK(cudaStreamSynchronize(st));
+    GS_CHECK(gs_sync(st));
     return GS_OK;
 }
 
@@ -530,7 +549,7 @@ static int put_out(void *dst, const void *src, size_t bytes, cudaStream_t st);
 
 static int mesh_impl(const double *atoms, const double *radii, int64_t n, double D, double c, double precision,
                      int max_depth, const gs_options &o, gs_mesh *out, cudaStream_t st, const BackReq *bw = nullptr,
-                     gs_mesh_buffers *into = nullptr)
+                     gs_mesh_buffers *into = nullptr, int64_t chunk = (int64_t)1 << 21, bool *retryable = nullptr)
 {
     gs_stats local;
     gs_stats *stats = o.stats ? o.stats : &local;
@@ -549,7 +568,10 @@ static int mesh_impl(const double *atoms, const double *radii, int64_t n, double
     GS_CHECK(cudaMemsetAsync(d_status, 0, sizeof(unsigned), st));
     GS_CHECK(cudaMemsetAsync(d_cnt, 0, 32 * sizeof(unsigned long long), st));
     Prepared PR;
-    rc = prepare(atoms, radii, n, D, c, o.cutoff_rel, precision, o.min_edge, max_depth, B, d_status, &PR, stats, T);
+    {
+        NvtxRange nr("gs: upload, prep, cell list");
+        rc = prepare(atoms, radii, n, D, c, o.cutoff_rel, precision, o.min_edge, max_depth, B, d_status, &PR, stats, T);
+    }
     if (rc) return rc;
     PR.P.order = o.decision_order;
     PR.P.norm = o.precision_norm;
@@ -571,6 +593,9 @@ static int mesh_impl(const double *atoms, const double *radii, int64_t n, double
     if (rc) return rc;
     B.keep(parents);
     for (int l = 0; l <= max_depth && n_oct > 0; l++) {
+        char lname[32];
+        snprintf(lname, sizeof(lname), "gs: level %d", l);
+        NvtxRange nr(lname);
         int ta = T.mark();
         GS_CHECK(cudaMemsetAsync(d_cnt, 0, 5 * sizeof(unsigned long long), st));
         uint64_t *next = nullptr;
@@ -580,20 +605,26 @@ static int mesh_impl(const double *atoms, const double *radii, int64_t n, double
         double *nextA = nullptr;
         rc = run_level(P, l, parents, n_oct, o.precision_mode, B, parts, cnts, &next, &nn, d_cnt, d_cnt + 8,
                        d_cnt + 13, d_cnt + 14, (o.debug_flags & 1) != 0, d_status, stats, reexpand, parentA,
-                       reexpand ? &nextA : nullptr, (o.debug_flags & 2) != 0);
+                       reexpand ? &nextA : nullptr, (o.debug_flags & 2) ? (int64_t)1000 : chunk);
         if (parentA) B.release(parentA);
         parentA = nextA;
         if (parentA) B.keep(parentA);
         for (size_t i = 0; i < parts.size(); i++) { B.keep(parts[i]); acc_all.push_back(parts[i]); acc_cnt.push_back(cnts[i]); }
         if (parents) B.release(parents);
-        if (rc) { gs_free(next, st); return rc; }
+        if (rc) {
+            // out of device memory or of an internal table in the level loop:
+            // the caller may try again with smaller level chunks
+            if (retryable && (rc == GS_ERR_OOM || rc == GS_ERR_CAPACITY)) *retryable = true;
+            gs_free(next, st);
+            return rc;
+        }
         parents = next;
         B.keep(parents);
         n_oct = nn;
         int tb = T.mark();
         unsigned long long h[5];
         GS_CHECK(cudaMemcpyAsync(h, d_cnt, sizeof(h), cudaMemcpyDeviceToHost, st));
-        GS_CHECK(cudaStreamSynchronize(st));
+        GS_CHECK(gs_sync(st));
         stats->examined[l] = (int64_t)h[0]; stats->discarded[l] = (int64_t)h[1]; stats->accepted[l] = (int64_t)h[2];
         stats->forced[l] = (int64_t)h[3]; stats->split[l] = (int64_t)h[4];
         stats->ms_level[l] = T.ms(ta, tb);
@@ -626,31 +657,34 @@ static int mesh_impl(const double *atoms, const double *radii, int64_t n, double
     int acc_levels = 0;
     for (int l = 0; l <= max_depth; l++) acc_levels += (stats->accepted[l] + stats->forced[l]) > 0 ? 1 : 0;
     const bool constrain = acc_levels > 1 && o.conform_mode == GS_CONFORM_CONSTRAIN;
+    NvtxRange nr_field("gs: conformity, lattice, field");
     if (acc_levels > 1) rc = gs_conformity(&cubes, &nc, max_depth, constrain ? 2 : 1, &splits, d_status, st);
     if (rc) { gs_free(cubes, st); return rc; }
     int tc1 = T.mark();
 
     // ---- lattice vertices, the field there (eq linear1's corner values)
     // and, for cubes of different sizes, the constrained values; a sign
-    // disagreement splits the coarser cubes and the whole is rebuilt
+    // disagreement splits the coarser cubes and the lattice is rebuilt, the
+    // vertices it had keeping their field values
+    const bool fp32 = o.precision_mode == GS_PREC_MIXED;
     uint64_t *vkeys = nullptr;
     int32_t *cvid = nullptr;
     int64_t nv = 0;
-    double *phi = nullptr;
-    float *err = nullptr;
+    double *phi = nullptr, *raw = nullptr;
+    float *err = nullptr, *raw_err = nullptr;
     int64_t *mark = nullptr;
     GsHash hv{nullptr, nullptr, 0}, hc{nullptr, nullptr, 0};
     uint64_t *vslot = nullptr;
     GsCons K{nullptr, nullptr, nullptr, 0, 0};
     uint8_t *mixed = nullptr;
     int64_t n_mixed = 0, nre = 0;
-    auto release_round = [&]() {
-        B.release(vkeys); B.release(cvid); B.release(phi); B.release(err); B.release(mark);
-        B.release(hv.keys); B.release(hv.vals); B.release(vslot); B.release(hc.keys); B.release(hc.vals);
-        B.release(K.lev); B.release(K.src); B.release(K.t); B.release(mixed);
-        vkeys = nullptr; cvid = nullptr; phi = nullptr; err = nullptr; mark = nullptr; vslot = nullptr;
-        hv = GsHash{nullptr, nullptr, 0}; hc = GsHash{nullptr, nullptr, 0};
-        K = GsCons{nullptr, nullptr, nullptr, 0, 0}; mixed = nullptr;
+    // the previous round's lattice (key -> slot -> id), raw field values and bounds
+    GsHash hv_old{nullptr, nullptr, 0};
+    uint64_t *vslot_old = nullptr;
+    double *raw_old = nullptr;
+    float *err_old = nullptr;
+    auto release_all = [&](std::initializer_list<void *> ps) {
+        for (void *q : ps) B.release(q);
     };
     B.keep(cubes);
     for (int iter = 0;; iter++) {
@@ -660,15 +694,25 @@ static int mesh_impl(const double *atoms, const double *radii, int64_t n, double
         B.keep(vkeys); B.keep(cvid); B.keep(hv.keys); B.keep(hv.vals); B.keep(vslot);
         if (rc) return rc;
         rc = B.get(&phi, (size_t)nv + 1);
+        if (!rc && fp32) rc = B.get(&err, (size_t)nv + 1);
+        if (!rc) rc = B.get(&mark, (size_t)nv + 1);
         if (rc) return rc;
-        if (o.precision_mode == GS_PREC_FP64) {
-            rc = gs_field_f64(P, vkeys, nullptr, nv, phi, nullptr, d_cnt + 9, st);
+        if (hv_old.keys) {
+            // after a split: the old vertices keep their values, the new ones are evaluated
+            int64_t ndone = 0;
+            rc = gs_field_reuse(vkeys, nv, hv_old, vslot_old, raw_old, err_old, phi, err, mark, st);
+            if (!rc) rc = gs_field_partial(P, fp32 ? 1 : 0, vkeys, nv, mark, phi, err, d_cnt + 9, &ndone, st);
+            release_all({hv_old.keys, hv_old.vals, vslot_old, raw_old, err_old});
+            hv_old = GsHash{nullptr, nullptr, 0}; vslot_old = nullptr; raw_old = nullptr; err_old = nullptr;
+        } else if (fp32) {
+            rc = gs_field_f32(P, vkeys, nullptr, nv, phi, nullptr, err, d_cnt + 9, st);
         } else {
-            // FP32 values; FP64 where the inside test could depend on the FP32 error
-            rc = B.get(&err, (size_t)nv + 1);
-            if (!rc) rc = B.get(&mark, (size_t)nv + 1);
-            if (!rc) rc = gs_field_f32_marked(P, vkeys, nv, phi, err, mark, d_cnt + 9, st);
+            rc = gs_field_f64(P, vkeys, nullptr, nv, phi, nullptr, d_cnt + 9, st);
+        }
+        if (!rc && fp32) {
+            // FP64 where the inside test could depend on the FP32 error
             int64_t n1 = 0;
+            rc = gs_field_flag_near(P, phi, err, nv, mark, st);
             if (!rc) rc = gs_field_recompute(P, vkeys, nv, mark, phi, err, &n1, st);
             nre += n1;
         }
@@ -681,19 +725,38 @@ static int mesh_impl(const double *atoms, const double *radii, int64_t n, double
         rc = gs_cons_alloc(&K, nv, st);
         if (rc) return rc;
         B.keep(K.lev); B.keep(K.src); B.keep(K.t);
-        if (mark) GS_CHECK(cudaMemsetAsync(mark, 0, sizeof(int64_t) * (size_t)(nv + 1), st));
-        rc = gs_cons_find(&K, hc, hv, vslot, vkeys, max_depth, mark, d_cnt + 26, d_status, st);
-        if (!rc && mark) {
-            // the constrained values and their sources in FP64: exact interpolants
+        rc = gs_cons_find(&K, hc, hv, vslot, vkeys, max_depth, nullptr, d_cnt + 26, d_status, st);
+        if (!rc && fp32 && K.ncons > 0) {
+            // certain signs of the constrained values: their sources in FP64
+            // where the interpolated bound leaves the side of c open
+            double *psi = nullptr;
+            float *epsi = nullptr;
+            rc = B.get(&psi, (size_t)nv + 1);
+            if (!rc) rc = B.get(&epsi, (size_t)nv + 1);
+            if (!rc) {
+                GS_CHECK(cudaMemcpyAsync(psi, phi, sizeof(double) * (size_t)nv, cudaMemcpyDeviceToDevice, st));
+                GS_CHECK(cudaMemcpyAsync(epsi, err, sizeof(float) * (size_t)nv, cudaMemcpyDeviceToDevice, st));
+                GS_CHECK(cudaMemsetAsync(mark, 0, sizeof(int64_t) * (size_t)(nv + 1), st));
+                rc = gs_cons_apply(K, hc, vkeys, max_depth, P.c, psi, epsi, mark, nullptr, nullptr, d_cnt + 27, st);
+            }
+            if (!rc) rc = gs_cons_mark_up(K, max_depth, mark, st);
+            if (!rc) rc = gs_cons_unmark(K, mark, st);
             int64_t n1 = 0;
-            rc = gs_field_recompute(P, vkeys, nv, mark, phi, err, &n1, st);
+            if (!rc) rc = gs_field_recompute(P, vkeys, nv, mark, phi, err, &n1, st);
             nre += n1;
+            release_all({psi, epsi});
         }
+        // the raw field values (and bounds), kept for a later round
+        if (!rc) rc = B.get(&raw, (size_t)nv + 1);
+        if (!rc && fp32) rc = B.get(&raw_err, (size_t)nv + 1);
+        if (rc) return rc;
+        GS_CHECK(cudaMemcpyAsync(raw, phi, sizeof(double) * (size_t)nv, cudaMemcpyDeviceToDevice, st));
+        if (fp32) GS_CHECK(cudaMemcpyAsync(raw_err, err, sizeof(float) * (size_t)nv, cudaMemcpyDeviceToDevice, st));
         int64_t *split = nullptr;
-        if (!rc) rc = B.get(&split, (size_t)nc + 1);
+        rc = B.get(&split, (size_t)nc + 1);
         if (!rc) rc = gs_fill_i64(split, nc, 1, st);
         int64_t nflip = 0;
-        if (!rc) rc = gs_cons_apply(K, hc, vkeys, max_depth, P.c, phi, split, &nflip, d_cnt + 27, st);
+        if (!rc) rc = gs_cons_apply(K, hc, vkeys, max_depth, P.c, phi, err, nullptr, split, &nflip, d_cnt + 27, st);
         if (!rc) rc = check_status(d_status, st, "constrained values");
         if (rc) return rc;
         if (nflip > 0) {
@@ -706,10 +769,17 @@ static int mesh_impl(const double *atoms, const double *radii, int64_t n, double
             if (rc) return rc;
             agree_splits += ns;
             splits += ns2;
-            release_round();
+            // this round's lattice, raw values and bounds serve the next
+            hv_old = hv; vslot_old = vslot; raw_old = raw; err_old = raw_err;
+            release_all({vkeys, cvid, phi, err, mark, hc.keys, hc.vals, K.lev, K.src, K.t});
+            vkeys = nullptr; cvid = nullptr; phi = nullptr; err = nullptr; mark = nullptr; raw = nullptr;
+            raw_err = nullptr; vslot = nullptr;
+            hv = GsHash{nullptr, nullptr, 0}; hc = GsHash{nullptr, nullptr, 0};
+            K = GsCons{nullptr, nullptr, nullptr, 0, 0};
             continue;
         }
-        B.release(split);
+        release_all({split, raw, raw_err});
+        raw = nullptr; raw_err = nullptr;
         rc = B.get(&mixed, (size_t)nc + 1);
         if (!rc) rc = gs_mixed_flags(K, cubes, nc, cvid, hv, vslot, max_depth, mixed, &n_mixed, d_cnt + 28, st);
         if (rc) return rc;
@@ -718,24 +788,28 @@ static int mesh_impl(const double *atoms, const double *radii, int64_t n, double
     stats->constrained_vertices = K.ncons;
     stats->agreement_splits = agree_splits;
     stats->mixed_cubes = n_mixed;
-    if (o.precision_mode == GS_PREC_MIXED) {
+    if (fp32) {
         // FP64 where a surface point's position (first-order bound 8e-6 A)
-        // or a face or fold decision could depend on the FP32 error; every
-        // corner of a cube with neighbours of another size
+        // or a face or fold decision could depend on the FP32 error (the
+        // constrained values carry their sources' interpolated bounds; a mark
+        // on one passes to its sources, then the values are set again)
         GS_CHECK(cudaMemsetAsync(mark, 0, sizeof(int64_t) * (size_t)(nv + 1), st));
         TriCtx X;
         memset(&X, 0, sizeof(X));
         X.cubes = cubes; X.cvid = cvid; X.phi = phi; X.ncubes = nc; X.c = P.c;
         for (int a3 = 0; a3 < 3; a3++) X.origin[a3] = P.origin[a3];
         X.min_edge = P.min_edge; X.max_depth = P.max_depth;
-        X.mixed = n_mixed > 0 ? mixed : nullptr;
         rc = gs_tri_marks(X, err, 8e-6, mark, d_cnt + 21, st);
+        if (!rc && constrain) rc = gs_cons_mark_up(K, max_depth, mark, st);
         if (!rc && constrain) rc = gs_cons_unmark(K, mark, st);
         int64_t n2 = 0;
         if (!rc) rc = gs_field_recompute(P, vkeys, nv, mark, phi, err, &n2, st);
         nre += n2;
+        if (!rc && constrain)
+            rc = gs_cons_apply(K, hc, vkeys, max_depth, P.c, phi, err, nullptr, nullptr, nullptr, d_cnt + 27, st);
         stats->recheck_vertices = nre;
     }
+    nr_field.end();
     if (rc) return rc;
     int tf1 = T.mark();
 
@@ -744,7 +818,10 @@ static int mesh_impl(const double *atoms, const double *radii, int64_t n, double
     M.cubes = cubes;
     M.nc = nc;
     MixInfo mx{n_mixed > 0 ? mixed : nullptr, hc, hv, vslot};
-    rc = surface_from_values(P, cubes, nc, cvid, phi, B, d_status, d_cnt + 10, M, stats, T, &mx);
+    {
+        NvtxRange nr("gs: triangulate, weld");
+        rc = surface_from_values(P, cubes, nc, cvid, phi, B, d_status, d_cnt + 10, M, stats, T, &mx);
+    }
     if (rc) return rc;
     int tw1 = T.mark();
     if (bw) {
@@ -779,14 +856,14 @@ static int mesh_impl(const double *atoms, const double *radii, int64_t n, double
         if (!rc && bw->g_radii) rc = put_out(bw->g_radii, g + 3 * n, sizeof(double) * (size_t)n, st);
         if (!rc && bw->g_D) rc = put_out(bw->g_D, g + 4 * n, sizeof(double), st);
         if (rc) return rc;
-        GS_CHECK(cudaStreamSynchronize(st));
+        GS_CHECK(gs_sync(st));
     }
     if (out) {
         rc = into ? finish_into(M, into, st) : finish_output(M, o, out, st);
         if (rc) return rc;
     }
     int tend = T.mark();
-    GS_CHECK(cudaStreamSynchronize(st));
+    GS_CHECK(gs_sync(st));
     unsigned long long h[32];
     GS_CHECK(cudaMemcpy(h, d_cnt, sizeof(h), cudaMemcpyDeviceToHost));
     stats->recheck_bounds = (int64_t)h[15];
@@ -821,6 +898,23 @@ static int mesh_impl(const double *atoms, const double *radii, int64_t n, double
     stats->ms_total = T.ms(tstart, tend);
     stats->n_kernel_launches = gs_launch_count() - launches0;
     return GS_OK;
+}
+
+// mesh_impl, tried once more with level chunks of 2^18 octets (1/8 of the
+// memory per chunk) when the level loop ran out of device memory or of an
+// internal table
+static int mesh_with_retry(const double *atoms, const double *radii, int64_t n, double D, double c, double precision,
+                           int max_depth, const gs_options &o, gs_mesh *out, cudaStream_t st,
+                           const BackReq *bw = nullptr, gs_mesh_buffers *into = nullptr)
+{
+    bool retry = false;
+    int rc = mesh_impl(atoms, radii, n, D, c, precision, max_depth, o, out, st, bw, into, (int64_t)1 << 21, &retry);
+    if (rc && retry) {
+        cudaGetLastError();
+        rc = mesh_impl(atoms, radii, n, D, c, precision, max_depth, o, out, st, bw, into, (int64_t)1 << 18);
+        if (!rc && o.stats) o.stats->retries = 1;
+    }
+    return rc;
 }
 
 static int check_mesh_args(const double *atoms, const double *radii, int64_t n_atoms, double D, double c,
@@ -867,8 +961,8 @@ extern "C" int mesh_gaussian_surface(const double *atoms, const double *radii, i
         GS_CHECK(cudaStreamCreateWithFlags(&st, cudaStreamNonBlocking));
         own = true;
     }
-    rc = mesh_impl(atoms, radii, n_atoms, D, c, precision, max_depth, o, out, st);
-    cudaError_t e = cudaStreamSynchronize(st);
+    rc = mesh_with_retry(atoms, radii, n_atoms, D, c, precision, max_depth, o, out, st);
+    cudaError_t e = gs_sync(st);
     if (own) cudaStreamDestroy(st);
     if (!rc && e != cudaSuccess) rc = gs_fail_cuda(e, "stream", __FILE__, __LINE__);
     if (rc) mesh_free(out);
@@ -898,8 +992,8 @@ extern "C" int mesh_gaussian_surface_into(const double *atoms, const double *rad
     }
     gs_mesh unused;
     memset(&unused, 0, sizeof(unused));
-    rc = mesh_impl(atoms, radii, n_atoms, D, c, precision, max_depth, o, &unused, st, nullptr, out);
-    cudaError_t e = cudaStreamSynchronize(st);
+    rc = mesh_with_retry(atoms, radii, n_atoms, D, c, precision, max_depth, o, &unused, st, nullptr, out);
+    cudaError_t e = gs_sync(st);
     if (own) cudaStreamDestroy(st);
     if (!rc && e != cudaSuccess) rc = gs_fail_cuda(e, "stream", __FILE__, __LINE__);
     return rc;
@@ -950,7 +1044,7 @@ extern "C" int mesh_gaussian_surface_batch(const double *atoms, const double *ra
             o.cuda_stream = st;
             o.stats = stats ? &stats[m] : nullptr;
             int r = mesh_impl(atoms + 3 * o0, radii + o0, n, D[m], c, precision, max_depth, o, &out[m], st);
-            cudaError_t e = cudaStreamSynchronize(st);
+            cudaError_t e = gs_sync(st);
             if (!r && e != cudaSuccess) r = gs_fail_cuda(e, "stream", __FILE__, __LINE__);
             if (r) {
                 std::lock_guard<std::mutex> lk(mu);
@@ -995,8 +1089,8 @@ extern "C" int gs_mesh_backward(const double *atoms, const double *radii, int64_
     bw.g_atoms = grad_atoms;
     bw.g_radii = grad_radii;
     bw.g_D = grad_D;
-    rc = mesh_impl(atoms, radii, n_atoms, D, c, precision, max_depth, o, nullptr, st, &bw);
-    cudaError_t e = cudaStreamSynchronize(st);
+    rc = mesh_with_retry(atoms, radii, n_atoms, D, c, precision, max_depth, o, nullptr, st, &bw);
+    cudaError_t e = gs_sync(st);
     if (own) cudaStreamDestroy(st);
     if (!rc && e != cudaSuccess) rc = gs_fail_cuda(e, "stream", __FILE__, __LINE__);
     return rc;
@@ -1021,7 +1115,7 @@ static int check_tri_ids(const int32_t *d_t, int64_t nt, int64_t nv, unsigned *d
     GS_LAUNCH(k_check_tri, (unsigned)((3 * nt + 255) / 256), 256, 0, st)(d_t, 3 * nt, nv, d_status);
     unsigned h = 0;
     GS_CHECK(cudaMemcpyAsync(&h, d_status, sizeof(h), cudaMemcpyDeviceToHost, st));
-    GS_CHECK(cudaStreamSynchronize(st));
+    GS_CHECK(gs_sync(st));
     return h ? gs_fail(GS_ERR_ARG, "a triangle index is outside [0, n_vertices)") : GS_OK;
 }
 
@@ -1061,7 +1155,7 @@ extern "C" int gs_mesh_intersections(const double *vertices, int64_t n_vertices,
         }
         if (!rc && n_triangles) rc = check_tri_ids(t, n_triangles, n_vertices, d_status, st);
         if (!rc) rc = gs_count_intersections(v, n_vertices, t, n_triangles, tol, n_pairs, st);
-        cudaError_t e = cudaStreamSynchronize(st);
+        cudaError_t e = gs_sync(st);
         if (!rc && e != cudaSuccess) rc = gs_fail_cuda(e, "stream", __FILE__, __LINE__);
     }
     if (own) cudaStreamDestroy(st);
@@ -1113,7 +1207,7 @@ extern "C" int gs_volume_area(const double *vertices, int64_t n_vertices, const 
         if (!rc) rc = put_out(volume_area, acc, 2 * sizeof(double), st);
         if (!rc && gV) rc = put_out(grad_volume, gV, sizeof(double) * 3 * (size_t)n_vertices, st);
         if (!rc && gA) rc = put_out(grad_area, gA, sizeof(double) * 3 * (size_t)n_vertices, st);
-        cudaError_t e = cudaStreamSynchronize(st);
+        cudaError_t e = gs_sync(st);
         if (!rc && e != cudaSuccess) rc = gs_fail_cuda(e, "stream", __FILE__, __LINE__);
     }
     if (own) cudaStreamDestroy(st);
@@ -1178,7 +1272,7 @@ extern "C" int gs_triangulate_grid(int64_t nx, int64_t ny, int64_t nz, const dou
         if (!rc) rc = finish_output(M, o, out, st);
         if (!rc) { stats->n_vertices = M.nv; stats->n_triangles = M.nt; stats->n_cubes_final = nc; }
     }
-    cudaError_t e = cudaStreamSynchronize(st);
+    cudaError_t e = gs_sync(st);
     if (own) cudaStreamDestroy(st);
     if (!rc && e != cudaSuccess) rc = gs_fail_cuda(e, "stream", __FILE__, __LINE__);
     if (rc) mesh_free(out);
@@ -1239,7 +1333,7 @@ extern "C" int gs_eval_field(const double *atoms, const double *radii, int64_t n
         }
         if (!rc) rc = check_status(d_status, st, "field");
     }
-    cudaError_t e = cudaStreamSynchronize(st);
+    cudaError_t e = gs_sync(st);
     if (own) cudaStreamDestroy(st);
     if (!rc && e != cudaSuccess) rc = gs_fail_cuda(e, "stream", __FILE__, __LINE__);
     return rc;
@@ -1274,7 +1368,7 @@ extern "C" int gs_cube_decisions(const double *atoms, const double *radii, int64
         if (!rc && n_cubes) {
             cudaError_t e = cudaMemcpyAsync(hk.data(), cube_keys, sizeof(uint64_t) * (size_t)n_cubes,
                                             on_device(cube_keys) ? cudaMemcpyDeviceToHost : cudaMemcpyHostToHost, st);
-            if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+            if (e == cudaSuccess) e = gs_sync(st);
             if (e != cudaSuccess) rc = gs_fail_cuda(e, "keys", __FILE__, __LINE__);
         }
         std::vector<double> hA, hB;
@@ -1311,7 +1405,7 @@ extern "C" int gs_cube_decisions(const double *atoms, const double *radii, int64
                 cudaMemcpyAsync(tA.data(), dA, sizeof(double) * tA.size(), cudaMemcpyDeviceToHost, st);
                 cudaMemcpyAsync(tB.data(), dB, sizeof(double) * tB.size(), cudaMemcpyDeviceToHost, st);
                 cudaMemcpyAsync(tD.data(), dd, tD.size(), cudaMemcpyDeviceToHost, st);
-                cudaError_t e = cudaStreamSynchronize(st);
+                cudaError_t e = gs_sync(st);
                 if (e != cudaSuccess) rc = gs_fail_cuda(e, "decisions", __FILE__, __LINE__);
             }
             for (int64_t t = 0; t < m && !rc; t++) {
@@ -1331,7 +1425,7 @@ extern "C" int gs_cube_decisions(const double *atoms, const double *radii, int64
             if (bounds) cudaMemcpy(bounds, hB.data(), sizeof(double) * hB.size(), on_device(bounds) ? cudaMemcpyHostToDevice : cudaMemcpyHostToHost);
         }
     }
-    cudaError_t e = cudaStreamSynchronize(st);
+    cudaError_t e = gs_sync(st);
     if (own) cudaStreamDestroy(st);
     if (!rc && e != cudaSuccess) rc = gs_fail_cuda(e, "stream", __FILE__, __LINE__);
     return rc;
@@ -1372,7 +1466,7 @@ extern "C" int gs_bin_atoms(const double *atoms, int64_t n_atoms, double cell_si
         if (!rc) rc = put_out(cell_start, cs, sizeof(int32_t) * (size_t)(ncell + 1), st);
         if (!rc) rc = put_out(atom_perm, pm, sizeof(int32_t) * (size_t)n_atoms, st);
     }
-    cudaError_t e = cudaStreamSynchronize(st);
+    cudaError_t e = gs_sync(st);
     if (own) cudaStreamDestroy(st);
     if (!rc && e != cudaSuccess) rc = gs_fail_cuda(e, "stream", __FILE__, __LINE__);
     return rc;

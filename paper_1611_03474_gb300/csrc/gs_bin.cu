@@ -136,7 +136,7 @@ int gs_prep_atoms(const double *d_xyz, const double *d_r, int64_t n, double D, d
     GS_LAUNCH(k_prep, blocks, 256, 0, st)(d_xyz, d_r, n, D, KD, d_R2, d_w, red, d_status);
     unsigned long long h[7];
     cudaError_t e = cudaMemcpyAsync(h, red, sizeof(h), cudaMemcpyDeviceToHost, st);
-    if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+    if (e == cudaSuccess) e = gs_sync(st);
     gs_free(red, st);
     if (e != cudaSuccess) return gs_fail_cuda(e, "prep readback", __FILE__, __LINE__);
     for (int a = 0; a < 6; a++) bbox[a] = ord_dbl(h[a]);

@@ -107,12 +107,18 @@ __global__ void __launch_bounds__(256) k_cons_find(GsHash hc, GsHash hv, const u
 }
 
 // values of the vertices constrained at level l from their sources (final
-// already); with split, count a sign disagreement with the field value and
-// mark the level-l cubes holding the vertex (cnt = 8)
+// already).  err (nullable): FP32 bounds, the interpolant's bound is the same
+// interpolant of its sources' bounds (a convex combination; the FP64
+// rounding of the interpolation is far below them), exact sources give 0.
+// mark (nullable): where |value - c| is within 4 bounds, the sources are
+// marked for FP64.  split (nullable): count a sign disagreement with the
+// vertex's own field value and mark the level-l cubes holding the vertex
+// (cnt = 8).
 __global__ void __launch_bounds__(256) k_cons_apply(int l, int md, double c, GsHash hc,
                                                     const uint64_t *__restrict__ vkeys, int64_t nv,
                                                     const int8_t *__restrict__ lev, const int32_t *__restrict__ src,
                                                     const double *__restrict__ tt, double *__restrict__ phi,
+                                                    float *__restrict__ err, int64_t *__restrict__ mark,
                                                     int64_t *__restrict__ split, unsigned long long *nflip)
 {
     const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
@@ -120,15 +126,24 @@ __global__ void __launch_bounds__(256) k_cons_apply(int l, int md, double c, GsH
     const int32_t *S = src + 4 * i;
     const double t0 = tt[2 * i], t1 = tt[2 * i + 1];
     double psi;
+    float e = 0.f;
     if (S[2] < 0) {
         const double a = phi[S[0]], b = phi[S[1]];
         psi = __dadd_rn(a, __dmul_rn(t0, __dsub_rn(b, a)));
+        if (err) e = (float)((1.0 - t0) * err[S[0]] + t0 * err[S[1]]);
     } else {
         const double q00 = phi[S[0]], q10 = phi[S[1]], q01 = phi[S[2]], q11 = phi[S[3]];
         const double e0 = __dadd_rn(q00, __dmul_rn(t0, __dsub_rn(q10, q00)));
         const double e1 = __dadd_rn(q01, __dmul_rn(t0, __dsub_rn(q11, q01)));
         psi = __dadd_rn(e0, __dmul_rn(t1, __dsub_rn(e1, e0)));
+        if (err)
+            e = (float)((1.0 - t0) * (1.0 - t1) * err[S[0]] + t0 * (1.0 - t1) * err[S[1]] +
+                        (1.0 - t0) * t1 * err[S[2]] + t0 * t1 * err[S[3]]);
     }
+    if (err && e > 0.f) e = e * 1.0001f + 1e-12f;  // the bound's own rounding
+    if (mark && fabs(psi - c) <= 4.0 * (double)e)
+        for (int q = 0; q < 4; q++)
+            if (S[q] >= 0) mark[S[q]] = 1;
     if (split && ((psi >= c) != (phi[i] >= c))) {
         atomicAdd(nflip, 1ull);
         const uint64_t k = vkeys[i];
@@ -140,6 +155,36 @@ __global__ void __launch_bounds__(256) k_cons_apply(int l, int md, double c, GsH
         cubes_holding(hc, X, md, l, al, [&](int64_t ci) { split[ci] = 8; return true; });
     }
     phi[i] = psi;
+    if (err) err[i] = e;
+}
+
+// marks on vertices constrained at level l pass to their sources (run from
+// the finest constraint level to the coarsest)
+__global__ void __launch_bounds__(256) k_cons_mark_up(int l, int64_t nv, const int8_t *__restrict__ lev,
+                                                      const int32_t *__restrict__ src, int64_t *__restrict__ mark)
+{
+    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= nv || lev[i] != l || !mark[i]) return;
+    for (int q = 0; q < 4; q++)
+        if (src[4 * i + q] >= 0) mark[src[4 * i + q]] = 1;
+}
+
+// a vertex of the new lattice that the previous one had keeps its field
+// value and bound; need[i] = 1 for the others
+__global__ void __launch_bounds__(256) k_field_reuse(const uint64_t *__restrict__ vkeys, int64_t n, GsHash hold,
+                                                     const uint64_t *__restrict__ slot_old,
+                                                     const double *__restrict__ phi_old,
+                                                     const float *__restrict__ err_old, double *__restrict__ phi,
+                                                     float *__restrict__ err, int64_t *__restrict__ need)
+{
+    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    const int64_t s = gs_hash_find(hold, vkeys[i]);
+    if (s < 0) { need[i] = 1; return; }
+    const int64_t j = (int64_t)slot_old[s];
+    phi[i] = phi_old[j];
+    if (err) err[i] = err_old[j];
+    need[i] = 0;
 }
 
 // a cube with a mixed-size contact: a constrained corner (a coarser cube
@@ -246,25 +291,26 @@ int gs_cons_find(GsCons *K, const GsHash &hc, const GsHash &hv, const uint64_t *
                                                                         K->src, K->t, d_mark, d_scratch, d_status);
     unsigned long long h = 0;
     GS_CHECK(cudaMemcpyAsync(&h, d_scratch, sizeof(h), cudaMemcpyDeviceToHost, st));
-    GS_CHECK(cudaStreamSynchronize(st));
+    GS_CHECK(gs_sync(st));
     K->ncons = (int64_t)h;
     return GS_OK;
 }
 
 int gs_cons_apply(const GsCons &K, const GsHash &hc, const uint64_t *d_vkeys, int md, double c, double *d_phi,
-                  int64_t *d_split, int64_t *n_flip, unsigned long long *d_scratch, cudaStream_t st)
+                  float *d_err, int64_t *d_mark, int64_t *d_split, int64_t *n_flip, unsigned long long *d_scratch,
+                  cudaStream_t st)
 {
     if (n_flip) *n_flip = 0;
     if (K.nv <= 0 || K.ncons == 0) return GS_OK;
     if (d_split) GS_CHECK(cudaMemsetAsync(d_scratch, 0, sizeof(unsigned long long), st));
     const unsigned nb = (unsigned)((K.nv + 255) / 256);
     for (int l = 0; l < md; l++)
-        GS_LAUNCH(k_cons_apply, nb, 256, 0, st)(l, md, c, hc, d_vkeys, K.nv, K.lev, K.src, K.t, d_phi, d_split,
-                                                d_scratch);
+        GS_LAUNCH(k_cons_apply, nb, 256, 0, st)(l, md, c, hc, d_vkeys, K.nv, K.lev, K.src, K.t, d_phi, d_err, d_mark,
+                                                d_split, d_scratch);
     if (d_split && n_flip) {
         unsigned long long h = 0;
         GS_CHECK(cudaMemcpyAsync(&h, d_scratch, sizeof(h), cudaMemcpyDeviceToHost, st));
-        GS_CHECK(cudaStreamSynchronize(st));
+        GS_CHECK(gs_sync(st));
         *n_flip = (int64_t)h;
     }
     GS_CHECK(cudaGetLastError());
@@ -282,8 +328,30 @@ int gs_mixed_flags(const GsCons &K, const uint64_t *d_cubes, int64_t n, const in
                                                                        d_mixed, d_scratch);
     unsigned long long h = 0;
     GS_CHECK(cudaMemcpyAsync(&h, d_scratch, sizeof(h), cudaMemcpyDeviceToHost, st));
-    GS_CHECK(cudaStreamSynchronize(st));
+    GS_CHECK(gs_sync(st));
     *n_mixed = (int64_t)h;
+    return GS_OK;
+}
+
+int gs_cons_mark_up(const GsCons &K, int md, int64_t *d_mark, cudaStream_t st)
+{
+    if (K.nv <= 0 || K.ncons == 0) return GS_OK;
+    const unsigned nb = (unsigned)((K.nv + 255) / 256);
+    for (int l = md - 1; l >= 0; l--) GS_LAUNCH(k_cons_mark_up, nb, 256, 0, st)(l, K.nv, K.lev, K.src, d_mark);
+    GS_CHECK(cudaGetLastError());
+    return GS_OK;
+}
+
+int gs_field_reuse(const uint64_t *d_vkeys, int64_t n, const GsHash &hold, const uint64_t *d_slot_old,
+                   const double *d_phi_old, const float *d_err_old, double *d_phi, float *d_err, int64_t *d_need,
+                   cudaStream_t st)
+{
+    if (n <= 0) return GS_OK;
+    // d_need is scanned over n + 1 entries: the last one must be 0
+    GS_CHECK(cudaMemsetAsync(d_need + n, 0, sizeof(int64_t), st));
+    GS_LAUNCH(k_field_reuse, (unsigned)((n + 255) / 256), 256, 0, st)(d_vkeys, n, hold, d_slot_old, d_phi_old, d_err_old,
+                                                                       d_phi, d_err, d_need);
+    GS_CHECK(cudaGetLastError());
     return GS_OK;
 }
 

@@ -2,6 +2,14 @@
 #pragma once
 #include "gs_internal.cuh"
 
+// gs_guard.cu: host waits with a deadline (cudaErrorTimeout after it) and
+// host-side fault injection (environment GS_FAULT); gs_guard_begin at each
+// API call
+cudaError_t gs_sync(cudaStream_t st);
+void gs_guard_begin(void);
+bool gs_fault_alloc(void);
+bool gs_fault_capacity(int level);
+
 struct GsAtomsSoA {
     double *x, *y, *z, *r, *R2, *w;
     float *fx, *fy, *fz;
@@ -43,6 +51,13 @@ int gs_field_f32_marked(const GsProblem &P, const uint64_t *d_vkeys, int64_t n, 
 // re-evaluate in FP64 the vertices with mark[v] = 1 (mark: n + 1 entries, scanned in place)
 int gs_field_recompute(const GsProblem &P, const uint64_t *d_vkeys, int64_t n, int64_t *d_mark, double *d_phi,
                        float *d_err, int64_t *n_recomputed, cudaStream_t st);
+// the field at the vertices with need[v] = 1 only (need: n + 1 entries,
+// scanned in place); fp32: FP32 values and bounds (d_err), else FP64
+int gs_field_partial(const GsProblem &P, int fp32, const uint64_t *d_vkeys, int64_t n, int64_t *d_need, double *d_phi,
+                     float *d_err, unsigned long long *d_terms, int64_t *n_done, cudaStream_t st);
+// mark[v] = 1 where |phi - c| is within 4 bounds
+int gs_field_flag_near(const GsProblem &P, const double *d_phi, const float *d_err, int64_t n, int64_t *d_mark,
+                       cudaStream_t st);
 int gs_field_mixed(const GsProblem &P, const uint64_t *d_vkeys, int64_t n, double *d_phi, unsigned long long *d_terms,
                    int64_t *n_rechecked, cudaStream_t st);
 int gs_field_f32(const GsProblem &P, const uint64_t *d_vkeys, const double *d_points, int64_t n, double *d_phi,
@@ -94,11 +109,21 @@ void gs_cons_free(GsCons *K, cudaStream_t st);
 // d_scratch: one device counter
 int gs_cons_find(GsCons *K, const GsHash &hc, const GsHash &hv, const uint64_t *d_slot_id, const uint64_t *d_vkeys,
                  int md, int64_t *d_mark, unsigned long long *d_scratch, unsigned *d_status, cudaStream_t st);
-// replaces the constrained values in d_phi (coarse to fine); with d_split
-// (n + 1 entries per cube, preset to 1) counts the sign disagreements and sets
-// 8 for the cubes to split
+// replaces the constrained values in d_phi (coarse to fine); d_err
+// (nullable) carries the FP32 bounds through the interpolants; d_mark
+// (nullable) marks the sources of values within 4 bounds of c; with d_split
+// (n + 1 entries per cube, preset to 1) counts the sign disagreements with
+// the vertices' own field values and sets 8 for the cubes to split
 int gs_cons_apply(const GsCons &K, const GsHash &hc, const uint64_t *d_vkeys, int md, double c, double *d_phi,
-                  int64_t *d_split, int64_t *n_flip, unsigned long long *d_scratch, cudaStream_t st);
+                  float *d_err, int64_t *d_mark, int64_t *d_split, int64_t *n_flip, unsigned long long *d_scratch,
+                  cudaStream_t st);
+// marks on constrained vertices pass to their sources, fine to coarse
+int gs_cons_mark_up(const GsCons &K, int md, int64_t *d_mark, cudaStream_t st);
+// the vertices of a previous lattice (hash hold, slot -> id d_slot_old) keep
+// their values and bounds; d_need[i] = 1 for the others (n + 1 entries)
+int gs_field_reuse(const uint64_t *d_vkeys, int64_t n, const GsHash &hold, const uint64_t *d_slot_old,
+                   const double *d_phi_old, const float *d_err_old, double *d_phi, float *d_err, int64_t *d_need,
+                   cudaStream_t st);
 int gs_mixed_flags(const GsCons &K, const uint64_t *d_cubes, int64_t n, const int32_t *d_cvid, const GsHash &hv,
                    const uint64_t *d_slot_id, int md, uint8_t *d_mixed, int64_t *n_mixed,
                    unsigned long long *d_scratch, cudaStream_t st);

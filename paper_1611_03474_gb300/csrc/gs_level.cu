@@ -1088,7 +1088,7 @@ int gs_level_compact(const GsProblem &P, int level, const uint64_t *d_parents, c
     int64_t h = 0;
     if (!rc) {
         cudaError_t e = cudaMemcpyAsync(&h, tot, sizeof(int64_t), cudaMemcpyDeviceToHost, st);
-        if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+        if (e == cudaSuccess) e = gs_sync(st);
         if (e != cudaSuccess) rc = gs_fail_cuda(e, "level counts", __FILE__, __LINE__);
     }
     int64_t ns = h & 0xffffffffll, na = h >> 32;
@@ -1825,7 +1825,7 @@ int gs_level_mixed(const GsProblem &P, int level, const uint64_t *d_parents, int
     int64_t nsub = 0;
     if (!rc) {
         cudaError_t e = cudaMemcpyAsync(&nsub, tot, sizeof(int64_t), cudaMemcpyDeviceToHost, st);
-        if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+        if (e == cudaSuccess) e = gs_sync(st);
         if (e != cudaSuccess) rc = gs_fail_cuda(e, "recheck count", __FILE__, __LINE__);
     }
     if (!rc && nsub > 0) {

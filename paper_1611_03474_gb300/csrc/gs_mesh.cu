@@ -117,7 +117,7 @@ int gs_split_counted(uint64_t **d_cubes, int64_t *n, int64_t *cnt, int64_t *spli
     int64_t total = 0;
     if (!rc) {
         cudaError_t e = cudaMemcpyAsync(&total, tot, sizeof(int64_t), cudaMemcpyDeviceToHost, st);
-        if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+        if (e == cudaSuccess) e = gs_sync(st);
         if (e != cudaSuccess) rc = gs_fail_cuda(e, "split count", __FILE__, __LINE__);
     }
     gs_free(tot, st);
@@ -253,7 +253,7 @@ int gs_lattice_vertices(const uint64_t *d_cubes, int64_t n, int max_depth, uint6
     int64_t total = 0;
     if (!rc) {
         cudaError_t e = cudaMemcpyAsync(&total, tot, sizeof(int64_t), cudaMemcpyDeviceToHost, st);
-        if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+        if (e == cudaSuccess) e = gs_sync(st);
         if (e != cudaSuccess) rc = gs_fail_cuda(e, "vertex count", __FILE__, __LINE__);
     }
     if (!rc) rc = gs_alloc((void **)d_vkeys, sizeof(uint64_t) * (size_t)(total + 1), st);
@@ -379,7 +379,7 @@ int gs_weld(const uint64_t *d_pk, const double *d_pxyz, int64_t npt, const uint6
     int64_t total = 0;
     if (!rc) {
         cudaError_t e = cudaMemcpyAsync(&total, tot, sizeof(int64_t), cudaMemcpyDeviceToHost, st);
-        if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+        if (e == cudaSuccess) e = gs_sync(st);
         if (e != cudaSuccess) rc = gs_fail_cuda(e, "weld count", __FILE__, __LINE__);
     }
     if (!rc) rc = gs_alloc((void **)d_vkeys, sizeof(uint64_t) * (size_t)(total + 1), st);
@@ -536,7 +536,7 @@ int gs_count_intersections(const double *d_v, int64_t nv, const int32_t *d_t, in
     std::vector<int32_t> ht((size_t)nt * 3);
     GS_CHECK(cudaMemcpyAsync(hv.data(), d_v, sizeof(double) * hv.size(), cudaMemcpyDeviceToHost, st));
     GS_CHECK(cudaMemcpyAsync(ht.data(), d_t, sizeof(int32_t) * ht.size(), cudaMemcpyDeviceToHost, st));
-    GS_CHECK(cudaStreamSynchronize(st));
+    GS_CHECK(gs_sync(st));
     double lo[3] = {1e300, 1e300, 1e300}, hi[3] = {-1e300, -1e300, -1e300}, ext = 0.0;
     for (int64_t i = 0; i < nv; i++)
         for (int a = 0; a < 3; a++) { lo[a] = fmin(lo[a], hv[3 * i + a]); hi[a] = fmax(hi[a], hv[3 * i + a]); }
@@ -571,7 +571,7 @@ int gs_count_intersections(const double *d_v, int64_t nv, const int32_t *d_t, in
     // counting sort of the triangles by cell on the host (cell array read back)
     std::vector<int32_t> hc((size_t)nt), hs((size_t)ncell + 1, 0), ho((size_t)nt);
     GS_CHECK(cudaMemcpyAsync(hc.data(), cell, sizeof(int32_t) * (size_t)nt, cudaMemcpyDeviceToHost, st));
-    GS_CHECK(cudaStreamSynchronize(st));
+    GS_CHECK(gs_sync(st));
     for (int64_t i = 0; i < nt; i++) hs[(size_t)hc[i] + 1]++;
     for (int64_t k = 0; k < ncell; k++) hs[(size_t)k + 1] += hs[(size_t)k];
     {
@@ -588,7 +588,7 @@ int gs_count_intersections(const double *d_v, int64_t nv, const int32_t *d_t, in
                                                                          cnt);
         unsigned long long h = 0;
         GS_CHECK(cudaMemcpyAsync(&h, cnt, sizeof(h), cudaMemcpyDeviceToHost, st));
-        GS_CHECK(cudaStreamSynchronize(st));
+        GS_CHECK(gs_sync(st));
         *n_pairs = (int64_t)h;
     }
     gs_free(d_lo, st); gs_free(d_dims, st); gs_free(cell, st); gs_free(cnt, st); gs_free(order, st); gs_free(start, st);

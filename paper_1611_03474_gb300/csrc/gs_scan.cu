@@ -4,7 +4,7 @@
 #include <cstdio>
 #include <cstring>
 
-#include "gs_internal.cuh"
+#include "gs_host.cuh"
 
 static thread_local char g_last_error[512] = "";
 
@@ -20,6 +20,10 @@ int gs_fail(int code, const char *fmt, ...)
 int gs_fail_cuda(cudaError_t e, const char *what, const char *file, int line)
 {
     const char *f = strrchr(file, '/');
+    if (e == cudaErrorTimeout) {
+        gs_fail(GS_ERR_TIMEOUT, "%s: host wait passed its deadline (%s:%d)", what, f ? f + 1 : file, line);
+        return GS_ERR_TIMEOUT;
+    }
     gs_fail(e == cudaErrorMemoryAllocation ? GS_ERR_OOM : GS_ERR_CUDA, "%s failed: %s (%s:%d)", what,
             cudaGetErrorString(e), f ? f + 1 : file, line);
     return e == cudaErrorMemoryAllocation ? GS_ERR_OOM : GS_ERR_CUDA;
@@ -36,6 +40,7 @@ long long gs_launch_count(void) { return g_launches; }
 int gs_alloc(void **p, size_t bytes, cudaStream_t st)
 {
     *p = nullptr;
+    if (gs_fault_alloc()) return gs_fail(GS_ERR_OOM, "device allocation failed (injected by GS_FAULT)");
     if (bytes == 0) bytes = 16;
     cudaError_t e = cudaMallocAsync(p, bytes, st);
     if (e != cudaSuccess) {

@@ -1204,7 +1204,7 @@ int gs_triangulate(const TriCtx &X0, uint64_t **d_tri_keys, int64_t *ntri_total,
         GS_LAUNCH(k_tri_class, nb, 128, 0, st)(X, cls, hist);
         unsigned hh[TRI_CLASSES];
         cudaMemcpyAsync(hh, hist, sizeof(hh), cudaMemcpyDeviceToHost, st);
-        cudaStreamSynchronize(st);
+        gs_sync(st);
         unsigned acc = 0;
         for (int k = 0; k < TRI_CLASSES; k++) { unsigned c = hh[k]; hh[k] = acc; acc += c; }
         cudaMemcpyAsync(hist, hh, sizeof(hh), cudaMemcpyHostToDevice, st);
@@ -1234,7 +1234,7 @@ int gs_triangulate(const TriCtx &X0, uint64_t **d_tri_keys, int64_t *ntri_total,
     int64_t h[2] = {0, 0};
     if (!rc) {
         cudaError_t e = cudaMemcpyAsync(h, tot, sizeof(h), cudaMemcpyDeviceToHost, st);
-        if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+        if (e == cudaSuccess) e = gs_sync(st);
         if (e != cudaSuccess) rc = gs_fail_cuda(e, "triangle counts", __FILE__, __LINE__);
     }
     if (!rc) {
@@ -1286,11 +1286,6 @@ __global__ void __launch_bounds__(128) k_tri_marks(TriCtx X, const float *__rest
 {
     int64_t ci = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (ci >= X.ncubes) return;
-    if (X.mixed && X.mixed[ci]) {
-        // neighbours of another size: every corner in FP64
-        for (int v = 0; v < 8; v++) mark[X.cvid[ci * 8 + v]] = 1;
-        return;
-    }
     uint64_t ck = X.cubes[ci];
     int lvl = (int)gk_level(ck);
     const float h = (float)ldexp(X.min_edge, X.max_depth - lvl);
