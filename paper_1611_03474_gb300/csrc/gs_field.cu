@@ -133,6 +133,87 @@ __global__ void __launch_bounds__(128) k_field_f32(GsProblem P, const uint64_t *
     }
 }
 
+// FP32 field at lattice vertices, warp-cooperative: a warp takes 32
+// consecutive vertices (neighbours on the lattice: the vertex order follows
+// the cube order), walks the cell rows of their bounding box once, and
+// stages 32 candidate atoms at a time in shared memory (offsets from the
+// origin as hi + lo floats, cutoff^2, r^2); every lane then sums over the
+// staged atoms from broadcast reads.  Rows come in the order of the
+// per-vertex walk and each row's range covers the vertex's own, so each
+// vertex sums the same terms in the same order, with the same membership
+// test and error bound as k_field_f32.
+#define FW_WARPS 8
+__global__ void __launch_bounds__(32 * FW_WARPS) k_field_f32w(GsProblem P, const uint64_t *__restrict__ vkeys, int64_t n,
+                                                              double *__restrict__ phi, float *__restrict__ err,
+                                                              unsigned long long *terms)
+{
+    __shared__ float4 s_a[FW_WARPS][32];   // hx, hy, hz, fR2
+    __shared__ float4 s_b[FW_WARPS][32];   // lx, ly, lz, fr2
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    const bool valid = i < n;
+    float ph[3] = {0.f, 0.f, 0.f}, pl[3] = {0.f, 0.f, 0.f};
+    if (valid) {
+        double p[3];
+        point_of(P, vkeys, nullptr, i, p);
+        for (int a = 0; a < 3; a++) {
+            double rel = p[a] - P.origin[a];
+            ph[a] = (float)rel;
+            pl[a] = (float)(rel - (double)ph[a]);
+        }
+    }
+    // the warp's bounding box
+    float lo[3], hi[3];
+    for (int a = 0; a < 3; a++) {
+        lo[a] = valid ? ph[a] : INFINITY;
+        hi[a] = valid ? ph[a] : -INFINITY;
+        for (int o = 16; o > 0; o >>= 1) {
+            lo[a] = fminf(lo[a], __shfl_xor_sync(0xffffffffu, lo[a], o));
+            hi[a] = fmaxf(hi[a], __shfl_xor_sync(0xffffffffu, hi[a], o));
+        }
+    }
+    if (!(lo[0] <= hi[0])) return;   // no vertex in this warp (uniform)
+    const float nDl2e = (float)(-P.D * 1.4426950408889634);
+    const float Df = (float)P.D;
+    float s = 0.f, comp = 0.f, eacc = 0.f;
+    unsigned long long cnt = 0;
+    gs_warp_candidates(P, lo, hi, lane, [&](int k) {
+        const unsigned have = __ballot_sync(0xffffffffu, k >= 0);
+        if (k >= 0) {
+            s_a[w][lane] = make_float4(P.hx[k], P.hy[k], P.hz[k], P.fR2[k]);
+            s_b[w][lane] = make_float4(P.lx[k], P.ly[k], P.lz[k], P.fr2[k]);
+        }
+        __syncwarp();
+        const int m = __popc(have);
+        if (valid) {
+            for (int j = 0; j < m; j++) {
+                const float4 a = s_a[w][j], b = s_b[w][j];
+                const float dx = (ph[0] - a.x) + (pl[0] - b.x);
+                const float dy = (ph[1] - a.y) + (pl[1] - b.y);
+                const float dz = (ph[2] - a.z) + (pl[2] - b.z);
+                const float d2 = dx * dx + dy * dy + dz * dz;
+                if (d2 > a.w) continue;
+                const float t = gs_ex2(nDl2e * (d2 - b.w));
+                const float y = t - comp;
+                const float u = s + y;
+                comp = (u - s) - y;
+                s = u;
+                eacc = fmaf(t, 3e-7f + 2.5e-7f * Df * (d2 + b.w), eacc);
+                cnt++;
+            }
+        }
+        __syncwarp();
+    });
+    if (valid) {
+        phi[i] = (double)s - (double)comp;
+        if (err) err[i] = eacc + 2.4e-7f * s + 4e-8f * (float)P.c;
+    }
+    if (terms) {
+        for (int o = 16; o > 0; o >>= 1) cnt += __shfl_xor_sync(0xffffffffu, cnt, o);
+        if (lane == 0 && cnt) atomicAdd(terms, cnt);
+    }
+}
+
 int gs_field_f64(const GsProblem &P, const uint64_t *d_vkeys, const double *d_points, int64_t n, double *d_phi,
                  double *d_grad, unsigned long long *d_terms, cudaStream_t st)
 {
@@ -151,7 +232,12 @@ int gs_field_f32(const GsProblem &P, const uint64_t *d_vkeys, const double *d_po
                  double *d_grad, float *d_err, unsigned long long *d_terms, cudaStream_t st)
 {
     if (n <= 0) return GS_OK;
-    GS_LAUNCH(k_field_f32, (unsigned)((n + 127) / 128), 128, 0, st)(P, d_vkeys, d_points, n, d_phi, d_grad, d_err, d_terms);
+    if (d_vkeys && !d_grad)   // lattice vertices: the warp-cooperative form
+        GS_LAUNCH(k_field_f32w, (unsigned)((n + 32 * FW_WARPS - 1) / (32 * FW_WARPS)), 32 * FW_WARPS, 0, st)(
+            P, d_vkeys, n, d_phi, d_err, d_terms);
+    else
+        GS_LAUNCH(k_field_f32, (unsigned)((n + 127) / 128), 128, 0, st)(P, d_vkeys, d_points, n, d_phi, d_grad, d_err,
+                                                                       d_terms);
     GS_CHECK(cudaGetLastError());
     return GS_OK;
 }

@@ -30,14 +30,19 @@ int gs_quadrature_init(void);
 // accumulate A for the 8 children of each parent (level-1 coords in parents,
 // or the implicit root blocks when parents == NULL); vmask (nullable) selects
 // children; A_out [n_oct*8][64]
+// d_probs, d_mol (nullable, the batched form): octet o belongs to molecule
+// d_mol[o] whose problem is d_probs[d_mol[o]] (P then only supplies what the
+// molecules share: D, c, precision, the lattice spacing)
 int gs_accum_f64(const GsProblem &P, int level, const uint64_t *d_parents, const uint8_t *d_vmask, int64_t n_oct,
-                 double *d_A, unsigned long long *d_pairs, unsigned *d_status, cudaStream_t st, float *ms = nullptr);
+                 double *d_A, unsigned long long *d_pairs, unsigned *d_status, cudaStream_t st, float *ms = nullptr,
+                 const GsProblem *d_probs = nullptr, const int32_t *d_mol = nullptr);
 int gs_estimate_f64(const GsProblem &P, int level, const double *d_A, int64_t n_cubes, const uint64_t *d_parents,
                     const uint8_t *d_vmask, uint8_t *d_dec, double *d_bounds, cudaStream_t st);
 // mixed precision: FP32 accumulate (Kahan) + error bound, FP32 estimate with margins
 int gs_accum_f32(const GsProblem &P, int level, const uint64_t *d_parents, const uint8_t *d_vmask, int64_t n_oct,
                  float *d_A, float *d_err, unsigned long long *d_pairs, unsigned *d_status, cudaStream_t st,
-                 float *ms = nullptr, unsigned long long *d_atom_octets = nullptr);
+                 float *ms = nullptr, unsigned long long *d_atom_octets = nullptr, const GsProblem *d_probs = nullptr,
+                 const int32_t *d_mol = nullptr);
 int gs_estimate_f32(const GsProblem &P, int level, const float *d_A, const float *d_err, int64_t n_cubes,
                     const uint64_t *d_parents, const uint8_t *d_vmask, uint8_t *d_dec, uint8_t *d_flag,
                     cudaStream_t st, unsigned long long *d_why = nullptr, float *d_dbg = nullptr);
@@ -67,14 +72,16 @@ int gs_field_f32(const GsProblem &P, const uint64_t *d_vkeys, const double *d_po
 int gs_level_compact(const GsProblem &P, int level, const uint64_t *d_parents, const uint8_t *d_vmask, int64_t n_oct,
                      const uint8_t *d_dec, uint64_t **d_next, int64_t *n_next, uint64_t *d_acc_base,
                      int64_t acc_cap, int64_t *n_acc, unsigned long long *d_counters, cudaStream_t st,
-                     const double *d_A = nullptr, double **d_nextA = nullptr);
+                     const double *d_A = nullptr, double **d_nextA = nullptr, const int32_t *d_mol = nullptr,
+                     int32_t **d_next_mol = nullptr, int32_t *d_acc_mol = nullptr);
 // child tensors [n_oct][8][64] re-expanded from the parents' tensors [n_oct][64]
 int gs_reexpand(const double *d_Apar, int64_t n_oct, double *d_A, cudaStream_t st);
 
 int gs_level_mixed(const GsProblem &P, int level, const uint64_t *d_parents, int64_t n_oct, uint8_t *d_dec,
                    unsigned long long *d_pairs, unsigned long long *d_rechecked, unsigned long long *d_mism,
                    bool both, unsigned *d_status, cudaStream_t st, float *ms = nullptr,
-                   unsigned long long *d_why = nullptr);
+                   unsigned long long *d_why = nullptr, const GsProblem *d_probs = nullptr,
+                   const int32_t *d_mol = nullptr, const uint8_t *d_vmask = nullptr);
 int gs_root_blocks(const GsProblem &P, uint64_t **d_keys, int64_t *n, cudaStream_t st);
 
 // gs_mesh.cu

@@ -208,11 +208,15 @@ __device__ __forceinline__ void axis_coeffs_f64(double xi, double e0, double e1,
     }
 }
 
-template <int GV, int NQ>
-__global__ void __launch_bounds__(32 * ACC_WARPS) k_accum_f64(GsProblem P, int level, const uint64_t *parents,
+// BATCH: octet o belongs to molecule mol[o], whose problem is probs[mol[o]]
+// (the molecules of one launch share D, so one quadrature rule serves all)
+template <int GV, int NQ, bool BATCH>
+__global__ void __launch_bounds__(32 * ACC_WARPS) k_accum_f64(GsProblem P0, int level, const uint64_t *parents,
                                                                const uint8_t *vmask, int64_t n_oct,
                                                                double pad, double *__restrict__ A_out,
-                                                               unsigned long long *pairs, unsigned *status)
+                                                               unsigned long long *pairs, unsigned *status,
+                                                               const GsProblem *__restrict__ probs,
+                                                               const int32_t *__restrict__ mol)
 {
     __shared__ double s_cf[ACC_WARPS][32][25];   // per queued atom: 3 axes x 2 intervals x 4, then w
     __shared__ int s_qi[ACC_WARPS][ACC_Q];
@@ -223,6 +227,7 @@ __global__ void __launch_bounds__(32 * ACC_WARPS) k_accum_f64(GsProblem P, int l
     const int cx = c & 1, cy = (c >> 1) & 1, cz = c >> 2;
     unsigned long long my_pairs = 0;
     for (int64_t o = (int64_t)blockIdx.x * ACC_WARPS + wl; o < n_oct; o += (int64_t)gridDim.x * ACC_WARPS) {
+        const GsProblem &P = BATCH ? probs[mol[o]] : P0;
         Octet q = octet_of(P, level, parents, vmask, o);
         int64_t base[3] = {2 * q.I, 2 * q.J, 2 * q.K};
         double e[3][3];
@@ -355,7 +360,8 @@ static int grid_for(int64_t n_items, int per_block)
 }
 
 int gs_accum_f64(const GsProblem &P, int level, const uint64_t *d_parents, const uint8_t *d_vmask, int64_t n_oct,
-                 double *d_A, unsigned long long *d_pairs, unsigned *d_status, cudaStream_t st, float *ms)
+                 double *d_A, unsigned long long *d_pairs, unsigned *d_status, cudaStream_t st, float *ms,
+                 const GsProblem *d_probs, const int32_t *d_mol)
 {
     if (n_oct <= 0) return GS_OK;
     double h = gs_h(P, level);
@@ -364,8 +370,16 @@ int gs_accum_f64(const GsProblem &P, int level, const uint64_t *d_parents, const
     if (ms) { cudaEventCreate(&e0); cudaEventCreate(&e1); cudaEventRecord(e0, st); }
     const unsigned grid = grid_for(n_oct, ACC_WARPS);
 #define GS_ACC64(V, N)                                                                                              \
-    GS_LAUNCH((k_accum_f64<V, N>), grid, 32 * ACC_WARPS, 0, st)(P, level, d_parents, d_vmask, n_oct, P.pad, d_A,    \
-                                                               d_pairs, d_status)
+    do {                                                                                                            \
+        if (d_probs)                                                                                                \
+            GS_LAUNCH((k_accum_f64<V, N, true>), grid, 32 * ACC_WARPS, 0, st)(P, level, d_parents, d_vmask, n_oct,  \
+                                                                             P.pad, d_A, d_pairs, d_status,         \
+                                                                             d_probs, d_mol);                       \
+        else                                                                                                        \
+            GS_LAUNCH((k_accum_f64<V, N, false>), grid, 32 * ACC_WARPS, 0, st)(P, level, d_parents, d_vmask, n_oct, \
+                                                                              P.pad, d_A, d_pairs, d_status,        \
+                                                                              nullptr, nullptr);                    \
+    } while (0)
     switch (gv) {
     case 0: GS_ACC64(0, 8); break;
     case 1: GS_ACC64(1, 12); break;
@@ -1050,9 +1064,12 @@ __global__ void __launch_bounds__(256) k_level_count(const uint8_t *__restrict__
     if (threadIdx.x < 5 && sh[threadIdx.x]) atomicAdd(&counters[threadIdx.x], sh[threadIdx.x]);
 }
 
+// mol (nullable, the batched form): the octets' molecules, passed on to the
+// children (next_mol) and the accepted cubes (acc_mol)
 __global__ void k_level_emit(GsProblem P, int level, const uint64_t *parents, const uint8_t *vmask,
                              const uint8_t *__restrict__ dec, int64_t n, const int64_t *__restrict__ off,
-                             uint64_t *__restrict__ next, uint64_t *__restrict__ acc)
+                             uint64_t *__restrict__ next, uint64_t *__restrict__ acc, const int32_t *__restrict__ mol,
+                             int32_t *__restrict__ next_mol, int32_t *__restrict__ acc_mol)
 {
     int64_t q = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (q >= n) return;
@@ -1062,16 +1079,23 @@ __global__ void k_level_emit(GsProblem P, int level, const uint64_t *parents, co
     int c = (int)(q & 7);
     uint64_t key = gk_make(2 * oc.I + (c & 1), 2 * oc.J + ((c >> 1) & 1), 2 * oc.K + (c >> 2), GT_CUBE, (unsigned)level);
     int64_t o = off[q];
-    if (d == DEC_SPLIT) next[o & 0xffffffffll] = key;
-    else acc[o >> 32] = key;
+    if (d == DEC_SPLIT) {
+        next[o & 0xffffffffll] = key;
+        if (mol) next_mol[o & 0xffffffffll] = mol[q >> 3];
+    } else {
+        acc[o >> 32] = key;
+        if (mol) acc_mol[o >> 32] = mol[q >> 3];
+    }
 }
 
 int gs_level_compact(const GsProblem &P, int level, const uint64_t *d_parents, const uint8_t *d_vmask, int64_t n_oct,
                      const uint8_t *d_dec, uint64_t **d_next, int64_t *n_next, uint64_t *d_acc_base,
                      int64_t acc_cap, int64_t *n_acc, unsigned long long *d_counters, cudaStream_t st,
-                     const double *d_A, double **d_nextA)
+                     const double *d_A, double **d_nextA, const int32_t *d_mol, int32_t **d_next_mol,
+                     int32_t *d_acc_mol)
 {
     if (d_nextA) *d_nextA = nullptr;
+    if (d_next_mol) *d_next_mol = nullptr;
     int64_t n = n_oct * 8;
     *d_next = nullptr; *n_next = 0; *n_acc = 0;
     if (n <= 0) return GS_OK;
@@ -1094,8 +1118,10 @@ int gs_level_compact(const GsProblem &P, int level, const uint64_t *d_parents, c
     int64_t ns = h & 0xffffffffll, na = h >> 32;
     if (!rc && na > acc_cap) rc = gs_fail(GS_ERR_CAPACITY, "accepted-cube buffer too small");
     if (!rc && ns > 0) rc = gs_alloc((void **)d_next, sizeof(uint64_t) * (size_t)ns, st);
+    if (!rc && ns > 0 && d_mol) rc = gs_alloc((void **)d_next_mol, sizeof(int32_t) * (size_t)ns, st);
     if (!rc) GS_LAUNCH(k_level_emit, (unsigned)((n + 255) / 256), 256, 0, st)(P, level, d_parents, d_vmask, d_dec, n, packed,
-                                                                      *d_next, d_acc_base);
+                                                                      *d_next, d_acc_base, d_mol,
+                                                                      d_mol ? *d_next_mol : nullptr, d_acc_mol);
     if (!rc && d_A && d_nextA && ns > 0) {
         rc = gs_alloc((void **)d_nextA, sizeof(double) * 64 * (size_t)ns, st);
         if (!rc)
@@ -1151,13 +1177,15 @@ int gs_root_blocks(const GsProblem &P, uint64_t **d_keys, int64_t *n, cudaStream
 
 // GV: quadrature variant (a compile-time constant, so the node loop unrolls
 // and the nodes and weights are immediate constant-bank operands)
-template <int GV, int NQ>
-__global__ void __launch_bounds__(32 * ACC_WARPS, 4) k_accum_f32(GsProblem P, int level, const uint64_t *parents,
+template <int GV, int NQ, bool BATCH>
+__global__ void __launch_bounds__(32 * ACC_WARPS, 4) k_accum_f32(GsProblem P0, int level, const uint64_t *parents,
                                                                   const uint8_t *vmask, int64_t n_oct,
                                                                   float hf, int lat_exact, float *__restrict__ A_out,
                                                                   float *__restrict__ E_out,
                                                                   unsigned long long *pairs,
-                                                                  unsigned long long *atom_octets)
+                                                                  unsigned long long *atom_octets,
+                                                                  const GsProblem *__restrict__ probs,
+                                                                  const int32_t *__restrict__ mol)
 {
     unsigned long long my_pairs = 0, my_atoms = 0;
     __shared__ __align__(16) float s_cf[ACC_WARPS][32][ACF_STRIDE];
@@ -1168,9 +1196,10 @@ __global__ void __launch_bounds__(32 * ACC_WARPS, 4) k_accum_f32(GsProblem P, in
     const int c = lane >> 2, j = lane & 3;
     const int cx = c & 1, cy = (c >> 1) & 1, cz = c >> 2;
     const int oWXY = ACF_WXY + ((cy * 2 + cx) * 4 + j) * 4, oZ = ACF_Z + 8 * cz, oEB = ACF_EB + c;
-    const float nDl2e = (float)(-P.D * 1.4426950408889634);
+    const float nDl2e = (float)(-P0.D * 1.4426950408889634);
     const float hh = 0.5f * hf;
     for (int64_t o = (int64_t)blockIdx.x * ACC_WARPS + wl; o < n_oct; o += (int64_t)gridDim.x * ACC_WARPS) {
+        const GsProblem &P = BATCH ? probs[mol[o]] : P0;
         Octet q = octet_of(P, level, parents, vmask, o);
         int64_t base[3] = {2 * q.I, 2 * q.J, 2 * q.K};
         // interval ends relative to the origin as hi + lo floats; when the
@@ -1408,7 +1437,7 @@ __global__ void __launch_bounds__(32 * ACC_WARPS, 4) k_accum_f32(GsProblem P, in
 
 int gs_accum_f32(const GsProblem &P, int level, const uint64_t *d_parents, const uint8_t *d_vmask, int64_t n_oct,
                  float *d_A, float *d_err, unsigned long long *d_pairs, unsigned *d_status, cudaStream_t st, float *ms,
-                 unsigned long long *d_atom_octets)
+                 unsigned long long *d_atom_octets, const GsProblem *d_probs, const int32_t *d_mol)
 {
     if (n_oct <= 0) return GS_OK;
     double h = gs_h(P, level);
@@ -1417,8 +1446,18 @@ int gs_accum_f32(const GsProblem &P, int level, const uint64_t *d_parents, const
     if (ms) { cudaEventCreate(&e0); cudaEventCreate(&e1); cudaEventRecord(e0, st); }
     const unsigned grid = grid_for(n_oct, ACC_WARPS);
 #define GS_ACC32(V, N)                                                                                              \
-    GS_LAUNCH((k_accum_f32<V, N>), grid, 32 * ACC_WARPS, 0, st)(P, level, d_parents, d_vmask, n_oct, (float)h,      \
-                                                               P.lat_exact_f32, d_A, d_err, d_pairs, d_atom_octets)
+    do {                                                                                                            \
+        if (d_probs)                                                                                                \
+            GS_LAUNCH((k_accum_f32<V, N, true>), grid, 32 * ACC_WARPS, 0, st)(P, level, d_parents, d_vmask, n_oct,  \
+                                                                             (float)h, P.lat_exact_f32, d_A, d_err, \
+                                                                             d_pairs, d_atom_octets, d_probs,      \
+                                                                             d_mol);                               \
+        else                                                                                                        \
+            GS_LAUNCH((k_accum_f32<V, N, false>), grid, 32 * ACC_WARPS, 0, st)(P, level, d_parents, d_vmask, n_oct, \
+                                                                              (float)h, P.lat_exact_f32, d_A,      \
+                                                                              d_err, d_pairs, d_atom_octets,       \
+                                                                              nullptr, nullptr);                   \
+    } while (0)
     switch (gv) {
     case 5: GS_ACC32(5, 5); break;
     case 4: GS_ACC32(4, 6); break;
@@ -1785,9 +1824,17 @@ __global__ void k_count_mismatch(const uint8_t *a, const uint8_t *b, int64_t n, 
 // d_why: [0..2] flag reasons (bounds band, precision band, zero tensor), [3] low 32 bits = float bits of
 // the largest |A32 - A64| / E seen in debug mode, [4] the same for the band ratio, [5] flags through a rank
 // rule, [10] cubes decided without the SVD (corner values straddle c)
+__global__ void k_gather_mol(const int64_t *__restrict__ si, int64_t m, const int32_t *__restrict__ mol,
+                             int32_t *__restrict__ sub_mol)
+{
+    int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (t < m) sub_mol[t] = mol[si[t]];
+}
+
 int gs_level_mixed(const GsProblem &P, int level, const uint64_t *d_parents, int64_t n_oct, uint8_t *d_dec,
                    unsigned long long *d_pairs, unsigned long long *d_rechecked, unsigned long long *d_mism,
-                   bool both, unsigned *d_status, cudaStream_t st, float *ms, unsigned long long *d_why)
+                   bool both, unsigned *d_status, cudaStream_t st, float *ms, unsigned long long *d_why,
+                   const GsProblem *d_probs, const int32_t *d_mol, const uint8_t *d_vmask)
 {
     float *A = nullptr, *E = nullptr;
     uint8_t *flag = nullptr;
@@ -1797,8 +1844,10 @@ int gs_level_mixed(const GsProblem &P, int level, const uint64_t *d_parents, int
     float *dbg = nullptr;
     if (!rc && both) rc = gs_alloc((void **)&dbg, sizeof(float) * 6 * 8 * (size_t)n_oct, st);
     // the counter block holds the atom-octet count 16 slots after the pair count
-    if (!rc) rc = gs_accum_f32(P, level, d_parents, nullptr, n_oct, A, E, d_pairs, d_status, st, ms, d_pairs + 16);
-    if (!rc) rc = gs_estimate_f32(P, level, A, E, n_oct * 8, d_parents, nullptr, d_dec, flag, st, d_why, dbg);
+    if (!rc)
+        rc = gs_accum_f32(P, level, d_parents, d_vmask, n_oct, A, E, d_pairs, d_status, st, ms, d_pairs + 16, d_probs,
+                          d_mol);
+    if (!rc) rc = gs_estimate_f32(P, level, A, E, n_oct * 8, d_parents, d_vmask, d_dec, flag, st, d_why, dbg);
     if (!rc) {
         // decisions resting on one rank rule near its threshold
         int32_t *lst = nullptr;
@@ -1838,11 +1887,14 @@ int gs_level_mixed(const GsProblem &P, int level, const uint64_t *d_parents, int
         if (!rc) rc = gs_alloc((void **)&sm, (size_t)nsub, st);
         if (!rc) rc = gs_alloc((void **)&A64, sizeof(double) * 64 * 8 * (size_t)nsub, st);
         if (!rc) rc = gs_alloc((void **)&sd, 8 * (size_t)nsub, st);
+        int32_t *smol = nullptr;
+        if (!rc && d_mol) rc = gs_alloc((void **)&smol, sizeof(int32_t) * (size_t)nsub, st);
         if (!rc) {
             GS_LAUNCH(k_octet_gather, (unsigned)((n_oct + 255) / 256), 256, 0, st)(cnt, n_oct, d_parents, flag, sp, si,
                                                                                   sm);
+            if (d_mol) GS_LAUNCH(k_gather_mol, (unsigned)((nsub + 255) / 256), 256, 0, st)(si, nsub, d_mol, smol);
             // only the flagged children are accumulated and estimated in FP64
-            rc = gs_accum_f64(P, level, sp, sm, nsub, A64, nullptr, d_status, st, nullptr);
+            rc = gs_accum_f64(P, level, sp, sm, nsub, A64, nullptr, d_status, st, nullptr, d_probs, smol);
         }
         int32_t *lst = nullptr;
         unsigned *nl = nullptr;
@@ -1856,7 +1908,7 @@ int gs_level_mixed(const GsProblem &P, int level, const uint64_t *d_parents, int
         }
         gs_free(lst, st); gs_free(nl, st);
         if (!rc) GS_LAUNCH(k_octet_scatter, (unsigned)((nsub * 8 + 255) / 256), 256, 0, st)(sd, si, sm, nsub, d_dec);
-        gs_free(sp, st); gs_free(si, st); gs_free(sm, st); gs_free(A64, st); gs_free(sd, st);
+        gs_free(sp, st); gs_free(si, st); gs_free(sm, st); gs_free(A64, st); gs_free(sd, st); gs_free(smol, st);
     }
     gs_free(cnt, st); gs_free(tot, st);
     if (!rc && both) {

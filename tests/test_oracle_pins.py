@@ -350,11 +350,20 @@ def test_two_equal_atoms_mirror_symmetry():
     mirrored = (keys & ~np.int64(0x3FFFF)) | (nl - 1 - x)
     assert set(mirrored.tolist()) == set(keys.tolist())
     V = m["vertices"]
-    A = np.round(V, 9)
-    B = np.round(V * np.array([-1, 1, 1]), 9)
-    sa = set(map(tuple, A))
-    sb = set(map(tuple, B))
-    assert len(sa ^ sb) <= 0.001 * len(sa)
+    # every surface point's mirror image is a surface point (to 1e-9 A; the
+    # two sides round t and 1 - t differently)
+    W = V * np.array([-1.0, 1.0, 1.0])
+    order = np.lexsort(V.T[::-1])
+    Vs = V[order]
+    for w in W:
+        k = np.searchsorted(Vs[:, 0], w[0] - 1e-9)
+        found = False
+        while k < len(Vs) and Vs[k, 0] <= w[0] + 1e-9:
+            if np.abs(Vs[k] - w).max() < 1e-9:
+                found = True
+                break
+            k += 1
+        assert found
     check_closed_manifold(V, m["triangles"])
 
 
