@@ -431,7 +431,7 @@ def main():
     adaptive = None
     if args.adaptive_steps > 0:
         at = []
-        for _ in range(args.adaptive_steps):
+        for it in range(args.adaptive_steps + 1):   # the first run warms up (pools, tuned launch shapes)
             flush.zero_()
             barrier()
             e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
@@ -440,7 +440,8 @@ def main():
                                           device_output=True, **kw)
             e1.record(stream)
             barrier()
-            at.append(e0.elapsed_time(e1))
+            if it > 0:
+                at.append(e0.elapsed_time(e1))
         sa = ma.stats
         adaptive = {"workload": workload_desc(args.workload).replace("precision 1e-3", "precision 5e-2"),
                     "mode": args.mode, "ms_per_mesh": float(np.mean(at)),
@@ -478,29 +479,37 @@ def main():
                 "ms_forward": float(np.mean(tf)), "ms_backward": float(np.mean(tb)),
                 "n_vertices": int(dm.vertices.shape[0]), "volume_A3": float(vol), "area_A2": float(area)}
 
-    # batch form: 64 molecules, one call, worker threads with a stream each,
-    # against the same molecules meshed one call at a time
+    # batch form: 64 molecules in one call, with the shared level loop (each
+    # level's kernels launched once over every molecule with the same D),
+    # against whole meshes on 8 worker threads and one call at a time
     batch = None
     if batch_mols is not None:
         kwb = dict(precision_mode=mode, device_output=True)
         res = {}
-        for label, nw in (("sequential", 1), ("concurrent", 8)):
+        for label, nw, bmode in (("sequential", 1, gs.GS_BATCH_THREADS), ("threads", 8, gs.GS_BATCH_THREADS),
+                                 ("shared_levels", 8, gs.GS_BATCH_SHARED_LEVELS)):
             ts = []
             for it in range(args.batch_steps + 1):
                 flush.zero_()
                 barrier()
                 t0 = time.perf_counter()
                 bm = gs.mesh_gaussian_surface_batch(batch_mols, cfg["c"], cfg["precision"], cfg["max_depth"],
-                                                    n_workers=nw, **kwb)
+                                                    n_workers=nw, batch_mode=bmode, **kwb)
                 t1 = time.perf_counter()
                 if it > 0:
                     ts.append((t1 - t0) * 1e3)
             res[label] = float(np.mean(ts))
+            if label == "shared_levels":
+                res["levels_ms"] = {}
+                for (xyz_, r_, D_), m in zip(batch_mols, bm):
+                    res["levels_ms"].setdefault("D=%g" % D_, float(m.stats["ms_levels"]))
         natoms = sum(len(m[1]) for m in batch_mols)
         batch = {"workload": "64 globular molecules, %d atoms in all, n log-uniform in [500, 50000], D in {0.5, 0.9}, "
                              "host inputs, device outputs" % natoms,
-                 "ms_per_batch_concurrent": res["concurrent"], "ms_per_batch_sequential": res["sequential"],
-                 "molecules_per_s": 64 * 1e3 / res["concurrent"], "n_workers": 8,
+                 "ms_per_batch": res["shared_levels"], "ms_per_batch_threads": res["threads"],
+                 "ms_per_batch_sequential": res["sequential"],
+                 "ms_level_loop_per_group": res["levels_ms"],
+                 "molecules_per_s": 64 * 1e3 / res["shared_levels"], "n_workers": 8,
                  "n_triangles": int(sum(m.n_triangles for m in bm))}
 
     # the alternative readings of section 2.2 on the 20,000-atom globular
@@ -554,6 +563,8 @@ def main():
                 "copy_GBps_est": float(nbytes_out / ((e2e_ms - ms_per_mesh) * 1e-3) / 1e9)
                 if e2e_ms > ms_per_mesh else None, "link": link, "stage_ms_last": e2e_stage},
         "gpu_launches": int(st["n_kernel_launches"]),
+        # launch shapes the autotuner chose in this process (kernel, size class, choice, trial ms per shape)
+        "autotune": gs.autotune_report(),
         "fp64_form": fp64,
         "adaptive_form": adaptive,
         "diff_form": diff,

@@ -91,6 +91,11 @@ extern "C" {
 #define GS_CONFORM_EQUAL 1      /* every cube touching a finer one is split until cubes sharing a face or an
                                    edge have one size */
 
+/* gs_options.batch_mode (mesh_gaussian_surface_batch) */
+#define GS_BATCH_SHARED_LEVELS 0  /* one level loop per group of molecules with equal D: each kernel of a level
+                                     runs once over the octets of all the group's molecules */
+#define GS_BATCH_THREADS 1        /* host threads run whole single-molecule meshes on their own streams */
+
 /* decisions reported by gs_cube_decisions */
 #define GS_DEC_DISCARD 0
 #define GS_DEC_ACCEPT 1
@@ -150,6 +155,7 @@ typedef struct {
     int decision_order;     /* GS_ORDER_BOUNDS_FIRST (default) or GS_ORDER_LITERAL (FP64 form only) */
     int precision_norm;     /* GS_NORM_SUM (default), GS_NORM_MAX or GS_NORM_RSS (FP64 form only) */
     int conform_mode;       /* cubes of different sizes: GS_CONFORM_CONSTRAIN (default) or GS_CONFORM_EQUAL */
+    int batch_mode;         /* mesh_gaussian_surface_batch: GS_BATCH_SHARED_LEVELS (default) or GS_BATCH_THREADS */
 } gs_options;
 
 typedef struct {
@@ -217,14 +223,30 @@ int mesh_gaussian_surface_into(const double *atoms, const double *radii, int64_t
  * method applies to each molecule on its own; the paper meshes one at a
  * time).  Molecule m is atoms[offsets[m] .. offsets[m+1]) with decay rate
  * D[m]; c, precision, max_depth and opt are shared (opt->stats and
- * opt->cuda_stream are ignored).  n_workers host threads, each with its own
- * CUDA stream, take the molecules largest first, so small molecules overlap
- * on the GPU.  out [n_mols] receives one mesh per molecule (release each with
- * mesh_free); stats [n_mols] (nullable) one record per molecule.
+ * opt->cuda_stream are ignored).  out [n_mols] receives one mesh per
+ * molecule, each identical to what mesh_gaussian_surface gives for that
+ * molecule alone (release each with mesh_free); stats [n_mols] (nullable)
+ * one record per molecule.
  *   offsets [n_mols + 1] host int64, offsets[0] = 0, strictly increasing;
  *   D [n_mols] host.  Atoms and radii host or device.
+ * opt->batch_mode:
+ *   GS_BATCH_SHARED_LEVELS (default; GS_CHILD_REPROJECT only, else as
+ *   GS_BATCH_THREADS): the molecules are grouped by D.  Per group one level
+ *   loop (section 2.2) runs each kernel of a level once over the octets of
+ *   all its molecules; every octet carries its molecule's index, and a
+ *   device table holds each molecule's atoms, cell list and root grid.  The
+ *   host reads one block of per-molecule counts per level and group.  Then
+ *   n_workers host threads, each with its own stream, finish the meshes
+ *   (conformity, lattice, field, triangulation, weld), largest first.  In
+ *   stats, examined .. split are the molecule's own; pair_terms,
+ *   atom_octets, recheck_cubes, the recheck reasons, estimate_fast_cubes,
+ *   ms_level, ms_levels and ms_accum are those of its group; ms_total
+ *   covers the molecule's own stages after the level loop.
+ *   GS_BATCH_THREADS: n_workers host threads run whole single-molecule
+ *   meshes on their own streams, largest molecules first.
  * Errors: as mesh_gaussian_surface for any molecule (the message names it);
- * on error every out[m] is released and zeroed.
+ * GS_ERR_ARG for an unknown batch_mode; on error every out[m] is released
+ * and zeroed.
  */
 int mesh_gaussian_surface_batch(const double *atoms, const double *radii, const int64_t *offsets, int64_t n_mols,
                                 const double *D, double c, double precision, int max_depth, const gs_options *opt,
@@ -238,6 +260,24 @@ const char *gs_status_string(int status);
 
 /* message for the calling thread's last failure ("" if none) */
 const char *gs_last_error(void);
+
+/*
+ * Launch-shape autotuner.  Kernels with several launch shapes that compute
+ * the same result (the lattice-field kernel's tile: warps per block and
+ * vertices per lane; the FP32 tensor accumulation's grid size) time every
+ * shape on the first call's own data for each size class (a power of two of
+ * the item count), keep the fastest for the process, and launch it from
+ * then on.  Results do not depend on the choice.  GS_AUTOTUNE=0
+ * (environment) turns tuning off (shape 0 everywhere); GS_AUTOTUNE=shape:K
+ * takes shape K everywhere (the last shape where a kernel has fewer).
+ * gs_autotune_report writes one line per (kernel, size class): "kernel 2^k
+ * choice t0 t1 ..." (trial milliseconds per shape) into buf [cap] (NUL-
+ * terminated, cut to fit; buf may be NULL) and returns the length the
+ * whole report needs, NUL included.  gs_autotune_reset forgets every
+ * choice.  Both are thread-safe.
+ */
+int64_t gs_autotune_report(char *buf, int64_t cap);
+void gs_autotune_reset(void);
 
 /* sizeof of the ABI structs (0: gs_stats, 1: gs_options, 2: gs_mesh; else -1),
  * for bindings to verify their layouts */

@@ -54,7 +54,8 @@ class Options(ctypes.Structure):
     _fields_ = [("min_edge", ctypes.c_double), ("precision_mode", ctypes.c_int), ("cutoff_rel", ctypes.c_double),
                 ("cuda_stream", ctypes.c_void_p), ("device_output", ctypes.c_int), ("debug_flags", ctypes.c_int),
                 ("stats", ctypes.POINTER(Stats)), ("child_mode", ctypes.c_int),
-                ("decision_order", ctypes.c_int), ("precision_norm", ctypes.c_int), ("conform_mode", ctypes.c_int)]
+                ("decision_order", ctypes.c_int), ("precision_norm", ctypes.c_int), ("conform_mode", ctypes.c_int),
+                ("batch_mode", ctypes.c_int)]
 
 
 class MeshBuffers(ctypes.Structure):
@@ -118,6 +119,10 @@ def load():
     L.mesh_gaussian_surface_batch.restype = i32
     L.gs_mesh_intersections.argtypes = [p, i64, p, i64, d, p, ctypes.POINTER(Options)]
     L.gs_mesh_intersections.restype = i32
+    L.gs_autotune_report.argtypes = [ctypes.c_char_p, i64]
+    L.gs_autotune_report.restype = i64
+    L.gs_autotune_reset.argtypes = []
+    L.gs_autotune_reset.restype = None
     for which, cls in ((0, Stats), (1, Options), (2, MeshC)):
         if L.gs_struct_size(which) != ctypes.sizeof(cls):
             raise GsError(-1, "ABI struct %s: library %d bytes, binding %d" % (cls.__name__, L.gs_struct_size(which),
@@ -195,6 +200,7 @@ GS_CHILD_REPROJECT, GS_CHILD_REEXPAND = 0, 1
 GS_ORDER_BOUNDS_FIRST, GS_ORDER_LITERAL = 0, 1
 GS_NORM_SUM, GS_NORM_MAX, GS_NORM_RSS = 0, 1, 2
 GS_CONFORM_CONSTRAIN, GS_CONFORM_EQUAL = 0, 1
+GS_BATCH_SHARED_LEVELS, GS_BATCH_THREADS = 0, 1
 
 
 def mesh_gaussian_surface(atoms, radii, D, c, precision, max_depth, min_edge=0.25, precision_mode=GS_PREC_FP64,
@@ -479,10 +485,13 @@ def gs_volume_area(vertices, triangles, grad=False, stream=None):
 
 
 def mesh_gaussian_surface_batch(molecules, c, precision, max_depth, min_edge=0.25, precision_mode=GS_PREC_FP64,
-                                cutoff_rel=1e-8, n_workers=8, device_output=False):
-    """Mesh several molecules concurrently: molecules is a list of (atoms
-    [n,3], radii [n], D).  Returns a list of Mesh (host arrays unless
-    device_output, as in mesh_gaussian_surface)."""
+                                cutoff_rel=1e-8, n_workers=8, device_output=False,
+                                batch_mode=GS_BATCH_SHARED_LEVELS, debug_flags=0):
+    """Mesh several molecules: molecules is a list of (atoms [n,3], radii
+    [n], D).  batch_mode GS_BATCH_SHARED_LEVELS runs one level loop per
+    group of equal D over all the group's molecules, GS_BATCH_THREADS whole
+    meshes on n_workers host threads.  Returns a list of Mesh (host arrays
+    unless device_output, as in mesh_gaussian_surface)."""
     L = load()
     xs = [np.ascontiguousarray(m[0], dtype=np.float64).reshape(-1, 3) for m in molecules]
     rs = [np.ascontiguousarray(m[1], dtype=np.float64).reshape(-1) for m in molecules]
@@ -499,6 +508,8 @@ def mesh_gaussian_surface_batch(molecules, c, precision, max_depth, min_edge=0.2
     o.precision_mode = precision_mode
     o.cutoff_rel = cutoff_rel
     o.device_output = 1 if device_output else 0
+    o.batch_mode = batch_mode
+    o.debug_flags = debug_flags
     _check(L.mesh_gaussian_surface_batch(_ptr(atoms), _ptr(radii), _ptr(offsets), nm, _ptr(Ds), c, precision,
                                          max_depth, ctypes.byref(o), n_workers, ctypes.cast(outs, ctypes.c_void_p),
                                          ctypes.cast(stats, ctypes.c_void_p)))
@@ -512,6 +523,26 @@ def mesh_gaussian_surface_batch(molecules, c, precision, max_depth, min_edge=0.2
         else:
             res.append(_mesh_from_c(outs[m], L, stats[m], max_depth))
     return res
+
+
+def autotune_report():
+    """The autotuner's choices: a list of dicts (kernel, size_class (log2 of
+    the item count), choice, trial_ms per shape)."""
+    L = load()
+    need = L.gs_autotune_report(None, 0)
+    buf = ctypes.create_string_buffer(int(need))
+    L.gs_autotune_report(buf, need)
+    out = []
+    for line in buf.value.decode().splitlines():
+        f = line.split()
+        out.append({"kernel": f[0], "size_class": int(f[1][2:]), "choice": int(f[2]),
+                    "trial_ms": [float(x) for x in f[3:]]})
+    return out
+
+
+def autotune_reset():
+    """Forget every autotuner choice."""
+    load().gs_autotune_reset()
 
 
 def gs_mesh_intersections(vertices, triangles, tol=1e-9, stream=None):

@@ -19,7 +19,9 @@
 
 #include <algorithm>
 #include <initializer_list>
+#include <memory>
 #include <atomic>
+#include <condition_variable>
 #include <string>
 #include <thread>
 #include <vector>
@@ -316,6 +318,19 @@ static int prepare(const double *atoms, const double *radii, int64_t n, double D
     return GS_OK;
 }
 
+// the batched form's extra level state: the problem records (device), the
+// parents' molecule indices, the root blocks' valid children (level 0),
+// and outputs: the accepted cubes' molecule indices (one array per part),
+// the next parents' molecule indices and per-molecule decision counts
+struct LevelBatch {
+    const GsProblem *d_probs = nullptr;
+    const int32_t *pmol = nullptr;
+    const uint8_t *pvmask = nullptr;
+    std::vector<int32_t *> acc_mol;
+    int32_t *next_mol = nullptr;
+    unsigned long long *molcnt = nullptr;
+};
+
 // process one level in chunks of parents; appends accepted keys; returns the next parents
 // d_parA (re-expansion only): the parents' tensors [n_oct][64]; *d_nextA
 // receives the split cubes' tensors for the next level
@@ -324,7 +339,7 @@ static int run_level(const GsProblem &P, int level, const uint64_t *d_parents, i
                      uint64_t **d_next, int64_t *n_next, unsigned long long *d_counters, unsigned long long *d_pairs,
                      unsigned long long *d_rechecked, unsigned long long *d_mism, bool both, unsigned *d_status,
                      gs_stats *stats, bool reexpand = false, const double *d_parA = nullptr,
-                     double **d_nextA = nullptr, int64_t CH = (int64_t)1 << 21)
+                     double **d_nextA = nullptr, int64_t CH = (int64_t)1 << 21, LevelBatch *lb = nullptr)
 {
     cudaStream_t st = B.st;
     // CH: octets per chunk (2^21: 8 GB of FP64 tensors; smaller after an
@@ -334,44 +349,64 @@ static int run_level(const GsProblem &P, int level, const uint64_t *d_parents, i
                                                  level);
     std::vector<uint64_t *> nexts;
     std::vector<double *> nextAs;
+    std::vector<int32_t *> nextMols;
     std::vector<int64_t> ncnt;
     *d_next = nullptr;
     *n_next = 0;
     if (d_nextA) *d_nextA = nullptr;
+    if (lb) lb->next_mol = nullptr;
+    // frees the chunks' next-level arrays on an error
+    auto drop_nexts = [&]() {
+        for (size_t i = 0; i < nexts.size(); i++) { gs_free(nexts[i], st); gs_free(nextAs[i], st); gs_free(nextMols[i], st); }
+    };
     for (int64_t o0 = 0; o0 < n_oct; o0 += CH) {
         int64_t m = n_oct - o0 < CH ? n_oct - o0 : CH;
         const uint64_t *par = d_parents + o0;
+        const int32_t *pmol = lb ? lb->pmol + o0 : nullptr;
+        const uint8_t *pvm = lb && lb->pvmask ? lb->pvmask + o0 : nullptr;
+        const GsProblem *probs = lb ? lb->d_probs : nullptr;
         uint8_t *dec = nullptr;
         int rc = gs_alloc((void **)&dec, (size_t)m * 8, st);
-        if (rc) return rc;
+        if (rc) { drop_nexts(); return rc; }
         float tacc = 0.f;
         if (mode == GS_PREC_MIXED) {
             rc = gs_level_mixed(P, level, par, m, dec, d_pairs, d_rechecked, d_mism, both, d_status, st,
-                                stats ? &tacc : nullptr, d_mism + 1);
+                                stats ? &tacc : nullptr, d_mism + 1, probs, pmol, pvm);
         }
         double *dA = nullptr;
         if (mode != GS_PREC_MIXED) {
             rc = gs_alloc((void **)&dA, sizeof(double) * 64 * 8 * (size_t)m, st);
-            if (rc) { gs_free(dec, st); return rc; }
+            if (rc) { gs_free(dec, st); drop_nexts(); return rc; }
             if (reexpand && d_parA) rc = gs_reexpand(d_parA + 64 * o0, m, dA, st);
-            else rc = gs_accum_f64(P, level, par, nullptr, m, dA, d_pairs, d_status, st, stats ? &tacc : nullptr);
-            if (!rc) rc = gs_estimate_f64(P, level, dA, m * 8, par, nullptr, dec, nullptr, st);
+            else
+                rc = gs_accum_f64(P, level, par, pvm, m, dA, d_pairs, d_status, st, stats ? &tacc : nullptr, probs,
+                                  pmol);
+            if (!rc) rc = gs_estimate_f64(P, level, dA, m * 8, par, pvm, dec, nullptr, st);
         }
         if (stats) { stats->ms_accum += tacc; stats->n_accum_launches++; }
+        if (!rc && lb) rc = gs_level_count_mol(dec, m * 8, pmol, lb->molcnt, st);
         uint64_t *acc = nullptr;
+        int32_t *accm = nullptr;
         if (!rc) rc = gs_alloc((void **)&acc, sizeof(uint64_t) * (size_t)m * 8, st);
+        if (!rc && lb) rc = gs_alloc((void **)&accm, sizeof(int32_t) * (size_t)m * 8, st);
         uint64_t *nx = nullptr;
         double *nA = nullptr;
+        int32_t *nm = nullptr;
         int64_t nn = 0, na = 0;
         if (!rc)
-            rc = gs_level_compact(P, level, par, nullptr, m, dec, &nx, &nn, acc, m * 8, &na, d_counters, st,
-                                  reexpand ? dA : nullptr, reexpand ? &nA : nullptr);
+            rc = gs_level_compact(P, level, par, pvm, m, dec, &nx, &nn, acc, m * 8, &na, d_counters, st,
+                                  reexpand ? dA : nullptr, reexpand ? &nA : nullptr, pmol, lb ? &nm : nullptr, accm);
         gs_free(dec, st);
         gs_free(dA, st);
-        if (rc) { gs_free(acc, st); gs_free(nx, st); gs_free(nA, st); return rc; }
+        if (rc) {
+            gs_free(acc, st); gs_free(accm, st); gs_free(nx, st); gs_free(nA, st); gs_free(nm, st);
+            drop_nexts();
+            return rc;
+        }
         acc_parts.push_back(acc);
         acc_counts.push_back(na);
-        if (nx) { nexts.push_back(nx); nextAs.push_back(nA); ncnt.push_back(nn); }
+        if (lb) lb->acc_mol.push_back(accm);
+        if (nx) { nexts.push_back(nx); nextAs.push_back(nA); nextMols.push_back(nm); ncnt.push_back(nn); }
     }
     int64_t total = 0;
     for (auto v : ncnt) total += v;
@@ -379,10 +414,12 @@ static int run_level(const GsProblem &P, int level, const uint64_t *d_parents, i
         *d_next = nexts[0];
         if (d_nextA) *d_nextA = nextAs[0];
         else gs_free(nextAs[0], st);
+        if (lb) lb->next_mol = nextMols[0];
     } else if (total > 0) {
         int rc = gs_alloc((void **)d_next, sizeof(uint64_t) * (size_t)total, st);
         if (!rc && reexpand && d_nextA) rc = gs_alloc((void **)d_nextA, sizeof(double) * 64 * (size_t)total, st);
-        if (rc) return rc;
+        if (!rc && lb) rc = gs_alloc((void **)&lb->next_mol, sizeof(int32_t) * (size_t)total, st);
+        if (rc) { drop_nexts(); return rc; }
         int64_t off = 0;
         for (size_t i = 0; i < nexts.size(); i++) {
             GS_CHECK(cudaMemcpyAsync(*d_next + off, nexts[i], sizeof(uint64_t) * (size_t)ncnt[i],
@@ -390,9 +427,13 @@ static int run_level(const GsProblem &P, int level, const uint64_t *d_parents, i
             if (reexpand && d_nextA && nextAs[i])
                 GS_CHECK(cudaMemcpyAsync(*d_nextA + 64 * off, nextAs[i], sizeof(double) * 64 * (size_t)ncnt[i],
                                          cudaMemcpyDeviceToDevice, st));
+            if (lb)
+                GS_CHECK(cudaMemcpyAsync(lb->next_mol + off, nextMols[i], sizeof(int32_t) * (size_t)ncnt[i],
+                                         cudaMemcpyDeviceToDevice, st));
             off += ncnt[i];
             gs_free(nexts[i], st);
             gs_free(nextAs[i], st);
+            gs_free(nextMols[i], st);
         }
     }
     *n_next = total;
@@ -538,51 +579,14 @@ __global__ void k_grid_cubes(int64_t nx, int64_t ny, int64_t nz, uint64_t *cubes
     cubes[i] = gk_make(i % nx, (i / nx) % ny, i / (nx * ny), GT_CUBE, 0);
 }
 
-// backward request: dL/d(mesh vertices) in, dL/d(atoms, radii, D) out
-struct BackReq {
-    const double *gv;   // [nv, 3], host or device
-    int64_t nv;
-    double *g_atoms, *g_radii, *g_D;   // host or device
-};
-
-static int put_out(void *dst, const void *src, size_t bytes, cudaStream_t st);
-
-static int mesh_impl(const double *atoms, const double *radii, int64_t n, double D, double c, double precision,
-                     int max_depth, const gs_options &o, gs_mesh *out, cudaStream_t st, const BackReq *bw = nullptr,
-                     gs_mesh_buffers *into = nullptr, int64_t chunk = (int64_t)1 << 21, bool *retryable = nullptr)
+// the level loop of one molecule (section 2.2, steps 1-3): the accepted
+// cubes, level by level, in *cubes (device, the caller owns them)
+static int single_levels(const GsProblem &P, const gs_options &o, int max_depth, DevBufs &B, Timer &T,
+                         unsigned long long *d_cnt, unsigned *d_status, gs_stats *stats, int64_t chunk,
+                         bool *retryable, uint64_t **cubes_out, int64_t *nc_out)
 {
-    gs_stats local;
-    gs_stats *stats = o.stats ? o.stats : &local;
-    memset(stats, 0, sizeof(*stats));
-    DevBufs B(st);
-    Timer T(st);
-    int tstart = T.mark();
-    long long launches0 = gs_launch_count();
-    unsigned *d_status = nullptr;
-    // counters: [0..4] level decisions, [8] pairs, [9] vertex terms, [10..12] triangulation,
-    // [13] rechecked cubes, [14] mismatches, [15..17] recheck reasons, [18] error-ratio bits
-    unsigned long long *d_cnt = nullptr;
-    int rc = B.get(&d_status, 1);
-    if (!rc) rc = B.get(&d_cnt, 32);
-    if (rc) return rc;
-    GS_CHECK(cudaMemsetAsync(d_status, 0, sizeof(unsigned), st));
-    GS_CHECK(cudaMemsetAsync(d_cnt, 0, 32 * sizeof(unsigned long long), st));
-    Prepared PR;
-    {
-        NvtxRange nr("gs: upload, prep, cell list");
-        rc = prepare(atoms, radii, n, D, c, o.cutoff_rel, precision, o.min_edge, max_depth, B, d_status, &PR, stats, T);
-    }
-    if (rc) return rc;
-    PR.P.order = o.decision_order;
-    PR.P.norm = o.precision_norm;
-    const GsProblem &P = PR.P;
-    if (o.precision_mode == GS_PREC_MIXED) {
-        rc = check_fp32_range(P);
-        if (rc) return rc;
-    }
-
-    // ---- level loop (section 2.2, steps 1-3)
-    int tl0 = T.mark();
+    cudaStream_t st = B.st;
+    int rc = GS_OK;
     std::vector<uint64_t *> acc_all;
     std::vector<int64_t> acc_cnt;
     uint64_t *parents = nullptr;
@@ -648,6 +652,115 @@ static int mesh_impl(const double *atoms, const double *radii, int64_t n, double
             B.release(acc_all[i]);
         }
     }
+    *cubes_out = cubes;
+    *nc_out = nc;
+    return GS_OK;
+}
+
+// backward request: dL/d(mesh vertices) in, dL/d(atoms, radii, D) out
+struct BackReq {
+    const double *gv;   // [nv, 3], host or device
+    int64_t nv;
+    double *g_atoms, *g_radii, *g_D;   // host or device
+};
+
+static int put_out(void *dst, const void *src, size_t bytes, cudaStream_t st);
+
+// the batched form's per-molecule state entering mesh_impl: the prepared
+// atoms (buffers owned by the batch), the accepted cubes of the shared level
+// loop (mesh_impl takes them over) and the level statistics
+struct PreMol {
+    Prepared PR;
+    uint64_t *cubes = nullptr;
+    int64_t nc = 0;
+    int64_t mismatches = 0;
+    gs_stats lv;
+};
+
+// the level loop's fields of gs_stats (in the batched form those of the
+// molecule's group, apart from the per-level decision counts)
+static void copy_level_stats(gs_stats *d, const gs_stats &s)
+{
+    memcpy(d->examined, s.examined, sizeof(s.examined));
+    memcpy(d->discarded, s.discarded, sizeof(s.discarded));
+    memcpy(d->accepted, s.accepted, sizeof(s.accepted));
+    memcpy(d->forced, s.forced, sizeof(s.forced));
+    memcpy(d->split, s.split, sizeof(s.split));
+    memcpy(d->ms_level, s.ms_level, sizeof(s.ms_level));
+    d->pair_terms = s.pair_terms;
+    d->atom_octets = s.atom_octets;
+    d->recheck_cubes = s.recheck_cubes;
+    d->recheck_bounds = s.recheck_bounds;
+    d->recheck_precision = s.recheck_precision;
+    d->recheck_zero = s.recheck_zero;
+    d->recheck_rank = s.recheck_rank;
+    d->estimate_fast_cubes = s.estimate_fast_cubes;
+    d->mixed_err_ratio = s.mixed_err_ratio;
+    d->mixed_band_ratio = s.mixed_band_ratio;
+    d->ms_upload = s.ms_upload;
+    d->ms_bin = s.ms_bin;
+    d->ms_levels = s.ms_levels;
+    d->ms_accum = s.ms_accum;
+    d->n_accum_launches = s.n_accum_launches;
+    d->retries = s.retries;
+}
+
+static int mesh_impl(const double *atoms, const double *radii, int64_t n, double D, double c, double precision,
+                     int max_depth, const gs_options &o, gs_mesh *out, cudaStream_t st, const BackReq *bw = nullptr,
+                     gs_mesh_buffers *into = nullptr, int64_t chunk = (int64_t)1 << 21, bool *retryable = nullptr,
+                     const PreMol *pre = nullptr)
+{
+    gs_stats local;
+    gs_stats *stats = o.stats ? o.stats : &local;
+    memset(stats, 0, sizeof(*stats));
+    if (pre) copy_level_stats(stats, pre->lv);
+    // the batch's cubes are this call's from here on: freed on an early
+    // return, handed to the conformity pass below
+    struct CubesGuard {
+        uint64_t *p;
+        cudaStream_t st;
+        ~CubesGuard() { gs_free(p, st); }
+    } pre_cubes{pre ? pre->cubes : nullptr, st};
+    DevBufs B(st);
+    Timer T(st);
+    int tstart = T.mark();
+    long long launches0 = gs_launch_count();
+    unsigned *d_status = nullptr;
+    // counters: [0..4] level decisions, [8] pairs, [9] vertex terms, [10..12] triangulation,
+    // [13] rechecked cubes, [14] mismatches, [15..17] recheck reasons, [18] error-ratio bits
+    unsigned long long *d_cnt = nullptr;
+    int rc = B.get(&d_status, 1);
+    if (!rc) rc = B.get(&d_cnt, 32);
+    if (rc) return rc;
+    GS_CHECK(cudaMemsetAsync(d_status, 0, sizeof(unsigned), st));
+    GS_CHECK(cudaMemsetAsync(d_cnt, 0, 32 * sizeof(unsigned long long), st));
+    Prepared PR;
+    if (pre) {
+        PR = pre->PR;
+    } else {
+        NvtxRange nr("gs: upload, prep, cell list");
+        rc = prepare(atoms, radii, n, D, c, o.cutoff_rel, precision, o.min_edge, max_depth, B, d_status, &PR, stats, T);
+    }
+    if (rc) return rc;
+    PR.P.order = o.decision_order;
+    PR.P.norm = o.precision_norm;
+    const GsProblem &P = PR.P;
+    if (o.precision_mode == GS_PREC_MIXED) {
+        rc = check_fp32_range(P);
+        if (rc) return rc;
+    }
+
+    // ---- level loop (section 2.2, steps 1-3), or the batched form's result
+    int tl0 = T.mark();
+    uint64_t *cubes = nullptr;
+    int64_t nc = 0;
+    if (pre) {
+        cubes = pre->cubes;
+        nc = pre->nc;
+    } else {
+        rc = single_levels(P, o, max_depth, B, T, d_cnt, d_status, stats, chunk, retryable, &cubes, &nc);
+        if (rc) return rc;
+    }
     int tl1 = T.mark();
 
     // ---- cubes of different sizes (section 2.3, the points of neighbouring
@@ -658,6 +771,7 @@ static int mesh_impl(const double *atoms, const double *radii, int64_t n, double
     for (int l = 0; l <= max_depth; l++) acc_levels += (stats->accepted[l] + stats->forced[l]) > 0 ? 1 : 0;
     const bool constrain = acc_levels > 1 && o.conform_mode == GS_CONFORM_CONSTRAIN;
     NvtxRange nr_field("gs: conformity, lattice, field");
+    pre_cubes.p = nullptr;
     if (acc_levels > 1) rc = gs_conformity(&cubes, &nc, max_depth, constrain ? 2 : 1, &splits, d_status, st);
     if (rc) { gs_free(cubes, st); return rc; }
     int tc1 = T.mark();
@@ -897,6 +1011,10 @@ static int mesh_impl(const double *atoms, const double *radii, int64_t n, double
     stats->ms_download = T.ms(tw1, tend);
     stats->ms_total = T.ms(tstart, tend);
     stats->n_kernel_launches = gs_launch_count() - launches0;
+    if (pre) {
+        copy_level_stats(stats, pre->lv);
+        if (out) out->mismatches = pre->mismatches;
+    }
     return GS_OK;
 }
 
@@ -999,28 +1117,193 @@ extern "C" int mesh_gaussian_surface_into(const double *atoms, const double *rad
     return rc;
 }
 
-extern "C" int mesh_gaussian_surface_batch(const double *atoms, const double *radii, const int64_t *offsets,
-                                           int64_t n_mols, const double *D, double c, double precision, int max_depth,
-                                           const gs_options *opt, int n_workers, gs_mesh *out, gs_stats *stats)
+// ---- the batched form
+
+// the level loop of a group of molecules sharing D (section 2.2, steps 1-3,
+// for all of them at once): each kernel of a level runs once over the
+// octets of every molecule of the group.  On return pm[mols[g]] holds the
+// molecule's accepted cubes, in the order its own level loop gives them,
+// and its level statistics.
+static int group_levels(const std::vector<int64_t> &mols, std::vector<PreMol> &pm, const gs_options &o,
+                        int max_depth, cudaStream_t st, int64_t CH, bool *retryable)
 {
-    if (!out || n_mols <= 0 || !offsets || !D) return gs_fail(GS_ERR_ARG, "need n_mols >= 1, offsets, D and out");
-    for (int64_t m = 0; m < n_mols; m++) memset(&out[m], 0, sizeof(gs_mesh));
-    gs_options base = opt ? *opt : gs_default_options();
-    if (offsets[0] != 0) return gs_fail(GS_ERR_ARG, "offsets[0] must be 0");
-    for (int64_t m = 0; m < n_mols; m++) {
-        if (offsets[m + 1] <= offsets[m]) return gs_fail(GS_ERR_ARG, "molecule %lld is empty", (long long)m);
-        gs_options o = base;
-        int rc = check_mesh_args(atoms, radii, offsets[m + 1] - offsets[m], D[m], c, precision, max_depth, o);
-        if (rc) return rc;
-    }
-    int rc = device_setup();
+    const int G = (int)mols.size();
+    const int L = max_depth + 1;
+    DevBufs B(st);
+    Timer T(st);
+    const int t0 = T.mark();
+    unsigned *d_status = nullptr;
+    unsigned long long *d_cnt = nullptr, *d_molcnt = nullptr;
+    GsProblem *d_probs = nullptr;
+    int rc = B.get(&d_status, 1);
+    if (!rc) rc = B.get(&d_cnt, 32);
+    if (!rc) rc = B.get(&d_molcnt, 5 * (size_t)G);
+    if (!rc) rc = B.get(&d_probs, (size_t)G);
     if (rc) return rc;
+    std::vector<GsProblem> hp((size_t)G);
+    for (int g = 0; g < G; g++) hp[(size_t)g] = pm[(size_t)mols[(size_t)g]].PR.P;
+    GS_CHECK(cudaMemsetAsync(d_status, 0, sizeof(unsigned), st));
+    GS_CHECK(cudaMemsetAsync(d_cnt, 0, 32 * sizeof(unsigned long long), st));
+    GS_CHECK(cudaMemcpyAsync(d_probs, hp.data(), sizeof(GsProblem) * (size_t)G, cudaMemcpyHostToDevice, st));
+    // the record the shared kernels read: the group's common scalars (D, c,
+    // precision, depth, order, norm); level-0 children outside a molecule's
+    // root grid are masked explicitly, so its root extent is unbounded
+    GsProblem P0 = hp[0];
+    for (int a = 0; a < 3; a++) P0.nroot[a] = (int64_t)1 << 40;
+    uint64_t *parents = nullptr;
+    uint8_t *vmask0 = nullptr;
+    int32_t *pmol = nullptr;
+    int64_t n_oct = 0;
+    rc = gs_root_blocks_batch(hp.data(), G, &parents, &vmask0, &pmol, &n_oct, st);
+    if (rc) return rc;
+    B.keep(parents); B.keep(vmask0); B.keep(pmol);
+    std::vector<std::vector<uint64_t *>> acc((size_t)L);
+    std::vector<std::vector<int32_t *>> accm((size_t)L);
+    std::vector<std::vector<int64_t>> accn((size_t)L);
+    std::vector<int64_t> molcnt((size_t)L * 5 * (size_t)G, 0);
+    gs_stats gst;
+    memset(&gst, 0, sizeof(gst));
+    for (int l = 0; l < L && n_oct > 0; l++) {
+        char lname[48];
+        snprintf(lname, sizeof(lname), "gs: batch level %d", l);
+        NvtxRange nr(lname);
+        const int ta = T.mark();
+        GS_CHECK(cudaMemsetAsync(d_cnt, 0, 5 * sizeof(unsigned long long), st));
+        GS_CHECK(cudaMemsetAsync(d_molcnt, 0, 5 * (size_t)G * sizeof(unsigned long long), st));
+        LevelBatch lb;
+        lb.d_probs = d_probs;
+        lb.pmol = pmol;
+        lb.pvmask = l == 0 ? vmask0 : nullptr;
+        lb.molcnt = d_molcnt;
+        uint64_t *next = nullptr;
+        int64_t nn = 0;
+        rc = run_level(P0, l, parents, n_oct, o.precision_mode, B, acc[(size_t)l], accn[(size_t)l], &next, &nn, d_cnt,
+                       d_cnt + 8, d_cnt + 13, d_cnt + 14, (o.debug_flags & 1) != 0, d_status, &gst, false, nullptr,
+                       nullptr, (o.debug_flags & 2) ? (int64_t)1000 : CH, &lb);
+        for (auto q : acc[(size_t)l]) B.keep(q);
+        for (auto q : lb.acc_mol) B.keep(q);
+        accm[(size_t)l] = lb.acc_mol;
+        B.release(parents); B.release(pmol);
+        if (l == 0) B.release(vmask0);
+        if (rc) {
+            if (retryable && (rc == GS_ERR_OOM || rc == GS_ERR_CAPACITY)) *retryable = true;
+            gs_free(next, st);
+            gs_free(lb.next_mol, st);
+            return rc;
+        }
+        parents = next;
+        pmol = lb.next_mol;
+        B.keep(parents); B.keep(pmol);
+        n_oct = nn;
+        const int tb = T.mark();
+        std::vector<unsigned long long> h((size_t)G * 5 + 5);
+        GS_CHECK(cudaMemcpyAsync(h.data(), d_molcnt, sizeof(unsigned long long) * 5 * (size_t)G,
+                                 cudaMemcpyDeviceToHost, st));
+        GS_CHECK(cudaMemcpyAsync(h.data() + 5 * (size_t)G, d_cnt, 5 * sizeof(unsigned long long),
+                                 cudaMemcpyDeviceToHost, st));
+        GS_CHECK(gs_sync(st));
+        for (size_t k = 0; k < 5 * (size_t)G; k++) molcnt[(size_t)l * 5 * G + k] = (int64_t)h[k];
+        const unsigned long long *tot = h.data() + 5 * (size_t)G;
+        gst.examined[l] = (int64_t)tot[0]; gst.discarded[l] = (int64_t)tot[1]; gst.accepted[l] = (int64_t)tot[2];
+        gst.forced[l] = (int64_t)tot[3]; gst.split[l] = (int64_t)tot[4];
+        gst.ms_level[l] = T.ms(ta, tb);
+    }
+    B.release(parents); B.release(pmol);
+    rc = check_status(d_status, st, "levels");
+    if (rc) return rc;
+    // each molecule's accepted cubes, level by level: per level the parts
+    // are grouped by molecule, molecule g's run starting at the sum of the
+    // earlier molecules' counts
+    auto nacc = [&](int l, int g) {
+        const int64_t *m = &molcnt[((size_t)l * G + (size_t)g) * 5];
+        return m[2] + m[3];
+    };
+    std::vector<int64_t> shift((size_t)L * G), ntot((size_t)G, 0);
+    for (int l = 0; l < L; l++) {
+        int64_t seg = 0, parts = 0;
+        for (int g = 0; g < G; g++) {
+            shift[(size_t)l * G + g] = ntot[(size_t)g] - seg;
+            seg += nacc(l, g);
+            ntot[(size_t)g] += nacc(l, g);
+        }
+        for (auto v : accn[(size_t)l]) parts += v;
+        if (parts != seg) return gs_fail(GS_ERR_DEVICE_STATUS, "level %d: %lld accepted cubes, %lld by molecule", l,
+                                         (long long)parts, (long long)seg);
+    }
+    std::vector<uint64_t *> outs((size_t)G, nullptr);
+    auto drop_outs = [&]() {
+        for (auto q : outs) gs_free(q, st);
+    };
+    for (int g = 0; g < G && !rc; g++) rc = gs_alloc((void **)&outs[(size_t)g], sizeof(uint64_t) * (size_t)(ntot[(size_t)g] + 1), st);
+    int64_t *d_shift = nullptr, *d_cap = nullptr;
+    uint64_t **d_outs = nullptr;
+    if (!rc) rc = B.get(&d_shift, shift.size());
+    if (!rc) rc = B.get(&d_cap, (size_t)G);
+    if (!rc) rc = B.get(&d_outs, (size_t)G);
+    if (rc) { drop_outs(); return rc; }
+    GS_CHECK(cudaMemcpyAsync(d_shift, shift.data(), sizeof(int64_t) * shift.size(), cudaMemcpyHostToDevice, st));
+    GS_CHECK(cudaMemcpyAsync(d_cap, ntot.data(), sizeof(int64_t) * (size_t)G, cudaMemcpyHostToDevice, st));
+    GS_CHECK(cudaMemcpyAsync(d_outs, outs.data(), sizeof(uint64_t *) * (size_t)G, cudaMemcpyHostToDevice, st));
+    for (int l = 0; l < L && !rc; l++) {
+        int64_t q0 = 0;
+        for (size_t p = 0; p < acc[(size_t)l].size() && !rc; p++) {
+            rc = gs_scatter_cubes(acc[(size_t)l][p], accm[(size_t)l][p], accn[(size_t)l][p], q0,
+                                  d_shift + (size_t)l * G, d_outs, d_cap, d_status, st);
+            q0 += accn[(size_t)l][p];
+        }
+    }
+    if (!rc) rc = check_status(d_status, st, "batch cubes");
+    const int t1 = T.mark();
+    unsigned long long h[32];
+    cudaError_t e = cudaMemcpyAsync(h, d_cnt, sizeof(h), cudaMemcpyDeviceToHost, st);
+    if (e == cudaSuccess) e = gs_sync(st);
+    if (!rc && e != cudaSuccess) rc = gs_fail_cuda(e, "batch levels", __FILE__, __LINE__);
+    if (rc) { drop_outs(); return rc; }
+    gst.pair_terms = (int64_t)h[8];
+    gst.atom_octets = (int64_t)h[24];
+    gst.recheck_cubes = (int64_t)h[13];
+    gst.recheck_bounds = (int64_t)h[15];
+    gst.recheck_precision = (int64_t)h[16];
+    gst.recheck_zero = (int64_t)h[17];
+    gst.recheck_rank = (int64_t)h[20];
+    gst.estimate_fast_cubes = (int64_t)h[25];
+    {
+        unsigned bits = (unsigned)(h[18] & 0xffffffffull);
+        float r;
+        memcpy(&r, &bits, sizeof(r));
+        gst.mixed_err_ratio = r;
+        bits = (unsigned)(h[19] & 0xffffffffull);
+        memcpy(&r, &bits, sizeof(r));
+        gst.mixed_band_ratio = r;
+    }
+    gst.ms_levels = T.ms(t0, t1);
+    for (int g = 0; g < G; g++) {
+        PreMol &q = pm[(size_t)mols[(size_t)g]];
+        q.lv = gst;
+        for (int l = 0; l < L; l++) {
+            const int64_t *m = &molcnt[((size_t)l * G + (size_t)g) * 5];
+            q.lv.examined[l] = m[0]; q.lv.discarded[l] = m[1]; q.lv.accepted[l] = m[2];
+            q.lv.forced[l] = m[3]; q.lv.split[l] = m[4];
+        }
+        q.cubes = outs[(size_t)g];
+        q.nc = ntot[(size_t)g];
+        q.mismatches = (int64_t)h[14];
+    }
+    return GS_OK;
+}
+
+// one host thread per worker, each with its own stream, runs whole
+// single-molecule meshes, largest molecules first
+static int batch_threads(const double *atoms, const double *radii, const int64_t *offsets, int64_t n_mols,
+                         const double *D, double c, double precision, int max_depth, const gs_options &base,
+                         int n_workers, gs_mesh *out, gs_stats *stats, std::vector<PreMol> *pm)
+{
     int dev = 0;
     GS_CHECK(cudaGetDevice(&dev));
-    // largest molecules first, taken by the workers as they free up
     std::vector<int64_t> order((size_t)n_mols);
     for (int64_t m = 0; m < n_mols; m++) order[(size_t)m] = m;
     std::stable_sort(order.begin(), order.end(), [&](int64_t a, int64_t b) {
+        if (pm) return (*pm)[(size_t)a].nc > (*pm)[(size_t)b].nc;
         return offsets[a + 1] - offsets[a] > offsets[b + 1] - offsets[b];
     });
     std::atomic<int64_t> next{0};
@@ -1029,9 +1312,8 @@ extern "C" int mesh_gaussian_surface_batch(const double *atoms, const double *ra
     int64_t first_mol = -1;
     std::string first_msg;
     auto worker = [&]() {
-        if (cudaSetDevice(dev) != cudaSuccess) return;
         cudaStream_t st = nullptr;
-        if (cudaStreamCreateWithFlags(&st, cudaStreamNonBlocking) != cudaSuccess) {
+        if (cudaSetDevice(dev) != cudaSuccess || cudaStreamCreateWithFlags(&st, cudaStreamNonBlocking) != cudaSuccess) {
             std::lock_guard<std::mutex> lk(mu);
             if (!first_rc) { first_rc = GS_ERR_CUDA; first_msg = "stream creation failed"; }
             return;
@@ -1043,7 +1325,14 @@ extern "C" int mesh_gaussian_surface_batch(const double *atoms, const double *ra
             gs_options o = base;
             o.cuda_stream = st;
             o.stats = stats ? &stats[m] : nullptr;
-            int r = mesh_impl(atoms + 3 * o0, radii + o0, n, D[m], c, precision, max_depth, o, &out[m], st);
+            int r;
+            if (pm) {
+                r = mesh_impl(atoms + 3 * o0, radii + o0, n, D[m], c, precision, max_depth, o, &out[m], st, nullptr,
+                              nullptr, (int64_t)1 << 21, nullptr, &(*pm)[(size_t)m]);
+                (*pm)[(size_t)m].cubes = nullptr;   // handed over
+            } else {
+                r = mesh_with_retry(atoms + 3 * o0, radii + o0, n, D[m], c, precision, max_depth, o, &out[m], st);
+            }
             cudaError_t e = gs_sync(st);
             if (!r && e != cudaSuccess) r = gs_fail_cuda(e, "stream", __FILE__, __LINE__);
             if (r) {
@@ -1059,11 +1348,193 @@ extern "C" int mesh_gaussian_surface_batch(const double *atoms, const double *ra
     for (int w = 1; w < nw; w++) pool.emplace_back(worker);
     worker();
     for (auto &th : pool) th.join();
-    if (first_rc) {
-        for (int64_t m = 0; m < n_mols; m++) mesh_free(&out[m]);
-        return gs_fail(first_rc, "molecule %lld: %s", (long long)first_mol, first_msg.c_str());
-    }
+    if (first_rc) return gs_fail(first_rc, "molecule %lld: %s", (long long)first_mol, first_msg.c_str());
     return GS_OK;
+}
+
+// shared level loops, pipelined: one host thread per group of molecules
+// with equal D prepares them (atoms uploaded, cell list) and runs the
+// group's level loop on its own stream, then hands the molecules to the
+// workers, which finish each mesh (conformity, lattice, field,
+// triangulation, weld) on their own streams, largest first.  A group's
+// meshes are finished while the next group's levels run.
+static int batch_shared(const double *atoms, const double *radii, const int64_t *offsets, int64_t n_mols,
+                        const double *D, double c, double precision, int max_depth, const gs_options &base,
+                        int n_workers, gs_mesh *out, gs_stats *stats)
+{
+    // groups of equal D, in order of first appearance
+    std::vector<std::vector<int64_t>> groups;
+    std::vector<int> group_of((size_t)n_mols);
+    {
+        std::vector<double> keys;
+        for (int64_t m = 0; m < n_mols; m++) {
+            size_t k = 0;
+            while (k < keys.size() && keys[k] != D[m]) k++;
+            if (k == keys.size()) { keys.push_back(D[m]); groups.emplace_back(); }
+            groups[k].push_back(m);
+            group_of[(size_t)m] = (int)k;
+        }
+    }
+    const int NG = (int)groups.size();
+    int dev = 0;
+    GS_CHECK(cudaGetDevice(&dev));
+    std::vector<cudaStream_t> gstream((size_t)NG, nullptr);
+    for (int k = 0; k < NG; k++) {
+        cudaError_t e = cudaStreamCreateWithFlags(&gstream[(size_t)k], cudaStreamNonBlocking);
+        if (e != cudaSuccess) {
+            for (int j = 0; j < k; j++) cudaStreamDestroy(gstream[(size_t)j]);
+            return gs_fail_cuda(e, "stream", __FILE__, __LINE__);
+        }
+    }
+    std::vector<PreMol> pm((size_t)n_mols);
+    std::vector<std::vector<std::unique_ptr<DevBufs>>> bufs((size_t)NG);
+    std::mutex mu;
+    std::condition_variable cv;
+    std::vector<int64_t> ready;
+    int groups_left = NG;
+    bool failed = false;
+    int first_rc = 0;
+    int64_t first_mol = -1;
+    std::string first_msg;
+    auto fail = [&](int r, int64_t m) {
+        std::lock_guard<std::mutex> lk(mu);
+        if (!first_rc) { first_rc = r; first_mol = m; first_msg = gs_last_error(); }
+        failed = true;
+        cv.notify_all();
+    };
+    auto group_job = [&](int k) {
+        cudaStream_t st = gstream[(size_t)k];
+        int rc = cudaSetDevice(dev) == cudaSuccess ? GS_OK : gs_fail(GS_ERR_CUDA, "cudaSetDevice failed");
+        int64_t bad = -1;
+        {
+            DevBufs B(st);
+            unsigned *d_status = nullptr;
+            if (!rc) rc = B.get(&d_status, 1);
+            if (!rc) {
+                cudaError_t e = cudaMemsetAsync(d_status, 0, sizeof(unsigned), st);
+                if (e != cudaSuccess) rc = gs_fail_cuda(e, "status", __FILE__, __LINE__);
+            }
+            Timer T(st);
+            for (int64_t m : groups[(size_t)k]) {
+                if (rc) break;
+                const int64_t o0 = offsets[m], n = offsets[m + 1] - o0;
+                bufs[(size_t)k].emplace_back(new DevBufs(st));
+                NvtxRange nr("gs: batch prepare");
+                rc = prepare(atoms + 3 * o0, radii + o0, n, D[m], c, base.cutoff_rel, precision, base.min_edge,
+                             max_depth, *bufs[(size_t)k].back(), d_status, &pm[(size_t)m].PR, nullptr, T);
+                if (!rc) {
+                    pm[(size_t)m].PR.P.order = base.decision_order;
+                    pm[(size_t)m].PR.P.norm = base.precision_norm;
+                    if (base.precision_mode == GS_PREC_MIXED) rc = check_fp32_range(pm[(size_t)m].PR.P);
+                }
+                if (rc) bad = m;
+            }
+        }
+        if (!rc) {
+            bool retry = false;
+            rc = group_levels(groups[(size_t)k], pm, base, max_depth, st, (int64_t)1 << 21, &retry);
+            if (rc && retry) {
+                cudaGetLastError();
+                rc = group_levels(groups[(size_t)k], pm, base, max_depth, st, (int64_t)1 << 18, nullptr);
+                if (!rc)
+                    for (int64_t m : groups[(size_t)k]) pm[(size_t)m].lv.retries = 1;
+            }
+        }
+        if (!rc) {
+            cudaError_t e = gs_sync(st);
+            if (e != cudaSuccess) rc = gs_fail_cuda(e, "batch levels", __FILE__, __LINE__);
+        }
+        if (rc) { fail(rc, bad); }
+        std::lock_guard<std::mutex> lk(mu);
+        if (!rc) ready.insert(ready.end(), groups[(size_t)k].begin(), groups[(size_t)k].end());
+        groups_left--;
+        cv.notify_all();
+    };
+    auto worker = [&]() {
+        cudaStream_t st = nullptr;
+        if (cudaSetDevice(dev) != cudaSuccess || cudaStreamCreateWithFlags(&st, cudaStreamNonBlocking) != cudaSuccess) {
+            fail(gs_fail(GS_ERR_CUDA, "worker stream creation failed"), -1);
+            return;
+        }
+        for (;;) {
+            int64_t m = -1;
+            {
+                std::unique_lock<std::mutex> lk(mu);
+                cv.wait(lk, [&] { return failed || !ready.empty() || groups_left == 0; });
+                if (failed || ready.empty()) break;
+                // the largest mesh waiting
+                size_t best = 0;
+                for (size_t i = 1; i < ready.size(); i++)
+                    if (pm[(size_t)ready[i]].nc > pm[(size_t)ready[best]].nc) best = i;
+                m = ready[best];
+                ready.erase(ready.begin() + (std::ptrdiff_t)best);
+            }
+            const int64_t o0 = offsets[m], n = offsets[m + 1] - o0;
+            gs_options o = base;
+            o.cuda_stream = st;
+            o.stats = stats ? &stats[m] : nullptr;
+            int r = mesh_impl(atoms + 3 * o0, radii + o0, n, D[m], c, precision, max_depth, o, &out[m], st, nullptr,
+                              nullptr, (int64_t)1 << 21, nullptr, &pm[(size_t)m]);
+            pm[(size_t)m].cubes = nullptr;   // handed over
+            cudaError_t e = gs_sync(st);
+            if (!r && e != cudaSuccess) r = gs_fail_cuda(e, "stream", __FILE__, __LINE__);
+            if (r) fail(r, m);
+        }
+        cudaStreamDestroy(st);
+    };
+    int nw = n_workers < 1 ? 1 : n_workers;
+    if (nw > n_mols) nw = (int)n_mols;
+    {
+        std::vector<std::thread> pool;
+        for (int k = 0; k < NG; k++) pool.emplace_back(group_job, k);
+        for (int w = 0; w < nw; w++) pool.emplace_back(worker);
+        for (auto &th : pool) th.join();
+    }
+    // cubes not handed to a worker, then the prepared atoms, on the streams
+    // they were made on (every worker has waited for its own stream)
+    for (int64_t m = 0; m < n_mols; m++) gs_free(pm[(size_t)m].cubes, gstream[(size_t)group_of[(size_t)m]]);
+    bufs.clear();
+    cudaError_t e = cudaSuccess;
+    for (auto st : gstream) {
+        cudaError_t e2 = cudaStreamSynchronize(st);
+        if (e == cudaSuccess) e = e2;
+        cudaStreamDestroy(st);
+    }
+    if (first_rc) {
+        if (first_mol >= 0) return gs_fail(first_rc, "molecule %lld: %s", (long long)first_mol, first_msg.c_str());
+        return gs_fail(first_rc, "%s", first_msg.c_str());
+    }
+    if (e != cudaSuccess) return gs_fail_cuda(e, "stream", __FILE__, __LINE__);
+    return GS_OK;
+}
+
+extern "C" int mesh_gaussian_surface_batch(const double *atoms, const double *radii, const int64_t *offsets,
+                                           int64_t n_mols, const double *D, double c, double precision, int max_depth,
+                                           const gs_options *opt, int n_workers, gs_mesh *out, gs_stats *stats)
+{
+    if (!out || n_mols <= 0 || !offsets || !D) return gs_fail(GS_ERR_ARG, "need n_mols >= 1, offsets, D and out");
+    for (int64_t m = 0; m < n_mols; m++) memset(&out[m], 0, sizeof(gs_mesh));
+    gs_options base = opt ? *opt : gs_default_options();
+    if (offsets[0] != 0) return gs_fail(GS_ERR_ARG, "offsets[0] must be 0");
+    if (base.batch_mode != GS_BATCH_SHARED_LEVELS && base.batch_mode != GS_BATCH_THREADS)
+        return gs_fail(GS_ERR_ARG, "unknown batch mode");
+    for (int64_t m = 0; m < n_mols; m++) {
+        if (offsets[m + 1] <= offsets[m]) return gs_fail(GS_ERR_ARG, "molecule %lld is empty", (long long)m);
+        int rc = check_mesh_args(atoms, radii, offsets[m + 1] - offsets[m], D[m], c, precision, max_depth, base);
+        if (rc) return rc;
+    }
+    int rc = device_setup();
+    if (rc) return rc;
+    // re-expanded child tensors follow each molecule's own parents: no shared loop
+    const bool shared = base.batch_mode == GS_BATCH_SHARED_LEVELS && base.child_mode != GS_CHILD_REEXPAND;
+    if (stats)
+        for (int64_t m = 0; m < n_mols; m++) memset(&stats[m], 0, sizeof(gs_stats));
+    rc = shared ? batch_shared(atoms, radii, offsets, n_mols, D, c, precision, max_depth, base, n_workers, out, stats)
+                : batch_threads(atoms, radii, offsets, n_mols, D, c, precision, max_depth, base, n_workers, out, stats,
+                                nullptr);
+    if (rc)
+        for (int64_t m = 0; m < n_mols; m++) mesh_free(&out[m]);
+    return rc;
 }
 
 extern "C" int gs_mesh_backward(const double *atoms, const double *radii, int64_t n_atoms, double D, double c,

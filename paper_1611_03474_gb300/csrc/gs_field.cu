@@ -142,40 +142,53 @@ __global__ void __launch_bounds__(128) k_field_f32(GsProblem P, const uint64_t *
 // per-vertex walk and each row's range covers the vertex's own, so each
 // vertex sums the same terms in the same order, with the same membership
 // test and error bound as k_field_f32.
-#define FW_WARPS 8
-__global__ void __launch_bounds__(32 * FW_WARPS) k_field_f32w(GsProblem P, const uint64_t *__restrict__ vkeys, int64_t n,
-                                                              double *__restrict__ phi, float *__restrict__ err,
-                                                              unsigned long long *terms)
+//
+// Tile shape (template): WARPS warps per block, VPL vertices per lane (a
+// warp tile of 32 VPL consecutive vertices; lane l holds vertices l, l + 32,
+// ...).  A larger tile stages each candidate for more vertices but widens
+// the bounding box; the sums are the same for every shape (each vertex sees
+// its own atoms in the same order), so the shape is free to be tuned.
+template <int WARPS, int VPL>
+__global__ void __launch_bounds__(32 * WARPS) k_field_f32w(GsProblem P, const uint64_t *__restrict__ vkeys, int64_t n,
+                                                           double *__restrict__ phi, float *__restrict__ err,
+                                                           unsigned long long *terms)
 {
-    __shared__ float4 s_a[FW_WARPS][32];   // hx, hy, hz, fR2
-    __shared__ float4 s_b[FW_WARPS][32];   // lx, ly, lz, fr2
+    __shared__ float4 s_a[WARPS][32];   // hx, hy, hz, fR2
+    __shared__ float4 s_b[WARPS][32];   // lx, ly, lz, fr2
     const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
-    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    const bool valid = i < n;
-    float ph[3] = {0.f, 0.f, 0.f}, pl[3] = {0.f, 0.f, 0.f};
-    if (valid) {
-        double p[3];
-        point_of(P, vkeys, nullptr, i, p);
-        for (int a = 0; a < 3; a++) {
-            double rel = p[a] - P.origin[a];
-            ph[a] = (float)rel;
-            pl[a] = (float)(rel - (double)ph[a]);
+    const int64_t i0 = ((int64_t)blockIdx.x * WARPS + w) * (32 * VPL) + lane;
+    bool valid[VPL];
+    float ph[VPL][3], pl[VPL][3];
+    float lo[3] = {INFINITY, INFINITY, INFINITY}, hi[3] = {-INFINITY, -INFINITY, -INFINITY};
+#pragma unroll
+    for (int v = 0; v < VPL; v++) {
+        const int64_t i = i0 + 32 * v;
+        valid[v] = i < n;
+        for (int a = 0; a < 3; a++) ph[v][a] = pl[v][a] = 0.f;
+        if (valid[v]) {
+            double p[3];
+            point_of(P, vkeys, nullptr, i, p);
+            for (int a = 0; a < 3; a++) {
+                double rel = p[a] - P.origin[a];
+                ph[v][a] = (float)rel;
+                pl[v][a] = (float)(rel - (double)ph[v][a]);
+                lo[a] = fminf(lo[a], ph[v][a]);
+                hi[a] = fmaxf(hi[a], ph[v][a]);
+            }
         }
     }
     // the warp's bounding box
-    float lo[3], hi[3];
-    for (int a = 0; a < 3; a++) {
-        lo[a] = valid ? ph[a] : INFINITY;
-        hi[a] = valid ? ph[a] : -INFINITY;
+    for (int a = 0; a < 3; a++)
         for (int o = 16; o > 0; o >>= 1) {
             lo[a] = fminf(lo[a], __shfl_xor_sync(0xffffffffu, lo[a], o));
             hi[a] = fmaxf(hi[a], __shfl_xor_sync(0xffffffffu, hi[a], o));
         }
-    }
     if (!(lo[0] <= hi[0])) return;   // no vertex in this warp (uniform)
     const float nDl2e = (float)(-P.D * 1.4426950408889634);
     const float Df = (float)P.D;
-    float s = 0.f, comp = 0.f, eacc = 0.f;
+    float s[VPL], comp[VPL], eacc[VPL];
+#pragma unroll
+    for (int v = 0; v < VPL; v++) s[v] = comp[v] = eacc[v] = 0.f;
     unsigned long long cnt = 0;
     gs_warp_candidates(P, lo, hi, lane, [&](int k) {
         const unsigned have = __ballot_sync(0xffffffffu, k >= 0);
@@ -185,32 +198,54 @@ __global__ void __launch_bounds__(32 * FW_WARPS) k_field_f32w(GsProblem P, const
         }
         __syncwarp();
         const int m = __popc(have);
-        if (valid) {
+#pragma unroll
+        for (int v = 0; v < VPL; v++) {
+            if (!valid[v]) continue;
             for (int j = 0; j < m; j++) {
                 const float4 a = s_a[w][j], b = s_b[w][j];
-                const float dx = (ph[0] - a.x) + (pl[0] - b.x);
-                const float dy = (ph[1] - a.y) + (pl[1] - b.y);
-                const float dz = (ph[2] - a.z) + (pl[2] - b.z);
+                const float dx = (ph[v][0] - a.x) + (pl[v][0] - b.x);
+                const float dy = (ph[v][1] - a.y) + (pl[v][1] - b.y);
+                const float dz = (ph[v][2] - a.z) + (pl[v][2] - b.z);
                 const float d2 = dx * dx + dy * dy + dz * dz;
                 if (d2 > a.w) continue;
                 const float t = gs_ex2(nDl2e * (d2 - b.w));
-                const float y = t - comp;
-                const float u = s + y;
-                comp = (u - s) - y;
-                s = u;
-                eacc = fmaf(t, 3e-7f + 2.5e-7f * Df * (d2 + b.w), eacc);
+                const float y = t - comp[v];
+                const float u = s[v] + y;
+                comp[v] = (u - s[v]) - y;
+                s[v] = u;
+                eacc[v] = fmaf(t, 3e-7f + 2.5e-7f * Df * (d2 + b.w), eacc[v]);
                 cnt++;
             }
         }
         __syncwarp();
     });
-    if (valid) {
-        phi[i] = (double)s - (double)comp;
-        if (err) err[i] = eacc + 2.4e-7f * s + 4e-8f * (float)P.c;
+#pragma unroll
+    for (int v = 0; v < VPL; v++) {
+        if (!valid[v]) continue;
+        const int64_t i = i0 + 32 * v;
+        phi[i] = (double)s[v] - (double)comp[v];
+        if (err) err[i] = eacc[v] + 2.4e-7f * s[v] + 4e-8f * (float)P.c;
     }
     if (terms) {
         for (int o = 16; o > 0; o >>= 1) cnt += __shfl_xor_sync(0xffffffffu, cnt, o);
         if (lane == 0 && cnt) atomicAdd(terms, cnt);
+    }
+}
+
+// the tile shapes the tuner chooses from: (warps per block, vertices per lane)
+static const int FW_SHAPES[][2] = {{8, 1}, {4, 1}, {8, 2}, {4, 2}};
+#define FW_NSHAPES 4
+
+static void launch_field_f32w(int shape, const GsProblem &P, const uint64_t *d_vkeys, int64_t n, double *d_phi,
+                              float *d_err, unsigned long long *d_terms, cudaStream_t st)
+{
+    const int W = FW_SHAPES[shape][0], V = FW_SHAPES[shape][1];
+    const unsigned grid = (unsigned)((n + 32 * W * V - 1) / (32 * W * V));
+    switch (shape) {
+    case 0: GS_LAUNCH((k_field_f32w<8, 1>), grid, 256, 0, st)(P, d_vkeys, n, d_phi, d_err, d_terms); break;
+    case 1: GS_LAUNCH((k_field_f32w<4, 1>), grid, 128, 0, st)(P, d_vkeys, n, d_phi, d_err, d_terms); break;
+    case 2: GS_LAUNCH((k_field_f32w<8, 2>), grid, 256, 0, st)(P, d_vkeys, n, d_phi, d_err, d_terms); break;
+    default: GS_LAUNCH((k_field_f32w<4, 2>), grid, 128, 0, st)(P, d_vkeys, n, d_phi, d_err, d_terms); break;
     }
 }
 
@@ -232,10 +267,13 @@ int gs_field_f32(const GsProblem &P, const uint64_t *d_vkeys, const double *d_po
                  double *d_grad, float *d_err, unsigned long long *d_terms, cudaStream_t st)
 {
     if (n <= 0) return GS_OK;
-    if (d_vkeys && !d_grad)   // lattice vertices: the warp-cooperative form
-        GS_LAUNCH(k_field_f32w, (unsigned)((n + 32 * FW_WARPS - 1) / (32 * FW_WARPS)), 32 * FW_WARPS, 0, st)(
-            P, d_vkeys, n, d_phi, d_err, d_terms);
-    else
+    if (d_vkeys && !d_grad) {   // lattice vertices: the warp-cooperative form, tile shape tuned
+        int rc = gs_tune_run("k_field_f32w", n, FW_NSHAPES, st, [&](int shape, unsigned long long *scratch) {
+            launch_field_f32w(shape, P, d_vkeys, n, d_phi, d_err, scratch ? (d_terms ? scratch : nullptr) : d_terms,
+                              st);
+        });
+        if (rc) return rc;
+    } else
         GS_LAUNCH(k_field_f32, (unsigned)((n + 127) / 128), 128, 0, st)(P, d_vkeys, d_points, n, d_phi, d_grad, d_err,
                                                                        d_terms);
     GS_CHECK(cudaGetLastError());

@@ -2,6 +2,8 @@
 #pragma once
 #include "gs_internal.cuh"
 
+#include <functional>
+
 // gs_guard.cu: host waits with a deadline (cudaErrorTimeout after it) and
 // host-side fault injection (environment GS_FAULT); gs_guard_begin at each
 // API call
@@ -83,6 +85,16 @@ int gs_level_mixed(const GsProblem &P, int level, const uint64_t *d_parents, int
                    unsigned long long *d_why = nullptr, const GsProblem *d_probs = nullptr,
                    const int32_t *d_mol = nullptr, const uint8_t *d_vmask = nullptr);
 int gs_root_blocks(const GsProblem &P, uint64_t **d_keys, int64_t *n, cudaStream_t st);
+// batched form: the root blocks of G molecules (probs: host records) with
+// their valid-child masks and molecule indices; per-molecule decision counts
+// (d_cnt [G][5], accumulated); accepted cubes of one compaction part to
+// their molecules' arrays (outs[g][j + q0 + shift[g]], g = mol[j])
+int gs_root_blocks_batch(const GsProblem *probs, int G, uint64_t **d_keys, uint8_t **d_vmask, int32_t **d_mol,
+                         int64_t *n, cudaStream_t st);
+int gs_level_count_mol(const uint8_t *d_dec, int64_t n_cubes, const int32_t *d_mol, unsigned long long *d_cnt,
+                       cudaStream_t st);
+int gs_scatter_cubes(const uint64_t *d_acc, const int32_t *d_acc_mol, int64_t n, int64_t q0, const int64_t *d_shift,
+                     uint64_t *const *d_outs, const int64_t *d_cap, unsigned *d_status, cudaStream_t st);
 
 // gs_mesh.cu
 int gs_hash_make(GsHash *H, int64_t n, cudaStream_t st);
@@ -184,3 +196,9 @@ int gs_tri_marks(const TriCtx &X, const float *d_err, double tol_A, int64_t *d_m
 // counters: [0] cubes skipped for an inconsistency, [1] degenerate ears, [2] surface cubes
 int gs_triangulate(const TriCtx &X, uint64_t **d_tri_keys, int64_t *ntri_total, uint64_t **d_pt_keys,
                    double **d_pt_xyz, int64_t *npt_total, unsigned long long *d_counters, cudaStream_t st);
+
+// launch-shape autotuner (gs_tune.cu): launch(shape, scratch) launches the
+// kernel in one of n_choices shapes that compute the same result; scratch
+// (non-null during trials) replaces the launch's counters
+int gs_tune_run(const char *kernel, int64_t n, int n_choices, cudaStream_t st,
+                const std::function<void(int, unsigned long long *)> &launch);

@@ -17,6 +17,7 @@
 // thread per cube.
 #include <cmath>
 #include <cstdio>
+#include <vector>
 
 #include "gs_host.cuh"
 
@@ -1444,28 +1445,42 @@ int gs_accum_f32(const GsProblem &P, int level, const uint64_t *d_parents, const
     int gv = gq_variant(P.D, 0.5 * h, true);
     cudaEvent_t e0 = nullptr, e1 = nullptr;
     if (ms) { cudaEventCreate(&e0); cudaEventCreate(&e1); cudaEventRecord(e0, st); }
-    const unsigned grid = grid_for(n_oct, ACC_WARPS);
+    // grid shapes the tuner chooses from: up to 64, 16 or 4 blocks per SM
+    // (each warp takes every grid-th octet; the sums do not depend on it)
+    static const int64_t caps[3] = {152 * 64, 152 * 16, 152 * 4};
+    auto run = [&](int shape, unsigned long long *scratch) {
+        int64_t g = (n_oct + ACC_WARPS - 1) / ACC_WARPS;
+        if (g > caps[shape]) g = caps[shape];
+        const unsigned grid = (unsigned)(g < 1 ? 1 : g);
+        unsigned long long *pairs = scratch ? scratch : d_pairs;
+        unsigned long long *aoct = scratch ? (d_atom_octets ? scratch + 1 : nullptr) : d_atom_octets;
 #define GS_ACC32(V, N)                                                                                              \
     do {                                                                                                            \
         if (d_probs)                                                                                                \
             GS_LAUNCH((k_accum_f32<V, N, true>), grid, 32 * ACC_WARPS, 0, st)(P, level, d_parents, d_vmask, n_oct,  \
                                                                              (float)h, P.lat_exact_f32, d_A, d_err, \
-                                                                             d_pairs, d_atom_octets, d_probs,      \
-                                                                             d_mol);                               \
+                                                                             pairs, aoct, d_probs, d_mol);          \
         else                                                                                                        \
             GS_LAUNCH((k_accum_f32<V, N, false>), grid, 32 * ACC_WARPS, 0, st)(P, level, d_parents, d_vmask, n_oct, \
                                                                               (float)h, P.lat_exact_f32, d_A,      \
-                                                                              d_err, d_pairs, d_atom_octets,       \
-                                                                              nullptr, nullptr);                   \
+                                                                              d_err, pairs, aoct, nullptr, nullptr); \
     } while (0)
-    switch (gv) {
-    case 5: GS_ACC32(5, 5); break;
-    case 4: GS_ACC32(4, 6); break;
-    case 0: GS_ACC32(0, 8); break;
-    case 1: GS_ACC32(1, 12); break;
-    default: GS_ACC32(2, 16); break;
-    }
+        switch (gv) {
+        case 5: GS_ACC32(5, 5); break;
+        case 4: GS_ACC32(4, 6); break;
+        case 0: GS_ACC32(0, 8); break;
+        case 1: GS_ACC32(1, 12); break;
+        default: GS_ACC32(2, 16); break;
+        }
 #undef GS_ACC32
+    };
+    char name[32];
+    snprintf(name, sizeof(name), "k_accum_f32<%d>", gv);
+    int rc = gs_tune_run(name, n_oct, 3, st, run);
+    if (rc) {
+        if (ms) { cudaEventDestroy(e0); cudaEventDestroy(e1); }
+        return rc;
+    }
     if (ms) {
         cudaEventRecord(e1, st);
         cudaEventSynchronize(e1);
@@ -1919,8 +1934,9 @@ int gs_level_mixed(const GsProblem &P, int level, const uint64_t *d_parents, int
         rc = gs_alloc((void **)&A64, sizeof(double) * 64 * 8 * (size_t)n_oct, st);
         if (!rc) rc = gs_alloc((void **)&b64, sizeof(double) * 6 * 8 * (size_t)n_oct, st);
         if (!rc) rc = gs_alloc((void **)&d64, 8 * (size_t)n_oct, st);
-        if (!rc) rc = gs_accum_f64(P, level, d_parents, nullptr, n_oct, A64, nullptr, d_status, st, nullptr);
-        if (!rc) rc = gs_estimate_f64(P, level, A64, n_oct * 8, d_parents, nullptr, d64, b64, st);
+        if (!rc)
+            rc = gs_accum_f64(P, level, d_parents, d_vmask, n_oct, A64, nullptr, d_status, st, nullptr, d_probs, d_mol);
+        if (!rc) rc = gs_estimate_f64(P, level, A64, n_oct * 8, d_parents, d_vmask, d64, b64, st);
         if (!rc) {
             unsigned nb = (unsigned)((n_oct * 8 + 255) / 256);
             GS_LAUNCH(k_count_mismatch, nb, 256, 0, st)(d_dec, d64, n_oct * 8, d_mism);
@@ -1934,6 +1950,140 @@ int gs_level_mixed(const GsProblem &P, int level, const uint64_t *d_parents, int
     gs_free(dbg, st);
     gs_free(flag, st);
     if (rc) return rc;
+    GS_CHECK(cudaGetLastError());
+    return GS_OK;
+}
+
+// ================================================================ batched form
+// Several molecules share one level loop: the octets of all molecules sit in
+// one array, molecule by molecule, with the molecule's index (its row in a
+// device table of problem records) beside each octet.  Compaction is stable,
+// so every level's arrays stay grouped by molecule and each molecule's
+// octets keep the order a single-molecule run gives them.
+
+// root blocks of every molecule: keys in the molecule's own lattice, the
+// valid children (inside the molecule's root grid) and the molecule index.
+// tab[g] = {first octet, bx, by, nroot x, nroot y, nroot z}; base[G] = total
+__global__ void k_root_blocks_batch(const int64_t *__restrict__ tab, int G, int64_t n, uint64_t *__restrict__ keys,
+                                    uint8_t *__restrict__ vmask, int32_t *__restrict__ mol)
+{
+    const int64_t o = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (o >= n) return;
+    int lo = 0, hi = G - 1;   // last g with tab[g].first <= o
+    while (lo < hi) {
+        const int mid = (lo + hi + 1) >> 1;
+        if (tab[6 * mid] <= o) lo = mid;
+        else hi = mid - 1;
+    }
+    const int64_t *t = tab + 6 * lo;
+    const int64_t r = o - t[0], bx = t[1], by = t[2];
+    const int64_t I = r % bx, J = (r / bx) % by, K = r / (bx * by);
+    uint8_t m = 0;
+    for (int c = 0; c < 8; c++) {
+        const int64_t x = 2 * I + (c & 1), y = 2 * J + ((c >> 1) & 1), z = 2 * K + (c >> 2);
+        if (x < t[3] && y < t[4] && z < t[5]) m |= (uint8_t)(1u << c);
+    }
+    keys[o] = gk_make(I, J, K, GT_CUBE, 0);
+    vmask[o] = m;
+    mol[o] = lo;
+}
+
+int gs_root_blocks_batch(const GsProblem *probs, int G, uint64_t **d_keys, uint8_t **d_vmask, int32_t **d_mol,
+                         int64_t *n, cudaStream_t st)
+{
+    *d_keys = nullptr; *d_vmask = nullptr; *d_mol = nullptr; *n = 0;
+    std::vector<int64_t> tab(6 * (size_t)G);
+    int64_t total = 0;
+    for (int g = 0; g < G; g++) {
+        const int64_t bx = (probs[g].nroot[0] + 1) / 2, by = (probs[g].nroot[1] + 1) / 2,
+                      bz = (probs[g].nroot[2] + 1) / 2;
+        int64_t *t = &tab[6 * (size_t)g];
+        t[0] = total; t[1] = bx; t[2] = by;
+        t[3] = probs[g].nroot[0]; t[4] = probs[g].nroot[1]; t[5] = probs[g].nroot[2];
+        total += bx * by * bz;
+    }
+    int64_t *d_tab = nullptr;
+    int rc = gs_alloc((void **)&d_tab, sizeof(int64_t) * tab.size(), st);
+    if (!rc) rc = gs_alloc((void **)d_keys, sizeof(uint64_t) * (size_t)total, st);
+    if (!rc) rc = gs_alloc((void **)d_vmask, (size_t)total, st);
+    if (!rc) rc = gs_alloc((void **)d_mol, sizeof(int32_t) * (size_t)total, st);
+    if (!rc) {
+        cudaError_t e = cudaMemcpyAsync(d_tab, tab.data(), sizeof(int64_t) * tab.size(), cudaMemcpyHostToDevice, st);
+        if (e != cudaSuccess) rc = gs_fail_cuda(e, "root table", __FILE__, __LINE__);
+    }
+    if (!rc) GS_LAUNCH(k_root_blocks_batch, (unsigned)((total + 255) / 256), 256, 0, st)(d_tab, G, total, *d_keys,
+                                                                                     *d_vmask, *d_mol);
+    gs_free(d_tab, st);
+    if (rc) {
+        gs_free(*d_keys, st); gs_free(*d_vmask, st); gs_free(*d_mol, st);
+        *d_keys = nullptr; *d_vmask = nullptr; *d_mol = nullptr;
+        return rc;
+    }
+    GS_CHECK(cudaGetLastError());
+    *n = total;
+    return GS_OK;
+}
+
+// per-molecule decision counts: cnt[g * 5 + k] (examined, discarded,
+// accepted, forced, split).  The cubes are grouped by molecule, so the lanes
+// of a warp mostly share one (molecule, decision) pair and one atomic per
+// pair and warp suffices.
+__global__ void __launch_bounds__(256) k_level_count_mol(const uint8_t *__restrict__ dec, int64_t n,
+                                                         const int32_t *__restrict__ mol,
+                                                         unsigned long long *__restrict__ cnt)
+{
+    const int64_t q = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    const unsigned full = 0xffffffffu;
+    unsigned d = q < n ? dec[q] : DEC_INVALID;
+    const int g = q < n ? mol[q >> 3] : 0;
+    // slot 0 (examined) for every valid cube, then the decision's own slot
+    const int k = d == DEC_DISCARD ? 1 : d == DEC_ACCEPT ? 2 : d == DEC_FORCED ? 3 : d == DEC_SPLIT ? 4 : -1;
+    const unsigned key0 = d != DEC_INVALID ? (unsigned)g * 8u : 0xFFFFFFFFu;
+    const unsigned p0 = __match_any_sync(full, key0);
+    if (key0 != 0xFFFFFFFFu && (threadIdx.x & 31) == __ffs(p0) - 1)
+        atomicAdd(&cnt[(int64_t)g * 5], (unsigned long long)__popc(p0));
+    const unsigned key1 = k >= 0 ? (unsigned)g * 8u + (unsigned)k : 0xFFFFFFFFu;
+    const unsigned p1 = __match_any_sync(full, key1);
+    if (key1 != 0xFFFFFFFFu && (threadIdx.x & 31) == __ffs(p1) - 1)
+        atomicAdd(&cnt[(int64_t)g * 5 + k], (unsigned long long)__popc(p1));
+}
+
+int gs_level_count_mol(const uint8_t *d_dec, int64_t n_cubes, const int32_t *d_mol, unsigned long long *d_cnt,
+                       cudaStream_t st)
+{
+    if (n_cubes <= 0) return GS_OK;
+    GS_LAUNCH(k_level_count_mol, (unsigned)((n_cubes + 255) / 256), 256, 0, st)(d_dec, n_cubes, d_mol, d_cnt);
+    GS_CHECK(cudaGetLastError());
+    return GS_OK;
+}
+
+// accepted cubes of one compaction part to their molecules' arrays: cube j
+// of the part (molecule g) goes to outs[g][j + q0 + shift[g]], q0 being the
+// part's first slot among its level's accepted cubes and shift[g] the
+// molecule's count over the earlier levels minus its first slot in this one
+// (cap[g]: the size of molecule g's array; a slot outside it, which only
+// cubes out of molecule order could give, sets GS_ST_CAPACITY instead)
+__global__ void k_scatter_cubes(const uint64_t *__restrict__ acc, const int32_t *__restrict__ acc_mol, int64_t n,
+                                int64_t q0, const int64_t *__restrict__ shift, uint64_t *const *__restrict__ outs,
+                                const int64_t *__restrict__ cap, unsigned *status)
+{
+    const int64_t j = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (j >= n) return;
+    const int g = acc_mol[j];
+    const int64_t d = j + q0 + shift[g];
+    if (d < 0 || d >= cap[g]) {
+        atomicOr(status, GS_ST_CAPACITY);
+        return;
+    }
+    outs[g][d] = acc[j];
+}
+
+int gs_scatter_cubes(const uint64_t *d_acc, const int32_t *d_acc_mol, int64_t n, int64_t q0, const int64_t *d_shift,
+                     uint64_t *const *d_outs, const int64_t *d_cap, unsigned *d_status, cudaStream_t st)
+{
+    if (n <= 0) return GS_OK;
+    GS_LAUNCH(k_scatter_cubes, (unsigned)((n + 255) / 256), 256, 0, st)(d_acc, d_acc_mol, n, q0, d_shift, d_outs,
+                                                                        d_cap, d_status);
     GS_CHECK(cudaGetLastError());
     return GS_OK;
 }
