@@ -449,7 +449,10 @@ def main():
                     "n_cubes_final": sa["n_cubes_final"], "n_triangles": sa["n_triangles"],
                     "constrained_vertices": sa["constrained_vertices"], "agreement_splits": sa["agreement_splits"],
                     "conformity_splits": sa["conformity_splits"], "mixed_cubes": sa["mixed_cubes"],
-                    "loop_errors": sa["loop_errors"], "stage_ms": {k: sa[k] for k in ("ms_levels", "ms_conformity",
+                    "loop_errors": sa["loop_errors"], "recheck_vertices": sa["recheck_vertices"],
+                    "n_lattice_vertices": sa["n_lattice_vertices"], "vertex_terms": sa["vertex_terms"],
+                    "vertex_mark_cubes": sa["vertex_mark_cubes"],
+                    "stage_ms": {k: sa[k] for k in ("ms_levels", "ms_conformity",
                                                                                       "ms_field", "ms_triangulate",
                                                                                       "ms_weld")}}
 
@@ -561,7 +564,11 @@ def main():
                 "d2h_bytes_per_step": int(nbytes_out), "runs": len(e2e_times), "warmup_runs": args.e2e_warmup,
                 "min_ms": float(np.min(e2e_times)), "max_ms": float(np.max(e2e_times)),
                 "copy_GBps_est": float(nbytes_out / ((e2e_ms - ms_per_mesh) * 1e-3) / 1e9)
-                if e2e_ms > ms_per_mesh else None, "link": link, "stage_ms_last": e2e_stage},
+                if e2e_ms > ms_per_mesh else None, "link": link, "stage_ms_last": e2e_stage,
+                "buffers_pinned": {"inputs": bool(xyz_h.is_pinned() and r_h.is_pinned()),
+                                   "outputs": bool(all(o.is_pinned() for o in outs)),
+                                   # 1: the library sees page-locked memory mapped into the device
+                                   "library_kind": [gs.memory_kind(b) for b in (xyz_h,) + outs]}},
         "gpu_launches": int(st["n_kernel_launches"]),
         # launch shapes the autotuner chose in this process (kernel, size class, choice, trial ms per shape)
         "autotune": gs.autotune_report(),

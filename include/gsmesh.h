@@ -137,6 +137,12 @@ typedef struct {
     int64_t mixed_cubes;          /* final cubes with a neighbour of another size across a face or an edge */
     int64_t retries;              /* 1 when the level loop ran out of device memory or of an internal table and
                                      the call was run again with smaller level chunks */
+    int64_t near_threshold[4];    /* decisions taken in FP64 whose margin was below 1e-10 relative: [0] bound
+                                     test, min(c-L, U-c) against |c|+|L|+|U|; [1] precision test, |precision -
+                                     sum|high|| against their sum; [2] a 99% rank rule, |sum_{i<=j} s_i - 0.99
+                                     sum s| against sum s; [3] lattice vertices with |value - c| < 1e-10 c.  Such
+                                     a decision may differ from an independent FP64 evaluation by rounding
+                                     alone (the oracle resolves them in quad precision) */
 } gs_stats;
 
 typedef struct {
@@ -278,6 +284,13 @@ const char *gs_last_error(void);
  */
 int64_t gs_autotune_report(char *buf, int64_t cap);
 void gs_autotune_reset(void);
+
+/* how the library sees a buffer: 0 device memory, 1 page-locked host memory
+ * mapped into the device (the library moves meshes into it with a copy
+ * kernel at the rate of the host link), 2 other host memory (pageable:
+ * cudaMemcpyAsync, staged by the runtime), -1 NULL.  A query only; no
+ * device work. */
+int gs_memory_kind(const void *p);
 
 /* sizeof of the ABI structs (0: gs_stats, 1: gs_options, 2: gs_mesh; else -1),
  * for bindings to verify their layouts */

@@ -11,6 +11,7 @@ orientation, single-valued pieces).
 """
 import ctypes
 import os
+import platform
 import subprocess
 
 import numpy as np
@@ -33,6 +34,8 @@ def build(force=False):
         return _LIB
     tmp = _LIB + ".tmp%d" % os.getpid()
     base = ["gcc", "-O2", "-ffp-contract=off", "-fno-fast-math", "-fPIC", "-shared", "-o", tmp, _SRC, "-lm"]
+    if platform.machine() in ("x86_64", "AMD64"):
+        base.append("-lquadmath")   # __float128 for the resolve mode (AArch64 has a binary128 long double)
     try:
         subprocess.check_call(base[:1] + ["-fopenmp"] + base[1:], stderr=subprocess.DEVNULL)
     except subprocess.CalledProcessError:
@@ -56,7 +59,9 @@ class Stats(ctypes.Structure):
                 ("n_cubes_surface", ctypes.c_int64), ("open_faces", ctypes.c_int64),
                 ("degenerate_ears", ctypes.c_int64), ("loop_errors", ctypes.c_int64),
                 ("min_margin", ctypes.c_double), ("constrained_vertices", ctypes.c_int64),
-                ("agreement_splits", ctypes.c_int64)]
+                ("agreement_splits", ctypes.c_int64), ("near", ctypes.c_int64 * 4),
+                ("resolved_cubes", ctypes.c_int64), ("resolved_vertices", ctypes.c_int64),
+                ("resolved_changed", ctypes.c_int64), ("vertex_sign_changed", ctypes.c_int64)]
 
 
 class MeshOut(ctypes.Structure):
@@ -112,6 +117,16 @@ def lib():
         L.or_mesh_grid.argtypes = [i64, i64, i64, p, d, ctypes.POINTER(MeshOut)]
         L.or_mesh_ex.argtypes = [i64, p, p, d, d, d, d, d, i32, i32, i32, i32, i32, ctypes.POINTER(MeshOut)]
         L.or_mesh_ex.restype = i32
+        L.or_mesh_ex2.argtypes = [i64, p, p, d, d, d, d, d, i32, i32, i32, i32, i32, i32, ctypes.POINTER(MeshOut)]
+        L.or_mesh_ex2.restype = i32
+        L.or_have_quad.restype = i32
+        if L.or_have_quad():
+            L.or_axis_coeffs_quad.argtypes = [d, d, d, d, p, p]
+            L.or_axis_coeffs_quad.restype = i32
+            L.or_field_quad.argtypes = [i64, p, p, d, d, d, i64, p, p, p]
+            L.or_field_quad.restype = i32
+            L.or_bounds_quad.argtypes = [p, p, p]
+            L.or_bounds_quad.restype = i32
         L.or_child_reexpand.argtypes = [p, i32, p]
         L.or_child_reexpand.restype = None
         L.or_mesh_grad.argtypes = [i64, p, p, d, d, d, d, d, i32, i64, p, p, p, p]
@@ -234,7 +249,9 @@ def _stats_dict(st, max_depth):
                 n_cubes_surface=int(st.n_cubes_surface), open_faces=int(st.open_faces),
                 degenerate_ears=int(st.degenerate_ears), loop_errors=int(st.loop_errors),
                 min_margin=float(st.min_margin), constrained_vertices=int(st.constrained_vertices),
-                agreement_splits=int(st.agreement_splits))
+                agreement_splits=int(st.agreement_splits), near=[int(st.near[k]) for k in range(4)],
+                resolved_cubes=int(st.resolved_cubes), resolved_vertices=int(st.resolved_vertices),
+                resolved_changed=int(st.resolved_changed), vertex_sign_changed=int(st.vertex_sign_changed))
 
 
 def _arr(ptr, n, dtype, shape=None):
@@ -253,19 +270,54 @@ def child_reexpand(A, c8):
     return B.reshape(4, 4, 4)
 
 
+def have_quad():
+    """Whether the oracle was built with a binary128 type (the resolve mode)."""
+    return bool(lib().or_have_quad())
+
+
+def axis_coeffs_quad(xi, a, b, D):
+    """axis_coeffs in quad precision, as (hi, lo) double pairs (value = hi + lo)."""
+    hi, lo = np.zeros(4), np.zeros(4)
+    lib().or_axis_coeffs_quad(xi, a, b, D, _ptr(hi), _ptr(lo))
+    return hi, lo
+
+
+def field_quad(xyz, r, D, c, pts, cutoff_rel=CUTOFF_REL):
+    """field in quad precision, as (hi, lo) double pairs."""
+    xyz, r, pts = _f64(xyz), _f64(r), _f64(pts).reshape(-1, 3)
+    hi, lo = np.zeros(len(pts)), np.zeros(len(pts))
+    e = lib().or_field_quad(len(r), _ptr(xyz), _ptr(r), D, c, cutoff_rel, len(pts), _ptr(pts), _ptr(hi), _ptr(lo))
+    if e:
+        raise ValueError("oracle status %d" % e)
+    return hi, lo
+
+
+def bounds_quad(A_hi, A_lo=None):
+    """(L, U, sum|R|, rank) of section 2.2.2 in quad precision for a tensor
+    given as hi + lo doubles."""
+    A_hi = _f64(A_hi, (64,))
+    A_lo = np.zeros(64) if A_lo is None else _f64(A_lo, (64,))
+    out = np.zeros(4)
+    lib().or_bounds_quad(_ptr(A_hi), _ptr(A_lo), _ptr(out))
+    return out
+
+
 def mesh(xyz, r, D, c, precision, min_edge, max_depth, cutoff_rel=CUTOFF_REL, child_mode=0, order=0, norm=0,
-         conform=0):
+         conform=0, resolve=False):
     """Whole path; returns dict(vertices, vkeys, triangles, cube_keys, pre_keys, stats, ...).
     child_mode 1: child tensors by re-expansion of the parent's polynomial;
     order 1: literal order of steps 2-3; norm 1/2: max |.| / Euclidean norm
     of the high-order coefficients in the precision test; conform 1: cubes
     sharing a face or an edge are split to one size (instead of constrained
-    vertex values with at most one level between them)."""
+    vertex values with at most one level between them).  stats["near"]
+    counts the decisions whose margin is below 1e-10 relative (bound test,
+    precision test, rank rule, vertex sign); resolve=True takes each of them
+    again in quad precision."""
     xyz, r = _f64(xyz), _f64(r)
     out = MeshOut()
     L = lib()
-    e = L.or_mesh_ex(len(r), _ptr(xyz), _ptr(r), D, c, cutoff_rel, precision, min_edge, max_depth, child_mode,
-                     order, norm, conform, ctypes.byref(out))
+    e = L.or_mesh_ex2(len(r), _ptr(xyz), _ptr(r), D, c, cutoff_rel, precision, min_edge, max_depth, child_mode,
+                      order, norm, conform, 1 if resolve else 0, ctypes.byref(out))
     if e:
         raise ValueError("oracle status %d" % e)
     try:

@@ -107,6 +107,7 @@ typedef struct {
     int norm;         /* size of the high-order coefficients: 0 sum of |.|, 1 max |.|, 2 sqrt of sum of squares */
     int conform;      /* mixed-size neighbours: 0 constrained vertex values with at most one level between
                          cubes that share a face or an edge; 1 equal sizes across every shared face and edge */
+    int resolve;      /* 1: decisions and vertex signs whose margin is in band are re-decided in quad precision */
 } oprob;
 
 /* Terms exp(-D(|x-xi|^2 - ri^2)) below cutoff_rel*c are dropped:
@@ -409,14 +410,20 @@ void or_cubic_bounds(const double *cf, double *lo, double *hi)
     *lo = a; *hi = b;
 }
 
-/* smallest j with sum_{i<=j} s_i >= 0.99 * sum s (eq SVD3); returns count */
-static int rank99(const double *s, int m)
+/* smallest j with sum_{i<=j} s_i >= 0.99 * sum s (eq SVD3); returns count.
+ * rel (nullable) is lowered to the smallest |sum_{i<=j} s_i - 0.99 sum s| /
+ * sum s over the rules evaluated (those up to the deciding one). */
+static int rank99_m(const double *s, int m, double *rel)
 {
     double tot = 0;
     for (int i = 0; i < m; i++) tot += s[i];
     double acc = 0;
     for (int j = 0; j < m; j++) {
         acc += s[j];
+        if (rel && tot > 0) {
+            double d = fabs(acc - 0.99 * tot) / tot;
+            if (d < *rel) *rel = d;
+        }
         if (acc >= 0.99 * tot) return j + 1;
     }
     return m;
@@ -431,7 +438,12 @@ static int rank99(const double *s, int m)
 /* out[4]=rank j  out[5]=sum of inner ranks                              */
 /* ================================================================== */
 
-void or_bounds(const double *A, double *out)
+static void or_bounds_r(const double *A, double *out, double *rank_rel);
+void or_bounds(const double *A, double *out) { or_bounds_r(A, out, NULL); }
+
+/* rank_rel (nullable): the smallest relative distance of a rank rule from
+ * its threshold, as rank99_m */
+static void or_bounds_r(const double *A, double *out, double *rank_rel)
 {
     double s[4], u[16], v[64];
     or_svd_rows(A, 4, 16, s, u, v);
@@ -445,7 +457,7 @@ void or_bounds(const double *A, double *out)
         out[0] = out[1] = out[2] = 0; out[3] = high; out[4] = 0; out[5] = 0;
         return;
     }
-    int jr = rank99(s, 4);
+    int jr = rank99_m(s, 4, rank_rel);
     double At[64];
     memset(At, 0, sizeof(At));
     double M = 0, m = 0;
@@ -455,7 +467,7 @@ void or_bounds(const double *A, double *out)
         for (int k = 0; k < 4; k++)
             for (int l = 0; l < 4; l++) Vi[4 * k + l] = v[16 * i + 4 * k + l];
         or_svd_rows(Vi, 4, 4, d, w, z);
-        int ji = rank99(d, 4);
+        int ji = rank99_m(d, 4, rank_rel);
         inner += ji;
         double Myz = 0, myz = 0;
         for (int k = 0; k < ji; k++) {
@@ -492,15 +504,20 @@ void or_bounds(const double *A, double *out)
 
 /* Decision (steps 1-3 of section 2.2, reading: bound test first, then the
  * trilinear-fit test, forced acceptance at max_depth). */
-int or_decide(const double *A, double c, double precision, int level, int max_depth, double *out6)
+static int or_decide_r(const double *A, double c, double precision, int level, int max_depth, double *out6,
+                       double *rank_rel)
 {
-    or_bounds(A, out6);
+    or_bounds_r(A, out6, rank_rel);
     double L = out6[0], U = out6[1];
     if (out6[4] == 0) return DEC_DISCARD; /* A == 0 */
     if (!(L <= c && c <= U)) return DEC_DISCARD;
     if (out6[3] <= precision) return DEC_ACCEPT;
     if (level >= max_depth) return DEC_FORCED;
     return DEC_SPLIT;
+}
+int or_decide(const double *A, double c, double precision, int level, int max_depth, double *out6)
+{
+    return or_decide_r(A, c, precision, level, max_depth, out6, NULL);
 }
 
 /* The alternative readings of section 2.2.3 and of steps 2-3 of section 2.2.
@@ -529,11 +546,11 @@ double or_high_norm(const double *A, int norm)
     return sum;
 }
 
-int or_decide_ex(const double *A, double c, double precision, int level, int max_depth, int order, int norm,
-                 double *out6)
+static int or_decide_ex_r(const double *A, double c, double precision, int level, int max_depth, int order,
+                          int norm, double *out6, double *rank_rel)
 {
-    if (order == 0 && norm == 0) return or_decide(A, c, precision, level, max_depth, out6);
-    or_bounds(A, out6);
+    if (order == 0 && norm == 0) return or_decide_r(A, c, precision, level, max_depth, out6, rank_rel);
+    or_bounds_r(A, out6, rank_rel);
     out6[3] = or_high_norm(A, norm);
     double L = out6[0], U = out6[1];
     int has_atoms = out6[4] != 0;
@@ -550,6 +567,11 @@ int or_decide_ex(const double *A, double c, double precision, int level, int max
     if (trilinear) return DEC_ACCEPT;
     if (level >= max_depth) return DEC_FORCED;
     return DEC_SPLIT;
+}
+int or_decide_ex(const double *A, double c, double precision, int level, int max_depth, int order, int norm,
+                 double *out6)
+{
+    return or_decide_ex_r(A, c, precision, level, max_depth, order, norm, out6, NULL);
 }
 
 /* ================================================================== */
@@ -573,6 +595,364 @@ static double phi_at(const oprob *P, const double *x, double *grad)
     if (grad) { grad[0] = g0; grad[1] = g1; grad[2] = g2; }
     return s;
 }
+
+/* ================================================================== */
+/* Quad-precision resolution (the decision-margin policy).  A decision   */
+/* or a vertex sign whose margin lies within 1e-10 of its threshold is   */
+/* taken again with every step in IEEE binary128 (113-bit significand):  */
+/* the Gauss-Legendre nodes, the 1-D coefficients with their C0          */
+/* correction, the tensor, the Jacobi SVDs, the cubic ranges, the 99%    */
+/* rank rules and the bounds of section 2.2.2; or the field sum of eq    */
+/* (Gaussian1) at the vertex.  The atoms taken are those of the FP64      */
+/* cutoff test (the truncation is part of the definition, not a          */
+/* rounding).  x86-64: __float128 (libquadmath); AArch64: long double.   */
+/* ================================================================== */
+#if defined(__x86_64__)
+#include <quadmath.h>
+typedef __float128 oq;
+#define QL(x) x##Q
+#define QEXP expq
+#define QSQRT sqrtq
+#define QFABS fabsq
+#define QCOS cosq
+#define OR_HAVE_QUAD 1
+#elif defined(__aarch64__) && (__LDBL_MANT_DIG__ == 113)
+typedef long double oq;
+#define QL(x) x##L
+#define QEXP expl
+#define QSQRT sqrtl
+#define QFABS fabsl
+#define QCOS cosl
+#define OR_HAVE_QUAD 1
+#else
+#define OR_HAVE_QUAD 0
+#endif
+
+#if OR_HAVE_QUAD
+static oq q_leg(int j, oq t)
+{
+    switch (j) {
+    case 0: return 1;
+    case 1: return t;
+    case 2: return (3 * t * t - 1) / 2;
+    default: return (5 * t * t * t - 3 * t) / 2;
+    }
+}
+
+/* nodes and weights of the q-point rule, Newton on P_q from the usual guesses */
+static void q_gauss_legendre(int q, oq *x, oq *w)
+{
+    const oq pi = (oq)QL(3.14159265358979323846264338327950288);
+    for (int i = 0; i < q; i++) {
+        oq t = QCOS(pi * ((oq)i + (oq)QL(0.75)) / ((oq)q + (oq)QL(0.5))), dp = 1;
+        for (int it = 0; it < 200; it++) {
+            oq p0 = 1, p1 = t;
+            for (int k = 2; k <= q; k++) {
+                oq p2 = ((2 * k - 1) * t * p1 - (k - 1) * p0) / k;
+                p0 = p1; p1 = p2;
+            }
+            dp = q * (t * p1 - p0) / (t * t - 1);
+            oq dt = p1 / dp;
+            t -= dt;
+            if (QFABS(dt) < (oq)QL(1e-33)) break;
+        }
+        x[i] = t;
+        w[i] = 2 / ((1 - t * t) * dp * dp);
+    }
+}
+
+/* or_axis_coeffs in quad: the projection of exp(-D (x - xi)^2) on [a, b]
+ * onto L_0..L_3 by the 24-point rule, then the C0 endpoint correction */
+static void q_axis_coeffs(const oq *gx, const oq *gw, oq xi, oq a, oq b, oq D, oq *out4)
+{
+    oq m = (a + b) / 2, hh = (b - a) / 2, al[4];
+    for (int j = 0; j < 4; j++) {
+        oq s = 0;
+        for (int k = 0; k < OR_Q; k++) {
+            oq d = (m + hh * gx[k]) - xi;
+            s += gw[k] * QEXP(-D * d * d) * q_leg(j, gx[k]);
+        }
+        al[j] = (oq)(2 * j + 1) / 2 * s;
+    }
+    oq fa = QEXP(-D * (a - xi) * (a - xi)), fb = QEXP(-D * (b - xi) * (b - xi));
+    oq eR = fb - (al[0] + al[1] + al[2] + al[3]), eL = fa - (al[0] - al[1] + al[2] - al[3]);
+    out4[0] = al[0];
+    out4[1] = al[1];
+    out4[2] = al[2] + (eR + eL) / 2;
+    out4[3] = al[3] + (eR - eL) / 2;
+}
+
+static void q_jacobi_rows(oq *M, int m, int n, oq *Q)
+{
+    for (int i = 0; i < m; i++)
+        for (int j = 0; j < m; j++) Q[i * m + j] = (i == j);
+    for (int sweep = 0; sweep < 120; sweep++) {
+        int rotated = 0;
+        for (int p = 0; p < m; p++)
+            for (int q = p + 1; q < m; q++) {
+                oq al = 0, be = 0, ga = 0;
+                for (int k = 0; k < n; k++) {
+                    al += M[p * n + k] * M[p * n + k];
+                    be += M[q * n + k] * M[q * n + k];
+                    ga += M[p * n + k] * M[q * n + k];
+                }
+                if (ga == 0 || QFABS(ga) <= (oq)QL(1e-32) * QSQRT(al * be)) continue;
+                rotated = 1;
+                oq zeta = (be - al) / (2 * ga);
+                oq t = (zeta >= 0 ? (oq)1 : (oq)-1) / (QFABS(zeta) + QSQRT(1 + zeta * zeta));
+                oq cs = 1 / QSQRT(1 + t * t), sn = cs * t;
+                for (int k = 0; k < n; k++) {
+                    oq mp = M[p * n + k], mq = M[q * n + k];
+                    M[p * n + k] = cs * mp - sn * mq;
+                    M[q * n + k] = sn * mp + cs * mq;
+                }
+                for (int k = 0; k < m; k++) {
+                    oq qp = Q[p * m + k], qq = Q[q * m + k];
+                    Q[p * m + k] = cs * qp - sn * qq;
+                    Q[q * m + k] = sn * qp + cs * qq;
+                }
+            }
+        if (!rotated) break;
+    }
+}
+
+static void q_svd_rows(const oq *X, int m, int n, oq *s, oq *u, oq *v)
+{
+    oq M[64], Q[16], sv[4];
+    int order[4];
+    memcpy(M, X, sizeof(oq) * (size_t)(m * n));
+    q_jacobi_rows(M, m, n, Q);
+    for (int p = 0; p < m; p++) {
+        oq s2 = 0;
+        for (int k = 0; k < n; k++) s2 += M[p * n + k] * M[p * n + k];
+        sv[p] = QSQRT(s2);
+        order[p] = p;
+    }
+    for (int i = 1; i < m; i++) {
+        int o = order[i], j = i - 1;
+        while (j >= 0 && sv[order[j]] < sv[o]) { order[j + 1] = order[j]; j--; }
+        order[j + 1] = o;
+    }
+    for (int i = 0; i < m; i++) {
+        int p = order[i];
+        s[i] = sv[p];
+        for (int k = 0; k < m; k++) u[i * m + k] = Q[p * m + k];
+        for (int k = 0; k < n; k++) v[i * n + k] = sv[p] > 0 ? M[p * n + k] / sv[p] : 0;
+    }
+}
+
+static void q_cubic_bounds(const oq *cf, oq *lo, oq *hi)
+{
+    oq c0 = cf[0], c1 = cf[1], c2 = cf[2], c3 = cf[3];
+    oq m0 = c0 - c2 / 2, m1 = c1 - 3 * c3 / 2, m2 = 3 * c2 / 2, m3 = 5 * c3 / 2;
+    oq vals[4], roots[2];
+    int nv = 0, nr = 0;
+    vals[nv++] = c0 + c1 + c2 + c3;
+    vals[nv++] = c0 - c1 + c2 - c3;
+    oq A2 = 3 * m3, B2 = 2 * m2, C2 = m1;
+    if (A2 == 0) {
+        if (B2 != 0) roots[nr++] = -C2 / B2;
+    } else {
+        oq disc = B2 * B2 - 4 * A2 * C2;
+        if (disc >= 0) {
+            oq sq = QSQRT(disc);
+            oq qq = -(B2 + (B2 >= 0 ? sq : -sq)) / 2;
+            if (qq != 0) { roots[nr++] = qq / A2; roots[nr++] = C2 / qq; }
+            else roots[nr++] = 0;
+        }
+    }
+    for (int i = 0; i < nr; i++) {
+        oq t = roots[i];
+        if (t > -1 && t < 1) vals[nv++] = m0 + t * (m1 + t * (m2 + t * m3));
+    }
+    oq a = vals[0], b = vals[0];
+    for (int i = 1; i < nv; i++) { if (vals[i] < a) a = vals[i]; if (vals[i] > b) b = vals[i]; }
+    *lo = a; *hi = b;
+}
+
+static int q_rank99(const oq *s, int m)
+{
+    oq tot = 0, acc = 0, thr;
+    for (int i = 0; i < m; i++) tot += s[i];
+    thr = (oq)QL(0.99) * tot;
+    for (int j = 0; j < m; j++) {
+        acc += s[j];
+        if (acc >= thr) return j + 1;
+    }
+    return m;
+}
+
+/* or_bounds in quad: out = L, U, sum|R|, rank */
+static void q_bounds(const oq *A, oq *out)
+{
+    oq s[4], u[16], v[64], At[64], Mx = 0, mn = 0;
+    q_svd_rows(A, 4, 16, s, u, v);
+    oq stot = s[0] + s[1] + s[2] + s[3];
+    if (stot == 0) { out[0] = out[1] = out[2] = out[3] = 0; return; }
+    int jr = q_rank99(s, 4);
+    for (int t = 0; t < 64; t++) At[t] = 0;
+    for (int i = 0; i < jr; i++) {
+        oq Vi[16], d[4], w[16], z[16], Myz = 0, myz = 0;
+        for (int t = 0; t < 16; t++) Vi[t] = v[16 * i + t];
+        q_svd_rows(Vi, 4, 4, d, w, z);
+        int ji = q_rank99(d, 4);
+        for (int k = 0; k < ji; k++) {
+            oq ly, hy, lz, hz;
+            q_cubic_bounds(w + 4 * k, &ly, &hy);
+            q_cubic_bounds(z + 4 * k, &lz, &hz);
+            oq p[4] = {hy * hz, hy * lz, ly * hz, ly * lz}, pmx = p[0], pmn = p[0];
+            for (int t = 1; t < 4; t++) { if (p[t] > pmx) pmx = p[t]; if (p[t] < pmn) pmn = p[t]; }
+            Myz += d[k] * pmx;
+            myz += d[k] * pmn;
+            for (int a = 0; a < 4; a++)
+                for (int b = 0; b < 4; b++)
+                    for (int cc = 0; cc < 4; cc++)
+                        At[16 * a + 4 * b + cc] += s[i] * u[4 * i + a] * d[k] * w[4 * k + b] * z[4 * k + cc];
+        }
+        oq lx, hx;
+        q_cubic_bounds(u + 4 * i, &lx, &hx);
+        oq p[4] = {hx * Myz, hx * myz, lx * Myz, lx * myz}, pmx = p[0], pmn = p[0];
+        for (int t = 1; t < 4; t++) { if (p[t] > pmx) pmx = p[t]; if (p[t] < pmn) pmn = p[t]; }
+        Mx += s[i] * pmx;
+        mn += s[i] * pmn;
+    }
+    oq sr = 0;
+    for (int t = 0; t < 64; t++) sr += QFABS(A[t] - At[t]);
+    out[0] = mn - sr;
+    out[1] = Mx + sr;
+    out[2] = sr;
+    out[3] = jr;
+}
+
+/* the tensor of cube [lo, hi] in quad (the atoms of the FP64 cutoff test) */
+static int64_t q_cube_tensor(const oprob *P, const double *lo, const double *hi, oq *A)
+{
+    oq gx[OR_Q], gw[OR_Q];
+    q_gauss_legendre(OR_Q, gx, gw);
+    for (int t = 0; t < 64; t++) A[t] = 0;
+    int64_t cnt = 0;
+    const oq D = P->D;
+    for (int64_t i = 0; i < P->n; i++) {
+        const double *x = P->xyz + 3 * i;
+        if (box_dist2(lo, hi, x) > P->R2[i]) continue;
+        cnt++;
+        oq ri = P->r[i], w = QEXP(D * ri * ri), ax[4], ay[4], az[4];
+        q_axis_coeffs(gx, gw, x[0], lo[0], hi[0], D, ax);
+        q_axis_coeffs(gx, gw, x[1], lo[1], hi[1], D, ay);
+        q_axis_coeffs(gx, gw, x[2], lo[2], hi[2], D, az);
+        for (int j = 0; j < 4; j++)
+            for (int k = 0; k < 4; k++)
+                for (int l = 0; l < 4; l++) A[16 * j + 4 * k + l] += w * ax[j] * ay[k] * az[l];
+    }
+    return cnt;
+}
+
+static int quad_decide(const oprob *P, const double *lo, const double *hi, int level, int *dec)
+{
+    oq A[64], b[4];
+    q_cube_tensor(P, lo, hi, A);
+    q_bounds(A, b);
+    oq high = 0, mx = 0, sq = 0;
+    for (int j = 0; j < 4; j++)
+        for (int k = 0; k < 4; k++)
+            for (int l = 0; l < 4; l++) {
+                if (j < 2 && k < 2 && l < 2) continue;
+                oq v = QFABS(A[16 * j + 4 * k + l]);
+                high += v;
+                if (v > mx) mx = v;
+                sq += v * v;
+            }
+    if (P->norm == 1) high = mx;
+    else if (P->norm == 2) high = QSQRT(sq);
+    const oq c = P->c, prec = P->precision;
+    const int straddles = b[0] <= c && c <= b[1], trilinear = high <= prec;
+    if (b[3] == 0) *dec = DEC_DISCARD;
+    else if (P->order == 1 && level > 0 && trilinear) *dec = DEC_ACCEPT;
+    else if (!straddles) *dec = DEC_DISCARD;
+    else if (P->order == 0 && trilinear) *dec = DEC_ACCEPT;
+    else if (level >= P->max_depth) *dec = DEC_FORCED;
+    else *dec = DEC_SPLIT;
+    return 0;
+}
+
+/* eq (Gaussian1) at x in quad, the atoms of the FP64 cutoff test */
+static int quad_phi(const oprob *P, const double *x, double *phi)
+{
+    oq s = 0;
+    const oq D = P->D;
+    for (int64_t i = 0; i < P->n; i++) {
+        const double *xi = P->xyz + 3 * i;
+        double dx = x[0] - xi[0], dy = x[1] - xi[1], dz = x[2] - xi[2];
+        if (dx * dx + dy * dy + dz * dz > P->R2[i]) continue;
+        oq qx = (oq)x[0] - (oq)xi[0], qy = (oq)x[1] - (oq)xi[1], qz = (oq)x[2] - (oq)xi[2], ri = P->r[i];
+        s += QEXP(-D * (qx * qx + qy * qy + qz * qz - ri * ri));
+    }
+    *phi = (double)s;
+    return 0;
+}
+
+/* pins of the quad path: the 1-D coefficients and the field as hi + lo
+ * pairs of doubles (value = hi + lo to ~1e-32 relative) */
+int or_axis_coeffs_quad(double xi, double a, double b, double D, double *hi4, double *lo4)
+{
+    oq gx[OR_Q], gw[OR_Q], o[4];
+    q_gauss_legendre(OR_Q, gx, gw);
+    q_axis_coeffs(gx, gw, xi, a, b, D, o);
+    for (int j = 0; j < 4; j++) {
+        hi4[j] = (double)o[j];
+        lo4[j] = (double)(o[j] - (oq)hi4[j]);
+    }
+    return OR_OK;
+}
+
+int or_field_quad(int64_t n, const double *xyz, const double *r, double D, double c, double cutoff_rel,
+                  int64_t np, const double *pts, double *hi, double *lo)
+{
+    oprob P;
+    int e = oprob_init(&P, n, xyz, r, D, c, cutoff_rel, 1.0, 0.25, 0);
+    if (e) return e;
+    const oq Dq = D;
+    for (int64_t k = 0; k < np; k++) {
+        const double *x = pts + 3 * k;
+        oq s = 0;
+        for (int64_t i = 0; i < n; i++) {
+            const double *xi = xyz + 3 * i;
+            double dx = x[0] - xi[0], dy = x[1] - xi[1], dz = x[2] - xi[2];
+            if (dx * dx + dy * dy + dz * dz > P.R2[i]) continue;
+            oq qx = (oq)x[0] - (oq)xi[0], qy = (oq)x[1] - (oq)xi[1], qz = (oq)x[2] - (oq)xi[2], ri = r[i];
+            s += QEXP(-Dq * (qx * qx + qy * qy + qz * qz - ri * ri));
+        }
+        hi[k] = (double)s;
+        lo[k] = (double)(s - (oq)hi[k]);
+    }
+    oprob_free(&P);
+    return OR_OK;
+}
+
+/* the bounds of section 2.2.2 in quad for a tensor given as hi + lo pairs:
+ * out = L, U, sum|R|, rank (rounded to double) */
+int or_bounds_quad(const double *Ahi, const double *Alo, double *out4)
+{
+    oq A[64], b[4];
+    for (int t = 0; t < 64; t++) A[t] = (oq)Ahi[t] + (oq)Alo[t];
+    q_bounds(A, b);
+    for (int t = 0; t < 4; t++) out4[t] = (double)b[t];
+    return OR_OK;
+}
+int or_have_quad(void) { return 1; }
+#else
+static int quad_decide(const oprob *P, const double *lo, const double *hi, int level, int *dec)
+{
+    (void)P; (void)lo; (void)hi; (void)level; (void)dec;
+    return -1;
+}
+static int quad_phi(const oprob *P, const double *x, double *phi)
+{
+    (void)P; (void)x; (void)phi;
+    return -1;
+}
+int or_have_quad(void) { return 0; }
+#endif
 
 /* ================================================================== */
 /* Sorted uint64 sets                                                   */
@@ -631,6 +1011,14 @@ typedef struct {
     double min_margin;        /* smallest |c-L|,|U-c|,|precision-high| seen (relative) */
     int64_t constrained_vertices; /* lattice vertices whose value is a coarser cube's interpolant */
     int64_t agreement_splits;     /* cubes split because a constrained value fell on the other side of c */
+    /* decisions whose margin is below 1e-10 relative: [0] bound test, min(c-L, U-c) against |c|+|L|+|U|;
+     * [1] precision test, |precision - sum|high|| against their sum; [2] a 99% rank rule, |sum_{i<=j} s_i -
+     * 0.99 sum s| against sum s (outer and inner rules); [3] vertex sign, |value - c| against c, over the
+     * final lattice values */
+    int64_t near[4];
+    int64_t resolved_cubes, resolved_vertices; /* re-decided in quad precision (resolve mode) */
+    int64_t resolved_changed;                  /* cubes whose decision the quad evaluation changed */
+    int64_t vertex_sign_changed;               /* vertices whose side of c the quad value changed */
 } ostats;
 
 static void cube_box(const oprob *P, uint64_t key, double *lo, double *hi)
@@ -676,6 +1064,10 @@ void or_child_reexpand(const double *A, int c8, double *B)
             }
 }
 
+#define OR_NEAR 1e-10
+static int quad_decide(const oprob *P, const double *lo, const double *hi, int level, int *dec);
+static int quad_phi(const oprob *P, const double *x, double *phi);
+
 static int partition(const oprob *P, vec64 *accepted, ostats *st, uint8_t *dec_log_unused)
 {
     (void)dec_log_unused;
@@ -696,11 +1088,12 @@ static int partition(const oprob *P, vec64 *accepted, ostats *st, uint8_t *dec_l
         /* each cube's tensor and decision depend on that cube alone: computed
          * in parallel, then taken in order */
         uint8_t *dec = (uint8_t *)malloc((size_t)cur.n);
+        uint8_t *near = (uint8_t *)malloc((size_t)cur.n);   /* bits: bound, precision, rank; 8 resolved, 16 changed */
         double *marg = (double *)malloc(sizeof(double) * (size_t)cur.n);
         int64_t *pairs = (int64_t *)malloc(sizeof(int64_t) * (size_t)cur.n);
         double *keepA = P->child_mode == 1 ? (double *)malloc(sizeof(double) * 64 * (size_t)cur.n) : NULL;
-        if (!dec || !marg || !pairs || (P->child_mode == 1 && !keepA)) {
-            free(dec); free(marg); free(pairs); free(keepA);
+        if (!dec || !near || !marg || !pairs || (P->child_mode == 1 && !keepA)) {
+            free(dec); free(near); free(marg); free(pairs); free(keepA);
             e = OR_ERR_OOM;
             break;
         }
@@ -713,14 +1106,32 @@ static int partition(const oprob *P, vec64 *accepted, ostats *st, uint8_t *dec_l
             pairs[q] = 0;
             if (P->child_mode == 1 && l > 0) memcpy(A, curA + 64 * q, sizeof(A));
             else pairs[q] = cube_tensor(P, lo, hi, A);
-            int d = or_decide_ex(A, P->c, P->precision, l, P->max_depth, P->order, P->norm, o6);
+            double rrel = INFINITY;
+            int d = or_decide_ex_r(A, P->c, P->precision, l, P->max_depth, P->order, P->norm, o6, &rrel);
             double mg = INFINITY;
+            unsigned nb = 0;
             if (o6[4] > 0) {
                 double scale = fabs(P->c) + fabs(o6[0]) + fabs(o6[1]);
-                mg = fmin(fabs(P->c - o6[0]), fabs(o6[1] - P->c)) / scale;
-                if (d != DEC_DISCARD) mg = fmin(mg, fabs(P->precision - o6[3]) / (P->precision + o6[3]));
+                double mb = fmin(fabs(P->c - o6[0]), fabs(o6[1] - P->c)) / scale;
+                mg = mb;
+                if (mb < OR_NEAR) nb |= 1;
+                if (rrel < OR_NEAR) nb |= 4;
+                if (d != DEC_DISCARD) {
+                    double mp = fabs(P->precision - o6[3]) / (P->precision + o6[3]);
+                    mg = fmin(mg, mp);
+                    if (mp < OR_NEAR) nb |= 2;
+                }
+            }
+            if (nb && P->resolve && !(P->child_mode == 1 && l > 0)) {
+                /* in band: the decision again, every step in quad precision */
+                int dq = d;
+                if (quad_decide(P, lo, hi, l, &dq) == 0) {
+                    nb |= 8;
+                    if (dq != d) { nb |= 16; d = dq; }
+                }
             }
             dec[q] = (uint8_t)d;
+            near[q] = (uint8_t)nb;
             marg[q] = mg;
             if (keepA) memcpy(keepA + 64 * q, A, sizeof(A));
         }
@@ -728,6 +1139,9 @@ static int partition(const oprob *P, vec64 *accepted, ostats *st, uint8_t *dec_l
             int d = dec[q];
             st->pair_terms += pairs[q];
             if (marg[q] < st->min_margin) st->min_margin = marg[q];
+            for (int k = 0; k < 3; k++) st->near[k] += (near[q] >> k) & 1;
+            st->resolved_cubes += (near[q] >> 3) & 1;
+            st->resolved_changed += (near[q] >> 4) & 1;
             if (d == DEC_DISCARD) { st->discarded[l]++; continue; }
             if (d == DEC_ACCEPT || d == DEC_FORCED) {
                 if (d == DEC_ACCEPT) st->accepted[l]++; else st->forced[l]++;
@@ -754,7 +1168,7 @@ static int partition(const oprob *P, vec64 *accepted, ostats *st, uint8_t *dec_l
                 }
             }
         }
-        free(dec); free(marg); free(pairs); free(keepA);
+        free(dec); free(near); free(marg); free(pairs); free(keepA);
         if (e) break;
         vec64 t = cur; cur = nxt; nxt = t;
         free(curA);
@@ -1755,17 +2169,30 @@ static int triangulate_all(const omesh_ctx *M, const uint64_t *cubes, int64_t n,
 }
 
 /* phi at lattice-vertex keys (finest lattice), one point at a time */
-static void lattice_field(const oprob *P, const uint64_t *vk, int64_t n, double *vphi)
+/* resolve mode: a value within 1e-10 c of c is summed again in quad
+ * precision (and rounded once); *resolved and *changed count those values
+ * and those whose side of c changed */
+static void lattice_field(const oprob *P, const uint64_t *vk, int64_t n, double *vphi, int64_t *resolved,
+                          int64_t *changed)
 {
+    int64_t nr = 0, nc = 0;
 #ifdef _OPENMP
-#pragma omp parallel for schedule(dynamic, 256) num_threads(OR_NT)
+#pragma omp parallel for schedule(dynamic, 256) num_threads(OR_NT) reduction(+ : nr, nc)
 #endif
     for (int64_t i = 0; i < n; i++) {
         int64_t x, y, z;
         okey_xyz(vk[i], &x, &y, &z);
         double p[3] = {lat_x(P, 0, x, P->max_depth), lat_x(P, 1, y, P->max_depth), lat_x(P, 2, z, P->max_depth)};
         vphi[i] = phi_at(P, p, NULL);
+        double q;
+        if (P->resolve && fabs(vphi[i] - P->c) < OR_NEAR * P->c && quad_phi(P, p, &q) == 0) {
+            nr++;
+            if ((q < P->c) != (vphi[i] < P->c)) nc++;
+            vphi[i] = q;
+        }
     }
+    if (resolved) *resolved = nr;
+    if (changed) *changed = nc;
 }
 
 static int cmp_vert(const void *a, const void *b)
@@ -1861,14 +2288,18 @@ int or_cube_batch(int64_t n, const double *xyz, const double *r, double D, doubl
 }
 
 /* the whole path: partition, conformity, vertex field, triangulation, weld */
-int or_mesh_ex(int64_t n, const double *xyz, const double *r, double D, double c, double cutoff_rel,
-               double precision, double min_edge, int max_depth, int child_mode, int order, int norm, int conform,
-               or_mesh_out *out)
+/* resolve: 1 takes every in-band decision and vertex sign again in quad
+ * precision (OR_ERR_ARG where the compiler has no binary128 type) */
+int or_mesh_ex2(int64_t n, const double *xyz, const double *r, double D, double c, double cutoff_rel,
+                double precision, double min_edge, int max_depth, int child_mode, int order, int norm, int conform,
+                int resolve, or_mesh_out *out)
 {
     memset(out, 0, sizeof(*out));
+    if (resolve != 0 && (resolve != 1 || !or_have_quad())) return OR_ERR_ARG;
     oprob P;
     int e = oprob_init(&P, n, xyz, r, D, c, cutoff_rel, precision, min_edge, max_depth);
     if (e) return e;
+    P.resolve = resolve;
     if (child_mode != 0 && child_mode != 1) { oprob_free(&P); return OR_ERR_ARG; }
     if (order != 0 && order != 1) { oprob_free(&P); return OR_ERR_ARG; }
     if (norm < 0 || norm > 2) { oprob_free(&P); return OR_ERR_ARG; }
@@ -1911,7 +2342,10 @@ int or_mesh_ex(int64_t n, const double *xyz, const double *r, double D, double c
             vpsi = (double *)malloc(sizeof(double) * (size_t)(vk.n ? vk.n : 1));
             ocons *cons = (ocons *)malloc(sizeof(ocons) * (size_t)(vk.n ? vk.n : 1));
             if (!vphi || !vpsi || !cons) { free(cons); free(vk.a); free(vphi); free(vpsi); e = OR_ERR_OOM; goto done; }
-            lattice_field(&P, vk.a, vk.n, vphi);
+            int64_t vres = 0, vchg = 0;
+            lattice_field(&P, vk.a, vk.n, vphi, &vres, &vchg);
+            st->resolved_vertices = vres;
+            st->vertex_sign_changed = vchg;
             e = constrain_values(&P, acc.a, acc.n, vk.a, vk.n, vphi, vpsi, cons);
             vec64 R = {0};
             if (!e) e = disagreeing_cubes(&P, acc.a, acc.n, vk.a, vk.n, vphi, vpsi, cons, &R);
@@ -1927,7 +2361,11 @@ int or_mesh_ex(int64_t n, const double *xyz, const double *r, double D, double c
             int64_t nr = R.n;
             free(R.a);
             if (e) { free(vk.a); free(vphi); free(vpsi); goto done; }
-            if (nr == 0) { st->constrained_vertices = ncons; break; }
+            if (nr == 0) {
+                st->constrained_vertices = ncons;
+                for (int64_t i = 0; i < vk.n; i++) st->near[3] += fabs(vpsi[i] - c) < OR_NEAR * c;
+                break;
+            }
         }
         st->n_cubes_final = acc.n;
         st->n_vertices_lattice = vk.n;
@@ -1973,6 +2411,14 @@ done:
     oprob_free(&P);
     if (e) or_mesh_free(out);
     return e;
+}
+
+int or_mesh_ex(int64_t n, const double *xyz, const double *r, double D, double c, double cutoff_rel,
+               double precision, double min_edge, int max_depth, int child_mode, int order, int norm, int conform,
+               or_mesh_out *out)
+{
+    return or_mesh_ex2(n, xyz, r, D, c, cutoff_rel, precision, min_edge, max_depth, child_mode, order, norm, conform,
+                       0, out);
 }
 
 /* partition only (level loop), returns the accepted cubes (sorted) */

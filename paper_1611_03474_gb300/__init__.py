@@ -12,7 +12,7 @@ from ._native import (GS_BATCH_SHARED_LEVELS, GS_BATCH_THREADS, GS_CHILD_REEXPAN
                       GS_ORDER_BOUNDS_FIRST, GS_ORDER_LITERAL, GS_PREC_FP64, GS_PREC_MIXED, GsError, Mesh, Stats,
                       autotune_report, autotune_reset, gs_bin_atoms, gs_bin_atoms_static, gs_cube_decisions,
                       gs_eval_field, gs_mesh_backward, gs_mesh_intersections, gs_triangulate_grid, gs_volume_area,
-                      library_path, load, mesh_gaussian_surface, mesh_gaussian_surface_batch,
+                      library_path, load, memory_kind, mesh_gaussian_surface, mesh_gaussian_surface_batch,
                       mesh_gaussian_surface_into)
 
 __all__ = ["GS_BATCH_SHARED_LEVELS", "GS_BATCH_THREADS", "GS_CHILD_REEXPAND", "GS_CHILD_REPROJECT",
@@ -20,5 +20,5 @@ __all__ = ["GS_BATCH_SHARED_LEVELS", "GS_BATCH_THREADS", "GS_CHILD_REEXPAND", "G
            "GS_ORDER_BOUNDS_FIRST", "GS_ORDER_LITERAL", "GS_PREC_FP64", "GS_PREC_MIXED", "GsError", "Mesh", "Stats",
            "autotune_report", "autotune_reset", "gs_bin_atoms", "gs_bin_atoms_static", "gs_cube_decisions",
            "gs_eval_field", "gs_mesh_backward", "gs_mesh_intersections", "gs_triangulate_grid", "gs_volume_area",
-           "library_path", "load", "mesh_gaussian_surface", "mesh_gaussian_surface_batch",
+           "library_path", "load", "memory_kind", "mesh_gaussian_surface", "mesh_gaussian_surface_batch",
            "mesh_gaussian_surface_into"]

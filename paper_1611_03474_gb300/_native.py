@@ -37,7 +37,8 @@ class Stats(ctypes.Structure):
                 ("mixed_err_ratio", ctypes.c_double), ("mixed_band_ratio", ctypes.c_double),
                 ("recheck_rank", ctypes.c_int64), ("vertex_mark_cubes", ctypes.c_int64 * 3),
                 ("estimate_fast_cubes", ctypes.c_int64), ("constrained_vertices", ctypes.c_int64),
-                ("agreement_splits", ctypes.c_int64), ("mixed_cubes", ctypes.c_int64), ("retries", ctypes.c_int64)]
+                ("agreement_splits", ctypes.c_int64), ("mixed_cubes", ctypes.c_int64), ("retries", ctypes.c_int64),
+                ("near_threshold", ctypes.c_int64 * 4)]
 
     def as_dict(self, max_depth=20):
         d = {}
@@ -123,6 +124,8 @@ def load():
     L.gs_autotune_report.restype = i64
     L.gs_autotune_reset.argtypes = []
     L.gs_autotune_reset.restype = None
+    L.gs_memory_kind.argtypes = [p]
+    L.gs_memory_kind.restype = i32
     for which, cls in ((0, Stats), (1, Options), (2, MeshC)):
         if L.gs_struct_size(which) != ctypes.sizeof(cls):
             raise GsError(-1, "ABI struct %s: library %d bytes, binding %d" % (cls.__name__, L.gs_struct_size(which),
@@ -538,6 +541,12 @@ def autotune_report():
         out.append({"kernel": f[0], "size_class": int(f[1][2:]), "choice": int(f[2]),
                     "trial_ms": [float(x) for x in f[3:]]})
     return out
+
+
+def memory_kind(buf):
+    """How the library sees a buffer (numpy array or torch tensor): 0 device,
+    1 page-locked host memory mapped into the device, 2 other host memory."""
+    return int(load().gs_memory_kind(_ptr(buf)))
 
 
 def autotune_reset():

@@ -50,6 +50,8 @@ extern "C" const char *gs_status_string(int s)
     }
 }
 
+extern "C" int gs_memory_kind(const void *p) { return gs_host_kind(p); }
+
 extern "C" int64_t gs_struct_size(int which)
 {
     switch (which) {
@@ -225,14 +227,16 @@ static int prepare(const double *atoms, const double *radii, int64_t n, double D
         double *p;
         int rc = B.get(&p, 3 * (size_t)n);
         if (rc) return rc;
-        GS_CHECK(cudaMemcpyAsync(p, atoms, sizeof(double) * 3 * (size_t)n, cudaMemcpyHostToDevice, st));
+        rc = gs_copy_from_host(p, atoms, sizeof(double) * 3 * (size_t)n, st);
+        if (rc) return rc;
         d_xyz = p;
     }
     if (!on_device(radii)) {
         double *p;
         int rc = B.get(&p, (size_t)n);
         if (rc) return rc;
-        GS_CHECK(cudaMemcpyAsync(p, radii, sizeof(double) * (size_t)n, cudaMemcpyHostToDevice, st));
+        rc = gs_copy_from_host(p, radii, sizeof(double) * (size_t)n, st);
+        if (rc) return rc;
         d_r = p;
     }
     int t1 = T.mark();
@@ -498,14 +502,14 @@ static int finish_into(MeshDev &M, gs_mesh_buffers *b, cudaStream_t st)
     if (M.nv > b->cap_vertices || M.nt > b->cap_triangles || (b->cube_keys && M.nc > b->cap_cubes))
         return gs_fail(GS_ERR_CAPACITY, "output buffers too small: the mesh has %lld vertices, %lld triangles, %lld cubes",
                        (long long)M.nv, (long long)M.nt, (long long)M.nc);
+    int rc = GS_OK;
     if (M.nv) {
-        GS_CHECK(cudaMemcpyAsync(b->vertices, M.vxyz, sizeof(double) * 3 * (size_t)M.nv, cudaMemcpyDefault, st));
-        if (b->vertex_keys)
-            GS_CHECK(cudaMemcpyAsync(b->vertex_keys, M.vkeys, sizeof(uint64_t) * (size_t)M.nv, cudaMemcpyDefault, st));
+        rc = gs_copy_to_host(b->vertices, M.vxyz, sizeof(double) * 3 * (size_t)M.nv, st);
+        if (!rc && b->vertex_keys) rc = gs_copy_to_host(b->vertex_keys, M.vkeys, sizeof(uint64_t) * (size_t)M.nv, st);
     }
-    if (M.nt) GS_CHECK(cudaMemcpyAsync(b->triangles, M.tri, sizeof(int32_t) * 3 * (size_t)M.nt, cudaMemcpyDefault, st));
-    if (M.nc && b->cube_keys)
-        GS_CHECK(cudaMemcpyAsync(b->cube_keys, M.cubes, sizeof(uint64_t) * (size_t)M.nc, cudaMemcpyDefault, st));
+    if (!rc && M.nt) rc = gs_copy_to_host(b->triangles, M.tri, sizeof(int32_t) * 3 * (size_t)M.nt, st);
+    if (!rc && M.nc && b->cube_keys) rc = gs_copy_to_host(b->cube_keys, M.cubes, sizeof(uint64_t) * (size_t)M.nc, st);
+    if (rc) return rc;
     GS_CHECK(gs_sync(st));
     return GS_OK;
 }
@@ -703,6 +707,7 @@ static void copy_level_stats(gs_stats *d, const gs_stats &s)
     d->ms_accum = s.ms_accum;
     d->n_accum_launches = s.n_accum_launches;
     d->retries = s.retries;
+    for (int k = 0; k < 3; k++) d->near_threshold[k] = s.near_threshold[k];
 }
 
 static int mesh_impl(const double *atoms, const double *radii, int64_t n, double D, double c, double precision,
@@ -732,8 +737,12 @@ static int mesh_impl(const double *atoms, const double *radii, int64_t n, double
     int rc = B.get(&d_status, 1);
     if (!rc) rc = B.get(&d_cnt, 32);
     if (rc) return rc;
+    unsigned long long *d_near = nullptr;   // near-threshold counts (gs_stats.near_threshold)
+    rc = B.get(&d_near, 4);
+    if (rc) return rc;
     GS_CHECK(cudaMemsetAsync(d_status, 0, sizeof(unsigned), st));
     GS_CHECK(cudaMemsetAsync(d_cnt, 0, 32 * sizeof(unsigned long long), st));
+    GS_CHECK(cudaMemsetAsync(d_near, 0, 4 * sizeof(unsigned long long), st));
     Prepared PR;
     if (pre) {
         PR = pre->PR;
@@ -744,6 +753,7 @@ static int mesh_impl(const double *atoms, const double *radii, int64_t n, double
     if (rc) return rc;
     PR.P.order = o.decision_order;
     PR.P.norm = o.precision_norm;
+    PR.P.near = d_near;
     const GsProblem &P = PR.P;
     if (o.precision_mode == GS_PREC_MIXED) {
         rc = check_fp32_range(P);
@@ -932,6 +942,8 @@ static int mesh_impl(const double *atoms, const double *radii, int64_t n, double
     M.cubes = cubes;
     M.nc = nc;
     MixInfo mx{n_mixed > 0 ? mixed : nullptr, hc, hv, vslot};
+    rc = gs_count_near(phi, nv, P.c, d_near + 3, st);
+    if (rc) return rc;
     {
         NvtxRange nr("gs: triangulate, weld");
         rc = surface_from_values(P, cubes, nc, cvid, phi, B, d_status, d_cnt + 10, M, stats, T, &mx);
@@ -978,8 +990,10 @@ static int mesh_impl(const double *atoms, const double *radii, int64_t n, double
     }
     int tend = T.mark();
     GS_CHECK(gs_sync(st));
-    unsigned long long h[32];
+    unsigned long long h[32], hn[4];
     GS_CHECK(cudaMemcpy(h, d_cnt, sizeof(h), cudaMemcpyDeviceToHost));
+    GS_CHECK(cudaMemcpy(hn, d_near, sizeof(hn), cudaMemcpyDeviceToHost));
+    for (int k = 0; k < 4; k++) stats->near_threshold[k] = (int64_t)hn[k];
     stats->recheck_bounds = (int64_t)h[15];
     stats->recheck_precision = (int64_t)h[16];
     stats->recheck_zero = (int64_t)h[17];
@@ -1139,7 +1153,10 @@ static int group_levels(const std::vector<int64_t> &mols, std::vector<PreMol> &p
     if (!rc) rc = B.get(&d_cnt, 32);
     if (!rc) rc = B.get(&d_molcnt, 5 * (size_t)G);
     if (!rc) rc = B.get(&d_probs, (size_t)G);
+    unsigned long long *d_near = nullptr;
+    if (!rc) rc = B.get(&d_near, 4);
     if (rc) return rc;
+    GS_CHECK(cudaMemsetAsync(d_near, 0, 4 * sizeof(unsigned long long), st));
     std::vector<GsProblem> hp((size_t)G);
     for (int g = 0; g < G; g++) hp[(size_t)g] = pm[(size_t)mols[(size_t)g]].PR.P;
     GS_CHECK(cudaMemsetAsync(d_status, 0, sizeof(unsigned), st));
@@ -1150,6 +1167,7 @@ static int group_levels(const std::vector<int64_t> &mols, std::vector<PreMol> &p
     // root grid are masked explicitly, so its root extent is unbounded
     GsProblem P0 = hp[0];
     for (int a = 0; a < 3; a++) P0.nroot[a] = (int64_t)1 << 40;
+    P0.near = d_near;
     uint64_t *parents = nullptr;
     uint8_t *vmask0 = nullptr;
     int32_t *pmol = nullptr;
@@ -1254,8 +1272,9 @@ static int group_levels(const std::vector<int64_t> &mols, std::vector<PreMol> &p
     }
     if (!rc) rc = check_status(d_status, st, "batch cubes");
     const int t1 = T.mark();
-    unsigned long long h[32];
+    unsigned long long h[32], hn[4];
     cudaError_t e = cudaMemcpyAsync(h, d_cnt, sizeof(h), cudaMemcpyDeviceToHost, st);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(hn, d_near, sizeof(hn), cudaMemcpyDeviceToHost, st);
     if (e == cudaSuccess) e = gs_sync(st);
     if (!rc && e != cudaSuccess) rc = gs_fail_cuda(e, "batch levels", __FILE__, __LINE__);
     if (rc) { drop_outs(); return rc; }
@@ -1277,6 +1296,7 @@ static int group_levels(const std::vector<int64_t> &mols, std::vector<PreMol> &p
         gst.mixed_band_ratio = r;
     }
     gst.ms_levels = T.ms(t0, t1);
+    for (int k = 0; k < 3; k++) gst.near_threshold[k] = (int64_t)hn[k];
     for (int g = 0; g < G; g++) {
         PreMol &q = pm[(size_t)mols[(size_t)g]];
         q.lv = gst;

@@ -512,3 +512,20 @@ int gs_field_adjoint(const GsProblem &P, const int32_t *d_perm, const uint64_t *
     GS_CHECK(cudaGetLastError());
     return GS_OK;
 }
+
+// lattice values within 1e-10 c of c (the vertex-sign margin): cnt += count
+__global__ void k_count_near(const double *__restrict__ v, int64_t n, double c, unsigned long long *cnt)
+{
+    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    const bool nr = i < n && fabs(v[i] - c) < GS_NEAR_REL * c;
+    const unsigned b = __ballot_sync(0xffffffffu, nr);
+    if ((threadIdx.x & 31) == 0 && b) atomicAdd(cnt, (unsigned long long)__popc(b));
+}
+
+int gs_count_near(const double *d_v, int64_t n, double c, unsigned long long *d_cnt, cudaStream_t st)
+{
+    if (n <= 0) return GS_OK;
+    GS_LAUNCH(k_count_near, (unsigned)((n + 255) / 256), 256, 0, st)(d_v, n, c, d_cnt);
+    GS_CHECK(cudaGetLastError());
+    return GS_OK;
+}

@@ -202,3 +202,14 @@ int gs_triangulate(const TriCtx &X, uint64_t **d_tri_keys, int64_t *ntri_total, 
 // (non-null during trials) replaces the launch's counters
 int gs_tune_run(const char *kernel, int64_t n, int n_choices, cudaStream_t st,
                 const std::function<void(int, unsigned long long *)> &launch);
+
+// lattice values within 1e-10 c of c: *d_cnt += their number
+int gs_count_near(const double *d_v, int64_t n, double c, unsigned long long *d_cnt, cudaStream_t st);
+
+// copies between device memory and host memory: page-locked mapped host
+// buffers through a copy kernel on their device mapping, other host memory
+// through cudaMemcpyAsync (gs_scan.cu); gs_host_kind: 0 device, 1 page-locked
+// host mapped into the device, 2 other host memory, -1 null
+int gs_copy_to_host(void *dst, const void *src, size_t bytes, cudaStream_t st);
+int gs_copy_from_host(void *dst, const void *src, size_t bytes, cudaStream_t st);
+int gs_host_kind(const void *p);

@@ -64,7 +64,11 @@ struct GsProblem {
     float cell_f, inv_cell_f, pad_f;             // FP32 copies for candidate enumeration
     int lat_exact_f32;                           // lattice coordinates (index * spacing) are exact in FP32
     const int32_t *cell_start;                   // [ncell + 1]
+    // nullable: counts of decisions whose margin is below 1e-10 relative
+    // ([0] bound test, [1] precision test, [2] rank rule, [3] vertex sign)
+    unsigned long long *near;
 };
+#define GS_NEAR_REL 1e-10
 
 // cube edge at level l (exact power-of-two scaling)
 __host__ __device__ __forceinline__ double gs_h(const GsProblem &P, int l)

@@ -705,7 +705,7 @@ __device__ __forceinline__ T gap_sens(const T (&s)[4], int kept)
 // fi to fj; rn (nullable) collects the rules near their thresholds
 template <typename T>
 __device__ __forceinline__ void estimate_bounds_sens(const T *A, T *out, T &rmargin, T &sens, int fo = 0, int fi = -1,
-                                                     int fj = 0, RankNear<T> *rn = nullptr);
+                                                     int fj = 0, RankNear<T> *rn = nullptr, T *rrel = nullptr);
 
 template <typename T>
 __device__ void estimate_bounds(const T *A, T *out, T &rmargin)
@@ -714,9 +714,11 @@ __device__ void estimate_bounds(const T *A, T *out, T &rmargin)
     estimate_bounds_sens<T>(A, out, rmargin, sens);
 }
 
+// rrel (nullable): the smallest distance of a rank rule from its threshold
+// relative to its own singular-value sum (outer and inner rules)
 template <typename T>
 __device__ __forceinline__ void estimate_bounds_sens(const T *A, T *out, T &rmargin, T &sens, int fo, int fi, int fj,
-                                                     RankNear<T> *rn)
+                                                     RankNear<T> *rn, T *rrel)
 {
     T X[4][16];
     T high = 0, tot = 0;
@@ -737,6 +739,7 @@ __device__ __forceinline__ void estimate_bounds_sens(const T *A, T *out, T &rmar
     jacobi4<T, 16>(X, s, u);
     T rm;
     int jr = rank99(s, rm);
+    if (rrel) *rrel = rm / (s[0] + s[1] + s[2] + s[3]);
     if (fo > 0) {
         jr = fo;
         rm = T(1e30);
@@ -761,6 +764,10 @@ __device__ __forceinline__ void estimate_bounds_sens(const T *A, T *out, T &rmar
         jacobi4<T, 4>(V, d, w);
         T rmi;
         int ji = rank99(d, rmi);
+        if (rrel) {
+            const T rr = rmi / (d[0] + d[1] + d[2] + d[3]);
+            *rrel = rr < *rrel ? rr : *rrel;
+        }
         if (i == fi) {
             ji = fj;
         } else {
@@ -900,11 +907,20 @@ __global__ void __launch_bounds__(128) k_estimate_f64(GsProblem P, int level, co
     double a[64];
 #pragma unroll
     for (int t = 0; t < 64; t++) a[t] = A[q * 64 + t];
-    double b[6], rm;
-    estimate_bounds<double>(a, b, rm);
+    double b[6], rm, sens, rrel = 1e30;
+    estimate_bounds_sens<double>(a, b, rm, sens, 0, -1, 0, nullptr, P.near ? &rrel : nullptr);
     if (P.norm != GS_NORM_SUM) b[3] = high_norm(a, P.norm);
-    dec[q] = (uint8_t)(P.order == GS_ORDER_LITERAL ? decide_literal(b, P.c, P.precision, level, P.max_depth)
-                                                   : decide<double>(b, P.c, P.precision, level, P.max_depth));
+    const int d = P.order == GS_ORDER_LITERAL ? decide_literal(b, P.c, P.precision, level, P.max_depth)
+                                              : decide<double>(b, P.c, P.precision, level, P.max_depth);
+    dec[q] = (uint8_t)d;
+    if (P.near && b[4] != 0.0) {
+        // the margins of the decision against its thresholds
+        const double scale = fabs(P.c) + fabs(b[0]) + fabs(b[1]);
+        if (fmin(fabs(P.c - b[0]), fabs(b[1] - P.c)) < GS_NEAR_REL * scale) atomicAdd(&P.near[0], 1ull);
+        if (d != DEC_DISCARD && fabs(P.precision - b[3]) < GS_NEAR_REL * (P.precision + b[3]))
+            atomicAdd(&P.near[1], 1ull);
+        if (rrel < GS_NEAR_REL) atomicAdd(&P.near[2], 1ull);
+    }
     if (bounds)
         for (int t = 0; t < 6; t++) bounds[q * 6 + t] = b[t];
 }
@@ -938,10 +954,13 @@ __global__ void __launch_bounds__(256) k_estimate_pre64(GsProblem P, int level, 
             double lo, hi;
             corner_range<double>(a, lo, hi);
             const double cm = 1e-12 * tot;
-            if (hi - P.c > cm && P.c - lo > cm)
+            if (hi - P.c > cm && P.c - lo > cm) {
                 dec[q] = (uint8_t)(high <= P.precision ? DEC_ACCEPT : (level >= P.max_depth ? DEC_FORCED : DEC_SPLIT));
-            else
+                if (P.near && fabs(P.precision - high) < GS_NEAR_REL * (P.precision + high))
+                    atomicAdd(&P.near[1], 1ull);
+            } else {
                 slow = true;
+            }
         }
     }
     const unsigned bal = __ballot_sync(0xffffffffu, slow);

@@ -157,3 +157,73 @@ int gs_scan_i64(int64_t *d_vals, int64_t n, int64_t *d_total, cudaStream_t st)
     GS_CHECK(cudaGetLastError());
     return GS_OK;
 }
+
+// ---------------------------------------------------------------- host copies
+// Copies between device memory and page-locked host memory run as a kernel
+// on the host buffer's device mapping (16-byte loads and stores, grid a
+// multiple of the SM count), so a large mesh leaves the device at the rate of
+// the host link without a staging step; other host memory (pageable,
+// unregistered) and unaligned buffers take cudaMemcpyAsync.
+__global__ void __launch_bounds__(256) k_copy16(int4 *__restrict__ dst, const int4 *__restrict__ src, int64_t n16)
+{
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n16; i += (int64_t)gridDim.x * blockDim.x)
+        dst[i] = src[i];
+}
+
+// the host buffer's device address when it is page-locked and mapped, else null
+static void *mapped_host(const void *p)
+{
+    cudaPointerAttributes a;
+    if (cudaPointerGetAttributes(&a, p) != cudaSuccess) {
+        cudaGetLastError();
+        return nullptr;
+    }
+    return a.type == cudaMemoryTypeHost ? a.devicePointer : nullptr;
+}
+
+int gs_host_kind(const void *p)
+{
+    cudaPointerAttributes a;
+    if (!p) return -1;
+    if (cudaPointerGetAttributes(&a, p) != cudaSuccess) {
+        cudaGetLastError();
+        return 2;
+    }
+    if (a.type == cudaMemoryTypeDevice || a.type == cudaMemoryTypeManaged) return 0;
+    if (a.type == cudaMemoryTypeHost) return a.devicePointer ? 1 : 2;
+    return 2;
+}
+
+static int copy_mapped(void *dst_dev, const void *src_dev, size_t bytes, cudaStream_t st)
+{
+    const int64_t n16 = (int64_t)(bytes / 16);
+    if (n16 > 0) {
+        int64_t blocks = (n16 + 255) / 256;
+        if (blocks > 152 * 8) blocks = 152 * 8;
+        GS_LAUNCH(k_copy16, (unsigned)blocks, 256, 0, st)((int4 *)dst_dev, (const int4 *)src_dev, n16);
+    }
+    const size_t tail = bytes - 16 * (size_t)n16;
+    if (tail)
+        GS_CHECK(cudaMemcpyAsync((char *)dst_dev + 16 * n16, (const char *)src_dev + 16 * n16, tail,
+                                 cudaMemcpyDefault, st));
+    GS_CHECK(cudaGetLastError());
+    return GS_OK;
+}
+
+int gs_copy_to_host(void *dst, const void *src, size_t bytes, cudaStream_t st)
+{
+    if (!bytes) return GS_OK;
+    void *dd = mapped_host(dst);
+    if (dd && ((uintptr_t)dd % 16) == 0 && ((uintptr_t)src % 16) == 0) return copy_mapped(dd, src, bytes, st);
+    GS_CHECK(cudaMemcpyAsync(dst, src, bytes, cudaMemcpyDefault, st));
+    return GS_OK;
+}
+
+int gs_copy_from_host(void *dst, const void *src, size_t bytes, cudaStream_t st)
+{
+    if (!bytes) return GS_OK;
+    void *sd = mapped_host(src);
+    if (sd && ((uintptr_t)sd % 16) == 0 && ((uintptr_t)dst % 16) == 0) return copy_mapped(dst, sd, bytes, st);
+    GS_CHECK(cudaMemcpyAsync(dst, src, bytes, cudaMemcpyDefault, st));
+    return GS_OK;
+}

@@ -96,3 +96,11 @@ def test_option_and_buffer_errors_without_gpu(lib):
         rc = L.mesh_gaussian_surface_into(nat._ptr(xyz), nat._ptr(r), 1, 0.5, 1.0, 1e-3, 2, ctypes.byref(opt),
                                           ctypes.byref(b))
         assert rc == -1 and (b.n_vertices, b.n_triangles, b.n_cubes) == (0, 0, 0)
+
+
+def test_memory_kind_without_gpu(lib):
+    """A host array is not device memory (no GPU: the query fails and the
+    library treats the buffer as ordinary host memory)."""
+    import numpy as np
+    import paper_1611_03474_gb300 as gs
+    assert gs.memory_kind(np.zeros(4)) == 2
