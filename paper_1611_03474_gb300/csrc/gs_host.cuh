@@ -199,7 +199,8 @@ int gs_triangulate(const TriCtx &X, uint64_t **d_tri_keys, int64_t *ntri_total, 
 
 // launch-shape autotuner (gs_tune.cu): launch(shape, scratch) launches the
 // kernel in one of n_choices shapes that compute the same result; scratch
-// (non-null during trials) replaces the launch's counters
+// (non-null during trials: 32 counters whose values are discarded) replaces
+// the launch's counters
 int gs_tune_run(const char *kernel, int64_t n, int n_choices, cudaStream_t st,
                 const std::function<void(int, unsigned long long *)> &launch);
 

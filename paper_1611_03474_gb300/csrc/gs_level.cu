@@ -1685,11 +1685,15 @@ __global__ void __launch_bounds__(256) k_estimate_pre(GsProblem P, int level, co
     if (slow) list[wb + __popc(bal & ((1u << lane) - 1u))] = (int32_t)q;
 }
 
-__global__ void __launch_bounds__(128) k_estimate_f32(GsProblem P, int level, const float *__restrict__ A,
-                                                      const float *__restrict__ E, uint8_t *__restrict__ dec,
-                                                      uint8_t *__restrict__ flag, unsigned long long *why_cnt,
-                                                      float *__restrict__ dbg, const int32_t *__restrict__ list,
-                                                      const unsigned *nlist)
+// MINB: blocks per SM the register allocation is held to (0: none; 3 caps
+// the registers at 168 and spills the rest to local memory), a shape the
+// tuner chooses; the arithmetic is the same
+template <int MINB>
+__global__ void __launch_bounds__(128, MINB) k_estimate_f32(GsProblem P, int level, const float *__restrict__ A,
+                                                            const float *__restrict__ E, uint8_t *__restrict__ dec,
+                                                            uint8_t *__restrict__ flag, unsigned long long *why_cnt,
+                                                            float *__restrict__ dbg, const int32_t *__restrict__ list,
+                                                            const unsigned *nlist)
 {
     const int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (t >= (int64_t)*nlist) return;
@@ -1757,14 +1761,20 @@ int gs_estimate_f32(const GsProblem &P, int level, const float *d_A, const float
     GS_LAUNCH(k_estimate_pre, (unsigned)((n_cubes + 255) / 256), 256, 0, st)(P, level, d_A, d_err, n_cubes, d_parents,
                                                                             d_vmask, d_dec, d_flag, d_why, d_dbg,
                                                                             list, nlist);
-    GS_LAUNCH(k_estimate_f32, (unsigned)((n_cubes + 127) / 128), 128, 0, st)(P, level, d_A, d_err, d_dec, d_flag,
-                                                                            d_why, d_dbg, list, nlist);
+    const unsigned grid = (unsigned)((n_cubes + 127) / 128);
+    rc = gs_tune_run("k_estimate_f32", n_cubes, 2, st, [&](int shape, unsigned long long *scratch) {
+        unsigned long long *why = scratch ? (d_why ? scratch : nullptr) : d_why;
+        if (shape == 0)
+            GS_LAUNCH(k_estimate_f32<0>, grid, 128, 0, st)(P, level, d_A, d_err, d_dec, d_flag, why, d_dbg, list, nlist);
+        else
+            GS_LAUNCH(k_estimate_f32<3>, grid, 128, 0, st)(P, level, d_A, d_err, d_dec, d_flag, why, d_dbg, list, nlist);
+    });
     gs_free(list, st);
     gs_free(nlist, st);
+    if (rc) return rc;
     GS_CHECK(cudaGetLastError());
     return GS_OK;
 }
-
 __global__ void k_add_u64(unsigned long long *dst, const unsigned long long *v) { *dst += *v; }
 
 // octets with a flagged child -> list of octet indices; counts flagged children

@@ -73,7 +73,7 @@ int gs_tune_run(const char *kernel, int64_t n, int n_choices, cudaStream_t st,
     if (!found && n_choices > 1 && cudaStreamIsCapturing(st, &cap) == cudaSuccess &&
         cap == cudaStreamCaptureStatusNone) {
         unsigned long long *scratch = nullptr;
-        int rc = gs_alloc((void **)&scratch, 8 * sizeof(unsigned long long), st);
+        int rc = gs_alloc((void **)&scratch, 32 * sizeof(unsigned long long), st);
         if (rc) return rc;
         cudaEvent_t e0, e1;
         GS_CHECK(cudaEventCreate(&e0));

@@ -60,10 +60,11 @@ def test_tuned_choices_are_recorded(restore_env):
         assert m.stats["vertex_terms"] == ref.stats["vertex_terms"]
     rep = gs.autotune_report()
     kernels = {e["kernel"] for e in rep}
-    assert "k_field_f32w" in kernels
+    assert "k_field_f32w" in kernels and "k_estimate_f32" in kernels
     assert any(k.startswith("k_accum_f32") for k in kernels)
+    shapes = {"k_field_f32w": 4, "k_estimate_f32": 2}
     for e in rep:
-        n = 4 if e["kernel"] == "k_field_f32w" else 3
+        n = shapes.get(e["kernel"], 3)
         assert len(e["trial_ms"]) == n and 0 <= e["choice"] < n
         assert e["trial_ms"][e["choice"]] == min(e["trial_ms"])
         assert all(t > 0 for t in e["trial_ms"])
