@@ -490,6 +490,8 @@ def main():
         kwb = dict(precision_mode=mode, device_output=True)
         res = {}
         for label, nw, bmode in (("sequential", 1, gs.GS_BATCH_THREADS), ("threads", 8, gs.GS_BATCH_THREADS),
+                                 ("shared_levels_w4", 4, gs.GS_BATCH_SHARED_LEVELS),
+                                 ("shared_levels_w16", 16, gs.GS_BATCH_SHARED_LEVELS),
                                  ("shared_levels", 8, gs.GS_BATCH_SHARED_LEVELS)):
             ts = []
             for it in range(args.batch_steps + 1):
@@ -511,6 +513,8 @@ def main():
                              "host inputs, device outputs" % natoms,
                  "ms_per_batch": res["shared_levels"], "ms_per_batch_threads": res["threads"],
                  "ms_per_batch_sequential": res["sequential"],
+                 "ms_per_batch_by_workers": {"4": res["shared_levels_w4"], "8": res["shared_levels"],
+                                             "16": res["shared_levels_w16"]},
                  "ms_level_loop_per_group": res["levels_ms"],
                  "molecules_per_s": 64 * 1e3 / res["shared_levels"], "n_workers": 8,
                  "n_triangles": int(sum(m.n_triangles for m in bm))}

@@ -330,9 +330,9 @@ int gs_bin_atoms(const double *atoms, int64_t n_atoms, double cell_size, const d
  *   every GPU that loads the library until the process exits).  Every call
  *   shares that array; calls whose work overlaps on the GPU race and give
  *   wrong results.  The first call on a device looks up the array's address
- *   (once per device); make that first call before any stream capture.
- *   Work runs on `stream` (NULL: the legacy default stream) and the call
- *   returns after it has completed.
+ *   (once per device).  Work runs on `stream` (NULL: the legacy default
+ *   stream) and the call returns after it has completed: it waits on the
+ *   stream, so it cannot be captured into a CUDA graph.
  */
 #define GS_STATIC_MAX_ATOMS (1 << 20)
 #define GS_STATIC_MAX_CELLS (1 << 20)

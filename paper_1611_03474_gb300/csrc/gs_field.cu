@@ -113,7 +113,7 @@ __global__ void __launch_bounds__(128) k_field_f32(GsProblem P, const uint64_t *
                 s = u;
                 // this term's error: ex2 (2 ulp) and the rounding of its
                 // argument, about 3 ulp of d^2 and r^2 times D
-                eacc = fmaf(t, 3e-7f + 2.5e-7f * Df * (d2 + r2), eacc);
+                eacc = fmaf(t, 3e-7f + 3e-7f * Df * (d2 + r2), eacc);
                 g0 = fmaf(m2D * dx, t, g0);
                 g1 = fmaf(m2D * dy, t, g1);
                 g2 = fmaf(m2D * dz, t, g2);
@@ -213,7 +213,7 @@ __global__ void __launch_bounds__(32 * WARPS) k_field_f32w(GsProblem P, const ui
                 const float u = s[v] + y;
                 comp[v] = (u - s[v]) - y;
                 s[v] = u;
-                eacc[v] = fmaf(t, 3e-7f + 2.5e-7f * Df * (d2 + b.w), eacc[v]);
+                eacc[v] = fmaf(t, 3e-7f + 3e-7f * Df * (d2 + b.w), eacc[v]);
                 cnt++;
             }
         }

@@ -196,17 +196,18 @@ def cube_boxes(keys, origin, min_edge, max_depth):
     return lo, lo + h[:, None]
 
 
-def window_oracle(cfg, centre, half=6.0, margin=10.0):
+def window_oracle(cfg, centre, half=6.0, margin=10.0, precision=None):
     """The oracle's mesh of the atoms within `margin` of the window
     [centre - half, centre + half]^3, with the shift of its root origin to
-    the whole problem's (finest-lattice units)."""
+    the whole problem's (finest-lattice units).  precision: the config's
+    unless given."""
     import oracle
     md, me = cfg["max_depth"], cfg["min_edge"]
     o_full, _, _ = oracle.root_grid(cfg["xyz"], cfg["r"], cfg["D"], cfg["c"], me, md)
     lo_w, hi_w = centre - half, centre + half
     sel = np.all((cfg["xyz"] >= lo_w - margin) & (cfg["xyz"] <= hi_w + margin), axis=1)
     sx, sr = np.ascontiguousarray(cfg["xyz"][sel]), np.ascontiguousarray(cfg["r"][sel])
-    ref = oracle.mesh(sx, sr, cfg["D"], cfg["c"], cfg["precision"], me, md)
+    ref = oracle.mesh(sx, sr, cfg["D"], cfg["c"], cfg["precision"] if precision is None else precision, me, md)
     assert ref["stats"]["loop_errors"] == 0
     o_sub, _, _ = oracle.root_grid(sx, sr, cfg["D"], cfg["c"], me, md)
     shift = np.round((o_sub - o_full) / me).astype(np.int64)

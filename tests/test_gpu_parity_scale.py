@@ -118,3 +118,27 @@ def test_window_parity_assembly1m():
         for mode in tris:
             tris[mode] += window_compare(full[mode], cfg, win)
     print("assembly1m windows: triangles compared", tris)
+
+
+def test_window_parity_assembly1m_adaptive():
+    """The adaptive path at full size: the assembly at precision 5e-2, where
+    surface cubes are accepted on two levels and cubes of different sizes
+    join through constrained vertex values and disagreement splits (rounds
+    to a fixpoint), in the mixed form, against the oracle's meshes of two
+    windows.  The splits and the 2:1 balance reach only a few cubes, so a
+    14 A margin around the window keeps them local."""
+    cfg = synth.config("assembly1m")
+    m = gs.mesh_gaussian_surface(cfg["xyz"], cfg["r"], cfg["D"], cfg["c"], 5e-2, cfg["max_depth"],
+                                 min_edge=cfg["min_edge"], precision_mode=_mode("mixed"))
+    st = m.stats
+    assert sum(st["accepted"][:cfg["max_depth"]]) > 0 and st["constrained_vertices"] > 0
+    full = dict(cube_keys=m.cube_keys, vkeys=m.vertex_keys, vertices=m.vertices, triangles=m.triangles)
+    del m
+    oracle.set_threads(0)
+    tris, coarse = 0, 0
+    for centre in _window_centres(cfg, count=2, seed=5):
+        win = window_oracle(cfg, centre, margin=14.0, precision=5e-2)
+        coarse += sum(win["ref"]["stats"]["accepted"][:cfg["max_depth"]])
+        tris += window_compare(full, cfg, win)
+    assert coarse > 0
+    print("assembly1m adaptive windows: triangles compared", tris)
