@@ -109,3 +109,17 @@ def test_batch_rejects_unknown_mode(mols):
     import paper_1611_03474_gb300 as gs
     with pytest.raises(gs.GsError):
         gs.mesh_gaussian_surface_batch(mols[:2], 1.0, 1e-3, 3, batch_mode=7)
+
+
+def test_batch_error_names_the_molecule(mols):
+    """A molecule outside the mixed form's FP32 range (D r^2 plus the cutoff
+    exponent above 80) fails the whole call with GS_ERR_ARG and a message
+    naming it; no mesh is returned."""
+    import paper_1611_03474_gb300 as gs
+    bad = list(mols[:3])
+    xyz, r, _ = bad[1]
+    bad[1] = (xyz, r, 40.0)
+    with pytest.raises(gs.GsError) as e:
+        gs.mesh_gaussian_surface_batch(bad, ARGS["c"], ARGS["precision"], ARGS["max_depth"],
+                                       precision_mode=gs.GS_PREC_MIXED)
+    assert e.value.code == -1 and "molecule 1" in str(e.value)
