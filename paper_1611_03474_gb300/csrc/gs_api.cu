@@ -799,7 +799,7 @@ static int mesh_impl(const double *atoms, const double *radii, int64_t n, double
     int64_t *mark = nullptr;
     GsHash hv{nullptr, nullptr, 0}, hc{nullptr, nullptr, 0};
     uint64_t *vslot = nullptr;
-    GsCons K{nullptr, nullptr, nullptr, 0, 0};
+    GsCons K{nullptr, nullptr, nullptr, 0, 0, nullptr, {0}};
     uint8_t *mixed = nullptr;
     int64_t n_mixed = 0, nre = 0;
     // the previous round's lattice (key -> slot -> id), raw field values and bounds
@@ -850,6 +850,7 @@ static int mesh_impl(const double *atoms, const double *radii, int64_t n, double
         if (rc) return rc;
         B.keep(K.lev); B.keep(K.src); B.keep(K.t);
         rc = gs_cons_find(&K, hc, hv, vslot, vkeys, max_depth, nullptr, d_cnt + 26, d_status, st);
+        B.keep(K.list);
         if (!rc && fp32 && K.ncons > 0) {
             // certain signs of the constrained values: their sources in FP64
             // where the interpolated bound leaves the side of c open
@@ -895,11 +896,11 @@ static int mesh_impl(const double *atoms, const double *radii, int64_t n, double
             splits += ns2;
             // this round's lattice, raw values and bounds serve the next
             hv_old = hv; vslot_old = vslot; raw_old = raw; err_old = raw_err;
-            release_all({vkeys, cvid, phi, err, mark, hc.keys, hc.vals, K.lev, K.src, K.t});
+            release_all({vkeys, cvid, phi, err, mark, hc.keys, hc.vals, K.lev, K.src, K.t, K.list});
             vkeys = nullptr; cvid = nullptr; phi = nullptr; err = nullptr; mark = nullptr; raw = nullptr;
             raw_err = nullptr; vslot = nullptr;
             hv = GsHash{nullptr, nullptr, 0}; hc = GsHash{nullptr, nullptr, 0};
-            K = GsCons{nullptr, nullptr, nullptr, 0, 0};
+            K = GsCons{nullptr, nullptr, nullptr, 0, 0, nullptr, {0}};
             continue;
         }
         release_all({split, raw, raw_err});

@@ -22,6 +22,8 @@
 // depends only on the face or edge, not on the cube that holds it, and is
 // evaluated with one rounding per operation (this file is compiled without
 // FMA contraction), as in the oracle.
+#include <cstring>
+
 #include "gs_host.cuh"
 
 __device__ __forceinline__ int64_t vert_id(const GsHash &hv, const uint64_t *slot_id, int64_t x, int64_t y, int64_t z)
@@ -114,15 +116,17 @@ __global__ void __launch_bounds__(256) k_cons_find(GsHash hc, GsHash hv, const u
 // marked for FP64.  split (nullable): count a sign disagreement with the
 // vertex's own field value and mark the level-l cubes holding the vertex
 // (cnt = 8).
+// (over the level-l group of the constrained-vertex list: ids[0 .. n))
 __global__ void __launch_bounds__(256) k_cons_apply(int l, int md, double c, GsHash hc,
-                                                    const uint64_t *__restrict__ vkeys, int64_t nv,
-                                                    const int8_t *__restrict__ lev, const int32_t *__restrict__ src,
+                                                    const uint64_t *__restrict__ vkeys, const int32_t *__restrict__ ids,
+                                                    int64_t n, const int32_t *__restrict__ src,
                                                     const double *__restrict__ tt, double *__restrict__ phi,
                                                     float *__restrict__ err, int64_t *__restrict__ mark,
                                                     int64_t *__restrict__ split, unsigned long long *nflip)
 {
-    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    if (i >= nv || lev[i] != l) return;
+    const int64_t q = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (q >= n) return;
+    const int64_t i = ids[q];
     const int32_t *S = src + 4 * i;
     const double t0 = tt[2 * i], t1 = tt[2 * i + 1];
     double psi;
@@ -160,11 +164,13 @@ __global__ void __launch_bounds__(256) k_cons_apply(int l, int md, double c, GsH
 
 // marks on vertices constrained at level l pass to their sources (run from
 // the finest constraint level to the coarsest)
-__global__ void __launch_bounds__(256) k_cons_mark_up(int l, int64_t nv, const int8_t *__restrict__ lev,
+__global__ void __launch_bounds__(256) k_cons_mark_up(const int32_t *__restrict__ ids, int64_t n,
                                                       const int32_t *__restrict__ src, int64_t *__restrict__ mark)
 {
-    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    if (i >= nv || lev[i] != l || !mark[i]) return;
+    const int64_t q = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (q >= n) return;
+    const int64_t i = ids[q];
+    if (!mark[i]) return;
     for (int q = 0; q < 4; q++)
         if (src[4 * i + q] >= 0) mark[src[4 * i + q]] = 1;
 }
@@ -220,20 +226,21 @@ __global__ void __launch_bounds__(256) k_mixed_flags(const uint64_t *__restrict_
 
 // constrained vertices keep their interpolants: no FP64 re-evaluation of
 // the field there (it would overwrite them)
-__global__ void k_cons_unmark(const int8_t *__restrict__ lev, int64_t nv, int64_t *__restrict__ mark)
+__global__ void k_cons_unmark(const int32_t *__restrict__ ids, int64_t n, int64_t *__restrict__ mark)
 {
-    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    if (i < nv && lev[i] >= 0) mark[i] = 0;
+    const int64_t q = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (q < n) mark[ids[q]] = 0;
 }
 
 // adjoint of the level-l constraints: each passes its adjoint on to its
 // sources with the interpolation weights (fine to coarse)
-__global__ void __launch_bounds__(256) k_cons_adjoint(int l, int64_t nv, const int8_t *__restrict__ lev,
+__global__ void __launch_bounds__(256) k_cons_adjoint(const int32_t *__restrict__ ids, int64_t n,
                                                       const int32_t *__restrict__ src, const double *__restrict__ tt,
                                                       double *__restrict__ lam)
 {
-    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    if (i >= nv || lev[i] != l) return;
+    const int64_t q = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (q >= n) return;
+    const int64_t i = ids[q];
     const double g = lam[i];
     lam[i] = 0.0;
     if (g == 0.0) return;
@@ -267,7 +274,8 @@ int gs_fill_i64(int64_t *d_a, int64_t n, int64_t v, cudaStream_t st)
 
 int gs_cons_alloc(GsCons *K, int64_t nv, cudaStream_t st)
 {
-    K->lev = nullptr; K->src = nullptr; K->t = nullptr; K->nv = nv; K->ncons = 0;
+    K->lev = nullptr; K->src = nullptr; K->t = nullptr; K->nv = nv; K->ncons = 0; K->list = nullptr;
+    memset(K->loff, 0, sizeof(K->loff));
     int rc = gs_alloc((void **)&K->lev, (size_t)(nv + 1), st);
     if (!rc) rc = gs_alloc((void **)&K->src, sizeof(int32_t) * 4 * (size_t)(nv + 1), st);
     if (!rc) rc = gs_alloc((void **)&K->t, sizeof(double) * 2 * (size_t)(nv + 1), st);
@@ -277,8 +285,58 @@ int gs_cons_alloc(GsCons *K, int64_t nv, cudaStream_t st)
 
 void gs_cons_free(GsCons *K, cudaStream_t st)
 {
-    gs_free(K->lev, st); gs_free(K->src, st); gs_free(K->t, st);
-    K->lev = nullptr; K->src = nullptr; K->t = nullptr;
+    gs_free(K->lev, st); gs_free(K->src, st); gs_free(K->t, st); gs_free(K->list, st);
+    K->lev = nullptr; K->src = nullptr; K->t = nullptr; K->list = nullptr;
+}
+
+__global__ void k_cons_flag(const int8_t *__restrict__ lev, int64_t nv, int l, int64_t *__restrict__ flag)
+{
+    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < nv) flag[i] = lev[i] == l;
+}
+__global__ void k_cons_group(const int64_t *__restrict__ off, int64_t nv, int32_t *__restrict__ out)
+{
+    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < nv && off[i + 1] != off[i]) out[off[i]] = (int32_t)i;
+}
+
+// the constrained vertices grouped by level, each group in vertex order
+// (a flag, scan and scatter per level)
+static int cons_list(GsCons *K, int md, cudaStream_t st)
+{
+    memset(K->loff, 0, sizeof(K->loff));
+    gs_free(K->list, st);
+    K->list = nullptr;
+    if (K->ncons <= 0) return GS_OK;
+    int64_t *flag = nullptr, *tot = nullptr;
+    int rc = gs_alloc((void **)&K->list, sizeof(int32_t) * (size_t)K->ncons, st);
+    if (!rc) rc = gs_alloc((void **)&flag, sizeof(int64_t) * (size_t)(K->nv + 1), st);
+    if (!rc) rc = gs_alloc((void **)&tot, sizeof(int64_t), st);
+    const unsigned nb = (unsigned)((K->nv + 255) / 256);
+    int64_t base = 0;
+    for (int l = 0; l < md && l < 21 && !rc; l++) {
+        K->loff[l] = base;
+        cudaMemsetAsync(flag + K->nv, 0, sizeof(int64_t), st);
+        GS_LAUNCH(k_cons_flag, nb, 256, 0, st)(K->lev, K->nv, l, flag);
+        rc = gs_scan_i64(flag, K->nv + 1, tot, st);
+        int64_t cnt = 0;
+        if (!rc) {
+            cudaError_t e = cudaMemcpyAsync(&cnt, tot, sizeof(int64_t), cudaMemcpyDeviceToHost, st);
+            if (e == cudaSuccess) e = gs_sync(st);
+            if (e != cudaSuccess) rc = gs_fail_cuda(e, "constraint groups", __FILE__, __LINE__);
+        }
+        if (!rc && base + cnt > K->ncons) rc = gs_fail(GS_ERR_DEVICE_STATUS, "constraint groups exceed their count");
+        if (!rc && cnt > 0) GS_LAUNCH(k_cons_group, nb, 256, 0, st)(flag, K->nv, K->list + base);
+        base += cnt;
+    }
+    for (int l = md < 21 ? md : 21; l < 22; l++) K->loff[l] = base;
+    gs_free(flag, st);
+    gs_free(tot, st);
+    if (!rc && base != K->ncons) rc = gs_fail(GS_ERR_DEVICE_STATUS, "constraint groups: %lld of %lld vertices",
+                                              (long long)base, (long long)K->ncons);
+    if (rc) return rc;
+    GS_CHECK(cudaGetLastError());
+    return GS_OK;
 }
 
 int gs_cons_find(GsCons *K, const GsHash &hc, const GsHash &hv, const uint64_t *d_slot_id, const uint64_t *d_vkeys,
@@ -293,7 +351,7 @@ int gs_cons_find(GsCons *K, const GsHash &hc, const GsHash &hv, const uint64_t *
     GS_CHECK(cudaMemcpyAsync(&h, d_scratch, sizeof(h), cudaMemcpyDeviceToHost, st));
     GS_CHECK(gs_sync(st));
     K->ncons = (int64_t)h;
-    return GS_OK;
+    return cons_list(K, md, st);
 }
 
 int gs_cons_apply(const GsCons &K, const GsHash &hc, const uint64_t *d_vkeys, int md, double c, double *d_phi,
@@ -303,10 +361,13 @@ int gs_cons_apply(const GsCons &K, const GsHash &hc, const uint64_t *d_vkeys, in
     if (n_flip) *n_flip = 0;
     if (K.nv <= 0 || K.ncons == 0) return GS_OK;
     if (d_split) GS_CHECK(cudaMemsetAsync(d_scratch, 0, sizeof(unsigned long long), st));
-    const unsigned nb = (unsigned)((K.nv + 255) / 256);
-    for (int l = 0; l < md; l++)
-        GS_LAUNCH(k_cons_apply, nb, 256, 0, st)(l, md, c, hc, d_vkeys, K.nv, K.lev, K.src, K.t, d_phi, d_err, d_mark,
-                                                d_split, d_scratch);
+    for (int l = 0; l < md && l < 21; l++) {
+        const int64_t n = K.loff[l + 1] - K.loff[l];
+        if (n > 0)
+            GS_LAUNCH(k_cons_apply, (unsigned)((n + 255) / 256), 256, 0, st)(l, md, c, hc, d_vkeys, K.list + K.loff[l],
+                                                                            n, K.src, K.t, d_phi, d_err, d_mark,
+                                                                            d_split, d_scratch);
+    }
     if (d_split && n_flip) {
         unsigned long long h = 0;
         GS_CHECK(cudaMemcpyAsync(&h, d_scratch, sizeof(h), cudaMemcpyDeviceToHost, st));
@@ -336,8 +397,11 @@ int gs_mixed_flags(const GsCons &K, const uint64_t *d_cubes, int64_t n, const in
 int gs_cons_mark_up(const GsCons &K, int md, int64_t *d_mark, cudaStream_t st)
 {
     if (K.nv <= 0 || K.ncons == 0) return GS_OK;
-    const unsigned nb = (unsigned)((K.nv + 255) / 256);
-    for (int l = md - 1; l >= 0; l--) GS_LAUNCH(k_cons_mark_up, nb, 256, 0, st)(l, K.nv, K.lev, K.src, d_mark);
+    for (int l = (md < 21 ? md : 21) - 1; l >= 0; l--) {
+        const int64_t n = K.loff[l + 1] - K.loff[l];
+        if (n > 0)
+            GS_LAUNCH(k_cons_mark_up, (unsigned)((n + 255) / 256), 256, 0, st)(K.list + K.loff[l], n, K.src, d_mark);
+    }
     GS_CHECK(cudaGetLastError());
     return GS_OK;
 }
@@ -358,7 +422,7 @@ int gs_field_reuse(const uint64_t *d_vkeys, int64_t n, const GsHash &hold, const
 int gs_cons_unmark(const GsCons &K, int64_t *d_mark, cudaStream_t st)
 {
     if (K.nv <= 0 || K.ncons == 0) return GS_OK;
-    GS_LAUNCH(k_cons_unmark, (unsigned)((K.nv + 255) / 256), 256, 0, st)(K.lev, K.nv, d_mark);
+    GS_LAUNCH(k_cons_unmark, (unsigned)((K.ncons + 255) / 256), 256, 0, st)(K.list, K.ncons, d_mark);
     GS_CHECK(cudaGetLastError());
     return GS_OK;
 }
@@ -366,9 +430,12 @@ int gs_cons_unmark(const GsCons &K, int64_t *d_mark, cudaStream_t st)
 int gs_cons_adjoint(const GsCons &K, int md, double *d_lambda, cudaStream_t st)
 {
     if (K.nv <= 0 || K.ncons == 0) return GS_OK;
-    const unsigned nb = (unsigned)((K.nv + 255) / 256);
-    for (int l = md - 1; l >= 0; l--)
-        GS_LAUNCH(k_cons_adjoint, nb, 256, 0, st)(l, K.nv, K.lev, K.src, K.t, d_lambda);
+    for (int l = (md < 21 ? md : 21) - 1; l >= 0; l--) {
+        const int64_t n = K.loff[l + 1] - K.loff[l];
+        if (n > 0)
+            GS_LAUNCH(k_cons_adjoint, (unsigned)((n + 255) / 256), 256, 0, st)(K.list + K.loff[l], n, K.src, K.t,
+                                                                              d_lambda);
+    }
     GS_CHECK(cudaGetLastError());
     return GS_OK;
 }

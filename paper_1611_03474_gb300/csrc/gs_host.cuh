@@ -121,6 +121,8 @@ struct GsCons {
     double *t;       // [nv][2] fractions along the edge, or along the face's axes
     int64_t nv;
     int64_t ncons;   // constrained vertices (after gs_cons_find)
+    int32_t *list;   // [ncons] the constrained vertices grouped by level (after gs_cons_find)
+    int64_t loff[22];   // level l's group: list[loff[l] .. loff[l + 1])
 };
 int gs_cons_alloc(GsCons *K, int64_t nv, cudaStream_t st);
 void gs_cons_free(GsCons *K, cudaStream_t st);

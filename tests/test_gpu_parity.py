@@ -110,7 +110,8 @@ def _assert_mesh_parity(m, ref):
     assert np.array_equal(np.sort(m.cube_keys), ref["cube_keys"])
     assert np.array_equal(np.sort(m.vertex_keys), ref["vkeys"])
     order = np.argsort(m.vertex_keys)
-    assert np.abs(m.vertices[order] - ref["vertices"]).max() < 1e-5
+    if len(order):
+        assert np.abs(m.vertices[order] - ref["vertices"]).max() < 1e-5
     assert np.array_equal(canonical_triangles(m.vertex_keys, m.triangles),
                           canonical_triangles(ref["vkeys"], ref["triangles"]))
 
@@ -135,6 +136,48 @@ def test_mesh_parity_single_atom_and_mixed_levels():
     m, ref = _mesh_both(cfg2)
     _assert_mesh_parity(m, ref)
     assert m.stats["conformity_splits"] == ref["stats"]["conformity_splits"]
+
+
+def _degenerate_cases():
+    rng = np.random.default_rng(41)
+    small = synth.config("chain100")
+    base = dict(D=0.5, c=1.0, precision=1e-3, min_edge=0.25, max_depth=3)
+    a, ra = synth.globular(150, seed=42)
+    b, rb = synth.globular(120, seed=43)
+    dup = small["xyz"][:20].copy()
+    return {
+        # root cubes only: every kept cube is forced at level 0
+        "max_depth_0": dict(base, xyz=small["xyz"], r=small["r"], max_depth=0),
+        "max_depth_1": dict(base, xyz=small["xyz"], r=small["r"], max_depth=1),
+        # deeper partition with larger root cubes (h0 = 8 A)
+        "max_depth_5": dict(base, xyz=small["xyz"][:30], r=small["r"][:30], max_depth=5),
+        # two molecules 120 A apart in one call: two closed components
+        "two_far_clusters": dict(base, xyz=np.vstack([a, b + 120.0]), r=np.concatenate([ra, rb])),
+        # coincident atoms: every atom twice (the field doubles)
+        "coincident_atoms": dict(base, xyz=np.vstack([dup, dup]), r=np.concatenate([small["r"][:20]] * 2)),
+        # a ragged count of tiny atoms far below c: no surface anywhere
+        "no_surface": dict(base, xyz=rng.uniform(0, 30, (37, 3)), r=np.full(37, 0.1), c=5.0),
+        # a non-dyadic min edge
+        "min_edge_0.3": dict(base, xyz=small["xyz"][:40], r=small["r"][:40], min_edge=0.3),
+    }
+
+
+@pytest.mark.parametrize("case", sorted(_degenerate_cases()))
+@pytest.mark.parametrize("mode", ["fp64", "mixed"])
+def test_degenerate_and_edge_inputs(case, mode):
+    """Edge cases of the method against the oracle: max_depth 0 (root cubes
+    only) and 1, a deep partition, disconnected components, coincident
+    atoms, an input without any surface, a non-dyadic min edge."""
+    cfg = _degenerate_cases()[case]
+    prec = gs.GS_PREC_FP64 if mode == "fp64" else gs.GS_PREC_MIXED
+    m, ref = _mesh_both(cfg, precision_mode=prec)
+    _assert_mesh_parity(m, ref)
+    assert m.stats["loop_errors"] == 0 and ref["stats"]["loop_errors"] == 0
+    if case == "no_surface":
+        assert len(m.triangles) == 0
+    else:
+        assert len(m.triangles) > 0
+        check_closed_manifold(m.vertices, m.triangles)
 
 
 def test_empty_surface_is_success():
