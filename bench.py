@@ -369,6 +369,11 @@ def main():
             e2e_stage = {k: est[k] for k in ("ms_total", "ms_upload", "ms_bin", "ms_levels", "ms_field",
                                              "ms_triangulate", "ms_weld", "ms_download")}
     nbytes_out = 24 * nv + 12 * nt + 8 * nv + 8 * nc
+    # the mesh of the last end-to-end step, copied out of the buffers before
+    # the link measurement below writes into them
+    mh = types.SimpleNamespace(vertices=outs[0][:nv].numpy().copy(), triangles=outs[1][:nt].numpy().copy(),
+                               vertex_keys=outs[2][:nv].numpy().view(np.uint64).copy(),
+                               cube_keys=outs[3][:nc].numpy().view(np.uint64).copy())
     # the host link itself: one 1 GiB device-to-host copy into pinned memory
     # (best of 5), the bound on the end-to-end step's copies; and one copy of
     # the vertex array's size into the step's own pinned vertex buffer
@@ -396,9 +401,6 @@ def main():
         del src, dst
     except Exception as e:  # noqa: BLE001 (reported, not fatal)
         link = {"error": str(e)[:200]}
-    mh = types.SimpleNamespace(vertices=outs[0][:nv].numpy(), triangles=outs[1][:nt].numpy(),
-                               vertex_keys=outs[2][:nv].numpy().view(np.uint64),
-                               cube_keys=outs[3][:nc].numpy().view(np.uint64))
     e2e_ms = float(np.mean(e2e_times))
 
     # FP64 form for the comparison the metric names
