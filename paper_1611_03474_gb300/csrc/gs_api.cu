@@ -802,32 +802,50 @@ static int mesh_impl(const double *atoms, const double *radii, int64_t n, double
     GsCons K{nullptr, nullptr, nullptr, 0, 0, nullptr, {0}};
     uint8_t *mixed = nullptr;
     int64_t n_mixed = 0, nre = 0;
-    // the previous round's lattice (key -> slot -> id), raw field values and bounds
-    GsHash hv_old{nullptr, nullptr, 0};
-    uint64_t *vslot_old = nullptr;
+    // after a round of splits: the new cubes (fresh), and the previous
+    // lattice's raw field values and bounds for its nv_keep vertices, which
+    // keep their ids in the extended lattice
+    uint8_t *fresh = nullptr;
     double *raw_old = nullptr;
     float *err_old = nullptr;
+    int64_t nv_keep = 0;
     auto release_all = [&](std::initializer_list<void *> ps) {
         for (void *q : ps) B.release(q);
     };
     B.keep(cubes);
     for (int iter = 0;; iter++) {
         if (iter > 64) return gs_fail(GS_ERR_CAPACITY, "cube sizes did not settle");
-        rc = gs_lattice_vertices(cubes, nc, max_depth, &vkeys, &nv, &cvid, d_status, st, constrain ? &hv : nullptr,
-                                 constrain ? &vslot : nullptr);
-        B.keep(vkeys); B.keep(cvid); B.keep(hv.keys); B.keep(hv.vals); B.keep(vslot);
+        if (!fresh) {
+            rc = gs_lattice_vertices(cubes, nc, max_depth, &vkeys, &nv, &cvid, d_status, st, constrain ? &hv : nullptr,
+                                     constrain ? &vslot : nullptr);
+            B.keep(vkeys); B.keep(cvid); B.keep(hv.keys); B.keep(hv.vals); B.keep(vslot);
+        } else {
+            // after splits: the lattice grows by the new cubes' corners
+            int64_t added = 0;
+            B.forget(vkeys); B.forget(cvid);
+            rc = gs_lattice_extend(cubes, nc, fresh, max_depth, hv, vslot, &vkeys, &nv, &cvid, &added, d_status, st);
+            B.keep(vkeys); B.keep(cvid);
+            B.release(fresh);
+            fresh = nullptr;
+        }
         if (rc) return rc;
         rc = B.get(&phi, (size_t)nv + 1);
         if (!rc && fp32) rc = B.get(&err, (size_t)nv + 1);
         if (!rc) rc = B.get(&mark, (size_t)nv + 1);
         if (rc) return rc;
-        if (hv_old.keys) {
-            // after a split: the old vertices keep their values, the new ones are evaluated
-            int64_t ndone = 0;
-            rc = gs_field_reuse(vkeys, nv, hv_old, vslot_old, raw_old, err_old, phi, err, mark, st);
-            if (!rc) rc = gs_field_partial(P, fp32 ? 1 : 0, vkeys, nv, mark, phi, err, d_cnt + 9, &ndone, st);
-            release_all({hv_old.keys, hv_old.vals, vslot_old, raw_old, err_old});
-            hv_old = GsHash{nullptr, nullptr, 0}; vslot_old = nullptr; raw_old = nullptr; err_old = nullptr;
+        if (raw_old) {
+            // the previous vertices keep their values and bounds, the new ones
+            // (appended, ids nv_keep .. nv) are evaluated
+            GS_CHECK(cudaMemcpyAsync(phi, raw_old, sizeof(double) * (size_t)nv_keep, cudaMemcpyDeviceToDevice, st));
+            if (fp32)
+                GS_CHECK(cudaMemcpyAsync(err, err_old, sizeof(float) * (size_t)nv_keep, cudaMemcpyDeviceToDevice, st));
+            const int64_t nn = nv - nv_keep;
+            if (nn > 0)
+                rc = fp32 ? gs_field_f32(P, vkeys + nv_keep, nullptr, nn, phi + nv_keep, nullptr, err + nv_keep,
+                                         d_cnt + 9, st)
+                          : gs_field_f64(P, vkeys + nv_keep, nullptr, nn, phi + nv_keep, nullptr, d_cnt + 9, st);
+            release_all({raw_old, err_old});
+            raw_old = nullptr; err_old = nullptr;
         } else if (fp32) {
             rc = gs_field_f32(P, vkeys, nullptr, nv, phi, nullptr, err, d_cnt + 9, st);
         } else {
@@ -887,19 +905,19 @@ static int mesh_impl(const double *atoms, const double *radii, int64_t n, double
         if (nflip > 0) {
             int64_t ns = 0, ns2 = 0;
             B.forget(cubes);   // replaced (and freed) by the split
-            rc = gs_split_counted(&cubes, &nc, split, &ns, st);
+            rc = gs_split_counted(&cubes, &nc, split, &ns, st, &fresh);
             B.release(split);
-            if (!rc) rc = gs_conformity(&cubes, &nc, max_depth, 2, &ns2, d_status, st);
-            B.keep(cubes);
+            if (!rc) rc = gs_conformity(&cubes, &nc, max_depth, 2, &ns2, d_status, st, &fresh);
+            B.keep(cubes); B.keep(fresh);
             if (rc) return rc;
             agree_splits += ns;
             splits += ns2;
-            // this round's lattice, raw values and bounds serve the next
-            hv_old = hv; vslot_old = vslot; raw_old = raw; err_old = raw_err;
-            release_all({vkeys, cvid, phi, err, mark, hc.keys, hc.vals, K.lev, K.src, K.t, K.list});
-            vkeys = nullptr; cvid = nullptr; phi = nullptr; err = nullptr; mark = nullptr; raw = nullptr;
-            raw_err = nullptr; vslot = nullptr;
-            hv = GsHash{nullptr, nullptr, 0}; hc = GsHash{nullptr, nullptr, 0};
+            // this round's lattice grows into the next one's; its raw values
+            // and bounds stay with its vertices
+            raw_old = raw; err_old = raw_err; nv_keep = nv;
+            release_all({phi, err, mark, hc.keys, hc.vals, K.lev, K.src, K.t, K.list});
+            phi = nullptr; err = nullptr; mark = nullptr; raw = nullptr; raw_err = nullptr;
+            hc = GsHash{nullptr, nullptr, 0};
             K = GsCons{nullptr, nullptr, nullptr, 0, 0, nullptr, {0}};
             continue;
         }

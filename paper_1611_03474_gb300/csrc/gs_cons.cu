@@ -175,24 +175,6 @@ __global__ void __launch_bounds__(256) k_cons_mark_up(const int32_t *__restrict_
         if (src[4 * i + q] >= 0) mark[src[4 * i + q]] = 1;
 }
 
-// a vertex of the new lattice that the previous one had keeps its field
-// value and bound; need[i] = 1 for the others
-__global__ void __launch_bounds__(256) k_field_reuse(const uint64_t *__restrict__ vkeys, int64_t n, GsHash hold,
-                                                     const uint64_t *__restrict__ slot_old,
-                                                     const double *__restrict__ phi_old,
-                                                     const float *__restrict__ err_old, double *__restrict__ phi,
-                                                     float *__restrict__ err, int64_t *__restrict__ need)
-{
-    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    if (i >= n) return;
-    const int64_t s = gs_hash_find(hold, vkeys[i]);
-    if (s < 0) { need[i] = 1; return; }
-    const int64_t j = (int64_t)slot_old[s];
-    phi[i] = phi_old[j];
-    if (err) err[i] = err_old[j];
-    need[i] = 0;
-}
-
 // a cube with a mixed-size contact: a constrained corner (a coarser cube
 // touches it) or a lattice vertex at an edge midpoint or face centre (a
 // finer one does)
@@ -406,18 +388,6 @@ int gs_cons_mark_up(const GsCons &K, int md, int64_t *d_mark, cudaStream_t st)
     return GS_OK;
 }
 
-int gs_field_reuse(const uint64_t *d_vkeys, int64_t n, const GsHash &hold, const uint64_t *d_slot_old,
-                   const double *d_phi_old, const float *d_err_old, double *d_phi, float *d_err, int64_t *d_need,
-                   cudaStream_t st)
-{
-    if (n <= 0) return GS_OK;
-    // d_need is scanned over n + 1 entries: the last one must be 0
-    GS_CHECK(cudaMemsetAsync(d_need + n, 0, sizeof(int64_t), st));
-    GS_LAUNCH(k_field_reuse, (unsigned)((n + 255) / 256), 256, 0, st)(d_vkeys, n, hold, d_slot_old, d_phi_old, d_err_old,
-                                                                       d_phi, d_err, d_need);
-    GS_CHECK(cudaGetLastError());
-    return GS_OK;
-}
 
 int gs_cons_unmark(const GsCons &K, int64_t *d_mark, cudaStream_t st)
 {

@@ -348,54 +348,6 @@ int gs_field_mixed(const GsProblem &P, const uint64_t *d_vkeys, int64_t n, doubl
     return GS_OK;
 }
 
-__global__ void k_field_scatter2(const double *sub_phi, const float *sub_err, const int64_t *sub_idx, int64_t m,
-                                 double *phi, float *err)
-{
-    int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    if (t >= m) return;
-    phi[sub_idx[t]] = sub_phi[t];
-    if (err) err[sub_idx[t]] = sub_err ? sub_err[t] : 0.f;
-}
-
-// the field at the vertices with need[v] = 1 only (need: n + 1 entries,
-// the last 0, scanned in place): FP64 values, or FP32 values with their bounds
-int gs_field_partial(const GsProblem &P, int fp32, const uint64_t *d_vkeys, int64_t n, int64_t *d_need, double *d_phi,
-                     float *d_err, unsigned long long *d_terms, int64_t *n_done, cudaStream_t st)
-{
-    *n_done = 0;
-    if (n <= 0) return GS_OK;
-    int64_t *tot = nullptr;
-    int rc = gs_alloc((void **)&tot, sizeof(int64_t), st);
-    if (!rc) rc = gs_scan_i64(d_need, n + 1, tot, st);
-    int64_t m = 0;
-    if (!rc) {
-        cudaError_t e = cudaMemcpyAsync(&m, tot, sizeof(int64_t), cudaMemcpyDeviceToHost, st);
-        if (e == cudaSuccess) e = gs_sync(st);
-        if (e != cudaSuccess) rc = gs_fail_cuda(e, "field count", __FILE__, __LINE__);
-    }
-    gs_free(tot, st);
-    if (!rc && m > 0) {
-        uint64_t *sk = nullptr;
-        int64_t *si = nullptr;
-        double *sp = nullptr;
-        float *se = nullptr;
-        rc = gs_alloc((void **)&sk, sizeof(uint64_t) * (size_t)m, st);
-        if (!rc) rc = gs_alloc((void **)&si, sizeof(int64_t) * (size_t)m, st);
-        if (!rc) rc = gs_alloc((void **)&sp, sizeof(double) * (size_t)m, st);
-        if (!rc && fp32) rc = gs_alloc((void **)&se, sizeof(float) * (size_t)m, st);
-        if (!rc) {
-            GS_LAUNCH(k_field_gather, (unsigned)((n + 255) / 256), 256, 0, st)(d_need, n, d_vkeys, sk, si);
-            rc = fp32 ? gs_field_f32(P, sk, nullptr, m, sp, nullptr, se, d_terms, st)
-                      : gs_field_f64(P, sk, nullptr, m, sp, nullptr, d_terms, st);
-        }
-        if (!rc) GS_LAUNCH(k_field_scatter2, (unsigned)((m + 255) / 256), 256, 0, st)(sp, se, si, m, d_phi, d_err);
-        gs_free(sk, st); gs_free(si, st); gs_free(sp, st); gs_free(se, st);
-    }
-    if (rc) return rc;
-    GS_CHECK(cudaGetLastError());
-    *n_done = m;
-    return GS_OK;
-}
 
 // mark[v] = 1 where |phi - c| is within 4 bounds (n + 1 entries, last 0)
 int gs_field_flag_near(const GsProblem &P, const double *d_phi, const float *d_err, int64_t n, int64_t *d_mark,

@@ -58,10 +58,6 @@ int gs_field_f32_marked(const GsProblem &P, const uint64_t *d_vkeys, int64_t n, 
 // re-evaluate in FP64 the vertices with mark[v] = 1 (mark: n + 1 entries, scanned in place)
 int gs_field_recompute(const GsProblem &P, const uint64_t *d_vkeys, int64_t n, int64_t *d_mark, double *d_phi,
                        float *d_err, int64_t *n_recomputed, cudaStream_t st);
-// the field at the vertices with need[v] = 1 only (need: n + 1 entries,
-// scanned in place); fp32: FP32 values and bounds (d_err), else FP64
-int gs_field_partial(const GsProblem &P, int fp32, const uint64_t *d_vkeys, int64_t n, int64_t *d_need, double *d_phi,
-                     float *d_err, unsigned long long *d_terms, int64_t *n_done, cudaStream_t st);
 // mark[v] = 1 where |phi - c| is within 4 bounds
 int gs_field_flag_near(const GsProblem &P, const double *d_phi, const float *d_err, int64_t n, int64_t *d_mark,
                        cudaStream_t st);
@@ -101,8 +97,15 @@ int gs_hash_make(GsHash *H, int64_t n, cudaStream_t st);
 void gs_hash_free(GsHash *H, cudaStream_t st);
 // min_gap: split a cube that touches one at least this many levels finer
 int gs_conformity(uint64_t **d_cubes, int64_t *n, int max_depth, int min_gap, int64_t *splits, unsigned *d_status,
-                  cudaStream_t st);
-int gs_split_counted(uint64_t **d_cubes, int64_t *n, int64_t *cnt, int64_t *splits, cudaStream_t st);
+                  cudaStream_t st, uint8_t **d_fresh = nullptr);
+int gs_split_counted(uint64_t **d_cubes, int64_t *n, int64_t *cnt, int64_t *splits, cudaStream_t st,
+                     uint8_t **d_fresh = nullptr);
+// lattice of a cube list grown by splits (fresh[ci] = 1 for the new cubes):
+// the previous vertices keep their ids, the new ones are appended; *d_vkeys
+// and *d_cvid are replaced (the old arrays freed), H and d_slot_id extended
+int gs_lattice_extend(const uint64_t *d_cubes, int64_t n, const uint8_t *d_fresh, int max_depth, const GsHash &H,
+                      uint64_t *d_slot_id, uint64_t **d_vkeys, int64_t *nv, int32_t **d_cvid, int64_t *n_added,
+                      unsigned *d_status, cudaStream_t st);
 // keep_hash (nullable): the key -> slot table of the vertices is handed over
 // (free with gs_hash_free), with *keep_slot_id mapping a slot to the vertex id
 int gs_lattice_vertices(const uint64_t *d_cubes, int64_t n, int max_depth, uint64_t **d_vkeys, int64_t *nv,
@@ -140,11 +143,7 @@ int gs_cons_apply(const GsCons &K, const GsHash &hc, const uint64_t *d_vkeys, in
                   cudaStream_t st);
 // marks on constrained vertices pass to their sources, fine to coarse
 int gs_cons_mark_up(const GsCons &K, int md, int64_t *d_mark, cudaStream_t st);
-// the vertices of a previous lattice (hash hold, slot -> id d_slot_old) keep
-// their values and bounds; d_need[i] = 1 for the others (n + 1 entries)
-int gs_field_reuse(const uint64_t *d_vkeys, int64_t n, const GsHash &hold, const uint64_t *d_slot_old,
-                   const double *d_phi_old, const float *d_err_old, double *d_phi, float *d_err, int64_t *d_need,
-                   cudaStream_t st);
+
 int gs_mixed_flags(const GsCons &K, const uint64_t *d_cubes, int64_t n, const int32_t *d_cvid, const GsHash &hv,
                    const uint64_t *d_slot_id, int md, uint8_t *d_mixed, int64_t *n_mixed,
                    unsigned long long *d_scratch, cudaStream_t st);

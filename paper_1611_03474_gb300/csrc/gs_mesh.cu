@@ -90,21 +90,32 @@ __global__ void k_fill_one(int64_t *cnt, int64_t n)
     if (i < n) cnt[i] = 1;
 }
 
-__global__ void k_conform_emit(const uint64_t *cubes, int64_t n, const int64_t *off, uint64_t *out)
+// fresh (nullable): 1 for cubes made by this or an earlier split since the
+// flags were last cleared (children 1; kept cubes carry their flag over)
+__global__ void k_conform_emit(const uint64_t *cubes, int64_t n, const int64_t *off, uint64_t *out,
+                               const uint8_t *fresh_in, uint8_t *fresh_out)
 {
     int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= n) return;
     uint64_t k = cubes[i];
     int64_t o = off[i], m = off[i + 1] - off[i];
-    if (m == 1) { out[o] = k; return; }
+    if (m == 1) {
+        out[o] = k;
+        if (fresh_out) fresh_out[o] = fresh_in ? fresh_in[i] : 0;
+        return;
+    }
     unsigned l = gk_level(k) + 1;
     int64_t x = gk_x(k), y = gk_y(k), z = gk_z(k);
-    for (int c = 0; c < 8; c++) out[o + c] = gk_make(2 * x + (c & 1), 2 * y + ((c >> 1) & 1), 2 * z + (c >> 2), GT_CUBE, l);
+    for (int c = 0; c < 8; c++) {
+        out[o + c] = gk_make(2 * x + (c & 1), 2 * y + ((c >> 1) & 1), 2 * z + (c >> 2), GT_CUBE, l);
+        if (fresh_out) fresh_out[o + c] = 1;
+    }
 }
 
 // cnt[i] = 8 splits cube i into its children, 1 keeps it (n + 1 entries,
 // scanned in place); in/out: *d_cubes (replaced when any cube splits), *n
-int gs_split_counted(uint64_t **d_cubes, int64_t *n, int64_t *cnt, int64_t *splits, cudaStream_t st)
+int gs_split_counted(uint64_t **d_cubes, int64_t *n, int64_t *cnt, int64_t *splits, cudaStream_t st,
+                     uint8_t **d_fresh)
 {
     const int64_t m = *n;
     *splits = 0;
@@ -123,11 +134,18 @@ int gs_split_counted(uint64_t **d_cubes, int64_t *n, int64_t *cnt, int64_t *spli
     gs_free(tot, st);
     if (rc || total == m) return rc;
     uint64_t *out = nullptr;
+    uint8_t *fr = nullptr;
     rc = gs_alloc((void **)&out, sizeof(uint64_t) * (size_t)total, st);
-    if (rc) return rc;
-    GS_LAUNCH(k_conform_emit, (unsigned)((m + 255) / 256), 256, 0, st)(*d_cubes, m, cnt, out);
+    if (!rc && d_fresh) rc = gs_alloc((void **)&fr, (size_t)total, st);
+    if (rc) { gs_free(out, st); return rc; }
+    GS_LAUNCH(k_conform_emit, (unsigned)((m + 255) / 256), 256, 0, st)(*d_cubes, m, cnt, out, d_fresh ? *d_fresh : nullptr,
+                                                                       fr);
     gs_free(*d_cubes, st);
     *d_cubes = out;
+    if (d_fresh) {
+        gs_free(*d_fresh, st);
+        *d_fresh = fr;
+    }
     *splits = (total - m) / 7;
     *n = total;
     GS_CHECK(cudaGetLastError());
@@ -136,7 +154,7 @@ int gs_split_counted(uint64_t **d_cubes, int64_t *n, int64_t *cnt, int64_t *spli
 
 // in/out: *d_cubes (replaced when split), *n
 int gs_conformity(uint64_t **d_cubes, int64_t *n, int max_depth, int min_gap, int64_t *splits, unsigned *d_status,
-                  cudaStream_t st)
+                  cudaStream_t st, uint8_t **d_fresh)
 {
     *splits = 0;
     (void)max_depth;
@@ -158,7 +176,7 @@ int gs_conformity(uint64_t **d_cubes, int64_t *n, int max_depth, int min_gap, in
         gs_hash_free(&H, st);
         gs_free(tot, st);
         int64_t ns = 0;
-        rc = gs_split_counted(d_cubes, n, cnt, &ns, st);
+        rc = gs_split_counted(d_cubes, n, cnt, &ns, st, d_fresh);
         gs_free(cnt, st);
         if (rc) return rc;
         if (ns == 0) return GS_OK;
@@ -259,6 +277,8 @@ int gs_lattice_vertices(const uint64_t *d_cubes, int64_t n, int max_depth, uint6
     if (!rc) rc = gs_alloc((void **)d_vkeys, sizeof(uint64_t) * (size_t)(total + 1), st);
     if (!rc) rc = gs_alloc((void **)d_cvid, sizeof(int32_t) * (size_t)m, st);
     if (!rc) {
+        // unused slots keep the sentinel ~0 (gs_lattice_extend tells new keys by it)
+        if (keep_hash) cudaMemsetAsync(slot_id, 0xFF, sizeof(uint64_t) * (size_t)(H.mask + 1), st);
         GS_LAUNCH(k_vert_write, nb, 256, 0, st)(d_cubes, n, max_depth, flag, slot, *d_vkeys, slot_id);
         GS_LAUNCH(k_vert_cvid, nb, 256, 0, st)(n, slot, slot_id, *d_cvid);
     }
@@ -274,6 +294,132 @@ int gs_lattice_vertices(const uint64_t *d_cubes, int64_t n, int max_depth, uint6
     if (rc) { gs_free(*d_vkeys, st); gs_free(*d_cvid, st); *d_vkeys = nullptr; *d_cvid = nullptr; return rc; }
     GS_CHECK(cudaGetLastError());
     *nv = total;
+    return GS_OK;
+}
+
+// ---------------------------------------------------------------- growing the lattice
+// After splits the vertex set only grows (a split cube's corners are corners
+// of its children).  gs_lattice_extend keeps the previous lattice's vertex
+// ids, appends the corners of the fresh cubes that it lacked (in the order
+// of first appearance among the fresh cubes' corners) and rebuilds the
+// corner ids of every cube by hash lookups.
+__global__ void k_fresh_flags(const uint8_t *__restrict__ fresh, int64_t n, int64_t *__restrict__ flag)
+{
+    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < n) flag[i] = fresh[i] ? 1 : 0;
+}
+__global__ void k_fresh_list(const int64_t *__restrict__ off, int64_t n, int64_t *__restrict__ list)
+{
+    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < n && off[i + 1] != off[i]) list[off[i]] = i;
+}
+// corner t of fresh cube list[t >> 3]: insert its key; vals elects the
+// smallest t among the corners claiming a slot
+__global__ void k_vert_claim_list(GsHash H, const uint64_t *__restrict__ cubes, const int64_t *__restrict__ list,
+                                  int64_t m, int max_depth, int64_t *__restrict__ slot, unsigned *status)
+{
+    const int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (t >= m * 8) return;
+    const uint64_t key = corner_key(cubes[list[t >> 3]], (int)(t & 7), max_depth);
+    const int64_t s = gs_hash_insert(H, key, status);
+    if (s >= 0) atomicMin((unsigned long long *)&H.vals[s], (unsigned long long)t);
+    slot[t] = s;
+}
+// a corner owns a new vertex when its slot had no id and it won the slot
+__global__ void k_vert_owner_new(GsHash H, int64_t m, const int64_t *__restrict__ slot,
+                                 const uint64_t *__restrict__ slot_id, int64_t *__restrict__ flag, unsigned *status)
+{
+    const int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (t >= m * 8) return;
+    const int64_t s = slot[t];
+    if (s < 0) atomicOr(status, GS_ST_LOOKUP);
+    flag[t] = (s >= 0 && slot_id[s] == ~0ull && H.vals[s] == (uint64_t)t) ? 1 : 0;
+}
+__global__ void k_vert_write_new(const uint64_t *__restrict__ cubes, const int64_t *__restrict__ list, int64_t m,
+                                 int max_depth, const int64_t *__restrict__ off, const int64_t *__restrict__ slot,
+                                 int64_t base, uint64_t *__restrict__ vkeys, uint64_t *__restrict__ slot_id)
+{
+    const int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (t >= m * 8 || off[t + 1] == off[t]) return;
+    vkeys[base + off[t]] = corner_key(cubes[list[t >> 3]], (int)(t & 7), max_depth);
+    slot_id[slot[t]] = (uint64_t)(base + off[t]);
+}
+__global__ void k_vert_cvid_find(GsHash H, const uint64_t *__restrict__ slot_id, const uint64_t *__restrict__ cubes,
+                                 int64_t n, int max_depth, int32_t *__restrict__ cvid, unsigned *status)
+{
+    const int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (t >= n * 8) return;
+    const int64_t s = gs_hash_find(H, corner_key(cubes[t >> 3], (int)(t & 7), max_depth));
+    uint64_t id = s >= 0 ? slot_id[s] : ~0ull;
+    if (id == ~0ull) {
+        atomicOr(status, GS_ST_LOOKUP);
+        id = 0;
+    }
+    cvid[t] = (int32_t)id;
+}
+
+int gs_lattice_extend(const uint64_t *d_cubes, int64_t n, const uint8_t *d_fresh, int max_depth, const GsHash &H,
+                      uint64_t *d_slot_id, uint64_t **d_vkeys, int64_t *nv, int32_t **d_cvid, int64_t *n_added,
+                      unsigned *d_status, cudaStream_t st)
+{
+    *n_added = 0;
+    int64_t *flag = nullptr, *tot = nullptr, *list = nullptr, *slot = nullptr;
+    uint64_t *vk = nullptr;
+    int32_t *cv = nullptr;
+    auto host_count = [&](int64_t *out) {
+        cudaError_t e = cudaMemcpyAsync(out, tot, sizeof(int64_t), cudaMemcpyDeviceToHost, st);
+        if (e == cudaSuccess) e = gs_sync(st);
+        return e == cudaSuccess ? GS_OK : gs_fail_cuda(e, "lattice extension", __FILE__, __LINE__);
+    };
+    int rc = gs_alloc((void **)&tot, sizeof(int64_t), st);
+    if (!rc) rc = gs_alloc((void **)&flag, sizeof(int64_t) * (size_t)(n + 1), st);
+    int64_t m = 0;
+    if (!rc) {
+        cudaMemsetAsync(flag + n, 0, sizeof(int64_t), st);
+        GS_LAUNCH(k_fresh_flags, (unsigned)((n + 255) / 256), 256, 0, st)(d_fresh, n, flag);
+        rc = gs_scan_i64(flag, n + 1, tot, st);
+    }
+    if (!rc) rc = host_count(&m);
+    if (!rc && m > 0) rc = gs_alloc((void **)&list, sizeof(int64_t) * (size_t)m, st);
+    if (!rc && m > 0) GS_LAUNCH(k_fresh_list, (unsigned)((n + 255) / 256), 256, 0, st)(flag, n, list);
+    gs_free(flag, st);
+    flag = nullptr;
+    int64_t added = 0;
+    if (!rc && m > 0) {
+        const int64_t c8 = m * 8;
+        const unsigned nb = (unsigned)((c8 + 255) / 256);
+        rc = gs_alloc((void **)&slot, sizeof(int64_t) * (size_t)c8, st);
+        if (!rc) rc = gs_alloc((void **)&flag, sizeof(int64_t) * (size_t)(c8 + 1), st);
+        if (!rc) {
+            GS_LAUNCH(k_vert_claim_list, nb, 256, 0, st)(H, d_cubes, list, m, max_depth, slot, d_status);
+            cudaMemsetAsync(flag + c8, 0, sizeof(int64_t), st);
+            GS_LAUNCH(k_vert_owner_new, nb, 256, 0, st)(H, m, slot, d_slot_id, flag, d_status);
+            rc = gs_scan_i64(flag, c8 + 1, tot, st);
+        }
+        if (!rc) rc = host_count(&added);
+        if (!rc) rc = gs_alloc((void **)&vk, sizeof(uint64_t) * (size_t)(*nv + added + 1), st);
+        if (!rc) {
+            GS_CHECK(cudaMemcpyAsync(vk, *d_vkeys, sizeof(uint64_t) * (size_t)*nv, cudaMemcpyDeviceToDevice, st));
+            if (added > 0)
+                GS_LAUNCH(k_vert_write_new, nb, 256, 0, st)(d_cubes, list, m, max_depth, flag, slot, *nv, vk,
+                                                            d_slot_id);
+        }
+    }
+    if (!rc) rc = gs_alloc((void **)&cv, sizeof(int32_t) * (size_t)(n * 8), st);
+    if (!rc)
+        GS_LAUNCH(k_vert_cvid_find, (unsigned)((n * 8 + 255) / 256), 256, 0, st)(H, d_slot_id, d_cubes, n, max_depth,
+                                                                                 cv, d_status);
+    gs_free(tot, st); gs_free(flag, st); gs_free(list, st); gs_free(slot, st);
+    if (rc) { gs_free(vk, st); gs_free(cv, st); return rc; }
+    GS_CHECK(cudaGetLastError());
+    if (vk) {
+        gs_free(*d_vkeys, st);
+        *d_vkeys = vk;
+    }
+    gs_free(*d_cvid, st);
+    *d_cvid = cv;
+    *nv += added;
+    *n_added = added;
     return GS_OK;
 }
 
