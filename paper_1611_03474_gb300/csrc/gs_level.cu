@@ -954,7 +954,10 @@ __global__ void __launch_bounds__(256) k_estimate_pre64(GsProblem P, int level, 
             double lo, hi;
             corner_range<double>(a, lo, hi);
             const double cm = 1e-12 * tot;
-            if (hi - P.c > cm && P.c - lo > cm) {
+            if (tot == 0.0) {
+                // no atom reaches the cube: the full estimate discards it
+                dec[q] = DEC_DISCARD;
+            } else if (hi - P.c > cm && P.c - lo > cm) {
                 dec[q] = (uint8_t)(high <= P.precision ? DEC_ACCEPT : (level >= P.max_depth ? DEC_FORCED : DEC_SPLIT));
                 if (P.near && fabs(P.precision - high) < GS_NEAR_REL * (P.precision + high))
                     atomicAdd(&P.near[1], 1ull);
@@ -1575,6 +1578,19 @@ __device__ __forceinline__ bool estimate_fast_f32(const GsProblem &P, int level,
     for (int t = 0; t < 64; t++) {
         tot += fabsf(a[t]);
         if ((t >> 4) >= 2 || ((t >> 2) & 3) >= 2 || (t & 3) >= 2) high += fabsf(a[t]);
+    }
+    if (tot == 0.f && E[q] == 0.f) {
+        // no atom reaches the cube: P~ = 0 and the full estimate discards it
+        // (zero bounds, no flag); common among the root cubes
+        dec[q] = DEC_DISCARD;
+        flag[q] = 0;
+        if (why_cnt) atomicAdd(&why_cnt[10], 1ull);   // decided without the SVD
+        if (dbg) {
+            float *o = dbg + 6 * q;
+            o[0] = o[1] = o[2] = o[3] = o[4] = 0.f;
+            o[5] = 2.f;   // no SVD bounds: the band check skips the cube
+        }
+        return true;
     }
     const float c = (float)P.c, prec = (float)P.precision;
     const float dA = MIXED_KAPPA * E[q] + 1e-7f * tot;
