@@ -143,6 +143,12 @@ typedef struct {
                                      sum s| against sum s; [3] lattice vertices with |value - c| < 1e-10 c.  Such
                                      a decision may differ from an independent FP64 evaluation by rounding
                                      alone (the oracle resolves them in quad precision) */
+    int64_t refine_vertices;      /* mixed mode: lattice vertex values re-evaluated in double-word FP32 (a hi + lo
+                                     float pair per value; bound about 1e-10 relative) where the FP32 bound was
+                                     too wide; recheck_vertices counts those that then went on to FP64 */
+    int64_t vertex_mark_all;      /* mixed mode: of vertex_mark_cubes, cubes with all eight corners marked */
+    int64_t vertex_mark_fp64_cubes[3]; /* mixed mode: cubes marked again with the double-word bounds (edge point,
+                                     face saddle, fold root), whose corners were re-evaluated in FP64 */
 } gs_stats;
 
 typedef struct {
@@ -347,6 +353,19 @@ int gs_bin_atoms_static(const double *atoms, int64_t n_atoms, double cell_size, 
 int gs_eval_field(const double *atoms, const double *radii, int64_t n_atoms, double D, double c,
                   double cutoff_rel, const double *points, int64_t n_points, double *phi, double *grad,
                   int precision_mode, void *stream);
+
+/*
+ * gs_eval_field_bounded -- phi at points in double-word FP32 (each value a hi
+ * + lo float pair: the evaluation the mixed mode uses where an FP32 bound is
+ * too wide), with an upper bound err[i] of |phi[i] - phi_exact| (eq Gaussian1
+ * with the truncation above; the terms are those of the FP64 form).
+ * points [n_points][3], phi [n_points] FP64, err [n_points] FP32; host or
+ * device pointers (all of one kind per array), not retained.  Needs D R^2 <=
+ * 80 (R the largest cutoff radius), else GS_ERR_ARG.
+ */
+int gs_eval_field_bounded(const double *atoms, const double *radii, int64_t n_atoms, double D, double c,
+                          double cutoff_rel, const double *points, int64_t n_points, double *phi, float *err,
+                          void *stream);
 
 /*
  * gs_cube_decisions -- coefficient tensor A (eqs polynew, tensor1, tensor2),

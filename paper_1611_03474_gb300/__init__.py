@@ -11,7 +11,7 @@ from ._native import (GS_BATCH_SHARED_LEVELS, GS_BATCH_THREADS, GS_CHILD_REEXPAN
                       GS_CONFORM_CONSTRAIN, GS_CONFORM_EQUAL, GS_NORM_MAX, GS_NORM_RSS, GS_NORM_SUM,
                       GS_ORDER_BOUNDS_FIRST, GS_ORDER_LITERAL, GS_PREC_FP64, GS_PREC_MIXED, GsError, Mesh, Stats,
                       autotune_report, autotune_reset, gs_bin_atoms, gs_bin_atoms_static, gs_cube_decisions,
-                      gs_eval_field, gs_mesh_backward, gs_mesh_intersections, gs_triangulate_grid, gs_volume_area,
+                      gs_eval_field, gs_eval_field_bounded, gs_mesh_backward, gs_mesh_intersections, gs_triangulate_grid, gs_volume_area,
                       library_path, load, memory_kind, mesh_gaussian_surface, mesh_gaussian_surface_batch,
                       mesh_gaussian_surface_into)
 
@@ -19,6 +19,6 @@ __all__ = ["GS_BATCH_SHARED_LEVELS", "GS_BATCH_THREADS", "GS_CHILD_REEXPAND", "G
            "GS_CONFORM_CONSTRAIN", "GS_CONFORM_EQUAL", "GS_NORM_MAX", "GS_NORM_RSS", "GS_NORM_SUM",
            "GS_ORDER_BOUNDS_FIRST", "GS_ORDER_LITERAL", "GS_PREC_FP64", "GS_PREC_MIXED", "GsError", "Mesh", "Stats",
            "autotune_report", "autotune_reset", "gs_bin_atoms", "gs_bin_atoms_static", "gs_cube_decisions",
-           "gs_eval_field", "gs_mesh_backward", "gs_mesh_intersections", "gs_triangulate_grid", "gs_volume_area",
+           "gs_eval_field", "gs_eval_field_bounded", "gs_mesh_backward", "gs_mesh_intersections", "gs_triangulate_grid", "gs_volume_area",
            "library_path", "load", "memory_kind", "mesh_gaussian_surface", "mesh_gaussian_surface_batch",
            "mesh_gaussian_surface_into"]

@@ -38,7 +38,8 @@ class Stats(ctypes.Structure):
                 ("recheck_rank", ctypes.c_int64), ("vertex_mark_cubes", ctypes.c_int64 * 3),
                 ("estimate_fast_cubes", ctypes.c_int64), ("constrained_vertices", ctypes.c_int64),
                 ("agreement_splits", ctypes.c_int64), ("mixed_cubes", ctypes.c_int64), ("retries", ctypes.c_int64),
-                ("near_threshold", ctypes.c_int64 * 4)]
+                ("near_threshold", ctypes.c_int64 * 4), ("refine_vertices", ctypes.c_int64),
+                ("vertex_mark_all", ctypes.c_int64), ("vertex_mark_fp64_cubes", ctypes.c_int64 * 3)]
 
     def as_dict(self, max_depth=20):
         d = {}
@@ -104,6 +105,8 @@ def load():
     L.gs_bin_atoms.restype = i32
     L.gs_eval_field.argtypes = [p, p, i64, d, d, d, p, i64, p, p, i32, p]
     L.gs_eval_field.restype = i32
+    L.gs_eval_field_bounded.argtypes = [p, p, i64, d, d, d, p, i64, p, p, p]
+    L.gs_eval_field_bounded.restype = i32
     L.gs_cube_decisions.argtypes = [p, p, i64, d, d, d, d, i32, d, p, i64, p, p, p, i32, p]
     L.gs_cube_decisions.restype = i32
     L.gs_triangulate_grid.argtypes = [i64, i64, i64, p, d, ctypes.POINTER(Options), ctypes.POINTER(MeshC)]
@@ -365,6 +368,21 @@ def gs_eval_field(atoms, radii, D, c, points, cutoff_rel=1e-8, grad=False, preci
     _check(L.gs_eval_field(_ptr(atoms), _ptr(radii), atoms.shape[0], D, c, cutoff_rel, _ptr(points), n, _ptr(phi),
                            _ptr(g), precision_mode, _stream_ptr(stream)))
     return (phi, g) if grad else phi
+
+
+def gs_eval_field_bounded(atoms, radii, D, c, points, cutoff_rel=1e-8, stream=None):
+    """(phi [n] FP64, err [n] FP32) at points [n,3]: the double-word FP32
+    evaluation with its bound on |phi - phi_exact|."""
+    L = load()
+    atoms = _host64(atoms, (-1, 3))
+    radii = _host64(radii)
+    points = _host64(points, (-1, 3))
+    n = points.shape[0]
+    phi = np.zeros(n)
+    err = np.zeros(n, dtype=np.float32)
+    _check(L.gs_eval_field_bounded(_ptr(atoms), _ptr(radii), atoms.shape[0], D, c, cutoff_rel, _ptr(points), n,
+                                   _ptr(phi), _ptr(err), _stream_ptr(stream)))
+    return phi, err
 
 
 def gs_cube_decisions(atoms, radii, D, c, precision, min_edge, max_depth, cube_keys, cutoff_rel=1e-8,

@@ -73,6 +73,9 @@ extern "C" void mesh_free(gs_mesh *m)
     memset(m, 0, sizeof(*m));
 }
 
+// device counters of one call (gs_stats fields and internal tallies)
+#define GS_NCNT 40
+
 static bool on_device(const void *p)
 {
     cudaPointerAttributes a;
@@ -91,6 +94,7 @@ static int device_setup(void)
     std::lock_guard<std::mutex> lk(g_init_mu);
     if (dev >= 0 && dev < 64 && g_dev_ready[dev]) return GS_OK;
     int rc = gs_quadrature_init();
+    if (!rc) rc = gs_field_init();
     if (rc) return rc;
     cudaMemPool_t pool;
     if (cudaDeviceGetDefaultMemPool(&pool, dev) == cudaSuccess) {
@@ -305,6 +309,7 @@ static int prepare(const double *atoms, const double *radii, int64_t n, double D
     if (!rc) rc = B.get(&S.fw, (size_t)n);
     if (!rc) rc = B.get(&S.fR2, (size_t)n);
     if (!rc) rc = B.get(&S.fr2, (size_t)n);
+    if (!rc) rc = B.get(&S.lr2, (size_t)n);
     if (rc) return rc;
     out->perm = perm;
     rc = gs_gather_atoms(perm, n, d_xyz, d_r, d_R2, d_w, P.origin, P.cell, P.cdim, &S, st);
@@ -312,6 +317,7 @@ static int prepare(const double *atoms, const double *radii, int64_t n, double D
     P.ax = S.x; P.ay = S.y; P.az = S.z; P.ar = S.r; P.aR2 = S.R2; P.aw = S.w;
     P.fx = S.fx; P.fy = S.fy; P.fz = S.fz;
     P.hx = S.hx; P.lx = S.lx; P.hy = S.hy; P.ly = S.ly; P.hz = S.hz; P.lz = S.lz; P.fw = S.fw; P.fR2 = S.fR2; P.fr2 = S.fr2;
+    P.lr2 = S.lr2;
     P.cell_start = out->cell_start;
     int t2 = T.mark();
     if (stats) {
@@ -735,13 +741,13 @@ static int mesh_impl(const double *atoms, const double *radii, int64_t n, double
     // [13] rechecked cubes, [14] mismatches, [15..17] recheck reasons, [18] error-ratio bits
     unsigned long long *d_cnt = nullptr;
     int rc = B.get(&d_status, 1);
-    if (!rc) rc = B.get(&d_cnt, 32);
+    if (!rc) rc = B.get(&d_cnt, GS_NCNT);
     if (rc) return rc;
     unsigned long long *d_near = nullptr;   // near-threshold counts (gs_stats.near_threshold)
     rc = B.get(&d_near, 4);
     if (rc) return rc;
     GS_CHECK(cudaMemsetAsync(d_status, 0, sizeof(unsigned), st));
-    GS_CHECK(cudaMemsetAsync(d_cnt, 0, 32 * sizeof(unsigned long long), st));
+    GS_CHECK(cudaMemsetAsync(d_cnt, 0, GS_NCNT * sizeof(unsigned long long), st));
     GS_CHECK(cudaMemsetAsync(d_near, 0, 4 * sizeof(unsigned long long), st));
     Prepared PR;
     if (pre) {
@@ -801,7 +807,7 @@ static int mesh_impl(const double *atoms, const double *radii, int64_t n, double
     uint64_t *vslot = nullptr;
     GsCons K{nullptr, nullptr, nullptr, 0, 0, nullptr, {0}};
     uint8_t *mixed = nullptr;
-    int64_t n_mixed = 0, nre = 0;
+    int64_t n_mixed = 0, nre = 0, ndw = 0;
     // after a round of splits: the new cubes (fresh), and the previous
     // lattice's raw field values and bounds for its nv_keep vertices, which
     // keep their ids in the extended lattice
@@ -852,11 +858,13 @@ static int mesh_impl(const double *atoms, const double *radii, int64_t n, double
             rc = gs_field_f64(P, vkeys, nullptr, nv, phi, nullptr, d_cnt + 9, st);
         }
         if (!rc && fp32) {
-            // FP64 where the inside test could depend on the FP32 error
-            int64_t n1 = 0;
+            // where the inside test could depend on the FP32 error: double-word
+            // FP32, and FP64 where that still leaves it open
+            int64_t n1 = 0, n1b = 0;
             rc = gs_field_flag_near(P, phi, err, nv, mark, st);
-            if (!rc) rc = gs_field_recompute(P, vkeys, nv, mark, phi, err, &n1, st);
-            nre += n1;
+            if (!rc) rc = gs_field_refine(P, vkeys, nv, mark, phi, err, &n1, &n1b, st);
+            ndw += n1;
+            nre += n1b;
         }
         if (rc) return rc;
         if (!constrain) break;
@@ -884,9 +892,22 @@ static int mesh_impl(const double *atoms, const double *radii, int64_t n, double
             }
             if (!rc) rc = gs_cons_mark_up(K, max_depth, mark, st);
             if (!rc) rc = gs_cons_unmark(K, mark, st);
-            int64_t n1 = 0;
-            if (!rc) rc = gs_field_recompute(P, vkeys, nv, mark, phi, err, &n1, st);
-            nre += n1;
+            int64_t n1 = 0, n1b = 0;
+            if (!rc) rc = gs_field_refine(P, vkeys, nv, mark, phi, err, &n1, &n1b, st);
+            ndw += n1;
+            nre += n1b;
+            if (!rc && n1 > n1b) {
+                // FP64 for the sources whose refined bounds still leave a side open
+                GS_CHECK(cudaMemcpyAsync(psi, phi, sizeof(double) * (size_t)nv, cudaMemcpyDeviceToDevice, st));
+                GS_CHECK(cudaMemcpyAsync(epsi, err, sizeof(float) * (size_t)nv, cudaMemcpyDeviceToDevice, st));
+                GS_CHECK(cudaMemsetAsync(mark, 0, sizeof(int64_t) * (size_t)(nv + 1), st));
+                rc = gs_cons_apply(K, hc, vkeys, max_depth, P.c, psi, epsi, mark, nullptr, nullptr, d_cnt + 27, st);
+                if (!rc) rc = gs_cons_mark_up(K, max_depth, mark, st);
+                if (!rc) rc = gs_cons_unmark(K, mark, st);
+                int64_t n1c = 0;
+                if (!rc) rc = gs_field_recompute(P, vkeys, nv, mark, phi, err, &n1c, st);
+                nre += n1c;
+            }
             release_all({psi, epsi});
         }
         // the raw field values (and bounds), kept for a later round
@@ -942,16 +963,35 @@ static int mesh_impl(const double *atoms, const double *radii, int64_t n, double
         X.cubes = cubes; X.cvid = cvid; X.phi = phi; X.ncubes = nc; X.c = P.c;
         for (int a3 = 0; a3 < 3; a3++) X.origin[a3] = P.origin[a3];
         X.min_edge = P.min_edge; X.max_depth = P.max_depth;
-        rc = gs_tri_marks(X, err, 8e-6, mark, d_cnt + 21, st);
+        // first the double-word FP32 values (a bound some 1e4 times tighter),
+        // then the same marks over the cubes that marked a corner, and FP64
+        // for what they mark again (folds near a double root, mostly)
+        int64_t *mlist = nullptr, nlist = 0;
+        rc = B.get(&mlist, (size_t)nc + 1);
+        if (!rc) rc = gs_tri_marks(X, err, 8e-6, mark, d_cnt + 32, nullptr, 0, mlist, &nlist, st);
         if (!rc && constrain) rc = gs_cons_mark_up(K, max_depth, mark, st);
         if (!rc && constrain) rc = gs_cons_unmark(K, mark, st);
-        int64_t n2 = 0;
-        if (!rc) rc = gs_field_recompute(P, vkeys, nv, mark, phi, err, &n2, st);
-        nre += n2;
+        int64_t n2 = 0, n2b = 0;
+        if (!rc) rc = gs_field_refine(P, vkeys, nv, mark, phi, err, &n2, &n2b, st);
+        ndw += n2;
+        nre += n2b;
         if (!rc && constrain)
             rc = gs_cons_apply(K, hc, vkeys, max_depth, P.c, phi, err, nullptr, nullptr, nullptr, d_cnt + 27, st);
+        if (!rc && nlist > 0) {
+            GS_CHECK(cudaMemsetAsync(mark, 0, sizeof(int64_t) * (size_t)(nv + 1), st));
+            rc = gs_tri_marks(X, err, 8e-6, mark, d_cnt + 36, mlist, nlist, nullptr, nullptr, st);
+            if (!rc && constrain) rc = gs_cons_mark_up(K, max_depth, mark, st);
+            if (!rc && constrain) rc = gs_cons_unmark(K, mark, st);
+            int64_t n3 = 0;
+            if (!rc) rc = gs_field_recompute(P, vkeys, nv, mark, phi, err, &n3, st);
+            nre += n3;
+            if (!rc && constrain && n3 > 0)
+                rc = gs_cons_apply(K, hc, vkeys, max_depth, P.c, phi, err, nullptr, nullptr, nullptr, d_cnt + 27, st);
+        }
+        B.release(mlist);
         stats->recheck_vertices = nre;
     }
+    stats->refine_vertices = ndw;
     nr_field.end();
     if (rc) return rc;
     int tf1 = T.mark();
@@ -1009,7 +1049,7 @@ static int mesh_impl(const double *atoms, const double *radii, int64_t n, double
     }
     int tend = T.mark();
     GS_CHECK(gs_sync(st));
-    unsigned long long h[32], hn[4];
+    unsigned long long h[GS_NCNT], hn[4];
     GS_CHECK(cudaMemcpy(h, d_cnt, sizeof(h), cudaMemcpyDeviceToHost));
     GS_CHECK(cudaMemcpy(hn, d_near, sizeof(hn), cudaMemcpyDeviceToHost));
     for (int k = 0; k < 4; k++) stats->near_threshold[k] = (int64_t)hn[k];
@@ -1017,7 +1057,9 @@ static int mesh_impl(const double *atoms, const double *radii, int64_t n, double
     stats->recheck_precision = (int64_t)h[16];
     stats->recheck_zero = (int64_t)h[17];
     stats->recheck_rank = (int64_t)h[20];
-    for (int k = 0; k < 3; k++) stats->vertex_mark_cubes[k] = (int64_t)h[21 + k];
+    for (int k = 0; k < 3; k++) stats->vertex_mark_cubes[k] = (int64_t)h[32 + k];
+    stats->vertex_mark_all = (int64_t)h[35];
+    for (int k = 0; k < 3; k++) stats->vertex_mark_fp64_cubes[k] = (int64_t)h[36 + k];
     stats->estimate_fast_cubes = (int64_t)h[25];
     {
         unsigned bits = (unsigned)(h[18] & 0xffffffffull);
@@ -1169,7 +1211,7 @@ static int group_levels(const std::vector<int64_t> &mols, std::vector<PreMol> &p
     unsigned long long *d_cnt = nullptr, *d_molcnt = nullptr;
     GsProblem *d_probs = nullptr;
     int rc = B.get(&d_status, 1);
-    if (!rc) rc = B.get(&d_cnt, 32);
+    if (!rc) rc = B.get(&d_cnt, GS_NCNT);
     if (!rc) rc = B.get(&d_molcnt, 5 * (size_t)G);
     if (!rc) rc = B.get(&d_probs, (size_t)G);
     unsigned long long *d_near = nullptr;
@@ -1179,7 +1221,7 @@ static int group_levels(const std::vector<int64_t> &mols, std::vector<PreMol> &p
     std::vector<GsProblem> hp((size_t)G);
     for (int g = 0; g < G; g++) hp[(size_t)g] = pm[(size_t)mols[(size_t)g]].PR.P;
     GS_CHECK(cudaMemsetAsync(d_status, 0, sizeof(unsigned), st));
-    GS_CHECK(cudaMemsetAsync(d_cnt, 0, 32 * sizeof(unsigned long long), st));
+    GS_CHECK(cudaMemsetAsync(d_cnt, 0, GS_NCNT * sizeof(unsigned long long), st));
     GS_CHECK(cudaMemcpyAsync(d_probs, hp.data(), sizeof(GsProblem) * (size_t)G, cudaMemcpyHostToDevice, st));
     // the record the shared kernels read: the group's common scalars (D, c,
     // precision, depth, order, norm); level-0 children outside a molecule's
@@ -1291,7 +1333,7 @@ static int group_levels(const std::vector<int64_t> &mols, std::vector<PreMol> &p
     }
     if (!rc) rc = check_status(d_status, st, "batch cubes");
     const int t1 = T.mark();
-    unsigned long long h[32], hn[4];
+    unsigned long long h[GS_NCNT], hn[4];
     cudaError_t e = cudaMemcpyAsync(h, d_cnt, sizeof(h), cudaMemcpyDeviceToHost, st);
     if (e == cudaSuccess) e = cudaMemcpyAsync(hn, d_near, sizeof(hn), cudaMemcpyDeviceToHost, st);
     if (e == cudaSuccess) e = gs_sync(st);
@@ -1840,6 +1882,52 @@ extern "C" int gs_eval_field(const double *atoms, const double *radii, int64_t n
             }
             if (!rc) rc = put_out(phi, d_phi, sizeof(double) * (size_t)n_points, st);
             if (!rc && grad) rc = put_out(grad, d_grad, sizeof(double) * 3 * (size_t)n_points, st);
+        }
+        if (!rc) rc = check_status(d_status, st, "field");
+    }
+    cudaError_t e = gs_sync(st);
+    if (own) cudaStreamDestroy(st);
+    if (!rc && e != cudaSuccess) rc = gs_fail_cuda(e, "stream", __FILE__, __LINE__);
+    return rc;
+}
+
+extern "C" int gs_eval_field_bounded(const double *atoms, const double *radii, int64_t n_atoms, double D, double c,
+                                     double cutoff_rel, const double *points, int64_t n_points, double *phi,
+                                     float *err, void *stream)
+{
+    if (!atoms || !radii || n_atoms <= 0 || n_atoms >= ((int64_t)1 << 31) || n_points < 0 ||
+        (n_points && (!points || !phi || !err)))
+        return gs_fail(GS_ERR_ARG, "bad sizes or NULL pointers");
+    if (!(D > 0) || !(c > 0) || !(cutoff_rel > 0 && cutoff_rel < 1)) return gs_fail(GS_ERR_ARG, "bad D, c or cutoff");
+    int rc = device_setup();
+    if (rc) return rc;
+    cudaStream_t st = (cudaStream_t)stream;
+    bool own = false;
+    if (!st) { GS_CHECK(cudaStreamCreateWithFlags(&st, cudaStreamNonBlocking)); own = true; }
+    {
+        DevBufs B(st);
+        Timer T(st);
+        unsigned *d_status = nullptr;
+        rc = B.get(&d_status, 1);
+        if (!rc) { cudaMemsetAsync(d_status, 0, sizeof(unsigned), st); }
+        Prepared PR;
+        if (!rc) rc = prepare(atoms, radii, n_atoms, D, c, cutoff_rel, 1.0, 0.25, 0, B, d_status, &PR, nullptr, T);
+        if (!rc) rc = check_fp32_range(PR.P);
+        if (!rc && n_points > 0) {
+            const double *d_pts = points;
+            double *d_phi = nullptr;
+            float *d_err = nullptr;
+            if (!on_device(points)) {
+                double *q;
+                rc = B.get(&q, 3 * (size_t)n_points);
+                if (!rc) rc = gs_copy_from_host(q, points, sizeof(double) * 3 * (size_t)n_points, st);
+                d_pts = q;
+            }
+            if (!rc) rc = B.get(&d_phi, (size_t)n_points);
+            if (!rc) rc = B.get(&d_err, (size_t)n_points);
+            if (!rc) rc = gs_field_dw(PR.P, nullptr, d_pts, n_points, d_phi, d_err, nullptr, st);
+            if (!rc) rc = put_out(phi, d_phi, sizeof(double) * (size_t)n_points, st);
+            if (!rc) rc = put_out(err, d_err, sizeof(float) * (size_t)n_points, st);
         }
         if (!rc) rc = check_status(d_status, st, "field");
     }

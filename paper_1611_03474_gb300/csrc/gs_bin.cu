@@ -97,7 +97,7 @@ __global__ void k_gather_atoms(const int32_t *__restrict__ perm, int64_t n, cons
                                float *__restrict__ fy, float *__restrict__ fz, float *__restrict__ hx,
                                float *__restrict__ lx, float *__restrict__ hy, float *__restrict__ ly,
                                float *__restrict__ hz, float *__restrict__ lz, float *__restrict__ fw,
-                               float *__restrict__ fR2, float *__restrict__ fr2)
+                               float *__restrict__ fR2, float *__restrict__ fr2, float *__restrict__ lr2)
 {
     int64_t p = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (p >= n) return;
@@ -118,7 +118,9 @@ __global__ void k_gather_atoms(const int32_t *__restrict__ perm, int64_t n, cons
     hz[p] = (float)rz; lz[p] = (float)(rz - (double)hz[p]);
     fw[p] = (float)w[i];
     fR2[p] = (float)R2[i];
-    fr2[p] = (float)(r[i] * r[i]);
+    const double rr = r[i] * r[i];
+    fr2[p] = (float)rr;
+    lr2[p] = (float)(rr - (double)fr2[p]);
 }
 
 // ---------------------------------------------------------------- host side
@@ -144,6 +146,41 @@ int gs_prep_atoms(const double *d_xyz, const double *d_r, int64_t n, double D, d
     return GS_OK;
 }
 
+int gs_sort_perm(int32_t *d_keys, int64_t n, int64_t nkeys, int32_t *d_perm, cudaStream_t st)
+{
+    if (n <= 0) return GS_OK;
+    const int passes = rs_passes(nkeys);
+    const int64_t nblk = (n + RS_TILE - 1) / RS_TILE;
+    int64_t *hist = nullptr;
+    int32_t *kb = nullptr, *vb = nullptr;
+    int rc = GS_OK;
+    if (passes > 0) {
+        rc = gs_alloc((void **)&hist, sizeof(int64_t) * (size_t)(256 * nblk + 1), st);
+        if (!rc) rc = gs_alloc((void **)&kb, sizeof(int32_t) * (size_t)n, st);
+        if (!rc) rc = gs_alloc((void **)&vb, sizeof(int32_t) * (size_t)n, st);
+    } else {
+        GS_LAUNCH(k_rs_iota, (unsigned)((n + 255) / 256), 256, 0, st)(d_perm, n);
+    }
+    int32_t *kbuf[2] = {kb, d_keys};
+    int32_t *vbuf[2];
+    vbuf[(passes - 1) & 1] = d_perm;   // the last pass writes the output
+    vbuf[passes & 1] = vb;
+    for (int p = 0; p < passes && !rc; p++) {
+        const int32_t *kin = p == 0 ? d_keys : kbuf[(p - 1) & 1];
+        int32_t *kout = p == passes - 1 ? nullptr : kbuf[p & 1];
+        const int32_t *vin = p == 0 ? nullptr : vbuf[(p - 1) & 1];
+        GS_LAUNCH(k_rs_hist<int64_t>, (unsigned)nblk, RS_THREADS, 0, st)(kin, n, 8 * p, hist, nblk);
+        rc = gs_scan_i64(hist, 256 * nblk, nullptr, st);
+        if (!rc)
+            GS_LAUNCH(k_rs_scatter<int64_t>, (unsigned)nblk, RS_THREADS, 0, st)(kin, vin, n, 8 * p, hist, nblk, kout,
+                                                                              vbuf[p & 1]);
+    }
+    gs_free(hist, st); gs_free(kb, st); gs_free(vb, st);
+    if (rc) return rc;
+    GS_CHECK(cudaGetLastError());
+    return GS_OK;
+}
+
 int gs_build_cells(const double *d_xyz, int64_t n, const double origin[3], double cell, const int cdim[3],
                    int32_t *d_cell_start, int32_t *d_perm, cudaStream_t st)
 {
@@ -162,32 +199,8 @@ int gs_build_cells(const double *d_xyz, int64_t n, const double origin[3], doubl
     if (!rc) GS_LAUNCH(k_cell_starts, (unsigned)((ncell + 1 + 255) / 256), 256, 0, st)(counts, ncell, d_cell_start);
     // atoms grouped by cell, ascending atom index within a cell: stable radix
     // passes on the cell index (time bounded by n whatever the cell sizes)
-    const int passes = rs_passes(ncell);
-    const int64_t nblk = (n + RS_TILE - 1) / RS_TILE;
-    int64_t *hist = nullptr;
-    int32_t *kb = nullptr, *vb = nullptr;
-    if (!rc && passes > 0) {
-        rc = gs_alloc((void **)&hist, sizeof(int64_t) * (size_t)(256 * nblk + 1), st);
-        if (!rc) rc = gs_alloc((void **)&kb, sizeof(int32_t) * (size_t)n, st);
-        if (!rc) rc = gs_alloc((void **)&vb, sizeof(int32_t) * (size_t)n, st);
-    }
-    if (!rc && passes == 0) GS_LAUNCH(k_rs_iota, nb, 256, 0, st)(d_perm, n);
-    int32_t *kbuf[2] = {kb, coa};
-    int32_t *vbuf[2];
-    vbuf[(passes - 1) & 1] = d_perm;   // the last pass writes the output
-    vbuf[passes & 1] = vb;
-    for (int p = 0; p < passes && !rc; p++) {
-        const int32_t *kin = p == 0 ? coa : kbuf[(p - 1) & 1];
-        int32_t *kout = p == passes - 1 ? nullptr : kbuf[p & 1];
-        const int32_t *vin = p == 0 ? nullptr : vbuf[(p - 1) & 1];
-        GS_LAUNCH(k_rs_hist<int64_t>, (unsigned)nblk, RS_THREADS, 0, st)(kin, n, 8 * p, hist, nblk);
-        rc = gs_scan_i64(hist, 256 * nblk, nullptr, st);
-        if (!rc)
-            GS_LAUNCH(k_rs_scatter<int64_t>, (unsigned)nblk, RS_THREADS, 0, st)(kin, vin, n, 8 * p, hist, nblk, kout,
-                                                                              vbuf[p & 1]);
-    }
+    if (!rc) rc = gs_sort_perm(coa, n, ncell, d_perm, st);
     gs_free(counts, st); gs_free(coa, st);
-    gs_free(hist, st); gs_free(kb, st); gs_free(vb, st);
     if (rc) return rc;
     GS_CHECK(cudaGetLastError());
     return GS_OK;
@@ -202,7 +215,7 @@ int gs_gather_atoms(const int32_t *d_perm, int64_t n, const double *d_xyz, const
                                                                  cdim[2], soa->x, soa->y, soa->z,
                                                                  soa->r, soa->R2, soa->w, soa->fx, soa->fy, soa->fz,
                                                                  soa->hx, soa->lx, soa->hy, soa->ly, soa->hz, soa->lz,
-                                                                 soa->fw, soa->fR2, soa->fr2);
+                                                                 soa->fw, soa->fR2, soa->fr2, soa->lr2);
     GS_CHECK(cudaGetLastError());
     return GS_OK;
 }

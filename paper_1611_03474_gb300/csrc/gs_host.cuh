@@ -15,12 +15,14 @@ bool gs_fault_capacity(int level);
 struct GsAtomsSoA {
     double *x, *y, *z, *r, *R2, *w;
     float *fx, *fy, *fz;
-    float *hx, *lx, *hy, *ly, *hz, *lz, *fw, *fR2, *fr2;
+    float *hx, *lx, *hy, *ly, *hz, *lz, *fw, *fR2, *fr2, *lr2;
 };
 
 // gs_bin.cu
 int gs_prep_atoms(const double *d_xyz, const double *d_r, int64_t n, double D, double KD, double *d_R2, double *d_w,
                   double bbox[6], double *r2max, unsigned *d_status, cudaStream_t st);
+// stable permutation sorting int32 keys in [0, nkeys) (d_keys is clobbered)
+int gs_sort_perm(int32_t *d_keys, int64_t n, int64_t nkeys, int32_t *d_perm, cudaStream_t st);
 int gs_build_cells(const double *d_xyz, int64_t n, const double origin[3], double cell, const int cdim[3],
                    int32_t *d_cell_start, int32_t *d_perm, cudaStream_t st);
 int gs_gather_atoms(const int32_t *d_perm, int64_t n, const double *d_xyz, const double *d_r, const double *d_R2,
@@ -56,6 +58,15 @@ int gs_field_f64(const GsProblem &P, const uint64_t *d_vkeys, const double *d_po
 int gs_field_f32_marked(const GsProblem &P, const uint64_t *d_vkeys, int64_t n, double *d_phi, float *d_err,
                         int64_t *d_mark, unsigned long long *d_terms, cudaStream_t st);
 // re-evaluate in FP64 the vertices with mark[v] = 1 (mark: n + 1 entries, scanned in place)
+// d_mark (n + 1 entries, consumed): the marked vertices re-evaluated in
+// double-word FP32 (value and bound), and those whose sign relative to c is
+// still within 4 bounds in FP64 (bound 0); *n_dw, *n_fp64 of them
+int gs_field_refine(const GsProblem &P, const uint64_t *d_vkeys, int64_t n, int64_t *d_mark, double *d_phi,
+                    float *d_err, int64_t *n_dw, int64_t *n_fp64, cudaStream_t st);
+// phi and its bound at lattice vertices (d_vkeys) or points, double-word FP32
+int gs_field_dw(const GsProblem &P, const uint64_t *d_vkeys, const double *d_points, int64_t n, double *d_phi,
+                float *d_err, unsigned long long *d_terms, cudaStream_t st);
+int gs_field_init(void);
 int gs_field_recompute(const GsProblem &P, const uint64_t *d_vkeys, int64_t n, int64_t *d_mark, double *d_phi,
                        float *d_err, int64_t *n_recomputed, cudaStream_t st);
 // mark[v] = 1 where |phi - c| is within 4 bounds
@@ -191,9 +202,11 @@ __global__ void k_hash_index(GsHash H, const uint64_t *keys, int64_t n, unsigned
 int gs_count_intersections(const double *d_v, int64_t nv, const int32_t *d_t, int64_t nt, double tol,
                            int64_t *n_pairs, cudaStream_t st);
 // d_why (nullable) counts the cubes marked through an edge point, a face
-// saddle and a fold root
+// saddle, a fold root, and of those all eight corners; d_in_list (nullable):
+// only the n_in listed cubes; d_out_list (nullable, capacity ncubes): the
+// cubes that marked a corner, *n_out of them
 int gs_tri_marks(const TriCtx &X, const float *d_err, double tol_A, int64_t *d_mark, unsigned long long *d_why,
-                 cudaStream_t st);
+                 const int64_t *d_in_list, int64_t n_in, int64_t *d_out_list, int64_t *n_out, cudaStream_t st);
 // counters: [0] cubes skipped for an inconsistency, [1] degenerate ears, [2] surface cubes
 int gs_triangulate(const TriCtx &X, uint64_t **d_tri_keys, int64_t *ntri_total, uint64_t **d_pt_keys,
                    double **d_pt_xyz, int64_t *npt_total, unsigned long long *d_counters, cudaStream_t st);

@@ -61,6 +61,7 @@ struct GsProblem {
     const float *fw;                             // exp(D r^2) in FP32
     const float *fR2;                            // cutoff^2 in FP32 (prefilters only)
     const float *fr2;                            // r^2 in FP32
+    const float *lr2;                            // r^2 - fr2 (r^2 = fr2 + lr2 to ~1e-14 relative)
     float cell_f, inv_cell_f, pad_f;             // FP32 copies for candidate enumeration
     int lat_exact_f32;                           // lattice coordinates (index * spacing) are exact in FP32
     const int32_t *cell_start;                   // [ncell + 1]

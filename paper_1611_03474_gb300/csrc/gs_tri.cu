@@ -1281,11 +1281,16 @@ int gs_triangulate(const TriCtx &X0, uint64_t **d_tri_keys, int64_t *ntri_total,
 // fold root (extreme and critical points) moves by at most the first-order
 // bound from the root's derivative.  Where any bound exceeds tol the corners
 // involved (all eight for a fold) are re-evaluated in FP64.
+// in_list (nullable): only the listed cubes; out_list (nullable): the cubes
+// that marked a corner are appended to it
 __global__ void __launch_bounds__(128) k_tri_marks(TriCtx X, const float *__restrict__ err, double tol,
-                                                   int64_t *__restrict__ mark, unsigned long long *why)
+                                                   int64_t *__restrict__ mark, unsigned long long *why,
+                                                   const int64_t *__restrict__ in_list, int64_t n_in,
+                                                   int64_t *__restrict__ out_list, unsigned long long *n_out)
 {
     int64_t ci = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    if (ci >= X.ncubes) return;
+    if (ci >= (in_list ? n_in : X.ncubes)) return;
+    if (in_list) ci = in_list[ci];
     uint64_t ck = X.cubes[ci];
     int lvl = (int)gk_level(ck);
     const float h = (float)ldexp(X.min_edge, X.max_depth - lvl);
@@ -1438,26 +1443,52 @@ __global__ void __launch_bounds__(128) k_tri_marks(TriCtx X, const float *__rest
     if (all) m = 0xFF;
     for (int v = 0; v < 8; v++)
         if ((m >> v) & 1) mark[vid[v]] = 1;
+    const unsigned act = __activemask();
+    const int leader = __ffs(act) - 1, lane = (int)(threadIdx.x & 31);
     if (why) {
-        // cubes marked through an edge point, a face saddle, a fold root (one
-        // atomic per warp and counter)
-        const unsigned act = __activemask();
+        // cubes marked through an edge point, a face saddle, a fold root, and
+        // of those all eight corners (one atomic per warp and counter)
         const unsigned b0 = __ballot_sync(act, r_edge), b1 = __ballot_sync(act, r_face),
-                       b2 = __ballot_sync(act, all || r_fold);
-        if ((int)(threadIdx.x & 31) == __ffs(act) - 1) {
+                       b2 = __ballot_sync(act, all || r_fold), b3 = __ballot_sync(act, all);
+        if (lane == leader) {
             if (b0) atomicAdd(&why[0], (unsigned long long)__popc(b0));
             if (b1) atomicAdd(&why[1], (unsigned long long)__popc(b1));
             if (b2) atomicAdd(&why[2], (unsigned long long)__popc(b2));
+            if (b3) atomicAdd(&why[3], (unsigned long long)__popc(b3));
         }
+    }
+    if (out_list) {
+        const unsigned b = __ballot_sync(act, m != 0);
+        unsigned long long base = 0;
+        if (lane == leader && b) base = atomicAdd(n_out, (unsigned long long)__popc(b));
+        base = __shfl_sync(act, base, leader);
+        if (m != 0) out_list[base + __popc(b & ((1u << lane) - 1u))] = ci;
     }
 }
 
 int gs_tri_marks(const TriCtx &X, const float *d_err, double tol_A, int64_t *d_mark, unsigned long long *d_why,
-                 cudaStream_t st)
+                 const int64_t *d_in_list, int64_t n_in, int64_t *d_out_list, int64_t *n_out, cudaStream_t st)
 {
-    if (X.ncubes <= 0) return GS_OK;
-    GS_LAUNCH(k_tri_marks, (unsigned)((X.ncubes + 127) / 128), 128, 0, st)(X, d_err, tol_A, d_mark, d_why);
+    const int64_t nt = d_in_list ? n_in : X.ncubes;
+    if (n_out) *n_out = 0;
+    if (nt <= 0) return GS_OK;
+    unsigned long long *d_n = nullptr;
+    if (d_out_list) {
+        int rc = gs_alloc((void **)&d_n, sizeof(unsigned long long), st);
+        if (rc) return rc;
+        GS_CHECK(cudaMemsetAsync(d_n, 0, sizeof(unsigned long long), st));
+    }
+    GS_LAUNCH(k_tri_marks, (unsigned)((nt + 127) / 128), 128, 0, st)(X, d_err, tol_A, d_mark, d_why, d_in_list, nt,
+                                                                    d_out_list, d_n);
     GS_CHECK(cudaGetLastError());
+    if (d_out_list) {
+        unsigned long long h = 0;
+        cudaError_t e = cudaMemcpyAsync(&h, d_n, sizeof(h), cudaMemcpyDeviceToHost, st);
+        if (e == cudaSuccess) e = gs_sync(st);
+        gs_free(d_n, st);
+        if (e != cudaSuccess) return gs_fail_cuda(e, "marked cube count", __FILE__, __LINE__);
+        if (n_out) *n_out = (int64_t)h;
+    }
     return GS_OK;
 }
 

@@ -399,3 +399,93 @@ def test_face_saddle_mark_criterion_is_sound():
         hsp = (hp[:, 0] * hp[:, 3] - hp[:, 1] * hp[:, 2]) / denp
         assert np.all((hsp < c) == (hs < c))
     assert checked > 10000
+
+
+def _dw_term(ph, pl, ah, al, fr2, lr2, Kh, Kl, L2h, L2l, tab):
+    """One double-word term 2^(K (r^2 - d^2)) in the steps the mixed mode's
+    vertex re-evaluation takes (numpy float32 rounds each operation as the
+    GPU does; an FMA is the exact product plus the addend, rounded once)."""
+    def add(a, b): return f32(f32(a) + f32(b))
+    def sub(a, b): return f32(f32(a) - f32(b))
+    def mul(a, b): return f32(f32(a) * f32(b))
+    def fma(a, b, c): return f32(np.float64(f32(a)) * np.float64(f32(b)) + np.float64(f32(c)))
+    def two_sum(a, b):
+        s = add(a, b)
+        bb = sub(s, a)
+        return s, add(sub(a, sub(s, bb)), sub(b, bb))
+    def two_prod(a, b):
+        p = mul(a, b)
+        return p, fma(a, b, -p)
+    sd = [two_sum(ph[a], -ah[a]) for a in range(3)]
+    lo = [add(sd[a][1], sub(pl[a], al[a])) for a in range(3)]
+    sq = [two_prod(sd[a][0], sd[a][0]) for a in range(3)]
+    q = [fma(add(add(sd[a][0], sd[a][0]), lo[a]), lo[a], sq[a][1]) for a in range(3)]
+    u1 = two_sum(sq[0][0], sq[1][0])
+    u2 = two_sum(u1[0], sq[2][0])
+    d2l = add(add(u1[1], u2[1]), add(add(q[0], q[1]), q[2]))
+    z = two_sum(fr2, -u2[0])
+    zl = add(z[1], sub(lr2, d2l))
+    yh = mul(Kh, z[0])
+    yl = fma(Kh, zl, fma(Kl, z[0], fma(Kh, z[0], -yh)))
+    n = f32(np.rint(yh))
+    f = sub(yh, n)
+    j = f32(np.rint(mul(f, 64)))
+    g = two_sum(sub(f, mul(j, f32(1 / 64))), yl)
+    sh = mul(L2h, g[0])
+    sl = fma(L2h, g[1], fma(L2l, g[0], fma(L2h, g[0], -sh)))
+    qq = fma(sh, fma(sh, fma(sh, f32(1 / 120), f32(1 / 24)), f32(1 / 6)), f32(0.5))
+    Q = fma(sh, sl, mul(mul(sh, sh), qq))
+    eh = add(f32(1), sh)
+    el = add(sub(sh, sub(eh, f32(1))), add(sl, Q))
+    th, tl = tab[int(j) + 32]
+    p = mul(th, eh)
+    pl2 = fma(th, el, fma(tl, eh, fma(th, eh, -p)))
+    sc = f32(2.0 ** int(n))
+    return np.longdouble(mul(p, sc)) + np.longdouble(mul(pl2, sc))
+
+
+@pytest.mark.parametrize("D", [0.5, 0.9])
+def test_double_word_term_within_its_bound(D):
+    """The double-word vertex term stays within its stated bound
+    D u^2 (90 R L + 120 R^2) + 2e-11 (u = 2^-24, L the vertex's largest
+    offset from the origin, R the cutoff radius) of the exact term, taken in
+    extended precision from the FP64 coordinates.  The random cases reach a
+    few percent of it."""
+    if np.finfo(np.longdouble).eps > 1e-18:
+        pytest.skip("needs an extended-precision long double")
+    ld = np.longdouble
+    tab = []
+    for j in range(-32, 33):
+        v = ld(2) ** (ld(j) / 64)
+        h = f32(v)
+        tab.append((h, f32(v - ld(h))))
+    K = D * 1.4426950408889634074
+    Kh = f32(K)
+    Kl = f32(K - np.float64(Kh))
+    L2h = f32(0.6931471805599453094)
+    L2l = f32(0.6931471805599453094 - np.float64(L2h))
+    rng = np.random.default_rng(int(D * 100))
+    origin = np.array([-3.0, -5.0, -7.0])
+    worst = 0.0
+    for _ in range(3000):
+        x = rng.uniform(0, 600, 3)
+        r = rng.choice([1.2, 1.7, 1.55, 1.52, 1.8])
+        R = np.sqrt(r * r - np.log(1e-8) / D)
+        dv = rng.normal(size=3)
+        p = x + dv / np.linalg.norm(dv) * rng.uniform(0, R)
+        rp, ra = p - origin, x - origin
+        ph, ah = rp.astype(f32), ra.astype(f32)
+        pl = (rp - ph.astype(np.float64)).astype(f32)
+        al = (ra - ah.astype(np.float64)).astype(f32)
+        rr = r * r
+        fr2 = f32(rr)
+        lr2 = f32(rr - np.float64(fr2))
+        t = _dw_term(ph, pl, ah, al, fr2, lr2, Kh, Kl, L2h, L2l, tab)
+        d2 = sum((ld(p[a]) - ld(x[a])) ** 2 for a in range(3))
+        exact = np.exp(-ld(D) * (d2 - ld(r) * ld(r)))
+        L = float(np.abs(ph).max())
+        bound = D * 2.0 ** -48 * (90 * R * L + 120 * R * R) + 2e-11
+        rel = abs(float((t - exact) / exact))
+        worst = max(worst, rel / bound)
+        assert rel <= bound
+    assert worst > 0.01
