@@ -977,9 +977,10 @@ __global__ void __launch_bounds__(128) k_fold_solve(TriCtx X, const uint32_t *__
 
 // first pass: trace every cube, count its output and stage it when it fits
 // Cube classes for the tracing order: cubes of one class take the same
-// branches (crossing edges, fold roots), so warps diverge less.  Class
-// 13 * min(roots, 3) + crossing edges; cubes without a surface go last.
-#define TRI_CLASSES 64
+// branches (which edges cross, how many fold roots), so warps diverge less.
+// Class 256 * min(roots, 3) + the corner sign pattern; cubes without a
+// surface go last.
+#define TRI_CLASSES 1025
 __global__ void k_tri_class(TriCtx X, int32_t *__restrict__ cls, unsigned *__restrict__ hist)
 {
     __shared__ unsigned sh[TRI_CLASSES];
@@ -991,23 +992,12 @@ __global__ void k_tri_class(TriCtx X, int32_t *__restrict__ cls, unsigned *__res
         for (int v = 0; v < 8; v++) sg |= (X.phi[X.cvid[ci * 8 + v]] >= X.c ? 1 : 0) << v;
         int k = TRI_CLASSES - 1;
         if (sg != 0 && sg != 0xFF) {
-            int ne = 0;
-            for (int a = 0; a < 3; a++) {
-                int ua, va;
-                axes_other(a, ua, va);
-                for (int e = 0; e < 4; e++) {
-                    int b0[3];
-                    b0[a] = 0; b0[ua] = e & 1; b0[va] = e >> 1;
-                    int v0 = b0[0] + 2 * b0[1] + 4 * b0[2], v1 = v0 + (1 << a);
-                    ne += ((sg >> v0) ^ (sg >> v1)) & 1;
-                }
-            }
             int nr = 0;
             if (X.fcount) {
                 uint32_t f = *reinterpret_cast<const uint32_t *>(X.fcount + ci * 4);
                 nr = (int)(f & 0xFF) + (int)((f >> 8) & 0xFF) + (int)((f >> 16) & 0xFF);
             }
-            k = 13 * (nr < 3 ? nr : 3) + ne;
+            k = 256 * (nr < 3 ? nr : 3) + sg;
         }
         cls[ci] = k;
         atomicAdd(&sh[k], 1u);
@@ -1040,10 +1030,49 @@ __global__ void k_tri_order(const int32_t *__restrict__ cls, int64_t n, unsigned
     if (k >= 0) order[base[k] + local] = (int32_t)ci;
 }
 
+// cubes grouped by class (order, n entries; nullptr when it cannot be
+// built, and then *n_surf = n); the first *n_surf have a surface
+static int tri_order(const TriCtx &X, int32_t **d_order, int64_t *n_surf, cudaStream_t st)
+{
+    const int64_t n = X.ncubes;
+    *d_order = nullptr;
+    *n_surf = n;
+    if (n <= 0 || n >= ((int64_t)1 << 31)) return GS_OK;
+    int32_t *cls = nullptr, *order = nullptr;
+    unsigned *hist = nullptr;
+    if (gs_alloc((void **)&cls, sizeof(int32_t) * (size_t)n, st) ||
+        gs_alloc((void **)&order, sizeof(int32_t) * (size_t)n, st) ||
+        gs_alloc((void **)&hist, sizeof(unsigned) * TRI_CLASSES, st)) {
+        cudaGetLastError();
+        gs_free(cls, st); gs_free(order, st); gs_free(hist, st);
+        return GS_OK;   // trace in cube order
+    }
+    const unsigned nb = (unsigned)((n + 127) / 128);
+    cudaMemsetAsync(hist, 0, sizeof(unsigned) * TRI_CLASSES, st);
+    GS_LAUNCH(k_tri_class, nb, 128, 0, st)(X, cls, hist);
+    unsigned hh[TRI_CLASSES];
+    cudaError_t e = cudaMemcpyAsync(hh, hist, sizeof(hh), cudaMemcpyDeviceToHost, st);
+    if (e == cudaSuccess) e = gs_sync(st);
+    if (e != cudaSuccess) {
+        gs_free(cls, st); gs_free(order, st); gs_free(hist, st);
+        return gs_fail_cuda(e, "cube classes", __FILE__, __LINE__);
+    }
+    unsigned acc = 0;
+    for (int k = 0; k < TRI_CLASSES; k++) { unsigned c = hh[k]; hh[k] = acc; acc += c; }
+    cudaMemcpyAsync(hist, hh, sizeof(hh), cudaMemcpyHostToDevice, st);
+    GS_LAUNCH(k_tri_order, nb, 128, 0, st)(cls, n, hist, order);
+    gs_free(cls, st);
+    gs_free(hist, st);
+    *d_order = order;
+    *n_surf = (int64_t)hh[TRI_CLASSES - 1];
+    return GS_OK;
+}
+
 // MIX: over the list of cubes with neighbours of another size (count only);
 // otherwise over all cubes, skipping those
 template <bool MIX>
-__global__ void __launch_bounds__(128) k_tri_count(TriCtx X, int64_t *__restrict__ ntri, int64_t *__restrict__ npt,
+__global__ void __launch_bounds__(128) k_tri_count(TriCtx X, int64_t n_trace, int64_t *__restrict__ ntri,
+                                                   int64_t *__restrict__ npt,
                                                    unsigned long long *errs, unsigned long long *surface,
                                                    uint64_t *st_tri, uint64_t *st_pk, double *st_xyz,
                                                    unsigned long long *degen, const int32_t *__restrict__ order,
@@ -1055,7 +1084,7 @@ __global__ void __launch_bounds__(128) k_tri_count(TriCtx X, int64_t *__restrict
         ci = mlist[ci];
         st_tri = nullptr;
     } else {
-        if (ci >= X.ncubes) return;
+        if (ci >= n_trace) return;
         if (order) ci = order[ci];
         if (X.mixed && X.mixed[ci]) return;
     }
@@ -1194,28 +1223,25 @@ int gs_triangulate(const TriCtx &X0, uint64_t **d_tri_keys, int64_t *ntri_total,
     }
     cudaMemsetAsync(ntri + n, 0, sizeof(int64_t), st);
     cudaMemsetAsync(npt + n, 0, sizeof(int64_t), st);
-    // tracing order by cube class (fewer divergent branches per warp)
-    int32_t *cls = nullptr, *order = nullptr;
-    unsigned *hist = nullptr;
-    if (n < ((int64_t)1 << 31) && !gs_alloc((void **)&cls, sizeof(int32_t) * (size_t)n, st) &&
-        !gs_alloc((void **)&order, sizeof(int32_t) * (size_t)n, st) &&
-        !gs_alloc((void **)&hist, sizeof(unsigned) * TRI_CLASSES, st)) {
-        cudaMemsetAsync(hist, 0, sizeof(unsigned) * TRI_CLASSES, st);
-        GS_LAUNCH(k_tri_class, nb, 128, 0, st)(X, cls, hist);
-        unsigned hh[TRI_CLASSES];
-        cudaMemcpyAsync(hh, hist, sizeof(hh), cudaMemcpyDeviceToHost, st);
-        gs_sync(st);
-        unsigned acc = 0;
-        for (int k = 0; k < TRI_CLASSES; k++) { unsigned c = hh[k]; hh[k] = acc; acc += c; }
-        cudaMemcpyAsync(hist, hh, sizeof(hh), cudaMemcpyHostToDevice, st);
-        GS_LAUNCH(k_tri_order, nb, 128, 0, st)(cls, n, hist, order);
-    } else {
-        cudaGetLastError();
-        gs_free(order, st);
-        order = nullptr;
+    // tracing order by cube class (fewer divergent branches per warp); the
+    // cubes without a surface come last and are not traced
+    int32_t *order = nullptr;
+    int64_t n_trace = n;
+    rc = tri_order(X, &order, &n_trace, st);
+    if (rc) {
+        gs_free(ntri, st); gs_free(npt, st); gs_free(tot, st);
+        gs_free(st_tri, st); gs_free(st_pk, st); gs_free(st_xyz, st);
+        gs_free(fcount, st); gs_free(froot, st);
+        return rc;
     }
-    GS_LAUNCH(k_tri_count<false>, nb, 128, 0, st)(X, ntri, npt, d_counters + 0, d_counters + 2, st_tri, st_pk, st_xyz,
-                                                 d_counters + 1, order, nullptr, nullptr);
+    if (order) {
+        cudaMemsetAsync(ntri, 0, sizeof(int64_t) * (size_t)n, st);
+        cudaMemsetAsync(npt, 0, sizeof(int64_t) * (size_t)n, st);
+    }
+    if (n_trace > 0)
+        GS_LAUNCH(k_tri_count<false>, (unsigned)((n_trace + 127) / 128), 128, 0, st)(
+            X, n_trace, ntri, npt, d_counters + 0, d_counters + 2, st_tri, st_pk, st_xyz, d_counters + 1, order,
+            nullptr, nullptr);
     int64_t *mlist = nullptr;
     unsigned long long *nmlist = nullptr;
     if (X.mixed) {
@@ -1224,11 +1250,11 @@ int gs_triangulate(const TriCtx &X0, uint64_t **d_tri_keys, int64_t *ntri_total,
         if (!rc) {
             cudaMemsetAsync(nmlist, 0, sizeof(unsigned long long), st);
             GS_LAUNCH(k_mixed_list, (unsigned)((n + 255) / 256), 256, 0, st)(X.mixed, n, mlist, nmlist);
-            GS_LAUNCH(k_tri_count<true>, nb, 128, 0, st)(X, ntri, npt, d_counters + 0, d_counters + 2, nullptr, nullptr,
-                                                        nullptr, d_counters + 1, nullptr, mlist, nmlist);
+            GS_LAUNCH(k_tri_count<true>, nb, 128, 0, st)(X, n, ntri, npt, d_counters + 0, d_counters + 2, nullptr,
+                                                        nullptr, nullptr, d_counters + 1, nullptr, mlist, nmlist);
         }
     }
-    gs_free(cls, st); gs_free(order, st); gs_free(hist, st);
+    gs_free(order, st);
     rc = gs_scan_i64(ntri, n + 1, tot, st);
     if (!rc) rc = gs_scan_i64(npt, n + 1, tot + 1, st);
     int64_t h[2] = {0, 0};
@@ -1281,16 +1307,18 @@ int gs_triangulate(const TriCtx &X0, uint64_t **d_tri_keys, int64_t *ntri_total,
 // fold root (extreme and critical points) moves by at most the first-order
 // bound from the root's derivative.  Where any bound exceeds tol the corners
 // involved (all eight for a fold) are re-evaluated in FP64.
-// in_list (nullable): only the listed cubes; out_list (nullable): the cubes
-// that marked a corner are appended to it
+// in_list or order (nullable): only the n_in listed cubes; out_list
+// (nullable): the cubes that marked a corner are appended to it
 __global__ void __launch_bounds__(128) k_tri_marks(TriCtx X, const float *__restrict__ err, double tol,
                                                    int64_t *__restrict__ mark, unsigned long long *why,
-                                                   const int64_t *__restrict__ in_list, int64_t n_in,
+                                                   const int64_t *__restrict__ in_list,
+                                                   const int32_t *__restrict__ order, int64_t n_in,
                                                    int64_t *__restrict__ out_list, unsigned long long *n_out)
 {
     int64_t ci = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    if (ci >= (in_list ? n_in : X.ncubes)) return;
+    if (ci >= n_in) return;
     if (in_list) ci = in_list[ci];
+    else if (order) ci = order[ci];
     uint64_t ck = X.cubes[ci];
     int lvl = (int)gk_level(ck);
     const float h = (float)ldexp(X.min_edge, X.max_depth - lvl);
@@ -1469,17 +1497,28 @@ __global__ void __launch_bounds__(128) k_tri_marks(TriCtx X, const float *__rest
 int gs_tri_marks(const TriCtx &X, const float *d_err, double tol_A, int64_t *d_mark, unsigned long long *d_why,
                  const int64_t *d_in_list, int64_t n_in, int64_t *d_out_list, int64_t *n_out, cudaStream_t st)
 {
-    const int64_t nt = d_in_list ? n_in : X.ncubes;
     if (n_out) *n_out = 0;
-    if (nt <= 0) return GS_OK;
+    // all cubes: those with a surface only, grouped by corner sign pattern
+    // (fewer divergent branches per warp)
+    int32_t *order = nullptr;
+    int64_t nt = d_in_list ? n_in : X.ncubes;
+    if (!d_in_list) {
+        int rc = tri_order(X, &order, &nt, st);
+        if (rc) return rc;
+    }
+    if (nt <= 0) {
+        gs_free(order, st);
+        return GS_OK;
+    }
     unsigned long long *d_n = nullptr;
     if (d_out_list) {
         int rc = gs_alloc((void **)&d_n, sizeof(unsigned long long), st);
-        if (rc) return rc;
+        if (rc) { gs_free(order, st); return rc; }
         GS_CHECK(cudaMemsetAsync(d_n, 0, sizeof(unsigned long long), st));
     }
-    GS_LAUNCH(k_tri_marks, (unsigned)((nt + 127) / 128), 128, 0, st)(X, d_err, tol_A, d_mark, d_why, d_in_list, nt,
-                                                                    d_out_list, d_n);
+    GS_LAUNCH(k_tri_marks, (unsigned)((nt + 127) / 128), 128, 0, st)(X, d_err, tol_A, d_mark, d_why, d_in_list, order,
+                                                                    nt, d_out_list, d_n);
+    gs_free(order, st);
     GS_CHECK(cudaGetLastError());
     if (d_out_list) {
         unsigned long long h = 0;
