@@ -714,8 +714,18 @@ __device__ void estimate_bounds(const T *A, T *out, T &rmargin)
     estimate_bounds_sens<T>(A, out, rmargin, sens);
 }
 
+// element i of four (static indices only, so that arrays stay in registers)
+template <typename T>
+__device__ __forceinline__ T sel4(int i, T a0, T a1, T a2, T a3)
+{
+    return i == 0 ? a0 : (i == 1 ? a1 : (i == 2 ? a2 : a3));
+}
+
 // rrel (nullable): the smallest distance of a rank rule from its threshold
-// relative to its own singular-value sum (outer and inner rules)
+// relative to its own singular-value sum (outer and inner rules).  The loops
+// over kept terms are rolled, each term's row picked by static selects: one
+// copy of the inner SVD and bound code instead of one per possible rank,
+// which keeps the kernel within the instruction cache.
 template <typename T>
 __device__ __forceinline__ void estimate_bounds_sens(const T *A, T *out, T &rmargin, T &sens, int fo, int fi, int fj,
                                                      RankNear<T> *rn, T *rrel)
@@ -755,12 +765,16 @@ __device__ __forceinline__ void estimate_bounds_sens(const T *A, T *out, T &rmar
     for (int t = 0; t < 64; t++) R[t] = A[t];
     T M = 0, m = 0;
     int inner = 0;
+#pragma unroll 1
     for (int i = 0; i < jr; i++) {
-        T V[4][4], d[4], w[4][4];
+        T V[4][4], d[4], w[4][4], ui[4];
 #pragma unroll
         for (int k = 0; k < 4; k++)
 #pragma unroll
-            for (int l = 0; l < 4; l++) V[k][l] = X[i][4 * k + l];
+            for (int l = 0; l < 4; l++) V[k][l] = sel4(i, X[0][4 * k + l], X[1][4 * k + l], X[2][4 * k + l], X[3][4 * k + l]);
+#pragma unroll
+        for (int a = 0; a < 4; a++) ui[a] = sel4(i, u[0][a], u[1][a], u[2][a], u[3][a]);
+        const T si0 = sel4(i, s[0], s[1], s[2], s[3]);
         jacobi4<T, 4>(V, d, w);
         T rmi;
         int ji = rank99(d, rmi);
@@ -778,38 +792,46 @@ __device__ __forceinline__ void estimate_bounds_sens(const T *A, T *out, T &rmar
         sens = si > sens ? si : sens;
         inner += ji;
         T Myz = 0, myz = 0;
+#pragma unroll 1
         for (int k = 0; k < ji; k++) {
+            T wk[4], Vk[4];
+#pragma unroll
+            for (int b = 0; b < 4; b++) {
+                wk[b] = sel4(k, w[0][b], w[1][b], w[2][b], w[3][b]);
+                Vk[b] = sel4(k, V[0][b], V[1][b], V[2][b], V[3][b]);
+            }
+            const T dk = sel4(k, d[0], d[1], d[2], d[3]);
             T ly, hy, lz, hz;
-            cubic_range(w[k], ly, hy);
-            cubic_range(V[k], lz, hz);
+            cubic_range(wk, ly, hy);
+            cubic_range(Vk, lz, hz);
             T p0 = hy * hz, p1 = hy * lz, p2 = ly * hz, p3 = ly * lz;
             T pmx = p0, pmn = p0;
             pmx = p1 > pmx ? p1 : pmx; pmn = p1 < pmn ? p1 : pmn;
             pmx = p2 > pmx ? p2 : pmx; pmn = p2 < pmn ? p2 : pmn;
             pmx = p3 > pmx ? p3 : pmx; pmn = p3 < pmn ? p3 : pmn;
-            Myz += d[k] * pmx;
-            myz += d[k] * pmn;
-            T sd = s[i] * d[k];
+            Myz += dk * pmx;
+            myz += dk * pmn;
+            T sd = si0 * dk;
 #pragma unroll
             for (int a = 0; a < 4; a++) {
-                T sa = sd * u[i][a];
+                T sa = sd * ui[a];
 #pragma unroll
                 for (int b = 0; b < 4; b++) {
-                    T sab = sa * w[k][b];
+                    T sab = sa * wk[b];
 #pragma unroll
-                    for (int cc = 0; cc < 4; cc++) R[16 * a + 4 * b + cc] -= sab * V[k][cc];
+                    for (int cc = 0; cc < 4; cc++) R[16 * a + 4 * b + cc] -= sab * Vk[cc];
                 }
             }
         }
         T lx, hx;
-        cubic_range(u[i], lx, hx);
+        cubic_range(ui, lx, hx);
         T p0 = hx * Myz, p1 = hx * myz, p2 = lx * Myz, p3 = lx * myz;
         T pmx = p0, pmn = p0;
         pmx = p1 > pmx ? p1 : pmx; pmn = p1 < pmn ? p1 : pmn;
         pmx = p2 > pmx ? p2 : pmx; pmn = p2 < pmn ? p2 : pmn;
         pmx = p3 > pmx ? p3 : pmx; pmn = p3 < pmn ? p3 : pmn;
-        M += s[i] * pmx;
-        m += s[i] * pmn;
+        M += si0 * pmx;
+        m += si0 * pmn;
     }
     T sr = 0;
 #pragma unroll
