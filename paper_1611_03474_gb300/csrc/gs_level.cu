@@ -224,8 +224,6 @@ __global__ void __launch_bounds__(32 * ACC_WARPS) k_accum_f64(GsProblem P0, int 
     __shared__ uint8_t s_qm[ACC_WARPS][ACC_Q];
     const int lane = threadIdx.x & 31, wl = threadIdx.x >> 5;
     const unsigned below = (1u << lane) - 1u;
-    const int c = lane >> 2, j = lane & 3;
-    const int cx = c & 1, cy = (c >> 1) & 1, cz = c >> 2;
     unsigned long long my_pairs = 0;
     for (int64_t o = (int64_t)blockIdx.x * ACC_WARPS + wl; o < n_oct; o += (int64_t)gridDim.x * ACC_WARPS) {
         const GsProblem &P = BATCH ? probs[mol[o]] : P0;
@@ -245,6 +243,21 @@ __global__ void __launch_bounds__(32 * ACC_WARPS) k_accum_f64(GsProblem P0, int 
         for (int t = 0; t < 16; t++) acc[t] = 0.0;
         int qn = 0;
         const uint8_t vm = q.vmask;
+        // update lanes: 4 per (accumulated child, x index); when at most four
+        // children are accumulated (a recheck of some cubes of the octet),
+        // G groups of lanes take every G-th queued atom and their sums are
+        // added at the end, so the FP64 updates issue for several atoms at once
+        const int nc = __popc(vm);
+        const int gsz = nc <= 1 ? 4 : (nc <= 2 ? 8 : (nc <= 4 ? 16 : 32)), G = 32 / gsz;
+        const int pg = lane / gsz, slot = (lane % gsz) >> 2, j = lane & 3;
+        int c = -1;
+        for (int cc = 0, k = 0; cc < 8; cc++)
+            if ((vm >> cc) & 1) {
+                if (k == slot) c = gsz == 32 ? (lane >> 2) : cc;
+                k++;
+            }
+        if (gsz == 32) c = lane >> 2;   // every child has its lanes (as without grouping)
+        const int cx = c & 1, cy = (c >> 1) & 1, cz = c >> 2;
 
         // intervals used by the selected children, per axis
         int need[3] = {0, 0, 0};
@@ -263,8 +276,8 @@ __global__ void __launch_bounds__(32 * ACC_WARPS) k_accum_f64(GsProblem P0, int 
                 s_cf[wl][lane][24] = P.aw[i];
             }
             __syncwarp();
-            for (int t = 0; t < nproc; t++) {
-                if ((s_qm[wl][t] >> c) & 1) {
+            for (int t = pg; t < nproc; t += G) {
+                if (c >= 0 && ((s_qm[wl][t] >> c) & 1)) {
                     const double *cf = s_cf[wl][t];
                     double wa = cf[24] * cf[4 * cx + j];
 #pragma unroll
@@ -340,9 +353,21 @@ __global__ void __launch_bounds__(32 * ACC_WARPS) k_accum_f64(GsProblem P0, int 
             gs_warp_candidates(P, flo, fhi, lane, filter);
             if (qn > 0) process(qn);
         }
-        double *dst = A_out + ((size_t)o * 8 + c) * 64 + 16 * j;
+        for (int off = gsz; off < 32; off <<= 1)
 #pragma unroll
-        for (int t = 0; t < 16; t++) dst[t] = acc[t];
+            for (int t = 0; t < 16; t++) acc[t] += __shfl_xor_sync(0xffffffffu, acc[t], off);
+        if (pg == 0 && c >= 0) {
+            double *dst = A_out + ((size_t)o * 8 + c) * 64 + 16 * j;
+#pragma unroll
+            for (int t = 0; t < 16; t++) dst[t] = acc[t];
+        }
+        if (gsz < 32)   // the children not accumulated hold zeros, as with one lane group
+            for (int cc = 0; cc < 8; cc++)
+                if (!((vm >> cc) & 1)) {
+                    double *z = A_out + ((size_t)o * 8 + cc) * 64;
+                    z[lane] = 0.0;
+                    z[32 + lane] = 0.0;
+                }
     }
     if (pairs) {
         for (int off = 16; off > 0; off >>= 1) my_pairs += __shfl_xor_sync(0xffffffffu, my_pairs, off);
