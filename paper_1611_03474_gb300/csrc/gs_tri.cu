@@ -977,10 +977,11 @@ __global__ void __launch_bounds__(128) k_fold_solve(TriCtx X, const uint32_t *__
 
 // first pass: trace every cube, count its output and stage it when it fits
 // Cube classes for the tracing order: cubes of one class take the same
-// branches (which edges cross, how many fold roots), so warps diverge less.
-// Class 256 * min(roots, 3) + the corner sign pattern; cubes without a
-// surface go last.
-#define TRI_CLASSES 1025
+// branches (which edges cross, how many fold roots, how many faces carry a
+// neighbour's fold ends), so warps diverge less.  Class 1024 * min(faces
+// whose neighbour has fold roots on the shared axis, 3) + 256 * min(roots,
+// 3) + the corner sign pattern; cubes without a surface go last.
+#define TRI_CLASSES 4097
 __global__ void k_tri_class(TriCtx X, int32_t *__restrict__ cls, unsigned *__restrict__ hist)
 {
     __shared__ unsigned sh[TRI_CLASSES];
@@ -992,12 +993,17 @@ __global__ void k_tri_class(TriCtx X, int32_t *__restrict__ cls, unsigned *__res
         for (int v = 0; v < 8; v++) sg |= (X.phi[X.cvid[ci * 8 + v]] >= X.c ? 1 : 0) << v;
         int k = TRI_CLASSES - 1;
         if (sg != 0 && sg != 0xFF) {
-            int nr = 0;
+            int nr = 0, nbf = 0;
             if (X.fcount) {
                 uint32_t f = *reinterpret_cast<const uint32_t *>(X.fcount + ci * 4);
                 nr = (int)(f & 0xFF) + (int)((f >> 8) & 0xFF) + (int)((f >> 16) & 0xFF);
+                if (X.nbr)
+                    for (int fc = 0; fc < 6; fc++) {
+                        const int nb = X.nbr[ci * 6 + fc];
+                        if (nb >= 0 && X.fcount[(int64_t)nb * 4 + (fc >> 1)]) nbf++;
+                    }
             }
-            k = 256 * (nr < 3 ? nr : 3) + sg;
+            k = 1024 * (nbf < 3 ? nbf : 3) + 256 * (nr < 3 ? nr : 3) + sg;
         }
         cls[ci] = k;
         atomicAdd(&sh[k], 1u);
