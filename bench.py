@@ -271,7 +271,8 @@ def main():
     ap.add_argument("--ref-half", type=float, default=6.0, help="half-width (A) of the oracle's window")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--e2e-warmup", type=int, default=2, help="untimed end-to-end calls before the timed ones")
-    ap.add_argument("--e2e-steps", type=int, default=5, help="timed end-to-end calls (host buffers, copies inside)")
+    ap.add_argument("--e2e-steps", type=int, default=5,
+                    help="timed end-to-end calls (host buffers, copies inside; at least 1)")
     ap.add_argument("--adaptive-steps", type=int, default=2,
                     help="mixed-form steps of the same assembly at precision 5e-2 (cubes on two levels)")
     ap.add_argument("--fp64-steps", type=int, default=1, help="extra FP64-form steps timed for comparison")
@@ -280,6 +281,7 @@ def main():
     ap.add_argument("--readings-steps", type=int, default=1,
                     help="steps per alternative reading (20k atoms, FP64 form) timed and compared")
     args = ap.parse_args()
+    args.e2e_steps = max(1, args.e2e_steps)   # the line's e2e needs one measured call
     ws, rank, local = dist_env()
     if args.impl == "reference":
         run_reference(args, ws, rank)
