@@ -1111,8 +1111,33 @@ __global__ void __launch_bounds__(128) k_tri_count(TriCtx X, int64_t n_trace, in
     npt[ci] = o.npt;
 }
 
-// staged cubes: copy to the scanned offsets; the others go to the list of
-// cubes traced again by k_tri_emit
+// copy the k-th element (of a warp's concatenated per-lane runs of len
+// elements, excl the exclusive prefix) from src_base + local to dst_base +
+// local, lane by lane over the total: consecutive lanes write consecutive
+// destination elements within a run
+template <typename T>
+__device__ __forceinline__ void warp_copy_runs(int len, int excl, int total, int lane, int64_t src_base,
+                                               int64_t dst_base, const T *__restrict__ src, T *__restrict__ dst)
+{
+    const unsigned full = 0xffffffffu;
+    for (int g0 = 0; g0 < total; g0 += 32) {
+        const int g = g0 + lane;
+        int owner = 0;   // the last lane whose run starts at or before g
+#pragma unroll
+        for (int step = 16; step > 0; step >>= 1) {
+            const int e = __shfl_sync(full, excl, owner + step);
+            if (e <= g) owner += step;
+        }
+        const int oe = __shfl_sync(full, excl, owner);
+        const int64_t sb = __shfl_sync(full, src_base, owner), db = __shfl_sync(full, dst_base, owner);
+        if (g < total) dst[db + (g - oe)] = src[sb + (g - oe)];
+    }
+    (void)len;
+}
+
+// staged cubes: copy to the scanned offsets, a warp's 32 cubes together
+// (coalesced stores); the others go to the list of cubes traced again by
+// k_tri_emit
 __global__ void __launch_bounds__(128) k_tri_copy(int64_t n, const int64_t *__restrict__ tri_off,
                                                   const int64_t *__restrict__ pt_off, const uint64_t *__restrict__ st_tri,
                                                   const uint64_t *__restrict__ st_pk, const double *__restrict__ st_xyz,
@@ -1120,25 +1145,36 @@ __global__ void __launch_bounds__(128) k_tri_copy(int64_t n, const int64_t *__re
                                                   double *__restrict__ pt_xyz, int64_t *__restrict__ redo,
                                                   unsigned long long *nredo, const uint8_t *__restrict__ mixed)
 {
-    int64_t ci = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    const unsigned full = 0xffffffffu;
+    const int64_t ci = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    const int lane = threadIdx.x & 31;
     bool over = false;
+    int nt = 0, np = 0;
+    int64_t t0 = 0, p0 = 0;
     if (ci < n && !(mixed && mixed[ci])) {
-        int64_t t0 = tri_off[ci], nt = tri_off[ci + 1] - t0;
-        int64_t p0 = pt_off[ci], np = pt_off[ci + 1] - p0;
-        if (nt > TRI_STAGE_T || np > TRI_STAGE_P) {
-            over = true;
-        } else {
-            for (int64_t k = 0; k < 3 * nt; k++) tri_keys[3 * t0 + k] = st_tri[3 * ci * TRI_STAGE_T + k];
-            for (int64_t k = 0; k < np; k++) pt_keys[p0 + k] = st_pk[ci * TRI_STAGE_P + k];
-            for (int64_t k = 0; k < 3 * np; k++) pt_xyz[3 * p0 + k] = st_xyz[3 * ci * TRI_STAGE_P + k];
-        }
+        t0 = tri_off[ci];
+        p0 = pt_off[ci];
+        const int64_t ntl = tri_off[ci + 1] - t0, npl = pt_off[ci + 1] - p0;
+        if (ntl > TRI_STAGE_T || npl > TRI_STAGE_P) over = true;
+        else { nt = (int)ntl; np = (int)npl; }
     }
-    unsigned bal = __ballot_sync(0xffffffffu, over);
+    // runs per lane: 3 nt triangle keys, np point keys, 3 np coordinates
+    int it = 3 * nt, ip = np;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        const int vt = __shfl_up_sync(full, it, o), vp = __shfl_up_sync(full, ip, o);
+        if (lane >= o) { it += vt; ip += vp; }
+    }
+    const int tt = __shfl_sync(full, it, 31), tp = __shfl_sync(full, ip, 31);
+    const int et = it - 3 * nt, ep = ip - np;
+    warp_copy_runs<uint64_t>(3 * nt, et, tt, lane, 3 * ci * TRI_STAGE_T, 3 * t0, st_tri, tri_keys);
+    warp_copy_runs<uint64_t>(np, ep, tp, lane, ci * TRI_STAGE_P, p0, st_pk, pt_keys);
+    warp_copy_runs<double>(3 * np, 3 * ep, 3 * tp, lane, 3 * ci * TRI_STAGE_P, 3 * p0, st_xyz, pt_xyz);
+    const unsigned bal = __ballot_sync(full, over);
     if (!bal) return;
-    unsigned lane = threadIdx.x & 31;
     unsigned long long base = 0;
     if (lane == 0) base = atomicAdd(nredo, (unsigned long long)__popc(bal));
-    base = __shfl_sync(0xffffffffu, base, 0);
+    base = __shfl_sync(full, base, 0);
     if (over) redo[base + __popc(bal & ((1u << lane) - 1u))] = ci;
 }
 
