@@ -978,7 +978,8 @@ __global__ void __launch_bounds__(128) k_fold_solve(TriCtx X, const uint32_t *__
 // first pass: trace every cube, count its output and stage it when it fits
 // Cube classes for the tracing order: cubes of one class take the same
 // branches (which edges cross, how many fold roots, how many faces carry a
-// neighbour's fold ends), so warps diverge less.  Class 1024 * min(faces
+// neighbour's fold ends; for the marks, which run before the fold table,
+// how many axes the FP32 fold screen leaves open), so warps diverge less.  Class 1024 * min(faces
 // whose neighbour has fold roots on the shared axis, 3) + 256 * min(roots,
 // 3) + the corner sign pattern; cubes without a surface go last.
 #define TRI_CLASSES 4097
@@ -990,11 +991,22 @@ __global__ void k_tri_class(TriCtx X, int32_t *__restrict__ cls, unsigned *__res
     int64_t ci = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (ci < X.ncubes) {
         int sg = 0;
-        for (int v = 0; v < 8; v++) sg |= (X.phi[X.cvid[ci * 8 + v]] >= X.c ? 1 : 0) << v;
+        double g[8];
+        for (int v = 0; v < 8; v++) {
+            g[v] = X.phi[X.cvid[ci * 8 + v]];
+            sg |= (g[v] >= X.c ? 1 : 0) << v;
+        }
         int k = TRI_CLASSES - 1;
         if (sg != 0 && sg != 0xFF) {
             int nr = 0, nbf = 0;
-            if (X.fcount) {
+            if (!X.fcount) {
+                // before the fold table (the marks): the axes whose fold
+                // quadratic the FP32 screen cannot rule out
+                float gc[8];
+                for (int v = 0; v < 8; v++) gc[v] = (float)(g[v] - X.c);
+                for (int a = 0; a < 3; a++)
+                    if (fold_faces_straddle(sg, a) && fold_may_have_roots(gc, a)) nr++;
+            } else {
                 uint32_t f = *reinterpret_cast<const uint32_t *>(X.fcount + ci * 4);
                 nr = (int)(f & 0xFF) + (int)((f >> 8) & 0xFF) + (int)((f >> 16) & 0xFF);
                 if (X.nbr)
