@@ -544,9 +544,10 @@ int gs_field_dw(const GsProblem &P, const uint64_t *d_vkeys, const double *d_poi
 }
 
 // ---------------------------------------------------------------- mixed field
-// FP32 values everywhere, FP64 re-evaluation of the vertices whose sign
-// relative to c (the inside test of the triangulation) is within the FP32
-// error bound.
+// FP32 values everywhere; where a vertex's bound leaves a decision open (its
+// sign relative to c, the inside test of the triangulation; a surface point's
+// position) the double-word re-evaluation above, and FP64 where its bound
+// still does.
 __global__ void k_field_flag(const double *phi, const float *err, int64_t n, double c, int64_t *cnt)
 {
     int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
@@ -568,67 +569,11 @@ __global__ void k_field_scatter(const double *sub_phi, const int64_t *sub_idx, i
     if (err) err[sub_idx[t]] = 0.f;
 }
 
-int gs_field_mixed(const GsProblem &P, const uint64_t *d_vkeys, int64_t n, double *d_phi, unsigned long long *d_terms,
-                   int64_t *n_rechecked, cudaStream_t st)
-{
-    *n_rechecked = 0;
-    if (n <= 0) return GS_OK;
-    float *err = nullptr;
-    int64_t *cnt = nullptr, *tot = nullptr;
-    int rc = gs_alloc((void **)&err, sizeof(float) * (size_t)n, st);
-    if (!rc) rc = gs_alloc((void **)&cnt, sizeof(int64_t) * (size_t)(n + 1), st);
-    if (!rc) rc = gs_alloc((void **)&tot, sizeof(int64_t), st);
-    if (!rc) rc = gs_field_f32(P, d_vkeys, nullptr, n, d_phi, nullptr, err, d_terms, st);
-    if (!rc) {
-        cudaMemsetAsync(cnt + n, 0, sizeof(int64_t), st);
-        GS_LAUNCH(k_field_flag, (unsigned)((n + 255) / 256), 256, 0, st)(d_phi, err, n, P.c, cnt);
-        rc = gs_scan_i64(cnt, n + 1, tot, st);
-    }
-    int64_t m = 0;
-    if (!rc) {
-        cudaError_t e = cudaMemcpyAsync(&m, tot, sizeof(int64_t), cudaMemcpyDeviceToHost, st);
-        if (e == cudaSuccess) e = gs_sync(st);
-        if (e != cudaSuccess) rc = gs_fail_cuda(e, "field recheck count", __FILE__, __LINE__);
-    }
-    if (!rc && m > 0) {
-        uint64_t *sk = nullptr;
-        int64_t *si = nullptr;
-        double *sp = nullptr;
-        rc = gs_alloc((void **)&sk, sizeof(uint64_t) * (size_t)m, st);
-        if (!rc) rc = gs_alloc((void **)&si, sizeof(int64_t) * (size_t)m, st);
-        if (!rc) rc = gs_alloc((void **)&sp, sizeof(double) * (size_t)m, st);
-        if (!rc) {
-            GS_LAUNCH(k_field_gather, (unsigned)((n + 255) / 256), 256, 0, st)(cnt, n, d_vkeys, sk, si);
-            rc = gs_field_f64(P, sk, nullptr, m, sp, nullptr, nullptr, st);
-        }
-        if (!rc) GS_LAUNCH(k_field_scatter, (unsigned)((m + 255) / 256), 256, 0, st)(sp, si, m, d_phi, nullptr);
-        gs_free(sk, st); gs_free(si, st); gs_free(sp, st);
-    }
-    gs_free(err, st); gs_free(cnt, st); gs_free(tot, st);
-    if (rc) return rc;
-    GS_CHECK(cudaGetLastError());
-    *n_rechecked = m;
-    return GS_OK;
-}
-
-
 // mark[v] = 1 where |phi - c| is within 4 bounds (n + 1 entries, last 0)
 int gs_field_flag_near(const GsProblem &P, const double *d_phi, const float *d_err, int64_t n, int64_t *d_mark,
                        cudaStream_t st)
 {
     if (n <= 0) return GS_OK;
-    cudaMemsetAsync(d_mark + n, 0, sizeof(int64_t), st);
-    GS_LAUNCH(k_field_flag, (unsigned)((n + 255) / 256), 256, 0, st)(d_phi, d_err, n, P.c, d_mark);
-    GS_CHECK(cudaGetLastError());
-    return GS_OK;
-}
-
-int gs_field_f32_marked(const GsProblem &P, const uint64_t *d_vkeys, int64_t n, double *d_phi, float *d_err,
-                        int64_t *d_mark, unsigned long long *d_terms, cudaStream_t st)
-{
-    if (n <= 0) return GS_OK;
-    int rc = gs_field_f32(P, d_vkeys, nullptr, n, d_phi, nullptr, d_err, d_terms, st);
-    if (rc) return rc;
     cudaMemsetAsync(d_mark + n, 0, sizeof(int64_t), st);
     GS_LAUNCH(k_field_flag, (unsigned)((n + 255) / 256), 256, 0, st)(d_phi, d_err, n, P.c, d_mark);
     GS_CHECK(cudaGetLastError());

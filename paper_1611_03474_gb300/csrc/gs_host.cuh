@@ -54,10 +54,6 @@ int gs_estimate_f32(const GsProblem &P, int level, const float *d_A, const float
 // gs_field.cu
 int gs_field_f64(const GsProblem &P, const uint64_t *d_vkeys, const double *d_points, int64_t n, double *d_phi,
                  double *d_grad, unsigned long long *d_terms, cudaStream_t st);
-// FP32 values and their bounds; mark[v] = 1 where |phi - c| is within 4 bounds
-int gs_field_f32_marked(const GsProblem &P, const uint64_t *d_vkeys, int64_t n, double *d_phi, float *d_err,
-                        int64_t *d_mark, unsigned long long *d_terms, cudaStream_t st);
-// re-evaluate in FP64 the vertices with mark[v] = 1 (mark: n + 1 entries, scanned in place)
 // d_mark (n + 1 entries, consumed): the marked vertices re-evaluated in
 // double-word FP32 (value and bound), and those whose sign relative to c is
 // still within 4 bounds in FP64 (bound 0); *n_dw, *n_fp64 of them
@@ -67,13 +63,12 @@ int gs_field_refine(const GsProblem &P, const uint64_t *d_vkeys, int64_t n, int6
 int gs_field_dw(const GsProblem &P, const uint64_t *d_vkeys, const double *d_points, int64_t n, double *d_phi,
                 float *d_err, unsigned long long *d_terms, cudaStream_t st);
 int gs_field_init(void);
+// re-evaluate in FP64 the vertices with mark[v] = 1 (mark: n + 1 entries, scanned in place)
 int gs_field_recompute(const GsProblem &P, const uint64_t *d_vkeys, int64_t n, int64_t *d_mark, double *d_phi,
                        float *d_err, int64_t *n_recomputed, cudaStream_t st);
 // mark[v] = 1 where |phi - c| is within 4 bounds
 int gs_field_flag_near(const GsProblem &P, const double *d_phi, const float *d_err, int64_t n, int64_t *d_mark,
                        cudaStream_t st);
-int gs_field_mixed(const GsProblem &P, const uint64_t *d_vkeys, int64_t n, double *d_phi, unsigned long long *d_terms,
-                   int64_t *n_rechecked, cudaStream_t st);
 int gs_field_f32(const GsProblem &P, const uint64_t *d_vkeys, const double *d_points, int64_t n, double *d_phi,
                  double *d_grad, float *d_err, unsigned long long *d_terms, cudaStream_t st);
 // d_A / d_nextA (optional): the level's tensors in, the split cubes' tensors
