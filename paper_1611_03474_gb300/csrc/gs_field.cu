@@ -398,7 +398,10 @@ __device__ __forceinline__ void dw_add_atom(const GsProblem &P, const double *p,
     const float zl = __fadd_rn(z.l, __fsub_rn(r2l, d2l));
     const float yh = __fmul_rn(C.Kh, z.h);
     const float yl = __fmaf_rn(C.Kh, zl, __fmaf_rn(C.Kl, z.h, __fmaf_rn(C.Kh, z.h, -yh)));
-    // 2^y = 2^nn 2^(jj/64) e^((g + yl) ln 2); yh - nn and f - jj/64 are exact
+    // 2^y = 2^nn 2^(jj/64) e^((g + yl) ln 2); yh - nn and f - jj/64 are exact.
+    // The mixed form's range check (D R^2 <= 80) keeps |y| below 116; the
+    // clamps only keep the table index and the exponent field in range for
+    // any input (a non-finite point, say)
     const float nn = fminf(fmaxf(rintf(yh), -120.f), 120.f);
     const float f = __fsub_rn(yh, nn);
     const float jj = rintf(__fmul_rn(f, 64.f));
@@ -409,7 +412,7 @@ __device__ __forceinline__ void dw_add_atom(const GsProblem &P, const double *p,
     const float Q = __fmaf_rn(sh, sl, __fmul_rn(__fmul_rn(sh, sh), q));
     const DWf E = dw_fast_two_sum(1.f, sh);
     const float el = __fadd_rn(E.l, __fadd_rn(sl, Q));
-    const float2 T = tab[(int)jj + 32];
+    const float2 T = tab[min(max((int)jj, -32), 32) + 32];
     const DWf TE = dw_two_prod(T.x, E.h);
     const float tl0 = __fmaf_rn(T.x, el, __fmaf_rn(T.y, E.h, TE.l));
     const float sc = __int_as_float(((int)nn + 127) << 23);
