@@ -15,7 +15,11 @@ operations (one rounding each) reproduce their arithmetic.
   the face-saddle criterion keeps the saddle decision.
 - The estimate's FP32 first pass (additions only, so no contraction can
   apply): its corner values of P~ lie within 64 dA + 4e-6 sum|A| of the
-  FP64 ones."""
+  FP64 ones.
+- The double-word vertex term stays within its stated bound.
+- The warp box filter of the field kernels keeps every atom one of the
+  warp's vertices accepts, and the double-word field's FP32 screen never
+  drops an FP64 member."""
 import numpy as np
 import pytest
 
@@ -489,3 +493,76 @@ def test_double_word_term_within_its_bound(D):
         worst = max(worst, rel / bound)
         assert rel <= bound
     assert worst > 0.01
+
+
+def _split2(x):
+    """offsets from the origin as hi + lo floats, as the kernels store them"""
+    h = x.astype(f32)
+    return h, (x - h.astype(np.float64)).astype(f32)
+
+
+@pytest.mark.parametrize("scale", [100.0, 60000.0])
+def test_warp_box_filter_keeps_every_accepted_atom(scale):
+    """The field kernels stage an atom for a warp only if its cutoff sphere
+    reaches the box of the warp's vertices (hi parts only; gaps lowered by
+    1e-3 A + 4e-7 |x|, sphere grown by 1% + 0.01 A^2).  Every atom that one
+    of the warp's vertices accepts, by the FP32 test of the FP32 field or by
+    the FP64 membership of the FP64 and double-word fields, must pass."""
+    rng = np.random.default_rng(int(scale))
+    kept = rejected = 0
+    for _ in range(300):
+        centre = rng.uniform(0.2 * scale, scale, 3)
+        verts = centre + rng.uniform(0, 2.5, (32, 3))
+        R2 = rng.uniform(20.0, 60.0)
+        dirs = rng.normal(size=(64, 3))
+        dirs /= np.linalg.norm(dirs, axis=1)[:, None]
+        atoms = centre + 1.25 + dirs * rng.uniform(0.0, np.sqrt(R2) + 3.0, 64)[:, None]
+        ph, pl = _split2(verts)
+        ah, al = _split2(atoms)
+        lo, hi = ph.min(axis=0), ph.max(axis=0)
+        fR2 = f32(R2)
+        for k in range(len(atoms)):
+            g2 = f32(0)
+            for a in range(3):
+                x = ah[k, a]
+                gap = max(f32(lo[a] - x), f32(x - hi[a]))
+                slack = f32(np.float64(f32(4e-7)) * np.float64(abs(x)) + np.float64(f32(1e-3)))
+                g = max(f32(0), f32(gap - slack))
+                g2 = f32(g2 + f32(g * g))
+            passes = g2 <= f32(np.float64(fR2) * np.float64(f32(1.01)) + np.float64(f32(0.01)))
+            d = (ph - ah[k]).astype(f32) + (pl - al[k]).astype(f32)
+            d2_32 = (d[:, 0] * d[:, 0] + d[:, 1] * d[:, 1] + d[:, 2] * d[:, 2]).astype(f32)
+            d2_64 = ((verts - atoms[k]) ** 2).sum(axis=1)
+            accepted = bool(np.any(d2_32 <= fR2) or np.any(d2_64 <= R2))
+            if accepted:
+                assert passes
+            kept += passes
+            rejected += not passes
+    assert rejected > 0.1 * (kept + rejected)   # the filter does drop atoms out of reach
+
+
+def test_double_word_screen_never_drops_a_member():
+    """The double-word field screens a candidate with the FP32 distance from
+    the two-float offsets: beyond R^2 (1 + 1e-5) + 1e-5 it is out, below
+    R^2 (1 - 1e-5) - 1e-5 it is in, and between the exact FP64 test decides.
+    So no FP64 member is screened out and every atom taken without the FP64
+    test is an FP64 member, for offsets up to thousands of A."""
+    rng = np.random.default_rng(11)
+    for scale in (50.0, 5000.0):
+        for _ in range(20000):
+            atom = rng.uniform(0.2 * scale, scale, 3)
+            R2 = rng.uniform(20.0, 60.0)
+            u = rng.normal(size=3)
+            u /= np.linalg.norm(u)
+            d = np.sqrt(R2) * (1.0 + rng.choice([-1, 1]) * 10.0 ** rng.uniform(-9, -3))
+            p = atom + u * d
+            ph, pl = _split2(p)
+            ah, al = _split2(atom)
+            f = (ph - ah).astype(f32) + (pl - al).astype(f32)
+            f2 = f32(f32(f32(f[0] * f[0]) + f32(f[1] * f[1])) + f32(f[2] * f[2]))
+            fR2 = f32(R2)
+            member = ((p - atom) ** 2).sum() <= R2
+            out = f2 > f32(f32(fR2 * f32(1.0 + 1e-5)) + f32(1e-5))
+            sure_in = f2 < f32(f32(fR2 * f32(1.0 - 1e-5)) - f32(1e-5))
+            assert not (member and out)
+            assert not (sure_in and not member)
