@@ -983,6 +983,7 @@ __global__ void __launch_bounds__(128) k_fold_solve(TriCtx X, const uint32_t *__
 // whose neighbour has fold roots on the shared axis, 3) + 256 * min(roots,
 // 3) + the corner sign pattern; cubes without a surface go last.
 #define TRI_CLASSES 4097
+static_assert(1024 * 3 + 256 * 3 + 255 < TRI_CLASSES - 1, "surface classes stay below the last (no surface)");
 __global__ void k_tri_class(TriCtx X, int32_t *__restrict__ cls, unsigned *__restrict__ hist)
 {
     __shared__ unsigned sh[TRI_CLASSES];
